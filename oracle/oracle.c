@@ -1,0 +1,1034 @@
+/*
+ * CPU oracle for the scaled-ILU Richardson smoother.
+ *
+ * TEST INFRASTRUCTURE.  This file is the plain, slow, single-threaded FP64
+ * statement of what the smoother computes, written step by step from
+ * Thomas, Carr, Mullowney, Swirydowicz and Day, "Scaled ILU Smoothers for
+ * Navier-Stokes Pressure Projection" (arXiv 2111.09512).  Only the tests, the
+ * smoke check and the benchmark's CPU-baseline leg use it.  It shares no code
+ * with the CUDA library and must be compiled with -ffp-contract=off so that
+ * every multiply and add rounds separately, in the order written here.
+ *
+ * Conventions.  CSR with int64 row pointers, int32 column indices sorted
+ * ascending within each row, FP64 values.  Vectors with R right-hand sides
+ * are row-major n x R (the R values of one row are adjacent).
+ *
+ * Factors.  L is unit lower triangular, L = I + L_s; only L_s is stored.  U is
+ * upper triangular with its diagonal stored first in each row.  After row
+ * scaling (Eq. extractD, Eq. newD) Utilde = D^{-1} U = I + Utilde_s; only
+ * Utilde_s and dinv = 1 / diag(U) are stored.
+ *
+ * Parity pins for every function live in tests/test_oracle_*.py.  Unpinned
+ * parts: none of the functions here is left without a pin, but the ILUT drop
+ * rule (Saad's dual threshold, which the paper uses without defining it) is
+ * pinned only through its limiting cases and stated invariants.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_BADARG 1
+#define ORC_ZERO_PIVOT 2
+#define ORC_NOT_CONVERGED 3
+#define ORC_NOMEM 4
+
+typedef struct orc_lu {
+  int64_t n;
+  int64_t* lp; /* strict lower part of L, n+1 row pointers */
+  int32_t* lc;
+  double* lv;
+  int64_t* up; /* U with its diagonal first in each row */
+  int32_t* uc;
+  double* uv;
+} orc_lu;
+
+/* ------------------------------------------------------------------------ */
+/* small helpers: growable arrays and a binary min-heap of column indices    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t* c;
+  double* v;
+  int64_t len, cap;
+} rowbuf;
+
+static int rb_push(rowbuf* b, int32_t c, double v) {
+  if (b->len == b->cap) {
+    int64_t cap = b->cap ? 2 * b->cap : 1024;
+    int32_t* nc = (int32_t*)realloc(b->c, sizeof(int32_t) * (size_t)cap);
+    if (!nc) return 0;
+    b->c = nc;
+    double* nv = (double*)realloc(b->v, sizeof(double) * (size_t)cap);
+    if (!nv) return 0;
+    b->v = nv;
+    b->cap = cap;
+  }
+  b->c[b->len] = c;
+  b->v[b->len] = v;
+  b->len++;
+  return 1;
+}
+
+typedef struct {
+  int32_t* h;
+  int64_t len;
+} minheap;
+
+static void heap_push(minheap* q, int32_t x) {
+  int64_t i = q->len++;
+  q->h[i] = x;
+  while (i > 0) {
+    int64_t p = (i - 1) / 2;
+    if (q->h[p] <= q->h[i]) break;
+    int32_t t = q->h[p];
+    q->h[p] = q->h[i];
+    q->h[i] = t;
+    i = p;
+  }
+}
+
+static int32_t heap_pop(minheap* q) {
+  int32_t top = q->h[0];
+  q->h[0] = q->h[--q->len];
+  int64_t i = 0;
+  for (;;) {
+    int64_t l = 2 * i + 1, r = l + 1, m = i;
+    if (l < q->len && q->h[l] < q->h[m]) m = l;
+    if (r < q->len && q->h[r] < q->h[m]) m = r;
+    if (m == i) break;
+    int32_t t = q->h[m];
+    q->h[m] = q->h[i];
+    q->h[i] = t;
+    i = m;
+  }
+  return top;
+}
+
+static int cmp_i32(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+static orc_lu* lu_from_rows(int64_t n, rowbuf* L, rowbuf* U, const int64_t* lrow, const int64_t* urow) {
+  orc_lu* f = (orc_lu*)calloc(1, sizeof(orc_lu));
+  if (!f) return NULL;
+  f->n = n;
+  f->lp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  f->up = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  if (!f->lp || !f->up) {
+    free(f->lp);
+    free(f->up);
+    free(f);
+    return NULL;
+  }
+  memcpy(f->lp, lrow, sizeof(int64_t) * (size_t)(n + 1));
+  memcpy(f->up, urow, sizeof(int64_t) * (size_t)(n + 1));
+  f->lc = L->c;
+  f->lv = L->v;
+  f->uc = U->c;
+  f->uv = U->v;
+  /* keep non-NULL pointers for empty factors */
+  if (!f->lc) f->lc = (int32_t*)malloc(sizeof(int32_t));
+  if (!f->lv) f->lv = (double*)malloc(sizeof(double));
+  if (!f->uc) f->uc = (int32_t*)malloc(sizeof(int32_t));
+  if (!f->uv) f->uv = (double*)malloc(sizeof(double));
+  return f;
+}
+
+void orc_lu_free(orc_lu* f) {
+  if (!f) return;
+  free(f->lp);
+  free(f->lc);
+  free(f->lv);
+  free(f->up);
+  free(f->uc);
+  free(f->uv);
+  free(f);
+}
+
+void orc_lu_nnz(const orc_lu* f, int64_t* nl, int64_t* nu) {
+  *nl = f->lp[f->n];
+  *nu = f->up[f->n];
+}
+
+void orc_lu_copy(const orc_lu* f, int64_t* lp, int32_t* lc, double* lv, int64_t* up, int32_t* uc, double* uv) {
+  const int64_t n = f->n;
+  memcpy(lp, f->lp, sizeof(int64_t) * (size_t)(n + 1));
+  memcpy(up, f->up, sizeof(int64_t) * (size_t)(n + 1));
+  memcpy(lc, f->lc, sizeof(int32_t) * (size_t)f->lp[n]);
+  memcpy(lv, f->lv, sizeof(double) * (size_t)f->lp[n]);
+  memcpy(uc, f->uc, sizeof(int32_t) * (size_t)f->up[n]);
+  memcpy(uv, f->uv, sizeof(double) * (size_t)f->up[n]);
+}
+
+/* CSR sanity: monotone row pointers, in-range strictly ascending columns */
+static int csr_ok(int64_t n, const int64_t* rp, const int32_t* ci) {
+  if (n < 0 || !rp || rp[0] != 0) return 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (rp[i + 1] < rp[i]) return 0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      if (ci[p] < 0 || ci[p] >= n) return 0;
+      if (p > rp[i] && ci[p] <= ci[p - 1]) return 0;
+    }
+  }
+  return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* ILU on a fixed pattern (the numeric phase of ILU(0) and ILU(k))           */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Numeric incomplete LU on the pattern P (row pointer pp, columns pc, which
+ * contains the pattern of A).  IKJ elimination over row i, Saad, "Iterative
+ * Methods for Sparse Linear Systems", the variant the paper names for ILU(0)
+ * (Matlab ilu with setup type 'nofill', pivoting off, Sec. 3.2):
+ *   for k < i in P(i), ascending:  a_ik <- a_ik / a_kk
+ *                                  a_ij <- a_ij - a_ik * a_kj  for j > k, j in P(i) and P(k)
+ */
+static orc_lu* ilu_on_pattern(int64_t n, const int64_t* rp, const int32_t* ci, const double* va, const int64_t* pp,
+                              const int32_t* pc, int* status) {
+  double* w = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  char* inrow = (char*)calloc((size_t)(n > 0 ? n : 1), 1);
+  int64_t* lrow = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int64_t* urow = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int64_t* udiag = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  rowbuf L = {0}, U = {0};
+  *status = ORC_NOMEM;
+  if (!w || !inrow || !lrow || !urow || !udiag) goto fail;
+  lrow[0] = urow[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t p = pp[i]; p < pp[i + 1]; ++p) {
+      inrow[pc[p]] = 1;
+      w[pc[p]] = 0.0;
+    }
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) w[ci[p]] = va[p];
+    for (int64_t p = pp[i]; p < pp[i + 1] && pc[p] < i; ++p) {
+      const int32_t k = pc[p];
+      const double ukk = U.v[udiag[k]];
+      w[k] = w[k] / ukk;
+      for (int64_t q = udiag[k] + 1; q < urow[k + 1]; ++q) {
+        const int32_t j = U.c[q];
+        if (inrow[j]) w[j] = w[j] - w[k] * U.v[q];
+      }
+    }
+    /* gather L (strict lower) and U (diagonal first) */
+    int has_diag = 0;
+    for (int64_t p = pp[i]; p < pp[i + 1]; ++p) {
+      const int32_t j = pc[p];
+      if (j < i) {
+        if (!rb_push(&L, j, w[j])) goto fail;
+      } else {
+        if (j == i) has_diag = 1;
+        if (!rb_push(&U, j, w[j])) goto fail;
+      }
+      inrow[j] = 0;
+    }
+    if (!has_diag || w[i] == 0.0 || !isfinite(w[i])) {
+      *status = ORC_ZERO_PIVOT;
+      goto fail_nomsg;
+    }
+    lrow[i + 1] = L.len;
+    urow[i + 1] = U.len;
+    udiag[i] = urow[i];
+  }
+  {
+    orc_lu* f = lu_from_rows(n, &L, &U, lrow, urow);
+    free(w);
+    free(inrow);
+    free(lrow);
+    free(urow);
+    free(udiag);
+    if (!f) {
+      free(L.c);
+      free(L.v);
+      free(U.c);
+      free(U.v);
+      *status = ORC_NOMEM;
+      return NULL;
+    }
+    *status = ORC_OK;
+    return f;
+  }
+fail:
+  *status = ORC_NOMEM;
+fail_nomsg:
+  free(w);
+  free(inrow);
+  free(lrow);
+  free(urow);
+  free(udiag);
+  free(L.c);
+  free(L.v);
+  free(U.c);
+  free(U.v);
+  return NULL;
+}
+
+/* ILU(0): the pattern of the factors is the pattern of A (Sec. 3.2, Table dep). */
+orc_lu* orc_ilu0(int64_t n, const int64_t* rp, const int32_t* ci, const double* va, int* status) {
+  if (!csr_ok(n, rp, ci) || !va) {
+    *status = ORC_BADARG;
+    return NULL;
+  }
+  return ilu_on_pattern(n, rp, ci, va, rp, ci, status);
+}
+
+/*
+ * Symbolic phase of ILU(k) (Sec. 1 names ILU(k); Saad's level-of-fill):
+ * lev(i,j) = 0 on the pattern of A; eliminating with pivot row k gives
+ * lev(i,j) = min(lev(i,j), lev(i,k) + lev(k,j) + 1); entries with
+ * lev <= k_fill are kept.  Returns the pattern (sorted) in *pp, *pc.
+ */
+int orc_iluk_symbolic(int64_t n, const int64_t* rp, const int32_t* ci, int kfill, int64_t** pp_out, int32_t** pc_out,
+                      int32_t** plev_out) {
+  if (!csr_ok(n, rp, ci) || kfill < 0) return ORC_BADARG;
+  int32_t* lev = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int32_t* cols = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  minheap q = {(int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1)), 0};
+  int64_t* pp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int64_t* udiag = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  rowbuf P = {0};   /* columns in c, levels stored as doubles in v */
+  if (!lev || !cols || !q.h || !pp || !udiag) goto fail;
+  for (int64_t j = 0; j < n; ++j) lev[j] = -1;
+  pp[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t ncols = 0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      lev[ci[p]] = 0;
+      cols[ncols++] = ci[p];
+      if (ci[p] < i) heap_push(&q, ci[p]);
+    }
+    while (q.len > 0) {
+      const int32_t k = heap_pop(&q);
+      const int32_t lik = lev[k];
+      /* row k of U: pattern entries of row k with column > k */
+      for (int64_t p = udiag[k] + 1; p < pp[k + 1]; ++p) {
+        const int32_t j = P.c[p];
+        const int32_t nl = lik + (int32_t)P.v[p] + 1;
+        if (nl > kfill) continue;
+        if (lev[j] < 0) {
+          lev[j] = nl;
+          cols[ncols++] = j;
+          if (j < i) heap_push(&q, j);
+        } else if (nl < lev[j]) {
+          lev[j] = nl;
+        }
+      }
+    }
+    qsort(cols, (size_t)ncols, sizeof(int32_t), cmp_i32);
+    int64_t dpos = -1;
+    for (int64_t t = 0; t < ncols; ++t) {
+      if (cols[t] == i) dpos = P.len;
+      if (!rb_push(&P, cols[t], (double)lev[cols[t]])) goto fail;
+      lev[cols[t]] = -1;
+    }
+    if (dpos < 0) {
+      /* no diagonal in the pattern: the pivot is structurally zero */
+      free(lev);
+      free(cols);
+      free(q.h);
+      free(pp);
+      free(udiag);
+      free(P.c);
+      free(P.v);
+      return ORC_ZERO_PIVOT;
+    }
+    udiag[i] = dpos;
+    pp[i + 1] = P.len;
+  }
+  {
+    int64_t nnz = P.len;
+    int32_t* plev = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!plev) goto fail;
+    for (int64_t p = 0; p < nnz; ++p) plev[p] = (int32_t)P.v[p];
+    free(P.v);
+    *pp_out = pp;
+    *pc_out = P.c ? P.c : (int32_t*)malloc(sizeof(int32_t));
+    if (plev_out)
+      *plev_out = plev;
+    else
+      free(plev);
+    free(lev);
+    free(cols);
+    free(q.h);
+    free(udiag);
+    return ORC_OK;
+  }
+fail:
+  free(lev);
+  free(cols);
+  free(q.h);
+  free(pp);
+  free(udiag);
+  free(P.c);
+  free(P.v);
+  return ORC_NOMEM;
+}
+
+/* ILU(k): symbolic level-of-fill pattern, then the numeric phase on it */
+orc_lu* orc_iluk(int64_t n, const int64_t* rp, const int32_t* ci, const double* va, int kfill, int* status) {
+  int64_t* pp = NULL;
+  int32_t* pc = NULL;
+  if (!va) {
+    *status = ORC_BADARG;
+    return NULL;
+  }
+  int st = orc_iluk_symbolic(n, rp, ci, kfill, &pp, &pc, NULL);
+  if (st != ORC_OK) {
+    *status = st;
+    return NULL;
+  }
+  orc_lu* f = ilu_on_pattern(n, rp, ci, va, pp, pc, status);
+  free(pp);
+  free(pc);
+  return f;
+}
+
+/* pattern of ILU(k) for the tests: caller frees with orc_free */
+int orc_iluk_pattern(int64_t n, const int64_t* rp, const int32_t* ci, int kfill, int64_t* nnz_out, int64_t** pp,
+                     int32_t** pc, int32_t** plev) {
+  int st = orc_iluk_symbolic(n, rp, ci, kfill, pp, pc, plev);
+  if (st == ORC_OK) *nnz_out = (*pp)[n];
+  return st;
+}
+
+void orc_free(void* p) { free(p); }
+
+/* ------------------------------------------------------------------------ */
+/* ILUT(tau, p), Saad's dual threshold, pivoting off                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t c;
+  double a;
+} cand;
+
+/* larger magnitude first; equal magnitudes: smaller column first */
+static int cmp_cand(const void* x, const void* y) {
+  const cand* u = (const cand*)x;
+  const cand* v = (const cand*)y;
+  if (u->a > v->a) return -1;
+  if (u->a < v->a) return 1;
+  return (u->c > v->c) - (u->c < v->c);
+}
+
+static int cmp_cand_col(const void* x, const void* y) {
+  const cand* u = (const cand*)x;
+  const cand* v = (const cand*)y;
+  return (u->c > v->c) - (u->c < v->c);
+}
+
+/*
+ * The paper uses ILUT with a drop tolerance and a fill limit per row
+ * (droptol, lfill; Sec. 3.2, Sec. 6.1) without defining the rule.  Reading:
+ * Saad's ILUT(tau, p) with pivoting off.  For row i:
+ *   tau_i = tau * ||a_{i,:}||_2
+ *   w = a_{i,:}
+ *   for k < i with w_k != 0, ascending:
+ *       w_k <- w_k / u_kk
+ *       if |w_k| < tau_i: w_k <- 0 (dropped, no update)
+ *       else w_j <- w_j - w_k * u_kj for j > k in row k of U
+ *   drop off-diagonal entries with |w_j| < tau_i
+ *   keep the p largest-magnitude entries of the L part and, separately, of
+ *   the U part (ties: smaller column); the diagonal is always kept.
+ * A zero or non-finite pivot is an error (no pivot boosting).
+ */
+orc_lu* orc_ilut(int64_t n, const int64_t* rp, const int32_t* ci, const double* va, double tau, int pfill,
+                 int* status) {
+  if (!csr_ok(n, rp, ci) || !va || !(tau >= 0.0) || pfill < 0) {
+    *status = ORC_BADARG;
+    return NULL;
+  }
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  double* w = (double*)calloc(nn, sizeof(double));
+  char* inrow = (char*)calloc(nn, 1);
+  int32_t* cols = (int32_t*)malloc(sizeof(int32_t) * nn);
+  cand* cl = (cand*)malloc(sizeof(cand) * nn);
+  cand* cu = (cand*)malloc(sizeof(cand) * nn);
+  minheap q = {(int32_t*)malloc(sizeof(int32_t) * nn), 0};
+  int64_t* lrow = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int64_t* urow = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  rowbuf L = {0}, U = {0};
+  *status = ORC_NOMEM;
+  if (!w || !inrow || !cols || !cl || !cu || !q.h || !lrow || !urow) goto fail;
+  lrow[0] = urow[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    double nrm2 = 0.0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) nrm2 = nrm2 + va[p] * va[p];
+    const double tau_i = tau * sqrt(nrm2);
+    int64_t ncols = 0, nl = 0, nu = 0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      const int32_t j = ci[p];
+      w[j] = va[p];
+      inrow[j] = 1;
+      cols[ncols++] = j;
+      if (j < i) heap_push(&q, j);
+    }
+    while (q.len > 0) {
+      const int32_t k = heap_pop(&q);
+      w[k] = w[k] / U.v[urow[k]];
+      if (fabs(w[k]) < tau_i) {
+        w[k] = 0.0;
+        continue;
+      }
+      cl[nl].c = k;
+      cl[nl].a = fabs(w[k]);
+      nl++;
+      for (int64_t qq = urow[k] + 1; qq < urow[k + 1]; ++qq) {
+        const int32_t j = U.c[qq];
+        if (!inrow[j]) {
+          inrow[j] = 1;
+          w[j] = 0.0;
+          cols[ncols++] = j;
+          if (j < i) heap_push(&q, j);
+        }
+        w[j] = w[j] - w[k] * U.v[qq];
+      }
+    }
+    const double piv = inrow[i] ? w[i] : 0.0;
+    if (piv == 0.0 || !isfinite(piv)) {
+      *status = ORC_ZERO_PIVOT;
+      goto fail_nomsg;
+    }
+    for (int64_t t = 0; t < ncols; ++t) {
+      const int32_t j = cols[t];
+      if (j > i && fabs(w[j]) >= tau_i) {
+        cu[nu].c = j;
+        cu[nu].a = fabs(w[j]);
+        nu++;
+      }
+    }
+    qsort(cl, (size_t)nl, sizeof(cand), cmp_cand);
+    qsort(cu, (size_t)nu, sizeof(cand), cmp_cand);
+    if (nl > pfill) nl = pfill;
+    if (nu > pfill) nu = pfill;
+    qsort(cl, (size_t)nl, sizeof(cand), cmp_cand_col);
+    qsort(cu, (size_t)nu, sizeof(cand), cmp_cand_col);
+    for (int64_t t = 0; t < nl; ++t)
+      if (!rb_push(&L, cl[t].c, w[cl[t].c])) goto fail;
+    if (!rb_push(&U, (int32_t)i, piv)) goto fail;
+    for (int64_t t = 0; t < nu; ++t)
+      if (!rb_push(&U, cu[t].c, w[cu[t].c])) goto fail;
+    for (int64_t t = 0; t < ncols; ++t) {
+      inrow[cols[t]] = 0;
+      w[cols[t]] = 0.0;
+    }
+    lrow[i + 1] = L.len;
+    urow[i + 1] = U.len;
+  }
+  {
+    orc_lu* f = lu_from_rows(n, &L, &U, lrow, urow);
+    free(w);
+    free(inrow);
+    free(cols);
+    free(cl);
+    free(cu);
+    free(q.h);
+    free(lrow);
+    free(urow);
+    if (!f) {
+      free(L.c);
+      free(L.v);
+      free(U.c);
+      free(U.v);
+      *status = ORC_NOMEM;
+      return NULL;
+    }
+    *status = ORC_OK;
+    return f;
+  }
+fail:
+  *status = ORC_NOMEM;
+fail_nomsg:
+  free(w);
+  free(inrow);
+  free(cols);
+  free(cl);
+  free(cu);
+  free(q.h);
+  free(lrow);
+  free(urow);
+  free(L.c);
+  free(L.v);
+  free(U.c);
+  free(U.v);
+  return NULL;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Row scaling (Eq. extractD, Eq. newD)                                      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * D = diag(U), Utilde = D^{-1} U, so Utilde_ij = u_ij / u_ii.  Writes
+ * dinv_i = 1 / u_ii and the strict upper part Utilde_s (row pointer sp with
+ * n+1 entries, nnz(U) - n entries).  diag(Utilde) = u_ii / u_ii = 1 exactly
+ * for finite nonzero u_ii, so it is not stored.
+ */
+int orc_row_scale(int64_t n, const int64_t* up, const int32_t* uc, const double* uv, double* dinv, int64_t* sp,
+                  int32_t* sc, double* sv) {
+  int64_t q = 0;
+  sp[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (up[i + 1] <= up[i] || uc[up[i]] != i) return ORC_BADARG;
+    const double d = uv[up[i]];
+    if (d == 0.0 || !isfinite(d)) return ORC_ZERO_PIVOT;
+    dinv[i] = 1.0 / d;
+    for (int64_t p = up[i] + 1; p < up[i + 1]; ++p) {
+      sc[q] = uc[p];
+      sv[q] = uv[p] / d;
+      ++q;
+    }
+    sp[i + 1] = q;
+  }
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Residual, SpMV and the Richardson sweeps (Alg. ILUJac, Eq. richard)        */
+/* ------------------------------------------------------------------------ */
+
+/* y = A x  (sum over the row in ascending column order) */
+void orc_spmv(int64_t n, int R, const int64_t* rp, const int32_t* ci, const double* va, const double* x, double* y) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int r = 0; r < R; ++r) {
+      double s = 0.0;
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s = s + va[p] * x[(int64_t)ci[p] * R + r];
+      y[i * R + r] = s;
+    }
+}
+
+/* r = b - A x (Eq. ILUsplit, the residual of the splitting iteration) */
+void orc_residual(int64_t n, int R, const int64_t* rp, const int32_t* ci, const double* va, const double* x,
+                  const double* b, double* r) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int c = 0; c < R; ++c) {
+      double s = 0.0;
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s = s + va[p] * x[(int64_t)ci[p] * R + c];
+      r[i * R + c] = b[i * R + c] - s;
+    }
+}
+
+/* one sweep: out = c - T_s in */
+static void sweep(int64_t n, int R, const int64_t* tp, const int32_t* tc, const double* tv, const double* c,
+                  const double* in, double* out) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < R; ++k) {
+      double s = 0.0;
+      for (int64_t p = tp[i]; p < tp[i + 1]; ++p) s = s + tv[p] * in[(int64_t)tc[p] * R + k];
+      out[i * R + k] = c[i * R + k] - s;
+    }
+}
+
+/*
+ * Richardson iteration for L y = r with L = I + L_s (Alg. ILUJac, first loop):
+ *   y^0 = 0;  y^k = r - L_s y^{k-1},  k = 1..m.
+ * Writes y^m.  m = 0 leaves y = 0.
+ */
+int orc_richardson_lower(int64_t n, int R, const int64_t* lp, const int32_t* lc, const double* lv, const double* r,
+                         int m, double* y) {
+  const size_t sz = (size_t)(n * R > 0 ? n * R : 1);
+  double* prev = (double*)calloc(sz, sizeof(double));
+  if (!prev) return ORC_NOMEM;
+  memset(y, 0, sizeof(double) * (size_t)(n * R));
+  for (int k = 1; k <= m; ++k) {
+    memcpy(prev, y, sizeof(double) * (size_t)(n * R));
+    sweep(n, R, lp, lc, lv, r, prev, y);
+  }
+  free(prev);
+  return ORC_OK;
+}
+
+/*
+ * Richardson iteration for Utilde v = D^{-1} y with Utilde = I + Utilde_s
+ * (Alg. ILUJac, second loop; Eq. richard with b_s = D_U^{-1} b):
+ *   c = dinv .* y;  v^0 = 0;  v^k = c - Utilde_s v^{k-1},  k = 1..m.
+ */
+int orc_richardson_upper(int64_t n, int R, const int64_t* sp, const int32_t* sc, const double* sv, const double* dinv,
+                         const double* y, int m, double* v) {
+  const size_t sz = (size_t)(n * R > 0 ? n * R : 1);
+  double* c = (double*)malloc(sz * sizeof(double));
+  double* prev = (double*)calloc(sz, sizeof(double));
+  if (!c || !prev) {
+    free(c);
+    free(prev);
+    return ORC_NOMEM;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < R; ++k) c[i * R + k] = dinv[i] * y[i * R + k];
+  memset(v, 0, sizeof(double) * (size_t)(n * R));
+  for (int k = 1; k <= m; ++k) {
+    memcpy(prev, v, sizeof(double) * (size_t)(n * R));
+    sweep(n, R, sp, sc, sv, c, prev, v);
+  }
+  free(c);
+  free(prev);
+  return ORC_OK;
+}
+
+/*
+ * One smoother application (Eq. ILUsplit with M = L D Utilde, Alg. ILUJac):
+ *   r = b - A x;  y = L^{-1} r by m_L sweeps;  v = Utilde^{-1} D^{-1} y by
+ *   m_U sweeps;  x <- x + v.
+ * A factor with zero sweeps is skipped (treated as the identity, with the
+ * D^{-1} scaling dropped too when m_U = 0).
+ */
+int orc_smooth(int64_t n, int R, const int64_t* ap, const int32_t* ac, const double* av, const int64_t* lp,
+               const int32_t* lc, const double* lv, const int64_t* sp, const int32_t* sc, const double* sv,
+               const double* dinv, double* x, const double* b, int mL, int mU) {
+  const size_t sz = (size_t)(n * R > 0 ? n * R : 1);
+  double* r = (double*)malloc(sz * sizeof(double));
+  double* y = (double*)malloc(sz * sizeof(double));
+  double* v = (double*)malloc(sz * sizeof(double));
+  int st = ORC_NOMEM;
+  if (!r || !y || !v) goto done;
+  orc_residual(n, R, ap, ac, av, x, b, r);
+  if (mL > 0) {
+    if ((st = orc_richardson_lower(n, R, lp, lc, lv, r, mL, y))) goto done;
+  } else {
+    memcpy(y, r, sizeof(double) * (size_t)(n * R));
+  }
+  if (mU > 0) {
+    if ((st = orc_richardson_upper(n, R, sp, sc, sv, dinv, y, mU, v))) goto done;
+  } else {
+    memcpy(v, y, sizeof(double) * (size_t)(n * R));
+  }
+  for (int64_t t = 0; t < n * R; ++t) x[t] = x[t] + v[t];
+  st = ORC_OK;
+done:
+  free(r);
+  free(y);
+  free(v);
+  return st;
+}
+
+/*
+ * Unscaled plain Richardson on U = D + U_s (diagonal stored first in each
+ * row): v^k = y - (U - I) v^{k-1}.  Converges only if every |1 - u_ii| < 1
+ * (Sec. 6.1: iterations on unscaled factors fail to converge unless
+ * preconditioned).
+ */
+int orc_upper_unscaled_richardson(int64_t n, int R, const int64_t* up, const int32_t* uc, const double* uv,
+                                  const double* y, int m, double* v) {
+  const size_t sz = (size_t)(n * R > 0 ? n * R : 1);
+  double* prev = (double*)calloc(sz, sizeof(double));
+  if (!prev) return ORC_NOMEM;
+  memset(v, 0, sizeof(double) * (size_t)(n * R));
+  for (int k = 1; k <= m; ++k) {
+    memcpy(prev, v, sizeof(double) * (size_t)(n * R));
+    for (int64_t i = 0; i < n; ++i)
+      for (int c = 0; c < R; ++c) {
+        double s = 0.0;
+        for (int64_t p = up[i]; p < up[i + 1]; ++p) {
+          const double t = (uc[p] == i) ? uv[p] - 1.0 : uv[p];
+          s = s + t * prev[(int64_t)uc[p] * R + c];
+        }
+        v[i * R + c] = y[i * R + c] - s;
+      }
+  }
+  free(prev);
+  return ORC_OK;
+}
+
+/*
+ * Unscaled Jacobi on U (Eq. LUiterMat, G_U = I - D_U^{-1} U):
+ *   v^k = v^{k-1} + D_U^{-1} (y - U v^{k-1}).
+ * In exact arithmetic equal to the scaled Richardson iterates.
+ */
+int orc_upper_jacobi(int64_t n, int R, const int64_t* up, const int32_t* uc, const double* uv, const double* y, int m,
+                     double* v) {
+  const size_t sz = (size_t)(n * R > 0 ? n * R : 1);
+  double* prev = (double*)calloc(sz, sizeof(double));
+  if (!prev) return ORC_NOMEM;
+  memset(v, 0, sizeof(double) * (size_t)(n * R));
+  for (int k = 1; k <= m; ++k) {
+    memcpy(prev, v, sizeof(double) * (size_t)(n * R));
+    for (int64_t i = 0; i < n; ++i)
+      for (int c = 0; c < R; ++c) {
+        double s = 0.0;
+        for (int64_t p = up[i]; p < up[i + 1]; ++p) s = s + uv[p] * prev[(int64_t)uc[p] * R + c];
+        v[i * R + c] = prev[i * R + c] + (y[i * R + c] - s) / uv[up[i]];
+      }
+  }
+  free(prev);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Direct triangular solves and level sets (Sec. 4, level-set scheduling)     */
+/* ------------------------------------------------------------------------ */
+
+/* forward substitution for (I + L_s) y = r */
+void orc_forward_subst(int64_t n, int R, const int64_t* lp, const int32_t* lc, const double* lv, const double* r,
+                       double* y) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int c = 0; c < R; ++c) {
+      double s = 0.0;
+      for (int64_t p = lp[i]; p < lp[i + 1]; ++p) s = s + lv[p] * y[(int64_t)lc[p] * R + c];
+      y[i * R + c] = r[i * R + c] - s;
+    }
+}
+
+/* backward substitution for (I + Utilde_s) v = c */
+void orc_backward_subst_unit(int64_t n, int R, const int64_t* sp, const int32_t* sc, const double* sv, const double* c,
+                             double* v) {
+  for (int64_t i = n - 1; i >= 0; --i)
+    for (int k = 0; k < R; ++k) {
+      double s = 0.0;
+      for (int64_t p = sp[i]; p < sp[i + 1]; ++p) s = s + sv[p] * v[(int64_t)sc[p] * R + k];
+      v[i * R + k] = c[i * R + k] - s;
+    }
+}
+
+/*
+ * Direct smoother application: x <- x + Utilde^{-1} D^{-1} L^{-1} (b - A x),
+ * the exact solves that the sweeps approximate.
+ */
+int orc_direct_apply(int64_t n, int R, const int64_t* ap, const int32_t* ac, const double* av, const int64_t* lp,
+                     const int32_t* lc, const double* lv, const int64_t* sp, const int32_t* sc, const double* sv,
+                     const double* dinv, double* x, const double* b) {
+  const size_t sz = (size_t)(n * R > 0 ? n * R : 1);
+  double* r = (double*)malloc(sz * sizeof(double));
+  double* y = (double*)malloc(sz * sizeof(double));
+  double* v = (double*)malloc(sz * sizeof(double));
+  if (!r || !y || !v) {
+    free(r);
+    free(y);
+    free(v);
+    return ORC_NOMEM;
+  }
+  orc_residual(n, R, ap, ac, av, x, b, r);
+  orc_forward_subst(n, R, lp, lc, lv, r, y);
+  for (int64_t i = 0; i < n; ++i)
+    for (int k = 0; k < R; ++k) y[i * R + k] = dinv[i] * y[i * R + k];
+  orc_backward_subst_unit(n, R, sp, sc, sv, y, v);
+  for (int64_t t = 0; t < n * R; ++t) x[t] = x[t] + v[t];
+  free(r);
+  free(y);
+  free(v);
+  return ORC_OK;
+}
+
+/*
+ * Level sets of a strictly lower triangular pattern: lev(i) = 0 for a row
+ * with no entries, else 1 + max lev(j) over its entries.  Returns the number
+ * of levels (0 for n = 0).
+ */
+int64_t orc_levels_lower(int64_t n, const int64_t* lp, const int32_t* lc, int32_t* lev) {
+  int64_t nlev = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t l = 0;
+    for (int64_t p = lp[i]; p < lp[i + 1]; ++p)
+      if (lev[lc[p]] + 1 > l) l = lev[lc[p]] + 1;
+    lev[i] = l;
+    if (l + 1 > nlev) nlev = l + 1;
+  }
+  return nlev;
+}
+
+/* Level sets of a strictly upper triangular pattern, computed from the bottom. */
+int64_t orc_levels_upper(int64_t n, const int64_t* sp, const int32_t* sc, int32_t* lev) {
+  int64_t nlev = 0;
+  for (int64_t i = n - 1; i >= 0; --i) {
+    int32_t l = 0;
+    for (int64_t p = sp[i]; p < sp[i + 1]; ++p)
+      if (lev[sc[p]] + 1 > l) l = lev[sc[p]] + 1;
+    lev[i] = l;
+    if (l + 1 > nlev) nlev = l + 1;
+  }
+  return nlev;
+}
+
+/* ------------------------------------------------------------------------ */
+/* FGMRES(m) with modified Gram-Schmidt (Sec. 6: Eq. relres, FGMRES, MGS)     */
+/* ------------------------------------------------------------------------ */
+
+static double dot(int64_t n, const double* a, const double* b) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s = s + a[i] * b[i];
+  return s;
+}
+
+/*
+ * Right-preconditioned flexible GMRES(m) for A x = b, one right-hand side.
+ * x holds the initial guess on entry.  precond: 0 = the Richardson smoother
+ * with (mL, mU) sweeps applied from a zero guess, 1 = direct triangular
+ * solves, 2 = none.  Arnoldi by modified Gram-Schmidt, Givens rotations with
+ * r = hypot(a, b).  Stops when the Arnoldi residual estimate falls to
+ * tol * ||b||; then the true residual ||b - A x|| / ||b|| (Eq. relres) is
+ * recomputed and the method restarts while it is above tol (the paper warns
+ * of false convergence).  maxit bounds the total number of inner iterations.
+ * Returns ORC_OK when the true relative residual is <= tol.
+ */
+int orc_fgmres(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, const int64_t* lp, const int32_t* lc,
+               const double* lv, const int64_t* sp, const int32_t* sc, const double* sv, const double* dinv, double* x,
+               const double* b, double tol, int m, int maxit, int mL, int mU, int precond, int* iters_out,
+               double* relres_out) {
+  if (n < 0 || m < 1 || maxit < 0 || precond < 0 || precond > 2) return ORC_BADARG;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  double* V = (double*)malloc(sizeof(double) * nn * (size_t)(m + 1));
+  double* Z = (double*)malloc(sizeof(double) * nn * (size_t)m);
+  double* H = (double*)calloc((size_t)(m + 1) * (size_t)m, sizeof(double));
+  double* cs = (double*)malloc(sizeof(double) * (size_t)m);
+  double* sn = (double*)malloc(sizeof(double) * (size_t)m);
+  double* g = (double*)malloc(sizeof(double) * (size_t)(m + 1));
+  double* yv = (double*)malloc(sizeof(double) * (size_t)m);
+  double* r = (double*)malloc(sizeof(double) * nn);
+  double* w = (double*)malloc(sizeof(double) * nn);
+  double* zero = (double*)calloc(nn, sizeof(double));
+  int st = ORC_NOMEM;
+  int its = 0;
+  double relres = 0.0;
+  if (!V || !Z || !H || !cs || !sn || !g || !yv || !r || !w || !zero) goto done;
+  const double bnorm = sqrt(dot(n, b, b));
+  if (bnorm == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    st = ORC_OK;
+    goto done;
+  }
+#define HH(i, j) H[(size_t)(i) * (size_t)m + (size_t)(j)]
+  for (;;) {
+    orc_residual(n, 1, ap, ac, av, x, b, r);
+    const double beta = sqrt(dot(n, r, r));
+    relres = beta / bnorm;
+    if (relres <= tol) {
+      st = ORC_OK;
+      break;
+    }
+    if (its >= maxit) {
+      st = ORC_NOT_CONVERGED;
+      break;
+    }
+    for (int64_t i = 0; i < n; ++i) V[i] = r[i] / beta;
+    for (int t = 0; t <= m; ++t) g[t] = 0.0;
+    g[0] = beta;
+    int jend = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = V + (size_t)j * nn;
+      double* zj = Z + (size_t)j * nn;
+      /* z_j = M^{-1} v_j */
+      if (precond == 0) {
+        memset(zj, 0, sizeof(double) * nn);
+        if ((st = orc_smooth(n, 1, ap, ac, av, lp, lc, lv, sp, sc, sv, dinv, zj, vj, mL, mU))) goto done;
+      } else if (precond == 1) {
+        memset(zj, 0, sizeof(double) * nn);
+        if ((st = orc_direct_apply(n, 1, ap, ac, av, lp, lc, lv, sp, sc, sv, dinv, zj, vj))) goto done;
+      } else {
+        memcpy(zj, vj, sizeof(double) * nn);
+      }
+      orc_spmv(n, 1, ap, ac, av, zj, w);
+      for (int i = 0; i <= j; ++i) {
+        const double* vi = V + (size_t)i * nn;
+        const double h = dot(n, w, vi);
+        HH(i, j) = h;
+        for (int64_t t = 0; t < n; ++t) w[t] = w[t] - h * vi[t];
+      }
+      const double hn = sqrt(dot(n, w, w));
+      HH(j + 1, j) = hn;
+      if (hn != 0.0) {
+        double* vn = V + (size_t)(j + 1) * nn;
+        for (int64_t t = 0; t < n; ++t) vn[t] = w[t] / hn;
+      }
+      for (int i = 0; i < j; ++i) {
+        const double a = HH(i, j), bb = HH(i + 1, j);
+        HH(i, j) = cs[i] * a + sn[i] * bb;
+        HH(i + 1, j) = -sn[i] * a + cs[i] * bb;
+      }
+      const double a = HH(j, j), bb = HH(j + 1, j);
+      const double den = hypot(a, bb);
+      cs[j] = a / den;
+      sn[j] = bb / den;
+      HH(j, j) = den;
+      HH(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      its++;
+      jend = j + 1;
+      if (fabs(g[j + 1]) <= tol * bnorm || its >= maxit || hn == 0.0) break;
+    }
+    /* solve the jend x jend upper triangular system and update x */
+    for (int i = jend - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int t = i + 1; t < jend; ++t) s = s - HH(i, t) * yv[t];
+      yv[i] = s / HH(i, i);
+    }
+    for (int i = 0; i < jend; ++i) {
+      const double* zi = Z + (size_t)i * nn;
+      for (int64_t t = 0; t < n; ++t) x[t] = x[t] + yv[i] * zi[t];
+    }
+  }
+#undef HH
+done:
+  if (iters_out) *iters_out = its;
+  if (relres_out) *relres_out = relres;
+  free(V);
+  free(Z);
+  free(H);
+  free(cs);
+  free(sn);
+  free(g);
+  free(yv);
+  free(r);
+  free(w);
+  free(zero);
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics (Eq. depB, Eq. diagDep, Eq. nbre)                              */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Henrici's departure from normality dep(T) = sqrt(||T||_F^2 - ||Lambda||_F^2)
+ * (Eq. depB) of a triangular T stored in CSR.  The eigenvalues of a
+ * triangular matrix are its diagonal, so ||T||_F^2 - ||Lambda||_F^2 is the
+ * sum of squares of the off-diagonal entries, which is what is summed (the
+ * same quantity without the cancellation of the difference).  With
+ * unit_diag != 0 the stored entries are the strict part of I + T_s and the
+ * result is ||T_s||_F (Eq. diagDep).
+ */
+double orc_dep_triangular(int64_t n, const int64_t* tp, const int32_t* tc, const double* tv, int unit_diag) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = tp[i]; p < tp[i + 1]; ++p)
+      if (unit_diag || tc[p] != i) s = s + tv[p] * tv[p];
+  return sqrt(s);
+}
+
+/* ||A||_2 of a symmetric A estimated by `iters` power iterations from ones */
+double orc_norm2_est(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, int iters) {
+  if (n <= 0) return 0.0;
+  double* v = (double*)malloc(sizeof(double) * (size_t)n);
+  double* w = (double*)malloc(sizeof(double) * (size_t)n);
+  double lam = 0.0;
+  if (!v || !w) {
+    free(v);
+    free(w);
+    return -1.0;
+  }
+  for (int64_t i = 0; i < n; ++i) v[i] = 1.0 / sqrt((double)n);
+  for (int it = 0; it < iters; ++it) {
+    orc_spmv(n, 1, ap, ac, av, v, w);
+    lam = sqrt(dot(n, w, w));
+    if (lam == 0.0) break;
+    for (int64_t i = 0; i < n; ++i) v[i] = w[i] / lam;
+  }
+  free(v);
+  free(w);
+  return lam;
+}
+
+/* NRBE = ||b - A x|| / (||b|| + ||A||_2 ||x||)  (Eq. nbre) */
+double orc_nrbe(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, double norm2A, const double* x,
+                const double* b) {
+  double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!r) return -1.0;
+  orc_residual(n, 1, ap, ac, av, x, b, r);
+  const double rn = sqrt(dot(n, r, r));
+  const double out = rn / (sqrt(dot(n, b, b)) + norm2A * sqrt(dot(n, x, x)));
+  free(r);
+  return out;
+}
