@@ -1,0 +1,443 @@
+#!/usr/bin/env python3
+"""Benchmark of the scaled-ILU Richardson smoother on GB300.
+
+Workload (one "step"): one smoother application x <- x + M^{-1}(b - A x)
+with 10 sweeps on L_s and 10 on the row-scaled Utilde_s (Alg. ILUJac; the
+paper's model counts twenty Richardson iterations per smoother application),
+on the 128^3 cut-cell pressure matrix (2,097,152 rows, ILUT(1e-3, 10), FP64,
+one right-hand side).  Metric: algorithmic GB/s of the application (bytes
+the method must move, defined below) and its fraction of the measured HBM
+bandwidth; then the FGMRES time to 1e-8 of the FP32-smoother path against the
+FP64 direct-trisolve path.
+
+Every rank runs an independent replica (the path does not shard on one
+GPU: replicas only); value = bytes of all ranks / max time over ranks.
+
+Algorithmic bytes (int32 CSR; vb = value bytes; R = right-hand sides):
+  residual   nnz(A)*12 + 4(n+1) + 3 n R 8          (A, x, b read; r written)
+  L sweep    nnz(L_s)(vb+4) + 4(n+1) + 3 n R vb     (L_s, y_in, r read; y_out written)
+  U sweep    nnz(Ut_s)(vb+4) + 4(n+1) + 3 n R vb
+  scaling    8 n  (dinv, read once, fused into the last L sweep)
+  update     n R 8 (x read by the fused last U sweep)
+  apply = residual + (mL-1) L sweeps + 8n + (mU-1) U sweeps + 8nR
+(the first sweep of each factor starts from zero and costs no SpMV).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+EDGE = 128
+TAU, FILL = 1e-3, 10
+ML, MU = 10, 10
+WORKLOAD = "cutcell7-128^3 ILUT(1e-3,10) FP64 smoother 10+10 sweeps, 1 RHS"
+
+
+def sweep_bytes(n, nnz, R, vb):
+    return nnz * (vb + 4) + 4 * (n + 1) + 3 * n * R * vb
+
+
+def resid_bytes(n, nnzA, R):
+    return nnzA * 12 + 4 * (n + 1) + 3 * n * R * 8
+
+
+def apply_bytes(n, nnzA, nnzL, nnzU, R, vb, mL, mU):
+    b = resid_bytes(n, nnzA, R)
+    b += max(mL - 1, 0) * sweep_bytes(n, nnzL, R, vb)
+    b += 8 * n
+    b += max(mU - 1, 0) * sweep_bytes(n, nnzU, R, vb)
+    b += 8 * n * R
+    return b
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def sweep_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels_sweep.cu", "device.cuh"):
+        with open(os.path.join(ROOT, "paper_2111_09512_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the sweep kernel from the committed ncu summary,
+    or None when the kernel source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "k_sweep_cutcell128_ilut_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    with open(p) as f:
+        for line in f:
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != sweep_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_sweep_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, which):
+        if which == 0:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for t, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append((t, parts))
+        inside = [r for r in rows if self.t0 is not None and self.t0 - 0.15 <= r[0] <= (self.t1 or 1e30) + 0.15]
+        use = inside or rows
+        if not use:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(p[1]) for _, p in use if num(p[1]) is not None]
+        mx = [num(p[2]) for _, p in use if num(p[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for _, p in use:
+            for k, name in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(use), "in_timed_region": bool(inside)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def build_workload():
+    import synth
+    A = synth.cutcell7(EDGE, seed=1)
+    n = len(A[0]) - 1
+    b = synth.rhs(n, 1, seed=1)
+    return A, b
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def oracle_rate(A, b, budget_s: float):
+    """Time the oracle's smoother application (single thread) on the workload;
+    repeats until budget_s elapses (at least one application)."""
+    import numpy as np
+    import oracle
+    F = oracle.ilut(A, TAU, FILL)
+    S = oracle.row_scale(F)
+    n = len(A[0]) - 1
+    nbytes = apply_bytes(n, len(A[1]), len(S.L[1]), len(S.Us[1]), 1, 8, ML, MU)
+    x0 = np.zeros((n, 1))
+    reps, t = 0, 0.0
+    while reps == 0 or t < budget_s:
+        t0 = time.perf_counter()
+        oracle.smooth(A, S, x0, b, ML, MU)
+        t += time.perf_counter() - t0
+        reps += 1
+    return nbytes * reps / t / 1e9, reps, t
+
+
+def slab_sample(nz: int):
+    """A 128 x 128 x nz slab of the same cut-cell generator: the same rows,
+    couplings and bandwidth as the full workload, fewer planes."""
+    import synth
+    A = synth.cutcell7(EDGE, EDGE, nz, seed=1)
+    n = len(A[0]) - 1
+    return A, synth.rhs(n, 1, seed=1)
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    oracle.build()
+    total_steps = args.steps + args.warmup
+    # size the per-step sample so the whole run stays within ~150 s
+    per_step_budget = min(2.0, 150.0 / max(total_steps, 1))
+    As, bs = slab_sample(8)
+    Fs = oracle.row_scale(oracle.ilut(As, TAU, FILL))
+    t0 = time.perf_counter()
+    oracle.smooth(As, Fs, np.zeros_like(bs), bs, ML, MU)
+    t8 = time.perf_counter() - t0
+    nz = int(max(1, min(EDGE, 8 * per_step_budget / max(t8, 1e-6))))
+    A, b = slab_sample(nz)
+    S = oracle.row_scale(oracle.ilut(A, TAU, FILL))
+    n = len(A[0]) - 1
+    nbytes = apply_bytes(n, len(A[1]), len(S.L[1]), len(S.Us[1]), 1, 8, ML, MU)
+    x0 = np.zeros((n, 1))
+    for _ in range(args.warmup):
+        oracle.smooth(A, S, x0, b, ML, MU)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.smooth(A, S, x0, b, ML, MU)
+    dt = time.perf_counter() - t0
+    value = nbytes * args.steps / dt / 1e9
+    sample = f"128x128x{nz} slab of the cut-cell generator ({n} rows), ILUT(1e-3,10), 10+10 sweeps per step"
+    line = {
+        "impl": "reference", "metric": "Richardson ILU-apply GB/s", "value": round(value, 3), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * dt / max(args.steps, 1), 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample, "l2": "oracle runs on host cores"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+
+def run_silu(args):
+    import numpy as np
+    import torch
+    import paper_2111_09512_gb300 as silu
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    silu.build()
+    stream = torch.cuda.current_stream()
+    ctx = silu.Context(local, stream)
+
+    A, b_np = build_workload()
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilut", TAU, FILL)
+    st = F.stats()
+    nnzA, nnzL, nnzU = len(A[1]), st["nnz_L"], st["nnz_U"]
+    step_bytes = apply_bytes(n, nnzA, nnzL, nnzU, 1, 8, ML, MU)
+    F.reserve(1, 30)
+    b = torch.from_numpy(b_np).cuda()
+    x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+
+    for _ in range(args.warmup):
+        x.zero_()
+        silu.ilu_smooth(F, x, b, ML, MU)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark(0)
+    e0.record(stream)
+    for _ in range(args.steps):
+        silu.ilu_smooth(F, x, b, ML, MU)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark(1)
+    ctx.profile(False)
+    if dist:
+        dist.barrier()
+    launches = ctx.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_read()
+    clocks = sampler.stop()
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = step_bytes * args.steps * world / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel: the sweep SpMV (L_s and Utilde_s)
+    nL, msL = prof["sweep_L"]
+    nU, msU = prof["sweep_U"]
+    sw_bytes = nL * sweep_bytes(n, nnzL, 1, 8) + nU * sweep_bytes(n, nnzU, 1, 8)
+    achieved = sw_bytes / ((msL + msU) * 1e-3) / 1e9 if msL + msU > 0 else None
+    peak, peak_kind = load_peaks()
+    traffic = recorded_traffic()
+    total_prof_ms = sum(v[1] for v in prof.values())
+
+    # end to end through the public API with host buffers, copies inside the region
+    xh = torch.zeros(n, 1, dtype=torch.float64).pin_memory()
+    bh = torch.from_numpy(b_np.copy()).pin_memory()
+    for _ in range(2):
+        x.copy_(xh, non_blocking=True)
+        b.copy_(bh, non_blocking=True)
+        silu.ilu_smooth(F, x, b, ML, MU)
+        xh.copy_(x, non_blocking=True)
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        x.copy_(xh, non_blocking=True)
+        b.copy_(bh, non_blocking=True)
+        silu.ilu_smooth(F, x, b, ML, MU)
+        xh.copy_(x, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3)
+    if dist:
+        t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = step_bytes * args.steps * world / (ms_e2e * 1e-3) / 1e9
+
+    solve = None
+    if not args.no_solve and rank == 0:
+        solve = solve_comparison(silu, ctx, A, b_np, torch)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gbs, reps, t = oracle_rate(A, b_np, args.cpu_budget)
+        cpu = {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"{reps} full application(s) of the 128^3 workload, {t:.1f} s, single thread"}
+
+    if rank == 0:
+        line = {
+            "metric": "Richardson ILU-apply GB/s", "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rows": n, "nnz_A": nnzA, "nnz_L": nnzL, "nnz_U": nnzU,
+                       "bytes_per_step": step_bytes, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (factors + A = %.0f MB > 129 MB)"
+                             % ((nnzA * 12 + (nnzL + nnzU) * 12) / 1e6)},
+            "hbm_frac_of_" + peak_kind: round(value / world / peak, 4),
+            "roofline": {"bound": "hbm", "kernel": "k_sweep (Richardson sweep SpMV on L_s / Utilde_s)",
+                         "achieved": round(achieved, 2) if achieved else None, "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4) if achieved else None, "peak_kind": peak_kind,
+                         "traffic": traffic, "launches": nL + nU,
+                         "share_of_timed_kernels": round((msL + msU) / total_prof_ms, 4) if total_prof_ms else None},
+            "kernel_ms": {k: [v[0], round(v[1], 4)] for k, v in prof.items() if v[0]},
+            "e2e": {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": 2 * n * 8,
+                    "d2h_bytes_per_step": n * 8},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        if solve:
+            line["solve"] = solve
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def solve_comparison(silu, ctx, A, b_np, torch):
+    """Time to 1e-8 relative residual: FGMRES(30) with the FP32 scaled-ILU
+    Richardson smoother (3+3 sweeps) against FGMRES(30) with FP64 direct
+    level-scheduled triangular solves, same matrix, same ILUT factors."""
+    n = len(A[0]) - 1
+    out = {"tol": 1e-8, "restart": 30}
+    b = torch.from_numpy(b_np[:, 0].copy()).cuda()
+    for name, prec, pc in (("fp32_sweeps_3_3", silu.FP32, silu.PRECOND_SWEEPS),
+                           ("fp64_direct", silu.FP64, silu.PRECOND_DIRECT)):
+        F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilut", TAU, FILL, prec=prec)
+        F.reserve(1, 30)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        silu.fgmres_solve(F, x, b, tol=1e-8, restart=30, maxit=1, sweeps_L=3, sweeps_U=3, precond=pc)
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, its, rel = silu.fgmres_solve(F, x, b, tol=1e-8, restart=30, maxit=2000, sweeps_L=3, sweeps_U=3,
+                                         precond=pc)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"seconds": round(dt, 5), "iterations": its, "relres": rel, "converged": st == silu.OK}
+        del F
+    if out["fp32_sweeps_3_3"]["seconds"] > 0:
+        out["speedup_sweeps_vs_direct"] = round(out["fp64_direct"]["seconds"] / out["fp32_sweeps_3_3"]["seconds"], 3)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["silu", "reference"], default="silu")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_silu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

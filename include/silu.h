@@ -1,0 +1,215 @@
+/*
+ * silu: scaled-ILU Richardson smoothers on GB300 (sm_103a).
+ *
+ * C ABI of libsilu.so.  The library applies an incomplete-LU smoother whose
+ * upper factor is row-scaled to unit diagonal, with the two triangular solves
+ * replaced by a fixed number of Richardson sweeps, each one CSR SpMV, as in
+ * Thomas, Carr, Mullowney, Swirydowicz and Day, "Scaled ILU Smoothers for
+ * Navier-Stokes Pressure Projection" (arXiv 2111.09512), and wraps it in a
+ * flexible GMRES solve.
+ *
+ * Conventions that hold for every call:
+ *  - Matrices are CSR with int64 row pointers (n+1 entries), int32 column
+ *    indices and FP64 values, all in HOST memory; the library copies them
+ *    (the caller keeps ownership).  Rows need not be sorted; duplicate
+ *    entries are summed.  n and nnz must be below 2^31.
+ *  - Vectors are DEVICE pointers owned by the caller, FP64, row-major
+ *    n x nrhs: the nrhs values of one row are adjacent (right-hand sides
+ *    interleaved).  8-byte alignment is required.
+ *  - Device calls are asynchronous and ordered on the context's stream,
+ *    except where a call says it blocks.  A context is used by one host
+ *    thread at a time; separate contexts may run concurrently.
+ *  - Every call returns a status; silu_last_error() gives the message of the
+ *    last failure on a context.  No call aborts, traps or leaves the device
+ *    in an error state on bad input: arguments are checked on the host first.
+ *  - Handles are freed by the matching *_destroy call; a silu_ilu refers to
+ *    the silu_mat it was built from, which must outlive it.
+ */
+#ifndef SILU_H
+#define SILU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SILU_OK = 0,
+  SILU_ERR_INVALID_ARG = 1,   /* bad argument, malformed CSR, NaN/Inf input  */
+  SILU_ERR_ZERO_PIVOT = 2,    /* zero or non-finite pivot (pivoting is off)  */
+  SILU_ERR_NOT_CONVERGED = 3, /* FGMRES hit maxit; best iterate is written   */
+  SILU_ERR_OOM = 4,           /* host or device allocation failed            */
+  SILU_ERR_CUDA = 5,          /* a CUDA runtime call failed                  */
+  SILU_ERR_TIMEOUT = 6,       /* a bounded device wait gave up               */
+  SILU_WARN_DIVERGED = 7,     /* iterate grew beyond a bound (not an error)  */
+  SILU_ERR_NO_DEVICE = 8      /* device call on a host-only context          */
+} silu_status;
+
+/* Incomplete factorisation kinds (Sec. 1, Sec. 3.2 of the paper). */
+typedef enum { SILU_ILU0 = 0, SILU_ILUK = 1, SILU_ILUT = 2 } silu_kind;
+
+/*
+ * How the upper factor is iterated (Sec. 5.1-5.2):
+ *  SILU_SCALE_ROW        Utilde = D^{-1} U, D = diag(U) (Eq. extractD,
+ *                        Eq. newD); Richardson v <- D^{-1} y - Utilde_s v
+ *                        (Eq. richard).  The method of the paper.
+ *  SILU_SCALE_NONE       raw U; Jacobi v <- v + D^{-1} (y - U v), iteration
+ *                        matrix G_U = I - D_U^{-1} U (Eq. LUiterMat).
+ *  SILU_SCALE_NONE_RICH  raw U; plain Richardson v <- y - (U - I) v, which
+ *                        the paper reports as failing to converge.
+ */
+typedef enum { SILU_SCALE_NONE = 0, SILU_SCALE_ROW = 1, SILU_SCALE_NONE_RICH = 2 } silu_scale;
+
+/* Precision of the stored factors and of the sweeps (the residual
+ * r = b - A x, FGMRES and the solution vector stay FP64). */
+typedef enum { SILU_FP64 = 0, SILU_FP32 = 1 } silu_prec;
+
+/* Preconditioner inside fgmres_solve. */
+typedef enum { SILU_PRECOND_SWEEPS = 0, SILU_PRECOND_DIRECT = 1, SILU_PRECOND_NONE = 2 } silu_precond;
+
+typedef struct silu_ctx_s* silu_ctx;
+typedef struct silu_mat_s* silu_mat;
+typedef struct silu_ilu_s* silu_ilu;
+
+/*
+ * Create a context on CUDA device `device` whose work is ordered on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream; it may be
+ * a stream owned by PyTorch).  device = -1 makes a host-only context: setup,
+ * statistics and export work, device calls return SILU_ERR_NO_DEVICE.
+ */
+silu_status silu_ctx_create(int device, void* cuda_stream, silu_ctx* out);
+void silu_ctx_destroy(silu_ctx ctx);
+
+/* Kernel classes for launch counting and timing. */
+typedef enum {
+  SILU_K_RESIDUAL = 0,    /* r = b - A x and w = A z (CSR SpMV with A)          */
+  SILU_K_SWEEP_L = 1,     /* Richardson sweep on L_s                            */
+  SILU_K_SWEEP_U = 2,     /* Richardson / Jacobi sweep on the upper factor      */
+  SILU_K_LEVEL = 3,       /* level-scheduled substitution (direct_trisolve)     */
+  SILU_K_KRYLOV = 4,      /* FGMRES dots, Gram-Schmidt, Givens, update          */
+  SILU_K_ELEMENTWISE = 5, /* scaling, casts, x updates                          */
+  SILU_K_NCLASS = 6
+} silu_kclass;
+
+/*
+ * Timing of the library's own kernels: with enable = 1 every later launch on
+ * ctx is bracketed by two CUDA events recorded on the context's stream (the
+ * launching stream); enable = 0 stops recording.  Enabling clears earlier
+ * records.  silu_ctx_profile_read blocks on the stream and returns, for one
+ * class, the launches recorded and the sum of their event-timed durations.
+ */
+silu_status silu_ctx_profile(silu_ctx ctx, int enable);
+silu_status silu_ctx_profile_read(silu_ctx ctx, int kclass, int64_t* launches, double* total_ms);
+/* Kernels launched on ctx since creation (all classes; always counted). */
+silu_status silu_ctx_launch_count(silu_ctx ctx, int64_t* launches);
+/* Message of the last failed call on ctx ("" if none); valid until the next call. */
+const char* silu_last_error(silu_ctx ctx);
+/* Library version string. */
+const char* silu_version(void);
+
+/*
+ * Copy the host CSR matrix A (n rows, nnz entries) into the library:
+ * validated (row pointers monotone, columns in range, values finite),
+ * columns sorted, duplicates summed, and uploaded to the device on a device
+ * context.  A is the pressure matrix of the paper's Eq. for the projection
+ * (Sec. 2); any square matrix with a nonzero diagonal is accepted.
+ */
+silu_status silu_mat_create(silu_ctx ctx, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                            const double* val, silu_mat* out);
+void silu_mat_destroy(silu_mat A);
+
+/*
+ * Host factorisation + scaling + packing, then one upload (blocks).
+ *  kind  SILU_ILU0: pattern of A (Sec. 3.2, Matlab ilu 'nofill').
+ *        SILU_ILUK: level-of-fill k = `fill` (Sec. 1).
+ *        SILU_ILUT: dual threshold, drop tolerance `tau` relative to the row's
+ *        2-norm and at most `fill` entries per row in each of L and U
+ *        (droptol / lfill, Sec. 3.2, Sec. 6.1); the paper does not define
+ *        the rule and this is Saad's ILUT.
+ *  Pivoting is off; a zero or non-finite pivot gives SILU_ERR_ZERO_PIVOT.
+ *  L is unit lower, stored as its strict part L_s.  The level sets of L_s and
+ *  of the upper factor (Sec. 4) are built for direct_trisolve.
+ */
+silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int fill, silu_scale scale,
+                      silu_prec prec, silu_ilu* out);
+
+/*
+ * Numeric refactorisation with new values of A on the SAME pattern (nnz
+ * values in the sorted, duplicate-free order of the silu_mat), reusing the
+ * symbolic phase (Sec. 3.2: the pattern of the pressure matrix does not change
+ * during a fluid step).  ILU0 and ILUK only (ILUT's pattern depends on the
+ * values): SILU_ERR_INVALID_ARG otherwise.  Blocks.
+ */
+silu_status ilu_refactor(silu_ilu F, const double* new_val);
+
+/*
+ * One smoother application (Eq. ILUsplit with M = L D Utilde, Alg. ILUJac):
+ *   r = b - A x;  y = r after sweeps_L sweeps y <- r - L_s y from y = 0;
+ *   v after sweeps_U sweeps on the upper factor from v = 0 (see silu_scale);
+ *   x <- x + v.
+ * x (in/out) and b are device n x nrhs FP64 and must not overlap.  A factor
+ * with 0 sweeps is skipped (identity; with SILU_SCALE_ROW and sweeps_U = 0
+ * the D^{-1} scaling is skipped too).  nrhs >= 1, sweeps >= 0.
+ */
+silu_status ilu_smooth(silu_ilu F, double* x, const double* b, int nrhs, int sweeps_L, int sweeps_U);
+
+/*
+ * The comparison path: the same update with exact triangular solves,
+ * x <- x + Utilde^{-1} D^{-1} L^{-1} (b - A x), by level-set scheduling
+ * (Sec. 4: rows of one level are independent; one device-wide ordering point
+ * per level).  Always FP64 arithmetic on the FP64 copy of the factors.
+ */
+silu_status direct_trisolve(silu_ilu F, double* x, const double* b, int nrhs);
+
+/*
+ * Right-preconditioned flexible GMRES(restart) on A x = b for one right-hand
+ * side (Sec. 6: FGMRES with modified Gram-Schmidt; stop on the relative
+ * residual of Eq. relres, with the true residual recomputed before
+ * returning, since the paper warns of false convergence).  x holds the
+ * initial guess and receives the solution; b is device FP64 length n.
+ * precond: SILU_PRECOND_SWEEPS (the smoother with sweeps_L / sweeps_U from a
+ * zero guess), SILU_PRECOND_DIRECT, SILU_PRECOND_NONE.  maxit bounds the
+ * total inner iterations.  Blocks until done; writes the iteration count and
+ * the true relative residual.  SILU_ERR_NOT_CONVERGED when maxit is reached
+ * above tol (x holds the last iterate).
+ */
+silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int restart, int maxit, int sweeps_L,
+                         int sweeps_U, int precond, int* iters_out, double* relres_out);
+
+/* Preallocate the device workspace for nrhs right-hand sides and a restart
+ * length (0 = none), so that later calls do not allocate. */
+silu_status silu_ilu_reserve(silu_ilu F, int nrhs, int restart);
+
+/* Sizes: rows, stored entries of L_s and of the stored upper factor
+ * (Utilde_s for SILU_SCALE_ROW, U with its diagonal otherwise), level counts. */
+silu_status silu_ilu_stats(silu_ilu F, int64_t* n, int64_t* nnz_L, int64_t* nnz_U, int32_t* levels_L,
+                           int32_t* levels_U);
+
+/*
+ * Copy the host factors out (parity tests).  Any pointer may be NULL.
+ *  Lp[n+1], Lc, Lv: strict lower L_s.   Up[n+1], Uc, Uv: U with the diagonal
+ *  first in each row (as factored, before scaling).  Sp[n+1], Sc, Sv:
+ *  Utilde_s = strict part of D^{-1} U.  dinv[n] = 1 / diag(U).
+ *  levL[n], levU[n]: level of each row in L_s and in the upper factor.
+ */
+silu_status silu_ilu_export(silu_ilu F, int64_t* Lp, int32_t* Lc, double* Lv, int64_t* Up, int32_t* Uc, double* Uv,
+                            int64_t* Sp, int32_t* Sc, double* Sv, double* dinv, int32_t* levL, int32_t* levU);
+/* Entry counts of U with diagonal (for export buffer sizing). */
+silu_status silu_ilu_export_sizes(silu_ilu F, int64_t* nnz_L, int64_t* nnz_Ufull, int64_t* nnz_Us);
+
+void silu_ilu_destroy(silu_ilu F);
+
+/*
+ * Kernel launch shape of the sweeps: lanes per row (power of two, 1..32) for
+ * L_s, the upper factor and A; 0 restores the library's choice.  Used by the
+ * autotuner; results do not depend on it beyond rounding order.
+ */
+silu_status silu_ilu_set_lanes(silu_ilu F, int lanes_L, int lanes_U, int lanes_A);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SILU_H */

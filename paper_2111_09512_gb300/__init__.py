@@ -1,0 +1,346 @@
+"""silu: scaled-ILU Richardson smoothers on GB300 (sm_103a).
+
+Thin ctypes binding of libsilu.so, the C ABI declared in include/silu.h.  The
+functions keep the C names (silu_ctx_create, silu_mat_create, ilu_setup,
+ilu_refactor, ilu_smooth, direct_trisolve, fgmres_solve, ...) and only
+marshal arguments: host CSR arrays as numpy, device vectors as torch CUDA
+tensors (or raw pointers), the stream as a torch stream.  Every step of the
+smoother runs in the library's CUDA kernels.  There is no fallback: if
+libsilu.so is missing or fails to load, every call raises.
+
+The method is that of Thomas, Carr, Mullowney, Swirydowicz and Day, "Scaled
+ILU Smoothers for Navier-Stokes Pressure Projection" (arXiv 2111.09512):
+incomplete LU factors with the upper factor row-scaled to unit diagonal
+(Eq. extractD, Eq. newD), triangular solves replaced by Richardson sweeps
+(Alg. ILUJac, Eq. richard), inside flexible GMRES (Sec. 6).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsilu.so")
+
+# silu_status
+OK, ERR_INVALID_ARG, ERR_ZERO_PIVOT, ERR_NOT_CONVERGED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, WARN_DIVERGED, \
+    ERR_NO_DEVICE = range(9)
+# silu_kind
+ILU0, ILUK, ILUT = 0, 1, 2
+# silu_scale
+SCALE_NONE, SCALE_ROW, SCALE_NONE_RICH = 0, 1, 2
+# silu_prec
+FP64, FP32 = 0, 1
+# silu_precond
+PRECOND_SWEEPS, PRECOND_DIRECT, PRECOND_NONE = 0, 1, 2
+# silu_kclass
+K_RESIDUAL, K_SWEEP_L, K_SWEEP_U, K_LEVEL, K_KRYLOV, K_ELEMENTWISE = range(6)
+K_NAMES = ["residual", "sweep_L", "sweep_U", "level", "krylov", "elementwise"]
+
+KINDS = {"ilu0": ILU0, "iluk": ILUK, "ilut": ILUT}
+
+_lib = None
+
+
+class SiluError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"silu status {status}: {message}")
+        self.status = status
+
+
+def build(force: bool = False) -> str:
+    """Compile libsilu.so for sm_103a (nvcc must be on the machine)."""
+    from . import _build
+    return _build.build(force=force)
+
+
+def load():
+    """Load libsilu.so and declare the C signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise SiluError(-1, f"{LIB_PATH} is not built: call paper_2111_09512_gb300.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    pvp = ctypes.POINTER(vp)
+    sigs = {
+        "silu_version": (ctypes.c_char_p, []),
+        "silu_ctx_create": (i32, [i32, vp, pvp]),
+        "silu_ctx_destroy": (None, [vp]),
+        "silu_last_error": (ctypes.c_char_p, [vp]),
+        "silu_mat_create": (i32, [vp, i64, i64, vp, vp, vp, pvp]),
+        "silu_mat_destroy": (None, [vp]),
+        "ilu_setup": (i32, [vp, vp, i32, dbl, i32, i32, i32, pvp]),
+        "ilu_refactor": (i32, [vp, vp]),
+        "ilu_smooth": (i32, [vp, vp, vp, i32, i32, i32]),
+        "direct_trisolve": (i32, [vp, vp, vp, i32]),
+        "fgmres_solve": (i32, [vp, vp, vp, dbl, i32, i32, i32, i32, i32, ctypes.POINTER(i32),
+                               ctypes.POINTER(dbl)]),
+        "silu_ilu_reserve": (i32, [vp, i32, i32]),
+        "silu_ilu_stats": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+        "silu_ilu_export": (i32, [vp] * 13),
+        "silu_ilu_export_sizes": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "silu_ilu_destroy": (None, [vp]),
+        "silu_ilu_set_lanes": (i32, [vp, i32, i32, i32]),
+        "silu_ctx_profile": (i32, [vp, i32]),
+        "silu_ctx_profile_read": (i32, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl)]),
+        "silu_ctx_launch_count": (i32, [vp, ctypes.POINTER(i64)]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names the binding declares (all must be exported by libsilu.so)."""
+    return ["silu_version", "silu_ctx_create", "silu_ctx_destroy", "silu_last_error", "silu_mat_create",
+            "silu_mat_destroy", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
+            "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
+            "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
+            "silu_ctx_launch_count"]
+
+
+def _ptr(t) -> int:
+    """Device (or host) address of a torch tensor / numpy array / int."""
+    if t is None:
+        return 0
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return int(t.data_ptr())
+
+
+def _check(ctx_handle, status: int, what: str):
+    if status != OK:
+        msg = load().silu_last_error(ctx_handle) if ctx_handle else b""
+        raise SiluError(status, f"{what}: {msg.decode() if msg else ''}")
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ----------------------------------------------------------------- handles
+
+class Context:
+    """silu_ctx: a device (or -1 for host-only setup) and a CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        lib = load()
+        h = ctypes.c_void_p()
+        st = lib.silu_ctx_create(device, _stream_handle(stream), ctypes.byref(h))
+        if st != OK:
+            raise SiluError(st, f"silu_ctx_create(device={device})")
+        self.handle = h.value
+        self.device = device
+        self.stream = stream
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().silu_ctx_destroy(self.handle)
+            self.handle = None
+
+    def profile(self, enable: bool):
+        """Start (clearing earlier records) or stop event timing of the library's launches."""
+        _check(self.handle, load().silu_ctx_profile(self.handle, 1 if enable else 0), "silu_ctx_profile")
+
+    def profile_read(self):
+        """{class name: (launches, total ms)} of the recorded launches (blocks on the stream)."""
+        out = {}
+        for k, name in enumerate(K_NAMES):
+            cnt, ms = ctypes.c_int64(), ctypes.c_double()
+            _check(self.handle, load().silu_ctx_profile_read(self.handle, k, ctypes.byref(cnt), ctypes.byref(ms)),
+                   "silu_ctx_profile_read")
+            out[name] = (cnt.value, ms.value)
+        return out
+
+    def launch_count(self) -> int:
+        """Kernels this context has launched since it was created."""
+        c = ctypes.c_int64()
+        _check(self.handle, load().silu_ctx_launch_count(self.handle, ctypes.byref(c)), "silu_ctx_launch_count")
+        return c.value
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Matrix:
+    """silu_mat: a CSR matrix copied into the library (and onto the device)."""
+
+    def __init__(self, ctx: Context, row_ptr, col_idx, val):
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        va = np.ascontiguousarray(val, dtype=np.float64)
+        n = len(rp) - 1
+        h = ctypes.c_void_p()
+        st = load().silu_mat_create(ctx.handle, n, int(rp[-1]), _ptr(rp), _ptr(ci), _ptr(va), ctypes.byref(h))
+        _check(ctx.handle, st, "silu_mat_create")
+        self.handle = h.value
+        self.ctx = ctx
+        self.n = n
+        self.nnz = int(rp[-1])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().silu_mat_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ILU:
+    """silu_ilu: factors of a Matrix, row-scaled and packed on the device."""
+
+    def __init__(self, A: Matrix, kind="ilu0", tau: float = 0.0, fill: int = 0, scale: int = SCALE_ROW,
+                 prec: int = FP64):
+        kind = KINDS[kind] if isinstance(kind, str) else kind
+        h = ctypes.c_void_p()
+        st = load().ilu_setup(A.ctx.handle, A.handle, kind, float(tau), int(fill), scale, prec, ctypes.byref(h))
+        _check(A.ctx.handle, st, "ilu_setup")
+        self.handle = h.value
+        self.A = A          # keeps the matrix alive as long as the factors
+        self.ctx = A.ctx
+        self.n = A.n
+        self.prec = prec
+        self.scale = scale
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().silu_ilu_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- queries
+    def stats(self):
+        n, nl, nu = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        ll, lu = ctypes.c_int32(), ctypes.c_int32()
+        _check(self.ctx.handle, load().silu_ilu_stats(self.handle, ctypes.byref(n), ctypes.byref(nl),
+                                                      ctypes.byref(nu), ctypes.byref(ll), ctypes.byref(lu)),
+               "silu_ilu_stats")
+        return {"n": n.value, "nnz_L": nl.value, "nnz_U": nu.value, "levels_L": ll.value, "levels_U": lu.value}
+
+    def export(self):
+        """Host copies: L_s, U (diagonal first), Utilde_s, dinv, level of each row."""
+        lib = load()
+        nl, nf, ns = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self.ctx.handle, lib.silu_ilu_export_sizes(self.handle, ctypes.byref(nl), ctypes.byref(nf),
+                                                          ctypes.byref(ns)), "silu_ilu_export_sizes")
+        n = self.n
+        Lp, Up, Sp = (np.empty(n + 1, np.int64) for _ in range(3))
+        Lc, Lv = np.empty(max(nl.value, 1), np.int32), np.empty(max(nl.value, 1), np.float64)
+        Uc, Uv = np.empty(max(nf.value, 1), np.int32), np.empty(max(nf.value, 1), np.float64)
+        Sc, Sv = np.empty(max(ns.value, 1), np.int32), np.empty(max(ns.value, 1), np.float64)
+        dinv = np.empty(max(n, 1), np.float64)
+        levL, levU = np.empty(max(n, 1), np.int32), np.empty(max(n, 1), np.int32)
+        st = lib.silu_ilu_export(self.handle, *[_ptr(a) for a in (Lp, Lc, Lv, Up, Uc, Uv, Sp, Sc, Sv, dinv,
+                                                                   levL, levU)])
+        _check(self.ctx.handle, st, "silu_ilu_export")
+        return {"L": (Lp, Lc[:nl.value], Lv[:nl.value]), "U": (Up, Uc[:nf.value], Uv[:nf.value]),
+                "Us": (Sp, Sc[:ns.value], Sv[:ns.value]), "dinv": dinv[:n], "levL": levL[:n],
+                "levU": levU[:n]}
+
+    def reserve(self, nrhs: int = 1, restart: int = 0):
+        _check(self.ctx.handle, load().silu_ilu_reserve(self.handle, nrhs, restart), "silu_ilu_reserve")
+
+    def set_lanes(self, lanes_L: int = 0, lanes_U: int = 0, lanes_A: int = 0):
+        _check(self.ctx.handle, load().silu_ilu_set_lanes(self.handle, lanes_L, lanes_U, lanes_A),
+               "silu_ilu_set_lanes")
+
+
+# ------------------------------------------------------- C-named functions
+
+def silu_version() -> str:
+    return load().silu_version().decode()
+
+
+def silu_ctx_create(device: int = 0, stream=None) -> Context:
+    return Context(device, stream)
+
+
+def silu_mat_create(ctx: Context, row_ptr, col_idx, val) -> Matrix:
+    return Matrix(ctx, row_ptr, col_idx, val)
+
+
+def ilu_setup(ctx: Context, A: Matrix, kind="ilu0", tau: float = 0.0, fill: int = 0, scale: int = SCALE_ROW,
+              prec: int = FP64) -> ILU:
+    if A.ctx is not ctx:
+        raise SiluError(ERR_INVALID_ARG, "matrix belongs to another context")
+    return ILU(A, kind, tau, fill, scale, prec)
+
+
+def ilu_refactor(F: ILU, new_val) -> None:
+    v = np.ascontiguousarray(new_val, dtype=np.float64)
+    if v.size != F.A.nnz:
+        raise SiluError(ERR_INVALID_ARG, "new values must match the matrix's entry count")
+    _check(F.ctx.handle, load().ilu_refactor(F.handle, _ptr(v)), "ilu_refactor")
+
+
+def _nrhs_of(x, n):
+    shape = tuple(x.shape)
+    if len(shape) == 1:
+        return 1
+    if shape[0] != n:
+        raise SiluError(ERR_INVALID_ARG, "vectors must be n x nrhs")
+    return int(shape[1])
+
+
+def _check_vec(t, n, nrhs):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise SiluError(ERR_INVALID_ARG, "vectors must be contiguous float64 CUDA tensors")
+    if t.numel() != n * nrhs:
+        raise SiluError(ERR_INVALID_ARG, "vector size mismatch")
+
+
+def ilu_smooth(F: ILU, x, b, sweeps_L: int, sweeps_U: int) -> None:
+    """x <- x + M^{-1}(b - A x) with sweeps_L / sweeps_U Richardson sweeps (in place)."""
+    nrhs = _nrhs_of(x, F.n)
+    _check_vec(x, F.n, nrhs)
+    _check_vec(b, F.n, nrhs)
+    _check(F.ctx.handle, load().ilu_smooth(F.handle, _ptr(x), _ptr(b), nrhs, sweeps_L, sweeps_U), "ilu_smooth")
+
+
+def direct_trisolve(F: ILU, x, b) -> None:
+    """x <- x + Utilde^{-1} D^{-1} L^{-1} (b - A x) by level-scheduled substitution."""
+    nrhs = _nrhs_of(x, F.n)
+    _check_vec(x, F.n, nrhs)
+    _check_vec(b, F.n, nrhs)
+    _check(F.ctx.handle, load().direct_trisolve(F.handle, _ptr(x), _ptr(b), nrhs), "direct_trisolve")
+
+
+def fgmres_solve(F: ILU, x, b, tol: float = 1e-8, restart: int = 30, maxit: int = 1000, sweeps_L: int = 3,
+                 sweeps_U: int = 3, precond: int = PRECOND_SWEEPS, raise_on_nonconvergence: bool = False):
+    """FGMRES(restart) on A x = b; returns (status, iterations, true relative residual)."""
+    _check_vec(x, F.n, 1)
+    _check_vec(b, F.n, 1)
+    its = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = load().fgmres_solve(F.handle, _ptr(x), _ptr(b), float(tol), int(restart), int(maxit), int(sweeps_L),
+                             int(sweeps_U), int(precond), ctypes.byref(its), ctypes.byref(rel))
+    if st not in (OK, ERR_NOT_CONVERGED) or (st == ERR_NOT_CONVERGED and raise_on_nonconvergence):
+        _check(F.ctx.handle, st, "fgmres_solve")
+    return st, its.value, rel.value

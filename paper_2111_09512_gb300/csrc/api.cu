@@ -1,0 +1,877 @@
+// C ABI of libsilu (declared in include/silu.h): handles, host setup and
+// the stream-ordered orchestration of the device kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "host_factor.h"
+#include "silu.h"
+
+using silu::DevCsr;
+
+namespace {
+
+// Owning device buffer.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t ensure(size_t b) {
+    if (b <= bytes && p) return cudaSuccess;
+    release();
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = b;
+    return cudaSuccess;
+  }
+  template <class T>
+  T* as() const {
+    return (T*)p;
+  }
+};
+
+}  // namespace
+
+struct silu_ctx_s {
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  double* pinned = nullptr;  // small host buffer for scalar read-backs
+  int64_t launches = 0;      // kernels launched on this context
+  // event timing of launches (silu_ctx_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;  // pool; records use pairs (2k, 2k+1)
+  std::vector<int> rec_class;       // class of record k
+  size_t nrec = 0;
+};
+
+struct silu_mat_s {
+  silu_ctx ctx = nullptr;
+  silu::Csr A;
+  DBuf rp, ci, va;
+  DevCsr d;
+};
+
+struct Workspace {
+  size_t vec_bytes = 0;  // per buffer
+  DBuf r, c, p0, p1;
+  int restart = 0;
+  DBuf V, Z, w, H, cs, sn, g, yk, part0, part1, scal;
+};
+
+struct silu_ilu_s {
+  silu_ctx ctx = nullptr;
+  silu_mat A = nullptr;
+  silu_kind kind = SILU_ILU0;
+  silu_scale scale = SILU_SCALE_ROW;
+  silu_prec prec = SILU_FP64;
+  double tau = 0.0;
+  int fill = 0;
+  silu::Factors F;
+  silu::Csr Us;
+  std::vector<double> dinv;
+  std::vector<int32_t> levL, levU, levLptr, levLrows, levUptr, levUrows;
+  int32_t nlevL = 0, nlevU = 0;
+  // device: sweep factors
+  DBuf L_rp, L_ci, L_va, U_rp, U_ci, U_va, d_dinv;
+  DevCsr dL, dU;
+  // device: FP64 L_s and Utilde_s for the direct path (aliases of dL/dU when possible)
+  DBuf L64_va, S_rp, S_ci, S_va, levLrows_d, levUrows_d;
+  DevCsr dL64, dS64;
+  bool direct_ready = false;
+  int lanesL = 0, lanesU = 0, lanesA = 0;
+  int autoL = 4, autoU = 4, autoA = 8;
+  Workspace ws;
+};
+
+namespace {
+
+silu_status set_err(silu_ctx ctx, silu_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+silu_status cuda_err(silu_ctx ctx, cudaError_t e, const char* what) {
+  return set_err(ctx, e == cudaErrorMemoryAllocation ? SILU_ERR_OOM : SILU_ERR_CUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct CudaFail {
+  cudaError_t e;
+  const char* what;
+};
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) throw CudaFail{e_, #call}; \
+  } while (0)
+
+// Counts a kernel launch and, while profiling, brackets it with events.
+struct ProfScope {
+  silu_ctx ctx;
+  size_t k = (size_t)-1;
+  ProfScope(silu_ctx c, int cls) : ctx(c) {
+    ctx->launches++;
+    if (!ctx->profiling) return;
+    k = ctx->nrec;
+    if (ctx->events.size() < 2 * (k + 1)) {
+      for (int t = 0; t < 2; ++t) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+          k = (size_t)-1;
+          return;
+        }
+        ctx->events.push_back(ev);
+      }
+    }
+    if (ctx->rec_class.size() <= k) ctx->rec_class.resize(k + 1);
+    ctx->rec_class[k] = cls;
+    ctx->nrec = k + 1;
+    cudaEventRecord(ctx->events[2 * k], ctx->stream);
+  }
+  ~ProfScope() {
+    if (k != (size_t)-1) cudaEventRecord(ctx->events[2 * k + 1], ctx->stream);
+  }
+};
+
+#define LAUNCH(ctx, cls, call)        \
+  do {                                \
+    ProfScope ps_((ctx), (cls));      \
+    CK(call);                         \
+  } while (0)
+
+int pick_lanes(const silu::Csr& T) {
+  const double avg = T.n ? (double)T.nnz() / (double)T.n : 0.0;
+  int g = 1;
+  while (g < 32 && g < avg) g <<= 1;
+  return std::max(2, g);
+}
+
+template <class T>
+cudaError_t upload(DBuf& b, const T* src, size_t count, cudaStream_t s) {
+  cudaError_t e = b.ensure(sizeof(T) * std::max<size_t>(count, 1));
+  if (e != cudaSuccess) return e;
+  if (count == 0) return cudaSuccess;
+  return cudaMemcpyAsync(b.p, src, sizeof(T) * count, cudaMemcpyHostToDevice, s);
+}
+
+// Upload CSR (int64 row pointers narrowed to int32) with values as double or float.
+cudaError_t upload_csr(const silu::Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& va, DevCsr& d, cudaStream_t s) {
+  std::vector<int32_t> rp32(T.rp.begin(), T.rp.end());
+  cudaError_t e = upload(rp, rp32.data(), rp32.size(), s);
+  if (e == cudaSuccess) e = upload(ci, T.ci.data(), T.ci.size(), s);
+  if (e == cudaSuccess) {
+    if (fp32) {
+      std::vector<float> v32(T.va.begin(), T.va.end());
+      e = upload(va, v32.data(), v32.size(), s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // v32 dies at return
+    } else {
+      e = upload(va, T.va.data(), T.va.size(), s);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // rp32 dies at return
+  d.n = (int)T.n;
+  d.nnz = T.nnz();
+  d.rp = rp.as<int>();
+  d.ci = ci.as<int>();
+  d.va = va.p;
+  d.fp32 = fp32;
+  return e;
+}
+
+silu_status device_ok(silu_ctx ctx) {
+  if (!ctx) return SILU_ERR_INVALID_ARG;
+  if (ctx->device < 0) return set_err(ctx, SILU_ERR_NO_DEVICE, "host-only context");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaSetDevice");
+  return SILU_OK;
+}
+
+cudaError_t ensure_vectors(silu_ilu F, int nrhs) {
+  const size_t bytes = sizeof(double) * (size_t)F->F.L.n * (size_t)nrhs;
+  Workspace& w = F->ws;
+  if (bytes <= w.vec_bytes && w.r.p) return cudaSuccess;
+  cudaError_t e;
+  if ((e = w.r.ensure(bytes)) != cudaSuccess) return e;
+  if ((e = w.c.ensure(bytes)) != cudaSuccess) return e;
+  if ((e = w.p0.ensure(bytes)) != cudaSuccess) return e;
+  if ((e = w.p1.ensure(bytes)) != cudaSuccess) return e;
+  w.vec_bytes = bytes;
+  return cudaSuccess;
+}
+
+cudaError_t ensure_krylov(silu_ilu F, int m) {
+  Workspace& w = F->ws;
+  if (m <= w.restart && w.V.p) return cudaSuccess;
+  const size_t n = (size_t)F->F.L.n;
+  cudaError_t e;
+  if ((e = w.V.ensure(sizeof(double) * n * (size_t)(m + 1))) != cudaSuccess) return e;
+  if ((e = w.Z.ensure(sizeof(double) * n * (size_t)m)) != cudaSuccess) return e;
+  if ((e = w.w.ensure(sizeof(double) * n)) != cudaSuccess) return e;
+  if ((e = w.H.ensure(sizeof(double) * (size_t)(m + 1) * (size_t)m)) != cudaSuccess) return e;
+  if ((e = w.cs.ensure(sizeof(double) * (size_t)m)) != cudaSuccess) return e;
+  if ((e = w.sn.ensure(sizeof(double) * (size_t)m)) != cudaSuccess) return e;
+  if ((e = w.g.ensure(sizeof(double) * (size_t)(m + 1))) != cudaSuccess) return e;
+  if ((e = w.yk.ensure(sizeof(double) * (size_t)m)) != cudaSuccess) return e;
+  if ((e = w.part0.ensure(sizeof(double) * 1024)) != cudaSuccess) return e;
+  if ((e = w.part1.ensure(sizeof(double) * 1024)) != cudaSuccess) return e;
+  if ((e = w.scal.ensure(sizeof(double) * 8)) != cudaSuccess) return e;
+  w.restart = m;
+  return cudaSuccess;
+}
+
+cudaError_t ensure_direct(silu_ilu F) {
+  if (F->direct_ready) return cudaSuccess;
+  cudaStream_t s = F->ctx->stream;
+  cudaError_t e = cudaSuccess;
+  // FP64 L_s: reuse the sweep copy when it is FP64
+  if (F->prec == SILU_FP64) {
+    F->dL64 = F->dL;
+  } else {
+    F->dL64 = F->dL;
+    e = upload(F->L64_va, F->F.L.va.data(), F->F.L.va.size(), s);
+    F->dL64.va = F->L64_va.p;
+    F->dL64.fp32 = false;
+  }
+  if (e != cudaSuccess) return e;
+  // FP64 Utilde_s: reuse when the sweeps use it in FP64
+  if (F->prec == SILU_FP64 && F->scale == SILU_SCALE_ROW) {
+    F->dS64 = F->dU;
+  } else {
+    e = upload_csr(F->Us, false, F->S_rp, F->S_ci, F->S_va, F->dS64, s);
+    if (e != cudaSuccess) return e;
+  }
+  e = upload(F->levLrows_d, F->levLrows.data(), F->levLrows.size(), s);
+  if (e == cudaSuccess) e = upload(F->levUrows_d, F->levUrows.data(), F->levUrows.size(), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) F->direct_ready = true;
+  return e;
+}
+
+int lanes_of(int fixed, int autov) { return fixed > 0 ? fixed : autov; }
+
+// ---------------------------------------------------------------------------
+// One smoother application on columns [0, R) of x/b (leading dimension ldx),
+// workspace pointers offset by the same column.  x_zero: x is an output only
+// (zero initial guess, so r = b and the result is stored, not added).
+// ---------------------------------------------------------------------------
+void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, int mL, int mU, bool x_zero) {
+  cudaStream_t s = F->ctx->stream;
+  const bool f32 = F->prec == SILU_FP32;
+  const size_t es = f32 ? sizeof(float) : sizeof(double);
+  const silu::Mode sm = f32 ? silu::MODE_F : silu::MODE_D;
+  const int n = (int)F->F.L.n;
+  const double* dinv = F->d_dinv.as<double>();
+  const DevCsr& A = F->A->d;
+  char* bufR = F->ws.r.as<char>() + col * es;
+  char* bufC = F->ws.c.as<char>() + col * es;
+  char* bufP0 = F->ws.p0.as<char>() + col * es;
+  char* bufP1 = F->ws.p1.as<char>() + col * es;
+  const int gL = lanes_of(F->lanesL, F->autoL), gU = lanes_of(F->lanesU, F->autoU), gA = lanes_of(F->lanesA, F->autoA);
+  const bool rowscale = F->scale == SILU_SCALE_ROW;
+  const bool jacobi = F->scale == SILU_SCALE_NONE;
+
+  // What happens to y = L^{-1} r once it is known.
+  //   FINAL_Y:   x (+)= y                        (m_U = 0, or m_U = 1 with plain Richardson)
+  //   FINAL_DY:  x (+)= D^{-1} y                 (m_U = 1 with scaling or Jacobi)
+  //   NEED_C:    c = D^{-1} y materialised        (m_U >= 2, row scaling)
+  //   NEED_Y:    y materialised                   (m_U >= 2, unscaled variants)
+  enum { FINAL_Y, FINAL_DY, NEED_C, NEED_Y } after;
+  if (mU == 0 || (mU == 1 && !rowscale && !jacobi))
+    after = FINAL_Y;
+  else if (mU == 1)
+    after = FINAL_DY;
+  else if (rowscale)
+    after = NEED_C;
+  else
+    after = NEED_Y;
+
+  // ---- residual ----------------------------------------------------------
+  const void* r = nullptr;
+  bool r_fused_to_c = false;
+  if (x_zero) {
+    if (f32) {
+      LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_scale(n, R, ldx, b, false, nullptr, bufR, true, s));
+      r = bufR;
+    } else {
+      r = b;
+    }
+  } else if (mL <= 1 && after == NEED_C) {
+    // r is only needed as D^{-1} r: fuse the scaling into the residual
+    LAUNCH(F->ctx, SILU_K_RESIDUAL, silu::launch_sweep(A, f32 ? silu::MODE_DF : silu::MODE_D, R, gA, ldx, b, x, bufC, dinv, nullptr,
+                          silu::EPI_SCALE, s));
+    r_fused_to_c = true;
+  } else {
+    LAUNCH(F->ctx, SILU_K_RESIDUAL, silu::launch_sweep(A, f32 ? silu::MODE_DF : silu::MODE_D, R, gA, ldx, b, x, bufR, dinv, nullptr,
+                          silu::EPI_STORE, s));
+    r = bufR;
+  }
+
+  // ---- L sweeps: y^1 = r, y^{k} = r - L_s y^{k-1} -------------------------
+  const void* y = r;  // current iterate
+  const void* cvec = r_fused_to_c ? (const void*)bufC : nullptr;
+  bool done = false;  // x already written
+  if (mL >= 2) {
+    const void* in = r;
+    char* pp[2] = {bufP0, bufP1};
+    for (int k = 2; k <= mL; ++k) {
+      const bool last = (k == mL);
+      char* out = pp[k & 1];
+      int epi = silu::EPI_STORE;
+      void* o = out;
+      if (last) {
+        if (after == FINAL_Y) {
+          epi = x_zero ? silu::EPI_SETX : silu::EPI_ADDX;
+          o = nullptr;
+        } else if (after == FINAL_DY) {
+          epi = x_zero ? silu::EPI_SCALE_SETX : silu::EPI_SCALE_ADDX;
+          o = nullptr;
+        } else if (after == NEED_C) {
+          epi = silu::EPI_SCALE;
+          o = bufC;
+        }
+      }
+      LAUNCH(F->ctx, SILU_K_SWEEP_L, silu::launch_sweep(F->dL, sm, R, gL, ldx, r, in, o, dinv, x, epi, s));
+      in = out;
+      if (last) {
+        if (after == FINAL_Y || after == FINAL_DY) done = true;
+        if (after == NEED_C) cvec = bufC;
+        if (after == NEED_Y) y = out;
+      }
+    }
+  }
+  if (!done && after == FINAL_Y) {
+    LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_addx(n, R, ldx, y, f32, nullptr, x, !x_zero, s));
+    done = true;
+  }
+  if (!done && after == FINAL_DY) {
+    LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_addx(n, R, ldx, y, f32, dinv, x, !x_zero, s));
+    done = true;
+  }
+  if (done) return;
+
+  // ---- U sweeps -----------------------------------------------------------
+  if (after == NEED_C) {
+    if (!cvec) {  // y = r came without a fused scaling (x_zero, m_L <= 1)
+      LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_scale(n, R, ldx, y, f32, dinv, bufC, f32, s));
+      cvec = bufC;
+    }
+    // v^1 = c; v^k = c - Utilde_s v^{k-1}
+    const void* in = cvec;
+    char* pp[2] = {bufP0, bufP1};
+    for (int k = 2; k <= mU; ++k) {
+      const bool last = (k == mU);
+      char* out = pp[k & 1];
+      const int epi = last ? (x_zero ? silu::EPI_SETX : silu::EPI_ADDX) : silu::EPI_STORE;
+      LAUNCH(F->ctx, SILU_K_SWEEP_U, silu::launch_sweep(F->dU, sm, R, gU, ldx, cvec, in, last ? nullptr : out, dinv, x, epi, s));
+      in = out;
+    }
+    return;
+  }
+  // unscaled variants: c = y (unscaled), two ping-pong buffers distinct from y
+  char* cand[4] = {bufC, bufP0, bufP1, bufR};
+  char* q[2] = {nullptr, nullptr};
+  int nq = 0;
+  for (int t = 0; t < 4 && nq < 2; ++t)
+    if ((const void*)cand[t] != y) q[nq++] = cand[t];
+  const void* in;
+  if (jacobi) {
+    // v^1 = D^{-1} y
+    LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_scale(n, R, ldx, y, f32, dinv, q[0], f32, s));
+    in = q[0];
+  } else {
+    in = y;  // v^1 = y
+  }
+  for (int k = 2; k <= mU; ++k) {
+    const bool last = (k == mU);
+    char* out = (in == q[0]) ? q[1] : q[0];
+    int epi;
+    if (jacobi)
+      epi = last ? (x_zero ? silu::EPI_JAC_SETX : silu::EPI_JAC_ADDX) : silu::EPI_JAC;
+    else
+      epi = last ? (x_zero ? silu::EPI_RICH_SETX : silu::EPI_RICH_ADDX) : silu::EPI_RICH;
+    LAUNCH(F->ctx, SILU_K_SWEEP_U, silu::launch_sweep(F->dU, sm, R, gU, ldx, y, in, last ? nullptr : out, dinv, x, epi, s));
+    in = out;
+  }
+}
+
+// Direct application on columns [0, R): x (+)= Utilde^{-1} D^{-1} L^{-1} (b - A x).
+// y holds r and is overwritten by L^{-1} r level by level; the lower level
+// kernel also writes c = D^{-1} y, which the upper levels overwrite with v.
+void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, bool x_zero) {
+  cudaStream_t s = F->ctx->stream;
+  const int n = (int)F->F.L.n;
+  const double* dinv = F->d_dinv.as<double>();
+  double* y = F->ws.r.as<double>() + col;
+  double* c = F->ws.c.as<double>() + col;
+  const int gL = lanes_of(F->lanesL, F->autoL), gU = lanes_of(F->lanesU, F->autoU), gA = lanes_of(F->lanesA, F->autoA);
+  if (x_zero)
+    LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_scale(n, R, ldx, b, false, nullptr, y, false, s));
+  else
+    LAUNCH(F->ctx, SILU_K_RESIDUAL, silu::launch_sweep(F->A->d, silu::MODE_D, R, gA, ldx, b, x, y, nullptr, nullptr, silu::EPI_STORE, s));
+  const int* rowsL = F->levLrows_d.as<int>();
+  const int* rowsU = F->levUrows_d.as<int>();
+  for (int l = 0; l < F->nlevL; ++l) {
+    const int b0 = F->levLptr[l], b1 = F->levLptr[l + 1];
+    LAUNCH(F->ctx, SILU_K_LEVEL, silu::launch_level(F->dL64, rowsL + b0, b1 - b0, R, gL, ldx, y, dinv, c, nullptr, s));
+  }
+  for (int l = 0; l < F->nlevU; ++l) {
+    const int b0 = F->levUptr[l], b1 = F->levUptr[l + 1];
+    LAUNCH(F->ctx, SILU_K_LEVEL, silu::launch_level(F->dS64, rowsU + b0, b1 - b0, R, gU, ldx, c, dinv, nullptr, x_zero ? nullptr : x, s));
+  }
+  if (x_zero) LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_addx(n, R, ldx, c, false, nullptr, x, false, s));
+}
+
+int chunk_width(int left) { return left >= 4 ? 4 : (left >= 2 ? 2 : 1); }
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char* silu_version(void) { return "silu 0.1 (sm_103a)"; }
+
+silu_status silu_ctx_create(int device, void* cuda_stream, silu_ctx* out) {
+  if (!out) return SILU_ERR_INVALID_ARG;
+  *out = nullptr;
+  silu_ctx c = new (std::nothrow) silu_ctx_s;
+  if (!c) return SILU_ERR_OOM;
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  if (device >= 0) {
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || device >= count) {
+      delete c;
+      return SILU_ERR_NO_DEVICE;
+    }
+    e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->pinned, 64 * sizeof(double));
+    if (e != cudaSuccess) {
+      delete c;
+      return SILU_ERR_CUDA;
+    }
+  }
+  *out = c;
+  return SILU_OK;
+}
+
+void silu_ctx_destroy(silu_ctx ctx) {
+  if (!ctx) return;
+  if (ctx->device >= 0) cudaSetDevice(ctx->device);
+  for (cudaEvent_t ev : ctx->events) cudaEventDestroy(ev);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  delete ctx;
+}
+
+silu_status silu_ctx_profile(silu_ctx ctx, int enable) {
+  if (!ctx) return SILU_ERR_INVALID_ARG;
+  if (enable) {
+    silu_status ds = device_ok(ctx);
+    if (ds != SILU_OK) return ds;
+    ctx->nrec = 0;
+  }
+  ctx->profiling = enable != 0;
+  return SILU_OK;
+}
+
+silu_status silu_ctx_profile_read(silu_ctx ctx, int kclass, int64_t* launches, double* total_ms) {
+  if (!ctx || kclass < 0 || kclass >= SILU_K_NCLASS) return SILU_ERR_INVALID_ARG;
+  int64_t cnt = 0;
+  double ms = 0.0;
+  if (ctx->nrec > 0) {
+    silu_status ds = device_ok(ctx);
+    if (ds != SILU_OK) return ds;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamSynchronize");
+    for (size_t k = 0; k < ctx->nrec; ++k) {
+      if (ctx->rec_class[k] != kclass) continue;
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ctx->events[2 * k], ctx->events[2 * k + 1]);
+      if (e != cudaSuccess) return cuda_err(ctx, e, "cudaEventElapsedTime");
+      ms += t;
+      ++cnt;
+    }
+  }
+  if (launches) *launches = cnt;
+  if (total_ms) *total_ms = ms;
+  return SILU_OK;
+}
+
+silu_status silu_ctx_launch_count(silu_ctx ctx, int64_t* launches) {
+  if (!ctx || !launches) return SILU_ERR_INVALID_ARG;
+  *launches = ctx->launches;
+  return SILU_OK;
+}
+
+const char* silu_last_error(silu_ctx ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+silu_status silu_mat_create(silu_ctx ctx, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                            const double* val, silu_mat* out) {
+  if (!ctx || !out) return SILU_ERR_INVALID_ARG;
+  *out = nullptr;
+  silu_mat M = new (std::nothrow) silu_mat_s;
+  if (!M) return set_err(ctx, SILU_ERR_OOM, "out of host memory");
+  M->ctx = ctx;
+  std::string msg;
+  try {
+    int st = silu::csr_canonical(n, nnz, row_ptr, col_idx, val, M->A, msg);
+    if (st != silu::H_OK) {
+      delete M;
+      return set_err(ctx, (silu_status)st, msg);
+    }
+    if (ctx->device >= 0) {
+      silu_status ds = device_ok(ctx);
+      if (ds != SILU_OK) {
+        delete M;
+        return ds;
+      }
+      cudaError_t e = upload_csr(M->A, false, M->rp, M->ci, M->va, M->d, ctx->stream);
+      if (e != cudaSuccess) {
+        delete M;
+        return cuda_err(ctx, e, "upload of A");
+      }
+    }
+  } catch (const std::bad_alloc&) {
+    delete M;
+    return set_err(ctx, SILU_ERR_OOM, "out of host memory");
+  }
+  *out = M;
+  return SILU_OK;
+}
+
+void silu_mat_destroy(silu_mat A) { delete A; }
+
+silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int fill, silu_scale scale,
+                      silu_prec prec, silu_ilu* out) {
+  if (!ctx || !A || !out || A->ctx != ctx) return set_err(ctx, SILU_ERR_INVALID_ARG, "bad handle");
+  *out = nullptr;
+  if (kind < SILU_ILU0 || kind > SILU_ILUT || scale < SILU_SCALE_NONE || scale > SILU_SCALE_NONE_RICH ||
+      prec < SILU_FP64 || prec > SILU_FP32)
+    return set_err(ctx, SILU_ERR_INVALID_ARG, "bad enum value");
+  silu_ilu F = new (std::nothrow) silu_ilu_s;
+  if (!F) return set_err(ctx, SILU_ERR_OOM, "out of host memory");
+  F->ctx = ctx;
+  F->A = A;
+  F->kind = kind;
+  F->scale = scale;
+  F->prec = prec;
+  F->tau = tau;
+  F->fill = fill;
+  std::string msg;
+  try {
+    int st;
+    if (kind == SILU_ILU0)
+      st = silu::factor_ilu0(A->A, F->F, msg);
+    else if (kind == SILU_ILUK)
+      st = silu::factor_iluk(A->A, fill, F->F, msg);
+    else
+      st = silu::factor_ilut(A->A, tau, fill, F->F, msg);
+    if (st == silu::H_OK) st = silu::row_scale(F->F.U, F->Us, F->dinv, msg);
+    if (st != silu::H_OK) {
+      delete F;
+      return set_err(ctx, (silu_status)st, msg);
+    }
+    F->nlevL = silu::levels_lower(F->F.L, F->levL);
+    F->nlevU = silu::levels_upper(F->F.U, true, F->levU);
+    silu::group_levels(F->levL, F->nlevL, F->levLptr, F->levLrows);
+    silu::group_levels(F->levU, F->nlevU, F->levUptr, F->levUrows);
+    const silu::Csr& Ut = (scale == SILU_SCALE_ROW) ? F->Us : F->F.U;
+    F->autoL = pick_lanes(F->F.L);
+    F->autoU = pick_lanes(Ut);
+    F->autoA = pick_lanes(A->A);
+    if (ctx->device >= 0) {
+      silu_status ds = device_ok(ctx);
+      if (ds != SILU_OK) {
+        delete F;
+        return ds;
+      }
+      cudaStream_t s = ctx->stream;
+      const bool f32 = prec == SILU_FP32;
+      cudaError_t e = upload_csr(F->F.L, f32, F->L_rp, F->L_ci, F->L_va, F->dL, s);
+      if (e == cudaSuccess) e = upload_csr(Ut, f32, F->U_rp, F->U_ci, F->U_va, F->dU, s);
+      if (e == cudaSuccess) e = upload(F->d_dinv, F->dinv.data(), F->dinv.size(), s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        delete F;
+        return cuda_err(ctx, e, "upload of the factors");
+      }
+    }
+  } catch (const std::bad_alloc&) {
+    delete F;
+    return set_err(ctx, SILU_ERR_OOM, "out of host memory");
+  }
+  *out = F;
+  return SILU_OK;
+}
+
+silu_status ilu_refactor(silu_ilu F, const double* new_val) {
+  if (!F || !new_val) return SILU_ERR_INVALID_ARG;
+  silu_ctx ctx = F->ctx;
+  if (F->kind == SILU_ILUT) return set_err(ctx, SILU_ERR_INVALID_ARG, "ILUT has no reusable symbolic phase");
+  std::string msg;
+  try {
+    silu::Csr& A = F->A->A;
+    for (int64_t p = 0; p < A.nnz(); ++p)
+      if (!std::isfinite(new_val[p])) return set_err(ctx, SILU_ERR_INVALID_ARG, "non-finite value");
+    std::copy(new_val, new_val + A.nnz(), A.va.begin());
+    int st = silu::refactor_numeric(A, F->F, msg);
+    if (st == silu::H_OK) st = silu::row_scale(F->F.U, F->Us, F->dinv, msg);
+    if (st != silu::H_OK) return set_err(ctx, (silu_status)st, msg);
+    if (ctx->device >= 0) {
+      silu_status ds = device_ok(ctx);
+      if (ds != SILU_OK) return ds;
+      cudaStream_t s = ctx->stream;
+      const bool f32 = F->prec == SILU_FP32;
+      const silu::Csr& Ut = (F->scale == SILU_SCALE_ROW) ? F->Us : F->F.U;
+      cudaError_t e = upload(F->A->va, A.va.data(), A.va.size(), s);
+      if (e == cudaSuccess) e = upload_csr(F->F.L, f32, F->L_rp, F->L_ci, F->L_va, F->dL, s);
+      if (e == cudaSuccess) e = upload_csr(Ut, f32, F->U_rp, F->U_ci, F->U_va, F->dU, s);
+      if (e == cudaSuccess) e = upload(F->d_dinv, F->dinv.data(), F->dinv.size(), s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_err(ctx, e, "upload of the refactored factors");
+      F->A->d.va = F->A->va.p;
+      F->direct_ready = false;
+    }
+  } catch (const std::bad_alloc&) {
+    return set_err(ctx, SILU_ERR_OOM, "out of host memory");
+  }
+  return SILU_OK;
+}
+
+silu_status silu_ilu_reserve(silu_ilu F, int nrhs, int restart) {
+  if (!F || nrhs < 1 || restart < 0) return SILU_ERR_INVALID_ARG;
+  silu_status ds = device_ok(F->ctx);
+  if (ds != SILU_OK) return ds;
+  cudaError_t e = ensure_vectors(F, nrhs);
+  if (e == cudaSuccess && restart > 0) e = ensure_krylov(F, restart);
+  if (e != cudaSuccess) return cuda_err(F->ctx, e, "workspace");
+  return SILU_OK;
+}
+
+silu_status ilu_smooth(silu_ilu F, double* x, const double* b, int nrhs, int sweeps_L, int sweeps_U) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  silu_ctx ctx = F->ctx;
+  if (!x || !b || nrhs < 1 || sweeps_L < 0 || sweeps_U < 0)
+    return set_err(ctx, SILU_ERR_INVALID_ARG, "ilu_smooth: bad argument");
+  silu_status ds = device_ok(ctx);
+  if (ds != SILU_OK) return ds;
+  if (F->F.L.n == 0) return SILU_OK;
+  try {
+    CK(ensure_vectors(F, nrhs));
+    for (int c0 = 0; c0 < nrhs;) {
+      const int R = chunk_width(nrhs - c0);
+      smooth_chunk(F, x + c0, b + c0, R, nrhs, (size_t)c0, sweeps_L, sweeps_U, false);
+      c0 += R;
+    }
+  } catch (const CudaFail& f) {
+    return cuda_err(ctx, f.e, f.what);
+  }
+  return SILU_OK;
+}
+
+silu_status direct_trisolve(silu_ilu F, double* x, const double* b, int nrhs) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  silu_ctx ctx = F->ctx;
+  if (!x || !b || nrhs < 1) return set_err(ctx, SILU_ERR_INVALID_ARG, "direct_trisolve: bad argument");
+  silu_status ds = device_ok(ctx);
+  if (ds != SILU_OK) return ds;
+  if (F->F.L.n == 0) return SILU_OK;
+  try {
+    CK(ensure_vectors(F, nrhs));
+    CK(ensure_direct(F));
+    for (int c0 = 0; c0 < nrhs;) {
+      const int R = chunk_width(nrhs - c0);
+      direct_chunk(F, x + c0, b + c0, R, nrhs, (size_t)c0, false);
+      c0 += R;
+    }
+  } catch (const CudaFail& f) {
+    return cuda_err(ctx, f.e, f.what);
+  }
+  return SILU_OK;
+}
+
+silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int restart, int maxit, int sweeps_L,
+                         int sweeps_U, int precond, int* iters_out, double* relres_out) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  silu_ctx ctx = F->ctx;
+  if (iters_out) *iters_out = 0;
+  if (relres_out) *relres_out = 0.0;
+  if (!x || !b || !(tol >= 0.0) || restart < 1 || maxit < 0 || sweeps_L < 0 || sweeps_U < 0 || precond < 0 ||
+      precond > 2)
+    return set_err(ctx, SILU_ERR_INVALID_ARG, "fgmres_solve: bad argument");
+  silu_status ds = device_ok(ctx);
+  if (ds != SILU_OK) return ds;
+  const int n = (int)F->F.L.n;
+  const int m = restart;
+  cudaStream_t s = ctx->stream;
+  int its = 0;
+  double relres = 0.0;
+  silu_status result = SILU_OK;
+  try {
+    CK(ensure_vectors(F, 1));
+    CK(ensure_krylov(F, m));
+    if (precond == SILU_PRECOND_DIRECT) CK(ensure_direct(F));
+    Workspace& W = F->ws;
+    double* V = W.V.as<double>();
+    double* Z = W.Z.as<double>();
+    double* w = W.w.as<double>();
+    double* H = W.H.as<double>();
+    double* g = W.g.as<double>();
+    double* part[2] = {W.part0.as<double>(), W.part1.as<double>()};
+    double* scal = W.scal.as<double>();
+    double* hp = ctx->pinned;
+    const int gA = lanes_of(F->lanesA, F->autoA);
+    auto vec = [&](double* base, int k) { return base + (size_t)k * (size_t)n; };
+    // ||b||
+    LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_dot_part(n, b, b, part[0], s));
+    LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_norm_final(n, part[0], scal, s));
+    CK(cudaMemcpyAsync(hp, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double bnorm = hp[0];
+    if (n == 0 || bnorm == 0.0) {
+      if (n > 0) CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, s));
+      CK(cudaStreamSynchronize(s));
+      return SILU_OK;
+    }
+    for (;;) {
+      // true residual r = b - A x into V_0, beta = ||r||
+      LAUNCH(F->ctx, SILU_K_RESIDUAL, silu::launch_sweep(F->A->d, silu::MODE_D, 1, gA, 1, b, x, V, nullptr, nullptr, silu::EPI_STORE, s));
+      LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_dot_part(n, V, V, part[0], s));
+      LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_norm_final(n, part[0], scal, s));
+      CK(cudaMemcpyAsync(hp, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      relres = hp[0] / bnorm;
+      if (relres <= tol) {
+        result = SILU_OK;
+        break;
+      }
+      if (its >= maxit) {
+        result = SILU_ERR_NOT_CONVERGED;
+        break;
+      }
+      CK(cudaMemsetAsync(g, 0, sizeof(double) * (size_t)(m + 1), s));
+      CK(cudaMemsetAsync(H, 0, sizeof(double) * (size_t)(m + 1) * (size_t)m, s));
+      LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_normalize(n, part[0], g, V, V, s));
+      int jend = 0;
+      for (int j = 0; j < m; ++j) {
+        double* vj = vec(V, j);
+        double* zj = vec(Z, j);
+        if (precond == SILU_PRECOND_SWEEPS)
+          smooth_chunk(F, zj, vj, 1, 1, 0, sweeps_L, sweeps_U, true);
+        else if (precond == SILU_PRECOND_DIRECT)
+          direct_chunk(F, zj, vj, 1, 1, 0, true);
+        else
+          CK(cudaMemcpyAsync(zj, vj, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        LAUNCH(F->ctx, SILU_K_RESIDUAL, silu::launch_sweep(F->A->d, silu::MODE_D, 1, gA, 1, nullptr, zj, w, nullptr, nullptr, silu::EPI_SPMV, s));
+        LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_dot_part(n, w, V, part[0], s));
+        int cur = 0;
+        for (int i = 0; i <= j; ++i) {
+          const double* vnext = (i < j) ? vec(V, i + 1) : nullptr;
+          LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_mgs_step(n, part[cur], H + (size_t)i * m + j, w, vec(V, i), vnext, part[cur ^ 1], s));
+          cur ^= 1;
+        }
+        LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_normalize(n, part[cur], H + (size_t)(j + 1) * m + j, w, vec(V, j + 1), s));
+        CK(cudaMemcpyAsync(hp + 1, H + (size_t)(j + 1) * m + j, sizeof(double), cudaMemcpyDeviceToHost, s));
+        LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_givens(j, m, H, W.cs.as<double>(), W.sn.as<double>(), g, scal + 1, s));
+        CK(cudaMemcpyAsync(hp + 2, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        ++its;
+        jend = j + 1;
+        const double hn = hp[1], res = hp[2];
+        if (!std::isfinite(res)) {
+          result = SILU_WARN_DIVERGED;
+          break;
+        }
+        if (res <= tol * bnorm || its >= maxit || hn == 0.0) break;
+      }
+      LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_update_x(n, jend, m, H, g, W.yk.as<double>(), Z, x, s));
+      if (result == SILU_WARN_DIVERGED) {
+        CK(cudaStreamSynchronize(s));
+        relres = NAN;
+        break;
+      }
+    }
+  } catch (const CudaFail& f) {
+    return cuda_err(ctx, f.e, f.what);
+  }
+  if (iters_out) *iters_out = its;
+  if (relres_out) *relres_out = relres;
+  if (result == SILU_ERR_NOT_CONVERGED) set_err(ctx, result, "fgmres_solve: maxit reached above tol");
+  if (result == SILU_WARN_DIVERGED) set_err(ctx, result, "fgmres_solve: non-finite residual estimate");
+  return result;
+}
+
+silu_status silu_ilu_stats(silu_ilu F, int64_t* n, int64_t* nnz_L, int64_t* nnz_U, int32_t* levels_L,
+                           int32_t* levels_U) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  if (n) *n = F->F.L.n;
+  if (nnz_L) *nnz_L = F->F.L.nnz();
+  if (nnz_U) *nnz_U = (F->scale == SILU_SCALE_ROW) ? F->Us.nnz() : F->F.U.nnz();
+  if (levels_L) *levels_L = F->nlevL;
+  if (levels_U) *levels_U = F->nlevU;
+  return SILU_OK;
+}
+
+silu_status silu_ilu_export_sizes(silu_ilu F, int64_t* nnz_L, int64_t* nnz_Ufull, int64_t* nnz_Us) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  if (nnz_L) *nnz_L = F->F.L.nnz();
+  if (nnz_Ufull) *nnz_Ufull = F->F.U.nnz();
+  if (nnz_Us) *nnz_Us = F->Us.nnz();
+  return SILU_OK;
+}
+
+silu_status silu_ilu_export(silu_ilu F, int64_t* Lp, int32_t* Lc, double* Lv, int64_t* Up, int32_t* Uc, double* Uv,
+                            int64_t* Sp, int32_t* Sc, double* Sv, double* dinv, int32_t* levL, int32_t* levU) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  auto cp = [](auto* dst, const auto& src) {
+    if (dst && !src.empty()) std::memcpy(dst, src.data(), sizeof(src[0]) * src.size());
+  };
+  cp(Lp, F->F.L.rp);
+  cp(Lc, F->F.L.ci);
+  cp(Lv, F->F.L.va);
+  cp(Up, F->F.U.rp);
+  cp(Uc, F->F.U.ci);
+  cp(Uv, F->F.U.va);
+  cp(Sp, F->Us.rp);
+  cp(Sc, F->Us.ci);
+  cp(Sv, F->Us.va);
+  cp(dinv, F->dinv);
+  cp(levL, F->levL);
+  cp(levU, F->levU);
+  return SILU_OK;
+}
+
+void silu_ilu_destroy(silu_ilu F) { delete F; }
+
+silu_status silu_ilu_set_lanes(silu_ilu F, int lanes_L, int lanes_U, int lanes_A) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  auto ok = [](int g) { return g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16 || g == 32; };
+  if (!ok(lanes_L) || !ok(lanes_U) || !ok(lanes_A))
+    return set_err(F->ctx, SILU_ERR_INVALID_ARG, "lanes must be 0 or a power of two up to 32");
+  F->lanesL = lanes_L;
+  F->lanesU = lanes_U;
+  F->lanesA = lanes_A;
+  return SILU_OK;
+}
+
+}  // extern "C"

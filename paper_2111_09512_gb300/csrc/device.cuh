@@ -1,0 +1,85 @@
+// Internal device-side declarations of libsilu: buffers, matrices in device
+// memory, and the launchers of the sm_103a kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+namespace silu {
+
+// Epilogues of the sweep kernel.  Each computes, for row i and column r,
+// s = sum_j T_ij in_j and then writes:
+enum Epi : int {
+  EPI_STORE = 0,       // out = c - s
+  EPI_SCALE = 1,       // out = dinv_i (c - s)                       (last L sweep -> D^{-1} y)
+  EPI_ADDX = 2,        // x += c - s                                 (last U sweep, fused update)
+  EPI_SCALE_ADDX = 3,  // x += dinv_i (c - s)                        (last L sweep when m_U = 1)
+  EPI_JAC = 4,         // out = in_i + dinv_i (c - s)                (Jacobi on raw U, Eq. LUiterMat)
+  EPI_JAC_ADDX = 5,    // x += in_i + dinv_i (c - s)
+  EPI_RICH = 6,        // out = c - s + in_i                         (plain Richardson on raw U)
+  EPI_RICH_ADDX = 7,   // x += c - s + in_i
+  EPI_SPMV = 8,        // out = s
+  EPI_SCALE_SETX = 9,  // x = dinv_i (c - s)                         (zero initial guess)
+  EPI_SETX = 10,       // x = c - s
+  EPI_JAC_SETX = 11,   // x = in_i + dinv_i (c - s)
+  EPI_RICH_SETX = 12   // x = c - s + in_i
+};
+
+// Arithmetic mode of a sweep launch.
+enum Mode : int {
+  MODE_D = 0,   // FP64 matrix, FP64 vectors
+  MODE_F = 1,   // FP32 matrix, FP32 vectors, FP32 accumulation
+  MODE_DF = 2   // FP64 matrix and input vectors, FP32 output (residual feeding FP32 sweeps)
+};
+
+struct DevCsr {
+  int n = 0;
+  int64_t nnz = 0;
+  int* rp = nullptr;
+  int* ci = nullptr;
+  void* va = nullptr;   // double or float
+  bool fp32 = false;
+};
+
+// Launch out/x = epilogue(c - T in) over all rows.  Vectors are row-major
+// with leading dimension ldx; the launch covers columns [0, R) of the
+// pointers given (callers offset them).  lanes = threads per row.
+cudaError_t launch_sweep(const DevCsr& T, Mode mode, int R, int lanes, int ldx, const void* c, const void* in,
+                         void* out, const double* dinv, double* x, int epi, cudaStream_t s);
+
+// Level-scheduled substitution over the rows listed in rows[0..nrows).
+//  lower:  y_i -= sum_j T_ij y_j ; if c_out: c_out_i = dinv_i y_i
+//  upper:  y_i -= sum_j T_ij y_j ; if x: x_i += y_i
+cudaError_t launch_level(const DevCsr& T, const int* rows, int nrows, int R, int lanes, int ldx, double* y,
+                         const double* dinv, double* c_out, double* x, cudaStream_t s);
+
+// Elementwise helpers over n rows x R columns (leading dimension ldx).
+//  out(float or double) = scale ? dinv_i in : in      (in: double or float)
+cudaError_t launch_scale(int n, int R, int ldx, const void* in, bool in_f32, const double* dinv, void* out,
+                         bool out_f32, cudaStream_t s);
+//  x (+)= (dinv_i) in
+cudaError_t launch_addx(int n, int R, int ldx, const void* in, bool in_f32, const double* dinv, double* x,
+                        bool accumulate, cudaStream_t s);
+
+// ---- Krylov (FP64, one right-hand side) --------------------------------
+// Block partial sums are written to part[0..nparts); every consumer reduces
+// them in the same fixed order, so results are bitwise reproducible.
+int krylov_parts(int n);
+cudaError_t launch_dot_part(int n, const double* a, const double* b, double* part, cudaStream_t s);
+// h = sum(part_in); if hout: *hout = h; w -= h vi; part_out = partials of w.vnext (or |w|^2 if vnext null)
+cudaError_t launch_mgs_step(int n, const double* part_in, double* hout, double* w, const double* vi,
+                            const double* vnext, double* part_out, cudaStream_t s);
+// h = sqrt(sum(part_in)); *hout = h; vout = w / h (skipped if h == 0)
+cudaError_t launch_normalize(int n, const double* part_in, double* hout, const double* w, double* vout,
+                             cudaStream_t s);
+// Givens on column j of H (row-major (m+1) x m, leading dim m); writes |g_{j+1}| to *res
+cudaError_t launch_givens(int j, int m, double* H, double* cs, double* sn, double* g, double* res, cudaStream_t s);
+// solve the jend x jend triangle, then x += sum_k y_k Z_k
+cudaError_t launch_update_x(int n, int jend, int m, const double* H, const double* g, double* y, const double* Z,
+                            double* x, cudaStream_t s);
+// *out = sqrt(sum(part_in)) for partials written by a launch over n rows
+cudaError_t launch_norm_final(int n, const double* part_in, double* out, cudaStream_t s);
+
+}  // namespace silu

@@ -1,0 +1,431 @@
+// Host-side setup of the scaled-ILU smoother (see host_factor.h).
+//
+// The factorisations follow the paper's setup step (Sec. 3.2, Sec. 5.1): an
+// incomplete LU with pivoting off, L unit lower, U upper, then the row
+// scaling D = diag(U), Utilde = D^{-1} U (Eq. extractD, Eq. newD).  ILU(k)
+// uses Saad's level-of-fill and ILUT Saad's dual threshold, the readings of
+// the paper's "fill level" and "droptol / lfill".
+#include "host_factor.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+namespace silu {
+
+int csr_canonical(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* va, Csr& out,
+                  std::string& msg) {
+  if (n < 0 || nnz < 0 || n >= INT32_MAX || nnz >= INT32_MAX) {
+    msg = "n and nnz must be in [0, 2^31 - 1)";
+    return H_BADARG;
+  }
+  if (!rp || (nnz > 0 && (!ci || !va))) {
+    msg = "null CSR array";
+    return H_BADARG;
+  }
+  if (rp[0] != 0 || rp[n] != nnz) {
+    msg = "row_ptr must start at 0 and end at nnz";
+    return H_BADARG;
+  }
+  out.n = n;
+  out.rp.assign(n + 1, 0);
+  out.ci.clear();
+  out.va.clear();
+  out.ci.reserve(nnz);
+  out.va.reserve(nnz);
+  std::vector<std::pair<int32_t, double>> row;
+  for (int64_t i = 0; i < n; ++i) {
+    if (rp[i + 1] < rp[i]) {
+      msg = "row_ptr is not monotone at row " + std::to_string(i);
+      return H_BADARG;
+    }
+    row.clear();
+    bool sorted = true;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+      if (ci[p] < 0 || ci[p] >= n) {
+        msg = "column index out of range in row " + std::to_string(i);
+        return H_BADARG;
+      }
+      if (!std::isfinite(va[p])) {
+        msg = "non-finite value in row " + std::to_string(i);
+        return H_BADARG;
+      }
+      if (!row.empty() && ci[p] <= row.back().first) sorted = false;
+      row.emplace_back(ci[p], va[p]);
+    }
+    if (!sorted)
+      std::stable_sort(row.begin(), row.end(),
+                       [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+                         return a.first < b.first;
+                       });
+    for (size_t t = 0; t < row.size(); ++t) {
+      if (!out.ci.empty() && (int64_t)out.ci.size() > out.rp[i] && out.ci.back() == row[t].first) {
+        out.va.back() += row[t].second;
+      } else {
+        out.ci.push_back(row[t].first);
+        out.va.push_back(row[t].second);
+      }
+    }
+    out.rp[i + 1] = (int64_t)out.ci.size();
+  }
+  return H_OK;
+}
+
+namespace {
+
+// Position of column c inside the sorted row [b, e) of ci, or -1.
+int64_t find_col(const std::vector<int32_t>& ci, int64_t b, int64_t e, int32_t c) {
+  auto it = std::lower_bound(ci.begin() + b, ci.begin() + e, c);
+  if (it == ci.begin() + e || *it != c) return -1;
+  return it - ci.begin();
+}
+
+// Numeric incomplete LU on a fixed pattern P (which contains the pattern of
+// A), IKJ order: for each row i and each k < i of P(i) in ascending order,
+// l_ik = a_ik / u_kk, then a_ij -= l_ik * u_kj for the j > k of row k that
+// are in P(i).  lu receives the values on P.
+int numeric_on_pattern(const Csr& A, const std::vector<int64_t>& prp, const std::vector<int32_t>& pci,
+                       std::vector<double>& lu, std::vector<int64_t>& dpos, std::string& msg) {
+  const int64_t n = A.n;
+  lu.assign(pci.size(), 0.0);
+  dpos.assign(n, -1);
+  std::vector<int64_t> slot(n, -1);
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t b = prp[i], e = prp[i + 1];
+    for (int64_t p = b; p < e; ++p) slot[pci[p]] = p;
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) lu[slot[A.ci[p]]] = A.va[p];
+    dpos[i] = slot[i];
+    if (dpos[i] < 0) {
+      for (int64_t p = b; p < e; ++p) slot[pci[p]] = -1;
+      msg = "structurally zero pivot in row " + std::to_string(i);
+      return H_ZERO_PIVOT;
+    }
+    for (int64_t p = b; p < dpos[i]; ++p) {
+      const int32_t k = pci[p];
+      lu[p] = lu[p] / lu[dpos[k]];
+      const double lik = lu[p];
+      for (int64_t q = dpos[k] + 1; q < prp[k + 1]; ++q) {
+        const int64_t s = slot[pci[q]];
+        if (s >= 0) lu[s] = lu[s] - lik * lu[q];
+      }
+    }
+    for (int64_t p = b; p < e; ++p) slot[pci[p]] = -1;
+    const double piv = lu[dpos[i]];
+    if (piv == 0.0 || !std::isfinite(piv)) {
+      msg = "zero or non-finite pivot in row " + std::to_string(i);
+      return H_ZERO_PIVOT;
+    }
+  }
+  return H_OK;
+}
+
+// Split values on pattern P at the diagonal into L (strict) and U (diagonal first).
+void split_lu(int64_t n, const std::vector<int64_t>& prp, const std::vector<int32_t>& pci,
+              const std::vector<double>& lu, const std::vector<int64_t>& dpos, Factors& F) {
+  F.L.n = F.U.n = n;
+  F.L.rp.assign(n + 1, 0);
+  F.U.rp.assign(n + 1, 0);
+  F.L.ci.clear();
+  F.L.va.clear();
+  F.U.ci.clear();
+  F.U.va.clear();
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t p = prp[i]; p < dpos[i]; ++p) {
+      F.L.ci.push_back(pci[p]);
+      F.L.va.push_back(lu[p]);
+    }
+    for (int64_t p = dpos[i]; p < prp[i + 1]; ++p) {
+      F.U.ci.push_back(pci[p]);
+      F.U.va.push_back(lu[p]);
+    }
+    F.L.rp[i + 1] = (int64_t)F.L.ci.size();
+    F.U.rp[i + 1] = (int64_t)F.U.ci.size();
+  }
+}
+
+}  // namespace
+
+int factor_ilu0(const Csr& A, Factors& F, std::string& msg) {
+  std::vector<double> lu;
+  std::vector<int64_t> dpos;
+  int st = numeric_on_pattern(A, A.rp, A.ci, lu, dpos, msg);
+  if (st != H_OK) return st;
+  split_lu(A.n, A.rp, A.ci, lu, dpos, F);
+  return H_OK;
+}
+
+// Level-of-fill symbolic phase.  Row i keeps a sorted singly linked list of
+// its columns (next[] indexed by column, -1 terminated, head = n as a
+// sentinel); walking it visits the L part in ascending order while fill is
+// spliced in behind the walker.
+int factor_iluk(const Csr& A, int kfill, Factors& F, std::string& msg) {
+  if (kfill < 0) {
+    msg = "ILU(k) needs k >= 0";
+    return H_BADARG;
+  }
+  const int64_t n = A.n;
+  std::vector<int64_t> prp(n + 1, 0);
+  std::vector<int32_t> pci;
+  std::vector<int32_t> plev;   // level of every pattern entry
+  std::vector<int64_t> pdiag(n, -1);
+  std::vector<int32_t> next(n + 1, -1);
+  std::vector<int32_t> lev(n, 0);
+  const int32_t head = (int32_t)n;
+  pci.reserve(A.ci.size() * 2);
+  plev.reserve(A.ci.size() * 2);
+  for (int64_t i = 0; i < n; ++i) {
+    // initial list: the sorted columns of A's row, level 0
+    int32_t tail = head;
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
+      next[tail] = A.ci[p];
+      tail = A.ci[p];
+      lev[A.ci[p]] = 0;
+    }
+    next[tail] = -1;
+    for (int32_t k = next[head]; k != -1 && k < i; k = next[k]) {
+      const int32_t lik = lev[k];
+      int32_t prev = k;
+      for (int64_t q = pdiag[k] + 1; q < prp[k + 1]; ++q) {
+        const int32_t j = pci[q];
+        const int32_t nl = lik + plev[q] + 1;
+        while (next[prev] != -1 && next[prev] < j) prev = next[prev];
+        if (next[prev] == j) {
+          if (nl < lev[j]) lev[j] = nl;
+        } else if (nl <= kfill) {
+          next[j] = next[prev];
+          next[prev] = j;
+          lev[j] = nl;
+        }
+        if (next[prev] == j) prev = j;
+      }
+    }
+    for (int32_t c = next[head]; c != -1; c = next[c]) {
+      if (c == i) pdiag[i] = (int64_t)pci.size();
+      pci.push_back(c);
+      plev.push_back(lev[c]);
+    }
+    prp[i + 1] = (int64_t)pci.size();
+    if (pdiag[i] < 0) {
+      msg = "structurally zero pivot in row " + std::to_string(i);
+      return H_ZERO_PIVOT;
+    }
+  }
+  std::vector<double> lu;
+  std::vector<int64_t> dpos;
+  int st = numeric_on_pattern(A, prp, pci, lu, dpos, msg);
+  if (st != H_OK) return st;
+  split_lu(n, prp, pci, lu, dpos, F);
+  return H_OK;
+}
+
+int refactor_numeric(const Csr& A, Factors& F, std::string& msg) {
+  const int64_t n = A.n;
+  std::vector<int64_t> prp(n + 1, 0);
+  std::vector<int32_t> pci;
+  pci.reserve(F.L.ci.size() + F.U.ci.size());
+  for (int64_t i = 0; i < n; ++i) {
+    pci.insert(pci.end(), F.L.ci.begin() + F.L.rp[i], F.L.ci.begin() + F.L.rp[i + 1]);
+    pci.insert(pci.end(), F.U.ci.begin() + F.U.rp[i], F.U.ci.begin() + F.U.rp[i + 1]);
+    prp[i + 1] = (int64_t)pci.size();
+    // the pattern must contain A's row
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p)
+      if (find_col(pci, prp[i], prp[i + 1], A.ci[p]) < 0) {
+        msg = "new values do not fit the factor pattern";
+        return H_BADARG;
+      }
+  }
+  std::vector<double> lu;
+  std::vector<int64_t> dpos;
+  int st = numeric_on_pattern(A, prp, pci, lu, dpos, msg);
+  if (st != H_OK) return st;
+  split_lu(n, prp, pci, lu, dpos, F);
+  return H_OK;
+}
+
+// ILUT(tau, p) with pivoting off.  The working row is a dense array w with a
+// membership flag; the L part's columns sit in a sorted linked list that the
+// elimination walks in ascending order (fill spliced in behind the walker),
+// the U part's columns in a plain list.
+int factor_ilut(const Csr& A, double tau, int pfill, Factors& F, std::string& msg) {
+  if (!(tau >= 0.0) || pfill < 0) {
+    msg = "ILUT needs tau >= 0 and fill >= 0";
+    return H_BADARG;
+  }
+  const int64_t n = A.n;
+  F.L.n = F.U.n = n;
+  F.L.rp.assign(n + 1, 0);
+  F.U.rp.assign(n + 1, 0);
+  F.L.ci.clear();
+  F.L.va.clear();
+  F.U.ci.clear();
+  F.U.va.clear();
+  std::vector<double> w(n, 0.0);
+  std::vector<char> member(n, 0);
+  std::vector<int32_t> next(n + 1, -1);
+  std::vector<int32_t> upper;
+  std::vector<int32_t> kept;
+  std::vector<std::pair<double, int32_t>> cand;
+  const int32_t head = (int32_t)n;
+  auto by_magnitude = [](const std::pair<double, int32_t>& a, const std::pair<double, int32_t>& b) {
+    return a.first > b.first || (a.first == b.first && a.second < b.second);
+  };
+  for (int64_t i = 0; i < n; ++i) {
+    double ss = 0.0;
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) ss = ss + A.va[p] * A.va[p];
+    const double tau_i = tau * std::sqrt(ss);
+    upper.clear();
+    kept.clear();
+    int32_t tail = head;
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
+      const int32_t j = A.ci[p];
+      w[j] = A.va[p];
+      member[j] = 1;
+      if (j < i) {
+        next[tail] = j;
+        tail = j;
+      } else {
+        upper.push_back(j);
+      }
+    }
+    next[tail] = -1;
+    for (int32_t k = next[head]; k != -1; k = next[k]) {
+      w[k] = w[k] / F.U.va[F.U.rp[k]];
+      if (std::fabs(w[k]) < tau_i) {
+        w[k] = 0.0;
+        continue;
+      }
+      kept.push_back(k);
+      const double wk = w[k];
+      int32_t prev = k;
+      for (int64_t q = F.U.rp[k] + 1; q < F.U.rp[k + 1]; ++q) {
+        const int32_t j = F.U.ci[q];
+        if (!member[j]) {
+          member[j] = 1;
+          w[j] = 0.0;
+          if (j < i) {
+            while (next[prev] != -1 && next[prev] < j) prev = next[prev];
+            next[j] = next[prev];
+            next[prev] = j;
+          } else {
+            upper.push_back(j);
+          }
+        }
+        w[j] = w[j] - wk * F.U.va[q];
+      }
+    }
+    const double piv = member[i] ? w[i] : 0.0;
+    if (piv == 0.0 || !std::isfinite(piv)) {
+      for (int32_t k = next[head]; k != -1; k = next[k]) member[k] = 0, w[k] = 0.0;
+      for (int32_t j : upper) member[j] = 0, w[j] = 0.0;
+      msg = "zero or non-finite pivot in row " + std::to_string(i);
+      return H_ZERO_PIVOT;
+    }
+    // L part: the kept multipliers, at most p of the largest
+    cand.clear();
+    for (int32_t k : kept) cand.emplace_back(std::fabs(w[k]), k);
+    if ((int64_t)cand.size() > pfill) {
+      std::nth_element(cand.begin(), cand.begin() + pfill, cand.end(), by_magnitude);
+      cand.resize(pfill);
+    }
+    std::sort(cand.begin(), cand.end(),
+              [](const std::pair<double, int32_t>& a, const std::pair<double, int32_t>& b) {
+                return a.second < b.second;
+              });
+    for (auto& c : cand) {
+      F.L.ci.push_back(c.second);
+      F.L.va.push_back(w[c.second]);
+    }
+    // U part: off-diagonals above the threshold, at most p of the largest
+    cand.clear();
+    for (int32_t j : upper)
+      if (j > i && std::fabs(w[j]) >= tau_i) cand.emplace_back(std::fabs(w[j]), j);
+    if ((int64_t)cand.size() > pfill) {
+      std::nth_element(cand.begin(), cand.begin() + pfill, cand.end(), by_magnitude);
+      cand.resize(pfill);
+    }
+    std::sort(cand.begin(), cand.end(),
+              [](const std::pair<double, int32_t>& a, const std::pair<double, int32_t>& b) {
+                return a.second < b.second;
+              });
+    F.U.ci.push_back((int32_t)i);
+    F.U.va.push_back(piv);
+    for (auto& c : cand) {
+      F.U.ci.push_back(c.second);
+      F.U.va.push_back(w[c.second]);
+    }
+    F.L.rp[i + 1] = (int64_t)F.L.ci.size();
+    F.U.rp[i + 1] = (int64_t)F.U.ci.size();
+    for (int32_t k = next[head]; k != -1; k = next[k]) member[k] = 0, w[k] = 0.0;
+    for (int32_t j : upper) member[j] = 0, w[j] = 0.0;
+  }
+  return H_OK;
+}
+
+int row_scale(const Csr& U, Csr& Us, std::vector<double>& dinv, std::string& msg) {
+  const int64_t n = U.n;
+  Us.n = n;
+  Us.rp.assign(n + 1, 0);
+  Us.ci.clear();
+  Us.va.clear();
+  Us.ci.reserve(U.ci.size() - std::min<size_t>(U.ci.size(), (size_t)n));
+  Us.va.reserve(U.ci.size() - std::min<size_t>(U.ci.size(), (size_t)n));
+  dinv.assign(n, 0.0);
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t b = U.rp[i], e = U.rp[i + 1];
+    if (e <= b || U.ci[b] != i) {
+      msg = "upper factor row without leading diagonal";
+      return H_BADARG;
+    }
+    const double d = U.va[b];
+    if (d == 0.0 || !std::isfinite(d)) {
+      msg = "zero pivot in row scaling";
+      return H_ZERO_PIVOT;
+    }
+    dinv[i] = 1.0 / d;
+    for (int64_t p = b + 1; p < e; ++p) {
+      Us.ci.push_back(U.ci[p]);
+      Us.va.push_back(U.va[p] / d);
+    }
+    Us.rp[i + 1] = (int64_t)Us.ci.size();
+  }
+  return H_OK;
+}
+
+int32_t levels_lower(const Csr& L, std::vector<int32_t>& lev) {
+  const int64_t n = L.n;
+  lev.assign(n, 0);
+  int32_t top = -1;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t l = 0;
+    for (int64_t p = L.rp[i]; p < L.rp[i + 1]; ++p) l = std::max(l, lev[L.ci[p]] + 1);
+    lev[i] = l;
+    top = std::max(top, l);
+  }
+  return top + 1;
+}
+
+int32_t levels_upper(const Csr& U, bool diag_first, std::vector<int32_t>& lev) {
+  const int64_t n = U.n;
+  lev.assign(n, 0);
+  int32_t top = -1;
+  for (int64_t i = n - 1; i >= 0; --i) {
+    int32_t l = 0;
+    for (int64_t p = U.rp[i] + (diag_first ? 1 : 0); p < U.rp[i + 1]; ++p) l = std::max(l, lev[U.ci[p]] + 1);
+    lev[i] = l;
+    top = std::max(top, l);
+  }
+  return top + 1;
+}
+
+void group_levels(const std::vector<int32_t>& lev, int32_t nlev, std::vector<int32_t>& level_ptr,
+                  std::vector<int32_t>& level_rows) {
+  const int64_t n = (int64_t)lev.size();
+  level_ptr.assign((size_t)nlev + 1, 0);
+  for (int64_t i = 0; i < n; ++i) level_ptr[lev[i] + 1]++;
+  for (int32_t l = 0; l < nlev; ++l) level_ptr[l + 1] += level_ptr[l];
+  level_rows.assign(n, 0);
+  std::vector<int32_t> fillp(level_ptr.begin(), level_ptr.end() - 1);
+  for (int64_t i = 0; i < n; ++i) level_rows[fillp[lev[i]]++] = (int32_t)i;
+}
+
+}  // namespace silu

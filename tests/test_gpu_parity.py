@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+FP64 results must agree to 1e-12 relative (||delta||_2 / ||ref||_2, per
+right-hand side); FP32 factors / sweeps report their error against the FP64
+oracle and are held to a bound derived from single-precision rounding.
+Sizes span many thread blocks and ragged tails (row counts not multiples of
+the launch tile)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _helpers import relerr
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def silu():
+    import paper_2111_09512_gb300 as s
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    s.build()
+    return s
+
+
+@pytest.fixture(scope="module")
+def ctx(silu):
+    return silu.Context(0, torch.cuda.current_stream())
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def percol_relerr(got, want):
+    got = got.reshape(want.shape[0], -1)
+    want = want.reshape(want.shape[0], -1)
+    return max(relerr(got[:, k], want[:, k]) for k in range(want.shape[1]))
+
+
+def oracle_scaled(A, kind, tau, fill):
+    F = oracle.factor(A, kind, tau, fill)
+    return F, oracle.row_scale(F)
+
+
+# --------------------------------------------------------------- smoother
+
+SMOOTH_CASES = [
+    # name, generator, kind, tau, fill, nrhs, (mL, mU) list
+    ("poisson32 ilu0 R4", lambda: synth.poisson7(32), "ilu0", 0.0, 0, 4, [(5, 5), (1, 1), (2, 3), (0, 4), (3, 0)]),
+    ("cutcell 37x29x23 ilu0 R1", lambda: synth.cutcell7(37, 29, 23, seed=1), "ilu0", 0.0, 0, 1,
+     [(5, 5), (1, 2), (2, 1), (7, 9)]),
+    ("cutcell 33x31x17 ilut R3", lambda: synth.cutcell7(33, 31, 17, seed=2), "ilut", 1e-3, 10, 3,
+     [(10, 10), (1, 1), (4, 6)]),
+    ("hex27 21x19x17 ilu0 R2", lambda: synth.hex27(21, 19, 17, seed=3), "ilu0", 0.0, 0, 2, [(3, 3), (6, 2)]),
+    ("cutcell 19x17x13 iluk2 R1", lambda: synth.cutcell7(19, 17, 13, seed=4), "iluk", 0.0, 2, 1, [(4, 4)]),
+    ("hex27 13x11x9 ilut R5", lambda: synth.hex27(13, 11, 9, seed=5), "ilut", 1e-3, 12, 5, [(3, 4)]),
+]
+
+
+@pytest.mark.parametrize("case", SMOOTH_CASES, ids=[c[0] for c in SMOOTH_CASES])
+def test_smooth_fp64_matches_oracle(silu, ctx, case):
+    name, gen, kind, tau, fill, nrhs, sweeps = case
+    A = gen()
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), kind, tau, fill)
+    _, S = oracle_scaled(A, kind, tau, fill)
+    b = synth.rhs(n, nrhs, seed=11)
+    x0 = synth.rhs(n, nrhs, seed=12) * 0.5
+    for mL, mU in sweeps:
+        want = oracle.smooth(A, S, x0, b, mL, mU)
+        x = dev(x0.copy())
+        silu.ilu_smooth(F, x, dev(b), mL, mU)
+        assert percol_relerr(host(x), want) < FP64_TOL, (mL, mU)
+
+
+@pytest.mark.parametrize("scale", ["none", "rich"])
+def test_unscaled_variants_match_oracle(silu, ctx, scale):
+    A = synth.cutcell7(24, 22, 20, seed=6)
+    n = len(A[0]) - 1
+    sc = silu.SCALE_NONE if scale == "none" else silu.SCALE_NONE_RICH
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilut", 1e-3, 10, scale=sc)
+    OF, S = oracle_scaled(A, "ilut", 1e-3, 10)
+    b = synth.rhs(n, 1, seed=3)
+    for mL, mU in [(3, 1), (3, 2), (2, 5)]:
+        r = oracle.residual(A, np.zeros((n, 1)), b)
+        y = oracle.richardson_lower(S.L, r, mL)
+        if scale == "none":
+            v = oracle.upper_jacobi(OF.U, y, mU)
+        else:
+            v = oracle.upper_unscaled_richardson(OF.U, y, mU)
+        x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+        silu.ilu_smooth(F, x, dev(b), mL, mU)
+        got = host(x)
+        if np.all(np.isfinite(v)) and np.linalg.norm(v) < 1e100:
+            assert relerr(got, v) < FP64_TOL * max(1.0, np.linalg.norm(v) / np.linalg.norm(b)), (mL, mU)
+
+
+def test_smooth_many_sweeps_equals_direct(silu, ctx):
+    """Nilpotence (Sec. 5.2): #levels sweeps on each factor reproduce the
+    direct triangular solves, on the device as in the oracle."""
+    A = synth.cutcell7(12, 10, 9, seed=7)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+    st = F.stats()
+    b = dev(synth.rhs(n, 2, seed=5))
+    x1 = torch.zeros(n, 2, dtype=torch.float64, device="cuda")
+    x2 = torch.zeros_like(x1)
+    silu.ilu_smooth(F, x1, b, st["levels_L"], st["levels_U"])
+    silu.direct_trisolve(F, x2, b)
+    assert relerr(host(x1), host(x2)) < FP64_TOL
+
+
+DIRECT_CASES = [
+    ("poisson32 R4", lambda: synth.poisson7(32), "ilu0", 0.0, 0, 4),
+    ("cutcell 29x23x19 ilut R1", lambda: synth.cutcell7(29, 23, 19, seed=8), "ilut", 1e-3, 10, 1),
+    ("hex27 15x13x11 ilu0 R3", lambda: synth.hex27(15, 13, 11, seed=9), "ilu0", 0.0, 0, 3),
+]
+
+
+@pytest.mark.parametrize("case", DIRECT_CASES, ids=[c[0] for c in DIRECT_CASES])
+def test_direct_trisolve_matches_oracle(silu, ctx, case):
+    name, gen, kind, tau, fill, nrhs = case
+    A = gen()
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), kind, tau, fill)
+    _, S = oracle_scaled(A, kind, tau, fill)
+    b = synth.rhs(n, nrhs, seed=21)
+    x0 = synth.rhs(n, nrhs, seed=22)
+    want = oracle.direct_apply(A, S, x0, b)
+    x = dev(x0.copy())
+    silu.direct_trisolve(F, x, dev(b))
+    assert percol_relerr(host(x), want) < FP64_TOL
+
+
+def test_fp32_error_against_fp64_oracle(silu, ctx):
+    """FP32 factors and sweeps: the error against the FP64 oracle is a number
+    (printed), bounded by single-precision rounding: each sweep perturbs the
+    iterate by a few units of 2^-24 relative, so 3+3 sweeps stay well below 1e-5."""
+    A = synth.cutcell7(40, 36, 30, seed=10)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0", prec=silu.FP32)
+    _, S = oracle_scaled(A, "ilu0", 0.0, 0)
+    b = synth.rhs(n, 1, seed=1)
+    for mL, mU in [(3, 3), (5, 5), (1, 1)]:
+        want = oracle.smooth(A, S, np.zeros((n, 1)), b, mL, mU)
+        x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+        silu.ilu_smooth(F, x, dev(b), mL, mU)
+        err = relerr(host(x), want)
+        print(f"FP32 smoother ({mL},{mU}) relative error vs FP64 oracle: {err:.3e}")
+        assert err < 1e-5
+
+
+def test_fgmres_matches_oracle(silu, ctx):
+    """Same iteration count (to rounding) and both iterates below tol in true
+    relative residual.  The unpreconditioned case uses a matrix without cut
+    cells: on the cut-cell matrix plain GMRES(30) does not converge at all."""
+    cases = (
+        (silu.PRECOND_SWEEPS, (3, 3), lambda: synth.cutcell7(20, 18, 16, seed=11)),
+        (silu.PRECOND_DIRECT, (0, 0), lambda: synth.cutcell7(20, 18, 16, seed=11)),
+        (silu.PRECOND_NONE, (0, 0), lambda: synth.cutcell7(12, 11, 10, seed=11, sigma=0.3, frac_cut=0.0)),
+    )
+    for precond, (mL, mU), gen in cases:
+        A = gen()
+        n = len(A[0]) - 1
+        F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+        _, S = oracle_scaled(A, "ilu0", 0.0, 0)
+        b = synth.rhs(n, 1, seed=2)[:, 0]
+        xo, sto, itso, relo = oracle.fgmres(A, S if precond != 2 else None, b, tol=1e-10, restart=30,
+                                            maxit=3000, mL=mL, mU=mU, precond=precond)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st, its, rel = silu.fgmres_solve(F, x, dev(b), tol=1e-10, restart=30, maxit=3000, sweeps_L=mL,
+                                         sweeps_U=mU, precond=precond)
+        assert st == silu.OK and sto == oracle.OK, (precond, st, sto, its, itso)
+        assert rel <= 1e-10 and relo <= 1e-10
+        assert abs(its - itso) <= 1 + itso // 20, (its, itso)
+        r = oracle.residual(A, host(x).reshape(n, 1), b.reshape(n, 1))
+        assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10
+
+
+def test_fgmres_fp32_smoother_reaches_fp64_tolerance(silu, ctx):
+    A = synth.hex27(24, 22, 20, seed=12)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0", prec=silu.FP32)
+    b = synth.rhs(n, 1, seed=3)[:, 0]
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st, its, rel = silu.fgmres_solve(F, x, dev(b), tol=1e-10, restart=30, maxit=500, sweeps_L=3, sweeps_U=3)
+    assert st == silu.OK and rel <= 1e-10
+    r = oracle.residual(A, host(x).reshape(n, 1), b.reshape(n, 1))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10
+
+
+def test_edge_cases(silu, ctx):
+    # 1x1 system
+    A1 = (np.array([0, 1], np.int64), np.array([0], np.int32), np.array([4.0]))
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A1), "ilu0")
+    x = torch.zeros(1, 1, dtype=torch.float64, device="cuda")
+    silu.ilu_smooth(F, x, dev(np.array([[2.0]])), 3, 3)
+    assert host(x)[0, 0] == 0.5
+    silu.direct_trisolve(F, x, dev(np.array([[2.0]])))
+    assert host(x)[0, 0] == 0.5
+    # empty system
+    A0 = (np.array([0], np.int64), np.zeros(0, np.int32), np.zeros(0))
+    F0 = silu.ilu_setup(ctx, silu.Matrix(ctx, *A0), "ilu0")
+    assert F0.stats()["n"] == 0
+    # bad arguments are rejected before any launch
+    A = synth.poisson7(5)
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+    xb = torch.zeros(125, 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(silu.SiluError):
+        silu.ilu_smooth(F, xb, xb, -1, 2)
+    with pytest.raises(silu.SiluError):
+        silu.ilu_smooth(F, xb.float(), xb, 1, 2)
+    assert silu.load().ilu_smooth(F.handle, 0, xb.data_ptr(), 1, 1, 1) == silu.ERR_INVALID_ARG

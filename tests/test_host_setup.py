@@ -1,0 +1,137 @@
+"""Host-side logic of libsilu on the CPU: the C ABI loads and exports every
+declared symbol, input validation, and the host factorisation / scaling /
+level sets against the oracle (patterns and levels bit-exact, values to
+1e-14 relative; both sides round every operation as written)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2111_09512_gb300 as silu
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    silu.build()
+    return silu.Context(device=-1)
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "silu.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", text)
+    return sorted({n for n in names if n.startswith(("silu_", "ilu_", "direct_", "fgmres_"))})
+
+
+def test_library_exports_every_declared_symbol():
+    silu.build()
+    import ctypes
+    lib = ctypes.CDLL(silu.LIB_PATH)
+    declared = header_functions()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(silu.exported_symbols()) <= set(declared)
+    assert "sm_103a" in silu.silu_version()
+
+
+def test_host_only_context_refuses_device_calls(ctx):
+    A = synth.poisson7(4)
+    M = silu.Matrix(ctx, *A)
+    F = silu.ILU(M, "ilu0")
+    st = silu.load().ilu_smooth(F.handle, 8, 8, 1, 1, 1)
+    assert st == silu.ERR_NO_DEVICE
+    assert b"host-only" in silu.load().silu_last_error(ctx.handle)
+
+
+def test_csr_validation(ctx):
+    rp = np.array([0, 2, 3], np.int64)
+    with pytest.raises(silu.SiluError) as e:
+        silu.Matrix(ctx, rp, np.array([0, 5, 1], np.int32), np.ones(3))
+    assert e.value.status == silu.ERR_INVALID_ARG
+    with pytest.raises(silu.SiluError):
+        silu.Matrix(ctx, rp, np.array([0, 1, 1], np.int32), np.array([1.0, np.nan, 1.0]))
+    with pytest.raises(silu.SiluError):
+        silu.Matrix(ctx, np.array([0, 2, 1], np.int64), np.array([0, 1, 1], np.int32), np.ones(3))
+    # unsorted columns and duplicates are canonicalised: same factors as the sorted matrix
+    Mu = silu.Matrix(ctx, np.array([0, 3, 5], np.int64), np.array([1, 0, 0, 1, 0], np.int32),
+                     np.array([-1.0, 2.0, 2.0, 4.0, -1.0]))
+    F = silu.ILU(Mu, "ilu0").export()
+    assert np.array_equal(F["U"][1], [0, 1, 1]) and np.array_equal(F["U"][2], [4.0, -1.0, 3.75])
+    assert np.array_equal(F["L"][2], [-0.25])
+
+
+def test_zero_pivot_reported(ctx):
+    M = silu.Matrix(ctx, np.array([0, 2, 4], np.int64), np.array([0, 1, 0, 1], np.int32),
+                    np.array([0.0, 1.0, 1.0, 2.0]))
+    for kind in ("ilu0", "ilut", "iluk"):
+        with pytest.raises(silu.SiluError) as e:
+            silu.ILU(M, kind, tau=0.0, fill=2)
+        assert e.value.status == silu.ERR_ZERO_PIVOT
+
+
+def compare_with_oracle(F, OF, OS):
+    ex = F.export()
+    for mine, theirs in ((ex["L"], OF.L), (ex["U"], OF.U), (ex["Us"], OS.Us)):
+        assert np.array_equal(mine[0], theirs[0])
+        assert np.array_equal(mine[1], theirs[1])
+        d = np.abs(mine[2] - theirs[2])
+        assert np.all(d <= 1e-14 * np.abs(theirs[2]))
+    assert np.all(np.abs(ex["dinv"] - OS.dinv) <= 1e-14 * np.abs(OS.dinv))
+    return ex
+
+
+CASES = [
+    ("poisson 9x7x5 ilu0", lambda: synth.poisson7(9, 7, 5), "ilu0", 0.0, 0),
+    ("cutcell 10x9x8 ilu0", lambda: synth.cutcell7(10, 9, 8, seed=3), "ilu0", 0.0, 0),
+    ("hex27 6x5x4 ilu0", lambda: synth.hex27(6, 5, 4, seed=2), "ilu0", 0.0, 0),
+    ("cutcell 8x8x6 iluk1", lambda: synth.cutcell7(8, 8, 6, seed=4), "iluk", 0.0, 1),
+    ("cutcell 7x6x5 iluk3", lambda: synth.cutcell7(7, 6, 5, seed=5), "iluk", 0.0, 3),
+    ("hex27 5x4x4 iluk2", lambda: synth.hex27(5, 4, 4, seed=6), "iluk", 0.0, 2),
+    ("cutcell 12x11x10 ilut", lambda: synth.cutcell7(12, 11, 10, seed=1), "ilut", 1e-3, 10),
+    ("cutcell 10x10x10 ilut tight", lambda: synth.cutcell7(10, 10, 10, seed=7), "ilut", 1e-2, 3),
+    ("hex27 6x6x5 ilut", lambda: synth.hex27(6, 6, 5, seed=8), "ilut", 1e-3, 8),
+]
+
+
+@pytest.mark.parametrize("name,gen,kind,tau,fill", CASES, ids=[c[0] for c in CASES])
+def test_host_factors_match_oracle(ctx, name, gen, kind, tau, fill):
+    A = gen()
+    F = silu.ILU(silu.Matrix(ctx, *A), kind, tau=tau, fill=fill)
+    OF = oracle.factor(A, kind, tau, fill)
+    OS = oracle.row_scale(OF)
+    ex = compare_with_oracle(F, OF, OS)
+    nl, levL = oracle.levels_lower(OS.L)
+    nu, levU = oracle.levels_upper(OS.Us)
+    st = F.stats()
+    assert st["levels_L"] == nl and st["levels_U"] == nu
+    assert np.array_equal(ex["levL"], levL) and np.array_equal(ex["levU"], levU)
+
+
+def test_host_ilut_cut_cell_64(ctx):
+    """A larger ILUT(1e-3, 10) cut-cell case: 262,144 rows, several thousand
+    drop decisions near the threshold, all identical to the oracle's."""
+    A = synth.cutcell7(64, 64, 64, seed=1)
+    F = silu.ILU(silu.Matrix(ctx, *A), "ilut", tau=1e-3, fill=10)
+    OF = oracle.ilut(A, 1e-3, 10)
+    compare_with_oracle(F, OF, oracle.row_scale(OF))
+
+
+def test_refactor_reuses_the_pattern(ctx):
+    A = synth.cutcell7(8, 7, 6, seed=2)
+    A2 = synth.cutcell7(8, 7, 6, seed=9)
+    assert np.array_equal(A[1], A2[1])
+    for kind, fill in (("ilu0", 0), ("iluk", 2)):
+        M = silu.Matrix(ctx, *A)
+        F = silu.ILU(M, kind, fill=fill)
+        silu.ilu_refactor(F, A2[2])
+        OF = oracle.factor(A2, kind, 0.0, fill)
+        compare_with_oracle(F, OF, oracle.row_scale(OF))
+    F = silu.ILU(silu.Matrix(ctx, *A), "ilut", tau=1e-3, fill=5)
+    with pytest.raises(silu.SiluError):
+        silu.ilu_refactor(F, A2[2])
