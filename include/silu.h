@@ -104,6 +104,13 @@ silu_status silu_ctx_profile(silu_ctx ctx, int enable);
 silu_status silu_ctx_profile_read(silu_ctx ctx, int kclass, int64_t* launches, double* total_ms);
 /* Kernels launched on ctx since creation (all classes; always counted). */
 silu_status silu_ctx_launch_count(silu_ctx ctx, int64_t* launches);
+/*
+ * Block on the context's stream and read (and clear) its device error word.
+ * Returns SILU_ERR_TIMEOUT if a kernel's bounded wait gave up since the last
+ * check (the results of the calls in between are invalid), else the status
+ * of the synchronisation.  fgmres_solve performs this check itself.
+ */
+silu_status silu_ctx_check(silu_ctx ctx);
 /* Message of the last failed call on ctx ("" if none); valid until the next call. */
 const char* silu_last_error(silu_ctx ctx);
 /* Library version string. */
@@ -207,6 +214,15 @@ void silu_ilu_destroy(silu_ilu F);
  * autotuner; results do not depend on it beyond rounding order.
  */
 silu_status silu_ilu_set_lanes(silu_ilu F, int lanes_L, int lanes_U, int lanes_A);
+
+/*
+ * Sweep kernel variant: 0 = automatic (the staged kernel for one right-hand
+ * side, the lanes-per-row kernel otherwise), 1 = always the lanes-per-row
+ * kernel, 2 = the staged kernel wherever it applies.  The staged kernel
+ * streams nnz-balanced row tiles of the factor into shared memory with bulk
+ * asynchronous copies; it needs rows of at most 4088 entries.
+ */
+silu_status silu_ilu_set_kernel(silu_ilu F, int variant);
 
 #ifdef __cplusplus
 }

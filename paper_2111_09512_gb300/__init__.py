@@ -89,6 +89,8 @@ def load():
         "silu_ctx_profile": (i32, [vp, i32]),
         "silu_ctx_profile_read": (i32, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl)]),
         "silu_ctx_launch_count": (i32, [vp, ctypes.POINTER(i64)]),
+        "silu_ctx_check": (i32, [vp]),
+        "silu_ilu_set_kernel": (i32, [vp, i32]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -104,7 +106,7 @@ def exported_symbols():
             "silu_mat_destroy", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
-            "silu_ctx_launch_count"]
+            "silu_ctx_launch_count", "silu_ctx_check", "silu_ilu_set_kernel"]
 
 
 def _ptr(t) -> int:
@@ -165,6 +167,10 @@ class Context:
                    "silu_ctx_profile_read")
             out[name] = (cnt.value, ms.value)
         return out
+
+    def check(self):
+        """Synchronise and raise if a kernel's bounded wait gave up (SILU_ERR_TIMEOUT)."""
+        _check(self.handle, load().silu_ctx_check(self.handle), "silu_ctx_check")
 
     def launch_count(self) -> int:
         """Kernels this context has launched since it was created."""
@@ -265,6 +271,10 @@ class ILU:
 
     def reserve(self, nrhs: int = 1, restart: int = 0):
         _check(self.ctx.handle, load().silu_ilu_reserve(self.handle, nrhs, restart), "silu_ilu_reserve")
+
+    def set_kernel(self, variant: int):
+        """0 automatic, 1 lanes-per-row kernel, 2 staged (bulk-copy) kernel where it applies."""
+        _check(self.ctx.handle, load().silu_ilu_set_kernel(self.handle, variant), "silu_ilu_set_kernel")
 
     def set_lanes(self, lanes_L: int = 0, lanes_U: int = 0, lanes_A: int = 0):
         _check(self.ctx.handle, load().silu_ilu_set_lanes(self.handle, lanes_L, lanes_U, lanes_A),

@@ -56,6 +56,7 @@ struct silu_ctx_s {
   std::string err;
   double* pinned = nullptr;  // small host buffer for scalar read-backs
   int64_t launches = 0;      // kernels launched on this context
+  silu::LaunchEnv env;       // SM count and device error word
   // event timing of launches (silu_ctx_profile)
   bool profiling = false;
   std::vector<cudaEvent_t> events;  // pool; records use pairs (2k, 2k+1)
@@ -66,7 +67,7 @@ struct silu_ctx_s {
 struct silu_mat_s {
   silu_ctx ctx = nullptr;
   silu::Csr A;
-  DBuf rp, ci, va;
+  DBuf rp, ci, va, tiles;
   DevCsr d;
 };
 
@@ -91,13 +92,14 @@ struct silu_ilu_s {
   std::vector<int32_t> levL, levU, levLptr, levLrows, levUptr, levUrows;
   int32_t nlevL = 0, nlevU = 0;
   // device: sweep factors
-  DBuf L_rp, L_ci, L_va, U_rp, U_ci, U_va, d_dinv;
+  DBuf L_rp, L_ci, L_va, L_tiles, U_rp, U_ci, U_va, U_tiles, d_dinv;
   DevCsr dL, dU;
   // device: FP64 L_s and Utilde_s for the direct path (aliases of dL/dU when possible)
-  DBuf L64_va, S_rp, S_ci, S_va, levLrows_d, levUrows_d;
+  DBuf L64_va, S_rp, S_ci, S_va, S_tiles, levLrows_d, levUrows_d;
   DevCsr dL64, dS64;
   bool direct_ready = false;
   int lanesL = 0, lanesU = 0, lanesA = 0;
+  int variant = 0;  // 0 auto, 1 plain lanes-per-row kernel, 2 staged kernel where possible
   int autoL = 4, autoU = 4, autoA = 8;
   Workspace ws;
 };
@@ -174,27 +176,44 @@ cudaError_t upload(DBuf& b, const T* src, size_t count, cudaStream_t s) {
   return cudaMemcpyAsync(b.p, src, sizeof(T) * count, cudaMemcpyHostToDevice, s);
 }
 
-// Upload CSR (int64 row pointers narrowed to int32) with values as double or float.
-cudaError_t upload_csr(const silu::Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& va, DevCsr& d, cudaStream_t s) {
+// Upload CSR (int64 row pointers narrowed to int32) with values as double or
+// float.  Arrays get kCsrPad spare (zeroed) elements for the staged kernel's
+// 16-byte-rounded copies, and the row tiles of the staged kernel are built.
+cudaError_t upload_csr(const silu::Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& va, DBuf& tiles, DevCsr& d,
+                       cudaStream_t s) {
+  const size_t n = (size_t)T.n, nnz = (size_t)T.nnz();
+  const size_t vs = fp32 ? sizeof(float) : sizeof(double);
   std::vector<int32_t> rp32(T.rp.begin(), T.rp.end());
-  cudaError_t e = upload(rp, rp32.data(), rp32.size(), s);
-  if (e == cudaSuccess) e = upload(ci, T.ci.data(), T.ci.size(), s);
-  if (e == cudaSuccess) {
+  cudaError_t e = rp.ensure(sizeof(int32_t) * (n + 1 + silu::kCsrPad));
+  if (e == cudaSuccess) e = ci.ensure(sizeof(int32_t) * (nnz + silu::kCsrPad));
+  if (e == cudaSuccess) e = va.ensure(vs * (nnz + silu::kCsrPad));
+  if (e == cudaSuccess) e = cudaMemsetAsync(rp.p, 0, rp.bytes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ci.p, 0, ci.bytes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(va.p, 0, va.bytes, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rp.p, rp32.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nnz)
+    e = cudaMemcpyAsync(ci.p, T.ci.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s);
+  std::vector<float> v32;
+  if (e == cudaSuccess && nnz) {
     if (fp32) {
-      std::vector<float> v32(T.va.begin(), T.va.end());
-      e = upload(va, v32.data(), v32.size(), s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // v32 dies at return
+      v32.assign(T.va.begin(), T.va.end());
+      e = cudaMemcpyAsync(va.p, v32.data(), sizeof(float) * nnz, cudaMemcpyHostToDevice, s);
     } else {
-      e = upload(va, T.va.data(), T.va.size(), s);
+      e = cudaMemcpyAsync(va.p, T.va.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s);
     }
   }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // rp32 dies at return
+  std::vector<int> tl;
+  const bool tiled = silu::make_tiles(T.rp.data(), T.n, tl);
+  if (e == cudaSuccess && tiled) e = upload(tiles, tl.data(), tl.size(), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging vectors die at return
   d.n = (int)T.n;
   d.nnz = T.nnz();
   d.rp = rp.as<int>();
   d.ci = ci.as<int>();
   d.va = va.p;
   d.fp32 = fp32;
+  d.tiles = tiled ? tiles.as<int4>() : nullptr;
+  d.ntiles = tiled ? (int)(tl.size() / 4) : 0;
   return e;
 }
 
@@ -248,7 +267,11 @@ cudaError_t ensure_direct(silu_ilu F) {
     F->dL64 = F->dL;
   } else {
     F->dL64 = F->dL;
-    e = upload(F->L64_va, F->F.L.va.data(), F->F.L.va.size(), s);
+    e = F->L64_va.ensure(sizeof(double) * (F->F.L.va.size() + silu::kCsrPad));
+    if (e == cudaSuccess) e = cudaMemsetAsync(F->L64_va.p, 0, F->L64_va.bytes, s);
+    if (e == cudaSuccess && !F->F.L.va.empty())
+      e = cudaMemcpyAsync(F->L64_va.p, F->F.L.va.data(), sizeof(double) * F->F.L.va.size(),
+                          cudaMemcpyHostToDevice, s);
     F->dL64.va = F->L64_va.p;
     F->dL64.fp32 = false;
   }
@@ -257,7 +280,7 @@ cudaError_t ensure_direct(silu_ilu F) {
   if (F->prec == SILU_FP64 && F->scale == SILU_SCALE_ROW) {
     F->dS64 = F->dU;
   } else {
-    e = upload_csr(F->Us, false, F->S_rp, F->S_ci, F->S_va, F->dS64, s);
+    e = upload_csr(F->Us, false, F->S_rp, F->S_ci, F->S_va, F->S_tiles, F->dS64, s);
     if (e != cudaSuccess) return e;
   }
   e = upload(F->levLrows_d, F->levLrows.data(), F->levLrows.size(), s);
@@ -268,6 +291,17 @@ cudaError_t ensure_direct(silu_ilu F) {
 }
 
 int lanes_of(int fixed, int autov) { return fixed > 0 ? fixed : autov; }
+
+// One sweep-shaped launch: the staged kernel for a single right-hand side
+// when the matrix has a tile partition (and the variant allows it), else the
+// lanes-per-row kernel.
+cudaError_t sweep_launch(silu_ilu F, const DevCsr& T, silu::Mode mode, int R, int lanes, int ldx, const void* c,
+                         const void* in, void* out, const double* dinv, double* x, int epi) {
+  cudaStream_t s = F->ctx->stream;
+  if (R == 1 && ldx == 1 && T.ntiles > 0 && F->variant != 1)
+    return silu::launch_sweep_staged(T, mode, F->ctx->env, c, in, out, dinv, x, epi, s);
+  return silu::launch_sweep(T, mode, R, lanes, ldx, c, in, out, dinv, x, epi, s);
+}
 
 // ---------------------------------------------------------------------------
 // One smoother application on columns [0, R) of x/b (leading dimension ldx),
@@ -317,12 +351,12 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
     }
   } else if (mL <= 1 && after == NEED_C) {
     // r is only needed as D^{-1} r: fuse the scaling into the residual
-    LAUNCH(F->ctx, SILU_K_RESIDUAL, silu::launch_sweep(A, f32 ? silu::MODE_DF : silu::MODE_D, R, gA, ldx, b, x, bufC, dinv, nullptr,
-                          silu::EPI_SCALE, s));
+    LAUNCH(F->ctx, SILU_K_RESIDUAL, sweep_launch(F, A, f32 ? silu::MODE_DF : silu::MODE_D, R, gA, ldx, b, x, bufC, dinv, nullptr,
+                          silu::EPI_SCALE));
     r_fused_to_c = true;
   } else {
-    LAUNCH(F->ctx, SILU_K_RESIDUAL, silu::launch_sweep(A, f32 ? silu::MODE_DF : silu::MODE_D, R, gA, ldx, b, x, bufR, dinv, nullptr,
-                          silu::EPI_STORE, s));
+    LAUNCH(F->ctx, SILU_K_RESIDUAL, sweep_launch(F, A, f32 ? silu::MODE_DF : silu::MODE_D, R, gA, ldx, b, x, bufR, dinv, nullptr,
+                          silu::EPI_STORE));
     r = bufR;
   }
 
@@ -350,7 +384,7 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
           o = bufC;
         }
       }
-      LAUNCH(F->ctx, SILU_K_SWEEP_L, silu::launch_sweep(F->dL, sm, R, gL, ldx, r, in, o, dinv, x, epi, s));
+      LAUNCH(F->ctx, SILU_K_SWEEP_L, sweep_launch(F, F->dL, sm, R, gL, ldx, r, in, o, dinv, x, epi));
       in = out;
       if (last) {
         if (after == FINAL_Y || after == FINAL_DY) done = true;
@@ -382,7 +416,7 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
       const bool last = (k == mU);
       char* out = pp[k & 1];
       const int epi = last ? (x_zero ? silu::EPI_SETX : silu::EPI_ADDX) : silu::EPI_STORE;
-      LAUNCH(F->ctx, SILU_K_SWEEP_U, silu::launch_sweep(F->dU, sm, R, gU, ldx, cvec, in, last ? nullptr : out, dinv, x, epi, s));
+      LAUNCH(F->ctx, SILU_K_SWEEP_U, sweep_launch(F, F->dU, sm, R, gU, ldx, cvec, in, last ? nullptr : out, dinv, x, epi));
       in = out;
     }
     return;
@@ -409,7 +443,7 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
       epi = last ? (x_zero ? silu::EPI_JAC_SETX : silu::EPI_JAC_ADDX) : silu::EPI_JAC;
     else
       epi = last ? (x_zero ? silu::EPI_RICH_SETX : silu::EPI_RICH_ADDX) : silu::EPI_RICH;
-    LAUNCH(F->ctx, SILU_K_SWEEP_U, silu::launch_sweep(F->dU, sm, R, gU, ldx, y, in, last ? nullptr : out, dinv, x, epi, s));
+    LAUNCH(F->ctx, SILU_K_SWEEP_U, sweep_launch(F, F->dU, sm, R, gU, ldx, y, in, last ? nullptr : out, dinv, x, epi));
     in = out;
   }
 }
@@ -427,7 +461,7 @@ void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
   if (x_zero)
     LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_scale(n, R, ldx, b, false, nullptr, y, false, s));
   else
-    LAUNCH(F->ctx, SILU_K_RESIDUAL, silu::launch_sweep(F->A->d, silu::MODE_D, R, gA, ldx, b, x, y, nullptr, nullptr, silu::EPI_STORE, s));
+    LAUNCH(F->ctx, SILU_K_RESIDUAL, sweep_launch(F, F->A->d, silu::MODE_D, R, gA, ldx, b, x, y, nullptr, nullptr, silu::EPI_STORE));
   const int* rowsL = F->levLrows_d.as<int>();
   const int* rowsU = F->levUrows_d.as<int>();
   for (int l = 0; l < F->nlevL; ++l) {
@@ -466,6 +500,9 @@ silu_status silu_ctx_create(int device, void* cuda_stream, silu_ctx* out) {
     }
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->pinned, 64 * sizeof(double));
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->env.sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->env.err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->env.err, 0, sizeof(int));
     if (e != cudaSuccess) {
       delete c;
       return SILU_ERR_CUDA;
@@ -480,6 +517,7 @@ void silu_ctx_destroy(silu_ctx ctx) {
   if (ctx->device >= 0) cudaSetDevice(ctx->device);
   for (cudaEvent_t ev : ctx->events) cudaEventDestroy(ev);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->env.err) cudaFree(ctx->env.err);
   delete ctx;
 }
 
@@ -517,6 +555,26 @@ silu_status silu_ctx_profile_read(silu_ctx ctx, int kclass, int64_t* launches, d
   return SILU_OK;
 }
 
+silu_status silu_ctx_check(silu_ctx ctx) {
+  silu_status ds = device_ok(ctx);
+  if (ds != SILU_OK) return ds;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "cudaStreamSynchronize");
+  int flag = 0;
+  e = cudaMemcpy(&flag, ctx->env.err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && flag) e = cudaMemset(ctx->env.err, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_err(ctx, e, "error word read-back");
+  if (flag) return set_err(ctx, SILU_ERR_TIMEOUT, "a bounded device wait gave up; results of the affected calls are invalid");
+  return SILU_OK;
+}
+
+silu_status silu_ilu_set_kernel(silu_ilu F, int variant) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  if (variant < 0 || variant > 2) return set_err(F->ctx, SILU_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+  F->variant = variant;
+  return SILU_OK;
+}
+
 silu_status silu_ctx_launch_count(silu_ctx ctx, int64_t* launches) {
   if (!ctx || !launches) return SILU_ERR_INVALID_ARG;
   *launches = ctx->launches;
@@ -545,7 +603,7 @@ silu_status silu_mat_create(silu_ctx ctx, int64_t n, int64_t nnz, const int64_t*
         delete M;
         return ds;
       }
-      cudaError_t e = upload_csr(M->A, false, M->rp, M->ci, M->va, M->d, ctx->stream);
+      cudaError_t e = upload_csr(M->A, false, M->rp, M->ci, M->va, M->tiles, M->d, ctx->stream);
       if (e != cudaSuccess) {
         delete M;
         return cuda_err(ctx, e, "upload of A");
@@ -607,8 +665,8 @@ silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int 
       }
       cudaStream_t s = ctx->stream;
       const bool f32 = prec == SILU_FP32;
-      cudaError_t e = upload_csr(F->F.L, f32, F->L_rp, F->L_ci, F->L_va, F->dL, s);
-      if (e == cudaSuccess) e = upload_csr(Ut, f32, F->U_rp, F->U_ci, F->U_va, F->dU, s);
+      cudaError_t e = upload_csr(F->F.L, f32, F->L_rp, F->L_ci, F->L_va, F->L_tiles, F->dL, s);
+      if (e == cudaSuccess) e = upload_csr(Ut, f32, F->U_rp, F->U_ci, F->U_va, F->U_tiles, F->dU, s);
       if (e == cudaSuccess) e = upload(F->d_dinv, F->dinv.data(), F->dinv.size(), s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) {
@@ -644,8 +702,8 @@ silu_status ilu_refactor(silu_ilu F, const double* new_val) {
       const bool f32 = F->prec == SILU_FP32;
       const silu::Csr& Ut = (F->scale == SILU_SCALE_ROW) ? F->Us : F->F.U;
       cudaError_t e = upload(F->A->va, A.va.data(), A.va.size(), s);
-      if (e == cudaSuccess) e = upload_csr(F->F.L, f32, F->L_rp, F->L_ci, F->L_va, F->dL, s);
-      if (e == cudaSuccess) e = upload_csr(Ut, f32, F->U_rp, F->U_ci, F->U_va, F->dU, s);
+      if (e == cudaSuccess) e = upload_csr(F->F.L, f32, F->L_rp, F->L_ci, F->L_va, F->L_tiles, F->dL, s);
+      if (e == cudaSuccess) e = upload_csr(Ut, f32, F->U_rp, F->U_ci, F->U_va, F->U_tiles, F->dU, s);
       if (e == cudaSuccess) e = upload(F->d_dinv, F->dinv.data(), F->dinv.size(), s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return cuda_err(ctx, e, "upload of the refactored factors");
@@ -755,7 +813,7 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
     }
     for (;;) {
       // true residual r = b - A x into V_0, beta = ||r||
-      LAUNCH(F->ctx, SILU_K_RESIDUAL, silu::launch_sweep(F->A->d, silu::MODE_D, 1, gA, 1, b, x, V, nullptr, nullptr, silu::EPI_STORE, s));
+      LAUNCH(F->ctx, SILU_K_RESIDUAL, sweep_launch(F, F->A->d, silu::MODE_D, 1, gA, 1, b, x, V, nullptr, nullptr, silu::EPI_STORE));
       LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_dot_part(n, V, V, part[0], s));
       LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_norm_final(n, part[0], scal, s));
       CK(cudaMemcpyAsync(hp, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -782,7 +840,7 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
           direct_chunk(F, zj, vj, 1, 1, 0, true);
         else
           CK(cudaMemcpyAsync(zj, vj, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
-        LAUNCH(F->ctx, SILU_K_RESIDUAL, silu::launch_sweep(F->A->d, silu::MODE_D, 1, gA, 1, nullptr, zj, w, nullptr, nullptr, silu::EPI_SPMV, s));
+        LAUNCH(F->ctx, SILU_K_RESIDUAL, sweep_launch(F, F->A->d, silu::MODE_D, 1, gA, 1, nullptr, zj, w, nullptr, nullptr, silu::EPI_SPMV));
         LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_dot_part(n, w, V, part[0], s));
         int cur = 0;
         for (int i = 0; i <= j; ++i) {
@@ -816,6 +874,10 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
   }
   if (iters_out) *iters_out = its;
   if (relres_out) *relres_out = relres;
+  {
+    silu_status cs = silu_ctx_check(ctx);
+    if (cs != SILU_OK) return cs;
+  }
   if (result == SILU_ERR_NOT_CONVERGED) set_err(ctx, result, "fgmres_solve: maxit reached above tol");
   if (result == SILU_WARN_DIVERGED) set_err(ctx, result, "fgmres_solve: non-finite residual estimate");
   return result;

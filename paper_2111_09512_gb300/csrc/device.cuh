@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 namespace silu {
 
@@ -41,6 +42,30 @@ struct DevCsr {
   int* ci = nullptr;
   void* va = nullptr;   // double or float
   bool fp32 = false;
+  // warp tiles for the staged sweep kernel: tile t is the descriptor
+  // {r0, r1, p0, p1} of rows [r0, r1) and entries [p0, p1): at most
+  // kTileRows rows (one per lane of a warp) and kTileNnz - 8 entries;
+  // ntiles = 0 when some row is too long to stage (the lanes-per-row kernel
+  // is used then)
+  int4* tiles = nullptr;
+  int ntiles = 0;
+};
+
+// Staged-sweep tile limits (rows and entries per warp tile).  The CSR arrays
+// of a tiled matrix are allocated with kCsrPad spare elements so that copies
+// rounded out to 16-byte boundaries stay inside the allocation.
+constexpr int kTileNnz = 384;
+constexpr int kTileRows = 32;
+constexpr int kCsrPad = 8;
+
+// Build the warp-tile descriptors of a CSR row pointer (host), four ints per
+// tile.  Returns false if a row has more than kTileNnz - 8 entries.
+bool make_tiles(const int64_t* rp, int64_t n, std::vector<int>& desc);
+
+// Device-side state shared by launches on one context.
+struct LaunchEnv {
+  int sms = 0;          // multiprocessors of the device
+  int* err = nullptr;   // device error word: bit 0 = a bounded wait gave up
 };
 
 // Launch out/x = epilogue(c - T in) over all rows.  Vectors are row-major
@@ -48,6 +73,11 @@ struct DevCsr {
 // pointers given (callers offset them).  lanes = threads per row.
 cudaError_t launch_sweep(const DevCsr& T, Mode mode, int R, int lanes, int ldx, const void* c, const void* in,
                          void* out, const double* dinv, double* x, int epi, cudaStream_t s);
+
+// Same result (one right-hand side), staged kernel: persistent CTAs stream
+// row tiles of T into shared memory with bulk asynchronous copies.
+cudaError_t launch_sweep_staged(const DevCsr& T, Mode mode, const LaunchEnv& env, const void* c, const void* in,
+                                void* out, const double* dinv, double* x, int epi, cudaStream_t s);
 
 // Level-scheduled substitution over the rows listed in rows[0..nrows).
 //  lower:  y_i -= sum_j T_ij y_j ; if c_out: c_out_i = dinv_i y_i

@@ -1,0 +1,334 @@
+// Staged Richardson sweep (sm_103a): out = epilogue(c - T in), one RHS.
+//
+// The sweep is a CSR SpMV that the paper's performance model treats as
+// bandwidth-bound (one full read of the factor per sweep, Sec. 6.4).  On
+// GB300 FP64 arithmetic is also scarce (about two FP64 lanes per clock per
+// SM), so at 12 bytes per FP64 entry the FP64 pipe saturates at nearly the
+// same rate as HBM: the kernel spends one FP64 fused multiply-add per entry
+// of the longest row in each warp and nothing else, and keeps the FP64 unit
+// fed while other warps wait on memory.
+//
+// Work is cut into warp tiles of up to 32 consecutive rows (one per lane).
+// Every warp walks its own fixed sequence of tiles with its own two-stage
+// shared-memory ring: lane 0 issues three bulk asynchronous copies per tile
+// (values, column indices, row pointers) that complete on the stage's
+// mbarrier, marked evict-first in L2; the warp computes one tile while the
+// next one lands.  Warps never wait for each other, so their gather and FMA
+// phases interleave on the SM.  A lane's accumulator starts at c_i and takes
+// acc <- acc - t_ij * in_j for each entry in column order, so c - T in costs
+// one FMA per entry; the iterate vectors are read and written evict-last so
+// they stay resident in L2 from one sweep to the next.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <vector>
+
+#include "device.cuh"
+
+namespace silu {
+
+bool make_tiles(const int64_t* rp, int64_t n, std::vector<int>& desc) {
+  desc.clear();
+  int64_t r0 = 0;
+  while (r0 < n) {
+    int64_t r1 = r0;
+    while (r1 < n && r1 - r0 < kTileRows && rp[r1 + 1] - rp[r0] <= kTileNnz - 8) ++r1;
+    if (r1 == r0) return false;  // a single row does not fit
+    desc.push_back((int)r0);
+    desc.push_back((int)r1);
+    desc.push_back((int)rp[r0]);
+    desc.push_back((int)rp[r1]);
+    r0 = r1;
+  }
+  return true;
+}
+
+namespace {
+
+constexpr int kWarpStages = 2;
+constexpr int kWarps = 20;
+constexpr int kStagedThreads = kWarps * 32;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of bar, giving up after kWaitNs.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// Vector accesses that keep the iterates resident in L2 across sweeps.
+__device__ __forceinline__ double ld_keep(const double* p, uint64_t pol) {
+  double v;
+  asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float ld_keep(const float* p, uint64_t pol) {
+  float v;
+  asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void st_keep(double* p, double v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_keep(float* p, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
+}
+
+// One stage: a 16-byte header (the tile descriptor, written by the issuing
+// lane), then values, column indices and row pointers as copied.
+template <class MT>
+struct StageLayout {
+  static constexpr int kValAlign = 16 / (int)sizeof(MT);  // elements per 16 bytes
+  static constexpr size_t kHdr = 16;
+  static constexpr size_t kVal = sizeof(MT) * (kTileNnz + 8);
+  static constexpr size_t kCol = sizeof(int) * (kTileNnz + 8);
+  static constexpr size_t kRp = sizeof(int) * (kTileRows + 8);
+  static constexpr size_t kBytes = kHdr + kVal + kCol + kRp;  // all multiples of 16
+};
+
+// Issuing lane: record the descriptor d of a tile in the stage header and
+// issue its three copies into stage buffer `st`.  The header store precedes
+// the arrive on the stage's mbarrier, so waiters see it.
+template <class MT>
+__device__ __forceinline__ void issue_tile(int4 d, unsigned char* st, uint64_t* bar, const int* __restrict__ rp,
+                                           const int* __restrict__ ci, const MT* __restrict__ va, uint64_t pol) {
+  using L = StageLayout<MT>;
+  const int r0 = d.x, r1 = d.y, p0 = d.z, p1 = d.w;
+  const int a0 = p0 & ~(L::kValAlign - 1), a1 = (p1 + L::kValAlign - 1) & ~(L::kValAlign - 1);
+  const int c0 = p0 & ~3, c1 = (p1 + 3) & ~3;
+  const int q0 = r0 & ~3, q1 = (r1 + 1 + 3) & ~3;
+  const uint32_t bv = (uint32_t)(a1 - a0) * (uint32_t)sizeof(MT);
+  const uint32_t bc = (uint32_t)(c1 - c0) * 4u;
+  const uint32_t br = (uint32_t)(q1 - q0) * 4u;
+  *(int4*)st = d;
+  fence_proxy_async();
+  mbar_expect_tx(bar, bv + bc + br);
+  if (bv) bulk_g2s(st + L::kHdr, va + a0, bv, bar, pol);
+  if (bc) bulk_g2s(st + L::kHdr + L::kVal, ci + c0, bc, bar, pol);
+  bulk_g2s(st + L::kHdr + L::kVal + L::kCol, rp + q0, br, bar, pol);
+}
+
+template <class MT, class VI, class VO>
+__device__ __forceinline__ void epilogue(int epi, int row, MT t, const VI* in, VO* out, const double* dinv,
+                                         double* x, uint64_t keep) {
+  switch (epi) {
+    case EPI_STORE: st_keep(out + row, (VO)t, keep); break;
+    case EPI_SCALE: st_keep(out + row, (VO)(dinv[row] * (double)t), keep); break;
+    case EPI_ADDX: x[row] += (double)t; break;
+    case EPI_SETX: x[row] = (double)t; break;
+    case EPI_SCALE_ADDX: x[row] += dinv[row] * (double)t; break;
+    case EPI_SCALE_SETX: x[row] = dinv[row] * (double)t; break;
+    case EPI_JAC: st_keep(out + row, (VO)((MT)in[row] + (MT)dinv[row] * t), keep); break;
+    case EPI_JAC_ADDX: x[row] += (double)((MT)in[row] + (MT)dinv[row] * t); break;
+    case EPI_JAC_SETX: x[row] = (double)((MT)in[row] + (MT)dinv[row] * t); break;
+    case EPI_RICH: st_keep(out + row, (VO)(t + (MT)in[row]), keep); break;
+    case EPI_RICH_ADDX: x[row] += (double)(t + (MT)in[row]); break;
+    case EPI_RICH_SETX: x[row] = (double)(t + (MT)in[row]); break;
+    default: break;
+  }
+}
+
+// acc -/+= sum_k v[k] * in[col[k]] over one row held in shared memory.  All
+// gathers of a chunk of kChunk entries are issued before the first FMA (one
+// latency round per chunk); the FMA loop runs to the longest row of the warp
+// (a warp-uniform bound) and padded lanes multiply zeros, which leaves acc
+// exactly unchanged.  Cost: one FP64 FMA per entry of the warp's longest row.
+constexpr int kChunk = 16;
+
+template <class MT, class VI, bool NEG>
+__device__ __forceinline__ MT row_accumulate(const MT* sv, const int* sc, int len, const VI* __restrict__ in,
+                                             MT acc, uint64_t keep) {
+  const int wmax = __reduce_max_sync(0xffffffffu, len);
+  for (int k0 = 0; k0 < wmax; k0 += kChunk) {
+    MT v[kChunk], xv[kChunk];
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+      if (k0 + k < len) {
+        v[k] = sv[k0 + k];
+        xv[k] = (MT)ld_keep(in + sc[k0 + k], keep);
+      } else {
+        v[k] = MT(0);
+        xv[k] = MT(0);
+      }
+    }
+    // warp-uniform exit: a predicated FMA would still occupy the FP64 pipe
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+      if (k0 + k >= wmax) break;
+      acc = fma(NEG ? -v[k] : v[k], xv[k], acc);
+    }
+  }
+  return acc;
+}
+
+template <class MT, class VI, class VO>
+__global__ void __launch_bounds__(kStagedThreads, 1)
+    k_sweep_staged(int ntiles, const int4* __restrict__ tiles, const int* __restrict__ rp, const int* __restrict__ ci,
+                   const MT* __restrict__ va, const VI* __restrict__ c, const VI* __restrict__ in,
+                   VO* __restrict__ out, const double* __restrict__ dinv, double* __restrict__ x, int epi,
+                   int* __restrict__ err) {
+  using L = StageLayout<MT>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kWarps][kWarpStages];
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int w = 0; w < kWarps; ++w)
+      for (int s = 0; s < kWarpStages; ++s) mbar_init(&full[w][s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int gw = blockIdx.x * kWarps + warp;  // this warp's first tile
+  const int nw = gridDim.x * kWarps;          // tile stride
+  unsigned char* ring = smem + (size_t)warp * kWarpStages * L::kBytes;
+  const uint64_t stream = policy_evict_first();
+  const uint64_t keep = policy_evict_last();
+  if (lane == 0)
+    for (int s = 0; s < kWarpStages; ++s) {
+      const int t = gw + s * nw;
+      if (t < ntiles) issue_tile<MT>(__ldg(tiles + t), ring + s * L::kBytes, &full[warp][s], rp, ci, va, stream);
+    }
+  int k = 0;
+  for (int t = gw; t < ntiles; t += nw, ++k) {
+    // the issuing lane fetches the descriptor of the tile it will issue next
+    const int tn = t + kWarpStages * nw;
+    int4 dn = make_int4(0, 0, 0, 0);
+    if (lane == 0 && tn < ntiles) dn = __ldg(tiles + tn);
+    const int s = k % kWarpStages;
+    const bool ok = mbar_wait_bounded(&full[warp][s], (uint32_t)(k / kWarpStages) & 1u);
+    if (!__all_sync(0xffffffffu, ok)) {
+      // a copy did not land in time: report, let the other stage's copy land, leave
+      if (lane == 0) {
+        atomicOr(err, 1);
+        for (int d = 1; d < kWarpStages; ++d) {
+          const int kd = k + d;
+          if (t + d * nw < ntiles) mbar_wait_bounded(&full[warp][kd % kWarpStages], (uint32_t)(kd / kWarpStages) & 1u);
+        }
+      }
+      return;
+    }
+    const unsigned char* st = ring + s * L::kBytes;
+    const int4 d = *(const int4*)st;
+    const MT* sv = (const MT*)(st + L::kHdr);
+    const int* sc = (const int*)(st + L::kHdr + L::kVal);
+    const int* sr = (const int*)(st + L::kHdr + L::kVal + L::kCol);
+    const int r0 = d.x, r1 = d.y, p0 = d.z;
+    const int q0 = r0 & ~3;
+    const int a0 = p0 & ~(L::kValAlign - 1);
+    const int c0 = p0 & ~3;
+    const int r = r0 + lane;
+    const bool act = r < r1;
+    const int b = act ? sr[r - q0] : p0;
+    const int len = act ? sr[r + 1 - q0] - b : 0;
+    MT acc = (act && c) ? (MT)ld_keep(c + r, keep) : MT(0);
+    if (epi == EPI_SPMV)
+      acc = row_accumulate<MT, VI, false>(sv + (b - a0), sc + (b - c0), len, in, acc, keep);
+    else
+      acc = row_accumulate<MT, VI, true>(sv + (b - a0), sc + (b - c0), len, in, acc, keep);
+    if (act) {
+      if (epi == EPI_SPMV)
+        st_keep(out + r, (VO)acc, keep);
+      else
+        epilogue<MT, VI, VO>(epi, r, acc, in, out, dinv, x, keep);
+    }
+    __syncwarp();
+    if (lane == 0 && tn < ntiles) issue_tile<MT>(dn, ring + s * L::kBytes, &full[warp][s], rp, ci, va, stream);
+  }
+}
+
+template <class MT, class VI, class VO>
+cudaError_t staged(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
+                   const double* dinv, double* x, int epi, cudaStream_t s) {
+  using L = StageLayout<MT>;
+  // the shared-memory opt-in is per function and per device
+  static std::atomic<unsigned long long> attr_set{0};
+  const size_t smem = (size_t)kWarps * kWarpStages * L::kBytes;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(attr_set.load() & bit)) {
+    e = cudaFuncSetAttribute(k_sweep_staged<MT, VI, VO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set.fetch_or(bit);
+  }
+  if (T.ntiles == 0) return cudaSuccess;
+  const int want = (T.ntiles + kWarps - 1) / kWarps;
+  const int grid = want < env.sms ? want : env.sms;
+  k_sweep_staged<MT, VI, VO><<<grid, kStagedThreads, smem, s>>>(T.ntiles, T.tiles, T.rp, T.ci, (const MT*)T.va,
+                                                                 (const VI*)c, (const VI*)in, (VO*)out, dinv, x,
+                                                                 epi, env.err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sweep_staged(const DevCsr& T, Mode mode, const LaunchEnv& env, const void* c, const void* in,
+                                void* out, const double* dinv, double* x, int epi, cudaStream_t s) {
+  switch (mode) {
+    case MODE_D: return staged<double, double, double>(T, env, c, in, out, dinv, x, epi, s);
+    case MODE_F: return staged<float, float, float>(T, env, c, in, out, dinv, x, epi, s);
+    case MODE_DF: return staged<double, double, float>(T, env, c, in, out, dinv, x, epi, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace silu

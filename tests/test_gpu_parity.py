@@ -67,12 +67,16 @@ SMOOTH_CASES = [
 ]
 
 
+@pytest.mark.parametrize("variant", [1, 2], ids=["lanes", "staged"])
 @pytest.mark.parametrize("case", SMOOTH_CASES, ids=[c[0] for c in SMOOTH_CASES])
-def test_smooth_fp64_matches_oracle(silu, ctx, case):
+def test_smooth_fp64_matches_oracle(silu, ctx, case, variant):
+    """Both sweep kernels: lanes-per-row (any R) and staged bulk-copy (R = 1;
+    with R > 1 the library uses the lanes kernel, covered again)."""
     name, gen, kind, tau, fill, nrhs, sweeps = case
     A = gen()
     n = len(A[0]) - 1
     F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), kind, tau, fill)
+    F.set_kernel(variant)
     _, S = oracle_scaled(A, kind, tau, fill)
     b = synth.rhs(n, nrhs, seed=11)
     x0 = synth.rhs(n, nrhs, seed=12) * 0.5
@@ -80,7 +84,16 @@ def test_smooth_fp64_matches_oracle(silu, ctx, case):
         want = oracle.smooth(A, S, x0, b, mL, mU)
         x = dev(x0.copy())
         silu.ilu_smooth(F, x, dev(b), mL, mU)
+        ctx.check()
         assert percol_relerr(host(x), want) < FP64_TOL, (mL, mU)
+    if nrhs > 1:
+        # the same columns one at a time go through the staged kernel
+        for k in range(nrhs):
+            want = oracle.smooth(A, S, x0[:, k:k + 1], b[:, k:k + 1], 3, 2)
+            x = dev(x0[:, k:k + 1].copy())
+            silu.ilu_smooth(F, x, dev(b[:, k:k + 1].copy()), 3, 2)
+            ctx.check()
+            assert percol_relerr(host(x), want) < FP64_TOL
 
 
 @pytest.mark.parametrize("scale", ["none", "rich"])
@@ -151,13 +164,16 @@ def test_fp32_error_against_fp64_oracle(silu, ctx):
     F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0", prec=silu.FP32)
     _, S = oracle_scaled(A, "ilu0", 0.0, 0)
     b = synth.rhs(n, 1, seed=1)
-    for mL, mU in [(3, 3), (5, 5), (1, 1)]:
-        want = oracle.smooth(A, S, np.zeros((n, 1)), b, mL, mU)
-        x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
-        silu.ilu_smooth(F, x, dev(b), mL, mU)
-        err = relerr(host(x), want)
-        print(f"FP32 smoother ({mL},{mU}) relative error vs FP64 oracle: {err:.3e}")
-        assert err < 1e-5
+    for variant in (1, 2):
+        F.set_kernel(variant)
+        for mL, mU in [(3, 3), (5, 5), (1, 1)]:
+            want = oracle.smooth(A, S, np.zeros((n, 1)), b, mL, mU)
+            x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+            silu.ilu_smooth(F, x, dev(b), mL, mU)
+            ctx.check()
+            err = relerr(host(x), want)
+            print(f"FP32 smoother kernel {variant} ({mL},{mU}) relative error vs FP64 oracle: {err:.3e}")
+            assert err < 1e-5
 
 
 def test_fgmres_matches_oracle(silu, ctx):
