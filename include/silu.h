@@ -47,7 +47,7 @@ typedef enum {
   SILU_ERR_NO_DEVICE = 8      /* device call on a host-only context          */
 } silu_status;
 
-/* Incomplete factorisation kinds (Sec. 1, Sec. 3.2 of the paper). */
+/* Incomplete factorisation kinds (Sec. 1, Sec. 4.2, Sec. 5.1 of the paper). */
 typedef enum { SILU_ILU0 = 0, SILU_ILUK = 1, SILU_ILUT = 2 } silu_kind;
 
 /*
@@ -120,8 +120,8 @@ const char* silu_version(void);
  * Copy the host CSR matrix A (n rows, nnz entries) into the library:
  * validated (row pointers monotone, columns in range, values finite),
  * columns sorted, duplicates summed, and uploaded to the device on a device
- * context.  A is the pressure matrix of the paper's Eq. for the projection
- * (Sec. 2); any square matrix with a nonzero diagonal is accepted.
+ * context.  A is the pressure matrix of the paper's projection step
+ * (Sec. 2, Eq. nodalP, Eq. press); any square matrix with a nonzero diagonal is accepted.
  */
 silu_status silu_mat_create(silu_ctx ctx, int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
                             const double* val, silu_mat* out);
@@ -129,11 +129,11 @@ void silu_mat_destroy(silu_mat A);
 
 /*
  * Host factorisation + scaling + packing, then one upload (blocks).
- *  kind  SILU_ILU0: pattern of A (Sec. 3.2, Matlab ilu 'nofill').
+ *  kind  SILU_ILU0: pattern of A (Sec. 5.1, Matlab ilu 'nofill').
  *        SILU_ILUK: level-of-fill k = `fill` (Sec. 1).
  *        SILU_ILUT: dual threshold, drop tolerance `tau` relative to the row's
  *        2-norm and at most `fill` entries per row in each of L and U
- *        (droptol / lfill, Sec. 3.2, Sec. 6.1); the paper does not define
+ *        (droptol / lfill, Sec. 4.2, Sec. 6.1); the paper does not define
  *        the rule and this is Saad's ILUT.
  *  Pivoting is off; a zero or non-finite pivot gives SILU_ERR_ZERO_PIVOT.
  *  L is unit lower, stored as its strict part L_s.  The level sets of L_s and
@@ -145,7 +145,7 @@ silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int 
 /*
  * Numeric refactorisation with new values of A on the SAME pattern (nnz
  * values in the sorted, duplicate-free order of the silu_mat), reusing the
- * symbolic phase (Sec. 3.2: the pattern of the pressure matrix does not change
+ * symbolic phase (Sec. 3.1: the pattern of the pressure matrix does not change
  * during a fluid step).  ILU0 and ILUK only (ILUT's pattern depends on the
  * values): SILU_ERR_INVALID_ARG otherwise.  Blocks.
  */

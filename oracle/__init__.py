@@ -3,7 +3,7 @@
 Plain, slow, single-threaded FP64 code (oracle.c, compiled with
 -ffp-contract=off) that states what the smoother computes, step by step from
 Thomas et al., "Scaled ILU Smoothers for Navier-Stokes Pressure Projection"
-(arXiv 2111.09512): ILU(0) / ILU(k) / ILUT factorisation (Sec. 3.2), row
+(arXiv 2111.09512): ILU(0) / ILU(k) / ILUT factorisation (Sec. 4.2, Sec. 5.1), row
 scaling (Eq. extractD, Eq. newD), the Richardson sweeps of Alg. ILUJac and
 Eq. richard, the direct triangular solves with level sets (Sec. 4), FGMRES
 with modified Gram-Schmidt (Sec. 6) and the diagnostics dep (Eq. depB) and

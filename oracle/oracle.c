@@ -184,7 +184,7 @@ static int csr_ok(int64_t n, const int64_t* rp, const int32_t* ci) {
  * Numeric incomplete LU on the pattern P (row pointer pp, columns pc, which
  * contains the pattern of A).  IKJ elimination over row i, Saad, "Iterative
  * Methods for Sparse Linear Systems", the variant the paper names for ILU(0)
- * (Matlab ilu with setup type 'nofill', pivoting off, Sec. 3.2):
+ * (Matlab ilu with setup type 'nofill', Sec. 5.1; pivoting off, Sec. 4.2):
  *   for k < i in P(i), ascending:  a_ik <- a_ik / a_kk
  *                                  a_ij <- a_ij - a_ik * a_kj  for j > k, j in P(i) and P(k)
  */
@@ -267,7 +267,7 @@ fail_nomsg:
   return NULL;
 }
 
-/* ILU(0): the pattern of the factors is the pattern of A (Sec. 3.2, Table dep). */
+/* ILU(0): the pattern of the factors is the pattern of A (Sec. 5.1, Table dep). */
 orc_lu* orc_ilu0(int64_t n, const int64_t* rp, const int32_t* ci, const double* va, int* status) {
   if (!csr_ok(n, rp, ci) || !va) {
     *status = ORC_BADARG;
@@ -423,7 +423,7 @@ static int cmp_cand_col(const void* x, const void* y) {
 
 /*
  * The paper uses ILUT with a drop tolerance and a fill limit per row
- * (droptol, lfill; Sec. 3.2, Sec. 6.1) without defining the rule.  Reading:
+ * (droptol, lfill; Sec. 4.2, Sec. 6.1) without defining the rule.  Reading:
  * Saad's ILUT(tau, p) with pivoting off.  For row i:
  *   tau_i = tau * ||a_{i,:}||_2
  *   w = a_{i,:}

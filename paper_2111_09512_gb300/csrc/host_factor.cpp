@@ -1,6 +1,6 @@
 // Host-side setup of the scaled-ILU smoother (see host_factor.h).
 //
-// The factorisations follow the paper's setup step (Sec. 3.2, Sec. 5.1): an
+// The factorisations follow the paper's setup step (Sec. 4.2, Sec. 5.1): an
 // incomplete LU with pivoting off, L unit lower, U upper, then the row
 // scaling D = diag(U), Utilde = D^{-1} U (Eq. extractD, Eq. newD).  ILU(k)
 // uses Saad's level-of-fill and ILUT Saad's dual threshold, the readings of

@@ -1,7 +1,7 @@
 // Staged Richardson sweep (sm_103a): out = epilogue(c - T in), one RHS.
 //
 // The sweep is a CSR SpMV that the paper's performance model treats as
-// bandwidth-bound (one full read of the factor per sweep, Sec. 6.4).  On
+// bandwidth-bound (one full read of the factor per sweep, Sec. 6.3).  On
 // GB300 FP64 arithmetic is also scarce (about two FP64 lanes per clock per
 // SM), so at 12 bytes per FP64 entry the FP64 pipe saturates at nearly the
 // same rate as HBM: the kernel spends one FP64 fused multiply-add per entry

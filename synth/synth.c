@@ -7,10 +7,10 @@
  * The paper's matrices (PeleLM nodal projection, Nalu-Wind pressure
  * continuity) are not available, so these generators stand in for them with
  * the properties the paper names: symmetric pressure-Poisson operators
- * (Sec. 2, Eq. for the nodal projection), cut cells with arbitrarily small
+ * (Sec. 2, Eq. nodalP), cut cells with arbitrarily small
  * volume and area fractions and coefficients spanning many orders of
  * magnitude (Sec. 1), and 26 neighbours per row for the unstructured-mesh
- * case (Sec. 6.4, performance model).
+ * case (Sec. 6.3, performance model).
  *
  * Kinds (natural lexicographic ordering, x fastest, Dirichlet boundaries
  * eliminated):
