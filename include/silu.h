@@ -44,7 +44,8 @@ typedef enum {
   SILU_ERR_CUDA = 5,          /* a CUDA runtime call failed                  */
   SILU_ERR_TIMEOUT = 6,       /* a bounded device wait gave up               */
   SILU_WARN_DIVERGED = 7,     /* iterate grew beyond a bound (not an error)  */
-  SILU_ERR_NO_DEVICE = 8      /* device call on a host-only context          */
+  SILU_ERR_NO_DEVICE = 8,     /* device call on a host-only context          */
+  SILU_ERR_TOO_LARGE = 9      /* problem exceeds a fixed-capacity entry point */
 } silu_status;
 
 /* Incomplete factorisation kinds (Sec. 1, Sec. 4.2, Sec. 5.1 of the paper). */
@@ -223,6 +224,39 @@ silu_status silu_ilu_set_lanes(silu_ilu F, int lanes_L, int lanes_U, int lanes_A
  * asynchronous copies; it needs rows of at most 4088 entries.
  */
 silu_status silu_ilu_set_kernel(silu_ilu F, int variant);
+
+/*
+ * Allocation-free smoother application (the paper has no counterpart; it
+ * exists for callers that cannot allocate device memory when they apply
+ * the smoother: applications whose device memory is owned up front by their
+ * own pool or another framework's allocator, and latency-critical loops
+ * that must not pay the implicit synchronisation of cudaMalloc / cudaFree).
+ *
+ * Computes the same update as ilu_smooth with row scaling, FP64, one
+ * right-hand side:  x <- x + v,  v from sweeps_U sweeps on Utilde_s after
+ * sweeps_L sweeps on L_s applied to r = b - A x.  All arrays are DEVICE
+ * arrays owned by the caller, with int32 row pointers (n+1 entries), int32
+ * column indices and FP64 values: A, the strict lower factor L_s, the
+ * strict scaled upper factor Utilde_s (as silu_ilu_export's Sp/Sc/Sv), and
+ * dinv = 1 / diag(U); x (in/out) and b have n entries.  Work is ordered on
+ * cuda_stream of `device` and is asynchronous.
+ *
+ * Nothing is allocated: the working vectors live in a fixed array compiled
+ * into the library (four vectors of 524288 doubles, 16 MiB, held by every
+ * device that loads the library until the process exits).  n above 524288
+ * returns SILU_ERR_TOO_LARGE before any work.  The first call on a device
+ * looks up that array's device address (with the device made current, the
+ * caller's current device restored afterwards).  All calls share the array
+ * and it keeps the last call's contents (every vector is written before it
+ * is read); calls whose work overlaps on the GPU race on it.
+ * Returns SILU_ERR_INVALID_ARG for null pointers or negative counts,
+ * SILU_ERR_NO_DEVICE if the device cannot be selected, SILU_ERR_CUDA if a
+ * launch fails.
+ */
+silu_status silu_smooth_noalloc(int device, void* cuda_stream, int64_t n, const int32_t* A_rp, const int32_t* A_ci,
+                                const double* A_val, const int32_t* L_rp, const int32_t* L_ci, const double* L_val,
+                                const int32_t* U_rp, const int32_t* U_ci, const double* U_val, const double* dinv,
+                                double* x, const double* b, int sweeps_L, int sweeps_U);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_PKG, "libsilu.so")
 
 # silu_status
 OK, ERR_INVALID_ARG, ERR_ZERO_PIVOT, ERR_NOT_CONVERGED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, WARN_DIVERGED, \
-    ERR_NO_DEVICE = range(9)
+    ERR_NO_DEVICE, ERR_TOO_LARGE = range(10)
 # silu_kind
 ILU0, ILUK, ILUT = 0, 1, 2
 # silu_scale
@@ -91,6 +91,7 @@ def load():
         "silu_ctx_launch_count": (i32, [vp, ctypes.POINTER(i64)]),
         "silu_ctx_check": (i32, [vp]),
         "silu_ilu_set_kernel": (i32, [vp, i32]),
+        "silu_smooth_noalloc": (i32, [i32, vp, i64] + [vp] * 12 + [i32, i32]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -106,7 +107,7 @@ def exported_symbols():
             "silu_mat_destroy", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
-            "silu_ctx_launch_count", "silu_ctx_check", "silu_ilu_set_kernel"]
+            "silu_ctx_launch_count", "silu_ctx_check", "silu_ilu_set_kernel", "silu_smooth_noalloc"]
 
 
 def _ptr(t) -> int:
@@ -340,6 +341,18 @@ def direct_trisolve(F: ILU, x, b) -> None:
     _check_vec(x, F.n, nrhs)
     _check_vec(b, F.n, nrhs)
     _check(F.ctx.handle, load().direct_trisolve(F.handle, _ptr(x), _ptr(b), nrhs), "direct_trisolve")
+
+
+def silu_smooth_noalloc(device: int, stream, n: int, A, L, Us, dinv, x, b, sweeps_L: int, sweeps_U: int) -> int:
+    """Allocation-free smoother application on caller-owned device arrays.
+
+    A, L and Us are (row_ptr int32, col int32, val float64) device tensors;
+    dinv, x (in/out) and b are float64 device vectors of length n.  Returns
+    the status (ERR_TOO_LARGE above the fixed capacity); nothing is allocated
+    by the library during the call.
+    """
+    args = [_ptr(t) for t in (*A, *L, *Us, dinv, x, b)]
+    return load().silu_smooth_noalloc(device, _stream_handle(stream), n, *args, sweeps_L, sweeps_U)
 
 
 def fgmres_solve(F: ILU, x, b, tol: float = 1e-8, restart: int = 30, maxit: int = 1000, sweeps_L: int = 3,
