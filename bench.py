@@ -7,8 +7,9 @@ paper's model counts twenty Richardson iterations per smoother application),
 on the 128^3 cut-cell pressure matrix (2,097,152 rows, ILUT(1e-3, 10), FP64,
 one right-hand side).  Metric: algorithmic GB/s of the application (bytes
 the method must move, defined below) and its fraction of the measured HBM
-bandwidth; then the FGMRES time to 1e-8 of the FP32-smoother path against the
-FP64 direct-trisolve path.
+bandwidth.  Then, on the 27-point 256^3 matrix (16.8M rows, 449M entries),
+the FGMRES(30) time to 1e-10 of the FP32-smoother path against the FP64
+direct-trisolve path, and the FP32 smoother's GB/s.
 
 Every rank runs an independent replica (the path does not shard on one
 GPU: replicas only); value = bytes of all ranks / max time over ranks.
@@ -71,7 +72,7 @@ def load_peaks():
 
 def sweep_source_hash():
     h = hashlib.sha256()
-    for f in ("kernels_sweep.cu", "device.cuh"):
+    for f in ("kernels_staged.cu", "device.cuh"):
         with open(os.path.join(ROOT, "paper_2111_09512_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -354,7 +355,7 @@ def run_silu(args):
 
     solve = None
     if not args.no_solve and rank == 0:
-        solve = solve_comparison(silu, ctx, A, b_np, torch)
+        solve = solve_comparison(silu, ctx, torch, args.solve_edge)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -395,30 +396,56 @@ def run_silu(args):
     return 0
 
 
-def solve_comparison(silu, ctx, A, b_np, torch):
-    """Time to 1e-8 relative residual: FGMRES(30) with the FP32 scaled-ILU
-    Richardson smoother (3+3 sweeps) against FGMRES(30) with FP64 direct
-    level-scheduled triangular solves, same matrix, same ILUT factors."""
+def solve_comparison(silu, ctx, torch, edge: int):
+    """The 27-point workload: FGMRES(30) to 1e-10 relative residual with the
+    FP32 scaled-ILU(0) Richardson smoother (3+3 FP32 sweeps, FP64 residual and
+    Krylov) against FGMRES(30) with FP64 level-scheduled direct triangular
+    solves of the same factors, on the 27-point perturbed-hex Laplacian
+    (edge^3 rows; 256^3 = 16.8M rows, 449M entries).  Also the FP32 smoother
+    application's algorithmic GB/s."""
+    import synth
+    A = synth.hex27(edge, seed=2)
     n = len(A[0]) - 1
-    out = {"tol": 1e-8, "restart": 30}
+    b_np = synth.rhs(n, 1, seed=2)
+    t0 = time.perf_counter()
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0", prec=silu.FP32)
+    setup_s = time.perf_counter() - t0
+    st = F.stats()
+    F.reserve(1, 30)
+    out = {"workload": f"hex27-{edge}^3 ILU(0)", "rows": n, "nnz_A": len(A[1]), "tol": 1e-10, "restart": 30,
+           "setup_s": round(setup_s, 2)}
+    del A
     b = torch.from_numpy(b_np[:, 0].copy()).cuda()
-    for name, prec, pc in (("fp32_sweeps_3_3", silu.FP32, silu.PRECOND_SWEEPS),
-                           ("fp64_direct", silu.FP64, silu.PRECOND_DIRECT)):
-        F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilut", TAU, FILL, prec=prec)
-        F.reserve(1, 30)
+    # FP32 smoother application rate (zero initial guess skips the residual)
+    x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+    b2 = b.reshape(n, 1)
+    for _ in range(3):
+        silu.ilu_smooth(F, x, b2, 3, 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record()
+    for _ in range(reps):
+        silu.ilu_smooth(F, x, b2, 3, 3)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = apply_bytes(n, out["nnz_A"], st["nnz_L"], st["nnz_U"], 1, 4, 3, 3)
+    out["fp32_apply"] = {"ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "bytes": nbytes}
+    for name, pc in (("fp32_sweeps_3_3", silu.PRECOND_SWEEPS), ("fp64_direct", silu.PRECOND_DIRECT)):
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
-        silu.fgmres_solve(F, x, b, tol=1e-8, restart=30, maxit=1, sweeps_L=3, sweeps_U=3, precond=pc)
+        silu.fgmres_solve(F, x, b, tol=1e-10, restart=30, maxit=1, sweeps_L=3, sweeps_U=3, precond=pc)
         x.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, its, rel = silu.fgmres_solve(F, x, b, tol=1e-8, restart=30, maxit=2000, sweeps_L=3, sweeps_U=3,
-                                         precond=pc)
+        stt, its, rel = silu.fgmres_solve(F, x, b, tol=1e-10, restart=30, maxit=3000, sweeps_L=3, sweeps_U=3,
+                                          precond=pc)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        out[name] = {"seconds": round(dt, 5), "iterations": its, "relres": rel, "converged": st == silu.OK}
-        del F
+        out[name] = {"seconds": round(dt, 4), "iterations": its, "relres": rel, "converged": stt == silu.OK}
     if out["fp32_sweeps_3_3"]["seconds"] > 0:
         out["speedup_sweeps_vs_direct"] = round(out["fp64_direct"]["seconds"] / out["fp32_sweeps_3_3"]["seconds"], 3)
+    del F
     return out
 
 
@@ -429,6 +456,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["silu", "reference"], default="silu")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--solve-edge", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()

@@ -71,9 +71,24 @@ struct silu_mat_s {
   DevCsr d;
 };
 
+// A captured level-scheduled solve on the workspace vectors of one column block.
+struct LevelGraph {
+  int R = 0, ldx = 0;
+  size_t col = 0;
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;
+};
+
 struct Workspace {
   size_t vec_bytes = 0;  // per buffer
   DBuf r, c, p0, p1;
+  std::vector<LevelGraph> graphs;  // valid while r and c keep their addresses
+  ~Workspace() { drop_graphs(); }
+  void drop_graphs() {
+    for (LevelGraph& g : graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
   int restart = 0;
   DBuf V, Z, w, H, cs, sn, g, yk, part0, part1, scal;
 };
@@ -203,7 +218,8 @@ cudaError_t upload_csr(const silu::Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& 
     }
   }
   std::vector<int> tl;
-  const bool tiled = silu::make_tiles(T.rp.data(), T.n, tl);
+  const int tlanes = silu::staged_lanes(T.rp.data(), T.n);
+  const bool tiled = silu::make_tiles(T.rp.data(), T.n, tlanes, tl);
   if (e == cudaSuccess && tiled) e = upload(tiles, tl.data(), tl.size(), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging vectors die at return
   d.n = (int)T.n;
@@ -214,6 +230,7 @@ cudaError_t upload_csr(const silu::Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& 
   d.fp32 = fp32;
   d.tiles = tiled ? tiles.as<int4>() : nullptr;
   d.ntiles = tiled ? (int)(tl.size() / 4) : 0;
+  d.tile_lanes = tlanes;
   return e;
 }
 
@@ -229,6 +246,7 @@ cudaError_t ensure_vectors(silu_ilu F, int nrhs) {
   const size_t bytes = sizeof(double) * (size_t)F->F.L.n * (size_t)nrhs;
   Workspace& w = F->ws;
   if (bytes <= w.vec_bytes && w.r.p) return cudaSuccess;
+  w.drop_graphs();
   cudaError_t e;
   if ((e = w.r.ensure(bytes)) != cudaSuccess) return e;
   if ((e = w.c.ensure(bytes)) != cudaSuccess) return e;
@@ -260,6 +278,7 @@ cudaError_t ensure_krylov(silu_ilu F, int m) {
 
 cudaError_t ensure_direct(silu_ilu F) {
   if (F->direct_ready) return cudaSuccess;
+  F->ws.drop_graphs();  // captured solves refer to the arrays uploaded here
   cudaStream_t s = F->ctx->stream;
   cudaError_t e = cudaSuccess;
   // FP64 L_s: reuse the sweep copy when it is FP64
@@ -448,31 +467,67 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
   }
 }
 
-// Direct application on columns [0, R): x (+)= Utilde^{-1} D^{-1} L^{-1} (b - A x).
-// y holds r and is overwritten by L^{-1} r level by level; the lower level
-// kernel also writes c = D^{-1} y, which the upper levels overwrite with v.
-void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, bool x_zero) {
-  cudaStream_t s = F->ctx->stream;
-  const int n = (int)F->F.L.n;
+// The level-scheduled substitutions of one column block, captured once into a
+// CUDA graph: one kernel node per level, each depending on the previous one
+// (Sec. 4: rows of a level are independent, levels are ordered).  The graph
+// works on the workspace vectors only: y (holding r on entry) becomes
+// L^{-1} r, c becomes Utilde^{-1} D^{-1} y.
+cudaGraphExec_t level_graph(silu_ilu F, int R, int ldx, size_t col) {
+  for (const LevelGraph& g : F->ws.graphs)
+    if (g.R == R && g.ldx == ldx && g.col == col) return g.exec;
+  cudaStream_t cap = nullptr;
+  CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   const double* dinv = F->d_dinv.as<double>();
   double* y = F->ws.r.as<double>() + col;
   double* c = F->ws.c.as<double>() + col;
-  const int gL = lanes_of(F->lanesL, F->autoL), gU = lanes_of(F->lanesU, F->autoU), gA = lanes_of(F->lanesA, F->autoA);
+  const int gL = lanes_of(F->lanesL, F->autoL), gU = lanes_of(F->lanesU, F->autoU);
+  const int* rowsL = F->levLrows_d.as<int>();
+  const int* rowsU = F->levUrows_d.as<int>();
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  for (int l = 0; e == cudaSuccess && l < F->nlevL; ++l) {
+    const int b0 = F->levLptr[l], b1 = F->levLptr[l + 1];
+    e = silu::launch_level(F->dL64, rowsL + b0, b1 - b0, R, gL, ldx, y, dinv, c, nullptr, cap);
+  }
+  for (int l = 0; e == cudaSuccess && l < F->nlevU; ++l) {
+    const int b0 = F->levUptr[l], b1 = F->levUptr[l + 1];
+    e = silu::launch_level(F->dS64, rowsU + b0, b1 - b0, R, gU, ldx, c, dinv, nullptr, nullptr, cap);
+  }
+  const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+  if (e == cudaSuccess) e = e2;
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  CK(e);
+  LevelGraph g;
+  g.R = R;
+  g.ldx = ldx;
+  g.col = col;
+  g.exec = exec;
+  g.kernels = F->nlevL + F->nlevU;
+  F->ws.graphs.push_back(g);
+  return exec;
+}
+
+// Direct application on columns [0, R): x (+)= Utilde^{-1} D^{-1} L^{-1} (b - A x).
+void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, bool x_zero) {
+  cudaStream_t s = F->ctx->stream;
+  const int n = (int)F->F.L.n;
+  double* y = F->ws.r.as<double>() + col;
+  double* c = F->ws.c.as<double>() + col;
+  const int gA = lanes_of(F->lanesA, F->autoA);
   if (x_zero)
     LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_scale(n, R, ldx, b, false, nullptr, y, false, s));
   else
     LAUNCH(F->ctx, SILU_K_RESIDUAL, sweep_launch(F, F->A->d, silu::MODE_D, R, gA, ldx, b, x, y, nullptr, nullptr, silu::EPI_STORE));
-  const int* rowsL = F->levLrows_d.as<int>();
-  const int* rowsU = F->levUrows_d.as<int>();
-  for (int l = 0; l < F->nlevL; ++l) {
-    const int b0 = F->levLptr[l], b1 = F->levLptr[l + 1];
-    LAUNCH(F->ctx, SILU_K_LEVEL, silu::launch_level(F->dL64, rowsL + b0, b1 - b0, R, gL, ldx, y, dinv, c, nullptr, s));
+  cudaGraphExec_t exec = level_graph(F, R, ldx, col);
+  {
+    ProfScope ps(F->ctx, SILU_K_LEVEL);
+    F->ctx->launches += F->nlevL + F->nlevU - 1;  // one count came from ProfScope
+    CK(cudaGraphLaunch(exec, s));
   }
-  for (int l = 0; l < F->nlevU; ++l) {
-    const int b0 = F->levUptr[l], b1 = F->levUptr[l + 1];
-    LAUNCH(F->ctx, SILU_K_LEVEL, silu::launch_level(F->dS64, rowsU + b0, b1 - b0, R, gU, ldx, c, dinv, nullptr, x_zero ? nullptr : x, s));
-  }
-  if (x_zero) LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_addx(n, R, ldx, c, false, nullptr, x, false, s));
+  LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_addx(n, R, ldx, c, false, nullptr, x, !x_zero, s));
 }
 
 int chunk_width(int left) { return left >= 4 ? 4 : (left >= 2 ? 2 : 1); }

@@ -49,18 +49,26 @@ struct DevCsr {
   // is used then)
   int4* tiles = nullptr;
   int ntiles = 0;
+  int tile_lanes = 1;  // lanes per row in the staged kernel (1, 2 or 4)
 };
 
-// Staged-sweep tile limits (rows and entries per warp tile).  The CSR arrays
-// of a tiled matrix are allocated with kCsrPad spare elements so that copies
-// rounded out to 16-byte boundaries stay inside the allocation.
-constexpr int kTileNnz = 384;
+// Staged-sweep tile limits (entries per warp tile; a tile has 32 / lanes
+// rows).  The CSR arrays of a tiled matrix are allocated with kCsrPad spare
+// elements so that copies rounded out to 16-byte boundaries stay inside the
+// allocation.
+constexpr int kTileNnz = 448;
 constexpr int kTileRows = 32;
 constexpr int kCsrPad = 8;
 
+// Lanes per row for the staged kernel from the mean row length: one lane per
+// row up to 16 entries, two up to 32, four beyond (each warp-wide FMA then
+// carries about as many useful entries as the longest row allows).
+int staged_lanes(const int64_t* rp, int64_t n);
+
 // Build the warp-tile descriptors of a CSR row pointer (host), four ints per
-// tile.  Returns false if a row has more than kTileNnz - 8 entries.
-bool make_tiles(const int64_t* rp, int64_t n, std::vector<int>& desc);
+// tile, for `lanes` lanes per row (32 / lanes rows per tile).  Returns false
+// if a row has more than kTileNnz - 8 entries.
+bool make_tiles(const int64_t* rp, int64_t n, int lanes, std::vector<int>& desc);
 
 // Device-side state shared by launches on one context.
 struct LaunchEnv {

@@ -28,12 +28,18 @@
 
 namespace silu {
 
-bool make_tiles(const int64_t* rp, int64_t n, std::vector<int>& desc) {
+int staged_lanes(const int64_t* rp, int64_t n) {
+  const double avg = n ? (double)rp[n] / (double)n : 0.0;
+  return avg <= 16.0 ? 1 : (avg <= 32.0 ? 2 : 4);
+}
+
+bool make_tiles(const int64_t* rp, int64_t n, int lanes, std::vector<int>& desc) {
   desc.clear();
+  const int rows = kTileRows / lanes;
   int64_t r0 = 0;
   while (r0 < n) {
     int64_t r1 = r0;
-    while (r1 < n && r1 - r0 < kTileRows && rp[r1 + 1] - rp[r0] <= kTileNnz - 8) ++r1;
+    while (r1 < n && r1 - r0 < rows && rp[r1 + 1] - rp[r0] <= kTileNnz - 8) ++r1;
     if (r1 == r0) return false;  // a single row does not fit
     desc.push_back((int)r0);
     desc.push_back((int)r1);
@@ -186,24 +192,29 @@ __device__ __forceinline__ void epilogue(int epi, int row, MT t, const VI* in, V
   }
 }
 
-// acc -/+= sum_k v[k] * in[col[k]] over one row held in shared memory.  All
-// gathers of a chunk of kChunk entries are issued before the first FMA (one
-// latency round per chunk); the FMA loop runs to the longest row of the warp
-// (a warp-uniform bound) and padded lanes multiply zeros, which leaves acc
-// exactly unchanged.  Cost: one FP64 FMA per entry of the warp's longest row.
+// acc -/+= sum v[p] * in[col[p]] over the entries p = sub, sub + G, ... of one
+// row held in shared memory (G lanes share a row; sub is this lane's place).
+// All gathers of a chunk of kChunk entries are issued before the first FMA
+// (one latency round per chunk); the FMA loop runs to the warp's largest
+// per-lane count (a warp-uniform bound) and padded slots multiply zeros,
+// which leaves acc exactly unchanged.  The G partial sums are then combined
+// with log2(G) shuffles.  Cost: one FP64 FMA per entry of the warp's longest
+// lane, plus log2(G) adds per row.
 constexpr int kChunk = 16;
 
-template <class MT, class VI, bool NEG>
-__device__ __forceinline__ MT row_accumulate(const MT* sv, const int* sc, int len, const VI* __restrict__ in,
-                                             MT acc, uint64_t keep) {
-  const int wmax = __reduce_max_sync(0xffffffffu, len);
+template <class MT, class VI, bool NEG, int G>
+__device__ __forceinline__ MT row_accumulate(const MT* sv, const int* sc, int len, int sub,
+                                             const VI* __restrict__ in, MT acc, uint64_t keep) {
+  const int cnt = len > sub ? (len - sub + G - 1) / G : 0;  // this lane's entries
+  const int wmax = __reduce_max_sync(0xffffffffu, cnt);
   for (int k0 = 0; k0 < wmax; k0 += kChunk) {
     MT v[kChunk], xv[kChunk];
 #pragma unroll
     for (int k = 0; k < kChunk; ++k) {
-      if (k0 + k < len) {
-        v[k] = sv[k0 + k];
-        xv[k] = (MT)ld_keep(in + sc[k0 + k], keep);
+      if (k0 + k < cnt) {
+        const int p = (k0 + k) * G + sub;
+        v[k] = sv[p];
+        xv[k] = (MT)ld_keep(in + sc[p], keep);
       } else {
         v[k] = MT(0);
         xv[k] = MT(0);
@@ -216,10 +227,12 @@ __device__ __forceinline__ MT row_accumulate(const MT* sv, const int* sc, int le
       acc = fma(NEG ? -v[k] : v[k], xv[k], acc);
     }
   }
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
   return acc;
 }
 
-template <class MT, class VI, class VO>
+template <class MT, class VI, class VO, int G>
 __global__ void __launch_bounds__(kStagedThreads, 1)
     k_sweep_staged(int ntiles, const int4* __restrict__ tiles, const int* __restrict__ rp, const int* __restrict__ ci,
                    const MT* __restrict__ va, const VI* __restrict__ c, const VI* __restrict__ in,
@@ -274,16 +287,18 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     const int q0 = r0 & ~3;
     const int a0 = p0 & ~(L::kValAlign - 1);
     const int c0 = p0 & ~3;
-    const int r = r0 + lane;
+    const int sub = lane % G;
+    const int r = r0 + lane / G;
     const bool act = r < r1;
     const int b = act ? sr[r - q0] : p0;
     const int len = act ? sr[r + 1 - q0] - b : 0;
-    MT acc = (act && c) ? (MT)ld_keep(c + r, keep) : MT(0);
+    // c enters once per row, through the lane that writes the result
+    MT acc = (act && c && sub == 0) ? (MT)ld_keep(c + r, keep) : MT(0);
     if (epi == EPI_SPMV)
-      acc = row_accumulate<MT, VI, false>(sv + (b - a0), sc + (b - c0), len, in, acc, keep);
+      acc = row_accumulate<MT, VI, false, G>(sv + (b - a0), sc + (b - c0), len, sub, in, acc, keep);
     else
-      acc = row_accumulate<MT, VI, true>(sv + (b - a0), sc + (b - c0), len, in, acc, keep);
-    if (act) {
+      acc = row_accumulate<MT, VI, true, G>(sv + (b - a0), sc + (b - c0), len, sub, in, acc, keep);
+    if (act && sub == 0) {
       if (epi == EPI_SPMV)
         st_keep(out + r, (VO)acc, keep);
       else
@@ -294,9 +309,9 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
   }
 }
 
-template <class MT, class VI, class VO>
-cudaError_t staged(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
-                   const double* dinv, double* x, int epi, cudaStream_t s) {
+template <class MT, class VI, class VO, int G>
+cudaError_t staged_g(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
+                     const double* dinv, double* x, int epi, cudaStream_t s) {
   using L = StageLayout<MT>;
   // the shared-memory opt-in is per function and per device
   static std::atomic<unsigned long long> attr_set{0};
@@ -306,17 +321,28 @@ cudaError_t staged(const DevCsr& T, const LaunchEnv& env, const void* c, const v
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(attr_set.load() & bit)) {
-    e = cudaFuncSetAttribute(k_sweep_staged<MT, VI, VO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_sweep_staged<MT, VI, VO, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set.fetch_or(bit);
   }
   if (T.ntiles == 0) return cudaSuccess;
   const int want = (T.ntiles + kWarps - 1) / kWarps;
   const int grid = want < env.sms ? want : env.sms;
-  k_sweep_staged<MT, VI, VO><<<grid, kStagedThreads, smem, s>>>(T.ntiles, T.tiles, T.rp, T.ci, (const MT*)T.va,
-                                                                 (const VI*)c, (const VI*)in, (VO*)out, dinv, x,
-                                                                 epi, env.err);
+  k_sweep_staged<MT, VI, VO, G><<<grid, kStagedThreads, smem, s>>>(T.ntiles, T.tiles, T.rp, T.ci, (const MT*)T.va,
+                                                                    (const VI*)c, (const VI*)in, (VO*)out, dinv, x,
+                                                                    epi, env.err);
   return cudaGetLastError();
+}
+
+template <class MT, class VI, class VO>
+cudaError_t staged(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
+                   const double* dinv, double* x, int epi, cudaStream_t s) {
+  switch (T.tile_lanes) {
+    case 1: return staged_g<MT, VI, VO, 1>(T, env, c, in, out, dinv, x, epi, s);
+    case 2: return staged_g<MT, VI, VO, 2>(T, env, c, in, out, dinv, x, epi, s);
+    case 4: return staged_g<MT, VI, VO, 4>(T, env, c, in, out, dinv, x, epi, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace

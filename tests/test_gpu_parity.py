@@ -237,3 +237,30 @@ def test_edge_cases(silu, ctx):
     with pytest.raises(silu.SiluError):
         silu.ilu_smooth(F, xb.float(), xb, 1, 2)
     assert silu.load().ilu_smooth(F.handle, 0, xb.data_ptr(), 1, 1, 1) == silu.ERR_INVALID_ARG
+
+
+def test_fp32_27pt_error_and_staged_lanes(silu, ctx):
+    """27-point rows (27 entries in A, 13 in each factor): the staged kernel runs
+    A with two lanes per row.  FP64 residual parity and the FP32 smoother's
+    error against the FP64 oracle (printed)."""
+    A = synth.hex27(40, 36, 30, seed=4)
+    n = len(A[0]) - 1
+    _, S = oracle_scaled(A, "ilu0", 0.0, 0)
+    b = synth.rhs(n, 1, seed=9)
+    x0 = synth.rhs(n, 1, seed=10)
+    F64 = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+    for variant in (1, 2):
+        F64.set_kernel(variant)
+        want = oracle.smooth(A, S, x0, b, 3, 3)
+        x = dev(x0.copy())
+        silu.ilu_smooth(F64, x, dev(b), 3, 3)
+        ctx.check()
+        assert relerr(host(x), want) < FP64_TOL
+    F32 = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0", prec=silu.FP32)
+    want = oracle.smooth(A, S, np.zeros((n, 1)), b, 3, 3)
+    x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+    silu.ilu_smooth(F32, x, dev(b), 3, 3)
+    ctx.check()
+    err = relerr(host(x), want)
+    print(f"27-point FP32 smoother (3,3) relative error vs FP64 oracle: {err:.3e}")
+    assert err < 1e-5
