@@ -357,6 +357,10 @@ def run_silu(args):
     if not args.no_solve and rank == 0:
         solve = solve_comparison(silu, ctx, torch, args.solve_edge)
 
+    batch = None
+    if not args.no_batch and rank == 0:
+        batch = batch_workload(silu, ctx, torch, args.batch_count)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gbs, reps, t = oracle_rate(A, b_np, args.cpu_budget)
@@ -387,6 +391,8 @@ def run_silu(args):
         }
         if solve:
             line["solve"] = solve
+        if batch:
+            line["batch"] = batch
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -449,6 +455,55 @@ def solve_comparison(silu, ctx, torch, edge: int):
     return out
 
 
+def batch_workload(silu, ctx, torch, count: int):
+    """512 independent cut-cell 7-point systems with edges uniform in [8, 64]
+    (512 to 262,144 rows each), FP32 ILU(0) factors packed block-diagonally:
+    setup time, autotuned launch shape, batched smoother GB/s (3+3 sweeps),
+    and the batched FGMRES(20) (one Krylov process per system) to 1e-8."""
+    import numpy as np
+    import synth
+    edges = synth.randint(3, 0, count, 8, 64)
+    systems = [synth.cutcell7(int(e), seed=10_000 + k) for k, e in enumerate(edges)]
+    nnzA = sum(len(A[1]) for A in systems)
+    t0 = time.perf_counter()
+    B = silu.Batch(ctx, systems, "ilu0", prec=silu.FP32)
+    setup_s = time.perf_counter() - t0
+    del systems
+    st = B.factors.stats()
+    n = B.n
+    choice, tune_ms = B.factors.autotune(3, 3)
+    b = torch.from_numpy(synth.rhs(n, 1, seed=3)[:, 0].copy()).cuda()
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        silu.silu_batch_smooth(B, x, b, 3, 3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record()
+    for _ in range(reps):
+        silu.silu_batch_smooth(B, x, b, 3, 3)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = apply_bytes(n, nnzA, st["nnz_L"], st["nnz_U"], 1, 4, 3, 3)
+    x.zero_()
+    silu.silu_batch_fgmres(B, x, b, tol=1e-8, restart=20, maxit=1, sweeps_L=3, sweeps_U=3)
+    x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stt, its, rel = silu.silu_batch_fgmres(B, x, b, tol=1e-8, restart=20, maxit=5000, sweeps_L=3, sweeps_U=3)
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t0
+    out = {"workload": f"{count} cut-cell 7-point systems, edges U[8,64], FP32 ILU(0)", "rows": n,
+           "nnz_A": nnzA, "setup_s": round(setup_s, 2), "autotune_choice": choice,
+           "smooth_3_3": {"ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1)},
+           "fgmres20_1e-8": {"seconds": round(solve_s, 4), "all_converged": stt == silu.OK,
+                             "iterations_max": int(np.max(its)), "iterations_mean": round(float(np.mean(its)), 1),
+                             "relres_max": float(np.max(rel))}}
+    B.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -457,6 +512,8 @@ def main():
     ap.add_argument("--impl", choices=["silu", "reference"], default="silu")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--solve-edge", type=int, default=256)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()

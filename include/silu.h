@@ -73,6 +73,7 @@ typedef enum { SILU_PRECOND_SWEEPS = 0, SILU_PRECOND_DIRECT = 1, SILU_PRECOND_NO
 typedef struct silu_ctx_s* silu_ctx;
 typedef struct silu_mat_s* silu_mat;
 typedef struct silu_ilu_s* silu_ilu;
+typedef struct silu_batch_s* silu_batch;
 
 /*
  * Create a context on CUDA device `device` whose work is ordered on
@@ -224,6 +225,51 @@ silu_status silu_ilu_set_lanes(silu_ilu F, int lanes_L, int lanes_U, int lanes_A
  * asynchronous copies; it needs rows of at most 4088 entries.
  */
 silu_status silu_ilu_set_kernel(silu_ilu F, int variant);
+
+/*
+ * Batches of independent systems (many pressure solves of uneven size).
+ *
+ * silu_batch_setup factors `count` host CSR systems (arrays as for
+ * silu_mat_create, system k with n[k] rows) independently and in parallel on
+ * the host, with the same kind / tau / fill / scale / prec for all, and
+ * packs them as one block-diagonal system on the device: the incomplete
+ * factors of a block-diagonal matrix are the block-diagonal of the systems'
+ * factors, so one sweep launch over the concatenation performs every
+ * system's sweep (Alg. ILUJac applied to each system).  Vectors of a batch
+ * are the systems' vectors concatenated: system k occupies rows
+ * [offsets[k], offsets[k+1]) (silu_batch_info).  Blocks.
+ */
+silu_status silu_batch_setup(silu_ctx ctx, int count, const int64_t* n, const int64_t* const* row_ptr,
+                             const int32_t* const* col_idx, const double* const* val, silu_kind kind, double tau,
+                             int fill, silu_scale scale, silu_prec prec, silu_batch* out);
+/* Count, offsets[count + 1], and the silu_ilu of the concatenated system
+ * (owned by the batch; usable with ilu_smooth, silu_ilu_set_kernel, ...). */
+silu_status silu_batch_info(silu_batch B, int* count, int64_t* offsets, silu_ilu* factors);
+/* One smoother application on every system (ilu_smooth on the concatenation). */
+silu_status silu_batch_smooth(silu_batch B, double* x, const double* b, int sweeps_L, int sweeps_U);
+/*
+ * Flexible GMRES(restart) on every system at once, each with its own Krylov
+ * basis, Hessenberg matrix, Givens rotations, iteration count and stopping
+ * test (Sec. 6, Eq. relres): dot products are reduced per system in a fixed
+ * order; a system stops updating once its estimate reaches tol * |b_k|, and
+ * every restart recomputes every true residual.  precond is
+ * SILU_PRECOND_SWEEPS or SILU_PRECOND_NONE.  Each inner iteration runs as a
+ * captured CUDA graph.  iters[count] and relres[count] (may be NULL) receive
+ * each system's inner iterations and true relative residual.  Blocks;
+ * SILU_ERR_NOT_CONVERGED if some system is still above tol at maxit.
+ */
+silu_status silu_batch_fgmres(silu_batch B, double* x, const double* b, double tol, int restart, int maxit,
+                              int sweeps_L, int sweeps_U, int precond, int* iters, double* relres);
+/*
+ * Autotuner: times one smoother application (sweeps_L, sweeps_U) with each
+ * candidate launch shape of the sweep kernels and keeps the fastest:
+ * rows per warp (one, two or four lanes per row in the staged kernel, or the
+ * lanes-per-row kernel with 2, 4 or 8 lanes) and gather width (8 or 16
+ * entries in flight per lane).  Writes the chosen candidate's index and its
+ * time per application.  Blocks.
+ */
+silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choice, double* ms);
+void silu_batch_destroy(silu_batch B);
 
 /*
  * Allocation-free smoother application (the paper has no counterpart; it

@@ -92,6 +92,12 @@ def load():
         "silu_ctx_check": (i32, [vp]),
         "silu_ilu_set_kernel": (i32, [vp, i32]),
         "silu_smooth_noalloc": (i32, [i32, vp, i64] + [vp] * 12 + [i32, i32]),
+        "silu_batch_setup": (i32, [vp, i32, vp, vp, vp, vp, i32, dbl, i32, i32, i32, pvp]),
+        "silu_batch_info": (i32, [vp, ctypes.POINTER(i32), vp, pvp]),
+        "silu_batch_smooth": (i32, [vp, vp, vp, i32, i32]),
+        "silu_batch_fgmres": (i32, [vp, vp, vp, dbl, i32, i32, i32, i32, i32, vp, vp]),
+        "silu_batch_destroy": (None, [vp]),
+        "silu_ilu_autotune": (i32, [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -107,7 +113,9 @@ def exported_symbols():
             "silu_mat_destroy", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
-            "silu_ctx_launch_count", "silu_ctx_check", "silu_ilu_set_kernel", "silu_smooth_noalloc"]
+            "silu_ctx_launch_count", "silu_ctx_check", "silu_ilu_set_kernel", "silu_smooth_noalloc",
+            "silu_batch_setup", "silu_batch_info", "silu_batch_smooth", "silu_batch_fgmres", "silu_batch_destroy",
+            "silu_ilu_autotune"]
 
 
 def _ptr(t) -> int:
@@ -231,9 +239,9 @@ class ILU:
         self.scale = scale
 
     def close(self):
-        if getattr(self, "handle", None):
+        if getattr(self, "handle", None) and not getattr(self, "_borrowed", False):
             load().silu_ilu_destroy(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __del__(self):
         try:
@@ -277,9 +285,89 @@ class ILU:
         """0 automatic, 1 lanes-per-row kernel, 2 staged (bulk-copy) kernel where it applies."""
         _check(self.ctx.handle, load().silu_ilu_set_kernel(self.handle, variant), "silu_ilu_set_kernel")
 
+    def autotune(self, sweeps_L: int = 3, sweeps_U: int = 3):
+        """Time the candidate launch shapes of the sweep kernels, keep the fastest; (choice, ms)."""
+        ch, ms = ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(self.ctx.handle, load().silu_ilu_autotune(self.handle, sweeps_L, sweeps_U, ctypes.byref(ch),
+                                                         ctypes.byref(ms)), "silu_ilu_autotune")
+        return ch.value, ms.value
+
     def set_lanes(self, lanes_L: int = 0, lanes_U: int = 0, lanes_A: int = 0):
         _check(self.ctx.handle, load().silu_ilu_set_lanes(self.handle, lanes_L, lanes_U, lanes_A),
                "silu_ilu_set_lanes")
+
+
+class Batch:
+    """silu_batch: independent systems factored in parallel, packed block-diagonally."""
+
+    def __init__(self, ctx: Context, systems, kind="ilu0", tau: float = 0.0, fill: int = 0,
+                 scale: int = SCALE_ROW, prec: int = FP64):
+        kind = KINDS[kind] if isinstance(kind, str) else kind
+        arrs = []
+        for rp, ci, va in systems:
+            arrs.append((np.ascontiguousarray(rp, dtype=np.int64), np.ascontiguousarray(ci, dtype=np.int32),
+                         np.ascontiguousarray(va, dtype=np.float64)))
+        cnt = len(arrs)
+        n = np.array([len(a[0]) - 1 for a in arrs], dtype=np.int64)
+        P = ctypes.c_void_p * cnt
+        rps = P(*[a[0].ctypes.data for a in arrs])
+        cis = P(*[a[1].ctypes.data for a in arrs])
+        vas = P(*[a[2].ctypes.data for a in arrs])
+        h = ctypes.c_void_p()
+        st = load().silu_batch_setup(ctx.handle, cnt, n.ctypes.data, ctypes.addressof(rps), ctypes.addressof(cis),
+                                     ctypes.addressof(vas), kind, float(tau), int(fill), scale, prec, ctypes.byref(h))
+        _check(ctx.handle, st, "silu_batch_setup")
+        self.handle = h.value
+        self.ctx = ctx
+        self.count = cnt
+        self.offsets = np.empty(cnt + 1, dtype=np.int64)
+        fh = ctypes.c_void_p()
+        c = ctypes.c_int(0)
+        _check(ctx.handle, load().silu_batch_info(self.handle, ctypes.byref(c), self.offsets.ctypes.data,
+                                                  ctypes.byref(fh)), "silu_batch_info")
+        self.n = int(self.offsets[-1])
+        # a non-owning view of the concatenated factors (owned by the batch)
+        self.factors = ILU.__new__(ILU)
+        self.factors.handle = fh.value
+        self.factors.ctx = ctx
+        self.factors.n = self.n
+        self.factors.prec = prec
+        self.factors.scale = scale
+        self.factors.A = None
+        self.factors._borrowed = True
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.factors.handle = None
+            load().silu_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def silu_batch_smooth(B: Batch, x, b, sweeps_L: int, sweeps_U: int) -> None:
+    _check_vec(x, B.n, 1)
+    _check_vec(b, B.n, 1)
+    _check(B.ctx.handle, load().silu_batch_smooth(B.handle, _ptr(x), _ptr(b), sweeps_L, sweeps_U),
+           "silu_batch_smooth")
+
+
+def silu_batch_fgmres(B: Batch, x, b, tol: float = 1e-8, restart: int = 20, maxit: int = 1000, sweeps_L: int = 3,
+                      sweeps_U: int = 3, precond: int = PRECOND_SWEEPS):
+    """Per-system FGMRES on the whole batch; returns (status, iterations[count], relres[count])."""
+    _check_vec(x, B.n, 1)
+    _check_vec(b, B.n, 1)
+    its = np.zeros(B.count, dtype=np.int32)
+    rel = np.zeros(B.count, dtype=np.float64)
+    st = load().silu_batch_fgmres(B.handle, _ptr(x), _ptr(b), float(tol), int(restart), int(maxit), int(sweeps_L),
+                                  int(sweeps_U), int(precond), its.ctypes.data, rel.ctypes.data)
+    if st not in (OK, ERR_NOT_CONVERGED):
+        _check(B.ctx.handle, st, "silu_batch_fgmres")
+    return st, its, rel
 
 
 # ------------------------------------------------------- C-named functions

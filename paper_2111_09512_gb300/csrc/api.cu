@@ -1,198 +1,11 @@
 // C ABI of libsilu (declared in include/silu.h): handles, host setup and
 // the stream-ordered orchestration of the device kernels.
-#include <cuda_runtime.h>
+#include "internal.h"
 
-#include <algorithm>
-#include <cmath>
-#include <cstring>
-#include <new>
-#include <string>
-#include <vector>
+using namespace silu;
 
-#include "device.cuh"
-#include "host_factor.h"
-#include "silu.h"
+namespace silu {
 
-using silu::DevCsr;
-
-namespace {
-
-// Owning device buffer.
-struct DBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-  DBuf() = default;
-  DBuf(const DBuf&) = delete;
-  DBuf& operator=(const DBuf&) = delete;
-  ~DBuf() { release(); }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-  }
-  cudaError_t ensure(size_t b) {
-    if (b <= bytes && p) return cudaSuccess;
-    release();
-    if (b == 0) b = 16;
-    cudaError_t e = cudaMalloc(&p, b);
-    if (e != cudaSuccess) {
-      p = nullptr;
-      return e;
-    }
-    bytes = b;
-    return cudaSuccess;
-  }
-  template <class T>
-  T* as() const {
-    return (T*)p;
-  }
-};
-
-}  // namespace
-
-struct silu_ctx_s {
-  int device = -1;
-  cudaStream_t stream = nullptr;
-  std::string err;
-  double* pinned = nullptr;  // small host buffer for scalar read-backs
-  int64_t launches = 0;      // kernels launched on this context
-  silu::LaunchEnv env;       // SM count and device error word
-  // event timing of launches (silu_ctx_profile)
-  bool profiling = false;
-  std::vector<cudaEvent_t> events;  // pool; records use pairs (2k, 2k+1)
-  std::vector<int> rec_class;       // class of record k
-  size_t nrec = 0;
-};
-
-struct silu_mat_s {
-  silu_ctx ctx = nullptr;
-  silu::Csr A;
-  DBuf rp, ci, va, tiles;
-  DevCsr d;
-};
-
-// A captured level-scheduled solve on the workspace vectors of one column block.
-struct LevelGraph {
-  int R = 0, ldx = 0;
-  size_t col = 0;
-  cudaGraphExec_t exec = nullptr;
-  int kernels = 0;
-};
-
-struct Workspace {
-  size_t vec_bytes = 0;  // per buffer
-  DBuf r, c, p0, p1;
-  std::vector<LevelGraph> graphs;  // valid while r and c keep their addresses
-  ~Workspace() { drop_graphs(); }
-  void drop_graphs() {
-    for (LevelGraph& g : graphs)
-      if (g.exec) cudaGraphExecDestroy(g.exec);
-    graphs.clear();
-  }
-  int restart = 0;
-  DBuf V, Z, w, H, cs, sn, g, yk, part0, part1, scal;
-};
-
-struct silu_ilu_s {
-  silu_ctx ctx = nullptr;
-  silu_mat A = nullptr;
-  silu_kind kind = SILU_ILU0;
-  silu_scale scale = SILU_SCALE_ROW;
-  silu_prec prec = SILU_FP64;
-  double tau = 0.0;
-  int fill = 0;
-  silu::Factors F;
-  silu::Csr Us;
-  std::vector<double> dinv;
-  std::vector<int32_t> levL, levU, levLptr, levLrows, levUptr, levUrows;
-  int32_t nlevL = 0, nlevU = 0;
-  // device: sweep factors
-  DBuf L_rp, L_ci, L_va, L_tiles, U_rp, U_ci, U_va, U_tiles, d_dinv;
-  DevCsr dL, dU;
-  // device: FP64 L_s and Utilde_s for the direct path (aliases of dL/dU when possible)
-  DBuf L64_va, S_rp, S_ci, S_va, S_tiles, levLrows_d, levUrows_d;
-  DevCsr dL64, dS64;
-  bool direct_ready = false;
-  int lanesL = 0, lanesU = 0, lanesA = 0;
-  int variant = 0;  // 0 auto, 1 plain lanes-per-row kernel, 2 staged kernel where possible
-  int autoL = 4, autoU = 4, autoA = 8;
-  Workspace ws;
-};
-
-namespace {
-
-silu_status set_err(silu_ctx ctx, silu_status st, const std::string& msg) {
-  if (ctx) ctx->err = msg;
-  return st;
-}
-
-silu_status cuda_err(silu_ctx ctx, cudaError_t e, const char* what) {
-  return set_err(ctx, e == cudaErrorMemoryAllocation ? SILU_ERR_OOM : SILU_ERR_CUDA,
-                 std::string(what) + ": " + cudaGetErrorString(e));
-}
-
-struct CudaFail {
-  cudaError_t e;
-  const char* what;
-};
-
-#define CK(call)                                      \
-  do {                                                \
-    cudaError_t e_ = (call);                          \
-    if (e_ != cudaSuccess) throw CudaFail{e_, #call}; \
-  } while (0)
-
-// Counts a kernel launch and, while profiling, brackets it with events.
-struct ProfScope {
-  silu_ctx ctx;
-  size_t k = (size_t)-1;
-  ProfScope(silu_ctx c, int cls) : ctx(c) {
-    ctx->launches++;
-    if (!ctx->profiling) return;
-    k = ctx->nrec;
-    if (ctx->events.size() < 2 * (k + 1)) {
-      for (int t = 0; t < 2; ++t) {
-        cudaEvent_t ev;
-        if (cudaEventCreate(&ev) != cudaSuccess) {
-          k = (size_t)-1;
-          return;
-        }
-        ctx->events.push_back(ev);
-      }
-    }
-    if (ctx->rec_class.size() <= k) ctx->rec_class.resize(k + 1);
-    ctx->rec_class[k] = cls;
-    ctx->nrec = k + 1;
-    cudaEventRecord(ctx->events[2 * k], ctx->stream);
-  }
-  ~ProfScope() {
-    if (k != (size_t)-1) cudaEventRecord(ctx->events[2 * k + 1], ctx->stream);
-  }
-};
-
-#define LAUNCH(ctx, cls, call)        \
-  do {                                \
-    ProfScope ps_((ctx), (cls));      \
-    CK(call);                         \
-  } while (0)
-
-int pick_lanes(const silu::Csr& T) {
-  const double avg = T.n ? (double)T.nnz() / (double)T.n : 0.0;
-  int g = 1;
-  while (g < 32 && g < avg) g <<= 1;
-  return std::max(2, g);
-}
-
-template <class T>
-cudaError_t upload(DBuf& b, const T* src, size_t count, cudaStream_t s) {
-  cudaError_t e = b.ensure(sizeof(T) * std::max<size_t>(count, 1));
-  if (e != cudaSuccess) return e;
-  if (count == 0) return cudaSuccess;
-  return cudaMemcpyAsync(b.p, src, sizeof(T) * count, cudaMemcpyHostToDevice, s);
-}
-
-// Upload CSR (int64 row pointers narrowed to int32) with values as double or
-// float.  Arrays get kCsrPad spare (zeroed) elements for the staged kernel's
 // 16-byte-rounded copies, and the row tiles of the staged kernel are built.
 cudaError_t upload_csr(const silu::Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& va, DBuf& tiles, DevCsr& d,
                        cudaStream_t s) {
@@ -309,7 +122,6 @@ cudaError_t ensure_direct(silu_ilu F) {
   return e;
 }
 
-int lanes_of(int fixed, int autov) { return fixed > 0 ? fixed : autov; }
 
 // One sweep-shaped launch: the staged kernel for a single right-hand side
 // when the matrix has a tile partition (and the variant allows it), else the
@@ -532,7 +344,35 @@ void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
 
 int chunk_width(int left) { return left >= 4 ? 4 : (left >= 2 ? 2 : 1); }
 
-}  // namespace
+
+silu_status finish_setup(silu_ilu F) {
+  silu_ctx ctx = F->ctx;
+  std::string msg;
+  int st = silu::row_scale(F->F.U, F->Us, F->dinv, msg);
+  if (st != silu::H_OK) return set_err(ctx, (silu_status)st, msg);
+  F->nlevL = silu::levels_lower(F->F.L, F->levL);
+  F->nlevU = silu::levels_upper(F->F.U, true, F->levU);
+  silu::group_levels(F->levL, F->nlevL, F->levLptr, F->levLrows);
+  silu::group_levels(F->levU, F->nlevU, F->levUptr, F->levUrows);
+  const silu::Csr& Ut = (F->scale == SILU_SCALE_ROW) ? F->Us : F->F.U;
+  F->autoL = pick_lanes(F->F.L);
+  F->autoU = pick_lanes(Ut);
+  F->autoA = pick_lanes(F->A->A);
+  if (ctx->device >= 0) {
+    silu_status ds = device_ok(ctx);
+    if (ds != SILU_OK) return ds;
+    cudaStream_t s = ctx->stream;
+    const bool f32 = F->prec == SILU_FP32;
+    cudaError_t e = upload_csr(F->F.L, f32, F->L_rp, F->L_ci, F->L_va, F->L_tiles, F->dL, s);
+    if (e == cudaSuccess) e = upload_csr(Ut, f32, F->U_rp, F->U_ci, F->U_va, F->U_tiles, F->dU, s);
+    if (e == cudaSuccess) e = upload(F->d_dinv, F->dinv.data(), F->dinv.size(), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "upload of the factors");
+  }
+  return SILU_OK;
+}
+
+}  // namespace silu
 
 // ===========================================================================
 extern "C" {
@@ -558,6 +398,7 @@ silu_status silu_ctx_create(int device, void* cuda_stream, silu_ctx* out) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->env.sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->env.err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->env.err, 0, sizeof(int));
+    if (e == cudaSuccess) e = silu::staged_prepare();
     if (e != cudaSuccess) {
       delete c;
       return SILU_ERR_CUDA;
@@ -621,6 +462,95 @@ silu_status silu_ctx_check(silu_ctx ctx) {
   if (e != cudaSuccess) return cuda_err(ctx, e, "error word read-back");
   if (flag) return set_err(ctx, SILU_ERR_TIMEOUT, "a bounded device wait gave up; results of the affected calls are invalid");
   return SILU_OK;
+}
+
+namespace {
+
+// Rebuild the staged-kernel tiles of T (host CSR h) for g lanes per row.
+cudaError_t retile(const Csr& h, DBuf& tiles, DevCsr& T, int g, cudaStream_t s) {
+  std::vector<int> tl;
+  if (!silu::make_tiles(h.rp.data(), h.n, g, tl)) return cudaSuccess;  // keeps the current tiles
+  cudaError_t e = upload(tiles, tl.data(), tl.size(), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) {
+    T.tiles = tiles.as<int4>();
+    T.ntiles = (int)(tl.size() / 4);
+    T.tile_lanes = g;
+  }
+  return e;
+}
+
+struct TuneCandidate {
+  int variant, lanes, chunk;  // variant 2: staged (lanes = lanes per row, 0 = automatic); 1: lanes-per-row kernel
+};
+
+const TuneCandidate kTune[] = {{2, 0, 16}, {2, 0, 8}, {2, 1, 16}, {2, 2, 16}, {2, 4, 16},
+                               {1, 2, 16}, {1, 4, 16}, {1, 8, 16}};
+
+}  // namespace
+
+silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choice, double* ms_out) {
+  if (!F || sweeps_L < 0 || sweeps_U < 0) return SILU_ERR_INVALID_ARG;
+  silu_ctx ctx = F->ctx;
+  silu_status ds = device_ok(ctx);
+  if (ds != SILU_OK) return ds;
+  const size_t n = (size_t)F->F.L.n;
+  if (n == 0) return SILU_OK;
+  cudaStream_t s = ctx->stream;
+  const Csr& Ut = (F->scale == SILU_SCALE_ROW) ? F->Us : F->F.U;
+  const int autoL = silu::staged_lanes(F->F.L.rp.data(), F->F.L.n);
+  const int autoU = silu::staged_lanes(Ut.rp.data(), Ut.n);
+  DBuf x, b;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best = 0;
+  double best_ms = 1e300;
+  try {
+    CK(x.ensure(sizeof(double) * n));
+    CK(b.ensure(sizeof(double) * n));
+    CK(cudaMemsetAsync(b.p, 0, sizeof(double) * n, s));
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(ensure_vectors(F, 1));
+    const int ncand = (int)(sizeof(kTune) / sizeof(kTune[0]));
+    auto apply = [&](const TuneCandidate& c) {
+      F->variant = c.variant;
+      if (c.variant == 1) {
+        F->lanesL = F->lanesU = c.lanes;
+      } else {
+        F->lanesL = F->lanesU = 0;
+        CK(retile(F->F.L, F->L_tiles, F->dL, c.lanes ? c.lanes : autoL, s));
+        CK(retile(Ut, F->U_tiles, F->dU, c.lanes ? c.lanes : autoU, s));
+        F->dL.chunk = F->dU.chunk = c.chunk;
+      }
+    };
+    for (int k = 0; k < ncand; ++k) {
+      apply(kTune[k]);
+      CK(cudaMemsetAsync(x.p, 0, sizeof(double) * n, s));
+      smooth_chunk(F, x.as<double>(), b.as<double>(), 1, 1, 0, sweeps_L, sweeps_U, false);
+      CK(cudaEventRecord(e0, s));
+      const int reps = 5;
+      for (int r = 0; r < reps; ++r) smooth_chunk(F, x.as<double>(), b.as<double>(), 1, 1, 0, sweeps_L, sweeps_U, false);
+      CK(cudaEventRecord(e1, s));
+      CK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, e0, e1));
+      const double per = (double)t / reps;
+      if (per < best_ms) {
+        best_ms = per;
+        best = k;
+      }
+    }
+    apply(kTune[best]);
+  } catch (const CudaFail& f) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return cuda_err(ctx, f.e, f.what);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (choice) *choice = best;
+  if (ms_out) *ms_out = best_ms;
+  return silu_ctx_check(ctx);
 }
 
 silu_status silu_ilu_set_kernel(silu_ilu F, int variant) {
@@ -699,35 +629,14 @@ silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int 
       st = silu::factor_iluk(A->A, fill, F->F, msg);
     else
       st = silu::factor_ilut(A->A, tau, fill, F->F, msg);
-    if (st == silu::H_OK) st = silu::row_scale(F->F.U, F->Us, F->dinv, msg);
     if (st != silu::H_OK) {
       delete F;
       return set_err(ctx, (silu_status)st, msg);
     }
-    F->nlevL = silu::levels_lower(F->F.L, F->levL);
-    F->nlevU = silu::levels_upper(F->F.U, true, F->levU);
-    silu::group_levels(F->levL, F->nlevL, F->levLptr, F->levLrows);
-    silu::group_levels(F->levU, F->nlevU, F->levUptr, F->levUrows);
-    const silu::Csr& Ut = (scale == SILU_SCALE_ROW) ? F->Us : F->F.U;
-    F->autoL = pick_lanes(F->F.L);
-    F->autoU = pick_lanes(Ut);
-    F->autoA = pick_lanes(A->A);
-    if (ctx->device >= 0) {
-      silu_status ds = device_ok(ctx);
-      if (ds != SILU_OK) {
-        delete F;
-        return ds;
-      }
-      cudaStream_t s = ctx->stream;
-      const bool f32 = prec == SILU_FP32;
-      cudaError_t e = upload_csr(F->F.L, f32, F->L_rp, F->L_ci, F->L_va, F->L_tiles, F->dL, s);
-      if (e == cudaSuccess) e = upload_csr(Ut, f32, F->U_rp, F->U_ci, F->U_va, F->U_tiles, F->dU, s);
-      if (e == cudaSuccess) e = upload(F->d_dinv, F->dinv.data(), F->dinv.size(), s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) {
-        delete F;
-        return cuda_err(ctx, e, "upload of the factors");
-      }
+    const silu_status fs = finish_setup(F);
+    if (fs != SILU_OK) {
+      delete F;
+      return fs;
     }
   } catch (const std::bad_alloc&) {
     delete F;

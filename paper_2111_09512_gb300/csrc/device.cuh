@@ -50,6 +50,7 @@ struct DevCsr {
   int4* tiles = nullptr;
   int ntiles = 0;
   int tile_lanes = 1;  // lanes per row in the staged kernel (1, 2 or 4)
+  int chunk = 16;      // entries gathered per lane before the FMAs (8 or 16)
 };
 
 // Staged-sweep tile limits (entries per warp tile; a tile has 32 / lanes
@@ -86,6 +87,9 @@ cudaError_t launch_sweep(const DevCsr& T, Mode mode, int R, int lanes, int ldx, 
 // row tiles of T into shared memory with bulk asynchronous copies.
 cudaError_t launch_sweep_staged(const DevCsr& T, Mode mode, const LaunchEnv& env, const void* c, const void* in,
                                 void* out, const double* dinv, double* x, int epi, cudaStream_t s);
+// Opt every staged-kernel instantiation into its shared-memory size on the
+// current device (done once per context, before any stream capture).
+cudaError_t staged_prepare();
 
 // Level-scheduled substitution over the rows listed in rows[0..nrows).
 //  lower:  y_i -= sum_j T_ij y_j ; if c_out: c_out_i = dinv_i y_i

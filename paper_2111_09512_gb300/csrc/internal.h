@@ -1,0 +1,221 @@
+// Internal declarations shared by the C-ABI translation units of libsilu
+// (api.cu, batch.cu): handle structures, device buffers, error plumbing,
+// launch accounting and the smoother orchestration helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "host_factor.h"
+#include "silu.h"
+
+namespace silu {
+
+// Owning device buffer.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  cudaError_t ensure(size_t b) {
+    if (b <= bytes && p) return cudaSuccess;
+    release();
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    bytes = b;
+    return cudaSuccess;
+  }
+  template <class T>
+  T* as() const {
+    return (T*)p;
+  }
+};
+
+
+}  // namespace silu
+
+using silu::DBuf;
+using silu::DevCsr;
+
+struct silu_ctx_s {
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  double* pinned = nullptr;  // small host buffer for scalar read-backs
+  int64_t launches = 0;      // kernels launched on this context
+  silu::LaunchEnv env;       // SM count and device error word
+  // event timing of launches (silu_ctx_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;  // pool; records use pairs (2k, 2k+1)
+  std::vector<int> rec_class;       // class of record k
+  size_t nrec = 0;
+};
+
+struct silu_mat_s {
+  silu_ctx ctx = nullptr;
+  silu::Csr A;
+  DBuf rp, ci, va, tiles;
+  DevCsr d;
+};
+
+// A captured level-scheduled solve on the workspace vectors of one column block.
+struct LevelGraph {
+  int R = 0, ldx = 0;
+  size_t col = 0;
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;
+};
+
+struct Workspace {
+  size_t vec_bytes = 0;  // per buffer
+  DBuf r, c, p0, p1;
+  std::vector<LevelGraph> graphs;  // valid while r and c keep their addresses
+  ~Workspace() { drop_graphs(); }
+  void drop_graphs() {
+    for (LevelGraph& g : graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
+  int restart = 0;
+  DBuf V, Z, w, H, cs, sn, g, yk, part0, part1, scal;
+};
+
+struct silu_ilu_s {
+  silu_ctx ctx = nullptr;
+  silu_mat A = nullptr;
+  silu_kind kind = SILU_ILU0;
+  silu_scale scale = SILU_SCALE_ROW;
+  silu_prec prec = SILU_FP64;
+  double tau = 0.0;
+  int fill = 0;
+  silu::Factors F;
+  silu::Csr Us;
+  std::vector<double> dinv;
+  std::vector<int32_t> levL, levU, levLptr, levLrows, levUptr, levUrows;
+  int32_t nlevL = 0, nlevU = 0;
+  // device: sweep factors
+  DBuf L_rp, L_ci, L_va, L_tiles, U_rp, U_ci, U_va, U_tiles, d_dinv;
+  DevCsr dL, dU;
+  // device: FP64 L_s and Utilde_s for the direct path (aliases of dL/dU when possible)
+  DBuf L64_va, S_rp, S_ci, S_va, S_tiles, levLrows_d, levUrows_d;
+  DevCsr dL64, dS64;
+  bool direct_ready = false;
+  int lanesL = 0, lanesU = 0, lanesA = 0;
+  int variant = 0;  // 0 auto, 1 plain lanes-per-row kernel, 2 staged kernel where possible
+  int autoL = 4, autoU = 4, autoA = 8;
+  Workspace ws;
+};
+
+
+namespace silu {
+
+inline silu_status set_err(silu_ctx ctx, silu_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+inline silu_status cuda_err(silu_ctx ctx, cudaError_t e, const char* what) {
+  return set_err(ctx, e == cudaErrorMemoryAllocation ? SILU_ERR_OOM : SILU_ERR_CUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct CudaFail {
+  cudaError_t e;
+  const char* what;
+};
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) throw CudaFail{e_, #call}; \
+  } while (0)
+
+// Counts a kernel launch and, while profiling, brackets it with events.
+struct ProfScope {
+  silu_ctx ctx;
+  size_t k = (size_t)-1;
+  ProfScope(silu_ctx c, int cls) : ctx(c) {
+    ctx->launches++;
+    if (!ctx->profiling) return;
+    k = ctx->nrec;
+    if (ctx->events.size() < 2 * (k + 1)) {
+      for (int t = 0; t < 2; ++t) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) {
+          k = (size_t)-1;
+          return;
+        }
+        ctx->events.push_back(ev);
+      }
+    }
+    if (ctx->rec_class.size() <= k) ctx->rec_class.resize(k + 1);
+    ctx->rec_class[k] = cls;
+    ctx->nrec = k + 1;
+    cudaEventRecord(ctx->events[2 * k], ctx->stream);
+  }
+  ~ProfScope() {
+    if (k != (size_t)-1) cudaEventRecord(ctx->events[2 * k + 1], ctx->stream);
+  }
+};
+
+#define LAUNCH(ctx, cls, call)        \
+  do {                                \
+    ProfScope ps_((ctx), (cls));      \
+    CK(call);                         \
+  } while (0)
+
+
+inline int pick_lanes(const silu::Csr& T) {
+  const double avg = T.n ? (double)T.nnz() / (double)T.n : 0.0;
+  int g = 1;
+  while (g < 32 && g < avg) g <<= 1;
+  return std::max(2, g);
+}
+
+template <class T>
+cudaError_t upload(DBuf& b, const T* src, size_t count, cudaStream_t s) {
+  cudaError_t e = b.ensure(sizeof(T) * std::max<size_t>(count, 1));
+  if (e != cudaSuccess) return e;
+  if (count == 0) return cudaSuccess;
+  return cudaMemcpyAsync(b.p, src, sizeof(T) * count, cudaMemcpyHostToDevice, s);
+}
+
+// Upload CSR (int64 row pointers narrowed to int32) with values as double or
+// float.  Arrays get kCsrPad spare (zeroed) elements for the staged kernel's
+
+cudaError_t upload_csr(const Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& va, DBuf& tiles, DevCsr& d,
+                       cudaStream_t s);
+silu_status device_ok(silu_ctx ctx);
+cudaError_t ensure_vectors(silu_ilu F, int nrhs);
+cudaError_t ensure_krylov(silu_ilu F, int m);
+cudaError_t ensure_direct(silu_ilu F);
+inline int lanes_of(int fixed, int autov) { return fixed > 0 ? fixed : autov; }
+cudaError_t sweep_launch(silu_ilu F, const DevCsr& T, Mode mode, int R, int lanes, int ldx, const void* c,
+                         const void* in, void* out, const double* dinv, double* x, int epi);
+// One smoother application on columns [0, R) (leading dimension ldx, workspace
+// column offset col); x_zero: zero initial guess, x is written, not updated.
+void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, int mL, int mU, bool x_zero);
+// The same update with level-scheduled exact solves.
+void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, bool x_zero);
+// Scale, level sets, launch shapes and upload for F->F already factored.
+silu_status finish_setup(silu_ilu F);
+
+}  // namespace silu

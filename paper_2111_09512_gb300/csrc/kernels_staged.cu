@@ -20,7 +20,6 @@
 // they stay resident in L2 from one sweep to the next.
 #include <cuda_runtime.h>
 
-#include <atomic>
 #include <cstdint>
 #include <vector>
 
@@ -200,9 +199,7 @@ __device__ __forceinline__ void epilogue(int epi, int row, MT t, const VI* in, V
 // which leaves acc exactly unchanged.  The G partial sums are then combined
 // with log2(G) shuffles.  Cost: one FP64 FMA per entry of the warp's longest
 // lane, plus log2(G) adds per row.
-constexpr int kChunk = 16;
-
-template <class MT, class VI, bool NEG, int G>
+template <class MT, class VI, bool NEG, int G, int kChunk>
 __device__ __forceinline__ MT row_accumulate(const MT* sv, const int* sc, int len, int sub,
                                              const VI* __restrict__ in, MT acc, uint64_t keep) {
   const int cnt = len > sub ? (len - sub + G - 1) / G : 0;  // this lane's entries
@@ -232,7 +229,7 @@ __device__ __forceinline__ MT row_accumulate(const MT* sv, const int* sc, int le
   return acc;
 }
 
-template <class MT, class VI, class VO, int G>
+template <class MT, class VI, class VO, int G, int CH>
 __global__ void __launch_bounds__(kStagedThreads, 1)
     k_sweep_staged(int ntiles, const int4* __restrict__ tiles, const int* __restrict__ rp, const int* __restrict__ ci,
                    const MT* __restrict__ va, const VI* __restrict__ c, const VI* __restrict__ in,
@@ -295,9 +292,9 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     // c enters once per row, through the lane that writes the result
     MT acc = (act && c && sub == 0) ? (MT)ld_keep(c + r, keep) : MT(0);
     if (epi == EPI_SPMV)
-      acc = row_accumulate<MT, VI, false, G>(sv + (b - a0), sc + (b - c0), len, sub, in, acc, keep);
+      acc = row_accumulate<MT, VI, false, G, CH>(sv + (b - a0), sc + (b - c0), len, sub, in, acc, keep);
     else
-      acc = row_accumulate<MT, VI, true, G>(sv + (b - a0), sc + (b - c0), len, sub, in, acc, keep);
+      acc = row_accumulate<MT, VI, true, G, CH>(sv + (b - a0), sc + (b - c0), len, sub, in, acc, keep);
     if (act && sub == 0) {
       if (epi == EPI_SPMV)
         st_keep(out + r, (VO)acc, keep);
@@ -309,43 +306,65 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
   }
 }
 
-template <class MT, class VI, class VO, int G>
+template <class MT, class VI, class VO, int G, int CH>
+cudaError_t staged_attr() {
+  using L = StageLayout<MT>;
+  const size_t smem = (size_t)kWarps * kWarpStages * L::kBytes;
+  return cudaFuncSetAttribute(k_sweep_staged<MT, VI, VO, G, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+template <class MT, class VI, class VO, int G, int CH>
 cudaError_t staged_g(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
                      const double* dinv, double* x, int epi, cudaStream_t s) {
   using L = StageLayout<MT>;
-  // the shared-memory opt-in is per function and per device
-  static std::atomic<unsigned long long> attr_set{0};
   const size_t smem = (size_t)kWarps * kWarpStages * L::kBytes;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  const unsigned long long bit = 1ull << (dev & 63);
-  if (!(attr_set.load() & bit)) {
-    e = cudaFuncSetAttribute(k_sweep_staged<MT, VI, VO, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set.fetch_or(bit);
-  }
   if (T.ntiles == 0) return cudaSuccess;
   const int want = (T.ntiles + kWarps - 1) / kWarps;
   const int grid = want < env.sms ? want : env.sms;
-  k_sweep_staged<MT, VI, VO, G><<<grid, kStagedThreads, smem, s>>>(T.ntiles, T.tiles, T.rp, T.ci, (const MT*)T.va,
-                                                                    (const VI*)c, (const VI*)in, (VO*)out, dinv, x,
-                                                                    epi, env.err);
+  k_sweep_staged<MT, VI, VO, G, CH><<<grid, kStagedThreads, smem, s>>>(
+      T.ntiles, T.tiles, T.rp, T.ci, (const MT*)T.va, (const VI*)c, (const VI*)in, (VO*)out, dinv, x, epi, env.err);
   return cudaGetLastError();
+}
+
+template <class MT, class VI, class VO, int G>
+cudaError_t staged_c(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
+                     const double* dinv, double* x, int epi, cudaStream_t s) {
+  if (T.chunk == 8) return staged_g<MT, VI, VO, G, 8>(T, env, c, in, out, dinv, x, epi, s);
+  return staged_g<MT, VI, VO, G, 16>(T, env, c, in, out, dinv, x, epi, s);
 }
 
 template <class MT, class VI, class VO>
 cudaError_t staged(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
                    const double* dinv, double* x, int epi, cudaStream_t s) {
   switch (T.tile_lanes) {
-    case 1: return staged_g<MT, VI, VO, 1>(T, env, c, in, out, dinv, x, epi, s);
-    case 2: return staged_g<MT, VI, VO, 2>(T, env, c, in, out, dinv, x, epi, s);
-    case 4: return staged_g<MT, VI, VO, 4>(T, env, c, in, out, dinv, x, epi, s);
+    case 1: return staged_c<MT, VI, VO, 1>(T, env, c, in, out, dinv, x, epi, s);
+    case 2: return staged_c<MT, VI, VO, 2>(T, env, c, in, out, dinv, x, epi, s);
+    case 4: return staged_c<MT, VI, VO, 4>(T, env, c, in, out, dinv, x, epi, s);
   }
   return cudaErrorInvalidValue;
 }
 
+template <class MT, class VI, class VO>
+cudaError_t prepare_mode() {
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, 1, 8>();
+  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, 1, 16>();
+  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, 2, 8>();
+  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, 2, 16>();
+  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, 4, 8>();
+  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, 4, 16>();
+  return e;
+}
+
 }  // namespace
+
+cudaError_t staged_prepare() {
+  cudaError_t e = prepare_mode<double, double, double>();
+  if (e == cudaSuccess) e = prepare_mode<float, float, float>();
+  if (e == cudaSuccess) e = prepare_mode<double, double, float>();
+  return e;
+}
 
 cudaError_t launch_sweep_staged(const DevCsr& T, Mode mode, const LaunchEnv& env, const void* c, const void* in,
                                 void* out, const double* dinv, double* x, int epi, cudaStream_t s) {

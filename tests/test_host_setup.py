@@ -135,3 +135,27 @@ def test_refactor_reuses_the_pattern(ctx):
     F = silu.ILU(silu.Matrix(ctx, *A), "ilut", tau=1e-3, fill=5)
     with pytest.raises(silu.SiluError):
         silu.ilu_refactor(F, A2[2])
+
+
+def test_batch_factors_are_the_systems_factors(ctx):
+    """silu_batch_setup factors each system on its own (in parallel) and packs
+    them block-diagonally: the packed factors equal the oracle's factors of
+    each system with columns shifted by the system's offset."""
+    edges = [3, 7, 4, 9, 5, 6, 8, 2]
+    systems = [synth.cutcell7(e, e + 1, e, seed=50 + k) for k, e in enumerate(edges)]
+    for kind, tau, fill in (("ilu0", 0.0, 0), ("ilut", 1e-3, 6), ("iluk", 0.0, 1)):
+        B = silu.Batch(ctx, systems, kind, tau=tau, fill=fill)
+        ex = B.factors.export()
+        off = B.offsets
+        for k, A in enumerate(systems):
+            OF = oracle.factor(A, kind, tau, fill)
+            OS = oracle.row_scale(OF)
+            r0, r1 = off[k], off[k + 1]
+            for mine, theirs in ((ex["L"], OS.L), (ex["Us"], OS.Us)):
+                rp = mine[0][r0:r1 + 1]
+                seg = slice(rp[0], rp[-1])
+                assert np.array_equal(rp - rp[0], theirs[0])
+                assert np.array_equal(mine[1][seg] - r0, theirs[1])
+                assert np.all(np.abs(mine[2][seg] - theirs[2]) <= 1e-14 * np.abs(theirs[2]))
+            assert np.allclose(ex["dinv"][r0:r1], OS.dinv, rtol=1e-14, atol=0)
+        B.close()
