@@ -45,7 +45,9 @@ typedef enum {
   SILU_ERR_TIMEOUT = 6,       /* a bounded device wait gave up               */
   SILU_WARN_DIVERGED = 7,     /* iterate grew beyond a bound (not an error)  */
   SILU_ERR_NO_DEVICE = 8,     /* device call on a host-only context          */
-  SILU_ERR_TOO_LARGE = 9      /* problem exceeds a fixed-capacity entry point */
+  SILU_ERR_TOO_LARGE = 9,     /* problem exceeds a fixed-capacity entry point */
+  SILU_ERR_BUSY = 10,         /* server queue full, or request already running */
+  SILU_ERR_CANCELLED = 11     /* request cancelled before it started         */
 } silu_status;
 
 /* Incomplete factorisation kinds (Sec. 1, Sec. 4.2, Sec. 5.1 of the paper). */
@@ -74,6 +76,7 @@ typedef struct silu_ctx_s* silu_ctx;
 typedef struct silu_mat_s* silu_mat;
 typedef struct silu_ilu_s* silu_ilu;
 typedef struct silu_batch_s* silu_batch;
+typedef struct silu_server_s* silu_server;
 
 /*
  * Create a context on CUDA device `device` whose work is ordered on
@@ -263,13 +266,69 @@ silu_status silu_batch_fgmres(silu_batch B, double* x, const double* b, double t
 /*
  * Autotuner: times one smoother application (sweeps_L, sweeps_U) with each
  * candidate launch shape of the sweep kernels and keeps the fastest:
- * rows per warp (one, two or four lanes per row in the staged kernel, or the
- * lanes-per-row kernel with 2, 4 or 8 lanes) and gather width (8 or 16
- * entries in flight per lane).  Writes the chosen candidate's index and its
+ * rows per warp (staged kernel: 8, 16, 32, 64 or 128 rows per warp tile,
+ * i.e. four or two lanes per row, one, or one lane taking two or four rows;
+ * or the lanes-per-row kernel with 2, 4 or 8 lanes) and gather width (8 or
+ * 16 entries in flight per lane).  Writes the chosen candidate's index and its
  * time per application.  Blocks.
  */
 silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choice, double* ms);
 void silu_batch_destroy(silu_batch B);
+
+/*
+ * Solve server: continuous batching of pressure solves on one GPU.
+ *
+ * Requests arrive at any time (silu_server_submit copies the host CSR system
+ * and right-hand side) and wait in a FIFO queue.  The head of the queue is
+ * admitted when one of `workers` slots is free and its device-memory
+ * estimate fits in what is left of hbm_budget_bytes; a request larger than
+ * the whole budget is refused (SILU_ERR_OOM) and so is any request while
+ * `max_queue` requests wait (SILU_ERR_BUSY).  Each slot has its own host
+ * thread, CUDA stream and context: it factors the system on the host
+ * (ilu_setup, row scaling), runs fgmres_solve from x = 0 on its stream and
+ * copies the solution back, so admitted requests overlap on the device and
+ * memory is released as each finishes.  Results do not depend on what else
+ * runs.  device = -1 makes a host-only server for testing the admission
+ * logic: requests are set up and finish with SILU_ERR_NO_DEVICE.
+ */
+typedef struct {
+  int kind;             /* silu_kind */
+  double tau;           /* ILUT drop tolerance */
+  int fill;             /* ILU(k) level / ILUT fill per row */
+  int prec;             /* silu_prec of the factors and sweeps */
+  double tol;           /* relative residual (Eq. relres) */
+  int restart, maxit;
+  int sweeps_L, sweeps_U;
+  int precond;          /* silu_precond */
+} silu_request_params;
+
+typedef struct {
+  int status;           /* silu_status of the request */
+  int iterations;       /* FGMRES inner iterations */
+  double relres;        /* true relative residual at return */
+  double t_submit;      /* seconds since the server was created */
+  double t_admit;
+  double t_setup_done;
+  double t_done;
+  int64_t device_bytes; /* HBM reserved while it ran */
+} silu_result;
+
+silu_status silu_server_create(int device, int64_t hbm_budget_bytes, int workers, int max_queue, silu_server* out);
+silu_status silu_server_submit(silu_server S, int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                               const double* val, const double* b, const silu_request_params* params,
+                               uint64_t* ticket);
+/* Cancel a request that has not been admitted (SILU_ERR_BUSY once it runs). */
+silu_status silu_server_cancel(silu_server S, uint64_t ticket);
+/*
+ * done = 1 once the request finished; then res and (if non-NULL) the
+ * solution x[n] are written and the ticket is released.  wait = 1 blocks
+ * until it finishes.
+ */
+silu_status silu_server_poll(silu_server S, uint64_t ticket, int wait, int* done, silu_result* res, double* x);
+silu_status silu_server_stats(silu_server S, int64_t* queued, int64_t* running, int64_t* completed,
+                              int64_t* refused, int64_t* bytes_in_use);
+/* Stop: requests not yet admitted finish as SILU_ERR_CANCELLED; running ones complete. */
+void silu_server_destroy(silu_server S);
 
 /*
  * Allocation-free smoother application (the paper has no counterpart; it

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_PKG, "libsilu.so")
 
 # silu_status
 OK, ERR_INVALID_ARG, ERR_ZERO_PIVOT, ERR_NOT_CONVERGED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, WARN_DIVERGED, \
-    ERR_NO_DEVICE, ERR_TOO_LARGE = range(10)
+    ERR_NO_DEVICE, ERR_TOO_LARGE, ERR_BUSY, ERR_CANCELLED = range(12)
 # silu_kind
 ILU0, ILUK, ILUT = 0, 1, 2
 # silu_scale
@@ -42,6 +42,20 @@ K_NAMES = ["residual", "sweep_L", "sweep_U", "level", "krylov", "elementwise"]
 KINDS = {"ilu0": ILU0, "iluk": ILUK, "ilut": ILUT}
 
 _lib = None
+
+
+class RequestParams(ctypes.Structure):
+    """silu_request_params"""
+    _fields_ = [("kind", ctypes.c_int), ("tau", ctypes.c_double), ("fill", ctypes.c_int), ("prec", ctypes.c_int),
+                ("tol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
+                ("sweeps_L", ctypes.c_int), ("sweeps_U", ctypes.c_int), ("precond", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    """silu_result"""
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("relres", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_setup_done", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
 
 
 class SiluError(RuntimeError):
@@ -98,6 +112,13 @@ def load():
         "silu_batch_fgmres": (i32, [vp, vp, vp, dbl, i32, i32, i32, i32, i32, vp, vp]),
         "silu_batch_destroy": (None, [vp]),
         "silu_ilu_autotune": (i32, [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(dbl)]),
+        "silu_server_create": (i32, [i32, i64, i32, i32, pvp]),
+        "silu_server_submit": (i32, [vp, i64, vp, vp, vp, vp, ctypes.POINTER(RequestParams),
+                                     ctypes.POINTER(ctypes.c_uint64)]),
+        "silu_server_cancel": (i32, [vp, ctypes.c_uint64]),
+        "silu_server_poll": (i32, [vp, ctypes.c_uint64, i32, ctypes.POINTER(i32), ctypes.POINTER(Result), vp]),
+        "silu_server_stats": (i32, [vp] + [ctypes.POINTER(i64)] * 5),
+        "silu_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -115,7 +136,8 @@ def exported_symbols():
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
             "silu_ctx_launch_count", "silu_ctx_check", "silu_ilu_set_kernel", "silu_smooth_noalloc",
             "silu_batch_setup", "silu_batch_info", "silu_batch_smooth", "silu_batch_fgmres", "silu_batch_destroy",
-            "silu_ilu_autotune"]
+            "silu_ilu_autotune", "silu_server_create", "silu_server_submit", "silu_server_cancel",
+            "silu_server_poll", "silu_server_stats", "silu_server_destroy"]
 
 
 def _ptr(t) -> int:
@@ -368,6 +390,69 @@ def silu_batch_fgmres(B: Batch, x, b, tol: float = 1e-8, restart: int = 20, maxi
     if st not in (OK, ERR_NOT_CONVERGED):
         _check(B.ctx.handle, st, "silu_batch_fgmres")
     return st, its, rel
+
+
+class Server:
+    """silu_server: continuous batching of FGMRES solves under an HBM budget."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 120 << 30, workers: int = 4, max_queue: int = 64):
+        h = ctypes.c_void_p()
+        st = load().silu_server_create(device, int(hbm_budget), workers, max_queue, ctypes.byref(h))
+        if st != OK:
+            raise SiluError(st, "silu_server_create")
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, A, b, kind="ilu0", tau=0.0, fill=0, prec=FP32, tol=1e-8, restart=30, maxit=5000,
+               sweeps_L=3, sweeps_U=3, precond=PRECOND_SWEEPS):
+        """Returns (status, ticket); status ERR_OOM / ERR_BUSY when refused."""
+        rp = np.ascontiguousarray(A[0], dtype=np.int64)
+        ci = np.ascontiguousarray(A[1], dtype=np.int32)
+        va = np.ascontiguousarray(A[2], dtype=np.float64)
+        bb = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
+        n = len(rp) - 1
+        p = RequestParams(KINDS[kind] if isinstance(kind, str) else kind, float(tau), int(fill), int(prec),
+                          float(tol), int(restart), int(maxit), int(sweeps_L), int(sweeps_U), int(precond))
+        t = ctypes.c_uint64(0)
+        st = load().silu_server_submit(self.handle, n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(bb), ctypes.byref(p),
+                                       ctypes.byref(t))
+        if st == OK:
+            self._keep[t.value] = n
+        return st, t.value
+
+    def poll(self, ticket: int, wait: bool = False, want_x: bool = True):
+        """(done, Result, x or None); a finished ticket is released."""
+        n = self._keep.get(ticket, 0)
+        x = np.empty(max(n, 1), dtype=np.float64) if want_x else None
+        done = ctypes.c_int(0)
+        res = Result()
+        st = load().silu_server_poll(self.handle, ticket, 1 if wait else 0, ctypes.byref(done), ctypes.byref(res),
+                                     _ptr(x) if x is not None else 0)
+        if st != OK:
+            raise SiluError(st, "silu_server_poll")
+        if done.value:
+            self._keep.pop(ticket, None)
+            return True, res, (x[:n] if x is not None else None)
+        return False, None, None
+
+    def cancel(self, ticket: int) -> int:
+        return load().silu_server_cancel(self.handle, ticket)
+
+    def stats(self):
+        vals = [ctypes.c_int64() for _ in range(5)]
+        load().silu_server_stats(self.handle, *[ctypes.byref(v) for v in vals])
+        return dict(zip(["queued", "running", "completed", "refused", "bytes_in_use"], [v.value for v in vals]))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().silu_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------- C-named functions

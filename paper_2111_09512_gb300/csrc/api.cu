@@ -32,7 +32,8 @@ cudaError_t upload_csr(const silu::Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& 
   }
   std::vector<int> tl;
   const int tlanes = silu::staged_lanes(T.rp.data(), T.n);
-  const bool tiled = silu::make_tiles(T.rp.data(), T.n, tlanes, tl);
+  const int tpasses = silu::staged_passes(T.rp.data(), T.n, tlanes);
+  const bool tiled = silu::make_tiles(T.rp.data(), T.n, tlanes, tpasses, tl);
   if (e == cudaSuccess && tiled) e = upload(tiles, tl.data(), tl.size(), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging vectors die at return
   d.n = (int)T.n;
@@ -44,6 +45,7 @@ cudaError_t upload_csr(const silu::Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& 
   d.tiles = tiled ? tiles.as<int4>() : nullptr;
   d.ntiles = tiled ? (int)(tl.size() / 4) : 0;
   d.tile_lanes = tlanes;
+  d.tile_passes = tpasses;
   return e;
 }
 
@@ -466,26 +468,32 @@ silu_status silu_ctx_check(silu_ctx ctx) {
 
 namespace {
 
-// Rebuild the staged-kernel tiles of T (host CSR h) for g lanes per row.
-cudaError_t retile(const Csr& h, DBuf& tiles, DevCsr& T, int g, cudaStream_t s) {
+// Rebuild the staged-kernel tiles of T (host CSR h) for g lanes per row and
+// rl rows per lane.
+cudaError_t retile(const Csr& h, DBuf& tiles, DevCsr& T, int g, int rl, cudaStream_t s) {
   std::vector<int> tl;
-  if (!silu::make_tiles(h.rp.data(), h.n, g, tl)) return cudaSuccess;  // keeps the current tiles
+  if (!silu::make_tiles(h.rp.data(), h.n, g, rl, tl)) return cudaSuccess;  // keeps the current tiles
   cudaError_t e = upload(tiles, tl.data(), tl.size(), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) {
     T.tiles = tiles.as<int4>();
     T.ntiles = (int)(tl.size() / 4);
     T.tile_lanes = g;
+    T.tile_passes = rl;
   }
   return e;
 }
 
+// variant 2: staged kernel with `lanes` lanes per row (0 = from the mean row
+// length) and `passes` rows per lane (0 = automatic), gather width `chunk`;
+// variant 1: lanes-per-row kernel with `lanes` lanes.
 struct TuneCandidate {
-  int variant, lanes, chunk;  // variant 2: staged (lanes = lanes per row, 0 = automatic); 1: lanes-per-row kernel
+  int variant, lanes, passes, chunk;
 };
 
-const TuneCandidate kTune[] = {{2, 0, 16}, {2, 0, 8}, {2, 1, 16}, {2, 2, 16}, {2, 4, 16},
-                               {1, 2, 16}, {1, 4, 16}, {1, 8, 16}};
+const TuneCandidate kTune[] = {{2, 0, 0, 16}, {2, 0, 0, 8}, {2, 1, 1, 16}, {2, 1, 2, 16}, {2, 1, 4, 16},
+                               {2, 1, 4, 8},  {2, 2, 1, 16}, {2, 4, 1, 16}, {1, 2, 0, 16}, {1, 4, 0, 16},
+                               {1, 8, 0, 16}};
 
 }  // namespace
 
@@ -518,8 +526,11 @@ silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choic
         F->lanesL = F->lanesU = c.lanes;
       } else {
         F->lanesL = F->lanesU = 0;
-        CK(retile(F->F.L, F->L_tiles, F->dL, c.lanes ? c.lanes : autoL, s));
-        CK(retile(Ut, F->U_tiles, F->dU, c.lanes ? c.lanes : autoU, s));
+        const int gL = c.lanes ? c.lanes : autoL, gU = c.lanes ? c.lanes : autoU;
+        const int pL = c.passes ? c.passes : silu::staged_passes(F->F.L.rp.data(), F->F.L.n, gL);
+        const int pU = c.passes ? c.passes : silu::staged_passes(Ut.rp.data(), Ut.n, gU);
+        CK(retile(F->F.L, F->L_tiles, F->dL, gL, gL == 1 ? pL : 1, s));
+        CK(retile(Ut, F->U_tiles, F->dU, gU, gU == 1 ? pU : 1, s));
         F->dL.chunk = F->dU.chunk = c.chunk;
       }
     };

@@ -50,14 +50,15 @@ struct DevCsr {
   int4* tiles = nullptr;
   int ntiles = 0;
   int tile_lanes = 1;  // lanes per row in the staged kernel (1, 2 or 4)
+  int tile_passes = 1; // rows per lane in a tile (1, 2 or 4; only with one lane per row)
   int chunk = 16;      // entries gathered per lane before the FMAs (8 or 16)
 };
 
-// Staged-sweep tile limits (entries per warp tile; a tile has 32 / lanes
-// rows).  The CSR arrays of a tiled matrix are allocated with kCsrPad spare
+// Staged-sweep tile limits (entries per warp tile; a tile has
+// 32 * passes / lanes rows).  The CSR arrays of a tiled matrix are allocated with kCsrPad spare
 // elements so that copies rounded out to 16-byte boundaries stay inside the
 // allocation.
-constexpr int kTileNnz = 448;
+constexpr int kTileNnz = 424;
 constexpr int kTileRows = 32;
 constexpr int kCsrPad = 8;
 
@@ -65,11 +66,15 @@ constexpr int kCsrPad = 8;
 // row up to 16 entries, two up to 32, four beyond (each warp-wide FMA then
 // carries about as many useful entries as the longest row allows).
 int staged_lanes(const int64_t* rp, int64_t n);
+// Rows per lane with one lane per row: 4 for rows of about 3 entries, 2 up
+// to about 6, else 1 (so that a tile's bulk copies stay a few KB).
+int staged_passes(const int64_t* rp, int64_t n, int lanes);
 
 // Build the warp-tile descriptors of a CSR row pointer (host), four ints per
-// tile, for `lanes` lanes per row (32 / lanes rows per tile).  Returns false
-// if a row has more than kTileNnz - 8 entries.
-bool make_tiles(const int64_t* rp, int64_t n, int lanes, std::vector<int>& desc);
+// tile, for `lanes` lanes per row and `passes` rows per lane (32 * passes /
+// lanes rows per tile).  Returns false if a row has more than kTileNnz - 8
+// entries.
+bool make_tiles(const int64_t* rp, int64_t n, int lanes, int passes, std::vector<int>& desc);
 
 // Device-side state shared by launches on one context.
 struct LaunchEnv {

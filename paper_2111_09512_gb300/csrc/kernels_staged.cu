@@ -8,7 +8,9 @@
 // of the longest row in each warp and nothing else, and keeps the FP64 unit
 // fed while other warps wait on memory.
 //
-// Work is cut into warp tiles of up to 32 consecutive rows (one per lane).
+// Work is cut into warp tiles of consecutive rows: 32 rows (one per lane),
+// or 16 / 8 with two / four lanes sharing a long row, or 64 / 128 with one
+// lane taking two / four short rows in turn.
 // Every warp walks its own fixed sequence of tiles with its own two-stage
 // shared-memory ring: lane 0 issues three bulk asynchronous copies per tile
 // (values, column indices, row pointers) that complete on the stage's
@@ -32,9 +34,16 @@ int staged_lanes(const int64_t* rp, int64_t n) {
   return avg <= 16.0 ? 1 : (avg <= 32.0 ? 2 : 4);
 }
 
-bool make_tiles(const int64_t* rp, int64_t n, int lanes, std::vector<int>& desc) {
+int staged_passes(const int64_t* rp, int64_t n, int lanes) {
+  if (lanes != 1) return 1;
+  const double avg = n ? (double)rp[n] / (double)n : 0.0;
+  const double room = (double)(kTileNnz - 8) / (double)kTileRows;  // entries per row at one pass
+  return avg * 4.0 <= room ? 4 : (avg * 2.0 <= room ? 2 : 1);
+}
+
+bool make_tiles(const int64_t* rp, int64_t n, int lanes, int passes, std::vector<int>& desc) {
   desc.clear();
-  const int rows = kTileRows / lanes;
+  const int rows = kTileRows * passes / lanes;
   int64_t r0 = 0;
   while (r0 < n) {
     int64_t r1 = r0;
@@ -145,7 +154,7 @@ struct StageLayout {
   static constexpr size_t kHdr = 16;
   static constexpr size_t kVal = sizeof(MT) * (kTileNnz + 8);
   static constexpr size_t kCol = sizeof(int) * (kTileNnz + 8);
-  static constexpr size_t kRp = sizeof(int) * (kTileRows + 8);
+  static constexpr size_t kRp = sizeof(int) * (4 * kTileRows + 8);
   static constexpr size_t kBytes = kHdr + kVal + kCol + kRp;  // all multiples of 16
 };
 
@@ -229,7 +238,7 @@ __device__ __forceinline__ MT row_accumulate(const MT* sv, const int* sc, int le
   return acc;
 }
 
-template <class MT, class VI, class VO, int G, int CH>
+template <class MT, class VI, class VO, int G, int CH, int RL>
 __global__ void __launch_bounds__(kStagedThreads, 1)
     k_sweep_staged(int ntiles, const int4* __restrict__ tiles, const int* __restrict__ rp, const int* __restrict__ ci,
                    const MT* __restrict__ va, const VI* __restrict__ c, const VI* __restrict__ in,
@@ -285,36 +294,39 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     const int a0 = p0 & ~(L::kValAlign - 1);
     const int c0 = p0 & ~3;
     const int sub = lane % G;
-    const int r = r0 + lane / G;
-    const bool act = r < r1;
-    const int b = act ? sr[r - q0] : p0;
-    const int len = act ? sr[r + 1 - q0] - b : 0;
-    // c enters once per row, through the lane that writes the result
-    MT acc = (act && c && sub == 0) ? (MT)ld_keep(c + r, keep) : MT(0);
-    if (epi == EPI_SPMV)
-      acc = row_accumulate<MT, VI, false, G, CH>(sv + (b - a0), sc + (b - c0), len, sub, in, acc, keep);
-    else
-      acc = row_accumulate<MT, VI, true, G, CH>(sv + (b - a0), sc + (b - c0), len, sub, in, acc, keep);
-    if (act && sub == 0) {
+#pragma unroll 1
+    for (int pass = 0; pass < RL; ++pass) {
+      const int r = r0 + pass * (32 / G) + lane / G;
+      const bool act = r < r1;
+      const int b = act ? sr[r - q0] : p0;
+      const int len = act ? sr[r + 1 - q0] - b : 0;
+      // c enters once per row, through the lane that writes the result
+      MT acc = (act && c && sub == 0) ? (MT)ld_keep(c + r, keep) : MT(0);
       if (epi == EPI_SPMV)
-        st_keep(out + r, (VO)acc, keep);
+        acc = row_accumulate<MT, VI, false, G, CH>(sv + (b - a0), sc + (b - c0), len, sub, in, acc, keep);
       else
-        epilogue<MT, VI, VO>(epi, r, acc, in, out, dinv, x, keep);
+        acc = row_accumulate<MT, VI, true, G, CH>(sv + (b - a0), sc + (b - c0), len, sub, in, acc, keep);
+      if (act && sub == 0) {
+        if (epi == EPI_SPMV)
+          st_keep(out + r, (VO)acc, keep);
+        else
+          epilogue<MT, VI, VO>(epi, r, acc, in, out, dinv, x, keep);
+      }
     }
     __syncwarp();
     if (lane == 0 && tn < ntiles) issue_tile<MT>(dn, ring + s * L::kBytes, &full[warp][s], rp, ci, va, stream);
   }
 }
 
-template <class MT, class VI, class VO, int G, int CH>
+template <class MT, class VI, class VO, int G, int CH, int RL>
 cudaError_t staged_attr() {
   using L = StageLayout<MT>;
   const size_t smem = (size_t)kWarps * kWarpStages * L::kBytes;
-  return cudaFuncSetAttribute(k_sweep_staged<MT, VI, VO, G, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_sweep_staged<MT, VI, VO, G, CH, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem);
 }
 
-template <class MT, class VI, class VO, int G, int CH>
+template <class MT, class VI, class VO, int G, int CH, int RL>
 cudaError_t staged_g(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
                      const double* dinv, double* x, int epi, cudaStream_t s) {
   using L = StageLayout<MT>;
@@ -322,38 +334,46 @@ cudaError_t staged_g(const DevCsr& T, const LaunchEnv& env, const void* c, const
   if (T.ntiles == 0) return cudaSuccess;
   const int want = (T.ntiles + kWarps - 1) / kWarps;
   const int grid = want < env.sms ? want : env.sms;
-  k_sweep_staged<MT, VI, VO, G, CH><<<grid, kStagedThreads, smem, s>>>(
+  k_sweep_staged<MT, VI, VO, G, CH, RL><<<grid, kStagedThreads, smem, s>>>(
       T.ntiles, T.tiles, T.rp, T.ci, (const MT*)T.va, (const VI*)c, (const VI*)in, (VO*)out, dinv, x, epi, env.err);
   return cudaGetLastError();
 }
 
-template <class MT, class VI, class VO, int G>
+template <class MT, class VI, class VO, int G, int RL>
 cudaError_t staged_c(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
                      const double* dinv, double* x, int epi, cudaStream_t s) {
-  if (T.chunk == 8) return staged_g<MT, VI, VO, G, 8>(T, env, c, in, out, dinv, x, epi, s);
-  return staged_g<MT, VI, VO, G, 16>(T, env, c, in, out, dinv, x, epi, s);
+  if (T.chunk == 8) return staged_g<MT, VI, VO, G, 8, RL>(T, env, c, in, out, dinv, x, epi, s);
+  return staged_g<MT, VI, VO, G, 16, RL>(T, env, c, in, out, dinv, x, epi, s);
 }
 
 template <class MT, class VI, class VO>
 cudaError_t staged(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
                    const double* dinv, double* x, int epi, cudaStream_t s) {
   switch (T.tile_lanes) {
-    case 1: return staged_c<MT, VI, VO, 1>(T, env, c, in, out, dinv, x, epi, s);
-    case 2: return staged_c<MT, VI, VO, 2>(T, env, c, in, out, dinv, x, epi, s);
-    case 4: return staged_c<MT, VI, VO, 4>(T, env, c, in, out, dinv, x, epi, s);
+    case 1:
+      if (T.tile_passes == 4) return staged_c<MT, VI, VO, 1, 4>(T, env, c, in, out, dinv, x, epi, s);
+      if (T.tile_passes == 2) return staged_c<MT, VI, VO, 1, 2>(T, env, c, in, out, dinv, x, epi, s);
+      return staged_c<MT, VI, VO, 1, 1>(T, env, c, in, out, dinv, x, epi, s);
+    case 2: return staged_c<MT, VI, VO, 2, 1>(T, env, c, in, out, dinv, x, epi, s);
+    case 4: return staged_c<MT, VI, VO, 4, 1>(T, env, c, in, out, dinv, x, epi, s);
   }
   return cudaErrorInvalidValue;
 }
 
+template <class MT, class VI, class VO, int G, int RL>
+cudaError_t prepare_shape() {
+  cudaError_t e = staged_attr<MT, VI, VO, G, 8, RL>();
+  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, G, 16, RL>();
+  return e;
+}
+
 template <class MT, class VI, class VO>
 cudaError_t prepare_mode() {
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, 1, 8>();
-  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, 1, 16>();
-  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, 2, 8>();
-  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, 2, 16>();
-  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, 4, 8>();
-  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, 4, 16>();
+  cudaError_t e = prepare_shape<MT, VI, VO, 1, 1>();
+  if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 1, 2>();
+  if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 1, 4>();
+  if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 2, 1>();
+  if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 4, 1>();
   return e;
 }
 

@@ -33,7 +33,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
                    check=True)
     os.replace(tmp, _SO)
     return _SO
@@ -57,6 +57,10 @@ def _load():
     lib.synth_rowptr27.argtypes = [i32, i32, i32, vp]
     lib.synth_fill27_range.restype = i32
     lib.synth_fill27_range.argtypes = [i32, i32, i32, vp, vp, i64, i64, vp, vp, vp]
+    lib.synth_rowptr7.restype = i32
+    lib.synth_rowptr7.argtypes = [i32, i32, i32, vp]
+    lib.synth_fill7_range.restype = i32
+    lib.synth_fill7_range.argtypes = [i32, i32, i32, i32, u64, dbl, dbl, i64, i64, vp, vp, vp]
     lib.synth_uniform.restype = None
     lib.synth_uniform.argtypes = [u64, u64, i64, dbl, dbl, vp]
     lib.synth_randint.restype = None
@@ -100,6 +104,18 @@ def matrix(kind: int, nx: int, ny: int, nz: int, seed: int = 0, sigma: float = 0
         with ThreadPoolExecutor(nt) as ex:
             if any(ex.map(work, range(nt))):
                 raise RuntimeError("synth_fill27_range failed")
+    elif kind in (POISSON7, CUTCELL7) and n > 200_000:
+        lib.synth_rowptr7(nx, ny, nz, _ptr(rp))
+        nt = threads or max(1, min(32, os.cpu_count() or 1))
+        bounds = np.linspace(0, n, nt + 1).astype(np.int64)
+
+        def work7(t):
+            return lib.synth_fill7_range(kind, nx, ny, nz, seed, sigma, frac_cut, int(bounds[t]),
+                                         int(bounds[t + 1]), _ptr(rp), _ptr(ci), _ptr(va))
+
+        with ThreadPoolExecutor(nt) as ex:
+            if any(ex.map(work7, range(nt))):
+                raise RuntimeError("synth_fill7_range failed")
     else:
         rc = lib.synth_fill(kind, nx, ny, nz, seed, sigma, frac_cut, _ptr(rp), _ptr(ci), _ptr(va))
         if rc:

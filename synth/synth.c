@@ -110,66 +110,92 @@ static double cc_vf(const gen7* g, int i, int j, int k) {
   return pow(10.0, -8.0 * unif(g->seed, ST_CUTVF, (uint64_t)cell));
 }
 
-/*
- * Fill a 7-point matrix.  row_ptr has n+1 entries, col/val have
- * synth_nnz() entries.  Columns come out in ascending order.
- */
-static void fill7(int kind, const gen7* g, int64_t* rp, int32_t* ci, double* va) {
-  const int nx = g->nx, ny = g->ny, nz = g->nz;
-  int64_t p = 0;
+static int64_t count7(int nx, int ny, int nz, int i, int j, int k) {
+  return 1 + (i > 0) + (i < nx - 1) + (j > 0) + (j < ny - 1) + (k > 0) + (k < nz - 1);
+}
+
+/* row pointer of the 7-point matrix (n+1 entries) */
+int synth_rowptr7(int nx, int ny, int nz, int64_t* rp) {
+  if (nx < 1 || ny < 1 || nz < 1 || !rp) return 1;
   rp[0] = 0;
+  int64_t row = 0;
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
-      for (int i = 0; i < nx; ++i) {
-        const int64_t row = ((int64_t)k * ny + j) * nx + i;
-        /* neighbour offsets in ascending column order */
-        const int di[6] = {0, 0, -1, 1, 0, 0};
-        const int dj[6] = {0, -1, 0, 0, 1, 0};
-        const int dk[6] = {-1, 0, 0, 0, 0, 1};
-        double coef[6];
-        int inside[6];
-        double diag = 0.0;
-        double rho_a = 0.0, vf_a = 1.0;
-        if (kind == SYNTH_CUTCELL7) {
-          rho_a = cc_rho(g, row);
-          vf_a = cc_vf(g, i, j, k);
-        }
-        for (int f = 0; f < 6; ++f) {
-          const int a = i + di[f], b = j + dj[f], c = k + dk[f];
-          inside[f] = (a >= 0 && a < nx && b >= 0 && b < ny && c >= 0 && c < nz);
-          if (kind == SYNTH_POISSON7) {
-            coef[f] = 1.0;
-            diag += 1.0; /* a Dirichlet ghost contributes to the diagonal */
-          } else if (inside[f]) {
-            const int64_t nb = ((int64_t)c * ny + b) * nx + a;
-            const double rho_b = cc_rho(g, nb);
-            const double vf_b = cc_vf(g, a, b, c);
-            const double alpha = vf_a < vf_b ? vf_a : vf_b;
-            coef[f] = alpha * 2.0 / (rho_a + rho_b);
-            diag += coef[f];
-          } else {
-            coef[f] = vf_a * 2.0 / rho_a;
-            diag += coef[f];
-          }
-        }
-        /* lower neighbours (faces 0..2), diagonal, upper neighbours (3..5) */
-        for (int f = 0; f < 3; ++f)
-          if (inside[f]) {
-            ci[p] = (int32_t)(row + (int64_t)dk[f] * nx * ny + (int64_t)dj[f] * nx + di[f]);
-            va[p] = -coef[f];
-            ++p;
-          }
-        ci[p] = (int32_t)row;
-        va[p] = diag;
-        ++p;
-        for (int f = 3; f < 6; ++f)
-          if (inside[f]) {
-            ci[p] = (int32_t)(row + (int64_t)dk[f] * nx * ny + (int64_t)dj[f] * nx + di[f]);
-            va[p] = -coef[f];
-            ++p;
-          }
-        rp[row + 1] = p;
+      for (int i = 0; i < nx; ++i, ++row) rp[row + 1] = rp[row] + count7(nx, ny, nz, i, j, k);
+  return 0;
+}
+
+/*
+ * Rows [r0, r1) of a 7-point matrix whose row pointer is complete.  Columns
+ * come out in ascending order.  Disjoint row ranges may be filled
+ * concurrently.
+ */
+static void fill7_rows(int kind, const gen7* g, int64_t r0, int64_t r1, const int64_t* rp, int32_t* ci, double* va) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+  for (int64_t row = r0; row < r1; ++row) {
+    const int i = (int)(row % nx), j = (int)((row / nx) % ny), k = (int)(row / ((int64_t)nx * ny));
+    int64_t p = rp[row];
+    /* neighbour offsets in ascending column order */
+    const int di[6] = {0, 0, -1, 1, 0, 0};
+    const int dj[6] = {0, -1, 0, 0, 1, 0};
+    const int dk[6] = {-1, 0, 0, 0, 0, 1};
+    double coef[6];
+    int inside[6];
+    double diag = 0.0;
+    double rho_a = 0.0, vf_a = 1.0;
+    if (kind == SYNTH_CUTCELL7) {
+      rho_a = cc_rho(g, row);
+      vf_a = cc_vf(g, i, j, k);
+    }
+    for (int f = 0; f < 6; ++f) {
+      const int a = i + di[f], b = j + dj[f], c = k + dk[f];
+      inside[f] = (a >= 0 && a < nx && b >= 0 && b < ny && c >= 0 && c < nz);
+      if (kind == SYNTH_POISSON7) {
+        coef[f] = 1.0;
+        diag += 1.0; /* a Dirichlet ghost contributes to the diagonal */
+      } else if (inside[f]) {
+        const int64_t nb = ((int64_t)c * ny + b) * nx + a;
+        const double rho_b = cc_rho(g, nb);
+        const double vf_b = cc_vf(g, a, b, c);
+        const double alpha = vf_a < vf_b ? vf_a : vf_b;
+        coef[f] = alpha * 2.0 / (rho_a + rho_b);
+        diag += coef[f];
+      } else {
+        coef[f] = vf_a * 2.0 / rho_a;
+        diag += coef[f];
       }
+    }
+    /* lower neighbours (faces 0..2), diagonal, upper neighbours (3..5) */
+    for (int f = 0; f < 3; ++f)
+      if (inside[f]) {
+        ci[p] = (int32_t)(row + (int64_t)dk[f] * nx * ny + (int64_t)dj[f] * nx + di[f]);
+        va[p] = -coef[f];
+        ++p;
+      }
+    ci[p] = (int32_t)row;
+    va[p] = diag;
+    ++p;
+    for (int f = 3; f < 6; ++f)
+      if (inside[f]) {
+        ci[p] = (int32_t)(row + (int64_t)dk[f] * nx * ny + (int64_t)dj[f] * nx + di[f]);
+        va[p] = -coef[f];
+        ++p;
+      }
+  }
+}
+
+int synth_fill7_range(int kind, int nx, int ny, int nz, uint64_t seed, double sigma, double frac_cut, int64_t r0,
+                      int64_t r1, const int64_t* rp, int32_t* ci, double* va) {
+  if (nx < 1 || ny < 1 || nz < 1 || !rp || !ci || !va) return 1;
+  if (kind != SYNTH_POISSON7 && kind != SYNTH_CUTCELL7) return 1;
+  gen7 g = {nx, ny, nz, seed, sigma, frac_cut};
+  fill7_rows(kind, &g, r0, r1, rp, ci, va);
+  return 0;
+}
+
+static void fill7(int kind, const gen7* g, int64_t* rp, int32_t* ci, double* va) {
+  synth_rowptr7(g->nx, g->ny, g->nz, rp);
+  fill7_rows(kind, g, 0, (int64_t)g->nx * g->ny * g->nz, rp, ci, va);
 }
 
 /* node index in the lattice extended by one ghost layer on every side */
