@@ -516,12 +516,11 @@ def serving(silu, args):
     edges log-uniform in [16, 192], each FGMRES(30) from zero to 1e-8, under a
     120 GB HBM budget.  Two paths on the same arrival stream: FP32 scaled-ILU(0)
     Richardson smoother (3+3 sweeps) and the plain FP64 direct-trisolve path.
-    The client generates each request's matrix ahead of its arrival time on a
-    small pool (bounded look-ahead) and submits it at that time; latency is
-    completion minus submission on the server's clock."""
-    import queue
-    import threading
-
+    The client draws every request's edge from the stream but takes its matrix
+    from a pool of args.serve_pool distinct systems generated before the clock
+    starts (request k uses pool entry k mod pool, whose edge is the pool's own
+    log-uniform draw), so submission is never held up by generation.  Latency
+    is completion minus submission on the server's clock."""
     import numpy as np
     import synth
     rate, dur = args.serve_rate, args.serve_seconds
@@ -529,62 +528,35 @@ def serving(silu, args):
     gaps = -np.log1p(-synth.uniform(4, 5, count, 0.0, 1.0)) / rate
     arrivals = np.cumsum(gaps)
     arrivals = arrivals[arrivals < dur]
-    ue = synth.uniform(4, 6, len(arrivals), 0.0, 1.0)
+    P = args.serve_pool
+    ue = synth.uniform(4, 6, P, 0.0, 1.0)
     edges = np.rint(np.exp(np.log(16.0) + ue * (np.log(192.0) - np.log(16.0)))).astype(int)
+    pool = []
+    for k, e in enumerate(edges):
+        A = synth.cutcell7(int(e), seed=40_000 + k)
+        pool.append((A, synth.rhs(int(e) ** 3, 1, seed=50_000 + k)[:, 0]))
     out = {"workload": "cut-cell 7-point solves, edges log-uniform [16,192], FGMRES(30) to 1e-8",
-           "rate_per_s": rate, "seconds": dur, "offered": int(len(arrivals)), "hbm_budget_gb": 120,
+           "rate_per_s": rate, "seconds": dur, "offered": int(len(arrivals)), "pool": P,
+           "pool_rows_mean": int(np.mean(edges.astype(np.int64) ** 3)), "hbm_budget_gb": 120,
            "workers": args.serve_workers, "max_queue": args.serve_queue}
     for name, prec, pc in (("fp32_sweeps_3_3", silu.FP32, silu.PRECOND_SWEEPS),
                            ("fp64_direct", silu.FP64, silu.PRECOND_DIRECT)):
         S = silu.Server(0, 120 << 30, workers=args.serve_workers, max_queue=args.serve_queue)
-        ready = {}
-        cond = threading.Condition()
-        nxt = [0]
-        stop = [False]
-
-        def producer():
-            while True:
-                with cond:
-                    while not stop[0] and (nxt[0] >= len(edges) or len(ready) >= 12):
-                        cond.wait(0.05)
-                    if stop[0] or nxt[0] >= len(edges):
-                        return
-                    k = nxt[0]
-                    nxt[0] += 1
-                e = int(edges[k])
-                A = synth.cutcell7(e, seed=40_000 + k)
-                b = synth.rhs(e * e * e, 1, seed=50_000 + k)[:, 0]
-                with cond:
-                    ready[k] = (A, b)
-                    cond.notify_all()
-
-        pool = [threading.Thread(target=producer, daemon=True) for _ in range(4)]
-        for th in pool:
-            th.start()
-        tickets, refused, late = [], 0, []
+        tickets, refused = [], 0
         start = time.perf_counter()
         for k, t_k in enumerate(arrivals):
-            with cond:
-                while k not in ready:
-                    cond.wait(0.05)
-                A, b = ready.pop(k)
-                cond.notify_all()
             now = time.perf_counter() - start
             if now < t_k:
                 time.sleep(t_k - now)
-            else:
-                late.append(now - t_k)
+            A, b = pool[k % P]
             st, t = S.submit(A, b, prec=prec, tol=1e-8, restart=30, maxit=20000, sweeps_L=3, sweeps_U=3,
                              precond=pc)
             if st == silu.OK:
-                tickets.append((t, int(edges[k])))
+                tickets.append(t)
             else:
                 refused += 1
-        with cond:
-            stop[0] = True
-            cond.notify_all()
         lat, solved, iters, t_first, t_last = [], 0, [], None, None
-        for t, e in tickets:
+        for t in tickets:
             _, res, _ = S.poll(t, wait=True, want_x=False)
             if res.status == silu.OK:
                 solved += 1
@@ -598,8 +570,7 @@ def serving(silu, args):
                      "solves_per_s": round(solved / span, 3) if span > 0 else None,
                      "p50_s": round(float(np.percentile(lat, 50)), 4) if lat else None,
                      "p99_s": round(float(np.percentile(lat, 99)), 4) if lat else None,
-                     "iterations_mean": round(float(np.mean(iters)), 1) if iters else None,
-                     "late_submissions": len(late)}
+                     "iterations_mean": round(float(np.mean(iters)), 1) if iters else None}
     return out
 
 
@@ -615,9 +586,10 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-workers", type=int, default=4)
-    ap.add_argument("--serve-queue", type=int, default=32)
+    ap.add_argument("--serve-queue", type=int, default=8)
+    ap.add_argument("--serve-pool", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()

@@ -74,6 +74,7 @@ cudaError_t ensure_vectors(silu_ilu F, int nrhs) {
 cudaError_t ensure_krylov(silu_ilu F, int m) {
   Workspace& w = F->ws;
   if (m <= w.restart && w.V.p) return cudaSuccess;
+  w.drop_graphs();
   const size_t n = (size_t)F->F.L.n;
   cudaError_t e;
   if ((e = w.V.ensure(sizeof(double) * n * (size_t)(m + 1))) != cudaSuccess) return e;
@@ -325,7 +326,8 @@ cudaGraphExec_t level_graph(silu_ilu F, int R, int ldx, size_t col) {
 }
 
 // Direct application on columns [0, R): x (+)= Utilde^{-1} D^{-1} L^{-1} (b - A x).
-void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, bool x_zero) {
+void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, bool x_zero,
+                  bool inline_levels) {
   cudaStream_t s = F->ctx->stream;
   const int n = (int)F->F.L.n;
   double* y = F->ws.r.as<double>() + col;
@@ -335,8 +337,21 @@ void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
     LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_scale(n, R, ldx, b, false, nullptr, y, false, s));
   else
     LAUNCH(F->ctx, SILU_K_RESIDUAL, sweep_launch(F, F->A->d, silu::MODE_D, R, gA, ldx, b, x, y, nullptr, nullptr, silu::EPI_STORE));
-  cudaGraphExec_t exec = level_graph(F, R, ldx, col);
-  {
+  if (inline_levels) {
+    const double* dinv = F->d_dinv.as<double>();
+    const int gL = lanes_of(F->lanesL, F->autoL), gU = lanes_of(F->lanesU, F->autoU);
+    const int* rowsL = F->levLrows_d.as<int>();
+    const int* rowsU = F->levUrows_d.as<int>();
+    for (int l = 0; l < F->nlevL; ++l) {
+      const int b0 = F->levLptr[l], b1 = F->levLptr[l + 1];
+      LAUNCH(F->ctx, SILU_K_LEVEL, silu::launch_level(F->dL64, rowsL + b0, b1 - b0, R, gL, ldx, y, dinv, c, nullptr, s));
+    }
+    for (int l = 0; l < F->nlevU; ++l) {
+      const int b0 = F->levUptr[l], b1 = F->levUptr[l + 1];
+      LAUNCH(F->ctx, SILU_K_LEVEL, silu::launch_level(F->dS64, rowsU + b0, b1 - b0, R, gU, ldx, c, dinv, nullptr, nullptr, s));
+    }
+  } else {
+    cudaGraphExec_t exec = level_graph(F, R, ldx, col);
     ProfScope ps(F->ctx, SILU_K_LEVEL);
     F->ctx->launches += F->nlevL + F->nlevU - 1;  // one count came from ProfScope
     CK(cudaGraphLaunch(exec, s));
@@ -346,6 +361,92 @@ void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
 
 int chunk_width(int left) { return left >= 4 ? 4 : (left >= 2 ? 2 : 1); }
 
+
+namespace {
+
+// The fixed kernel sequence of FGMRES inner iteration j on the workspace:
+// z_j = M^{-1} v_j, w = A z_j, modified Gram-Schmidt against v_0..v_j,
+// h_{j+1,j} and v_{j+1}, then the Givens update of column j, which leaves
+// |g_{j+1}| and h_{j+1,j} in scal[1], scal[2].
+void fgmres_inner(silu_ilu F, int j, int m, int mL, int mU, int precond, bool capturing) {
+  cudaStream_t s = F->ctx->stream;
+  Workspace& W = F->ws;
+  const int n = (int)F->F.L.n;
+  const int gA = lanes_of(F->lanesA, F->autoA);
+  double* V = W.V.as<double>();
+  double* Z = W.Z.as<double>();
+  double* w = W.w.as<double>();
+  double* H = W.H.as<double>();
+  double* part[2] = {W.part0.as<double>(), W.part1.as<double>()};
+  auto vec = [&](double* base, int k) { return base + (size_t)k * (size_t)n; };
+  double* vj = vec(V, j);
+  double* zj = vec(Z, j);
+  if (precond == SILU_PRECOND_SWEEPS)
+    smooth_chunk(F, zj, vj, 1, 1, 0, mL, mU, true);
+  else if (precond == SILU_PRECOND_DIRECT)
+    direct_chunk(F, zj, vj, 1, 1, 0, true, capturing);
+  else
+    CK(cudaMemcpyAsync(zj, vj, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+  LAUNCH(F->ctx, SILU_K_RESIDUAL, sweep_launch(F, F->A->d, silu::MODE_D, 1, gA, 1, nullptr, zj, w, nullptr, nullptr, silu::EPI_SPMV));
+  LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_dot_part(n, w, V, part[0], s));
+  int cur = 0;
+  for (int i = 0; i <= j; ++i) {
+    const double* vnext = (i < j) ? vec(V, i + 1) : nullptr;
+    LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_mgs_step(n, part[cur], H + (size_t)i * m + j, w, vec(V, i), vnext, part[cur ^ 1], s));
+    cur ^= 1;
+  }
+  LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_normalize(n, part[cur], H + (size_t)(j + 1) * m + j, w, vec(V, j + 1), s));
+  LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_givens(j, m, H, W.cs.as<double>(), W.sn.as<double>(), W.g.as<double>(), W.scal.as<double>() + 1, s));
+}
+
+// Run inner iteration j from its captured graph (capturing it on first use).
+void fgmres_inner_graph(silu_ilu F, int j, int m, int mL, int mU, int precond) {
+  silu_ctx ctx = F->ctx;
+  for (KrylovGraph& kg : F->ws.kgraphs)
+    if (kg.j == j && kg.m == m && kg.mL == mL && kg.mU == mU && kg.precond == precond && kg.gen == F->config_gen) {
+      ctx->launches += kg.kernels;
+      CK(cudaGraphLaunch(kg.exec, ctx->stream));
+      return;
+    }
+  cudaStream_t cap = nullptr;
+  CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaStream_t saved = ctx->stream;
+  const bool prof = ctx->profiling;
+  ctx->profiling = false;
+  ctx->stream = cap;
+  const int64_t l0 = ctx->launches;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    try {
+      fgmres_inner(F, j, m, mL, mU, precond, true);
+    } catch (const CudaFail& f) {
+      e = f.e;
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  ctx->stream = saved;
+  ctx->profiling = prof;
+  KrylovGraph kg;
+  kg.j = j;
+  kg.m = m;
+  kg.mL = mL;
+  kg.mU = mU;
+  kg.precond = precond;
+  kg.gen = F->config_gen;
+  kg.kernels = ctx->launches - l0;
+  ctx->launches = l0;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&kg.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  CK(e);
+  F->ws.kgraphs.push_back(kg);
+  ctx->launches += kg.kernels;
+  CK(cudaGraphLaunch(kg.exec, ctx->stream));
+}
+
+}  // namespace
 
 silu_status finish_setup(silu_ilu F) {
   silu_ctx ctx = F->ctx;
@@ -552,6 +653,8 @@ silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choic
       }
     }
     apply(kTune[best]);
+    F->ws.drop_graphs();
+    F->config_gen++;
   } catch (const CudaFail& f) {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -568,6 +671,8 @@ silu_status silu_ilu_set_kernel(silu_ilu F, int variant) {
   if (!F) return SILU_ERR_INVALID_ARG;
   if (variant < 0 || variant > 2) return set_err(F->ctx, SILU_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
   F->variant = variant;
+  F->ws.drop_graphs();
+  F->config_gen++;
   return SILU_OK;
 }
 
@@ -774,7 +879,6 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
     double* scal = W.scal.as<double>();
     double* hp = ctx->pinned;
     const int gA = lanes_of(F->lanesA, F->autoA);
-    auto vec = [&](double* base, int k) { return base + (size_t)k * (size_t)n; };
     // ||b||
     LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_dot_part(n, b, b, part[0], s));
     LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_norm_final(n, part[0], scal, s));
@@ -807,30 +911,15 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
       LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_normalize(n, part[0], g, V, V, s));
       int jend = 0;
       for (int j = 0; j < m; ++j) {
-        double* vj = vec(V, j);
-        double* zj = vec(Z, j);
-        if (precond == SILU_PRECOND_SWEEPS)
-          smooth_chunk(F, zj, vj, 1, 1, 0, sweeps_L, sweeps_U, true);
-        else if (precond == SILU_PRECOND_DIRECT)
-          direct_chunk(F, zj, vj, 1, 1, 0, true);
+        if (F->ctx->profiling)
+          fgmres_inner(F, j, m, sweeps_L, sweeps_U, precond, false);  // per-kernel events need eager launches
         else
-          CK(cudaMemcpyAsync(zj, vj, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
-        LAUNCH(F->ctx, SILU_K_RESIDUAL, sweep_launch(F, F->A->d, silu::MODE_D, 1, gA, 1, nullptr, zj, w, nullptr, nullptr, silu::EPI_SPMV));
-        LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_dot_part(n, w, V, part[0], s));
-        int cur = 0;
-        for (int i = 0; i <= j; ++i) {
-          const double* vnext = (i < j) ? vec(V, i + 1) : nullptr;
-          LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_mgs_step(n, part[cur], H + (size_t)i * m + j, w, vec(V, i), vnext, part[cur ^ 1], s));
-          cur ^= 1;
-        }
-        LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_normalize(n, part[cur], H + (size_t)(j + 1) * m + j, w, vec(V, j + 1), s));
-        CK(cudaMemcpyAsync(hp + 1, H + (size_t)(j + 1) * m + j, sizeof(double), cudaMemcpyDeviceToHost, s));
-        LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_givens(j, m, H, W.cs.as<double>(), W.sn.as<double>(), g, scal + 1, s));
-        CK(cudaMemcpyAsync(hp + 2, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+          fgmres_inner_graph(F, j, m, sweeps_L, sweeps_U, precond);
+        CK(cudaMemcpyAsync(hp + 1, scal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         ++its;
         jend = j + 1;
-        const double hn = hp[1], res = hp[2];
+        const double res = hp[1], hn = hp[2];
         if (!std::isfinite(res)) {
           result = SILU_WARN_DIVERGED;
           break;
@@ -908,6 +997,8 @@ silu_status silu_ilu_set_lanes(silu_ilu F, int lanes_L, int lanes_U, int lanes_A
   F->lanesL = lanes_L;
   F->lanesU = lanes_U;
   F->lanesA = lanes_A;
+  F->ws.drop_graphs();
+  F->config_gen++;
   return SILU_OK;
 }
 

@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(KB) k_bdivide(int nch, const int4* __restrict_
 
 struct InnerGraph {
   int j = -1, mL = 0, mU = 0, precond = 0;
+  int64_t gen = -1;  // launch configuration of the factors at capture
   cudaGraphExec_t exec = nullptr;
   int64_t kernels = 0;
 };
@@ -364,7 +365,7 @@ void inner_iteration(silu_batch B, int j, int m, int mL, int mU, int precond, do
 void run_inner(silu_batch B, int j, int m, int mL, int mU, int precond, double tol, int maxit) {
   silu_ctx ctx = B->ctx;
   for (InnerGraph& ig : B->graphs)
-    if (ig.j == j && ig.mL == mL && ig.mU == mU && ig.precond == precond) {
+    if (ig.j == j && ig.mL == mL && ig.mU == mU && ig.precond == precond && ig.gen == B->F->config_gen) {
       ctx->launches += ig.kernels;
       CK(cudaGraphLaunch(ig.exec, ctx->stream));
       return;
@@ -396,6 +397,7 @@ void run_inner(silu_batch B, int j, int m, int mL, int mU, int precond, double t
   ig.mL = mL;
   ig.mU = mU;
   ig.precond = precond;
+  ig.gen = B->F->config_gen;
   ig.kernels = ctx->launches - l0;
   ctx->launches = l0;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&ig.exec, graph, 0);

@@ -121,7 +121,8 @@ cudaError_t launch_mgs_step(int n, const double* part_in, double* hout, double* 
 // h = sqrt(sum(part_in)); *hout = h; vout = w / h (skipped if h == 0)
 cudaError_t launch_normalize(int n, const double* part_in, double* hout, const double* w, double* vout,
                              cudaStream_t s);
-// Givens on column j of H (row-major (m+1) x m, leading dim m); writes |g_{j+1}| to *res
+// Givens on column j of H (row-major (m+1) x m, leading dim m); writes
+// res[0] = |g_{j+1}| and res[1] = h_{j+1,j}
 cudaError_t launch_givens(int j, int m, double* H, double* cs, double* sn, double* g, double* res, cudaStream_t s);
 // solve the jend x jend triangle, then x += sum_k y_k Z_k
 cudaError_t launch_update_x(int n, int jend, int m, const double* H, const double* g, double* y, const double* Z,

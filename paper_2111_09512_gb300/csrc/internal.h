@@ -84,15 +84,27 @@ struct LevelGraph {
   int kernels = 0;
 };
 
+// A captured FGMRES inner iteration (Arnoldi index j) on the Krylov workspace.
+struct KrylovGraph {
+  int j = -1, m = 0, mL = 0, mU = 0, precond = 0;
+  int64_t gen = -1;  // launch configuration the graph was captured with
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;
+};
+
 struct Workspace {
   size_t vec_bytes = 0;  // per buffer
   DBuf r, c, p0, p1;
-  std::vector<LevelGraph> graphs;  // valid while r and c keep their addresses
+  std::vector<LevelGraph> graphs;    // valid while r and c keep their addresses
+  std::vector<KrylovGraph> kgraphs;  // valid while every workspace buffer keeps its address
   ~Workspace() { drop_graphs(); }
   void drop_graphs() {
     for (LevelGraph& g : graphs)
       if (g.exec) cudaGraphExecDestroy(g.exec);
     graphs.clear();
+    for (KrylovGraph& g : kgraphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    kgraphs.clear();
   }
   int restart = 0;
   DBuf V, Z, w, H, cs, sn, g, yk, part0, part1, scal;
@@ -119,6 +131,7 @@ struct silu_ilu_s {
   DevCsr dL64, dS64;
   bool direct_ready = false;
   int lanesL = 0, lanesU = 0, lanesA = 0;
+  int64_t config_gen = 0;  // bumped whenever a launch shape changes (captured graphs go stale)
   int variant = 0;  // 0 auto, 1 plain lanes-per-row kernel, 2 staged kernel where possible
   int autoL = 4, autoU = 4, autoA = 8;
   Workspace ws;
@@ -213,8 +226,11 @@ cudaError_t sweep_launch(silu_ilu F, const DevCsr& T, Mode mode, int R, int lane
 // One smoother application on columns [0, R) (leading dimension ldx, workspace
 // column offset col); x_zero: zero initial guess, x is written, not updated.
 void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, int mL, int mU, bool x_zero);
-// The same update with level-scheduled exact solves.
-void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, bool x_zero);
+// The same update with level-scheduled exact solves.  `inline_levels`
+// launches the level kernels directly instead of through the cached graph
+// (used while a stream capture is recording).
+void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, bool x_zero,
+                  bool inline_levels = false);
 // Scale, level sets, launch shapes and upload for F->F already factored.
 silu_status finish_setup(silu_ilu F);
 

@@ -104,7 +104,8 @@ __global__ void k_givens(int j, int m, double* H, double* cs, double* sn, double
   H[(j + 1) * m + j] = 0.0;
   g[j + 1] = -s * g[j];
   g[j] = c * g[j];
-  *res = fabs(g[j + 1]);
+  res[0] = fabs(g[j + 1]);
+  res[1] = b;  // h_{j+1,j}: zero means the Krylov space is exhausted
 }
 
 // Every block solves the small triangle (redundantly, same order) and then
