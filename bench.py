@@ -177,6 +177,22 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_max(value: float, dist, device) -> float:
+    """Max of a per-rank number over all ranks (identity without a process group)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(step_bytes: int, steps: int, world: int, max_ms: float) -> float:
+    """Replicas: every rank moves step_bytes per step; the job's rate is all
+    ranks' bytes over the slowest rank's time."""
+    return step_bytes * steps * world / (max_ms * 1e-3) / 1e9
+
+
 def build_workload():
     import synth
     A = synth.cutcell7(EDGE, seed=1)
@@ -313,11 +329,8 @@ def run_silu(args):
     ms = e0.elapsed_time(e1)
     prof = ctx.profile_read()
     clocks = sampler.stop()
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = step_bytes * args.steps * world / (ms * 1e-3) / 1e9
+    ms = reduce_max(ms, dist, "cuda")
+    value = whole_job_gbs(step_bytes, args.steps, world, ms)
 
     # roofline of the dominant kernel: the sweep SpMV (L_s and Utilde_s)
     nL, msL = prof["sweep_L"]
@@ -347,11 +360,8 @@ def run_silu(args):
     e3.record(stream)
     torch.cuda.synchronize()
     ms_e2e = e2.elapsed_time(e3)
-    if dist:
-        t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = step_bytes * args.steps * world / (ms_e2e * 1e-3) / 1e9
+    ms_e2e = reduce_max(ms_e2e, dist, "cuda")
+    e2e = whole_job_gbs(step_bytes, args.steps, world, ms_e2e)
 
     solve = None
     if not args.no_solve and rank == 0:

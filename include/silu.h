@@ -116,6 +116,14 @@ silu_status silu_ctx_launch_count(silu_ctx ctx, int64_t* launches);
  * of the synchronisation.  fgmres_solve performs this check itself.
  */
 silu_status silu_ctx_check(silu_ctx ctx);
+/*
+ * Self-test of the bounded-wait error path: one GPU thread waits, for at
+ * most timeout_ms (1..10000) of the device's global timer, on a device flag
+ * that nothing sets, then records the timeout in the context's error word
+ * and returns.  The next silu_ctx_check returns SILU_ERR_TIMEOUT; the context
+ * stays usable.  Nothing faults, traps or hangs.  Asynchronous.
+ */
+silu_status silu_ctx_selftest_timeout(silu_ctx ctx, int timeout_ms);
 /* Message of the last failed call on ctx ("" if none); valid until the next call. */
 const char* silu_last_error(silu_ctx ctx);
 /* Library version string. */

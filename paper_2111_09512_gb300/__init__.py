@@ -104,6 +104,7 @@ def load():
         "silu_ctx_profile_read": (i32, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(dbl)]),
         "silu_ctx_launch_count": (i32, [vp, ctypes.POINTER(i64)]),
         "silu_ctx_check": (i32, [vp]),
+        "silu_ctx_selftest_timeout": (i32, [vp, i32]),
         "silu_ilu_set_kernel": (i32, [vp, i32]),
         "silu_smooth_noalloc": (i32, [i32, vp, i64] + [vp] * 12 + [i32, i32]),
         "silu_batch_setup": (i32, [vp, i32, vp, vp, vp, vp, i32, dbl, i32, i32, i32, pvp]),
@@ -134,7 +135,7 @@ def exported_symbols():
             "silu_mat_destroy", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
-            "silu_ctx_launch_count", "silu_ctx_check", "silu_ilu_set_kernel", "silu_smooth_noalloc",
+            "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_smooth_noalloc",
             "silu_batch_setup", "silu_batch_info", "silu_batch_smooth", "silu_batch_fgmres", "silu_batch_destroy",
             "silu_ilu_autotune", "silu_server_create", "silu_server_submit", "silu_server_cancel",
             "silu_server_poll", "silu_server_stats", "silu_server_destroy"]
@@ -202,6 +203,10 @@ class Context:
     def check(self):
         """Synchronise and raise if a kernel's bounded wait gave up (SILU_ERR_TIMEOUT)."""
         _check(self.handle, load().silu_ctx_check(self.handle), "silu_ctx_check")
+
+    def selftest_timeout(self, timeout_ms: int = 50):
+        """Run a bounded GPU wait on a flag nothing sets (the next check() reports ERR_TIMEOUT)."""
+        _check(self.handle, load().silu_ctx_selftest_timeout(self.handle, timeout_ms), "silu_ctx_selftest_timeout")
 
     def launch_count(self) -> int:
         """Kernels this context has launched since it was created."""

@@ -499,8 +499,8 @@ silu_status silu_ctx_create(int device, void* cuda_stream, silu_ctx* out) {
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->pinned, 64 * sizeof(double));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->env.sms, cudaDevAttrMultiProcessorCount, device);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->env.err, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(c->env.err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->env.err, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->env.err, 0, 2 * sizeof(int));
     if (e == cudaSuccess) e = silu::staged_prepare();
     if (e != cudaSuccess) {
       delete c;
@@ -665,6 +665,20 @@ silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choic
   if (choice) *choice = best;
   if (ms_out) *ms_out = best_ms;
   return silu_ctx_check(ctx);
+}
+
+silu_status silu_ctx_selftest_timeout(silu_ctx ctx, int timeout_ms) {
+  if (!ctx || timeout_ms < 1 || timeout_ms > 10000) return SILU_ERR_INVALID_ARG;
+  silu_status ds = device_ok(ctx);
+  if (ds != SILU_OK) return ds;
+  try {
+    LAUNCH(ctx, SILU_K_ELEMENTWISE,
+           silu::launch_wait_flag(ctx->env.err + 1, (unsigned long long)timeout_ms * 1000000ull, ctx->env.err,
+                                  ctx->stream));
+  } catch (const CudaFail& f) {
+    return cuda_err(ctx, f.e, f.what);
+  }
+  return SILU_OK;
 }
 
 silu_status silu_ilu_set_kernel(silu_ilu F, int variant) {

@@ -79,8 +79,13 @@ bool make_tiles(const int64_t* rp, int64_t n, int lanes, int passes, std::vector
 // Device-side state shared by launches on one context.
 struct LaunchEnv {
   int sms = 0;          // multiprocessors of the device
-  int* err = nullptr;   // device error word: bit 0 = a bounded wait gave up
+  int* err = nullptr;   // err[0]: device error word (bit 0: a copy wait gave up,
+                        // bit 1: the self-test wait gave up); err[1]: a flag
+                        // that nothing sets (self-test)
 };
+
+// Self-test of the bounded-wait error path (one thread, no fault).
+cudaError_t launch_wait_flag(const int* flag, unsigned long long timeout_ns, int* err, cudaStream_t s);
 
 // Launch out/x = epilogue(c - T in) over all rows.  Vectors are row-major
 // with leading dimension ldx; the launch covers columns [0, R) of the

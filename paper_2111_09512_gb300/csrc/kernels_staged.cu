@@ -377,7 +377,24 @@ cudaError_t prepare_mode() {
   return e;
 }
 
+// Waits up to timeout_ns for *flag to become non-zero; nothing sets it, so
+// the wait runs out and the error word records it (bit 1).
+__global__ void k_wait_flag(const int* flag, unsigned long long timeout_ns, int* err) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned long long t0 = global_ns();
+  while (atomicAdd((int*)flag, 0) == 0)
+    if (global_ns() - t0 > timeout_ns) {
+      atomicOr(err, 2);
+      return;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_wait_flag(const int* flag, unsigned long long timeout_ns, int* err, cudaStream_t s) {
+  k_wait_flag<<<1, 32, 0, s>>>(flag, timeout_ns, err);
+  return cudaGetLastError();
+}
 
 cudaError_t staged_prepare() {
   cudaError_t e = prepare_mode<double, double, double>();

@@ -264,3 +264,24 @@ def test_fp32_27pt_error_and_staged_lanes(silu, ctx):
     err = relerr(host(x), want)
     print(f"27-point FP32 smoother (3,3) relative error vs FP64 oracle: {err:.3e}")
     assert err < 1e-5
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(silu, ctx):
+    """Failure detection without a fault: a GPU wait on a flag that nothing
+    sets gives up after its limit and records the timeout; the host reads
+    ERR_TIMEOUT, the error word is cleared, and the context keeps working."""
+    ctx.check()
+    ctx.selftest_timeout(50)
+    with pytest.raises(silu.SiluError) as e:
+        ctx.check()
+    assert e.value.status == silu.ERR_TIMEOUT
+    ctx.check()  # cleared
+    A = synth.cutcell7(12, seed=5)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+    _, S = oracle_scaled(A, "ilu0", 0.0, 0)
+    b = synth.rhs(n, 1, seed=6)
+    x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+    silu.ilu_smooth(F, x, dev(b), 2, 2)
+    ctx.check()
+    assert relerr(host(x), oracle.smooth(A, S, np.zeros((n, 1)), b, 2, 2)) < FP64_TOL

@@ -1,0 +1,54 @@
+"""The N > 1 path of bench.py on the CPU with two gloo ranks: each GPU runs an
+independent replica, the job's time is the slowest rank's, and the job's
+GB/s counts every rank's bytes; the reference arm does its work on rank 0
+only and the other ranks leave at once."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    local_ms = 10.0 + 5.0 * rank            # rank 1 is the slower replica
+    ms = bench.reduce_max(local_ms, dist, "cpu")
+    value = bench.whole_job_gbs(1_000_000_000, 4, world, ms)
+    with open(os.path.join(out_dir, f"r{rank}.txt"), "w") as f:
+        f.write(f"{ms} {value}\n")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time(tmp_path):
+    import torch.multiprocessing as mp
+    port = free_port()
+    mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    vals = [open(tmp_path / f"r{r}.txt").read().split() for r in range(2)]
+    for ms, value in vals:
+        assert float(ms) == 15.0
+        # 2 ranks x 4 steps x 1 GB over 15 ms
+        assert abs(float(value) - 2 * 4 * 1.0 / 0.015) < 1e-6
+
+
+def test_reference_arm_nonzero_rank_exits_without_work():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], env=env, capture_output=True, text=True, timeout=120)
+    assert p.returncode == 0
+    assert p.stdout.strip() == ""
