@@ -375,6 +375,9 @@ def run_silu(args):
     if not args.no_serve and rank == 0:
         serve = serving(silu, args)
 
+    p32 = poisson32(silu, ctx, torch) if rank == 0 else None
+    study = sweep_study(silu, ctx, torch) if (args.study and rank == 0) else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gbs, reps, t = oracle_rate(A, b_np, args.cpu_budget)
@@ -409,6 +412,10 @@ def run_silu(args):
             line["batch"] = batch
         if serve:
             line["serving"] = serve
+        if p32:
+            line["poisson32"] = p32
+        if study:
+            line["sweep_study"] = study
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -584,6 +591,80 @@ def serving(silu, args):
     return out
 
 
+def poisson32(silu, ctx, torch):
+    """7-point Poisson 32^3 (32,768 rows), ILU(0), 4 interleaved right-hand
+    sides U[-1,1] (seed 0): one smoother application (5+5 sweeps) against
+    one direct level-scheduled application.  L2-resident, so reported as time
+    and GB/s only, not as a fraction of HBM."""
+    import synth
+    A = synth.poisson7(32)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+    st = F.stats()
+    F.reserve(4, 0)
+    b = torch.from_numpy(synth.rhs(n, 4, seed=0)).cuda()
+    x = torch.zeros(n, 4, dtype=torch.float64, device="cuda")
+    out = {"workload": "poisson7-32^3 ILU(0), 4 RHS", "levels": st["levels_L"]}
+    nbytes = apply_bytes(n, len(A[1]), st["nnz_L"], st["nnz_U"], 4, 8, 5, 5)
+    for name, fn in (("smooth_5_5", lambda: silu.ilu_smooth(F, x, b, 5, 5)),
+                     ("direct", lambda: silu.direct_trisolve(F, x, b))):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(200):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 200
+        out[name] = {"us": round(1e3 * ms, 2)}
+        if name == "smooth_5_5":
+            out[name]["gbs"] = round(nbytes / (ms * 1e-3) / 1e9, 1)
+    out["speedup_smooth_vs_direct"] = round(out["direct"]["us"] / out["smooth_5_5"]["us"], 2)
+    return out
+
+
+def sweep_study(silu, ctx, torch):
+    """Cut-cell 128^3, ILUT(1e-3, 10), FP64, one right-hand side (seed 1):
+    for m = 1..20 sweeps on each factor, one smoother application from zero
+    with the row-scaled factors (the method), unscaled Jacobi and unscaled
+    plain Richardson; reports ||b - A x_m|| / ||b|| and the distance
+    ||x_m - x*|| / ||x*|| to the exact application x* (direct solves)."""
+    import numpy as np
+    import synth
+    import oracle
+    A = synth.cutcell7(EDGE, seed=1)
+    n = len(A[0]) - 1
+    bh = synth.rhs(n, 1, seed=1)
+    b = torch.from_numpy(bh).cuda()
+    out = {"workload": WORKLOAD.split(" smoother")[0], "sweeps": list(range(1, 21))}
+    xstar = None
+    for name, sc in (("row_scaled_richardson", silu.SCALE_ROW), ("unscaled_jacobi", silu.SCALE_NONE),
+                     ("unscaled_richardson", silu.SCALE_NONE_RICH)):
+        F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilut", TAU, FILL, scale=sc)
+        if xstar is None:
+            xs = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+            silu.direct_trisolve(F, xs, b)
+            xstar = xs.cpu().numpy()
+        rel, dist = [], []
+        for m in range(1, 21):
+            x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+            silu.ilu_smooth(F, x, b, m, m)
+            xh = x.cpu().numpy()
+            if not np.all(np.isfinite(xh)):
+                rel.append(None)
+                dist.append(None)
+                continue
+            r = oracle.residual(A, xh, bh)
+            rel.append(float(np.linalg.norm(r) / np.linalg.norm(bh)))
+            dist.append(float(np.linalg.norm(xh - xstar) / np.linalg.norm(xstar)))
+        out[name] = {"relres": [None if v is None else float(f"{v:.4e}") for v in rel],
+                     "dist_to_exact": [None if v is None else float(f"{v:.4e}") for v in dist]}
+        del F
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -595,6 +676,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--study", action="store_true", help="add the 1..20-sweep scaled/unscaled study")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-workers", type=int, default=4)
