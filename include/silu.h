@@ -230,12 +230,34 @@ silu_status silu_ilu_set_lanes(silu_ilu F, int lanes_L, int lanes_U, int lanes_A
 
 /*
  * Sweep kernel variant: 0 = automatic (the staged kernel for one right-hand
- * side, the lanes-per-row kernel otherwise), 1 = always the lanes-per-row
- * kernel, 2 = the staged kernel wherever it applies.  The staged kernel
+ * side, on a factor's length-sorted copy where one was made; the
+ * lanes-per-row kernel otherwise), 1 = always the lanes-per-row kernel, 2 =
+ * the staged kernel wherever it applies, rows in their natural order, 3 = as
+ * 2 but on the length-sorted copies where they exist.  The staged kernel
  * streams nnz-balanced row tiles of the factor into shared memory with bulk
- * asynchronous copies; it needs rows of at most 4088 entries.
+ * asynchronous copies; it needs rows of at most 416 entries.  A sorted copy
+ * keeps each row's entries in order, so with one lane per row variants 2 and
+ * 3 give the same bits.
  */
 silu_status silu_ilu_set_kernel(silu_ilu F, int variant);
+
+/*
+ * Storage layout of the sweep factors (no counterpart in the paper, whose
+ * performance model of Sec. 6.3 charges one read of each factor per sweep
+ * and no arithmetic).  The staged kernel gives each row of a 32-row warp
+ * tile one lane and spends, per tile, as many FP64 multiply-adds as the
+ * tile's longest row has entries; rows of uneven length (ILUT factors) waste
+ * some of that work.  At setup the library measures it for L_s (index 0) and
+ * the upper sweep factor (index 1): pad_natural[k] = FMA slots per stored
+ * entry with rows in their natural order, pad_sorted[k] = the same after
+ * sorting the rows of every 512-row window by length (row numbers then
+ * travel with each tile so results land in their rows).  A device copy in
+ * sorted order is kept where pad_natural >= 1.08 and sorting saves at least
+ * 0.05 of it; in_use[k] = 1 when the current variant sweeps that copy.
+ * Pads are 0 for an empty factor or one with a row too long to stage.
+ * Works on host-only contexts (in_use = 0 there).  Any pointer may be NULL.
+ */
+silu_status silu_ilu_layout(silu_ilu F, double* pad_natural, double* pad_sorted, int32_t* in_use);
 
 /*
  * Batches of independent systems (many pressure solves of uneven size).

@@ -106,6 +106,7 @@ def load():
         "silu_ctx_check": (i32, [vp]),
         "silu_ctx_selftest_timeout": (i32, [vp, i32]),
         "silu_ilu_set_kernel": (i32, [vp, i32]),
+        "silu_ilu_layout": (i32, [vp, vp, vp, vp]),
         "silu_smooth_noalloc": (i32, [i32, vp, i64] + [vp] * 12 + [i32, i32]),
         "silu_batch_setup": (i32, [vp, i32, vp, vp, vp, vp, i32, dbl, i32, i32, i32, pvp]),
         "silu_batch_info": (i32, [vp, ctypes.POINTER(i32), vp, pvp]),
@@ -135,7 +136,8 @@ def exported_symbols():
             "silu_mat_destroy", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
-            "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_smooth_noalloc",
+            "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_layout",
+            "silu_smooth_noalloc",
             "silu_batch_setup", "silu_batch_info", "silu_batch_smooth", "silu_batch_fgmres", "silu_batch_destroy",
             "silu_ilu_autotune", "silu_server_create", "silu_server_submit", "silu_server_cancel",
             "silu_server_poll", "silu_server_stats", "silu_server_destroy"]
@@ -309,8 +311,18 @@ class ILU:
         _check(self.ctx.handle, load().silu_ilu_reserve(self.handle, nrhs, restart), "silu_ilu_reserve")
 
     def set_kernel(self, variant: int):
-        """0 automatic, 1 lanes-per-row kernel, 2 staged (bulk-copy) kernel where it applies."""
+        """0 automatic, 1 lanes-per-row kernel, 2 staged (bulk-copy) kernel where it applies (natural
+        row order), 3 staged kernel on the length-sorted copies where they exist."""
         _check(self.ctx.handle, load().silu_ilu_set_kernel(self.handle, variant), "silu_ilu_set_kernel")
+
+    def layout(self):
+        """FMA slots per entry of one-lane-per-row tiles, natural and length-sorted rows, for
+        (L_s, upper factor), and whether the current variant sweeps a sorted copy."""
+        nat, srt = np.zeros(2), np.zeros(2)
+        use = np.zeros(2, np.int32)
+        _check(self.ctx.handle, load().silu_ilu_layout(self.handle, _ptr(nat), _ptr(srt), _ptr(use)),
+               "silu_ilu_layout")
+        return {"pad_natural": nat, "pad_sorted": srt, "in_use": use.astype(bool)}
 
     def autotune(self, sweeps_L: int = 3, sweeps_U: int = 3):
         """Time the candidate launch shapes of the sweep kernels, keep the fastest; (choice, ms)."""

@@ -49,6 +49,91 @@ cudaError_t upload_csr(const silu::Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& 
   return e;
 }
 
+cudaError_t upload_sorted(const Csr& T, bool fp32, SortedBufs& b, DevCsr& d, cudaStream_t s) {
+  d.srp = nullptr;
+  d.sci = nullptr;
+  d.sva = nullptr;
+  d.perm = nullptr;
+  d.stiles = nullptr;
+  d.nstiles = 0;
+  d.use_sorted = false;
+  std::vector<int64_t> srp;
+  std::vector<int32_t> sci, perm;
+  std::vector<double> sva;
+  if (!silu::make_sorted(T.rp.data(), T.ci.data(), T.va.data(), T.n, srp, sci, sva, perm)) {
+    b.rp.release();
+    b.ci.release();
+    b.va.release();
+    b.perm.release();
+    b.tiles.release();
+    return cudaSuccess;
+  }
+  Csr S;
+  S.n = T.n;
+  S.rp.swap(srp);
+  S.ci.swap(sci);
+  S.va.swap(sva);
+  DevCsr sd;
+  cudaError_t e = upload_csr(S, fp32, b.rp, b.ci, b.va, b.tiles, sd, s);
+  std::vector<int> tl;
+  if (e == cudaSuccess && !silu::make_tiles(S.rp.data(), S.n, 1, 1, tl)) return cudaSuccess;
+  if (e == cudaSuccess) e = upload(b.tiles, tl.data(), tl.size(), s);
+  if (e == cudaSuccess) e = b.perm.ensure(sizeof(int32_t) * (perm.size() + silu::kCsrPad));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.perm.p, 0, b.perm.bytes, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b.perm.p, perm.data(), sizeof(int32_t) * perm.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  d.srp = sd.rp;
+  d.sci = sd.ci;
+  d.sva = sd.va;
+  d.perm = b.perm.as<int>();
+  d.stiles = b.tiles.as<int4>();
+  d.nstiles = (int)(tl.size() / 4);
+  d.use_sorted = true;
+  return cudaSuccess;
+}
+
+namespace {
+
+// Re-apply a launch shape kept from before an upload: tiles for g lanes per
+// row and rl rows per lane, gather width, sorted-copy choice.
+cudaError_t keep_shape(const Csr& h, DBuf& tiles, DevCsr& T, const DevCsr& old, cudaStream_t s) {
+  T.chunk = old.chunk;
+  T.use_sorted = T.nstiles > 0 && old.use_sorted;
+  if (old.tile_lanes == T.tile_lanes && old.tile_passes == T.tile_passes) return cudaSuccess;
+  std::vector<int> tl;
+  if (!silu::make_tiles(h.rp.data(), h.n, old.tile_lanes, old.tile_passes, tl)) return cudaSuccess;
+  cudaError_t e = upload(tiles, tl.data(), tl.size(), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) {
+    T.tiles = tiles.as<int4>();
+    T.ntiles = (int)(tl.size() / 4);
+    T.tile_lanes = old.tile_lanes;
+    T.tile_passes = old.tile_passes;
+  }
+  return e;
+}
+
+}  // namespace
+
+cudaError_t upload_factors(silu_ilu F) {
+  cudaStream_t s = F->ctx->stream;
+  const bool f32 = F->prec == SILU_FP32;
+  const Csr& Ut = (F->scale == SILU_SCALE_ROW) ? F->Us : F->F.U;
+  const bool had = F->dL.rp != nullptr;
+  const DevCsr oldL = F->dL, oldU = F->dU;
+  F->ws.drop_graphs();  // captured launches refer to the shapes and arrays replaced here
+  F->config_gen++;
+  cudaError_t e = upload_csr(F->F.L, f32, F->L_rp, F->L_ci, F->L_va, F->L_tiles, F->dL, s);
+  if (e == cudaSuccess) e = upload_csr(Ut, f32, F->U_rp, F->U_ci, F->U_va, F->U_tiles, F->dU, s);
+  if (e == cudaSuccess) e = upload_sorted(F->F.L, f32, F->Lsort, F->dL, s);
+  if (e == cudaSuccess) e = upload_sorted(Ut, f32, F->Usort, F->dU, s);
+  if (e == cudaSuccess && had) e = keep_shape(F->F.L, F->L_tiles, F->dL, oldL, s);
+  if (e == cudaSuccess && had) e = keep_shape(Ut, F->U_tiles, F->dU, oldU, s);
+  return e;
+}
+
 silu_status device_ok(silu_ctx ctx) {
   if (!ctx) return SILU_ERR_INVALID_ARG;
   if (ctx->device < 0) return set_err(ctx, SILU_ERR_NO_DEVICE, "host-only context");
@@ -127,13 +212,17 @@ cudaError_t ensure_direct(silu_ilu F) {
 
 
 // One sweep-shaped launch: the staged kernel for a single right-hand side
-// when the matrix has a tile partition (and the variant allows it), else the
-// lanes-per-row kernel.
+// when the matrix has a tile partition (and the variant allows it), on the
+// length-sorted copy when that is selected, else the lanes-per-row kernel.
 cudaError_t sweep_launch(silu_ilu F, const DevCsr& T, silu::Mode mode, int R, int lanes, int ldx, const void* c,
                          const void* in, void* out, const double* dinv, double* x, int epi) {
   cudaStream_t s = F->ctx->stream;
-  if (R == 1 && ldx == 1 && T.ntiles > 0 && F->variant != 1)
-    return silu::launch_sweep_staged(T, mode, F->ctx->env, c, in, out, dinv, x, epi, s);
+  if (R == 1 && ldx == 1 && T.ntiles > 0 && F->variant != 1) {
+    if (F->variant == 0) return silu::launch_sweep_staged(T, mode, F->ctx->env, c, in, out, dinv, x, epi, s);
+    DevCsr t = T;  // variant 2: natural row order; 3: the sorted copy where there is one
+    t.use_sorted = F->variant == 3 && T.nstiles > 0;
+    return silu::launch_sweep_staged(t, mode, F->ctx->env, c, in, out, dinv, x, epi, s);
+  }
   return silu::launch_sweep(T, mode, R, lanes, ldx, c, in, out, dinv, x, epi, s);
 }
 
@@ -461,13 +550,21 @@ silu_status finish_setup(silu_ilu F) {
   F->autoL = pick_lanes(F->F.L);
   F->autoU = pick_lanes(Ut);
   F->autoA = pick_lanes(F->A->A);
+  {
+    const Csr* fac[2] = {&F->F.L, &Ut};
+    std::vector<int32_t> perm;
+    std::vector<int64_t> srp;
+    for (int k = 0; k < 2; ++k) {
+      F->pad_nat[k] = silu::tile_pad(fac[k]->rp.data(), fac[k]->n);
+      silu::window_sort(fac[k]->rp.data(), fac[k]->n, perm, srp);
+      F->pad_sorted[k] = silu::tile_pad(srp.data(), fac[k]->n);
+    }
+  }
   if (ctx->device >= 0) {
     silu_status ds = device_ok(ctx);
     if (ds != SILU_OK) return ds;
     cudaStream_t s = ctx->stream;
-    const bool f32 = F->prec == SILU_FP32;
-    cudaError_t e = upload_csr(F->F.L, f32, F->L_rp, F->L_ci, F->L_va, F->L_tiles, F->dL, s);
-    if (e == cudaSuccess) e = upload_csr(Ut, f32, F->U_rp, F->U_ci, F->U_va, F->U_tiles, F->dU, s);
+    cudaError_t e = upload_factors(F);
     if (e == cudaSuccess) e = upload(F->d_dinv, F->dinv.data(), F->dinv.size(), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_err(ctx, e, "upload of the factors");
@@ -587,6 +684,8 @@ cudaError_t retile(const Csr& h, DBuf& tiles, DevCsr& T, int g, int rl, cudaStre
 
 // variant 2: staged kernel with `lanes` lanes per row (0 = from the mean row
 // length) and `passes` rows per lane (0 = automatic), gather width `chunk`;
+// variant 3: staged kernel on the length-sorted copies (where they exist;
+// one lane per row), gather width `chunk`;
 // variant 1: lanes-per-row kernel with `lanes` lanes.
 struct TuneCandidate {
   int variant, lanes, passes, chunk;
@@ -594,7 +693,7 @@ struct TuneCandidate {
 
 const TuneCandidate kTune[] = {{2, 0, 0, 16}, {2, 0, 0, 8}, {2, 1, 1, 16}, {2, 1, 2, 16}, {2, 1, 4, 16},
                                {2, 1, 4, 8},  {2, 2, 1, 16}, {2, 4, 1, 16}, {1, 2, 0, 16}, {1, 4, 0, 16},
-                               {1, 8, 0, 16}};
+                               {1, 8, 0, 16}, {3, 1, 1, 16}, {3, 1, 1, 8}};
 
 }  // namespace
 
@@ -621,8 +720,11 @@ silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choic
     CK(cudaEventCreate(&e1));
     CK(ensure_vectors(F, 1));
     const int ncand = (int)(sizeof(kTune) / sizeof(kTune[0]));
+    const bool have_sorted = F->dL.nstiles > 0 || F->dU.nstiles > 0;
     auto apply = [&](const TuneCandidate& c) {
       F->variant = c.variant;
+      F->dL.use_sorted = c.variant == 3 && F->dL.nstiles > 0;
+      F->dU.use_sorted = c.variant == 3 && F->dU.nstiles > 0;
       if (c.variant == 1) {
         F->lanesL = F->lanesU = c.lanes;
       } else {
@@ -636,6 +738,7 @@ silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choic
       }
     };
     for (int k = 0; k < ncand; ++k) {
+      if (kTune[k].variant == 3 && !have_sorted) continue;
       apply(kTune[k]);
       CK(cudaMemsetAsync(x.p, 0, sizeof(double) * n, s));
       smooth_chunk(F, x.as<double>(), b.as<double>(), 1, 1, 0, sweeps_L, sweeps_U, false);
@@ -683,10 +786,24 @@ silu_status silu_ctx_selftest_timeout(silu_ctx ctx, int timeout_ms) {
 
 silu_status silu_ilu_set_kernel(silu_ilu F, int variant) {
   if (!F) return SILU_ERR_INVALID_ARG;
-  if (variant < 0 || variant > 2) return set_err(F->ctx, SILU_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+  if (variant < 0 || variant > 3) return set_err(F->ctx, SILU_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
   F->variant = variant;
   F->ws.drop_graphs();
   F->config_gen++;
+  return SILU_OK;
+}
+
+silu_status silu_ilu_layout(silu_ilu F, double* pad_natural, double* pad_sorted, int32_t* in_use) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  const DevCsr* d[2] = {&F->dL, &F->dU};
+  for (int k = 0; k < 2; ++k) {
+    if (pad_natural) pad_natural[k] = F->pad_nat[k];
+    if (pad_sorted) pad_sorted[k] = F->pad_sorted[k];
+    if (in_use) {
+      const bool have = F->ctx->device >= 0 && d[k]->nstiles > 0;
+      in_use[k] = have && ((F->variant == 0 && d[k]->use_sorted) || F->variant == 3) ? 1 : 0;
+    }
+  }
   return SILU_OK;
 }
 
@@ -793,11 +910,8 @@ silu_status ilu_refactor(silu_ilu F, const double* new_val) {
       silu_status ds = device_ok(ctx);
       if (ds != SILU_OK) return ds;
       cudaStream_t s = ctx->stream;
-      const bool f32 = F->prec == SILU_FP32;
-      const silu::Csr& Ut = (F->scale == SILU_SCALE_ROW) ? F->Us : F->F.U;
       cudaError_t e = upload(F->A->va, A.va.data(), A.va.size(), s);
-      if (e == cudaSuccess) e = upload_csr(F->F.L, f32, F->L_rp, F->L_ci, F->L_va, F->L_tiles, F->dL, s);
-      if (e == cudaSuccess) e = upload_csr(Ut, f32, F->U_rp, F->U_ci, F->U_va, F->U_tiles, F->dU, s);
+      if (e == cudaSuccess) e = upload_factors(F);
       if (e == cudaSuccess) e = upload(F->d_dinv, F->dinv.data(), F->dinv.size(), s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return cuda_err(ctx, e, "upload of the refactored factors");

@@ -49,6 +49,16 @@ struct DevCsr {
   // is used then)
   int4* tiles = nullptr;
   int ntiles = 0;
+  // length-sorted copy for the staged kernel (rows of each kSortWindow-row
+  // window in descending length, perm = their row numbers); used when
+  // use_sorted, with one lane per row
+  int* srp = nullptr;
+  int* sci = nullptr;
+  void* sva = nullptr;
+  int* perm = nullptr;
+  int4* stiles = nullptr;
+  int nstiles = 0;
+  bool use_sorted = false;
   int tile_lanes = 1;  // lanes per row in the staged kernel (1, 2 or 4)
   int tile_passes = 1; // rows per lane in a tile (1, 2 or 4; only with one lane per row)
   int chunk = 16;      // entries gathered per lane before the FMAs (8 or 16)
@@ -69,6 +79,27 @@ int staged_lanes(const int64_t* rp, int64_t n);
 // Rows per lane with one lane per row: 4 for rows of about 3 entries, 2 up
 // to about 6, else 1 (so that a tile's bulk copies stay a few KB).
 int staged_passes(const int64_t* rp, int64_t n, int lanes);
+
+// Rows of every kSortWindow consecutive rows are sorted by length for the
+// sorted copy; it is made when tiles of consecutive rows would spend more
+// than kSortPadMin FMA slots per entry and sorting removes at least
+// kSortGain of them.
+constexpr int kSortWindow = 512;
+constexpr double kSortPadMin = 1.08;
+constexpr double kSortGain = 0.05;
+
+// FMA slots per stored entry of one-lane-per-row tiles of a row pointer: a
+// tile costs 32 lanes times its longest row.  0 when some row is too long.
+double tile_pad(const int64_t* rp, int64_t n);
+// Rows of each kSortWindow-row window in descending length (stable): perm[s]
+// is the original row of stored row s, srp the sorted row pointer.
+void window_sort(const int64_t* rp, int64_t n, std::vector<int32_t>& perm, std::vector<int64_t>& srp);
+// The sorted copy is made for tile_pad values natural -> sorted when this holds.
+bool sorting_pays(double natural, double sorted);
+// Length-sorted copy of a CSR matrix (host): returns false when it would not
+// pay (see above).
+bool make_sorted(const int64_t* rp, const int32_t* ci, const double* va, int64_t n, std::vector<int64_t>& srp,
+                 std::vector<int32_t>& sci, std::vector<double>& sva, std::vector<int32_t>& perm);
 
 // Build the warp-tile descriptors of a CSR row pointer (host), four ints per
 // tile, for `lanes` lanes per row and `passes` rows per lane (32 * passes /

@@ -110,6 +110,11 @@ struct Workspace {
   DBuf V, Z, w, H, cs, sn, g, yk, part0, part1, scal;
 };
 
+// Device arrays of a length-sorted copy of a factor (staged kernel only).
+struct SortedBufs {
+  DBuf rp, ci, va, perm, tiles;
+};
+
 struct silu_ilu_s {
   silu_ctx ctx = nullptr;
   silu_mat A = nullptr;
@@ -123,8 +128,10 @@ struct silu_ilu_s {
   std::vector<double> dinv;
   std::vector<int32_t> levL, levU, levLptr, levLrows, levUptr, levUrows;
   int32_t nlevL = 0, nlevU = 0;
-  // device: sweep factors
+  // device: sweep factors, and their length-sorted copies where those pay
   DBuf L_rp, L_ci, L_va, L_tiles, U_rp, U_ci, U_va, U_tiles, d_dinv;
+  SortedBufs Lsort, Usort;
+  double pad_nat[2] = {0.0, 0.0}, pad_sorted[2] = {0.0, 0.0};  // L_s, upper sweep factor
   DevCsr dL, dU;
   // device: FP64 L_s and Utilde_s for the direct path (aliases of dL/dU when possible)
   DBuf L64_va, S_rp, S_ci, S_va, S_tiles, levLrows_d, levUrows_d;
@@ -216,6 +223,12 @@ cudaError_t upload(DBuf& b, const T* src, size_t count, cudaStream_t s) {
 
 cudaError_t upload_csr(const Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& va, DBuf& tiles, DevCsr& d,
                        cudaStream_t s);
+// Length-sorted copy of T for the staged kernel (silu::make_sorted); clears
+// the copy in d when it would not pay.  use_sorted is set when one is made.
+cudaError_t upload_sorted(const Csr& T, bool fp32, SortedBufs& b, DevCsr& d, cudaStream_t s);
+// Upload L_s and the upper sweep factor of F with their sorted copies,
+// keeping the launch shapes chosen earlier (autotuner, variant).
+cudaError_t upload_factors(silu_ilu F);
 silu_status device_ok(silu_ctx ctx);
 cudaError_t ensure_vectors(silu_ilu F, int nrhs);
 cudaError_t ensure_krylov(silu_ilu F, int m);

@@ -10,10 +10,14 @@
 //
 // Work is cut into warp tiles of consecutive rows: 32 rows (one per lane),
 // or 16 / 8 with two / four lanes sharing a long row, or 64 / 128 with one
-// lane taking two / four short rows in turn.
+// lane taking two / four short rows in turn.  When row lengths vary, a second
+// copy of the factor stores the rows of every 512-row window sorted by length
+// (with their row numbers), so a warp's rows are about equally long and few
+// FMA slots are spent on padding.
 // Every warp walks its own fixed sequence of tiles with its own two-stage
 // shared-memory ring: lane 0 issues three bulk asynchronous copies per tile
-// (values, column indices, row pointers) that complete on the stage's
+// (values, column indices, row pointers; a fourth with the row numbers of a
+// sorted copy) that complete on the stage's
 // mbarrier, marked evict-first in L2; the warp computes one tile while the
 // next one lands.  Warps never wait for each other, so their gather and FMA
 // phases interleave on the SM.  A lane's accumulator starts at c_i and takes
@@ -22,6 +26,7 @@
 // they stay resident in L2 from one sweep to the next.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <vector>
 
@@ -54,6 +59,54 @@ bool make_tiles(const int64_t* rp, int64_t n, int lanes, int passes, std::vector
     desc.push_back((int)rp[r0]);
     desc.push_back((int)rp[r1]);
     r0 = r1;
+  }
+  return true;
+}
+
+double tile_pad(const int64_t* rp, int64_t n) {
+  std::vector<int> d;
+  if (n <= 0 || rp[n] == 0 || !make_tiles(rp, n, 1, 1, d)) return 0.0;
+  double slots = 0.0;
+  for (size_t t = 0; t < d.size(); t += 4) {
+    int64_t wmax = 0;
+    for (int64_t r = d[t]; r < d[t + 1]; ++r) wmax = std::max<int64_t>(wmax, rp[r + 1] - rp[r]);
+    slots += 32.0 * (double)wmax;
+  }
+  return slots / (double)rp[n];
+}
+
+void window_sort(const int64_t* rp, int64_t n, std::vector<int32_t>& perm, std::vector<int64_t>& srp) {
+  perm.resize((size_t)n);
+  for (int64_t w0 = 0; w0 < n; w0 += kSortWindow) {
+    const int64_t w1 = std::min<int64_t>(n, w0 + kSortWindow);
+    for (int64_t r = w0; r < w1; ++r) perm[(size_t)r] = (int32_t)r;
+    std::stable_sort(perm.begin() + w0, perm.begin() + w1,
+                     [rp](int32_t a, int32_t b) { return rp[a + 1] - rp[a] > rp[b + 1] - rp[b]; });
+  }
+  srp.assign((size_t)n + 1, 0);
+  for (int64_t s = 0; s < n; ++s) {
+    const int32_t r = perm[(size_t)s];
+    srp[(size_t)s + 1] = srp[(size_t)s] + (rp[r + 1] - rp[r]);
+  }
+}
+
+bool sorting_pays(double natural, double sorted) {
+  return natural >= kSortPadMin && sorted > 0.0 && natural - sorted >= kSortGain;
+}
+
+bool make_sorted(const int64_t* rp, const int32_t* ci, const double* va, int64_t n, std::vector<int64_t>& srp,
+                 std::vector<int32_t>& sci, std::vector<double>& sva, std::vector<int32_t>& perm) {
+  if (n <= 0 || rp[n] == 0) return false;
+  const double pad0 = tile_pad(rp, n);
+  if (pad0 < kSortPadMin) return false;
+  window_sort(rp, n, perm, srp);
+  if (!sorting_pays(pad0, tile_pad(srp.data(), n))) return false;
+  sci.resize((size_t)rp[n]);
+  sva.resize((size_t)rp[n]);
+  for (int64_t s = 0; s < n; ++s) {
+    const int32_t r = perm[(size_t)s];
+    std::copy(ci + rp[r], ci + rp[r + 1], sci.begin() + srp[(size_t)s]);
+    std::copy(va + rp[r], va + rp[r + 1], sva.begin() + srp[(size_t)s]);
   }
   return true;
 }
@@ -147,39 +200,47 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 // One stage: a 16-byte header (the tile descriptor, written by the issuing
-// lane), then values, column indices and row pointers as copied.
-template <class MT>
+// lane), then values, column indices and row pointers as copied, and, for a
+// length-sorted layout, the tile's row numbers in the vectors.
+template <class MT, int RL, bool PERM>
 struct StageLayout {
   static constexpr int kValAlign = 16 / (int)sizeof(MT);  // elements per 16 bytes
   static constexpr size_t kHdr = 16;
   static constexpr size_t kVal = sizeof(MT) * (kTileNnz + 8);
   static constexpr size_t kCol = sizeof(int) * (kTileNnz + 8);
-  static constexpr size_t kRp = sizeof(int) * (4 * kTileRows + 8);
-  static constexpr size_t kBytes = kHdr + kVal + kCol + kRp;  // all multiples of 16
+  static constexpr size_t kRp = sizeof(int) * (RL * kTileRows + 8);
+  static constexpr size_t kPerm = PERM ? sizeof(int) * (kTileRows + 8) : 0;
+  static constexpr size_t kBytes = kHdr + kVal + kCol + kRp + kPerm;  // all multiples of 16
 };
 
 // Issuing lane: record the descriptor d of a tile in the stage header and
-// issue its three copies into stage buffer `st`.  The header store precedes
-// the arrive on the stage's mbarrier, so waiters see it.
-template <class MT>
+// issue its copies into stage buffer `st` (three, or four with the row
+// numbers of a sorted layout).  The header store precedes the arrive on the
+// stage's mbarrier, so waiters see it.
+template <class MT, int RL, bool PERM>
 __device__ __forceinline__ void issue_tile(int4 d, unsigned char* st, uint64_t* bar, const int* __restrict__ rp,
-                                           const int* __restrict__ ci, const MT* __restrict__ va, uint64_t pol) {
-  using L = StageLayout<MT>;
+                                           const int* __restrict__ ci, const MT* __restrict__ va,
+                                           const int* __restrict__ perm, uint64_t pol) {
+  using L = StageLayout<MT, RL, PERM>;
   const int r0 = d.x, r1 = d.y, p0 = d.z, p1 = d.w;
   const int a0 = p0 & ~(L::kValAlign - 1), a1 = (p1 + L::kValAlign - 1) & ~(L::kValAlign - 1);
   const int c0 = p0 & ~3, c1 = (p1 + 3) & ~3;
   const int q0 = r0 & ~3, q1 = (r1 + 1 + 3) & ~3;
+  const int m1 = (r1 + 3) & ~3;
   const uint32_t bv = (uint32_t)(a1 - a0) * (uint32_t)sizeof(MT);
   const uint32_t bc = (uint32_t)(c1 - c0) * 4u;
   const uint32_t br = (uint32_t)(q1 - q0) * 4u;
+  const uint32_t bp = PERM ? (uint32_t)(m1 - q0) * 4u : 0u;
   *(int4*)st = d;
   fence_proxy_async();
-  mbar_expect_tx(bar, bv + bc + br);
+  mbar_expect_tx(bar, bv + bc + br + bp);
   if (bv) bulk_g2s(st + L::kHdr, va + a0, bv, bar, pol);
   if (bc) bulk_g2s(st + L::kHdr + L::kVal, ci + c0, bc, bar, pol);
   bulk_g2s(st + L::kHdr + L::kVal + L::kCol, rp + q0, br, bar, pol);
+  if (PERM && bp) bulk_g2s(st + L::kHdr + L::kVal + L::kCol + L::kRp, perm + q0, bp, bar, pol);
 }
 
+// t = c_row - (T in)_row, already formed by the accumulation
 template <class MT, class VI, class VO>
 __device__ __forceinline__ void epilogue(int epi, int row, MT t, const VI* in, VO* out, const double* dinv,
                                          double* x, uint64_t keep) {
@@ -238,13 +299,13 @@ __device__ __forceinline__ MT row_accumulate(const MT* sv, const int* sc, int le
   return acc;
 }
 
-template <class MT, class VI, class VO, int G, int CH, int RL>
+template <class MT, class VI, class VO, int G, int CH, int RL, bool PERM>
 __global__ void __launch_bounds__(kStagedThreads, 1)
     k_sweep_staged(int ntiles, const int4* __restrict__ tiles, const int* __restrict__ rp, const int* __restrict__ ci,
-                   const MT* __restrict__ va, const VI* __restrict__ c, const VI* __restrict__ in,
-                   VO* __restrict__ out, const double* __restrict__ dinv, double* __restrict__ x, int epi,
-                   int* __restrict__ err) {
-  using L = StageLayout<MT>;
+                   const MT* __restrict__ va, const int* __restrict__ perm, const VI* __restrict__ c,
+                   const VI* __restrict__ in, VO* __restrict__ out, const double* __restrict__ dinv,
+                   double* __restrict__ x, int epi, int* __restrict__ err) {
+  using L = StageLayout<MT, RL, PERM>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kWarps][kWarpStages];
   const int tid = threadIdx.x;
@@ -263,7 +324,8 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
   if (lane == 0)
     for (int s = 0; s < kWarpStages; ++s) {
       const int t = gw + s * nw;
-      if (t < ntiles) issue_tile<MT>(__ldg(tiles + t), ring + s * L::kBytes, &full[warp][s], rp, ci, va, stream);
+      if (t < ntiles)
+        issue_tile<MT, RL, PERM>(__ldg(tiles + t), ring + s * L::kBytes, &full[warp][s], rp, ci, va, perm, stream);
     }
   int k = 0;
   for (int t = gw; t < ntiles; t += nw, ++k) {
@@ -289,6 +351,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     const MT* sv = (const MT*)(st + L::kHdr);
     const int* sc = (const int*)(st + L::kHdr + L::kVal);
     const int* sr = (const int*)(st + L::kHdr + L::kVal + L::kCol);
+    const int* sp = (const int*)(st + L::kHdr + L::kVal + L::kCol + L::kRp);  // sorted layout only
     const int r0 = d.x, r1 = d.y, p0 = d.z;
     const int q0 = r0 & ~3;
     const int a0 = p0 & ~(L::kValAlign - 1);
@@ -296,84 +359,95 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     const int sub = lane % G;
 #pragma unroll 1
     for (int pass = 0; pass < RL; ++pass) {
-      const int r = r0 + pass * (32 / G) + lane / G;
+      const int r = r0 + pass * (32 / G) + lane / G;  // stored row
       const bool act = r < r1;
       const int b = act ? sr[r - q0] : p0;
       const int len = act ? sr[r + 1 - q0] - b : 0;
+      const int o = (PERM && act) ? sp[r - q0] : r;  // the row's place in the vectors
       // c enters once per row, through the lane that writes the result
-      MT acc = (act && c && sub == 0) ? (MT)ld_keep(c + r, keep) : MT(0);
+      MT acc = (act && c && sub == 0) ? (MT)ld_keep(c + o, keep) : MT(0);
       if (epi == EPI_SPMV)
         acc = row_accumulate<MT, VI, false, G, CH>(sv + (b - a0), sc + (b - c0), len, sub, in, acc, keep);
       else
         acc = row_accumulate<MT, VI, true, G, CH>(sv + (b - a0), sc + (b - c0), len, sub, in, acc, keep);
       if (act && sub == 0) {
         if (epi == EPI_SPMV)
-          st_keep(out + r, (VO)acc, keep);
+          st_keep(out + o, (VO)acc, keep);
         else
-          epilogue<MT, VI, VO>(epi, r, acc, in, out, dinv, x, keep);
+          epilogue<MT, VI, VO>(epi, o, acc, in, out, dinv, x, keep);
       }
     }
     __syncwarp();
-    if (lane == 0 && tn < ntiles) issue_tile<MT>(dn, ring + s * L::kBytes, &full[warp][s], rp, ci, va, stream);
+    if (lane == 0 && tn < ntiles)
+      issue_tile<MT, RL, PERM>(dn, ring + s * L::kBytes, &full[warp][s], rp, ci, va, perm, stream);
   }
 }
 
-template <class MT, class VI, class VO, int G, int CH, int RL>
+template <class MT, class VI, class VO, int G, int CH, int RL, bool PERM>
 cudaError_t staged_attr() {
-  using L = StageLayout<MT>;
+  using L = StageLayout<MT, RL, PERM>;
   const size_t smem = (size_t)kWarps * kWarpStages * L::kBytes;
-  return cudaFuncSetAttribute(k_sweep_staged<MT, VI, VO, G, CH, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)smem);
+  return cudaFuncSetAttribute(k_sweep_staged<MT, VI, VO, G, CH, RL, PERM>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <class MT, class VI, class VO, int G, int CH, int RL>
+template <class MT, class VI, class VO, int G, int CH, int RL, bool PERM>
 cudaError_t staged_g(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
                      const double* dinv, double* x, int epi, cudaStream_t s) {
-  using L = StageLayout<MT>;
+  using L = StageLayout<MT, RL, PERM>;
   const size_t smem = (size_t)kWarps * kWarpStages * L::kBytes;
-  if (T.ntiles == 0) return cudaSuccess;
-  const int want = (T.ntiles + kWarps - 1) / kWarps;
+  const int nt = PERM ? T.nstiles : T.ntiles;
+  if (nt == 0) return cudaSuccess;
+  const int want = (nt + kWarps - 1) / kWarps;
   const int grid = want < env.sms ? want : env.sms;
-  k_sweep_staged<MT, VI, VO, G, CH, RL><<<grid, kStagedThreads, smem, s>>>(
-      T.ntiles, T.tiles, T.rp, T.ci, (const MT*)T.va, (const VI*)c, (const VI*)in, (VO*)out, dinv, x, epi, env.err);
+  if (PERM)
+    k_sweep_staged<MT, VI, VO, G, CH, RL, PERM><<<grid, kStagedThreads, smem, s>>>(
+        nt, T.stiles, T.srp, T.sci, (const MT*)T.sva, T.perm, (const VI*)c, (const VI*)in, (VO*)out, dinv, x, epi,
+        env.err);
+  else
+    k_sweep_staged<MT, VI, VO, G, CH, RL, PERM><<<grid, kStagedThreads, smem, s>>>(
+        nt, T.tiles, T.rp, T.ci, (const MT*)T.va, nullptr, (const VI*)c, (const VI*)in, (VO*)out, dinv, x, epi,
+        env.err);
   return cudaGetLastError();
 }
 
-template <class MT, class VI, class VO, int G, int RL>
+template <class MT, class VI, class VO, int G, int RL, bool PERM>
 cudaError_t staged_c(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
                      const double* dinv, double* x, int epi, cudaStream_t s) {
-  if (T.chunk == 8) return staged_g<MT, VI, VO, G, 8, RL>(T, env, c, in, out, dinv, x, epi, s);
-  return staged_g<MT, VI, VO, G, 16, RL>(T, env, c, in, out, dinv, x, epi, s);
+  if (T.chunk == 8) return staged_g<MT, VI, VO, G, 8, RL, PERM>(T, env, c, in, out, dinv, x, epi, s);
+  return staged_g<MT, VI, VO, G, 16, RL, PERM>(T, env, c, in, out, dinv, x, epi, s);
 }
 
 template <class MT, class VI, class VO>
 cudaError_t staged(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
                    const double* dinv, double* x, int epi, cudaStream_t s) {
+  if (T.use_sorted && T.nstiles > 0) return staged_c<MT, VI, VO, 1, 1, true>(T, env, c, in, out, dinv, x, epi, s);
   switch (T.tile_lanes) {
     case 1:
-      if (T.tile_passes == 4) return staged_c<MT, VI, VO, 1, 4>(T, env, c, in, out, dinv, x, epi, s);
-      if (T.tile_passes == 2) return staged_c<MT, VI, VO, 1, 2>(T, env, c, in, out, dinv, x, epi, s);
-      return staged_c<MT, VI, VO, 1, 1>(T, env, c, in, out, dinv, x, epi, s);
-    case 2: return staged_c<MT, VI, VO, 2, 1>(T, env, c, in, out, dinv, x, epi, s);
-    case 4: return staged_c<MT, VI, VO, 4, 1>(T, env, c, in, out, dinv, x, epi, s);
+      if (T.tile_passes == 4) return staged_c<MT, VI, VO, 1, 4, false>(T, env, c, in, out, dinv, x, epi, s);
+      if (T.tile_passes == 2) return staged_c<MT, VI, VO, 1, 2, false>(T, env, c, in, out, dinv, x, epi, s);
+      return staged_c<MT, VI, VO, 1, 1, false>(T, env, c, in, out, dinv, x, epi, s);
+    case 2: return staged_c<MT, VI, VO, 2, 1, false>(T, env, c, in, out, dinv, x, epi, s);
+    case 4: return staged_c<MT, VI, VO, 4, 1, false>(T, env, c, in, out, dinv, x, epi, s);
   }
   return cudaErrorInvalidValue;
 }
 
-template <class MT, class VI, class VO, int G, int RL>
+template <class MT, class VI, class VO, int G, int RL, bool PERM>
 cudaError_t prepare_shape() {
-  cudaError_t e = staged_attr<MT, VI, VO, G, 8, RL>();
-  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, G, 16, RL>();
+  cudaError_t e = staged_attr<MT, VI, VO, G, 8, RL, PERM>();
+  if (e == cudaSuccess) e = staged_attr<MT, VI, VO, G, 16, RL, PERM>();
   return e;
 }
 
 template <class MT, class VI, class VO>
 cudaError_t prepare_mode() {
-  cudaError_t e = prepare_shape<MT, VI, VO, 1, 1>();
-  if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 1, 2>();
-  if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 1, 4>();
-  if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 2, 1>();
-  if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 4, 1>();
+  cudaError_t e = prepare_shape<MT, VI, VO, 1, 1, false>();
+  if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 1, 2, false>();
+  if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 1, 4, false>();
+  if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 2, 1, false>();
+  if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 4, 1, false>();
+  if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 1, 1, true>();
   return e;
 }
 

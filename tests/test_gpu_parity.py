@@ -67,11 +67,12 @@ SMOOTH_CASES = [
 ]
 
 
-@pytest.mark.parametrize("variant", [1, 2], ids=["lanes", "staged"])
+@pytest.mark.parametrize("variant", [1, 2, 3], ids=["lanes", "staged", "sorted"])
 @pytest.mark.parametrize("case", SMOOTH_CASES, ids=[c[0] for c in SMOOTH_CASES])
 def test_smooth_fp64_matches_oracle(silu, ctx, case, variant):
     """Both sweep kernels: lanes-per-row (any R) and staged bulk-copy (R = 1;
-    with R > 1 the library uses the lanes kernel, covered again)."""
+    with R > 1 the library uses the lanes kernel, covered again), the staged
+    kernel also on the length-sorted factor copies where they exist."""
     name, gen, kind, tau, fill, nrhs, sweeps = case
     A = gen()
     n = len(A[0]) - 1
@@ -153,6 +154,69 @@ def test_direct_trisolve_matches_oracle(silu, ctx, case):
     x = dev(x0.copy())
     silu.direct_trisolve(F, x, dev(b))
     assert percol_relerr(host(x), want) < FP64_TOL
+
+
+SORTED_CASES = [
+    # rows not a multiple of the 512-row sort window; ILUT rows of uneven length
+    ("cutcell 33x31x17 ilut", lambda: synth.cutcell7(33, 31, 17, seed=2), "ilut", 1e-3, 10),
+    ("cutcell 41x37x23 ilut tight", lambda: synth.cutcell7(41, 37, 23, seed=6), "ilut", 1e-2, 6),
+    ("hex27 13x11x9 ilut", lambda: synth.hex27(13, 11, 9, seed=5), "ilut", 1e-3, 12),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", SORTED_CASES, ids=[c[0] for c in SORTED_CASES])
+def test_sorted_copy_gives_the_same_bits(silu, ctx, case, prec):
+    """The length-sorted factor copy keeps each row's entries in order, so
+    the staged kernel on it (variant 3) returns the same bits as on the
+    natural order (variant 2), FP64 and FP32; the FP64 result also matches
+    the oracle.  The automatic variant sweeps the sorted copy of L_s."""
+    name, gen, kind, tau, fill = case
+    A = gen()
+    n = len(A[0]) - 1
+    p = silu.FP32 if prec == "fp32" else silu.FP64
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), kind, tau, fill, prec=p)
+    lay = F.layout()
+    print(name, "pads natural", lay["pad_natural"], "sorted", lay["pad_sorted"], "in use", lay["in_use"])
+    assert lay["in_use"][0], lay
+    b = synth.rhs(n, 1, seed=31)
+    x0 = synth.rhs(n, 1, seed=32)
+    got = {}
+    for variant in (2, 3, 0):
+        F.set_kernel(variant)
+        for mL, mU in [(4, 3), (1, 1), (0, 2)]:
+            x = dev(x0.copy())
+            silu.ilu_smooth(F, x, dev(b), mL, mU)
+            ctx.check()
+            got[variant, mL, mU] = host(x)
+    for key, val in got.items():
+        assert np.array_equal(val, got[(2,) + key[1:]]), key
+    if p == silu.FP64:
+        _, S = oracle_scaled(A, kind, tau, fill)
+        for mL, mU in [(4, 3), (1, 1), (0, 2)]:
+            assert relerr(got[3, mL, mU], oracle.smooth(A, S, x0, b, mL, mU)) < FP64_TOL
+
+
+def test_sorted_copy_follows_refactor(silu, ctx):
+    """ilu_refactor re-uploads the factors with their sorted copies (the
+    27-point ILU(0) factors of a thin lattice have many short boundary rows)
+    and keeps the chosen variant; results match the oracle's factors of the
+    new values."""
+    A = synth.hex27(9, 7, 30, seed=3)
+    A2 = synth.hex27(9, 7, 30, seed=8)
+    assert np.array_equal(A[1], A2[1])
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+    F.set_kernel(3)
+    assert F.layout()["in_use"].all()
+    silu.ilu_refactor(F, A2[2])
+    assert F.layout()["in_use"].all()
+    _, S = oracle_scaled(A2, "ilu0", 0.0, 0)
+    b = synth.rhs(n, 1, seed=5)
+    x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+    silu.ilu_smooth(F, x, dev(b), 5, 5)
+    ctx.check()
+    assert relerr(host(x), oracle.smooth(A2, S, np.zeros((n, 1)), b, 5, 5)) < FP64_TOL
 
 
 def test_fp32_error_against_fp64_oracle(silu, ctx):

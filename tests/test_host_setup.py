@@ -159,3 +159,45 @@ def test_batch_factors_are_the_systems_factors(ctx):
                 assert np.all(np.abs(mine[2][seg] - theirs[2]) <= 1e-14 * np.abs(theirs[2]))
             assert np.allclose(ex["dinv"][r0:r1], OS.dinv, rtol=1e-14, atol=0)
         B.close()
+
+
+def _tile_slots_per_entry(rp, rows=32, cap=416):
+    """FMA slots per entry of one-lane-per-row warp tiles (32 rows, at most
+    `cap` entries per tile), each costing 32 times its longest row."""
+    n = len(rp) - 1
+    lens = np.diff(rp)
+    slots, r0 = 0, 0
+    while r0 < n:
+        r1 = r0
+        while r1 < n and r1 - r0 < rows and rp[r1 + 1] - rp[r0] <= cap:
+            r1 += 1
+        slots += 32 * int(lens[r0:r1].max())
+        r0 = r1
+    return slots / rp[-1]
+
+
+def _window_sorted_rp(rp, window=512):
+    lens = np.diff(rp)
+    order = np.concatenate([w0 + np.argsort(-lens[w0:w0 + window], kind="stable")
+                            for w0 in range(0, len(lens), window)])
+    return np.concatenate([[0], np.cumsum(lens[order])])
+
+
+def test_layout_pads(ctx):
+    """silu_ilu_layout's padding figures equal a direct count over the
+    exported factors; ILUT's uneven L rows get a sorted copy, Poisson's
+    uniform rows do not, and a host-only context sweeps nothing."""
+    for A, kind, tau, fill, sorted_L in ((synth.cutcell7(20, 18, 16, seed=1), "ilut", 1e-3, 10, True),
+                                         (synth.poisson7(17, 15, 13), "ilu0", 0.0, 0, False)):
+        F = silu.ILU(silu.Matrix(ctx, *A), kind, tau=tau, fill=fill)
+        lay = F.layout()
+        ex = F.export()
+        for k, fac in enumerate(("L", "Us")):
+            rp = ex[fac][0]
+            nat, srt = _tile_slots_per_entry(rp), _tile_slots_per_entry(_window_sorted_rp(rp))
+            assert lay["pad_natural"][k] == pytest.approx(nat, rel=1e-12)
+            assert lay["pad_sorted"][k] == pytest.approx(srt, rel=1e-12)
+            assert srt <= nat + 1e-12
+        pays = lay["pad_natural"][0] >= 1.08 and lay["pad_natural"][0] - lay["pad_sorted"][0] >= 0.05
+        assert pays == sorted_L
+        assert not lay["in_use"].any()
