@@ -230,10 +230,11 @@ silu_status silu_ilu_set_lanes(silu_ilu F, int lanes_L, int lanes_U, int lanes_A
 
 /*
  * Sweep kernel variant: 0 = automatic (the staged kernel for one right-hand
- * side, on a factor's length-sorted copy where one was made; the
- * lanes-per-row kernel otherwise), 1 = always the lanes-per-row kernel, 2 =
- * the staged kernel wherever it applies, rows in their natural order, 3 = as
- * 2 but on the length-sorted copies where they exist.  The staged kernel
+ * side, the lanes-per-row kernel otherwise), 1 = always the lanes-per-row
+ * kernel, 2 = the staged kernel wherever it applies, 3 = as 2 but on
+ * length-sorted copies of the factors (built on first selection, for the
+ * factors where silu_ilu_layout shows sorting pays; device memory for one
+ * more copy of those factors).  The staged kernel
  * streams nnz-balanced row tiles of the factor into shared memory with bulk
  * asynchronous copies; it needs rows of at most 416 entries.  A sorted copy
  * keeps each row's entries in order, so with one lane per row variants 2 and
@@ -251,9 +252,11 @@ silu_status silu_ilu_set_kernel(silu_ilu F, int variant);
  * the upper sweep factor (index 1): pad_natural[k] = FMA slots per stored
  * entry with rows in their natural order, pad_sorted[k] = the same after
  * sorting the rows of every 512-row window by length (row numbers then
- * travel with each tile so results land in their rows).  A device copy in
- * sorted order is kept where pad_natural >= 1.08 and sorting saves at least
- * 0.05 of it; in_use[k] = 1 when the current variant sweeps that copy.
+ * travel with each tile so results land in their rows).  Sorting pays where
+ * pad_natural >= 1.08 and it saves at least 0.05; variant 3 of
+ * silu_ilu_set_kernel (or the autotuner) then sweeps a sorted device copy,
+ * and in_use[k] = 1.  Fewer FMA slots do not always mean a faster sweep:
+ * lanes of one warp then gather from rows further apart.
  * Pads are 0 for an empty factor or one with a row too long to stage.
  * Works on host-only contexts (in_use = 0 there).  Any pointer may be NULL.
  */
@@ -303,6 +306,16 @@ silu_status silu_batch_fgmres(silu_batch B, double* x, const double* b, double t
  * time per application.  Blocks.
  */
 silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choice, double* ms);
+/*
+ * The autotuner's candidates and their times from the last silu_ilu_autotune
+ * on F: *count = number of candidates (0 before any tuning); for the first
+ * min(cap, *count) candidates, shape[4 k .. 4 k + 3] = {variant (1 lanes-per-
+ * row kernel, 2 staged kernel, 3 staged kernel on sorted copies), lanes per
+ * row (0 = from the mean row length), rows per lane (0 = automatic), gather
+ * width} and ms[k] = time per application (-1 for a candidate not run: a
+ * sorted-copy candidate when no factor has one).  shape and ms may be NULL.
+ */
+silu_status silu_ilu_tune_table(silu_ilu F, int cap, int32_t* shape, double* ms, int* count);
 void silu_batch_destroy(silu_batch B);
 
 /*

@@ -107,6 +107,7 @@ def load():
         "silu_ctx_selftest_timeout": (i32, [vp, i32]),
         "silu_ilu_set_kernel": (i32, [vp, i32]),
         "silu_ilu_layout": (i32, [vp, vp, vp, vp]),
+        "silu_ilu_tune_table": (i32, [vp, i32, vp, vp, vp]),
         "silu_smooth_noalloc": (i32, [i32, vp, i64] + [vp] * 12 + [i32, i32]),
         "silu_batch_setup": (i32, [vp, i32, vp, vp, vp, vp, i32, dbl, i32, i32, i32, pvp]),
         "silu_batch_info": (i32, [vp, ctypes.POINTER(i32), vp, pvp]),
@@ -136,7 +137,7 @@ def exported_symbols():
             "silu_mat_destroy", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
-            "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_layout",
+            "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_layout", "silu_ilu_tune_table",
             "silu_smooth_noalloc",
             "silu_batch_setup", "silu_batch_info", "silu_batch_smooth", "silu_batch_fgmres", "silu_batch_destroy",
             "silu_ilu_autotune", "silu_server_create", "silu_server_submit", "silu_server_cancel",
@@ -330,6 +331,17 @@ class ILU:
         _check(self.ctx.handle, load().silu_ilu_autotune(self.handle, sweeps_L, sweeps_U, ctypes.byref(ch),
                                                          ctypes.byref(ms)), "silu_ilu_autotune")
         return ch.value, ms.value
+
+    def tune_table(self):
+        """[(variant, lanes, passes, chunk, ms)] of the last autotune (ms -1: candidate not run)."""
+        cnt = ctypes.c_int(0)
+        _check(self.ctx.handle, load().silu_ilu_tune_table(self.handle, 0, 0, 0, ctypes.byref(cnt)),
+               "silu_ilu_tune_table")
+        shape = np.zeros(4 * cnt.value, np.int32)
+        ms = np.zeros(cnt.value)
+        _check(self.ctx.handle, load().silu_ilu_tune_table(self.handle, cnt.value, _ptr(shape), _ptr(ms),
+                                                           ctypes.byref(cnt)), "silu_ilu_tune_table")
+        return [tuple(int(v) for v in shape[4 * k:4 * k + 4]) + (float(ms[k]),) for k in range(cnt.value)]
 
     def set_lanes(self, lanes_L: int = 0, lanes_U: int = 0, lanes_A: int = 0):
         _check(self.ctx.handle, load().silu_ilu_set_lanes(self.handle, lanes_L, lanes_U, lanes_A),

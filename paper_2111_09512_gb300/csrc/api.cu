@@ -90,17 +90,15 @@ cudaError_t upload_sorted(const Csr& T, bool fp32, SortedBufs& b, DevCsr& d, cud
   d.perm = b.perm.as<int>();
   d.stiles = b.tiles.as<int4>();
   d.nstiles = (int)(tl.size() / 4);
-  d.use_sorted = true;
   return cudaSuccess;
 }
 
 namespace {
 
 // Re-apply a launch shape kept from before an upload: tiles for g lanes per
-// row and rl rows per lane, gather width, sorted-copy choice.
+// row and rl rows per lane, gather width.
 cudaError_t keep_shape(const Csr& h, DBuf& tiles, DevCsr& T, const DevCsr& old, cudaStream_t s) {
   T.chunk = old.chunk;
-  T.use_sorted = T.nstiles > 0 && old.use_sorted;
   if (old.tile_lanes == T.tile_lanes && old.tile_passes == T.tile_passes) return cudaSuccess;
   std::vector<int> tl;
   if (!silu::make_tiles(h.rp.data(), h.n, old.tile_lanes, old.tile_passes, tl)) return cudaSuccess;
@@ -117,6 +115,19 @@ cudaError_t keep_shape(const Csr& h, DBuf& tiles, DevCsr& T, const DevCsr& old, 
 
 }  // namespace
 
+cudaError_t ensure_sorted(silu_ilu F) {
+  if (F->sorted_ready) return cudaSuccess;
+  cudaStream_t s = F->ctx->stream;
+  const bool f32 = F->prec == SILU_FP32;
+  const Csr& Ut = (F->scale == SILU_SCALE_ROW) ? F->Us : F->F.U;
+  F->ws.drop_graphs();
+  F->config_gen++;
+  cudaError_t e = upload_sorted(F->F.L, f32, F->Lsort, F->dL, s);
+  if (e == cudaSuccess) e = upload_sorted(Ut, f32, F->Usort, F->dU, s);
+  if (e == cudaSuccess) F->sorted_ready = true;
+  return e;
+}
+
 cudaError_t upload_factors(silu_ilu F) {
   cudaStream_t s = F->ctx->stream;
   const bool f32 = F->prec == SILU_FP32;
@@ -127,8 +138,10 @@ cudaError_t upload_factors(silu_ilu F) {
   F->config_gen++;
   cudaError_t e = upload_csr(F->F.L, f32, F->L_rp, F->L_ci, F->L_va, F->L_tiles, F->dL, s);
   if (e == cudaSuccess) e = upload_csr(Ut, f32, F->U_rp, F->U_ci, F->U_va, F->U_tiles, F->dU, s);
-  if (e == cudaSuccess) e = upload_sorted(F->F.L, f32, F->Lsort, F->dL, s);
-  if (e == cudaSuccess) e = upload_sorted(Ut, f32, F->Usort, F->dU, s);
+  if (e == cudaSuccess && F->sorted_ready) {  // sorted copies in use: rebuild them from the new values
+    F->sorted_ready = false;
+    e = ensure_sorted(F);
+  }
   if (e == cudaSuccess && had) e = keep_shape(F->F.L, F->L_tiles, F->dL, oldL, s);
   if (e == cudaSuccess && had) e = keep_shape(Ut, F->U_tiles, F->dU, oldU, s);
   return e;
@@ -218,9 +231,9 @@ cudaError_t sweep_launch(silu_ilu F, const DevCsr& T, silu::Mode mode, int R, in
                          const void* in, void* out, const double* dinv, double* x, int epi) {
   cudaStream_t s = F->ctx->stream;
   if (R == 1 && ldx == 1 && T.ntiles > 0 && F->variant != 1) {
-    if (F->variant == 0) return silu::launch_sweep_staged(T, mode, F->ctx->env, c, in, out, dinv, x, epi, s);
-    DevCsr t = T;  // variant 2: natural row order; 3: the sorted copy where there is one
-    t.use_sorted = F->variant == 3 && T.nstiles > 0;
+    if (F->variant != 3 || T.nstiles == 0) return silu::launch_sweep_staged(T, mode, F->ctx->env, c, in, out, dinv, x, epi, s);
+    DevCsr t = T;  // variant 3: the length-sorted copy
+    t.use_sorted = true;
     return silu::launch_sweep_staged(t, mode, F->ctx->env, c, in, out, dinv, x, epi, s);
   }
   return silu::launch_sweep(T, mode, R, lanes, ldx, c, in, out, dinv, x, epi, s);
@@ -720,11 +733,12 @@ silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choic
     CK(cudaEventCreate(&e1));
     CK(ensure_vectors(F, 1));
     const int ncand = (int)(sizeof(kTune) / sizeof(kTune[0]));
-    const bool have_sorted = F->dL.nstiles > 0 || F->dU.nstiles > 0;
+    bool have_sorted = false;
+    for (int k = 0; k < 2; ++k) have_sorted = have_sorted || silu::sorting_pays(F->pad_nat[k], F->pad_sorted[k]);
+    if (have_sorted) CK(ensure_sorted(F));
+    have_sorted = F->dL.nstiles > 0 || F->dU.nstiles > 0;
     auto apply = [&](const TuneCandidate& c) {
       F->variant = c.variant;
-      F->dL.use_sorted = c.variant == 3 && F->dL.nstiles > 0;
-      F->dU.use_sorted = c.variant == 3 && F->dU.nstiles > 0;
       if (c.variant == 1) {
         F->lanesL = F->lanesU = c.lanes;
       } else {
@@ -737,6 +751,7 @@ silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choic
         F->dL.chunk = F->dU.chunk = c.chunk;
       }
     };
+    F->tune_ms.assign((size_t)ncand, -1.0);
     for (int k = 0; k < ncand; ++k) {
       if (kTune[k].variant == 3 && !have_sorted) continue;
       apply(kTune[k]);
@@ -750,6 +765,7 @@ silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choic
       float t = 0.f;
       CK(cudaEventElapsedTime(&t, e0, e1));
       const double per = (double)t / reps;
+      F->tune_ms[(size_t)k] = per;
       if (per < best_ms) {
         best_ms = per;
         best = k;
@@ -770,6 +786,22 @@ silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choic
   return silu_ctx_check(ctx);
 }
 
+silu_status silu_ilu_tune_table(silu_ilu F, int cap, int32_t* shape, double* ms, int* count) {
+  if (!F || cap < 0 || !count) return SILU_ERR_INVALID_ARG;
+  const int nc = (int)F->tune_ms.size();
+  *count = nc;
+  for (int k = 0; k < nc && k < cap; ++k) {
+    if (shape) {
+      shape[4 * k] = kTune[k].variant;
+      shape[4 * k + 1] = kTune[k].lanes;
+      shape[4 * k + 2] = kTune[k].passes;
+      shape[4 * k + 3] = kTune[k].chunk;
+    }
+    if (ms) ms[k] = F->tune_ms[(size_t)k];
+  }
+  return SILU_OK;
+}
+
 silu_status silu_ctx_selftest_timeout(silu_ctx ctx, int timeout_ms) {
   if (!ctx || timeout_ms < 1 || timeout_ms > 10000) return SILU_ERR_INVALID_ARG;
   silu_status ds = device_ok(ctx);
@@ -787,6 +819,12 @@ silu_status silu_ctx_selftest_timeout(silu_ctx ctx, int timeout_ms) {
 silu_status silu_ilu_set_kernel(silu_ilu F, int variant) {
   if (!F) return SILU_ERR_INVALID_ARG;
   if (variant < 0 || variant > 3) return set_err(F->ctx, SILU_ERR_INVALID_ARG, "variant must be 0, 1, 2 or 3");
+  if (variant == 3 && F->ctx->device >= 0) {
+    silu_status ds = device_ok(F->ctx);
+    if (ds != SILU_OK) return ds;
+    cudaError_t e = ensure_sorted(F);
+    if (e != cudaSuccess) return cuda_err(F->ctx, e, "upload of the sorted factor copies");
+  }
   F->variant = variant;
   F->ws.drop_graphs();
   F->config_gen++;
@@ -800,8 +838,7 @@ silu_status silu_ilu_layout(silu_ilu F, double* pad_natural, double* pad_sorted,
     if (pad_natural) pad_natural[k] = F->pad_nat[k];
     if (pad_sorted) pad_sorted[k] = F->pad_sorted[k];
     if (in_use) {
-      const bool have = F->ctx->device >= 0 && d[k]->nstiles > 0;
-      in_use[k] = have && ((F->variant == 0 && d[k]->use_sorted) || F->variant == 3) ? 1 : 0;
+      in_use[k] = F->ctx->device >= 0 && d[k]->nstiles > 0 && F->variant == 3 ? 1 : 0;
     }
   }
   return SILU_OK;

@@ -50,8 +50,9 @@ struct DevCsr {
   int4* tiles = nullptr;
   int ntiles = 0;
   // length-sorted copy for the staged kernel (rows of each kSortWindow-row
-  // window in descending length, perm = their row numbers); used when
-  // use_sorted, with one lane per row
+  // window in descending length, perm = their row numbers; nstiles = 0 when
+  // there is none); swept instead of the natural order when use_sorted, with
+  // one lane per row
   int* srp = nullptr;
   int* sci = nullptr;
   void* sva = nullptr;

@@ -131,7 +131,9 @@ struct silu_ilu_s {
   // device: sweep factors, and their length-sorted copies where those pay
   DBuf L_rp, L_ci, L_va, L_tiles, U_rp, U_ci, U_va, U_tiles, d_dinv;
   SortedBufs Lsort, Usort;
+  bool sorted_ready = false;  // sorted copies built (where they pay) for the current values
   double pad_nat[2] = {0.0, 0.0}, pad_sorted[2] = {0.0, 0.0};  // L_s, upper sweep factor
+  std::vector<double> tune_ms;  // per autotuner candidate, last tuning (-1: not run)
   DevCsr dL, dU;
   // device: FP64 L_s and Utilde_s for the direct path (aliases of dL/dU when possible)
   DBuf L64_va, S_rp, S_ci, S_va, S_tiles, levLrows_d, levUrows_d;
@@ -224,11 +226,13 @@ cudaError_t upload(DBuf& b, const T* src, size_t count, cudaStream_t s) {
 cudaError_t upload_csr(const Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& va, DBuf& tiles, DevCsr& d,
                        cudaStream_t s);
 // Length-sorted copy of T for the staged kernel (silu::make_sorted); clears
-// the copy in d when it would not pay.  use_sorted is set when one is made.
+// the copy in d when it would not pay.
 cudaError_t upload_sorted(const Csr& T, bool fp32, SortedBufs& b, DevCsr& d, cudaStream_t s);
 // Upload L_s and the upper sweep factor of F with their sorted copies,
 // keeping the launch shapes chosen earlier (autotuner, variant).
 cudaError_t upload_factors(silu_ilu F);
+// Build the length-sorted copies of the sweep factors (once; where they pay).
+cudaError_t ensure_sorted(silu_ilu F);
 silu_status device_ok(silu_ctx ctx);
 cudaError_t ensure_vectors(silu_ilu F, int nrhs);
 cudaError_t ensure_krylov(silu_ilu F, int m);

@@ -100,8 +100,31 @@ def test_autotune_keeps_results(silu, ctx):
     x1 = torch.zeros(B.n, dtype=torch.float64, device="cuda")
     silu.silu_batch_smooth(B, x1, b, 3, 3)
     choice, ms = B.factors.autotune(3, 3)
-    assert 0 <= choice < 11 and ms > 0
+    table = B.factors.tune_table()
+    run = [row[4] for row in table if row[4] >= 0]
+    assert 0 <= choice < len(table) and ms > 0 and table[choice][4] == ms == min(run)
     x2 = torch.zeros_like(x1)
     silu.silu_batch_smooth(B, x2, b, 3, 3)
+    ctx.check()
+    assert relerr(x2.cpu().numpy(), x1.cpu().numpy()) < 1e-12
+
+
+def test_autotune_tries_sorted_copies_where_they_pay(silu, ctx):
+    """ILUT factors of a cut-cell matrix have rows of uneven length, so the
+    autotuner also times the length-sorted copies (variant 3); whatever it
+    picks, results stay within FP64 rounding of the untuned ones."""
+    A = synth.cutcell7(40, 36, 30, seed=4)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilut", 1e-3, 10)
+    b = torch.from_numpy(synth.rhs(n, 1, seed=3)).cuda()
+    x1 = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+    silu.ilu_smooth(F, x1, b, 4, 4)
+    choice, ms = F.autotune(4, 4)
+    table = F.tune_table()
+    sorted_rows = [row for row in table if row[0] == 3]
+    assert sorted_rows and all(row[4] > 0 for row in sorted_rows)
+    assert table[choice][4] == ms == min(row[4] for row in table if row[4] >= 0)
+    x2 = torch.zeros_like(x1)
+    silu.ilu_smooth(F, x2, b, 4, 4)
     ctx.check()
     assert relerr(x2.cpu().numpy(), x1.cpu().numpy()) < 1e-12
