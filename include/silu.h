@@ -101,12 +101,26 @@ typedef enum {
 /*
  * Timing of the library's own kernels: with enable = 1 every later launch on
  * ctx is bracketed by two CUDA events recorded on the context's stream (the
- * launching stream); enable = 0 stops recording.  Enabling clears earlier
- * records.  silu_ctx_profile_read blocks on the stream and returns, for one
- * class, the launches recorded and the sum of their event-timed durations.
+ * launching stream), except that the consecutive L sweeps (and U sweeps) of
+ * one smoother application share one pair around all of them, so that no
+ * event separates one sweep from the next; enable = 0 stops recording.
+ * Enabling clears earlier records.  silu_ctx_profile_read blocks on the
+ * stream and returns, for one class, the launches recorded and the sum of
+ * their event-timed durations.
  */
 silu_status silu_ctx_profile(silu_ctx ctx, int enable);
 silu_status silu_ctx_profile_read(silu_ctx ctx, int kclass, int64_t* launches, double* total_ms);
+/*
+ * Sweep overlap (default on): each staged sweep launch is a programmatic
+ * dependent of the kernel before it in the stream, so its CTAs start as the
+ * previous kernel's CTAs leave the SMs and copy their first factor tiles
+ * (which no sweep writes) before waiting for that kernel to complete; every
+ * read or write of a vector still waits for it.  Results are the same bits
+ * either way.  Applies to launches (and graph captures) made after the call.
+ * No counterpart in the paper: it concerns only how consecutive sweeps are
+ * launched.
+ */
+silu_status silu_ctx_set_overlap(silu_ctx ctx, int enable);
 /* Kernels launched on ctx since creation (all classes; always counted). */
 silu_status silu_ctx_launch_count(silu_ctx ctx, int64_t* launches);
 /*

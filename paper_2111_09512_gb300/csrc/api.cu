@@ -301,6 +301,7 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
   const void* cvec = r_fused_to_c ? (const void*)bufC : nullptr;
   bool done = false;  // x already written
   if (mL >= 2) {
+    ProfRun run(F->ctx, SILU_K_SWEEP_L);
     const void* in = r;
     char* pp[2] = {bufP0, bufP1};
     for (int k = 2; k <= mL; ++k) {
@@ -346,6 +347,7 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
       cvec = bufC;
     }
     // v^1 = c; v^k = c - Utilde_s v^{k-1}
+    ProfRun run(F->ctx, SILU_K_SWEEP_U);
     const void* in = cvec;
     char* pp[2] = {bufP0, bufP1};
     for (int k = 2; k <= mU; ++k) {
@@ -371,6 +373,7 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
   } else {
     in = y;  // v^1 = y
   }
+  ProfRun run(F->ctx, SILU_K_SWEEP_U);
   for (int k = 2; k <= mU; ++k) {
     const bool last = (k == mU);
     char* out = (in == q[0]) ? q[1] : q[0];
@@ -641,6 +644,12 @@ silu_status silu_ctx_profile(silu_ctx ctx, int enable) {
   return SILU_OK;
 }
 
+silu_status silu_ctx_set_overlap(silu_ctx ctx, int enable) {
+  if (!ctx) return SILU_ERR_INVALID_ARG;
+  ctx->env.overlap = enable != 0;
+  return SILU_OK;
+}
+
 silu_status silu_ctx_profile_read(silu_ctx ctx, int kclass, int64_t* launches, double* total_ms) {
   if (!ctx || kclass < 0 || kclass >= SILU_K_NCLASS) return SILU_ERR_INVALID_ARG;
   int64_t cnt = 0;
@@ -656,7 +665,7 @@ silu_status silu_ctx_profile_read(silu_ctx ctx, int kclass, int64_t* launches, d
       e = cudaEventElapsedTime(&t, ctx->events[2 * k], ctx->events[2 * k + 1]);
       if (e != cudaSuccess) return cuda_err(ctx, e, "cudaEventElapsedTime");
       ms += t;
-      ++cnt;
+      cnt += ctx->rec_count[k];
     }
   }
   if (launches) *launches = cnt;

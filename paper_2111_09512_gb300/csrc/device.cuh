@@ -114,6 +114,8 @@ struct LaunchEnv {
   int* err = nullptr;   // err[0]: device error word (bit 0: a copy wait gave up,
                         // bit 1: the self-test wait gave up); err[1]: a flag
                         // that nothing sets (self-test)
+  bool overlap = true;  // staged sweeps launched as programmatic dependents of
+                        // the kernel before them (prologue overlaps its tail)
 };
 
 // Self-test of the bounded-wait error path (one thread, no fault).

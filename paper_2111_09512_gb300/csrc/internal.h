@@ -66,7 +66,10 @@ struct silu_ctx_s {
   bool profiling = false;
   std::vector<cudaEvent_t> events;  // pool; records use pairs (2k, 2k+1)
   std::vector<int> rec_class;       // class of record k
+  std::vector<int64_t> rec_count;   // launches covered by record k
   size_t nrec = 0;
+  int run_class = -1;               // class of the open run of launches (ProfRun), or -1
+  long run_rec = -1;                // its record once started
 };
 
 struct silu_mat_s {
@@ -171,30 +174,63 @@ struct CudaFail {
   } while (0)
 
 // Counts a kernel launch and, while profiling, brackets it with events.
+// Opens a record for a launch of class cls: its start event on the
+// context's stream.  Returns the record index, or -1 if no event is free.
+inline long prof_open(silu_ctx ctx, int cls) {
+  const size_t k = ctx->nrec;
+  if (ctx->events.size() < 2 * (k + 1)) {
+    for (int t = 0; t < 2; ++t) {
+      cudaEvent_t ev;
+      if (cudaEventCreate(&ev) != cudaSuccess) return -1;
+      ctx->events.push_back(ev);
+    }
+  }
+  if (ctx->rec_class.size() <= k) {
+    ctx->rec_class.resize(k + 1);
+    ctx->rec_count.resize(k + 1);
+  }
+  ctx->rec_class[k] = cls;
+  ctx->rec_count[k] = 1;
+  ctx->nrec = k + 1;
+  cudaEventRecord(ctx->events[2 * k], ctx->stream);
+  return (long)k;
+}
+
+// Times one launch (when profiling): start and end events around it, or,
+// inside a ProfRun of the same class, one more launch of the run's record.
 struct ProfScope {
   silu_ctx ctx;
-  size_t k = (size_t)-1;
+  long k = -1;
   ProfScope(silu_ctx c, int cls) : ctx(c) {
     ctx->launches++;
     if (!ctx->profiling) return;
-    k = ctx->nrec;
-    if (ctx->events.size() < 2 * (k + 1)) {
-      for (int t = 0; t < 2; ++t) {
-        cudaEvent_t ev;
-        if (cudaEventCreate(&ev) != cudaSuccess) {
-          k = (size_t)-1;
-          return;
-        }
-        ctx->events.push_back(ev);
-      }
+    if (ctx->run_class == cls) {
+      if (ctx->run_rec >= 0)
+        ctx->rec_count[(size_t)ctx->run_rec]++;
+      else
+        ctx->run_rec = prof_open(ctx, cls);
+      return;
     }
-    if (ctx->rec_class.size() <= k) ctx->rec_class.resize(k + 1);
-    ctx->rec_class[k] = cls;
-    ctx->nrec = k + 1;
-    cudaEventRecord(ctx->events[2 * k], ctx->stream);
+    k = prof_open(ctx, cls);
   }
   ~ProfScope() {
-    if (k != (size_t)-1) cudaEventRecord(ctx->events[2 * k + 1], ctx->stream);
+    if (k >= 0) cudaEventRecord(ctx->events[2 * (size_t)k + 1], ctx->stream);
+  }
+};
+
+// Consecutive launches of one class (the sweeps of one factor in one
+// smoother application) timed as one record: events between them would stop
+// each sweep from starting while the previous one drains.
+struct ProfRun {
+  silu_ctx ctx;
+  ProfRun(silu_ctx c, int cls) : ctx(c) {
+    ctx->run_class = cls;
+    ctx->run_rec = -1;
+  }
+  ~ProfRun() {
+    if (ctx->run_rec >= 0) cudaEventRecord(ctx->events[2 * (size_t)ctx->run_rec + 1], ctx->stream);
+    ctx->run_class = -1;
+    ctx->run_rec = -1;
   }
 };
 

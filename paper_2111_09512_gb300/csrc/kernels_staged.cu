@@ -161,6 +161,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
+// Programmatic dependent launch: let the next kernel in the stream be
+// scheduled now (its CTAs take SMs as ours leave), and wait here until the
+// kernel before this one has completed and its writes are visible.  Both are
+// no-ops for a kernel not launched as a programmatic dependent.
+__device__ __forceinline__ void grid_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_wait_prior() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -321,12 +330,16 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
   unsigned char* ring = smem + (size_t)warp * kWarpStages * L::kBytes;
   const uint64_t stream = policy_evict_first();
   const uint64_t keep = policy_evict_last();
+  grid_launch_dependents();
+  // the factor and its tiles are never written by a sweep: the first copies
+  // may start before the kernel that produced c and in has finished
   if (lane == 0)
     for (int s = 0; s < kWarpStages; ++s) {
       const int t = gw + s * nw;
       if (t < ntiles)
         issue_tile<MT, RL, PERM>(__ldg(tiles + t), ring + s * L::kBytes, &full[warp][s], rp, ci, va, perm, stream);
     }
+  grid_wait_prior();  // c, in, out and x below belong to the previous kernel until it completes
   int k = 0;
   for (int t = gw; t < ntiles; t += nw, ++k) {
     // the issuing lane fetches the descriptor of the tile it will issue next
@@ -399,16 +412,23 @@ cudaError_t staged_g(const DevCsr& T, const LaunchEnv& env, const void* c, const
   const int nt = PERM ? T.nstiles : T.ntiles;
   if (nt == 0) return cudaSuccess;
   const int want = (nt + kWarps - 1) / kWarps;
-  const int grid = want < env.sms ? want : env.sms;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(want < env.sms ? want : env.sms));
+  cfg.blockDim = dim3(kStagedThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = env.overlap ? 1 : 0;
   if (PERM)
-    k_sweep_staged<MT, VI, VO, G, CH, RL, PERM><<<grid, kStagedThreads, smem, s>>>(
-        nt, T.stiles, T.srp, T.sci, (const MT*)T.sva, T.perm, (const VI*)c, (const VI*)in, (VO*)out, dinv, x, epi,
-        env.err);
-  else
-    k_sweep_staged<MT, VI, VO, G, CH, RL, PERM><<<grid, kStagedThreads, smem, s>>>(
-        nt, T.tiles, T.rp, T.ci, (const MT*)T.va, nullptr, (const VI*)c, (const VI*)in, (VO*)out, dinv, x, epi,
-        env.err);
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, k_sweep_staged<MT, VI, VO, G, CH, RL, PERM>, nt, (const int4*)T.stiles,
+                              (const int*)T.srp, (const int*)T.sci, (const MT*)T.sva, (const int*)T.perm,
+                              (const VI*)c, (const VI*)in, (VO*)out, dinv, x, epi, env.err);
+  return cudaLaunchKernelEx(&cfg, k_sweep_staged<MT, VI, VO, G, CH, RL, PERM>, nt, (const int4*)T.tiles,
+                            (const int*)T.rp, (const int*)T.ci, (const MT*)T.va, (const int*)nullptr, (const VI*)c,
+                            (const VI*)in, (VO*)out, dinv, x, epi, env.err);
 }
 
 template <class MT, class VI, class VO, int G, int RL, bool PERM>

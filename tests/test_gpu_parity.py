@@ -351,3 +351,55 @@ def test_bounded_wait_reports_timeout_and_context_survives(silu, ctx):
     silu.ilu_smooth(F, x, dev(b), 2, 2)
     ctx.check()
     assert relerr(host(x), oracle.smooth(A, S, np.zeros((n, 1)), b, 2, 2)) < FP64_TOL
+
+
+def test_sweep_overlap_gives_the_same_bits(silu):
+    """Programmatic dependent launch of consecutive sweeps (the default) only
+    moves each kernel's first factor copies ahead of the previous kernel's
+    completion: smoother and FGMRES results (graphs included) are the same
+    bits with it off, and the smoother matches the oracle."""
+    A = synth.cutcell7(44, 40, 36, seed=12)
+    n = len(A[0]) - 1
+    b = synth.rhs(n, 1, seed=13)
+    x0 = synth.rhs(n, 1, seed=14)
+    out = {}
+    for overlap in (True, False):
+        c = silu.Context(0, torch.cuda.current_stream())
+        c.set_overlap(overlap)
+        F = silu.ilu_setup(c, silu.Matrix(c, *A), "ilut", 1e-3, 10)
+        x = dev(x0.copy())
+        silu.ilu_smooth(F, x, dev(b), 6, 5)
+        c.check()
+        xs = host(x)
+        xf = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st, its, rel = silu.fgmres_solve(F, xf, dev(b[:, 0].copy()), tol=1e-9, restart=20, maxit=400,
+                                         sweeps_L=3, sweeps_U=3, precond=silu.PRECOND_SWEEPS)
+        assert st == silu.OK
+        out[overlap] = (xs, host(xf), its)
+    assert np.array_equal(out[True][0], out[False][0])
+    assert np.array_equal(out[True][1], out[False][1]) and out[True][2] == out[False][2]
+    _, S = oracle_scaled(A, "ilut", 1e-3, 10)
+    assert relerr(out[True][0], oracle.smooth(A, S, x0, b, 6, 5)) < FP64_TOL
+
+
+def test_profile_records_sweep_runs(silu):
+    """Profiling counts every launch; the L sweeps (and the U sweeps) of one
+    application are timed as one run, so each class reports its launches
+    and a positive total time."""
+    c = silu.Context(0, torch.cuda.current_stream())
+    A = synth.cutcell7(30, 28, 26, seed=2)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(c, silu.Matrix(c, *A), "ilut", 1e-3, 10)
+    b = dev(synth.rhs(n, 1, seed=3))
+    x = dev(synth.rhs(n, 1, seed=4))
+    silu.ilu_smooth(F, x, b, 4, 5)
+    torch.cuda.synchronize()
+    l0 = c.launch_count()
+    c.profile(True)
+    for _ in range(3):
+        silu.ilu_smooth(F, x, b, 4, 5)
+    c.profile(False)
+    prof = c.profile_read()
+    assert c.launch_count() - l0 == 3 * (1 + 3 + 4)
+    assert prof["residual"][0] == 3 and prof["sweep_L"][0] == 9 and prof["sweep_U"][0] == 12
+    assert all(prof[k][1] > 0 for k in ("residual", "sweep_L", "sweep_U"))
