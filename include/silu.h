@@ -194,6 +194,10 @@ silu_status ilu_smooth(silu_ilu F, double* x, const double* b, int nrhs, int swe
  * x <- x + Utilde^{-1} D^{-1} L^{-1} (b - A x), by level-set scheduling
  * (Sec. 4: rows of one level are independent; one device-wide ordering point
  * per level).  Always FP64 arithmetic on the FP64 copy of the factors.
+ * The levels run as one captured CUDA graph per column block; the first one
+ * built on F is captured twice, with and without each level launched as a
+ * programmatic dependent of the previous one (see silu_ctx_set_overlap), and
+ * both are timed once; the faster form is kept for F (same bits either way).
  */
 silu_status direct_trisolve(silu_ilu F, double* x, const double* b, int nrhs);
 

@@ -387,14 +387,13 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
   }
 }
 
-// The level-scheduled substitutions of one column block, captured once into a
-// CUDA graph: one kernel node per level, each depending on the previous one
+// The level-scheduled substitutions of one column block captured into a CUDA
+// graph: one kernel node per level, each depending on the previous one
 // (Sec. 4: rows of a level are independent, levels are ordered).  The graph
 // works on the workspace vectors only: y (holding r on entry) becomes
-// L^{-1} r, c becomes Utilde^{-1} D^{-1} y.
-cudaGraphExec_t level_graph(silu_ilu F, int R, int ldx, size_t col) {
-  for (const LevelGraph& g : F->ws.graphs)
-    if (g.R == R && g.ldx == ldx && g.col == col) return g.exec;
+// L^{-1} r, c becomes Utilde^{-1} D^{-1} y.  overlap: each level launched as
+// a programmatic dependent of the one before.
+cudaGraphExec_t capture_levels(silu_ilu F, int R, int ldx, size_t col, bool overlap) {
   cudaStream_t cap = nullptr;
   CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   const double* dinv = F->d_dinv.as<double>();
@@ -407,11 +406,11 @@ cudaGraphExec_t level_graph(silu_ilu F, int R, int ldx, size_t col) {
   cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   for (int l = 0; e == cudaSuccess && l < F->nlevL; ++l) {
     const int b0 = F->levLptr[l], b1 = F->levLptr[l + 1];
-    e = silu::launch_level(F->dL64, rowsL + b0, b1 - b0, R, gL, ldx, y, dinv, c, nullptr, cap);
+    e = silu::launch_level(F->dL64, rowsL + b0, b1 - b0, R, gL, ldx, y, dinv, c, nullptr, overlap, cap);
   }
   for (int l = 0; e == cudaSuccess && l < F->nlevU; ++l) {
     const int b0 = F->levUptr[l], b1 = F->levUptr[l + 1];
-    e = silu::launch_level(F->dS64, rowsU + b0, b1 - b0, R, gU, ldx, c, dinv, nullptr, nullptr, cap);
+    e = silu::launch_level(F->dS64, rowsU + b0, b1 - b0, R, gU, ldx, c, dinv, nullptr, nullptr, overlap, cap);
   }
   const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
   if (e == cudaSuccess) e = e2;
@@ -420,6 +419,57 @@ cudaGraphExec_t level_graph(silu_ilu F, int R, int ldx, size_t col) {
   if (graph) cudaGraphDestroy(graph);
   cudaStreamDestroy(cap);
   CK(e);
+  return exec;
+}
+
+// Event-timed duration of one launch of a level graph (after one untimed
+// launch); it overwrites the workspace vectors y and c of its column block.
+float time_levels(silu_ilu F, cudaGraphExec_t exec) {
+  cudaStream_t s = F->ctx->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  CK(e);
+  return t;
+}
+
+// The level graph of one column block (cached).  Whether levels overlap is
+// decided once per factor object by timing both captures of the first graph
+// built: overlapping helps when levels are small and launch-bound, and can
+// cost when they are large; both give the same bits.  Building a graph
+// overwrites the workspace vectors y and c of its column block.
+cudaGraphExec_t level_graph(silu_ilu F, int R, int ldx, size_t col) {
+  for (const LevelGraph& g : F->ws.graphs)
+    if (g.R == R && g.ldx == ldx && g.col == col) return g.exec;
+  cudaGraphExec_t exec = nullptr;
+  if (F->ctx->env.overlap && F->level_overlap < 0) {
+    cudaGraphExec_t on = capture_levels(F, R, ldx, col, true);
+    cudaGraphExec_t off = nullptr;
+    float t_on = 0.f, t_off = 0.f;
+    try {
+      off = capture_levels(F, R, ldx, col, false);
+      t_on = time_levels(F, on);
+      t_off = time_levels(F, off);
+    } catch (const CudaFail&) {
+      cudaGraphExecDestroy(on);
+      if (off) cudaGraphExecDestroy(off);
+      throw;
+    }
+    F->level_overlap = t_on < t_off ? 1 : 0;
+    exec = F->level_overlap ? on : off;
+    cudaGraphExecDestroy(F->level_overlap ? off : on);
+  } else {
+    exec = capture_levels(F, R, ldx, col, F->ctx->env.overlap && F->level_overlap != 0);
+  }
   LevelGraph g;
   g.R = R;
   g.ldx = ldx;
@@ -438,6 +488,9 @@ void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
   double* y = F->ws.r.as<double>() + col;
   double* c = F->ws.c.as<double>() + col;
   const int gA = lanes_of(F->lanesA, F->autoA);
+  // built before y is written: building may run the graph on the workspace
+  cudaGraphExec_t exec = inline_levels ? nullptr : level_graph(F, R, ldx, col);
+  const bool overlap = F->ctx->env.overlap && F->level_overlap != 0;
   if (x_zero)
     LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_scale(n, R, ldx, b, false, nullptr, y, false, s));
   else
@@ -449,14 +502,15 @@ void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
     const int* rowsU = F->levUrows_d.as<int>();
     for (int l = 0; l < F->nlevL; ++l) {
       const int b0 = F->levLptr[l], b1 = F->levLptr[l + 1];
-      LAUNCH(F->ctx, SILU_K_LEVEL, silu::launch_level(F->dL64, rowsL + b0, b1 - b0, R, gL, ldx, y, dinv, c, nullptr, s));
+      LAUNCH(F->ctx, SILU_K_LEVEL, silu::launch_level(F->dL64, rowsL + b0, b1 - b0, R, gL, ldx, y, dinv, c, nullptr,
+                                                        overlap, s));
     }
     for (int l = 0; l < F->nlevU; ++l) {
       const int b0 = F->levUptr[l], b1 = F->levUptr[l + 1];
-      LAUNCH(F->ctx, SILU_K_LEVEL, silu::launch_level(F->dS64, rowsU + b0, b1 - b0, R, gU, ldx, c, dinv, nullptr, nullptr, s));
+      LAUNCH(F->ctx, SILU_K_LEVEL, silu::launch_level(F->dS64, rowsU + b0, b1 - b0, R, gU, ldx, c, dinv, nullptr, nullptr,
+                                                        overlap, s));
     }
   } else {
-    cudaGraphExec_t exec = level_graph(F, R, ldx, col);
     ProfScope ps(F->ctx, SILU_K_LEVEL);
     F->ctx->launches += F->nlevL + F->nlevU - 1;  // one count came from ProfScope
     CK(cudaGraphLaunch(exec, s));
@@ -1042,7 +1096,10 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
   try {
     CK(ensure_vectors(F, 1));
     CK(ensure_krylov(F, m));
-    if (precond == SILU_PRECOND_DIRECT) CK(ensure_direct(F));
+    if (precond == SILU_PRECOND_DIRECT) {
+      CK(ensure_direct(F));
+      level_graph(F, 1, 1, 0);  // settles the level launch form before iterations are captured
+    }
     Workspace& W = F->ws;
     double* V = W.V.as<double>();
     double* Z = W.Z.as<double>();

@@ -118,6 +118,17 @@ struct LaunchEnv {
                         // the kernel before them (prologue overlaps its tail)
 };
 
+#ifdef __CUDACC__
+// Programmatic dependent launch: let the next kernel in the stream be
+// scheduled now, and wait here until the kernel before this one has completed
+// and its writes are visible.  Both are no-ops for a kernel not launched as a
+// programmatic dependent.
+__device__ __forceinline__ void grid_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_wait_prior() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
 // Self-test of the bounded-wait error path (one thread, no fault).
 cudaError_t launch_wait_flag(const int* flag, unsigned long long timeout_ns, int* err, cudaStream_t s);
 
@@ -138,8 +149,9 @@ cudaError_t staged_prepare();
 // Level-scheduled substitution over the rows listed in rows[0..nrows).
 //  lower:  y_i -= sum_j T_ij y_j ; if c_out: c_out_i = dinv_i y_i
 //  upper:  y_i -= sum_j T_ij y_j ; if x: x_i += y_i
+// overlap: launched as a programmatic dependent of the previous level.
 cudaError_t launch_level(const DevCsr& T, const int* rows, int nrows, int R, int lanes, int ldx, double* y,
-                         const double* dinv, double* c_out, double* x, cudaStream_t s);
+                         const double* dinv, double* c_out, double* x, bool overlap, cudaStream_t s);
 
 // Elementwise helpers over n rows x R columns (leading dimension ldx).
 //  out(float or double) = scale ? dinv_i in : in      (in: double or float)

@@ -142,6 +142,7 @@ struct silu_ilu_s {
   DBuf L64_va, S_rp, S_ci, S_va, S_tiles, levLrows_d, levUrows_d;
   DevCsr dL64, dS64;
   bool direct_ready = false;
+  int level_overlap = -1;  // levels launched as programmatic dependents: -1 undecided, 0 no, 1 yes
   int lanesL = 0, lanesU = 0, lanesA = 0;
   int64_t config_gen = 0;  // bumped whenever a launch shape changes (captured graphs go stale)
   int variant = 0;  // 0 auto, 1 plain lanes-per-row kernel, 2 staged kernel where possible

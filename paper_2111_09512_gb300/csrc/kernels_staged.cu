@@ -161,15 +161,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
-// Programmatic dependent launch: let the next kernel in the stream be
-// scheduled now (its CTAs take SMs as ours leave), and wait here until the
-// kernel before this one has completed and its writes are visible.  Both are
-// no-ops for a kernel not launched as a programmatic dependent.
-__device__ __forceinline__ void grid_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void grid_wait_prior() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));

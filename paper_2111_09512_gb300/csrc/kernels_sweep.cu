@@ -146,6 +146,9 @@ __global__ void __launch_bounds__(kThreads) k_level(int nrows, const int* __rest
     p0 = __ldg(rp + row);
     p1 = __ldg(rp + row + 1);
   }
+  // the level's rows and pointers are fixed; y is not until the previous level is done
+  grid_wait_prior();
+  grid_launch_dependents();
   for (int p = p0 + lane; p < p1; p += G) {
     const double a = __ldg(va + p);
     const size_t j = (size_t)__ldg(ci + p) * (size_t)ldx;
@@ -170,21 +173,33 @@ __global__ void __launch_bounds__(kThreads) k_level(int nrows, const int* __rest
 
 template <int R>
 cudaError_t level_g(const DevCsr& T, const int* rows, int nrows, int lanes, int ldx, double* y, const double* dinv,
-                    double* c_out, double* x, cudaStream_t s) {
+                    double* c_out, double* x, bool overlap, cudaStream_t s) {
   const long long threads = (long long)nrows * lanes;
   const unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
   if (blocks == 0) return cudaSuccess;
   const double* va = (const double*)T.va;
+  // each level is a programmatic dependent of the one before: its CTAs load
+  // their rows' pointers while the previous level finishes
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = overlap ? 1 : 0;
+  const int* rp = T.rp;
+  const int* ci = T.ci;
   switch (lanes) {
-    case 1: k_level<R, 1><<<blocks, kThreads, 0, s>>>(nrows, rows, T.rp, T.ci, va, y, ldx, dinv, c_out, x); break;
-    case 2: k_level<R, 2><<<blocks, kThreads, 0, s>>>(nrows, rows, T.rp, T.ci, va, y, ldx, dinv, c_out, x); break;
-    case 4: k_level<R, 4><<<blocks, kThreads, 0, s>>>(nrows, rows, T.rp, T.ci, va, y, ldx, dinv, c_out, x); break;
-    case 8: k_level<R, 8><<<blocks, kThreads, 0, s>>>(nrows, rows, T.rp, T.ci, va, y, ldx, dinv, c_out, x); break;
-    case 16: k_level<R, 16><<<blocks, kThreads, 0, s>>>(nrows, rows, T.rp, T.ci, va, y, ldx, dinv, c_out, x); break;
-    case 32: k_level<R, 32><<<blocks, kThreads, 0, s>>>(nrows, rows, T.rp, T.ci, va, y, ldx, dinv, c_out, x); break;
-    default: return cudaErrorInvalidValue;
+    case 1: return cudaLaunchKernelEx(&cfg, k_level<R, 1>, nrows, rows, rp, ci, va, y, ldx, dinv, c_out, x);
+    case 2: return cudaLaunchKernelEx(&cfg, k_level<R, 2>, nrows, rows, rp, ci, va, y, ldx, dinv, c_out, x);
+    case 4: return cudaLaunchKernelEx(&cfg, k_level<R, 4>, nrows, rows, rp, ci, va, y, ldx, dinv, c_out, x);
+    case 8: return cudaLaunchKernelEx(&cfg, k_level<R, 8>, nrows, rows, rp, ci, va, y, ldx, dinv, c_out, x);
+    case 16: return cudaLaunchKernelEx(&cfg, k_level<R, 16>, nrows, rows, rp, ci, va, y, ldx, dinv, c_out, x);
+    case 32: return cudaLaunchKernelEx(&cfg, k_level<R, 32>, nrows, rows, rp, ci, va, y, ldx, dinv, c_out, x);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 template <class VI, class VO>
@@ -223,11 +238,11 @@ cudaError_t launch_sweep(const DevCsr& T, Mode mode, int R, int lanes, int ldx, 
 }
 
 cudaError_t launch_level(const DevCsr& T, const int* rows, int nrows, int R, int lanes, int ldx, double* y,
-                         const double* dinv, double* c_out, double* x, cudaStream_t s) {
+                         const double* dinv, double* c_out, double* x, bool overlap, cudaStream_t s) {
   switch (R) {
-    case 1: return level_g<1>(T, rows, nrows, lanes, ldx, y, dinv, c_out, x, s);
-    case 2: return level_g<2>(T, rows, nrows, lanes, ldx, y, dinv, c_out, x, s);
-    case 4: return level_g<4>(T, rows, nrows, lanes, ldx, y, dinv, c_out, x, s);
+    case 1: return level_g<1>(T, rows, nrows, lanes, ldx, y, dinv, c_out, x, overlap, s);
+    case 2: return level_g<2>(T, rows, nrows, lanes, ldx, y, dinv, c_out, x, overlap, s);
+    case 4: return level_g<4>(T, rows, nrows, lanes, ldx, y, dinv, c_out, x, overlap, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -354,10 +354,11 @@ def test_bounded_wait_reports_timeout_and_context_survives(silu, ctx):
 
 
 def test_sweep_overlap_gives_the_same_bits(silu):
-    """Programmatic dependent launch of consecutive sweeps (the default) only
-    moves each kernel's first factor copies ahead of the previous kernel's
-    completion: smoother and FGMRES results (graphs included) are the same
-    bits with it off, and the smoother matches the oracle."""
+    """Programmatic dependent launch of consecutive sweeps and levels (the
+    default) only moves each kernel's first factor copies or row pointers
+    ahead of the previous kernel's completion: smoother, FGMRES and direct
+    results (graphs included) are the same bits with it off, and match the
+    oracle."""
     A = synth.cutcell7(44, 40, 36, seed=12)
     n = len(A[0]) - 1
     b = synth.rhs(n, 1, seed=13)
@@ -375,11 +376,16 @@ def test_sweep_overlap_gives_the_same_bits(silu):
         st, its, rel = silu.fgmres_solve(F, xf, dev(b[:, 0].copy()), tol=1e-9, restart=20, maxit=400,
                                          sweeps_L=3, sweeps_U=3, precond=silu.PRECOND_SWEEPS)
         assert st == silu.OK
-        out[overlap] = (xs, host(xf), its)
+        xd = dev(x0.copy())
+        silu.direct_trisolve(F, xd, dev(b))
+        c.check()
+        out[overlap] = (xs, host(xf), its, host(xd))
     assert np.array_equal(out[True][0], out[False][0])
     assert np.array_equal(out[True][1], out[False][1]) and out[True][2] == out[False][2]
+    assert np.array_equal(out[True][3], out[False][3])
     _, S = oracle_scaled(A, "ilut", 1e-3, 10)
     assert relerr(out[True][0], oracle.smooth(A, S, x0, b, 6, 5)) < FP64_TOL
+    assert relerr(out[True][3], oracle.direct_apply(A, S, x0, b)) < FP64_TOL
 
 
 def test_profile_records_sweep_runs(silu):
