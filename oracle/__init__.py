@@ -7,7 +7,8 @@ Thomas et al., "Scaled ILU Smoothers for Navier-Stokes Pressure Projection"
 scaling (Eq. extractD, Eq. newD), the Richardson sweeps of Alg. ILUJac and
 Eq. richard, the direct triangular solves with level sets (Sec. 4), FGMRES
 with modified Gram-Schmidt (Sec. 6) and the diagnostics dep (Eq. depB) and
-NRBE (Eq. nbre).
+NRBE (Eq. nbre), the polynomial Gauss-Seidel smoother of Sec. 3.1 and the
+row/column (Ruiz) scaling of Eq. rowcolScale.
 
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
 import this package.  It shares no code with the CUDA library.  Each wrapper
@@ -81,6 +82,11 @@ def _load():
         "orc_dep_triangular": (dbl, [i64, vp, vp, vp, i32]),
         "orc_norm2_est": (dbl, [i64, vp, vp, vp, i32]),
         "orc_nrbe": (dbl, [i64, vp, vp, vp, dbl, vp, vp]),
+        "orc_poly_gs_lower": (i32, [i64, i32, vp, vp, vp, vp, i32, vp]),
+        "orc_poly_gs_upper_unit": (i32, [i64, i32, vp, vp, vp, vp, i32, vp]),
+        "orc_poly_gs_smooth": (i32, [i64, i32, vp, vp, vp, vp, vp, i32, i32, i32]),
+        "orc_ruiz_rowcol": (i32, [i64, vp, vp, vp, i32, dbl, vp, vp, vp, vp, vp]),
+        "orc_smooth_rowcol": (i32, [i64, i32] + [vp] * 13 + [i32, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -397,3 +403,85 @@ def nrbe(A, x, b, norm2A: float) -> float:
     x = np.ascontiguousarray(x, np.float64).reshape(n)
     b = np.ascontiguousarray(b, np.float64).reshape(n)
     return float(_load().orc_nrbe(n, _p(ap), _p(ac), _p(av), float(norm2A), _p(x), _p(b)))
+
+
+def poly_gs_lower(A, r, p: int):
+    """sum_{j=0}^{p} (-D^{-1} L)^j D^{-1} r, term by term (Sec. 3.1, polynomial Gauss-Seidel)."""
+    ap, ac, av = _csr(A)
+    n = len(ap) - 1
+    r = _vec(r, n)
+    z = np.empty_like(r)
+    st = _load().orc_poly_gs_lower(n, r.shape[1], _p(ap), _p(ac), _p(av), _p(r), int(p), _p(z))
+    if st:
+        raise OracleError(st, "poly_gs_lower")
+    return z
+
+
+def poly_gs_upper_unit(A, z, q: int):
+    """sum_{j=0}^{q} (-D^{-1} U)^j z, term by term (backward half of symmetric Gauss-Seidel)."""
+    ap, ac, av = _csr(A)
+    n = len(ap) - 1
+    z = _vec(z, n)
+    w = np.empty_like(z)
+    st = _load().orc_poly_gs_upper_unit(n, z.shape[1], _p(ap), _p(ac), _p(av), _p(z), int(q), _p(w))
+    if st:
+        raise OracleError(st, "poly_gs_upper_unit")
+    return w
+
+
+def poly_gs_smooth(A, x, b, pL: int, pU: int = 0, symmetric: bool = False):
+    """x + M^{-1}(b - A x) with M^{-1} the truncated Gauss-Seidel polynomial (returns a new array)."""
+    ap, ac, av = _csr(A)
+    n = len(ap) - 1
+    x = _vec(x, n).copy()
+    b = _vec(b, n)
+    st = _load().orc_poly_gs_smooth(n, b.shape[1], _p(ap), _p(ac), _p(av), _p(x), _p(b), int(pL), int(pU),
+                                    1 if symmetric else 0)
+    if st:
+        raise OracleError(st, "poly_gs_smooth")
+    return x
+
+
+@dataclass
+class RowCol:
+    """Row/column-scaled factors: L_s, Uhat_s = strict part of D_r U D_c (unit
+    diagonal), dr, dc, and the number of Ruiz steps taken."""
+    n: int
+    L: tuple
+    Us: tuple
+    dr: np.ndarray
+    dc: np.ndarray
+    steps: int
+
+
+def ruiz_rowcol(F: Factors, maxit: int = 20, tol: float = 1e-2) -> RowCol:
+    up, uc, uv = F.U
+    n = F.n
+    k = len(uc) - n
+    dr = np.empty(max(n, 1), np.float64)
+    dc = np.empty(max(n, 1), np.float64)
+    sp = np.empty(n + 1, np.int64)
+    sc = np.empty(max(k, 1), np.int32)
+    sv = np.empty(max(k, 1), np.float64)
+    st = _load().orc_ruiz_rowcol(n, _p(up), _p(uc), _p(uv), int(maxit), float(tol), _p(dr), _p(dc), _p(sp),
+                                 _p(sc), _p(sv))
+    if st < 0:
+        raise OracleError(-st, "ruiz_rowcol")
+    return RowCol(n, F.L, (sp, sc[:k], sv[:k]), dr[:n], dc[:n], int(st))
+
+
+def smooth_rowcol(A, S: RowCol, x, b, mL: int, mU: int):
+    """x + D_c Uhat^{-1} D_r L^{-1} (b - A x), each inverse by Richardson sweeps (new array)."""
+    ap, ac, av = _csr(A)
+    n = len(ap) - 1
+    x = _vec(x, n).copy()
+    b = _vec(b, n)
+    lp, lc, lv = _csr(S.L)
+    sp, sc, sv = _csr(S.Us)
+    dr = np.ascontiguousarray(S.dr, np.float64)
+    dc = np.ascontiguousarray(S.dc, np.float64)
+    st = _load().orc_smooth_rowcol(n, b.shape[1], _p(ap), _p(ac), _p(av), _p(lp), _p(lc), _p(lv), _p(sp),
+                                   _p(sc), _p(sv), _p(dr), _p(dc), _p(x), _p(b), int(mL), int(mU))
+    if st:
+        raise OracleError(st, "smooth_rowcol")
+    return x

@@ -1032,3 +1032,214 @@ double orc_nrbe(int64_t n, const int64_t* ap, const int32_t* ac, const double* a
   free(r);
   return out;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Polynomial Gauss-Seidel (Sec. 3.1: the Gauss-Seidel splitting M = D + L   */
+/* with (D + L)^{-1} written as (I + D^{-1} L)^{-1} D^{-1} and the inverse   */
+/* replaced by a truncated Neumann series)                                   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * z = sum_{j=0}^{p} (-D^{-1} T)^j s, where D = diag(A), T is the strictly
+ * lower (upper = 0) or strictly upper (upper != 0) part of A, and
+ * s = D^{-1} r (scale_first != 0) or s = r.  The terms are formed one after
+ * another, t_0 = s and t_j = -D^{-1} (T t_{j-1}), and summed in order
+ * j = 0..p.  p = -1 gives z = 0.  A zero or non-finite diagonal entry gives
+ * ORC_ZERO_PIVOT.
+ */
+static int poly_gs_terms(int64_t n, int R, const int64_t* ap, const int32_t* ac, const double* av, const double* r,
+                         int p, int upper, int scale_first, double* z) {
+  const size_t sz = (size_t)(n * R > 0 ? n * R : 1);
+  double* d = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* t = (double*)malloc(sz * sizeof(double));
+  double* u = (double*)malloc(sz * sizeof(double));
+  int st = ORC_NOMEM;
+  if (!d || !t || !u) goto done;
+  st = ORC_ZERO_PIVOT;
+  for (int64_t i = 0; i < n; ++i) {
+    d[i] = 0.0;
+    for (int64_t q = ap[i]; q < ap[i + 1]; ++q)
+      if (ac[q] == i) d[i] = d[i] + av[q];
+    if (d[i] == 0.0 || !isfinite(d[i])) goto done;
+  }
+  memset(z, 0, sizeof(double) * (size_t)(n * R));
+  if (p >= 0) {
+    for (int64_t i = 0; i < n; ++i)
+      for (int k = 0; k < R; ++k) t[i * R + k] = scale_first ? r[i * R + k] / d[i] : r[i * R + k];
+    for (int64_t e = 0; e < n * R; ++e) z[e] = z[e] + t[e];
+  }
+  for (int j = 1; j <= p; ++j) {
+    for (int64_t i = 0; i < n; ++i)
+      for (int k = 0; k < R; ++k) {
+        double s = 0.0;
+        for (int64_t q = ap[i]; q < ap[i + 1]; ++q) {
+          const int in_part = upper ? (ac[q] > i) : (ac[q] < i);
+          if (in_part) s = s + av[q] * t[(int64_t)ac[q] * R + k];
+        }
+        u[i * R + k] = -(s / d[i]);
+      }
+    memcpy(t, u, sizeof(double) * (size_t)(n * R));
+    for (int64_t e = 0; e < n * R; ++e) z[e] = z[e] + t[e];
+  }
+  st = ORC_OK;
+done:
+  free(d);
+  free(t);
+  free(u);
+  return st;
+}
+
+/* z = sum_{j=0}^{p} (-D^{-1} L)^j D^{-1} r: the forward Gauss-Seidel solve
+ * (D + L) z = r with its inverse truncated after p + 1 Neumann terms. */
+int orc_poly_gs_lower(int64_t n, int R, const int64_t* ap, const int32_t* ac, const double* av, const double* r,
+                      int p, double* z) {
+  return poly_gs_terms(n, R, ap, ac, av, r, p, 0, 1, z);
+}
+
+/* w = sum_{j=0}^{q} (-D^{-1} U)^j z: (I + D^{-1} U)^{-1} z truncated after q + 1
+ * terms, the backward half of symmetric Gauss-Seidel, whose splitting matrix
+ * is (D + L) D^{-1} (D + U), so that M^{-1} r = (I + D^{-1} U)^{-1} (D + L)^{-1} r. */
+int orc_poly_gs_upper_unit(int64_t n, int R, const int64_t* ap, const int32_t* ac, const double* av,
+                           const double* z, int q, double* w) {
+  return poly_gs_terms(n, R, ap, ac, av, z, q, 1, 0, w);
+}
+
+/*
+ * One polynomial Gauss-Seidel smoothing step (Eq. ILUsplit with M = D + L,
+ * or M = (D + L) D^{-1} (D + U) when symmetric != 0):
+ *   r = b - A x;  z = sum_{j<=pL} (-D^{-1} L)^j D^{-1} r;
+ *   symmetric: w = sum_{j<=pU} (-D^{-1} U)^j z, else w = z;  x <- x + w.
+ */
+int orc_poly_gs_smooth(int64_t n, int R, const int64_t* ap, const int32_t* ac, const double* av, double* x,
+                       const double* b, int pL, int pU, int symmetric) {
+  const size_t sz = (size_t)(n * R > 0 ? n * R : 1);
+  double* r = (double*)malloc(sz * sizeof(double));
+  double* z = (double*)malloc(sz * sizeof(double));
+  double* w = (double*)malloc(sz * sizeof(double));
+  int st = ORC_NOMEM;
+  if (!r || !z || !w) goto done;
+  orc_residual(n, R, ap, ac, av, x, b, r);
+  if ((st = orc_poly_gs_lower(n, R, ap, ac, av, r, pL, z))) goto done;
+  if (symmetric) {
+    if ((st = orc_poly_gs_upper_unit(n, R, ap, ac, av, z, pU, w))) goto done;
+  } else {
+    memcpy(w, z, sizeof(double) * (size_t)(n * R));
+  }
+  for (int64_t e = 0; e < n * R; ++e) x[e] = x[e] + w[e];
+  st = ORC_OK;
+done:
+  free(r);
+  free(z);
+  free(w);
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Row/column scaling of U (Sec. 5.1, Eq. rowcolScale: Richardson on the     */
+/* unit-diagonal D_r U D_c)                                                  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Ruiz equilibration of U (diagonal first in each row), then the unit
+ * diagonal.  Step k: with B = diag(rs) U diag(cs) (rs = cs = 1 at the start),
+ * every row i is divided by sqrt(max_j |b_ij|) and every column j by
+ * sqrt(max_i |b_ij|), both maxima taken on the same B; stop after `maxit`
+ * steps or when every row and column maximum of B lies within `tol` of 1.
+ * The column scaling is then dc = cs, and the row scaling is the one that
+ * makes the diagonal of D_r U D_c exactly one: dr_i = 1 / (u_ii dc_i).
+ * Writes dr, dc and Uhat_s = strict part of D_r U D_c (n+1 row pointers,
+ * nnz(U) - n entries): uhat_ij = (dr_i u_ij) dc_j.  Returns the number of
+ * Ruiz steps taken, or -ORC_ZERO_PIVOT / -ORC_NOMEM.
+ */
+int orc_ruiz_rowcol(int64_t n, const int64_t* up, const int32_t* uc, const double* uv, int maxit, double tol,
+                    double* dr, double* dc, int64_t* sp, int32_t* sc, double* sv) {
+  double* rs = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* rmax = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* cmax = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  int steps = 0;
+  if (!rs || !rmax || !cmax) {
+    steps = -ORC_NOMEM;
+    goto done;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (up[i + 1] <= up[i] || uc[up[i]] != i || uv[up[i]] == 0.0 || !isfinite(uv[up[i]])) {
+      steps = -ORC_ZERO_PIVOT;
+      goto done;
+    }
+    rs[i] = 1.0;
+    dc[i] = 1.0;
+  }
+  for (;;) {
+    for (int64_t i = 0; i < n; ++i) {
+      rmax[i] = 0.0;
+      cmax[i] = 0.0;
+    }
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = up[i]; p < up[i + 1]; ++p) {
+        const double b = fabs(rs[i] * uv[p] * dc[uc[p]]);
+        if (b > rmax[i]) rmax[i] = b;
+        if (b > cmax[uc[p]]) cmax[uc[p]] = b;
+      }
+    int equilibrated = 1;
+    for (int64_t i = 0; i < n; ++i)
+      if (fabs(1.0 - rmax[i]) > tol || fabs(1.0 - cmax[i]) > tol) equilibrated = 0;
+    if (equilibrated || steps >= maxit) break;
+    for (int64_t i = 0; i < n; ++i) {
+      rs[i] = rs[i] / sqrt(rmax[i]);
+      dc[i] = dc[i] / sqrt(cmax[i]);
+    }
+    ++steps;
+  }
+  sp[0] = 0;
+  for (int64_t i = 0, q = 0; i < n; ++i) {
+    dr[i] = 1.0 / (uv[up[i]] * dc[i]);
+    for (int64_t p = up[i] + 1; p < up[i + 1]; ++p) {
+      sc[q] = uc[p];
+      sv[q] = (dr[i] * uv[p]) * dc[uc[p]];
+      ++q;
+    }
+    sp[i + 1] = q;
+  }
+done:
+  free(rs);
+  free(rmax);
+  free(cmax);
+  return steps;
+}
+
+/*
+ * One smoother application with row/column scaling (Alg. ILUJac with
+ * Uhat = D_r U D_c, Eq. rowcolScale):  r = b - A x;  y = L^{-1} r by m_L
+ * sweeps;  w^k = D_r y - Uhat_s w^{k-1} for m_U sweeps from w^0 = 0;
+ * x <- x + D_c w (the final multiply of Alg. ILUJac).  m_U = 0 skips the
+ * upper factor (x <- x + y).
+ */
+int orc_smooth_rowcol(int64_t n, int R, const int64_t* ap, const int32_t* ac, const double* av, const int64_t* lp,
+                      const int32_t* lc, const double* lv, const int64_t* sp, const int32_t* sc, const double* sv,
+                      const double* dr, const double* dc, double* x, const double* b, int mL, int mU) {
+  const size_t sz = (size_t)(n * R > 0 ? n * R : 1);
+  double* r = (double*)malloc(sz * sizeof(double));
+  double* y = (double*)malloc(sz * sizeof(double));
+  double* w = (double*)malloc(sz * sizeof(double));
+  int st = ORC_NOMEM;
+  if (!r || !y || !w) goto done;
+  orc_residual(n, R, ap, ac, av, x, b, r);
+  if (mL > 0) {
+    if ((st = orc_richardson_lower(n, R, lp, lc, lv, r, mL, y))) goto done;
+  } else {
+    memcpy(y, r, sizeof(double) * (size_t)(n * R));
+  }
+  if (mU > 0) {
+    if ((st = orc_richardson_upper(n, R, sp, sc, sv, dr, y, mU, w))) goto done;
+    for (int64_t i = 0; i < n; ++i)
+      for (int k = 0; k < R; ++k) x[i * R + k] = x[i * R + k] + dc[i] * w[i * R + k];
+  } else {
+    for (int64_t e = 0; e < n * R; ++e) x[e] = x[e] + y[e];
+  }
+  st = ORC_OK;
+done:
+  free(r);
+  free(y);
+  free(w);
+  return st;
+}
