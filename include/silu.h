@@ -50,8 +50,21 @@ typedef enum {
   SILU_ERR_CANCELLED = 11     /* request cancelled before it started         */
 } silu_status;
 
-/* Incomplete factorisation kinds (Sec. 1, Sec. 4.2, Sec. 5.1 of the paper). */
-typedef enum { SILU_ILU0 = 0, SILU_ILUK = 1, SILU_ILUT = 2 } silu_kind;
+/*
+ * Factorisation kinds.  ILU0 / ILUK / ILUT are the incomplete factorisations
+ * of Sec. 1, Sec. 4.2 and Sec. 5.1.  GS and SGS are the Gauss-Seidel
+ * splittings of Sec. 3.1 written as factors, with A = D + L_A + U_A:
+ *  SILU_GS   M = D + L_A = (I + L_A D^{-1}) D: L_s = L_A D^{-1}, U = D.
+ *            ilu_smooth with sweeps_L = p + 1 and sweeps_U = 1 is the
+ *            polynomial Gauss-Seidel smoother of Sec. 3.1,
+ *            x <- x + sum_{j=0}^{p} (-D^{-1} L_A)^j D^{-1} (b - A x).
+ *  SILU_SGS  M = (D + L_A) D^{-1} (D + U_A) = (I + L_A D^{-1}) D (I + D^{-1} U_A):
+ *            the same with a backward half (symmetric Gauss-Seidel), row-
+ *            scaled upper factor Utilde_s = D^{-1} U_A.
+ * For GS / SGS `tau` and `fill` are ignored and direct_trisolve performs
+ * exact Gauss-Seidel.
+ */
+typedef enum { SILU_ILU0 = 0, SILU_ILUK = 1, SILU_ILUT = 2, SILU_GS = 3, SILU_SGS = 4 } silu_kind;
 
 /*
  * How the upper factor is iterated (Sec. 5.1-5.2):
@@ -62,8 +75,19 @@ typedef enum { SILU_ILU0 = 0, SILU_ILUK = 1, SILU_ILUT = 2 } silu_kind;
  *                        matrix G_U = I - D_U^{-1} U (Eq. LUiterMat).
  *  SILU_SCALE_NONE_RICH  raw U; plain Richardson v <- y - (U - I) v, which
  *                        the paper reports as failing to converge.
+ *  SILU_SCALE_ROWCOL     row/column scaling (Sec. 5.1, Eq. rowcolScale):
+ *                        Uhat = D_r U D_c with D_c from Ruiz equilibration
+ *                        of U (at most 20 steps, each dividing every row and
+ *                        column by the square root of its largest magnitude,
+ *                        stopping once all are within 1e-2 of one) and
+ *                        D_r = (D D_c)^{-1}, which makes diag(Uhat) = 1;
+ *                        Richardson w <- D_r y - Uhat_s w, then x += D_c w.
+ *                        Uhat = D_c^{-1} (D^{-1} U) D_c, so the smoother's
+ *                        result equals SILU_SCALE_ROW's up to rounding; the
+ *                        factor's departure from normality and the norms of
+ *                        the powers of Uhat_s differ (Table dep, Fig. Up).
  */
-typedef enum { SILU_SCALE_NONE = 0, SILU_SCALE_ROW = 1, SILU_SCALE_NONE_RICH = 2 } silu_scale;
+typedef enum { SILU_SCALE_NONE = 0, SILU_SCALE_ROW = 1, SILU_SCALE_NONE_RICH = 2, SILU_SCALE_ROWCOL = 3 } silu_scale;
 
 /* Precision of the stored factors and of the sweeps (the residual
  * r = b - A x, FGMRES and the solution vector stay FP64). */
@@ -173,8 +197,8 @@ silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int 
  * Numeric refactorisation with new values of A on the SAME pattern (nnz
  * values in the sorted, duplicate-free order of the silu_mat), reusing the
  * symbolic phase (Sec. 3.1: the pattern of the pressure matrix does not change
- * during a fluid step).  ILU0 and ILUK only (ILUT's pattern depends on the
- * values): SILU_ERR_INVALID_ARG otherwise.  Blocks.
+ * during a fluid step).  ILU0, ILUK, GS and SGS (ILUT's pattern depends on
+ * the values): SILU_ERR_INVALID_ARG otherwise.  Blocks.
  */
 silu_status ilu_refactor(silu_ilu F, const double* new_val);
 
@@ -234,6 +258,10 @@ silu_status silu_ilu_stats(silu_ilu F, int64_t* n, int64_t* nnz_L, int64_t* nnz_
  */
 silu_status silu_ilu_export(silu_ilu F, int64_t* Lp, int32_t* Lc, double* Lv, int64_t* Up, int32_t* Uc, double* Uv,
                             int64_t* Sp, int32_t* Sc, double* Sv, double* dinv, int32_t* levL, int32_t* levU);
+/* Row/column scaling only: D_c (n doubles) and the number of Ruiz steps
+ * taken (the Sv / dinv arrays of silu_ilu_export then hold Uhat_s and D_r).
+ * SILU_ERR_INVALID_ARG for another scaling.  Either pointer may be NULL. */
+silu_status silu_ilu_export_colscale(silu_ilu F, double* dcol, int32_t* ruiz_steps);
 /* Entry counts of U with diagonal (for export buffer sizing). */
 silu_status silu_ilu_export_sizes(silu_ilu F, int64_t* nnz_L, int64_t* nnz_Ufull, int64_t* nnz_Us);
 

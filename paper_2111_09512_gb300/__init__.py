@@ -28,9 +28,9 @@ LIB_PATH = os.path.join(_PKG, "libsilu.so")
 OK, ERR_INVALID_ARG, ERR_ZERO_PIVOT, ERR_NOT_CONVERGED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, WARN_DIVERGED, \
     ERR_NO_DEVICE, ERR_TOO_LARGE, ERR_BUSY, ERR_CANCELLED = range(12)
 # silu_kind
-ILU0, ILUK, ILUT = 0, 1, 2
+ILU0, ILUK, ILUT, GS, SGS = 0, 1, 2, 3, 4
 # silu_scale
-SCALE_NONE, SCALE_ROW, SCALE_NONE_RICH = 0, 1, 2
+SCALE_NONE, SCALE_ROW, SCALE_NONE_RICH, SCALE_ROWCOL = 0, 1, 2, 3
 # silu_prec
 FP64, FP32 = 0, 1
 # silu_precond
@@ -39,7 +39,7 @@ PRECOND_SWEEPS, PRECOND_DIRECT, PRECOND_NONE = 0, 1, 2
 K_RESIDUAL, K_SWEEP_L, K_SWEEP_U, K_LEVEL, K_KRYLOV, K_ELEMENTWISE = range(6)
 K_NAMES = ["residual", "sweep_L", "sweep_U", "level", "krylov", "elementwise"]
 
-KINDS = {"ilu0": ILU0, "iluk": ILUK, "ilut": ILUT}
+KINDS = {"ilu0": ILU0, "iluk": ILUK, "ilut": ILUT, "gs": GS, "sgs": SGS}
 
 _lib = None
 
@@ -98,6 +98,7 @@ def load():
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
         "silu_ilu_export": (i32, [vp] * 13),
         "silu_ilu_export_sizes": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "silu_ilu_export_colscale": (i32, [vp, vp, ctypes.POINTER(ctypes.c_int32)]),
         "silu_ilu_destroy": (None, [vp]),
         "silu_ilu_set_lanes": (i32, [vp, i32, i32, i32]),
         "silu_ctx_profile": (i32, [vp, i32]),
@@ -137,6 +138,7 @@ def exported_symbols():
     return ["silu_version", "silu_ctx_create", "silu_ctx_destroy", "silu_last_error", "silu_mat_create",
             "silu_mat_destroy", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
+            "silu_ilu_export_colscale",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
             "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_layout", "silu_ilu_tune_table", "silu_ctx_set_overlap",
             "silu_smooth_noalloc",
@@ -312,6 +314,14 @@ class ILU:
         return {"L": (Lp, Lc[:nl.value], Lv[:nl.value]), "U": (Up, Uc[:nf.value], Uv[:nf.value]),
                 "Us": (Sp, Sc[:ns.value], Sv[:ns.value]), "dinv": dinv[:n], "levL": levL[:n],
                 "levU": levU[:n]}
+
+    def colscale(self):
+        """Row/column scaling only: (D_c, number of Ruiz steps)."""
+        dc = np.empty(max(self.n, 1), np.float64)
+        steps = ctypes.c_int32()
+        _check(self.ctx.handle, load().silu_ilu_export_colscale(self.handle, _ptr(dc), ctypes.byref(steps)),
+               "silu_ilu_export_colscale")
+        return dc[:self.n], steps.value
 
     def reserve(self, nrhs: int = 1, restart: int = 0):
         _check(self.ctx.handle, load().silu_ilu_reserve(self.handle, nrhs, restart), "silu_ilu_reserve")

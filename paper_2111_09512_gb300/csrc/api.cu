@@ -119,7 +119,7 @@ cudaError_t ensure_sorted(silu_ilu F) {
   if (F->sorted_ready) return cudaSuccess;
   cudaStream_t s = F->ctx->stream;
   const bool f32 = F->prec == SILU_FP32;
-  const Csr& Ut = (F->scale == SILU_SCALE_ROW) ? F->Us : F->F.U;
+  const Csr& Ut = scaled_upper(F) ? F->Us : F->F.U;
   F->ws.drop_graphs();
   F->config_gen++;
   cudaError_t e = upload_sorted(F->F.L, f32, F->Lsort, F->dL, s);
@@ -131,7 +131,7 @@ cudaError_t ensure_sorted(silu_ilu F) {
 cudaError_t upload_factors(silu_ilu F) {
   cudaStream_t s = F->ctx->stream;
   const bool f32 = F->prec == SILU_FP32;
-  const Csr& Ut = (F->scale == SILU_SCALE_ROW) ? F->Us : F->F.U;
+  const Csr& Ut = scaled_upper(F) ? F->Us : F->F.U;
   const bool had = F->dL.rp != nullptr;
   const DevCsr oldL = F->dL, oldU = F->dU;
   F->ws.drop_graphs();  // captured launches refer to the shapes and arrays replaced here
@@ -210,7 +210,7 @@ cudaError_t ensure_direct(silu_ilu F) {
   }
   if (e != cudaSuccess) return e;
   // FP64 Utilde_s: reuse when the sweeps use it in FP64
-  if (F->prec == SILU_FP64 && F->scale == SILU_SCALE_ROW) {
+  if (F->prec == SILU_FP64 && scaled_upper(F)) {
     F->dS64 = F->dU;
   } else {
     e = upload_csr(F->Us, false, F->S_rp, F->S_ci, F->S_va, F->S_tiles, F->dS64, s);
@@ -257,18 +257,20 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
   char* bufP0 = F->ws.p0.as<char>() + col * es;
   char* bufP1 = F->ws.p1.as<char>() + col * es;
   const int gL = lanes_of(F->lanesL, F->autoL), gU = lanes_of(F->lanesU, F->autoU), gA = lanes_of(F->lanesA, F->autoA);
-  const bool rowscale = F->scale == SILU_SCALE_ROW;
+  const bool rowscale = scaled_upper(F);
+  const bool rowcol = F->scale == SILU_SCALE_ROWCOL;
+  const double* dcol = F->d_dcol.as<double>();
   const bool jacobi = F->scale == SILU_SCALE_NONE;
 
   // What happens to y = L^{-1} r once it is known.
   //   FINAL_Y:   x (+)= y                        (m_U = 0, or m_U = 1 with plain Richardson)
-  //   FINAL_DY:  x (+)= D^{-1} y                 (m_U = 1 with scaling or Jacobi)
-  //   NEED_C:    c = D^{-1} y materialised        (m_U >= 2, row scaling)
+  //   FINAL_DY:  x (+)= D^{-1} y                 (m_U = 1 with row scaling or Jacobi)
+  //   NEED_C:    c = D^{-1} y (or D_r y) materialised  (m_U >= 2 with scaling; m_U = 1 with row/column scaling)
   //   NEED_Y:    y materialised                   (m_U >= 2, unscaled variants)
   enum { FINAL_Y, FINAL_DY, NEED_C, NEED_Y } after;
   if (mU == 0 || (mU == 1 && !rowscale && !jacobi))
     after = FINAL_Y;
-  else if (mU == 1)
+  else if (mU == 1 && !rowcol)
     after = FINAL_DY;
   else if (rowscale)
     after = NEED_C;
@@ -346,15 +348,22 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
       LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_scale(n, R, ldx, y, f32, dinv, bufC, f32, s));
       cvec = bufC;
     }
-    // v^1 = c; v^k = c - Utilde_s v^{k-1}
+    // v^1 = c; v^k = c - Utilde_s v^{k-1}; with row/column scaling the
+    // update is x (+)= D_c v (the dcol vector takes dinv's place in the epilogue)
+    if (rowcol && mU == 1) {
+      LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_addx(n, R, ldx, cvec, f32, dcol, x, !x_zero, s));
+      return;
+    }
     ProfRun run(F->ctx, SILU_K_SWEEP_U);
     const void* in = cvec;
     char* pp[2] = {bufP0, bufP1};
     for (int k = 2; k <= mU; ++k) {
       const bool last = (k == mU);
       char* out = pp[k & 1];
-      const int epi = last ? (x_zero ? silu::EPI_SETX : silu::EPI_ADDX) : silu::EPI_STORE;
-      LAUNCH(F->ctx, SILU_K_SWEEP_U, sweep_launch(F, F->dU, sm, R, gU, ldx, cvec, in, last ? nullptr : out, dinv, x, epi));
+      int epi = last ? (x_zero ? silu::EPI_SETX : silu::EPI_ADDX) : silu::EPI_STORE;
+      if (last && rowcol) epi = x_zero ? silu::EPI_SCALE_SETX : silu::EPI_SCALE_ADDX;
+      LAUNCH(F->ctx, SILU_K_SWEEP_U, sweep_launch(F, F->dU, sm, R, gU, ldx, cvec, in, last ? nullptr : out,
+                                                  last && rowcol ? dcol : dinv, x, epi));
       in = out;
     }
     return;
@@ -515,7 +524,8 @@ void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
     F->ctx->launches += F->nlevL + F->nlevU - 1;  // one count came from ProfScope
     CK(cudaGraphLaunch(exec, s));
   }
-  LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_addx(n, R, ldx, c, false, nullptr, x, !x_zero, s));
+  const double* dcol = F->scale == SILU_SCALE_ROWCOL ? F->d_dcol.as<double>() : nullptr;  // x += D_c v
+  LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_addx(n, R, ldx, c, false, dcol, x, !x_zero, s));
 }
 
 int chunk_width(int left) { return left >= 4 ? 4 : (left >= 2 ? 2 : 1); }
@@ -607,16 +617,25 @@ void fgmres_inner_graph(silu_ilu F, int j, int m, int mL, int mU, int precond) {
 
 }  // namespace
 
+// Unit-diagonal copy of the upper factor: row scaling (Eq. newD) or, for
+// SILU_SCALE_ROWCOL, row/column scaling (Eq. rowcolScale).
+int scale_upper(silu_ilu F, std::string& msg) {
+  if (F->scale == SILU_SCALE_ROWCOL)
+    return silu::rowcol_scale(F->F.U, kRuizMaxit, kRuizTol, F->Us, F->dinv, F->dcol, F->ruiz_steps, msg);
+  F->dcol.clear();
+  return silu::row_scale(F->F.U, F->Us, F->dinv, msg);
+}
+
 silu_status finish_setup(silu_ilu F) {
   silu_ctx ctx = F->ctx;
   std::string msg;
-  int st = silu::row_scale(F->F.U, F->Us, F->dinv, msg);
+  int st = scale_upper(F, msg);
   if (st != silu::H_OK) return set_err(ctx, (silu_status)st, msg);
   F->nlevL = silu::levels_lower(F->F.L, F->levL);
   F->nlevU = silu::levels_upper(F->F.U, true, F->levU);
   silu::group_levels(F->levL, F->nlevL, F->levLptr, F->levLrows);
   silu::group_levels(F->levU, F->nlevU, F->levUptr, F->levUrows);
-  const silu::Csr& Ut = (F->scale == SILU_SCALE_ROW) ? F->Us : F->F.U;
+  const silu::Csr& Ut = scaled_upper(F) ? F->Us : F->F.U;
   F->autoL = pick_lanes(F->F.L);
   F->autoU = pick_lanes(Ut);
   F->autoA = pick_lanes(F->A->A);
@@ -636,6 +655,7 @@ silu_status finish_setup(silu_ilu F) {
     cudaStream_t s = ctx->stream;
     cudaError_t e = upload_factors(F);
     if (e == cudaSuccess) e = upload(F->d_dinv, F->dinv.data(), F->dinv.size(), s);
+    if (e == cudaSuccess && !F->dcol.empty()) e = upload(F->d_dcol, F->dcol.data(), F->dcol.size(), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_err(ctx, e, "upload of the factors");
   }
@@ -781,7 +801,7 @@ silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choic
   const size_t n = (size_t)F->F.L.n;
   if (n == 0) return SILU_OK;
   cudaStream_t s = ctx->stream;
-  const Csr& Ut = (F->scale == SILU_SCALE_ROW) ? F->Us : F->F.U;
+  const Csr& Ut = scaled_upper(F) ? F->Us : F->F.U;
   const int autoL = silu::staged_lanes(F->F.L.rp.data(), F->F.L.n);
   const int autoU = silu::staged_lanes(Ut.rp.data(), Ut.n);
   DBuf x, b;
@@ -955,7 +975,7 @@ silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int 
                       silu_prec prec, silu_ilu* out) {
   if (!ctx || !A || !out || A->ctx != ctx) return set_err(ctx, SILU_ERR_INVALID_ARG, "bad handle");
   *out = nullptr;
-  if (kind < SILU_ILU0 || kind > SILU_ILUT || scale < SILU_SCALE_NONE || scale > SILU_SCALE_NONE_RICH ||
+  if (kind < SILU_ILU0 || kind > SILU_SGS || scale < SILU_SCALE_NONE || scale > SILU_SCALE_ROWCOL ||
       prec < SILU_FP64 || prec > SILU_FP32)
     return set_err(ctx, SILU_ERR_INVALID_ARG, "bad enum value");
   silu_ilu F = new (std::nothrow) silu_ilu_s;
@@ -969,13 +989,7 @@ silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int 
   F->fill = fill;
   std::string msg;
   try {
-    int st;
-    if (kind == SILU_ILU0)
-      st = silu::factor_ilu0(A->A, F->F, msg);
-    else if (kind == SILU_ILUK)
-      st = silu::factor_iluk(A->A, fill, F->F, msg);
-    else
-      st = silu::factor_ilut(A->A, tau, fill, F->F, msg);
+    const int st = silu::factor_kind(A->A, (int)kind, tau, fill, F->F, msg);
     if (st != silu::H_OK) {
       delete F;
       return set_err(ctx, (silu_status)st, msg);
@@ -1003,8 +1017,9 @@ silu_status ilu_refactor(silu_ilu F, const double* new_val) {
     for (int64_t p = 0; p < A.nnz(); ++p)
       if (!std::isfinite(new_val[p])) return set_err(ctx, SILU_ERR_INVALID_ARG, "non-finite value");
     std::copy(new_val, new_val + A.nnz(), A.va.begin());
-    int st = silu::refactor_numeric(A, F->F, msg);
-    if (st == silu::H_OK) st = silu::row_scale(F->F.U, F->Us, F->dinv, msg);
+    int st = (F->kind == SILU_GS || F->kind == SILU_SGS) ? silu::factor_gs(A, F->kind == SILU_SGS, F->F, msg)
+                                                          : silu::refactor_numeric(A, F->F, msg);
+    if (st == silu::H_OK) st = silu::scale_upper(F, msg);
     if (st != silu::H_OK) return set_err(ctx, (silu_status)st, msg);
     if (ctx->device >= 0) {
       silu_status ds = device_ok(ctx);
@@ -1013,6 +1028,7 @@ silu_status ilu_refactor(silu_ilu F, const double* new_val) {
       cudaError_t e = upload(F->A->va, A.va.data(), A.va.size(), s);
       if (e == cudaSuccess) e = upload_factors(F);
       if (e == cudaSuccess) e = upload(F->d_dinv, F->dinv.data(), F->dinv.size(), s);
+      if (e == cudaSuccess && !F->dcol.empty()) e = upload(F->d_dcol, F->dcol.data(), F->dcol.size(), s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return cuda_err(ctx, e, "upload of the refactored factors");
       F->A->d.va = F->A->va.p;
@@ -1183,7 +1199,7 @@ silu_status silu_ilu_stats(silu_ilu F, int64_t* n, int64_t* nnz_L, int64_t* nnz_
   if (!F) return SILU_ERR_INVALID_ARG;
   if (n) *n = F->F.L.n;
   if (nnz_L) *nnz_L = F->F.L.nnz();
-  if (nnz_U) *nnz_U = (F->scale == SILU_SCALE_ROW) ? F->Us.nnz() : F->F.U.nnz();
+  if (nnz_U) *nnz_U = scaled_upper(F) ? F->Us.nnz() : F->F.U.nnz();
   if (levels_L) *levels_L = F->nlevL;
   if (levels_U) *levels_U = F->nlevU;
   return SILU_OK;
@@ -1215,6 +1231,14 @@ silu_status silu_ilu_export(silu_ilu F, int64_t* Lp, int32_t* Lc, double* Lv, in
   cp(dinv, F->dinv);
   cp(levL, F->levL);
   cp(levU, F->levU);
+  return SILU_OK;
+}
+
+silu_status silu_ilu_export_colscale(silu_ilu F, double* dcol, int32_t* ruiz_steps) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  if (F->scale != SILU_SCALE_ROWCOL) return set_err(F->ctx, SILU_ERR_INVALID_ARG, "factor is not row/column scaled");
+  if (dcol && !F->dcol.empty()) std::memcpy(dcol, F->dcol.data(), sizeof(double) * F->dcol.size());
+  if (ruiz_steps) *ruiz_steps = F->ruiz_steps;
   return SILU_OK;
 }
 

@@ -418,7 +418,7 @@ silu_status silu_batch_setup(silu_ctx ctx, int count, const int64_t* n, const in
                              int fill, silu_scale scale, silu_prec prec, silu_batch* out) {
   if (!ctx || !out || count < 1 || !n || !row_ptr || !col_idx || !val) return set_err(ctx, SILU_ERR_INVALID_ARG, "bad argument");
   *out = nullptr;
-  if (kind < SILU_ILU0 || kind > SILU_ILUT || scale < SILU_SCALE_NONE || scale > SILU_SCALE_NONE_RICH ||
+  if (kind < SILU_ILU0 || kind > SILU_SGS || scale < SILU_SCALE_NONE || scale > SILU_SCALE_ROWCOL ||
       prec < SILU_FP64 || prec > SILU_FP32)
     return set_err(ctx, SILU_ERR_INVALID_ARG, "bad enum value");
   silu_batch B = nullptr;
@@ -441,12 +441,7 @@ silu_status silu_batch_setup(silu_ctx ctx, int count, const int64_t* n, const in
           }
           st[k] = csr_canonical(nk, row_ptr[k][nk], row_ptr[k], col_idx[k], val[k], As[k], msg[k]);
           if (st[k] != H_OK) continue;
-          if (kind == SILU_ILU0)
-            st[k] = factor_ilu0(As[k], Fs[k], msg[k]);
-          else if (kind == SILU_ILUK)
-            st[k] = factor_iluk(As[k], fill, Fs[k], msg[k]);
-          else
-            st[k] = factor_ilut(As[k], tau, fill, Fs[k], msg[k]);
+          st[k] = factor_kind(As[k], (int)kind, tau, fill, Fs[k], msg[k]);
         }
       });
     for (std::thread& th : pool) th.join();

@@ -218,6 +218,54 @@ int factor_iluk(const Csr& A, int kfill, Factors& F, std::string& msg) {
   return H_OK;
 }
 
+int factor_gs(const Csr& A, bool symmetric, Factors& F, std::string& msg) {
+  const int64_t n = A.n;
+  std::vector<double> d(n, 0.0);
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t q = find_col(A.ci, A.rp[i], A.rp[i + 1], (int32_t)i);
+    if (q < 0 || A.va[q] == 0.0 || !std::isfinite(A.va[q])) {
+      msg = "zero diagonal entry in row " + std::to_string(i);
+      return H_ZERO_PIVOT;
+    }
+    d[i] = A.va[q];
+  }
+  F.L.n = F.U.n = n;
+  F.L.rp.assign(n + 1, 0);
+  F.U.rp.assign(n + 1, 0);
+  F.L.ci.clear();
+  F.L.va.clear();
+  F.U.ci.clear();
+  F.U.va.clear();
+  for (int64_t i = 0; i < n; ++i) {
+    F.U.ci.push_back((int32_t)i);
+    F.U.va.push_back(d[i]);
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
+      const int32_t j = A.ci[p];
+      if (j < i) {
+        F.L.ci.push_back(j);
+        F.L.va.push_back(A.va[p] / d[j]);
+      } else if (j > i && symmetric) {
+        F.U.ci.push_back(j);
+        F.U.va.push_back(A.va[p]);
+      }
+    }
+    F.L.rp[i + 1] = (int64_t)F.L.ci.size();
+    F.U.rp[i + 1] = (int64_t)F.U.ci.size();
+  }
+  return H_OK;
+}
+
+int factor_kind(const Csr& A, int kind, double tau, int fill, Factors& F, std::string& msg) {
+  switch (kind) {
+    case (int)Kind::ILU0: return factor_ilu0(A, F, msg);
+    case (int)Kind::ILUK: return factor_iluk(A, fill, F, msg);
+    case (int)Kind::ILUT: return factor_ilut(A, tau, fill, F, msg);
+    case (int)Kind::GS: return factor_gs(A, false, F, msg);
+    case (int)Kind::SGS: return factor_gs(A, true, F, msg);
+    default: msg = "bad factorisation kind"; return H_BADARG;
+  }
+}
+
 int refactor_numeric(const Csr& A, Factors& F, std::string& msg) {
   const int64_t n = A.n;
   std::vector<int64_t> prp(n + 1, 0);
@@ -385,6 +433,57 @@ int row_scale(const Csr& U, Csr& Us, std::vector<double>& dinv, std::string& msg
     for (int64_t p = b + 1; p < e; ++p) {
       Us.ci.push_back(U.ci[p]);
       Us.va.push_back(U.va[p] / d);
+    }
+    Us.rp[i + 1] = (int64_t)Us.ci.size();
+  }
+  return H_OK;
+}
+
+int rowcol_scale(const Csr& U, int maxit, double tol, Csr& Us, std::vector<double>& dr, std::vector<double>& dc,
+                 int& steps, std::string& msg) {
+  const int64_t n = U.n;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t b = U.rp[i];
+    if (U.rp[i + 1] <= b || U.ci[b] != i) {
+      msg = "upper factor row without leading diagonal";
+      return H_BADARG;
+    }
+    if (U.va[b] == 0.0 || !std::isfinite(U.va[b])) {
+      msg = "zero pivot in row/column scaling";
+      return H_ZERO_PIVOT;
+    }
+  }
+  std::vector<double> r(n, 1.0), rmax(n), cmax(n);
+  dc.assign(n, 1.0);
+  steps = 0;
+  for (;;) {
+    std::fill(rmax.begin(), rmax.end(), 0.0);
+    std::fill(cmax.begin(), cmax.end(), 0.0);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = U.rp[i]; p < U.rp[i + 1]; ++p) {
+        const double a = std::fabs(r[i] * U.va[p] * dc[U.ci[p]]);
+        rmax[i] = std::max(rmax[i], a);
+        cmax[U.ci[p]] = std::max(cmax[U.ci[p]], a);
+      }
+    double dev = 0.0;
+    for (int64_t i = 0; i < n; ++i) dev = std::max(dev, std::max(std::fabs(1.0 - rmax[i]), std::fabs(1.0 - cmax[i])));
+    if (dev <= tol || steps >= maxit) break;
+    for (int64_t i = 0; i < n; ++i) {
+      r[i] /= std::sqrt(rmax[i]);
+      dc[i] /= std::sqrt(cmax[i]);
+    }
+    ++steps;
+  }
+  dr.resize(n);
+  Us.n = n;
+  Us.rp.assign(n + 1, 0);
+  Us.ci.clear();
+  Us.va.clear();
+  for (int64_t i = 0; i < n; ++i) {
+    dr[i] = 1.0 / (U.va[U.rp[i]] * dc[i]);
+    for (int64_t p = U.rp[i] + 1; p < U.rp[i + 1]; ++p) {
+      Us.ci.push_back(U.ci[p]);
+      Us.va.push_back(dr[i] * U.va[p] * dc[U.ci[p]]);
     }
     Us.rp[i + 1] = (int64_t)Us.ci.size();
   }

@@ -128,11 +128,13 @@ struct silu_ilu_s {
   int fill = 0;
   silu::Factors F;
   silu::Csr Us;
-  std::vector<double> dinv;
+  std::vector<double> dinv;  // D^{-1} (row scaling), or D_r (row/column scaling)
+  std::vector<double> dcol;  // D_c (row/column scaling only)
+  int ruiz_steps = 0;
   std::vector<int32_t> levL, levU, levLptr, levLrows, levUptr, levUrows;
   int32_t nlevL = 0, nlevU = 0;
   // device: sweep factors, and their length-sorted copies where those pay
-  DBuf L_rp, L_ci, L_va, L_tiles, U_rp, U_ci, U_va, U_tiles, d_dinv;
+  DBuf L_rp, L_ci, L_va, L_tiles, U_rp, U_ci, U_va, U_tiles, d_dinv, d_dcol;
   SortedBufs Lsort, Usort;
   bool sorted_ready = false;  // sorted copies built (where they pay) for the current values
   double pad_nat[2] = {0.0, 0.0}, pad_sorted[2] = {0.0, 0.0};  // L_s, upper sweep factor
@@ -150,6 +152,10 @@ struct silu_ilu_s {
   Workspace ws;
 };
 
+// The upper sweep factor is a unit-diagonal scaled copy (F->Us) rather than raw U.
+inline bool scaled_upper(const silu_ilu_s* F) {
+  return F->scale == SILU_SCALE_ROW || F->scale == SILU_SCALE_ROWCOL;
+}
 
 namespace silu {
 
@@ -285,6 +291,12 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
 // (used while a stream capture is recording).
 void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, bool x_zero,
                   bool inline_levels = false);
+// Ruiz equilibration limits for SILU_SCALE_ROWCOL.
+constexpr int kRuizMaxit = 20;
+constexpr double kRuizTol = 1e-2;
+// Unit-diagonal copy of the upper factor (row or row/column scaling) into
+// F->Us, F->dinv (and F->dcol); returns a silu::HostStatus.
+int scale_upper(silu_ilu F, std::string& msg);
 // Scale, level sets, launch shapes and upload for F->F already factored.
 silu_status finish_setup(silu_ilu F);
 

@@ -217,7 +217,7 @@ silu_status silu_server_submit(silu_server S, int64_t n, const int64_t* row_ptr,
                                uint64_t* ticket) {
   if (!S || !params || !ticket || (n > 0 && !b)) return SILU_ERR_INVALID_ARG;
   const silu_request_params& p = *params;
-  if (p.kind < SILU_ILU0 || p.kind > SILU_ILUT || p.prec < SILU_FP64 || p.prec > SILU_FP32 || p.restart < 1 ||
+  if (p.kind < SILU_ILU0 || p.kind > SILU_SGS || p.prec < SILU_FP64 || p.prec > SILU_FP32 || p.restart < 1 ||
       p.maxit < 0 || p.precond < 0 || p.precond > 2 || !(p.tol >= 0.0))
     return SILU_ERR_INVALID_ARG;
   auto r = std::make_shared<Request>();

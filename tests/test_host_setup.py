@@ -201,3 +201,63 @@ def test_layout_pads(ctx):
         pays = lay["pad_natural"][0] >= 1.08 and lay["pad_natural"][0] - lay["pad_sorted"][0] >= 0.05
         assert pays == sorted_L
         assert not lay["in_use"].any()
+
+
+@pytest.mark.parametrize("kind", ["gs", "sgs"])
+def test_gauss_seidel_factors(ctx, kind):
+    """GS / SGS as factors (Sec. 3.1): L_s = L_A D^{-1}, Utilde_s = D^{-1} U_A
+    (SGS only), dinv = 1 / diag(A), each one division of A's entries; and the
+    row-scaled Richardson sweeps on them reproduce the oracle's polynomial
+    Gauss-Seidel, sum_{j<=p} (-D^{-1} L_A)^j D^{-1} r, formed term by term."""
+    from _helpers import dense
+    A = synth.cutcell7(6, 5, 4, seed=9)
+    n = len(A[0]) - 1
+    M = dense(A)
+    d = np.diag(M)
+    ex = silu.ILU(silu.Matrix(ctx, *A), kind).export()
+    assert np.array_equal(ex["dinv"], 1.0 / d)
+    assert np.array_equal(dense(ex["L"], n), np.tril(M, -1) / d[None, :])
+    want_us = np.triu(M, 1) / d[:, None] if kind == "sgs" else np.zeros((n, n))
+    assert np.array_equal(dense(ex["Us"], n), want_us)
+    S = oracle.Scaled(n, ex["L"], ex["Us"], ex["dinv"])
+    b = synth.rhs(n, 2, seed=3)
+    x0 = synth.rhs(n, 2, seed=4)
+    for p, q in ((0, 0), (1, 0), (3, 2), (6, 5)):
+        mine = oracle.smooth(A, S, x0, b, p + 1, q + 1)
+        want = oracle.poly_gs_smooth(A, x0, b, p, q, symmetric=(kind == "sgs"))
+        assert np.linalg.norm(mine - want) / np.linalg.norm(want) < 1e-13
+    # zero diagonal refused
+    Z = silu.Matrix(ctx, np.array([0, 2, 4], np.int64), np.array([0, 1, 0, 1], np.int32),
+                    np.array([0.0, 1.0, 1.0, 2.0]))
+    with pytest.raises(silu.SiluError) as e:
+        silu.ILU(Z, kind)
+    assert e.value.status == silu.ERR_ZERO_PIVOT
+
+
+@pytest.mark.parametrize("kind,tau,fill", [("ilu0", 0.0, 0), ("ilut", 1e-3, 6)])
+def test_rowcol_scaling_matches_oracle(ctx, kind, tau, fill):
+    """Row/column scaling (Eq. rowcolScale): the library's Ruiz equilibration
+    and unit-diagonal row fix reproduce the oracle's bit for bit (both round
+    every operation as written); the Richardson smoother on the host copies
+    equals the row-scaled one (Uhat = D_c^{-1} (D^{-1} U) D_c)."""
+    A = synth.cutcell7(9, 8, 7, seed=12)
+    n = len(A[0]) - 1
+    F = silu.ILU(silu.Matrix(ctx, *A), kind, tau, fill, scale=silu.SCALE_ROWCOL)
+    ex = F.export()
+    dc, steps = F.colscale()
+    OF = oracle.factor(A, kind, tau, fill)
+    RC = oracle.ruiz_rowcol(OF, maxit=20, tol=1e-2)
+    assert steps == RC.steps and 1 <= steps <= 20
+    assert np.array_equal(dc, RC.dc)
+    assert np.array_equal(ex["dinv"], RC.dr)
+    for mine, theirs in zip(ex["Us"], RC.Us):
+        assert np.array_equal(mine, theirs)
+    b = synth.rhs(n, 1, seed=2)
+    S = oracle.row_scale(OF)
+    want = oracle.smooth(A, S, np.zeros((n, 1)), b, 4, 4)
+    got = oracle.smooth_rowcol(A, RC, np.zeros((n, 1)), b, 4, 4)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-13
+    # another scaling has no column factor
+    G = silu.ILU(silu.Matrix(ctx, *A), kind, tau, fill)
+    with pytest.raises(silu.SiluError):
+        G.colscale()
