@@ -8,7 +8,8 @@ scaling (Eq. extractD, Eq. newD), the Richardson sweeps of Alg. ILUJac and
 Eq. richard, the direct triangular solves with level sets (Sec. 4), FGMRES
 with modified Gram-Schmidt (Sec. 6) and the diagnostics dep (Eq. depB) and
 NRBE (Eq. nbre), the polynomial Gauss-Seidel smoother of Sec. 3.1 and the
-row/column (Ruiz) scaling of Eq. rowcolScale.
+row/column (Ruiz) scaling of Eq. rowcolScale, and the power-iteration
+estimates of ||T_s^p||_2 behind the paper's numerical nilpotence (Fig. Up).
 
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
 import this package.  It shares no code with the CUDA library.  Each wrapper
@@ -87,6 +88,7 @@ def _load():
         "orc_poly_gs_smooth": (i32, [i64, i32, vp, vp, vp, vp, vp, i32, i32, i32]),
         "orc_ruiz_rowcol": (i32, [i64, vp, vp, vp, i32, dbl, vp, vp, vp, vp, vp]),
         "orc_smooth_rowcol": (i32, [i64, i32] + [vp] * 13 + [i32, i32]),
+        "orc_power_norms": (i32, [i64, vp, vp, vp, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -485,3 +487,15 @@ def smooth_rowcol(A, S: RowCol, x, b, mL: int, mU: int):
     if st:
         raise OracleError(st, "smooth_rowcol")
     return x
+
+
+def power_norms(T, pmax: int, iters: int, v0) -> np.ndarray:
+    """Power-iteration estimates of ||T^p||_2 for p = 1..pmax from start vector v0 (Sec. 5.2, Fig. Up)."""
+    tp, tc, tv = _csr(T)
+    n = len(tp) - 1
+    v0 = np.ascontiguousarray(v0, np.float64).reshape(n)
+    out = np.empty(max(pmax, 1), np.float64)
+    st = _load().orc_power_norms(n, _p(tp), _p(tc), _p(tv), int(pmax), int(iters), _p(v0), _p(out))
+    if st:
+        raise OracleError(st, "power_norms")
+    return out[:pmax]

@@ -1243,3 +1243,58 @@ done:
   free(w);
   return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Numerical nilpotence: ||T_s^p||_2 (Sec. 5.2, Fig. Up)                      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Estimates of the spectral norms ||T^p||_2, p = 1..pmax, of a strictly
+ * triangular T (CSR) by power iteration on (T^p)^T T^p.  For each p, from
+ * v = v0 / ||v0||: `iters` times, w = T^p v (p products), s = ||w||,
+ * z = (T^T)^p w (p products with the transpose, formed by scattering
+ * t_ij w_i into z_j), v = z / ||z||.  out[p-1] = s of the last iteration
+ * (the norm of T^p on a unit vector: a lower bound that rises to ||T^p||_2).
+ * When T^p v vanishes (T nilpotent of index <= p on that vector) s = 0 and
+ * the iteration for that p stops.
+ */
+int orc_power_norms(int64_t n, const int64_t* tp, const int32_t* tc, const double* tv, int pmax, int iters,
+                    const double* v0, double* out) {
+  double* v = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* a = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* b = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!v || !a || !b) {
+    free(v);
+    free(a);
+    free(b);
+    return ORC_NOMEM;
+  }
+  const double n0 = sqrt(dot(n, v0, v0));
+  for (int p = 1; p <= pmax; ++p) {
+    for (int64_t i = 0; i < n; ++i) v[i] = v0[i] / n0;
+    double s = 0.0;
+    for (int it = 0; it < iters; ++it) {
+      memcpy(a, v, sizeof(double) * (size_t)n);
+      for (int k = 0; k < p; ++k) { /* a <- T a */
+        orc_spmv(n, 1, tp, tc, tv, a, b);
+        memcpy(a, b, sizeof(double) * (size_t)n);
+      }
+      s = sqrt(dot(n, a, a));
+      if (s == 0.0) break;
+      for (int k = 0; k < p; ++k) { /* a <- T^T a */
+        for (int64_t j = 0; j < n; ++j) b[j] = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+          for (int64_t q = tp[i]; q < tp[i + 1]; ++q) b[tc[q]] = b[tc[q]] + tv[q] * a[i];
+        memcpy(a, b, sizeof(double) * (size_t)n);
+      }
+      const double z = sqrt(dot(n, a, a));
+      if (z == 0.0) break;
+      for (int64_t i = 0; i < n; ++i) v[i] = a[i] / z;
+    }
+    out[p - 1] = s;
+  }
+  free(v);
+  free(a);
+  free(b);
+  return ORC_OK;
+}
