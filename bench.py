@@ -626,42 +626,115 @@ def poisson32(silu, ctx, torch):
 
 
 def sweep_study(silu, ctx, torch):
-    """Cut-cell 128^3, ILUT(1e-3, 10), FP64, one right-hand side (seed 1):
-    for m = 1..20 sweeps on each factor, one smoother application from zero
-    with the row-scaled factors (the method), unscaled Jacobi and unscaled
-    plain Richardson; reports ||b - A x_m|| / ||b|| and the distance
-    ||x_m - x*|| / ||x*|| to the exact application x* (direct solves)."""
+    """Sweep studies (the paper's Sec. 5.2 and Sec. 6.1 questions on synthetic
+    matrices), all computed by the library on the device.
+
+    scaling: cut-cell 128^3, ILUT(1e-3, 10), FP64, one right-hand side
+    (seed 1): for m = 1..20 sweeps on each factor, one smoother application
+    from zero with the row-scaled factors (the method), row/column (Ruiz)
+    scaled factors, unscaled Jacobi and unscaled plain Richardson; reports
+    ||b - A x_m|| / ||b|| and the distance ||x_m - x*|| / ||x*|| to the exact
+    application x* (direct solves).
+
+    kinds: the same matrix under ILU(0), ILU(1), ILUT(1e-2, 10),
+    ILUT(1e-3, 10), ILUT(1e-4, 20) and the polynomial Gauss-Seidel
+    splittings: relres of one application for m = 1..20, the factor sizes
+    and level counts, and FGMRES(30) to 1e-8 with 3+3 sweeps against the
+    direct solves (iterations, seconds).
+
+    nilpotence: ||T_s^p||_2 for p = 1..40 (power iteration, 30 steps per p)
+    on a 24^3 cut-cell matrix (13,824 rows, the size of the paper's
+    14,186-row PeleLM matrix of Fig. Up), upper factor of ILUT(tau, 30) for
+    tau in {1e-2, 1e-3, 1e-4} with row and with row/column scaling, and L_s."""
     import numpy as np
     import synth
-    import oracle
+    out = {}
+
+    def norms_of(M, x, bt):
+        r = torch.empty_like(bt)
+        M.residual(r, x, bt)
+        return float(torch.linalg.norm(r) / torch.linalg.norm(bt))
+
     A = synth.cutcell7(EDGE, seed=1)
     n = len(A[0]) - 1
     bh = synth.rhs(n, 1, seed=1)
     b = torch.from_numpy(bh).cuda()
-    out = {"workload": WORKLOAD.split(" smoother")[0], "sweeps": list(range(1, 21))}
+    M = silu.Matrix(ctx, *A)
+    sweeps = list(range(1, 21))
+    sc_out = {"workload": WORKLOAD.split(" smoother")[0], "sweeps": sweeps}
     xstar = None
-    for name, sc in (("row_scaled_richardson", silu.SCALE_ROW), ("unscaled_jacobi", silu.SCALE_NONE),
-                     ("unscaled_richardson", silu.SCALE_NONE_RICH)):
-        F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilut", TAU, FILL, scale=sc)
+    for name, sc in (("row_scaled_richardson", silu.SCALE_ROW), ("rowcol_scaled_richardson", silu.SCALE_ROWCOL),
+                     ("unscaled_jacobi", silu.SCALE_NONE), ("unscaled_richardson", silu.SCALE_NONE_RICH)):
+        F = silu.ilu_setup(ctx, M, "ilut", TAU, FILL, scale=sc)
         if xstar is None:
-            xs = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
-            silu.direct_trisolve(F, xs, b)
-            xstar = xs.cpu().numpy()
+            xstar = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+            silu.direct_trisolve(F, xstar, b)
         rel, dist = [], []
-        for m in range(1, 21):
+        for m in sweeps:
             x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
             silu.ilu_smooth(F, x, b, m, m)
-            xh = x.cpu().numpy()
-            if not np.all(np.isfinite(xh)):
+            if not bool(torch.isfinite(x).all()):
                 rel.append(None)
                 dist.append(None)
                 continue
-            r = oracle.residual(A, xh, bh)
-            rel.append(float(np.linalg.norm(r) / np.linalg.norm(bh)))
-            dist.append(float(np.linalg.norm(xh - xstar) / np.linalg.norm(xstar)))
-        out[name] = {"relres": [None if v is None else float(f"{v:.4e}") for v in rel],
-                     "dist_to_exact": [None if v is None else float(f"{v:.4e}") for v in dist]}
+            rel.append(norms_of(M, x, b))
+            dist.append(float(torch.linalg.norm(x - xstar) / torch.linalg.norm(xstar)))
+        sc_out[name] = {"relres": [None if v is None else float(f"{v:.4e}") for v in rel],
+                        "dist_to_exact": [None if v is None else float(f"{v:.4e}") for v in dist]}
         del F
+    out["scaling"] = sc_out
+
+    kinds = [("ilu0", "ilu0", 0.0, 0), ("iluk1", "iluk", 0.0, 1), ("ilut_1e-2_10", "ilut", 1e-2, 10),
+             ("ilut_1e-3_10", "ilut", 1e-3, 10), ("ilut_1e-4_20", "ilut", 1e-4, 20), ("gs", "gs", 0.0, 0),
+             ("sgs", "sgs", 0.0, 0)]
+    k_out = {"workload": "cutcell7-128^3 FP64, 1 RHS (seed 1)", "sweeps": sweeps,
+             "fgmres": "FGMRES(30) to 1e-8 from x = 0, 3+3 sweeps vs direct solves"}
+    for name, kind, tau, fill in kinds:
+        t0 = time.perf_counter()
+        F = silu.ilu_setup(ctx, M, kind, tau, fill)
+        setup_s = time.perf_counter() - t0
+        st = F.stats()
+        rel = []
+        for m in sweeps:
+            x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+            silu.ilu_smooth(F, x, b, m, 1 if kind == "gs" else m)
+            rel.append(float(f"{norms_of(M, x, b):.4e}") if bool(torch.isfinite(x).all()) else None)
+        rec = {"setup_s": round(setup_s, 2), "nnz_L": st["nnz_L"], "nnz_U": st["nnz_U"],
+               "levels_L": st["levels_L"], "levels_U": st["levels_U"], "relres_one_application": rel}
+        for label, pre, mL, mU in (("sweeps_3_3", silu.PRECOND_SWEEPS, 3, 1 if kind == "gs" else 3),
+                                   ("direct", silu.PRECOND_DIRECT, 0, 0)):
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            status, its, rr = silu.fgmres_solve(F, x, b[:, 0].contiguous(), tol=1e-8, restart=30, maxit=3000,
+                                                sweeps_L=mL, sweeps_U=mU, precond=pre)
+            torch.cuda.synchronize()
+            rec[label] = {"seconds": round(time.perf_counter() - t0, 3), "iterations": its,
+                          "relres": float(f"{rr:.3e}"), "converged": status == silu.OK}
+        k_out[name] = rec
+        del F
+    out["kinds"] = k_out
+
+    B = synth.cutcell7(24, seed=1)
+    nb = len(B[0]) - 1
+    MB = silu.Matrix(ctx, *B)
+    v0 = synth.rhs(nb, 1, seed=5)[:, 0]
+    P, iters = 40, 30
+    nil = {"workload": "cutcell7-24^3 (13,824 rows), ILUT(tau, 30), FP64", "p": list(range(1, P + 1)),
+           "iterations_per_p": iters}
+    for tau in (1e-2, 1e-3, 1e-4):
+        for label, sc in (("row", silu.SCALE_ROW), ("rowcol", silu.SCALE_ROWCOL)):
+            F = silu.ilu_setup(ctx, MB, "ilut", tau, 30, scale=sc)
+            nu = F.power_norms("U", P, iters, v0)
+            below = [p + 1 for p in range(P) if nu[p] < 1.0]
+            rec = {"norm_Us_p": [float(f"{v:.4e}") for v in nu], "first_p_below_1": below[0] if below else None,
+                   "levels_U": F.stats()["levels_U"]}
+            if label == "row":
+                nl = F.power_norms("L", P, iters, v0)
+                rec["norm_Ls_p"] = [float(f"{v:.4e}") for v in nl]
+            nil[f"ilut_{tau:g}_{label}"] = rec
+            del F
+    out["nilpotence"] = nil
     return out
 
 
@@ -676,7 +749,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--study", action="store_true", help="add the 1..20-sweep scaled/unscaled study")
+    ap.add_argument("--study", action="store_true",
+                    help="add the sweep studies: scaling variants, factorisation kinds, ||T_s^p||_2")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--serve-workers", type=int, default=4)

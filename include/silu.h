@@ -179,6 +179,13 @@ silu_status silu_mat_create(silu_ctx ctx, int64_t n, int64_t nnz, const int64_t*
 void silu_mat_destroy(silu_mat A);
 
 /*
+ * r = b - A x on the device (the residual of Eq. ILUsplit), ordered on A's
+ * context stream.  r, x, b: device n x nrhs FP64 (row-major, right-hand sides
+ * interleaved); r must not overlap x or b.  Device context only.
+ */
+silu_status silu_mat_residual(silu_mat A, double* r, const double* x, const double* b, int nrhs);
+
+/*
  * Host factorisation + scaling + packing, then one upload (blocks).
  *  kind  SILU_ILU0: pattern of A (Sec. 5.1, Matlab ilu 'nofill').
  *        SILU_ILUK: level-of-fill k = `fill` (Sec. 1).
@@ -262,6 +269,19 @@ silu_status silu_ilu_export(silu_ilu F, int64_t* Lp, int32_t* Lc, double* Lv, in
  * taken (the Sv / dinv arrays of silu_ilu_export then hold Uhat_s and D_r).
  * SILU_ERR_INVALID_ARG for another scaling.  Either pointer may be NULL. */
 silu_status silu_ilu_export_colscale(silu_ilu F, double* dcol, int32_t* ruiz_steps);
+/*
+ * Numerical nilpotence of a sweep factor (Sec. 5.2, Fig. Up): estimates of
+ * ||T^p||_2 for p = 1..pmax, where T = L_s (which = 0) or the strict part of
+ * the unit-diagonal upper factor (which = 1: Utilde_s, or Uhat_s under
+ * SILU_SCALE_ROWCOL), always in FP64 from the host copy of the factor.  For
+ * each p: v = v0 / ||v0||, then `iters` times s = ||T^p v||,
+ * v = (T^T)^p T^p v / ||(T^T)^p T^p v||; out[p-1] = the last s, a lower bound
+ * that rises to ||T^p||_2 (0 once T^p v vanishes, as it must for p at or
+ * beyond the factor's number of levels).  v0: host array of n finite values,
+ * not all zero.  out: host array of pmax doubles.  Allocates device copies of
+ * T and of its transpose for the call; blocks.  Device context only.
+ */
+silu_status silu_ilu_power_norms(silu_ilu F, int which, int pmax, int iters, const double* v0, double* out);
 /* Entry counts of U with diagonal (for export buffer sizing). */
 silu_status silu_ilu_export_sizes(silu_ilu F, int64_t* nnz_L, int64_t* nnz_Ufull, int64_t* nnz_Us);
 

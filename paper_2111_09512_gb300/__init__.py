@@ -87,6 +87,7 @@ def load():
         "silu_last_error": (ctypes.c_char_p, [vp]),
         "silu_mat_create": (i32, [vp, i64, i64, vp, vp, vp, pvp]),
         "silu_mat_destroy": (None, [vp]),
+        "silu_mat_residual": (i32, [vp, vp, vp, vp, i32]),
         "ilu_setup": (i32, [vp, vp, i32, dbl, i32, i32, i32, pvp]),
         "ilu_refactor": (i32, [vp, vp]),
         "ilu_smooth": (i32, [vp, vp, vp, i32, i32, i32]),
@@ -99,6 +100,7 @@ def load():
         "silu_ilu_export": (i32, [vp] * 13),
         "silu_ilu_export_sizes": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "silu_ilu_export_colscale": (i32, [vp, vp, ctypes.POINTER(ctypes.c_int32)]),
+        "silu_ilu_power_norms": (i32, [vp, i32, i32, i32, vp, vp]),
         "silu_ilu_destroy": (None, [vp]),
         "silu_ilu_set_lanes": (i32, [vp, i32, i32, i32]),
         "silu_ctx_profile": (i32, [vp, i32]),
@@ -136,9 +138,9 @@ def load():
 def exported_symbols():
     """Names the binding declares (all must be exported by libsilu.so)."""
     return ["silu_version", "silu_ctx_create", "silu_ctx_destroy", "silu_last_error", "silu_mat_create",
-            "silu_mat_destroy", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
+            "silu_mat_destroy", "silu_mat_residual", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
-            "silu_ilu_export_colscale",
+            "silu_ilu_export_colscale", "silu_ilu_power_norms",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
             "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_layout", "silu_ilu_tune_table", "silu_ctx_set_overlap",
             "silu_smooth_noalloc",
@@ -247,6 +249,13 @@ class Matrix:
         self.n = n
         self.nnz = int(rp[-1])
 
+    def residual(self, r, x, b):
+        """r = b - A x on the device (torch tensors n x nrhs or length n, FP64)."""
+        nrhs = 1 if b.dim() == 1 else int(b.shape[1])
+        _check(self.ctx.handle, load().silu_mat_residual(self.handle, _ptr(r), _ptr(x), _ptr(b), nrhs),
+               "silu_mat_residual")
+        return r
+
     def close(self):
         if getattr(self, "handle", None):
             load().silu_mat_destroy(self.handle)
@@ -322,6 +331,15 @@ class ILU:
         _check(self.ctx.handle, load().silu_ilu_export_colscale(self.handle, _ptr(dc), ctypes.byref(steps)),
                "silu_ilu_export_colscale")
         return dc[:self.n], steps.value
+
+    def power_norms(self, which: str, pmax: int, iters: int, v0) -> np.ndarray:
+        """Estimates of ||T^p||_2, p = 1..pmax, for T = L_s ("L") or the scaled strict upper factor ("U")."""
+        v0 = np.ascontiguousarray(v0, np.float64).reshape(self.n)
+        out = np.empty(max(pmax, 1), np.float64)
+        st = load().silu_ilu_power_norms(self.handle, 0 if which == "L" else 1, int(pmax), int(iters), _ptr(v0),
+                                         _ptr(out))
+        _check(self.ctx.handle, st, "silu_ilu_power_norms")
+        return out[:pmax]
 
     def reserve(self, nrhs: int = 1, restart: int = 0):
         _check(self.ctx.handle, load().silu_ilu_reserve(self.handle, nrhs, restart), "silu_ilu_reserve")

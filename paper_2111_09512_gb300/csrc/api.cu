@@ -971,6 +971,32 @@ silu_status silu_mat_create(silu_ctx ctx, int64_t n, int64_t nnz, const int64_t*
 
 void silu_mat_destroy(silu_mat A) { delete A; }
 
+silu_status silu_mat_residual(silu_mat A, double* r, const double* x, const double* b, int nrhs) {
+  if (!A || !r || !x || !b || nrhs < 1) return SILU_ERR_INVALID_ARG;
+  silu_ctx ctx = A->ctx;
+  silu_status ds = device_ok(ctx);
+  if (ds != SILU_OK) return ds;
+  if (A->A.n == 0) return SILU_OK;
+  cudaStream_t s = ctx->stream;
+  try {
+    if (nrhs == 1 && A->d.ntiles > 0) {
+      LAUNCH(ctx, SILU_K_RESIDUAL, silu::launch_sweep_staged(A->d, silu::MODE_D, ctx->env, b, x, r, nullptr, nullptr,
+                                                             silu::EPI_STORE, s));
+    } else {
+      // column blocks of at most 4 right-hand sides, as the smoother's residual
+      for (int c0 = 0; c0 < nrhs;) {
+        const int w = chunk_width(nrhs - c0);
+        LAUNCH(ctx, SILU_K_RESIDUAL, silu::launch_sweep(A->d, silu::MODE_D, w, pick_lanes(A->A), nrhs, b + c0, x + c0,
+                                                        r + c0, nullptr, nullptr, silu::EPI_STORE, s));
+        c0 += w;
+      }
+    }
+  } catch (const silu::CudaFail& f) {
+    return cuda_err(ctx, f.e, f.what);
+  }
+  return SILU_OK;
+}
+
 silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int fill, silu_scale scale,
                       silu_prec prec, silu_ilu* out) {
   if (!ctx || !A || !out || A->ctx != ctx) return set_err(ctx, SILU_ERR_INVALID_ARG, "bad handle");

@@ -169,3 +169,52 @@ def test_rowcol_fp32_and_fgmres(silu, ctx):
     st, its, rel = silu.fgmres_solve(F, xs, dev(b[:, 0].copy()), tol=1e-10, restart=30, maxit=3000, sweeps_L=3,
                                      sweeps_U=3)
     assert st == silu.OK and rel <= 1e-10, (st, its, rel)
+
+
+@pytest.mark.parametrize("which,kind,scale", [("U", "ilut", "row"), ("U", "ilut", "rowcol"), ("L", "ilu0", "row"),
+                                              ("U", "iluk", "row")])
+def test_power_norms_match_oracle(silu, ctx, which, kind, scale):
+    """||T^p||_2 estimates (Sec. 5.2, Fig. Up): the device's power iteration
+    against the oracle's from the same start vector and iteration count; and
+    exactly zero from p = #levels on (nilpotence)."""
+    A = synth.cutcell7(14, 12, 11, seed=5)
+    n = len(A[0]) - 1
+    tau, fill = {"ilut": (1e-4, 10), "ilu0": (0.0, 0), "iluk": (0.0, 1)}[kind]
+    sc = silu.SCALE_ROWCOL if scale == "rowcol" else silu.SCALE_ROW
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), kind, tau, fill, scale=sc)
+    OF = oracle.factor(A, kind, tau, fill)
+    if scale == "rowcol":
+        T = oracle.ruiz_rowcol(OF, maxit=20, tol=1e-2).Us
+    else:
+        S = oracle.row_scale(OF)
+        T = S.L if which == "L" else S.Us
+    v0 = synth.rhs(n, 1, seed=9)[:, 0]
+    pmax, iters = 12, 25
+    got = F.power_norms(which, pmax, iters, v0)
+    want = oracle.power_norms(T, pmax, iters, v0)
+    for p in range(pmax):
+        if want[p] == 0.0:
+            assert got[p] == 0.0
+        else:
+            assert abs(got[p] - want[p]) <= 1e-10 * want[p], (p, got[p], want[p])
+    # a 4 x 3 grid's ILU(0) upper factor has 4 + 3 + 1 - 2 = 6 levels: T^5 v != 0, T^6 = 0
+    B = synth.poisson7(4, 3, 1)
+    G = silu.ilu_setup(ctx, silu.Matrix(ctx, *B), "ilu0")
+    assert G.stats()["levels_U"] == 6
+    z = G.power_norms("U", 7, 3, synth.rhs(12, 1, seed=1)[:, 0])
+    assert np.all(z[:5] > 0.0) and np.all(z[5:] == 0.0)
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 6])
+def test_mat_residual_matches_oracle(silu, ctx, nrhs):
+    """silu_mat_residual: r = b - A x on the device, the residual step of the
+    smoother (Eq. ILUsplit), against the oracle's (column blocks of up to four
+    right-hand sides, and the staged kernel for one)."""
+    A = synth.hex27(23, 19, 17, seed=4)
+    n = len(A[0]) - 1
+    M = silu.Matrix(ctx, *A)
+    x = synth.rhs(n, nrhs, seed=2)
+    b = synth.rhs(n, nrhs, seed=3)
+    r = torch.empty(n, nrhs, dtype=torch.float64, device="cuda")
+    M.residual(r, dev(x), dev(b))
+    assert percol(host(r), oracle.residual(A, x, b)) < FP64_TOL
