@@ -9,7 +9,10 @@ Eq. richard, the direct triangular solves with level sets (Sec. 4), FGMRES
 with modified Gram-Schmidt (Sec. 6) and the diagnostics dep (Eq. depB) and
 NRBE (Eq. nbre), the polynomial Gauss-Seidel smoother of Sec. 3.1 and the
 row/column (Ruiz) scaling of Eq. rowcolScale, and the power-iteration
-estimates of ||T_s^p||_2 behind the paper's numerical nilpotence (Fig. Up).
+estimates of ||T_s^p||_2 behind the paper's numerical nilpotence (Fig. Up),
+and algebraic multigrid (Sec. 3: Ruge-Stueben coarsening, direct
+interpolation, Galerkin coarse operators, the V-cycle of Alg. mgcycle with
+the ILU smoother on the finest level).
 
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
 import this package.  It shares no code with the CUDA library.  Each wrapper
@@ -89,6 +92,12 @@ def _load():
         "orc_ruiz_rowcol": (i32, [i64, vp, vp, vp, i32, dbl, vp, vp, vp, vp, vp]),
         "orc_smooth_rowcol": (i32, [i64, i32] + [vp] * 13 + [i32, i32]),
         "orc_power_norms": (i32, [i64, vp, vp, vp, i32, i32, vp, vp]),
+        "orc_amg_setup": (vp, [i64, vp, vp, vp, dbl, i32, i64, ip]),
+        "orc_amg_free": (None, [vp]),
+        "orc_amg_nlev": (i32, [vp]),
+        "orc_amg_level_sizes": (None, [vp, i32] + [ctypes.POINTER(i64)] * 4),
+        "orc_amg_level_copy": (None, [vp, i32] + [vp] * 7),
+        "orc_amg_vcycle": (i32, [vp] + [vp] * 7 + [i32, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -499,3 +508,69 @@ def power_norms(T, pmax: int, iters: int, v0) -> np.ndarray:
     if st:
         raise OracleError(st, "power_norms")
     return out[:pmax]
+
+
+@dataclass
+class AMGLevel:
+    """One level: A_l (CSR), and below the coarsest P_l (CSR, n_l x n_{l+1}) and the C/F marks."""
+    n: int
+    A: tuple
+    P: tuple | None
+    cf: np.ndarray | None
+
+
+class AMG:
+    """AMG hierarchy built by the oracle (Sec. 3).  levels[l] holds copies of A_l, P_l, cf."""
+
+    def __init__(self, A, theta: float = 0.25, max_levels: int = 25, coarse_size: int = 400):
+        ap, ac, av = _csr(A)
+        n = len(ap) - 1
+        st = ctypes.c_int(0)
+        lib = _load()
+        self._h = lib.orc_amg_setup(n, _p(ap), _p(ac), _p(av), float(theta), int(max_levels), int(coarse_size),
+                                    ctypes.byref(st))
+        if st.value:
+            raise OracleError(st.value, "amg_setup")
+        self.levels = []
+        for l in range(lib.orc_amg_nlev(self._h)):
+            nn, nz, nc, pz = (ctypes.c_int64() for _ in range(4))
+            lib.orc_amg_level_sizes(self._h, l, ctypes.byref(nn), ctypes.byref(nz), ctypes.byref(nc),
+                                    ctypes.byref(pz))
+            m = nn.value
+            lap = np.empty(m + 1, np.int64)
+            lac = np.empty(max(nz.value, 1), np.int32)
+            lav = np.empty(max(nz.value, 1), np.float64)
+            if pz.value or nc.value:
+                pp = np.empty(m + 1, np.int64)
+                pc = np.empty(max(pz.value, 1), np.int32)
+                pv = np.empty(max(pz.value, 1), np.float64)
+                cf = np.empty(max(m, 1), np.int32)
+                lib.orc_amg_level_copy(self._h, l, _p(lap), _p(lac), _p(lav), _p(pp), _p(pc), _p(pv), _p(cf))
+                P = (pp, pc[:pz.value], pv[:pz.value])
+                cf = cf[:m]
+            else:
+                lib.orc_amg_level_copy(self._h, l, _p(lap), _p(lac), _p(lav), None, None, None, None)
+                P, cf = None, None
+            self.levels.append(AMGLevel(m, (lap, lac[:nz.value], lav[:nz.value]), P, cf))
+
+    def vcycle(self, S: Scaled, x, b, mL: int, mU: int, nu: int = 1):
+        """One V-cycle (Alg. mgcycle) from x: ILU smoother (m_L + m_U sweeps on S) on the finest
+        level, nu l1-Jacobi sweeps below, direct solve on the coarsest.  Returns a new array."""
+        n = self.levels[0].n
+        x = np.ascontiguousarray(x, np.float64).reshape(n).copy()
+        b = np.ascontiguousarray(b, np.float64).reshape(n)
+        lp, lc, lv = _csr(S.L)
+        sp, sc, sv = _csr(S.Us)
+        st = _load().orc_amg_vcycle(self._h, _p(lp), _p(lc), _p(lv), _p(sp), _p(sc), _p(sv), _p(S.dinv), int(mL),
+                                    int(mU), int(nu), _p(x), _p(b))
+        if st:
+            raise OracleError(st, "amg_vcycle")
+        return x
+
+    def __del__(self):
+        try:
+            if self._h:
+                _load().orc_amg_free(self._h)
+                self._h = None
+        except Exception:
+            pass

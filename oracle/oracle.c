@@ -18,6 +18,11 @@
  * scaling (Eq. extractD, Eq. newD) Utilde = D^{-1} U = I + Utilde_s; only
  * Utilde_s and dinv = 1 / diag(U) are stored.
  *
+ * Beyond the smoother itself: the polynomial Gauss-Seidel smoother of
+ * Sec. 3.1, row/column (Ruiz) scaling (Eq. rowcolScale), power-iteration
+ * estimates of ||T_s^p||_2 (Fig. Up), and algebraic multigrid (Sec. 3,
+ * Alg. mgcycle) with the ILU smoother on the finest level.
+ *
  * Parity pins for every function live in tests/test_oracle_*.py.  Unpinned
  * parts: none of the functions here is left without a pin, but the ILUT drop
  * rule (Saad's dual threshold, which the paper uses without defining it) is
@@ -1297,4 +1302,447 @@ int orc_power_norms(int64_t n, const int64_t* tp, const int32_t* tc, const doubl
   free(a);
   free(b);
   return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algebraic multigrid (Sec. 3: Ruge-Stueben coarsening with the strength    */
+/* threshold theta, Galerkin coarse operators A_{l+1} = P^T A_l P, and the   */
+/* V-cycle of Alg. mgcycle with the ILU smoother on the finest level)        */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_AMG_MAXLEV 32
+
+typedef struct {
+  int64_t n, nc;
+  int64_t* ap; /* A_l */
+  int32_t* ac;
+  double* av;
+  int64_t* pp; /* P_l: n x nc (NULL on the coarsest level) */
+  int32_t* pc;
+  double* pv;
+  int32_t* cf; /* 1 = coarse point, 0 = fine point */
+} orc_amg_level;
+
+typedef struct {
+  int nlev;
+  orc_amg_level lev[ORC_AMG_MAXLEV];
+} orc_amg;
+
+void orc_amg_free(orc_amg* h) {
+  if (!h) return;
+  for (int l = 0; l < h->nlev; ++l) {
+    free(h->lev[l].ap);
+    free(h->lev[l].ac);
+    free(h->lev[l].av);
+    free(h->lev[l].pp);
+    free(h->lev[l].pc);
+    free(h->lev[l].pv);
+    free(h->lev[l].cf);
+  }
+  free(h);
+}
+
+/*
+ * Strength of connection (Sec. 3): j != i strongly influences i when
+ * |a_ij| >= theta * max_{k != i} |a_ik|.  s[p] = 1 marks such an entry p of
+ * row i; a row without off-diagonal entries has none.
+ */
+static void amg_strength(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, double theta,
+                         char* s) {
+  for (int64_t i = 0; i < n; ++i) {
+    double mx = 0.0;
+    for (int64_t p = ap[i]; p < ap[i + 1]; ++p)
+      if (ac[p] != i && fabs(av[p]) > mx) mx = fabs(av[p]);
+    for (int64_t p = ap[i]; p < ap[i + 1]; ++p)
+      s[p] = (char)(ac[p] != i && mx > 0.0 && fabs(av[p]) >= theta * mx);
+  }
+}
+
+/*
+ * Ruge-Stueben first pass.  lambda_i = number of points that i strongly
+ * influences.  Repeatedly the undecided point of largest lambda (smallest
+ * index among equals) becomes C; every undecided point it strongly
+ * influences becomes F, and each undecided point that strongly influences
+ * a new F point gains one in lambda.  When the largest lambda left is zero,
+ * the remaining undecided points become F.  The scan for the largest lambda
+ * is a plain loop over all points.
+ */
+static void amg_split(int64_t n, const int64_t* ap, const int32_t* ac, const char* s, int32_t* cf) {
+  int64_t* lam = (int64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  char* und = (char*)malloc((size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) {
+    und[i] = 1;
+    cf[i] = 0;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = ap[i]; p < ap[i + 1]; ++p)
+      if (s[p]) lam[ac[p]]++;
+  /* S^T: for each point k the rows j with k in S_j, in ascending j */
+  int64_t* stp = (int64_t*)calloc((size_t)(n + 1), sizeof(int64_t));
+  int64_t* stj = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ap[n] + 1));
+  for (int64_t k = 0; k < n; ++k) stp[k + 1] = stp[k] + lam[k];
+  {
+    int64_t* f = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    for (int64_t k = 0; k < n; ++k) f[k] = stp[k];
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t p = ap[j]; p < ap[j + 1]; ++p)
+        if (s[p]) stj[f[ac[p]]++] = j;
+    free(f);
+  }
+  for (;;) {
+    int64_t best = -1;
+    for (int64_t i = 0; i < n; ++i)
+      if (und[i] && (best < 0 || lam[i] > lam[best])) best = i;
+    if (best < 0) break;
+    if (lam[best] == 0) {
+      for (int64_t i = 0; i < n; ++i) und[i] = 0; /* the rest become F */
+      break;
+    }
+    cf[best] = 1;
+    und[best] = 0;
+    /* points j that best strongly influences (best in S_j), ascending j */
+    for (int64_t t = stp[best]; t < stp[best + 1]; ++t) {
+      const int64_t j = stj[t];
+      if (!und[j]) continue;
+      und[j] = 0; /* F */
+      for (int64_t p = ap[j]; p < ap[j + 1]; ++p)
+        if (s[p] && und[ac[p]]) lam[ac[p]]++;
+    }
+  }
+  free(lam);
+  free(und);
+  free(stp);
+  free(stj);
+}
+
+/*
+ * Direct interpolation (Stueben's, the classical choice of Ruge and
+ * Stueben).  For a C point, its own coarse value.  For an F point i with
+ * strong coarse neighbours C_i:  with sneg / spos the sums of the negative /
+ * positive off-diagonal entries of row i and cneg / cpos the same over C_i,
+ * d = a_ii, plus spos when cpos = 0 and plus sneg when cneg = 0, and
+ * w_ij = -(alpha a_ij) / d, alpha = sneg / cneg for a_ij < 0, spos / cpos for
+ * a_ij > 0.  An F point without strong coarse neighbours gets an empty row.
+ */
+static int amg_interp(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, const char* s,
+                      const int32_t* cf, int64_t** pp_o, int32_t** pc_o, double** pv_o, int64_t* nc_o) {
+  int64_t* cidx = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  int64_t nc = 0;
+  for (int64_t i = 0; i < n; ++i) cidx[i] = cf[i] ? nc++ : -1;
+  int64_t* pp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  int64_t cap = ap[n] + n + 1;
+  int32_t* pc = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+  double* pv = (double*)malloc(sizeof(double) * (size_t)cap);
+  int64_t q = 0;
+  pp[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (cf[i]) {
+      pc[q] = (int32_t)cidx[i];
+      pv[q] = 1.0;
+      ++q;
+    } else {
+      double aii = 0.0, sneg = 0.0, spos = 0.0, cneg = 0.0, cpos = 0.0;
+      for (int64_t p = ap[i]; p < ap[i + 1]; ++p) {
+        const int32_t j = ac[p];
+        if (j == i) {
+          aii = aii + av[p];
+          continue;
+        }
+        if (av[p] < 0.0) sneg = sneg + av[p];
+        if (av[p] > 0.0) spos = spos + av[p];
+        if (s[p] && cf[j]) {
+          if (av[p] < 0.0) cneg = cneg + av[p];
+          if (av[p] > 0.0) cpos = cpos + av[p];
+        }
+      }
+      double d = aii;
+      if (cpos == 0.0) d = d + spos;
+      if (cneg == 0.0) d = d + sneg;
+      const double alpha = (cneg != 0.0) ? sneg / cneg : 0.0;
+      const double beta = (cpos != 0.0) ? spos / cpos : 0.0;
+      for (int64_t p = ap[i]; p < ap[i + 1]; ++p) {
+        const int32_t j = ac[p];
+        if (j == i || !s[p] || !cf[j]) continue;
+        const double f = av[p] < 0.0 ? alpha : beta;
+        pc[q] = (int32_t)cidx[j];
+        pv[q] = -(f * av[p]) / d;
+        ++q;
+      }
+    }
+    pp[i + 1] = q;
+  }
+  free(cidx);
+  *pp_o = pp;
+  *pc_o = pc;
+  *pv_o = pv;
+  *nc_o = nc;
+  return ORC_OK;
+}
+
+/*
+ * Galerkin product A_c = P^T A P (Sec. 3): entry (I, J) is the sum over fine
+ * i with p_iI != 0 (ascending), then over j in row i of A (ascending), then
+ * over J in row j of P, of (p_iI a_ij) p_jJ, added in that order.  Every
+ * entry that receives a contribution is stored (columns ascending).
+ */
+static void amg_galerkin(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, const int64_t* pp,
+                         const int32_t* pc, const double* pv, int64_t nc, int64_t** cp_o, int32_t** cc_o,
+                         double** cv_o) {
+  /* rows of P^T: for each coarse I the fine i with p_iI != 0, ascending */
+  int64_t* tp = (int64_t*)calloc((size_t)(nc + 1), sizeof(int64_t));
+  for (int64_t q = 0; q < pp[n]; ++q) tp[pc[q] + 1]++;
+  for (int64_t I = 0; I < nc; ++I) tp[I + 1] += tp[I];
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nc + 1));
+  int32_t* ti = (int32_t*)malloc(sizeof(int32_t) * (size_t)(pp[n] + 1));
+  double* tv = (double*)malloc(sizeof(double) * (size_t)(pp[n] + 1));
+  for (int64_t I = 0; I < nc; ++I) fill[I] = tp[I];
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t q = pp[i]; q < pp[i + 1]; ++q) {
+      ti[fill[pc[q]]] = (int32_t)i;
+      tv[fill[pc[q]]] = pv[q];
+      fill[pc[q]]++;
+    }
+  double* acc = (double*)calloc((size_t)(nc > 0 ? nc : 1), sizeof(double));
+  char* hit = (char*)calloc((size_t)(nc > 0 ? nc : 1), 1);
+  int64_t cap = 16, len = 0;
+  int64_t* cp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nc + 1));
+  int32_t* cc = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+  double* cv = (double*)malloc(sizeof(double) * (size_t)cap);
+  cp[0] = 0;
+  for (int64_t I = 0; I < nc; ++I) {
+    for (int64_t t = tp[I]; t < tp[I + 1]; ++t) {
+      const int64_t i = ti[t];
+      const double piI = tv[t];
+      for (int64_t p = ap[i]; p < ap[i + 1]; ++p) {
+        const int64_t j = ac[p];
+        const double w = piI * av[p];
+        for (int64_t q = pp[j]; q < pp[j + 1]; ++q) {
+          acc[pc[q]] = acc[pc[q]] + w * pv[q];
+          hit[pc[q]] = 1;
+        }
+      }
+    }
+    for (int64_t J = 0; J < nc; ++J) { /* plain scan of the dense accumulator */
+      if (!hit[J]) continue;
+      if (len == cap) {
+        cap *= 2;
+        cc = (int32_t*)realloc(cc, sizeof(int32_t) * (size_t)cap);
+        cv = (double*)realloc(cv, sizeof(double) * (size_t)cap);
+      }
+      cc[len] = (int32_t)J;
+      cv[len] = acc[J];
+      ++len;
+      acc[J] = 0.0;
+      hit[J] = 0;
+    }
+    cp[I + 1] = len;
+  }
+  free(tp);
+  free(fill);
+  free(ti);
+  free(tv);
+  free(acc);
+  free(hit);
+  *cp_o = cp;
+  *cc_o = cc;
+  *cv_o = cv;
+}
+
+/*
+ * AMG setup: levels are coarsened while the level has more than
+ * coarse_size rows and fewer than max_levels levels exist; a level whose
+ * split gives no C point, or only C points, ends the hierarchy.  The input
+ * matrix is copied as level 0.
+ */
+orc_amg* orc_amg_setup(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, double theta,
+                       int max_levels, int64_t coarse_size, int* status) {
+  orc_amg* h = (orc_amg*)calloc(1, sizeof(orc_amg));
+  *status = ORC_OK;
+  if (max_levels > ORC_AMG_MAXLEV) max_levels = ORC_AMG_MAXLEV;
+  if (max_levels < 1) max_levels = 1;
+  orc_amg_level* L0 = &h->lev[0];
+  L0->n = n;
+  L0->ap = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  L0->ac = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ap[n] + 1));
+  L0->av = (double*)malloc(sizeof(double) * (size_t)(ap[n] + 1));
+  memcpy(L0->ap, ap, sizeof(int64_t) * (size_t)(n + 1));
+  memcpy(L0->ac, ac, sizeof(int32_t) * (size_t)ap[n]);
+  memcpy(L0->av, av, sizeof(double) * (size_t)ap[n]);
+  h->nlev = 1;
+  while (h->nlev < max_levels) {
+    orc_amg_level* L = &h->lev[h->nlev - 1];
+    if (L->n <= coarse_size) break;
+    char* s = (char*)malloc((size_t)(L->ap[L->n] + 1));
+    int32_t* cf = (int32_t*)malloc(sizeof(int32_t) * (size_t)(L->n + 1));
+    amg_strength(L->n, L->ap, L->ac, L->av, theta, s);
+    amg_split(L->n, L->ap, L->ac, s, cf);
+    int64_t nc = 0;
+    for (int64_t i = 0; i < L->n; ++i) nc += cf[i];
+    if (nc == 0 || nc == L->n) {
+      free(s);
+      free(cf);
+      break;
+    }
+    amg_interp(L->n, L->ap, L->ac, L->av, s, cf, &L->pp, &L->pc, &L->pv, &L->nc);
+    L->cf = cf;
+    free(s);
+    orc_amg_level* C = &h->lev[h->nlev];
+    C->n = nc;
+    amg_galerkin(L->n, L->ap, L->ac, L->av, L->pp, L->pc, L->pv, nc, &C->ap, &C->ac, &C->av);
+    h->nlev++;
+  }
+  return h;
+}
+
+int orc_amg_nlev(const orc_amg* h) { return h->nlev; }
+
+/* Sizes of level l: rows, entries of A_l, coarse points and entries of P_l (0 on the coarsest). */
+void orc_amg_level_sizes(const orc_amg* h, int l, int64_t* n, int64_t* nnz, int64_t* nc, int64_t* pnnz) {
+  const orc_amg_level* L = &h->lev[l];
+  *n = L->n;
+  *nnz = L->ap[L->n];
+  *nc = L->pp ? L->nc : 0;
+  *pnnz = L->pp ? L->pp[L->n] : 0;
+}
+
+/* Copy level l out (any pointer may be NULL; P and cf only below the coarsest level). */
+void orc_amg_level_copy(const orc_amg* h, int l, int64_t* ap, int32_t* ac, double* av, int64_t* pp, int32_t* pc,
+                        double* pv, int32_t* cf) {
+  const orc_amg_level* L = &h->lev[l];
+  if (ap) memcpy(ap, L->ap, sizeof(int64_t) * (size_t)(L->n + 1));
+  if (ac) memcpy(ac, L->ac, sizeof(int32_t) * (size_t)L->ap[L->n]);
+  if (av) memcpy(av, L->av, sizeof(double) * (size_t)L->ap[L->n]);
+  if (L->pp) {
+    if (pp) memcpy(pp, L->pp, sizeof(int64_t) * (size_t)(L->n + 1));
+    if (pc) memcpy(pc, L->pc, sizeof(int32_t) * (size_t)L->pp[L->n]);
+    if (pv) memcpy(pv, L->pv, sizeof(double) * (size_t)L->pp[L->n]);
+    if (cf) memcpy(cf, L->cf, sizeof(int32_t) * (size_t)L->n);
+  }
+}
+
+/* x = A^{-1} b for a small dense copy of A: Gaussian elimination with partial pivoting. */
+static int dense_solve(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, const double* b,
+                       double* x) {
+  double* M = (double*)calloc((size_t)(n * n > 0 ? n * n : 1), sizeof(double));
+  double* y = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!M || !y) {
+    free(M);
+    free(y);
+    return ORC_NOMEM;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t p = ap[i]; p < ap[i + 1]; ++p) M[i * n + ac[p]] = M[i * n + ac[p]] + av[p];
+    y[i] = b[i];
+  }
+  for (int64_t k = 0; k < n; ++k) {
+    int64_t piv = k;
+    for (int64_t i = k + 1; i < n; ++i)
+      if (fabs(M[i * n + k]) > fabs(M[piv * n + k])) piv = i;
+    if (M[piv * n + k] == 0.0) {
+      free(M);
+      free(y);
+      return ORC_ZERO_PIVOT;
+    }
+    if (piv != k) {
+      for (int64_t j = 0; j < n; ++j) {
+        const double t = M[k * n + j];
+        M[k * n + j] = M[piv * n + j];
+        M[piv * n + j] = t;
+      }
+      const double t = y[k];
+      y[k] = y[piv];
+      y[piv] = t;
+    }
+    for (int64_t i = k + 1; i < n; ++i) {
+      const double f = M[i * n + k] / M[k * n + k];
+      if (f == 0.0) continue;
+      for (int64_t j = k; j < n; ++j) M[i * n + j] = M[i * n + j] - f * M[k * n + j];
+      y[i] = y[i] - f * y[k];
+    }
+  }
+  for (int64_t i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int64_t j = i + 1; j < n; ++j) s = s - M[i * n + j] * x[j];
+    x[i] = s / M[i * n + i];
+  }
+  free(M);
+  free(y);
+  return ORC_OK;
+}
+
+/* nu sweeps of l1-Jacobi on level L: x <- x + (b - A x) / d, d_i = sum_j |a_ij|. */
+static void l1_jacobi(const orc_amg_level* L, const double* b, double* x, int nu) {
+  const int64_t n = L->n;
+  double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int k = 0; k < nu; ++k) {
+    orc_residual(n, 1, L->ap, L->ac, L->av, x, b, r);
+    for (int64_t i = 0; i < n; ++i) {
+      double d = 0.0;
+      for (int64_t p = L->ap[i]; p < L->ap[i + 1]; ++p) d = d + fabs(L->av[p]);
+      x[i] = x[i] + r[i] / d;
+    }
+  }
+  free(r);
+}
+
+typedef struct {
+  const int64_t *lp, *sp;
+  const int32_t *lc, *sc;
+  const double *lv, *sv, *dinv;
+  int mL, mU, nu;
+} amg_smoother;
+
+/* Alg. mgcycle, Multilevel(A_l, b, x, l) with nu = 1 (V-cycle). */
+static int multilevel(const orc_amg* h, int l, const amg_smoother* sm, const double* b, double* x) {
+  const orc_amg_level* L = &h->lev[l];
+  const int64_t n = L->n;
+  if (l == h->nlev - 1) /* coarsest level: direct solve */
+    return dense_solve(n, L->ap, L->ac, L->av, b, x);
+  int st;
+  if (l == 0) { /* pre-smoothing with the ILU smoother */
+    if ((st = orc_smooth(n, 1, L->ap, L->ac, L->av, sm->lp, sm->lc, sm->lv, sm->sp, sm->sc, sm->sv, sm->dinv, x, b,
+                         sm->mL, sm->mU)))
+      return st;
+  } else {
+    l1_jacobi(L, b, x, sm->nu);
+  }
+  double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* bc = (double*)calloc((size_t)(L->nc > 0 ? L->nc : 1), sizeof(double));
+  double* v = (double*)calloc((size_t)(L->nc > 0 ? L->nc : 1), sizeof(double));
+  orc_residual(n, 1, L->ap, L->ac, L->av, x, b, r);
+  /* r_{l+1} = R_l r with R_l = P_l^T: scatter row by row */
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t q = L->pp[i]; q < L->pp[i + 1]; ++q) bc[L->pc[q]] = bc[L->pc[q]] + L->pv[q] * r[i];
+  st = multilevel(h, l + 1, sm, bc, v);
+  if (!st) {
+    for (int64_t i = 0; i < n; ++i) { /* x = x + P_l v */
+      double s = 0.0;
+      for (int64_t q = L->pp[i]; q < L->pp[i + 1]; ++q) s = s + L->pv[q] * v[L->pc[q]];
+      x[i] = x[i] + s;
+    }
+    if (l == 0)
+      st = orc_smooth(n, 1, L->ap, L->ac, L->av, sm->lp, sm->lc, sm->lv, sm->sp, sm->sc, sm->sv, sm->dinv, x, b,
+                      sm->mL, sm->mU);
+    else
+      l1_jacobi(L, b, x, sm->nu);
+  }
+  free(r);
+  free(bc);
+  free(v);
+  return st;
+}
+
+/*
+ * One V-cycle (Alg. mgcycle, nu = 1) on A_0 x = b, updating x in place:
+ * the finest level is smoothed before and after the coarse-grid correction
+ * by the ILU smoother (m_L + m_U Richardson sweeps on the row-scaled factors
+ * L_s, Utilde_s, dinv), every coarser level by nu sweeps of l1-Jacobi, and
+ * the coarsest level is solved directly.  A single-level hierarchy is one
+ * direct solve.
+ */
+int orc_amg_vcycle(const orc_amg* h, const int64_t* lp, const int32_t* lc, const double* lv, const int64_t* sp,
+                   const int32_t* sc, const double* sv, const double* dinv, int mL, int mU, int nu, double* x,
+                   const double* b) {
+  amg_smoother sm = {lp, sp, lc, sc, lv, sv, dinv, mL, mU, nu};
+  return multilevel(h, 0, &sm, b, x);
 }
