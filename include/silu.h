@@ -93,8 +93,9 @@ typedef enum { SILU_SCALE_NONE = 0, SILU_SCALE_ROW = 1, SILU_SCALE_NONE_RICH = 2
  * r = b - A x, FGMRES and the solution vector stay FP64). */
 typedef enum { SILU_FP64 = 0, SILU_FP32 = 1 } silu_prec;
 
-/* Preconditioner inside fgmres_solve. */
-typedef enum { SILU_PRECOND_SWEEPS = 0, SILU_PRECOND_DIRECT = 1, SILU_PRECOND_NONE = 2 } silu_precond;
+/* Preconditioner inside fgmres_solve.  SILU_PRECOND_AMG: one AMG V-cycle
+ * from zero (silu_amg_setup must have been called on the factor object). */
+typedef enum { SILU_PRECOND_SWEEPS = 0, SILU_PRECOND_DIRECT = 1, SILU_PRECOND_NONE = 2, SILU_PRECOND_AMG = 3 } silu_precond;
 
 typedef struct silu_ctx_s* silu_ctx;
 typedef struct silu_mat_s* silu_mat;
@@ -327,6 +328,48 @@ silu_status silu_ilu_set_kernel(silu_ilu F, int variant);
  * Works on host-only contexts (in_use = 0 there).  Any pointer may be NULL.
  */
 silu_status silu_ilu_layout(silu_ilu F, double* pad_natural, double* pad_sorted, int32_t* in_use);
+
+/*
+ * Algebraic multigrid (Sec. 3, Alg. mgcycle): the paper's solver
+ * configuration, a V-cycle whose finest level is smoothed by the scaled-ILU
+ * smoother.
+ *
+ * silu_amg_setup builds the hierarchy of A (the silu_mat F was set up from)
+ * on the host and uploads it; it is attached to F and freed with it (a second
+ * call replaces it).  Strength of connection (Sec. 3): j strongly influences
+ * i when |a_ij| >= theta max_{k != i} |a_ik|.  Coarse points: the
+ * Ruge-Stueben first pass (largest number of strongly influenced points
+ * first, smallest index on ties).  Interpolation: Stueben's direct
+ * interpolation from the strong coarse neighbours.  Coarse operators:
+ * A_{l+1} = P^T A_l P.  Coarsening stops at max_levels levels, at
+ * coarse_size rows or fewer, or when no further split is possible; the
+ * coarsest level (at most 4096 rows, else SILU_ERR_INVALID_ARG) is solved by
+ * its dense inverse.  Levels below the finest are smoothed by jacobi_sweeps
+ * sweeps of l1-Jacobi, x <- x + D^{-1}(b - A x) with d_i = sum_j |a_ij|, before
+ * and after their coarse-grid correction.  params NULL = {0.25, 25, 400, 1}.
+ * Blocks.
+ */
+typedef struct {
+  double theta;       /* strength threshold, 0 < theta <= 1 */
+  int max_levels;     /* >= 1 */
+  int coarse_size;    /* stop coarsening at this many rows or fewer, >= 1 */
+  int jacobi_sweeps;  /* l1-Jacobi sweeps before and after the correction below the finest level */
+} silu_amg_params;
+silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params);
+/*
+ * One V-cycle on A x = b (device, one right-hand side, x in/out, stream-
+ * ordered): the finest level is smoothed before and after the coarse-grid
+ * correction by ilu_smooth's update with sweeps_L / sweeps_U sweeps of F's
+ * smoother.  A one-level hierarchy is the direct solve x = A^{-1} b.
+ */
+silu_status silu_amg_vcycle(silu_ilu F, double* x, const double* b, int sweeps_L, int sweeps_U);
+/* Levels and, for l < cap, rows, entries of A_l and of P_l (0 on the coarsest level). */
+silu_status silu_amg_stats(silu_ilu F, int cap, int* levels, int64_t* rows, int64_t* nnz_A, int64_t* nnz_P);
+/* Host copies of level l (parity tests): A_l (row pointers n_l + 1), P_l
+ * (row pointers n_l + 1) and the coarse-point marks (n_l), the last two only
+ * below the coarsest level.  Any pointer may be NULL. */
+silu_status silu_amg_export_level(silu_ilu F, int level, int64_t* Ap, int32_t* Ac, double* Av, int64_t* Pp,
+                                  int32_t* Pc, double* Pv, int32_t* cf);
 
 /*
  * Batches of independent systems (many pressure solves of uneven size).

@@ -34,7 +34,7 @@ SCALE_NONE, SCALE_ROW, SCALE_NONE_RICH, SCALE_ROWCOL = 0, 1, 2, 3
 # silu_prec
 FP64, FP32 = 0, 1
 # silu_precond
-PRECOND_SWEEPS, PRECOND_DIRECT, PRECOND_NONE = 0, 1, 2
+PRECOND_SWEEPS, PRECOND_DIRECT, PRECOND_NONE, PRECOND_AMG = 0, 1, 2, 3
 # silu_kclass
 K_RESIDUAL, K_SWEEP_L, K_SWEEP_U, K_LEVEL, K_KRYLOV, K_ELEMENTWISE = range(6)
 K_NAMES = ["residual", "sweep_L", "sweep_U", "level", "krylov", "elementwise"]
@@ -101,6 +101,10 @@ def load():
         "silu_ilu_export_sizes": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "silu_ilu_export_colscale": (i32, [vp, vp, ctypes.POINTER(ctypes.c_int32)]),
         "silu_ilu_power_norms": (i32, [vp, i32, i32, i32, vp, vp]),
+        "silu_amg_setup": (i32, [vp, vp]),
+        "silu_amg_vcycle": (i32, [vp, vp, vp, i32, i32]),
+        "silu_amg_stats": (i32, [vp, i32, ctypes.POINTER(i32), vp, vp, vp]),
+        "silu_amg_export_level": (i32, [vp, i32] + [vp] * 7),
         "silu_ilu_destroy": (None, [vp]),
         "silu_ilu_set_lanes": (i32, [vp, i32, i32, i32]),
         "silu_ctx_profile": (i32, [vp, i32]),
@@ -140,7 +144,8 @@ def exported_symbols():
     return ["silu_version", "silu_ctx_create", "silu_ctx_destroy", "silu_last_error", "silu_mat_create",
             "silu_mat_destroy", "silu_mat_residual", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
-            "silu_ilu_export_colscale", "silu_ilu_power_norms",
+            "silu_ilu_export_colscale", "silu_ilu_power_norms", "silu_amg_setup", "silu_amg_vcycle",
+            "silu_amg_stats", "silu_amg_export_level",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
             "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_layout", "silu_ilu_tune_table", "silu_ctx_set_overlap",
             "silu_smooth_noalloc",
@@ -231,6 +236,12 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+class AmgParams(ctypes.Structure):
+    """silu_amg_params."""
+    _fields_ = [("theta", ctypes.c_double), ("max_levels", ctypes.c_int), ("coarse_size", ctypes.c_int),
+                ("jacobi_sweeps", ctypes.c_int)]
 
 
 class Matrix:
@@ -340,6 +351,42 @@ class ILU:
                                          _ptr(out))
         _check(self.ctx.handle, st, "silu_ilu_power_norms")
         return out[:pmax]
+
+    def amg_setup(self, theta: float = 0.25, max_levels: int = 25, coarse_size: int = 400, jacobi_sweeps: int = 1):
+        """Build and attach the AMG hierarchy of A (Sec. 3); this factor object smooths its finest level."""
+        p = AmgParams(float(theta), int(max_levels), int(coarse_size), int(jacobi_sweeps))
+        _check(self.ctx.handle, load().silu_amg_setup(self.handle, ctypes.byref(p)), "silu_amg_setup")
+
+    def amg_vcycle(self, x, b, sweeps_L: int, sweeps_U: int):
+        """One V-cycle on A x = b (device tensors of length n), x in/out."""
+        _check(self.ctx.handle, load().silu_amg_vcycle(self.handle, _ptr(x), _ptr(b), int(sweeps_L),
+                                                       int(sweeps_U)), "silu_amg_vcycle")
+
+    def amg_stats(self):
+        """Per level: rows, entries of A_l, entries of P_l."""
+        lev = ctypes.c_int()
+        rows, nza, nzp = (np.zeros(64, np.int64) for _ in range(3))
+        _check(self.ctx.handle, load().silu_amg_stats(self.handle, 64, ctypes.byref(lev), _ptr(rows), _ptr(nza),
+                                                      _ptr(nzp)), "silu_amg_stats")
+        k = lev.value
+        return {"levels": k, "rows": rows[:k].tolist(), "nnz_A": nza[:k].tolist(), "nnz_P": nzp[:k].tolist()}
+
+    def amg_level(self, level: int):
+        """Host copies of level `level`: A_l, P_l (None on the coarsest level), coarse-point marks."""
+        st = self.amg_stats()
+        n, nza, nzp = st["rows"][level], st["nnz_A"][level], st["nnz_P"][level]
+        Ap = np.empty(n + 1, np.int64)
+        Ac, Av = np.empty(max(nza, 1), np.int32), np.empty(max(nza, 1), np.float64)
+        last = level == st["levels"] - 1
+        Pp = np.empty(n + 1, np.int64)
+        Pc, Pv = np.empty(max(nzp, 1), np.int32), np.empty(max(nzp, 1), np.float64)
+        cf = np.empty(max(n, 1), np.int32)
+        _check(self.ctx.handle, load().silu_amg_export_level(self.handle, int(level), _ptr(Ap), _ptr(Ac), _ptr(Av),
+                                                             None if last else _ptr(Pp), None if last else _ptr(Pc),
+                                                             None if last else _ptr(Pv),
+                                                             None if last else _ptr(cf)), "silu_amg_export_level")
+        return {"A": (Ap, Ac[:nza], Av[:nza]), "P": None if last else (Pp, Pc[:nzp], Pv[:nzp]),
+                "cf": None if last else cf[:n]}
 
     def reserve(self, nrhs: int = 1, restart: int = 0):
         _check(self.ctx.handle, load().silu_ilu_reserve(self.handle, nrhs, restart), "silu_ilu_reserve")

@@ -8,10 +8,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
 
+#include "amg_setup.h"
 #include "device.cuh"
 #include "host_factor.h"
 #include "silu.h"
@@ -118,6 +120,28 @@ struct SortedBufs {
   DBuf rp, ci, va, perm, tiles;
 };
 
+// Device copy of one AMG level (Sec. 3).  Level 0's operator is the
+// silu_mat's; coarser levels keep their own.  P is stored negated so that the
+// prolongation x += P v is the sweep kernel's x += c - (-P) v with c = 0.
+struct AmgDevLevel {
+  int64_t n = 0;
+  DBuf A_rp, A_ci, A_va, A_tiles, P_rp, P_ci, P_va, P_tiles, R_rp, R_ci, R_va, R_tiles;
+  DevCsr A, Pneg, R;
+  DBuf l1inv, x, t, b, r;
+};
+
+// An AMG hierarchy attached to a factor object: the factors smooth the
+// finest level, l1-Jacobi the coarser ones, the coarsest is solved directly.
+struct AmgState {
+  silu::AmgHost host;
+  std::vector<std::unique_ptr<AmgDevLevel>> lev;
+  DBuf cinv;  // dense inverse of the coarsest operator
+  int nu = 1;  // l1-Jacobi sweeps before and after the correction on levels >= 1
+  double theta = 0.25;
+  int max_levels = 25;
+  int64_t coarse_size = 400;
+};
+
 struct silu_ilu_s {
   silu_ctx ctx = nullptr;
   silu_mat A = nullptr;
@@ -150,6 +174,7 @@ struct silu_ilu_s {
   int variant = 0;  // 0 auto, 1 plain lanes-per-row kernel, 2 staged kernel where possible
   int autoL = 4, autoU = 4, autoA = 8;
   Workspace ws;
+  std::unique_ptr<AmgState> amg;  // silu_amg_setup
 };
 
 // The upper sweep factor is a unit-diagonal scaled copy (F->Us) rather than raw U.
@@ -291,6 +316,11 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
 // (used while a stream capture is recording).
 void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, bool x_zero,
                   bool inline_levels = false);
+// One AMG V-cycle (Alg. mgcycle) on A x = b for one right-hand side, the
+// finest level smoothed by m_L + m_U sweeps of F's smoother (x_zero: x is
+// an output, the cycle starts from zero).  Requires F->amg and F's
+// one-column workspace.
+void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_zero);
 // Ruiz equilibration limits for SILU_SCALE_ROWCOL.
 constexpr int kRuizMaxit = 20;
 constexpr double kRuizTol = 1e-2;

@@ -261,3 +261,38 @@ def test_rowcol_scaling_matches_oracle(ctx, kind, tau, fill):
     G = silu.ILU(silu.Matrix(ctx, *A), kind, tau, fill)
     with pytest.raises(silu.SiluError):
         G.colscale()
+
+
+@pytest.mark.parametrize("gen,theta", [("cutcell", 0.25), ("hex27", 0.25), ("poisson", 0.5), ("cutcell", 0.05)])
+def test_amg_hierarchy_matches_oracle(ctx, gen, theta):
+    """AMG setup (Sec. 3): the library's C/F splits, interpolation and Galerkin
+    operators equal the oracle's bit for bit on every level (both sum in the
+    same stated orders without FMA contraction)."""
+    A = {"cutcell": lambda: synth.cutcell7(11, 10, 9, seed=4), "hex27": lambda: synth.hex27(9, 8, 8, seed=5),
+         "poisson": lambda: synth.poisson7(12, 11, 10)}[gen]()
+    F = silu.ILU(silu.Matrix(ctx, *A), "ilu0")
+    F.amg_setup(theta=theta, max_levels=10, coarse_size=30, jacobi_sweeps=1)
+    H = oracle.AMG(A, theta=theta, max_levels=10, coarse_size=30)
+    st = F.amg_stats()
+    assert st["levels"] == len(H.levels) and st["levels"] >= 3
+    for l, OL in enumerate(H.levels):
+        mine = F.amg_level(l)
+        for a, b in zip(mine["A"], OL.A):
+            assert np.array_equal(a, b), (l, "A")
+        if OL.P is None:
+            assert mine["P"] is None
+            continue
+        assert np.array_equal(mine["cf"], OL.cf), l
+        for a, b in zip(mine["P"], OL.P):
+            assert np.array_equal(a, b), (l, "P")
+
+
+def test_amg_bad_parameters(ctx):
+    A = synth.poisson7(5)
+    F = silu.ILU(silu.Matrix(ctx, *A), "ilu0")
+    for kw in ({"theta": 0.0}, {"theta": 1.5}, {"max_levels": 0}, {"coarse_size": 0}, {"jacobi_sweeps": -1}):
+        with pytest.raises(silu.SiluError) as e:
+            F.amg_setup(**kw)
+        assert e.value.status == silu.ERR_INVALID_ARG
+    with pytest.raises(silu.SiluError):
+        F.amg_stats()
