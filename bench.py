@@ -375,6 +375,8 @@ def run_silu(args):
     if not args.no_serve and rank == 0:
         serve = serving(silu, args)
 
+    amg = amg_comparison(silu, ctx, torch, args.amg_edge) if (args.amg_edge > 0 and rank == 0) else None
+
     p32 = poisson32(silu, ctx, torch) if rank == 0 else None
     study = sweep_study(silu, ctx, torch) if (args.study and rank == 0) else None
 
@@ -412,6 +414,8 @@ def run_silu(args):
             line["batch"] = batch
         if serve:
             line["serving"] = serve
+        if amg:
+            line["amg"] = amg
         if p32:
             line["poisson32"] = p32
         if study:
@@ -591,6 +595,60 @@ def serving(silu, args):
     return out
 
 
+def amg_comparison(silu, ctx, torch, edge: int):
+    """GMRES + AMG, the paper's solver configuration (Sec. 3, Sec. 6): the
+    cut-cell 7-point matrix on edge^3 (seed 1, one right-hand side U[-1,1),
+    seed 1), FP64 ILU(0) factors smoothing the finest level of a Ruge-Stueben
+    hierarchy (theta 0.25, coarsest <= 400 rows, one l1-Jacobi sweep before and
+    after each coarser correction).  FGMRES(30) to 1e-8 with one V-cycle as the
+    preconditioner, the finest level smoothed by 3+3 Richardson sweeps against
+    the same cycle smoothed by exact level-scheduled triangular solves (the
+    comparison behind the paper's GMRES+AMG gains), and the single-level
+    3+3-sweep smoother for reference.  Also each V-cycle's time alone."""
+    import synth
+    A = synth.cutcell7(edge, seed=1)
+    n = len(A[0]) - 1
+    M = silu.Matrix(ctx, *A)
+    F = silu.ilu_setup(ctx, M, "ilu0")
+    t0 = time.perf_counter()
+    F.amg_setup(theta=0.25, max_levels=25, coarse_size=400, jacobi_sweeps=1)
+    setup_s = time.perf_counter() - t0
+    st = F.amg_stats()
+    st_f = F.stats()
+    out = {"workload": f"cutcell7-{edge}^3 ILU(0) FP64 + AMG", "rows": n, "nnz_A": len(A[1]),
+           "amg_setup_s": round(setup_s, 2), "levels": st["levels"], "level_rows": st["rows"],
+           "operator_complexity": round(sum(st["nnz_A"]) / st["nnz_A"][0], 3),
+           "ilu_levels": [st_f["levels_L"], st_f["levels_U"]], "tol": 1e-8, "restart": 30}
+    b = torch.from_numpy(synth.rhs(n, 1, seed=1)[:, 0].copy()).cuda()
+    F.reserve(1, 30)
+    for label, sL, sU in (("vcycle_sweeps_3_3_ms", 3, 3), ("vcycle_direct_ms", -1, -1)):
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            F.amg_vcycle(x, b, sL, sU)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            F.amg_vcycle(x, b, sL, sU)
+        e1.record()
+        torch.cuda.synchronize()
+        out[label] = round(e0.elapsed_time(e1) / 10, 3)
+    for label, pre, mL, mU in (("amg_sweeps_3_3", silu.PRECOND_AMG, 3, 3), ("amg_direct", silu.PRECOND_AMG_DIRECT, 0, 0),
+                               ("single_level_sweeps_3_3", silu.PRECOND_SWEEPS, 3, 3)):
+        for rep in range(2):  # the first solve also captures the iteration graphs
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            status, its, rr = silu.fgmres_solve(F, x, b, tol=1e-8, restart=30, maxit=5000, sweeps_L=mL,
+                                                sweeps_U=mU, precond=pre)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+        out[label] = {"seconds": round(sec, 4), "iterations": its, "relres": float(f"{rr:.3e}"),
+                      "converged": status == silu.OK}
+    out["speedup_amg_sweeps_vs_amg_direct"] = round(out["amg_direct"]["seconds"] / out["amg_sweeps_3_3"]["seconds"], 2)
+    return out
+
+
 def poisson32(silu, ctx, torch):
     """7-point Poisson 32^3 (32,768 rows), ILU(0), 4 interleaved right-hand
     sides U[-1,1] (seed 0): one smoother application (5+5 sweeps) against
@@ -749,6 +807,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--amg-edge", type=int, default=0,
+                    help="grid edge of the GMRES+AMG comparison (0 = skip)")
     ap.add_argument("--study", action="store_true",
                     help="add the sweep studies: scaling variants, factorisation kinds, ||T_s^p||_2")
     ap.add_argument("--serve-rate", type=float, default=200.0)

@@ -94,8 +94,17 @@ typedef enum { SILU_SCALE_NONE = 0, SILU_SCALE_ROW = 1, SILU_SCALE_NONE_RICH = 2
 typedef enum { SILU_FP64 = 0, SILU_FP32 = 1 } silu_prec;
 
 /* Preconditioner inside fgmres_solve.  SILU_PRECOND_AMG: one AMG V-cycle
- * from zero (silu_amg_setup must have been called on the factor object). */
-typedef enum { SILU_PRECOND_SWEEPS = 0, SILU_PRECOND_DIRECT = 1, SILU_PRECOND_NONE = 2, SILU_PRECOND_AMG = 3 } silu_precond;
+ * from zero whose finest level is smoothed by sweeps_L + sweeps_U Richardson
+ * sweeps; SILU_PRECOND_AMG_DIRECT: the same cycle smoothed by the exact
+ * level-scheduled triangular solves of the same factors (the comparison of
+ * Sec. 6).  Both need silu_amg_setup on the factor object. */
+typedef enum {
+  SILU_PRECOND_SWEEPS = 0,
+  SILU_PRECOND_DIRECT = 1,
+  SILU_PRECOND_NONE = 2,
+  SILU_PRECOND_AMG = 3,
+  SILU_PRECOND_AMG_DIRECT = 4
+} silu_precond;
 
 typedef struct silu_ctx_s* silu_ctx;
 typedef struct silu_mat_s* silu_mat;
@@ -360,7 +369,9 @@ silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params);
  * One V-cycle on A x = b (device, one right-hand side, x in/out, stream-
  * ordered): the finest level is smoothed before and after the coarse-grid
  * correction by ilu_smooth's update with sweeps_L / sweeps_U sweeps of F's
- * smoother.  A one-level hierarchy is the direct solve x = A^{-1} b.
+ * smoother, or, with sweeps_L and sweeps_U both negative, by
+ * direct_trisolve's update (exact triangular solves).  A one-level hierarchy
+ * is the direct solve x = A^{-1} b.
  */
 silu_status silu_amg_vcycle(silu_ilu F, double* x, const double* b, int sweeps_L, int sweeps_U);
 /* Levels and, for l < cap, rows, entries of A_l and of P_l (0 on the coarsest level). */

@@ -34,7 +34,7 @@ SCALE_NONE, SCALE_ROW, SCALE_NONE_RICH, SCALE_ROWCOL = 0, 1, 2, 3
 # silu_prec
 FP64, FP32 = 0, 1
 # silu_precond
-PRECOND_SWEEPS, PRECOND_DIRECT, PRECOND_NONE, PRECOND_AMG = 0, 1, 2, 3
+PRECOND_SWEEPS, PRECOND_DIRECT, PRECOND_NONE, PRECOND_AMG, PRECOND_AMG_DIRECT = 0, 1, 2, 3, 4
 # silu_kclass
 K_RESIDUAL, K_SWEEP_L, K_SWEEP_U, K_LEVEL, K_KRYLOV, K_ELEMENTWISE = range(6)
 K_NAMES = ["residual", "sweep_L", "sweep_U", "level", "krylov", "elementwise"]

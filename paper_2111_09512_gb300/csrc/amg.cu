@@ -111,7 +111,7 @@ cudaError_t upload_level(const silu::AmgLevel& H, AmgDevLevel& D, bool own_a, bo
 
 namespace silu {
 
-void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_zero) {
+void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_zero, bool capturing) {
   AmgState& G = *F->amg;
   AmgDevLevel& L0 = *G.lev[0];
   if (G.lev.size() == 1) {  // a single level: the direct solve
@@ -122,12 +122,19 @@ void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_ze
   }
   const DevCsr& A = F->A->d;
   AmgDevLevel& C = *G.lev[1];
-  smooth_chunk(F, x, b, 1, 1, 0, mL, mU, x_zero);                                   // pre-smoothing
+  // finest-level smoother: Richardson sweeps, or the exact triangular solves when mL < 0
+  auto smooth = [&](bool xz) {
+    if (mL < 0)
+      direct_chunk(F, x, b, 1, 1, 0, xz, capturing);
+    else
+      smooth_chunk(F, x, b, 1, 1, 0, mL, mU, xz);
+  };
+  smooth(x_zero);                                                                   // pre-smoothing
   op(F, A, SILU_K_RESIDUAL, b, x, L0.r.as<double>(), nullptr, nullptr, EPI_STORE);  // r = b - A x
   op(F, L0.R, SILU_K_RESIDUAL, nullptr, L0.r.as<double>(), C.b.as<double>(), nullptr, nullptr, EPI_SPMV);
   const double* v = level_cycle(F, 1);
   op(F, L0.Pneg, SILU_K_RESIDUAL, nullptr, v, nullptr, nullptr, x, EPI_ADDX);        // x += P v
-  smooth_chunk(F, x, b, 1, 1, 0, mL, mU, false);                                    // post-smoothing
+  smooth(false);                                                                    // post-smoothing
 }
 
 }  // namespace silu
@@ -175,7 +182,7 @@ silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params) {
 }
 
 silu_status silu_amg_vcycle(silu_ilu F, double* x, const double* b, int sweeps_L, int sweeps_U) {
-  if (!F || !x || !b || sweeps_L < 0 || sweeps_U < 0) return SILU_ERR_INVALID_ARG;
+  if (!F || !x || !b || (sweeps_L < 0) != (sweeps_U < 0)) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = F->ctx;
   if (!F->amg) return silu::set_err(ctx, SILU_ERR_INVALID_ARG, "no AMG hierarchy (silu_amg_setup)");
   silu_status ds = silu::device_ok(ctx);
@@ -183,7 +190,8 @@ silu_status silu_amg_vcycle(silu_ilu F, double* x, const double* b, int sweeps_L
   if (F->F.L.n == 0) return SILU_OK;
   try {
     CK(silu::ensure_vectors(F, 1));
-    silu::amg_cycle(F, x, b, sweeps_L, sweeps_U, false);
+    if (sweeps_L < 0) CK(silu::ensure_direct(F));
+    silu::amg_cycle(F, x, b, sweeps_L, sweeps_U, false, false);
   } catch (const CudaFail& f) {
     return silu::cuda_err(ctx, f.e, f.what);
   }

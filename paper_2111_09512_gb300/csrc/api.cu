@@ -555,7 +555,9 @@ void fgmres_inner(silu_ilu F, int j, int m, int mL, int mU, int precond, bool ca
   else if (precond == SILU_PRECOND_DIRECT)
     direct_chunk(F, zj, vj, 1, 1, 0, true, capturing);
   else if (precond == SILU_PRECOND_AMG)
-    amg_cycle(F, zj, vj, mL, mU, true);
+    amg_cycle(F, zj, vj, mL, mU, true, capturing);
+  else if (precond == SILU_PRECOND_AMG_DIRECT)
+    amg_cycle(F, zj, vj, -1, -1, true, capturing);
   else
     CK(cudaMemcpyAsync(zj, vj, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
   LAUNCH(F->ctx, SILU_K_RESIDUAL, sweep_launch(F, F->A->d, silu::MODE_D, 1, gA, 1, nullptr, zj, w, nullptr, nullptr, silu::EPI_SPMV));
@@ -1127,7 +1129,7 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
   if (iters_out) *iters_out = 0;
   if (relres_out) *relres_out = 0.0;
   if (!x || !b || !(tol >= 0.0) || restart < 1 || maxit < 0 || sweeps_L < 0 || sweeps_U < 0 || precond < 0 ||
-      precond > 3 || (precond == SILU_PRECOND_AMG && !F->amg))
+      precond > 4 || (precond >= SILU_PRECOND_AMG && !F->amg))
     return set_err(ctx, SILU_ERR_INVALID_ARG, "fgmres_solve: bad argument");
   silu_status ds = device_ok(ctx);
   if (ds != SILU_OK) return ds;
@@ -1140,7 +1142,7 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
   try {
     CK(ensure_vectors(F, 1));
     CK(ensure_krylov(F, m));
-    if (precond == SILU_PRECOND_DIRECT) {
+    if (precond == SILU_PRECOND_DIRECT || precond == SILU_PRECOND_AMG_DIRECT) {
       CK(ensure_direct(F));
       level_graph(F, 1, 1, 0);  // settles the level launch form before iterations are captured
     }

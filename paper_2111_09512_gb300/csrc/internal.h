@@ -317,10 +317,11 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
 void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, bool x_zero,
                   bool inline_levels = false);
 // One AMG V-cycle (Alg. mgcycle) on A x = b for one right-hand side, the
-// finest level smoothed by m_L + m_U sweeps of F's smoother (x_zero: x is
-// an output, the cycle starts from zero).  Requires F->amg and F's
-// one-column workspace.
-void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_zero);
+// finest level smoothed by m_L + m_U sweeps of F's smoother, or by its exact
+// triangular solves when mL < 0 (x_zero: x is an output, the cycle starts
+// from zero; capturing: a stream capture is recording).  Requires F->amg and
+// F's one-column workspace (and ensure_direct for mL < 0).
+void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_zero, bool capturing);
 // Ruiz equilibration limits for SILU_SCALE_ROWCOL.
 constexpr int kRuizMaxit = 20;
 constexpr double kRuizTol = 1e-2;

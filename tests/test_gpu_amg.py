@@ -108,3 +108,28 @@ def test_fgmres_with_amg_preconditioner(silu, ctx, prec):
     assert st1 == silu.OK
     print(f"{prec}: FGMRES(30) iterations, AMG V-cycle {its} vs single-level smoother {its1}")
     assert its * 3 < its1
+
+
+def test_vcycle_with_exact_triangular_solves(silu, ctx):
+    """With negative sweep counts the finest level is smoothed by the exact
+    level-scheduled solves; Richardson sweeps reach the same operator once
+    their count equals the factor's level count (nilpotence, Sec. 5.2), so the
+    oracle's cycle with that many sweeps is the reference."""
+    A = synth.cutcell7(17, 15, 13, seed=6)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+    F.amg_setup(theta=0.25, coarse_size=60, jacobi_sweeps=1)
+    st = F.stats()
+    H = oracle.AMG(A, theta=0.25, coarse_size=60)
+    S = oracle.row_scale(oracle.ilu0(A))
+    b = synth.rhs(n, 1, seed=8)[:, 0]
+    want = H.vcycle(S, np.zeros(n), b, st["levels_L"], st["levels_U"])
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    F.amg_vcycle(x, dev(b), -1, -1)
+    assert relerr(host(x), want) < 1e-12
+    xs = torch.zeros(n, dtype=torch.float64, device="cuda")
+    status, its, rel = silu.fgmres_solve(F, xs, dev(b), tol=1e-10, restart=30, maxit=500, sweeps_L=0, sweeps_U=0,
+                                         precond=silu.PRECOND_AMG_DIRECT)
+    assert status == silu.OK and rel <= 1e-10
+    r = oracle.residual(A, host(xs).reshape(n, 1), b.reshape(n, 1))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10
