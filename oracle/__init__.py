@@ -12,7 +12,8 @@ row/column (Ruiz) scaling of Eq. rowcolScale, and the power-iteration
 estimates of ||T_s^p||_2 behind the paper's numerical nilpotence (Fig. Up),
 and algebraic multigrid (Sec. 3: Ruge-Stueben coarsening, direct
 interpolation, Galerkin coarse operators, the V-cycle of Alg. mgcycle with
-the ILU smoother on the finest level).
+the ILU smoother on the finest level), and the ILUT Schur complement
+smoother of Sec. 3.1 (Eq. schur).
 
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may
 import this package.  It shares no code with the CUDA library.  Each wrapper
@@ -98,6 +99,8 @@ def _load():
         "orc_amg_level_sizes": (None, [vp, i32] + [ctypes.POINTER(i64)] * 4),
         "orc_amg_level_copy": (None, [vp, i32] + [vp] * 7),
         "orc_amg_vcycle": (i32, [vp] + [vp] * 7 + [i32, i32, i32, vp, vp]),
+        "orc_schur_interface": (i64, [i64, vp, vp, i32, vp]),
+        "orc_schur_apply": (i32, [i64, vp, vp, vp, i32, dbl, i32, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -574,3 +577,25 @@ class AMG:
                 self._h = None
         except Exception:
             pass
+
+
+def schur_interface(A, parts: int):
+    """Interface rows (1) of a parts-way contiguous block-row partition; returns (count, marks)."""
+    ap, ac, _ = _csr(A)
+    n = len(ap) - 1
+    marks = np.empty(max(n, 1), np.int32)
+    k = _load().orc_schur_interface(n, _p(ap), _p(ac), int(parts), _p(marks))
+    return int(k), marks[:n]
+
+
+def schur_apply(A, r, parts: int, tau: float, fill: int, mL: int, mU: int):
+    """z = M^{-1} r of the ILUT Schur complement smoother (Sec. 3.1, Eq. schur), one right-hand side."""
+    ap, ac, av = _csr(A)
+    n = len(ap) - 1
+    r = np.ascontiguousarray(r, np.float64).reshape(n)
+    z = np.empty(max(n, 1), np.float64)
+    st = _load().orc_schur_apply(n, _p(ap), _p(ac), _p(av), int(parts), float(tau), int(fill), int(mL), int(mU),
+                                 _p(r), _p(z))
+    if st:
+        raise OracleError(st, "schur_apply")
+    return z[:n]

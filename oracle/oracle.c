@@ -1746,3 +1746,202 @@ int orc_amg_vcycle(const orc_amg* h, const int64_t* lp, const int32_t* lc, const
   amg_smoother sm = {lp, sp, lc, sc, lv, sv, dinv, mL, mU, nu};
   return multilevel(h, 0, &sm, b, x);
 }
+
+/* ------------------------------------------------------------------------ */
+/* ILUT Schur complement smoother (Sec. 3.1, Eq. schur)                       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Interface of a `parts`-way partition into contiguous row blocks (block k
+ * holds rows [k n / parts, (k+1) n / parts)), the stand-in for the paper's
+ * MPI ranks: row i is an interface row when it has an entry in a column of
+ * another block.  iface[i] = 1 for interface rows.  Returns their number.
+ */
+int64_t orc_schur_interface(int64_t n, const int64_t* ap, const int32_t* ac, int parts, int32_t* iface) {
+  int64_t ni = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t bi = (i * parts) / n;
+    int32_t f = 0;
+    for (int64_t p = ap[i]; p < ap[i + 1]; ++p) {
+      /* block of column j: the k with k n / parts <= j < (k+1) n / parts */
+      int64_t bj = 0;
+      while ((bj + 1) * n / parts <= ac[p]) ++bj;
+      if (bj != bi) f = 1;
+    }
+    iface[i] = f;
+    ni += f;
+  }
+  return ni;
+}
+
+/* submatrix of A with rows `rows` (count nr) and columns mapped by cmap (-1 = dropped) */
+static void submatrix(const int64_t* ap, const int32_t* ac, const double* av, const int64_t* rows, int64_t nr,
+                      const int64_t* cmap, int64_t** sp_o, int32_t** sc_o, double** sv_o) {
+  int64_t cnt = 0;
+  for (int64_t t = 0; t < nr; ++t)
+    for (int64_t p = ap[rows[t]]; p < ap[rows[t] + 1]; ++p)
+      if (cmap[ac[p]] >= 0) ++cnt;
+  int64_t* sp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nr + 1));
+  int32_t* sc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(cnt + 1));
+  double* sv = (double*)malloc(sizeof(double) * (size_t)(cnt + 1));
+  int64_t q = 0;
+  sp[0] = 0;
+  for (int64_t t = 0; t < nr; ++t) {
+    for (int64_t p = ap[rows[t]]; p < ap[rows[t] + 1]; ++p)
+      if (cmap[ac[p]] >= 0) {
+        sc[q] = (int32_t)cmap[ac[p]];
+        sv[q] = av[p];
+        ++q;
+      }
+    sp[t + 1] = q;
+  }
+  *sp_o = sp;
+  *sc_o = sc;
+  *sv_o = sv;
+}
+
+typedef struct {
+  int64_t nI, nG;
+  int64_t *rowsI, *rowsG;     /* original row numbers, ascending */
+  int64_t *bp, *ep, *fp, *cp; /* B = A_II, E = A_IG, F = A_GI, C = A_GG */
+  int32_t *bc, *ec, *fc, *cc;
+  double *bv, *ev, *fv, *cv;
+  int64_t *lp, *sp; /* row-scaled ILUT factors of B */
+  int32_t *lc, *sc;
+  double *lv, *sv, *dinv;
+} schur_parts;
+
+static void schur_free(schur_parts* S) {
+  void* ptrs[] = {S->rowsI, S->rowsG, S->bp, S->ep, S->fp, S->cp, S->bc, S->ec, S->fc, S->cc, S->bv, S->ev,
+                  S->fv, S->cv, S->lp, S->sp, S->lc, S->sc, S->lv, S->sv, S->dinv};
+  for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
+}
+
+static int schur_build(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, int parts, double tau,
+                       int fill, schur_parts* S) {
+  memset(S, 0, sizeof(*S));
+  int32_t* iface = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  S->nG = orc_schur_interface(n, ap, ac, parts, iface);
+  S->nI = n - S->nG;
+  S->rowsI = (int64_t*)malloc(sizeof(int64_t) * (size_t)(S->nI + 1));
+  S->rowsG = (int64_t*)malloc(sizeof(int64_t) * (size_t)(S->nG + 1));
+  int64_t* mapI = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  int64_t* mapG = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  int64_t a = 0, g = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    mapI[i] = iface[i] ? -1 : a;
+    mapG[i] = iface[i] ? g : -1;
+    if (iface[i])
+      S->rowsG[g++] = i;
+    else
+      S->rowsI[a++] = i;
+  }
+  submatrix(ap, ac, av, S->rowsI, S->nI, mapI, &S->bp, &S->bc, &S->bv);
+  submatrix(ap, ac, av, S->rowsI, S->nI, mapG, &S->ep, &S->ec, &S->ev);
+  submatrix(ap, ac, av, S->rowsG, S->nG, mapI, &S->fp, &S->fc, &S->fv);
+  submatrix(ap, ac, av, S->rowsG, S->nG, mapG, &S->cp, &S->cc, &S->cv);
+  free(iface);
+  free(mapI);
+  free(mapG);
+  int st = ORC_OK;
+  orc_lu* lu = orc_ilut(S->nI, S->bp, S->bc, S->bv, tau, fill, &st);
+  if (!lu) return st ? st : ORC_NOMEM;
+  int64_t nl, nu;
+  orc_lu_nnz(lu, &nl, &nu);
+  S->lp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(S->nI + 1));
+  S->lc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nl + 1));
+  S->lv = (double*)malloc(sizeof(double) * (size_t)(nl + 1));
+  int64_t* up = (int64_t*)malloc(sizeof(int64_t) * (size_t)(S->nI + 1));
+  int32_t* uc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nu + 1));
+  double* uv = (double*)malloc(sizeof(double) * (size_t)(nu + 1));
+  orc_lu_copy(lu, S->lp, S->lc, S->lv, up, uc, uv);
+  orc_lu_free(lu);
+  S->sp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(S->nI + 1));
+  S->sc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nu + 1));
+  S->sv = (double*)malloc(sizeof(double) * (size_t)(nu + 1));
+  S->dinv = (double*)malloc(sizeof(double) * (size_t)(S->nI + 1));
+  st = orc_row_scale(S->nI, up, uc, uv, S->dinv, S->sp, S->sc, S->sv);
+  free(up);
+  free(uc);
+  free(uv);
+  return st;
+}
+
+/* u = B^{-1} f approximated by the ILU smoother from zero (m_L + m_U sweeps) */
+static int schur_binv(const schur_parts* S, const double* f, int mL, int mU, double* u) {
+  const int64_t m = S->nI;
+  double* x = (double*)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
+  int st = orc_smooth(m, 1, S->bp, S->bc, S->bv, S->lp, S->lc, S->lv, S->sp, S->sc, S->sv, S->dinv, x, f, mL, mU);
+  memcpy(u, x, sizeof(double) * (size_t)m);
+  free(x);
+  return st;
+}
+
+/*
+ * z = M^{-1} r for the Schur complement smoother, in the paper's order, with
+ * A permuted to [B E; F C] (interior rows first, interface rows last, each
+ * in ascending original order) and B ~ L D Utilde from ILUT(tau, fill)
+ * (row-scaled, the triangular solves replaced by m_L + m_U sweeps):
+ *   f = r_I, g = r_G;  s = g - F B^{-1} f  (right-hand side of Eq. schur);
+ *   one GMRES iteration on S y = s, S = C - F B^{-1} E, from y = 0:
+ *     beta = ||s||, v = s / beta, w = S v, h11 = v.w, h21 = ||w - h11 v||,
+ *     Givens rho = hypot(h11, h21), y = (beta h11 / rho^2) v
+ *   (no residual of the full system is formed);
+ *   x_I = B^{-1} (f - E y);  z = [x_I; y] in the original order.
+ */
+int orc_schur_apply(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, int parts, double tau,
+                    int fill, int mL, int mU, const double* r, double* z) {
+  schur_parts S;
+  int st = schur_build(n, ap, ac, av, parts, tau, fill, &S);
+  const int64_t nI = S.nI, nG = S.nG;
+  const size_t mi = (size_t)(nI > 0 ? nI : 1), mg = (size_t)(nG > 0 ? nG : 1);
+  double* f = (double*)malloc(sizeof(double) * mi);
+  double* u = (double*)malloc(sizeof(double) * mi);
+  double* t = (double*)malloc(sizeof(double) * mi);
+  double* s = (double*)malloc(sizeof(double) * mg);
+  double* v = (double*)malloc(sizeof(double) * mg);
+  double* w = (double*)malloc(sizeof(double) * mg);
+  double* y = (double*)calloc(mg, sizeof(double));
+  if (st) goto done;
+  for (int64_t k = 0; k < nI; ++k) f[k] = r[S.rowsI[k]];
+  /* s = g - F B^{-1} f */
+  if ((st = schur_binv(&S, f, mL, mU, u))) goto done;
+  orc_spmv(nG, 1, S.fp, S.fc, S.fv, u, w);
+  for (int64_t k = 0; k < nG; ++k) s[k] = r[S.rowsG[k]] - w[k];
+  /* one GMRES iteration on S y = s */
+  {
+    const double beta = sqrt(dot(nG, s, s));
+    if (beta > 0.0) {
+      for (int64_t k = 0; k < nG; ++k) v[k] = s[k] / beta;
+      orc_spmv(nI, 1, S.ep, S.ec, S.ev, v, t);                 /* E v */
+      if ((st = schur_binv(&S, t, mL, mU, u))) goto done;      /* B^{-1} E v */
+      orc_spmv(nG, 1, S.fp, S.fc, S.fv, u, w);                 /* F B^{-1} E v */
+      double* cvv = (double*)malloc(sizeof(double) * mg);
+      orc_spmv(nG, 1, S.cp, S.cc, S.cv, v, cvv);               /* C v */
+      for (int64_t k = 0; k < nG; ++k) w[k] = cvv[k] - w[k];   /* w = S v */
+      free(cvv);
+      const double h11 = dot(nG, v, w);
+      for (int64_t k = 0; k < nG; ++k) w[k] = w[k] - h11 * v[k];
+      const double h21 = sqrt(dot(nG, w, w));
+      const double rho = hypot(h11, h21);
+      const double coef = rho > 0.0 ? (beta * h11) / (rho * rho) : 0.0;
+      for (int64_t k = 0; k < nG; ++k) y[k] = coef * v[k];
+    }
+  }
+  /* x_I = B^{-1} (f - E y) */
+  orc_spmv(nI, 1, S.ep, S.ec, S.ev, y, t);
+  for (int64_t k = 0; k < nI; ++k) t[k] = f[k] - t[k];
+  if ((st = schur_binv(&S, t, mL, mU, u))) goto done;
+  for (int64_t k = 0; k < nI; ++k) z[S.rowsI[k]] = u[k];
+  for (int64_t k = 0; k < nG; ++k) z[S.rowsG[k]] = y[k];
+done:
+  schur_free(&S);
+  free(f);
+  free(u);
+  free(t);
+  free(s);
+  free(v);
+  free(w);
+  free(y);
+  return st;
+}
