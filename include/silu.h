@@ -103,7 +103,8 @@ typedef enum {
   SILU_PRECOND_DIRECT = 1,
   SILU_PRECOND_NONE = 2,
   SILU_PRECOND_AMG = 3,
-  SILU_PRECOND_AMG_DIRECT = 4
+  SILU_PRECOND_AMG_DIRECT = 4,
+  SILU_PRECOND_SCHUR = 5  /* one application of the Schur complement smoother (silu_schur_setup) */
 } silu_precond;
 
 typedef struct silu_ctx_s* silu_ctx;
@@ -381,6 +382,28 @@ silu_status silu_amg_stats(silu_ilu F, int cap, int* levels, int64_t* rows, int6
  * below the coarsest level.  Any pointer may be NULL. */
 silu_status silu_amg_export_level(silu_ilu F, int level, int64_t* Ap, int32_t* Ac, double* Av, int64_t* Pp,
                                   int32_t* Pc, double* Pv, int32_t* cf);
+
+/*
+ * ILUT Schur complement smoother (Sec. 3.1, Eq. schur), attached to F (freed
+ * with it; a second call replaces it).  The rows are split into `parts`
+ * contiguous blocks, the single-device stand-in for the paper's MPI ranks
+ * (block k holds rows [k n / parts, (k+1) n / parts)); a row with an entry in
+ * another block is an interface row.  With A permuted to [B E; F C] (interior
+ * rows first, each group in ascending order), B (block diagonal) is factored
+ * by ILUT(tau, fill) with row scaling in F's precision.  One application
+ * z = M^{-1} r:  s = r_G - F B^{-1} r_I;  one GMRES iteration on S y = s,
+ * S = C - F B^{-1} E, from y = 0 (the minimal-residual step, no residual of
+ * the full system formed);  z_I = B^{-1} (r_I - E y), z_G = y.  Every B^{-1}
+ * is sweeps_L + sweeps_U Richardson sweeps on B's row-scaled factors.
+ * Blocks; works on host-only contexts (setup and statistics only).
+ */
+silu_status silu_schur_setup(silu_ilu F, int parts, double tau, int fill);
+/* x <- x + M^{-1} (b - A x) with the Schur complement smoother (device, one
+ * right-hand side, stream-ordered). */
+silu_status silu_schur_smooth(silu_ilu F, double* x, const double* b, int sweeps_L, int sweeps_U);
+/* Interior and interface counts, and the interface mark of every row (n
+ * int32, may be NULL). */
+silu_status silu_schur_stats(silu_ilu F, int64_t* n_interior, int64_t* n_interface, int32_t* iface);
 
 /*
  * Batches of independent systems (many pressure solves of uneven size).

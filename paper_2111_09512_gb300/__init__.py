@@ -34,7 +34,7 @@ SCALE_NONE, SCALE_ROW, SCALE_NONE_RICH, SCALE_ROWCOL = 0, 1, 2, 3
 # silu_prec
 FP64, FP32 = 0, 1
 # silu_precond
-PRECOND_SWEEPS, PRECOND_DIRECT, PRECOND_NONE, PRECOND_AMG, PRECOND_AMG_DIRECT = 0, 1, 2, 3, 4
+PRECOND_SWEEPS, PRECOND_DIRECT, PRECOND_NONE, PRECOND_AMG, PRECOND_AMG_DIRECT, PRECOND_SCHUR = 0, 1, 2, 3, 4, 5
 # silu_kclass
 K_RESIDUAL, K_SWEEP_L, K_SWEEP_U, K_LEVEL, K_KRYLOV, K_ELEMENTWISE = range(6)
 K_NAMES = ["residual", "sweep_L", "sweep_U", "level", "krylov", "elementwise"]
@@ -105,6 +105,9 @@ def load():
         "silu_amg_vcycle": (i32, [vp, vp, vp, i32, i32]),
         "silu_amg_stats": (i32, [vp, i32, ctypes.POINTER(i32), vp, vp, vp]),
         "silu_amg_export_level": (i32, [vp, i32] + [vp] * 7),
+        "silu_schur_setup": (i32, [vp, i32, dbl, i32]),
+        "silu_schur_smooth": (i32, [vp, vp, vp, i32, i32]),
+        "silu_schur_stats": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), vp]),
         "silu_ilu_destroy": (None, [vp]),
         "silu_ilu_set_lanes": (i32, [vp, i32, i32, i32]),
         "silu_ctx_profile": (i32, [vp, i32]),
@@ -145,7 +148,8 @@ def exported_symbols():
             "silu_mat_destroy", "silu_mat_residual", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
             "silu_ilu_export_colscale", "silu_ilu_power_norms", "silu_amg_setup", "silu_amg_vcycle",
-            "silu_amg_stats", "silu_amg_export_level",
+            "silu_amg_stats", "silu_amg_export_level", "silu_schur_setup", "silu_schur_smooth",
+            "silu_schur_stats",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
             "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_layout", "silu_ilu_tune_table", "silu_ctx_set_overlap",
             "silu_smooth_noalloc",
@@ -387,6 +391,23 @@ class ILU:
                                                              None if last else _ptr(cf)), "silu_amg_export_level")
         return {"A": (Ap, Ac[:nza], Av[:nza]), "P": None if last else (Pp, Pc[:nzp], Pv[:nzp]),
                 "cf": None if last else cf[:n]}
+
+    def schur_setup(self, parts: int, tau: float, fill: int):
+        """Attach the ILUT Schur complement smoother (Sec. 3.1) over `parts` contiguous row blocks."""
+        _check(self.ctx.handle, load().silu_schur_setup(self.handle, int(parts), float(tau), int(fill)),
+               "silu_schur_setup")
+
+    def schur_smooth(self, x, b, sweeps_L: int, sweeps_U: int):
+        """x <- x + M^{-1}(b - A x) with the Schur complement smoother (device tensors of length n)."""
+        _check(self.ctx.handle, load().silu_schur_smooth(self.handle, _ptr(x), _ptr(b), int(sweeps_L),
+                                                         int(sweeps_U)), "silu_schur_smooth")
+
+    def schur_stats(self):
+        ni, ng = ctypes.c_int64(), ctypes.c_int64()
+        marks = np.empty(max(self.n, 1), np.int32)
+        _check(self.ctx.handle, load().silu_schur_stats(self.handle, ctypes.byref(ni), ctypes.byref(ng),
+                                                        _ptr(marks)), "silu_schur_stats")
+        return {"interior": ni.value, "interface": ng.value, "marks": marks[:self.n]}
 
     def reserve(self, nrhs: int = 1, restart: int = 0):
         _check(self.ctx.handle, load().silu_ilu_reserve(self.handle, nrhs, restart), "silu_ilu_reserve")

@@ -558,6 +558,8 @@ void fgmres_inner(silu_ilu F, int j, int m, int mL, int mU, int precond, bool ca
     amg_cycle(F, zj, vj, mL, mU, true, capturing);
   else if (precond == SILU_PRECOND_AMG_DIRECT)
     amg_cycle(F, zj, vj, -1, -1, true, capturing);
+  else if (precond == SILU_PRECOND_SCHUR)
+    schur_apply(F, vj, zj, mL, mU);
   else
     CK(cudaMemcpyAsync(zj, vj, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
   LAUNCH(F->ctx, SILU_K_RESIDUAL, sweep_launch(F, F->A->d, silu::MODE_D, 1, gA, 1, nullptr, zj, w, nullptr, nullptr, silu::EPI_SPMV));
@@ -1129,7 +1131,8 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
   if (iters_out) *iters_out = 0;
   if (relres_out) *relres_out = 0.0;
   if (!x || !b || !(tol >= 0.0) || restart < 1 || maxit < 0 || sweeps_L < 0 || sweeps_U < 0 || precond < 0 ||
-      precond > 4 || (precond >= SILU_PRECOND_AMG && !F->amg))
+      precond > 5 || ((precond == SILU_PRECOND_AMG || precond == SILU_PRECOND_AMG_DIRECT) && !F->amg) ||
+      (precond == SILU_PRECOND_SCHUR && !F->schur))
     return set_err(ctx, SILU_ERR_INVALID_ARG, "fgmres_solve: bad argument");
   silu_status ds = device_ok(ctx);
   if (ds != SILU_OK) return ds;

@@ -178,6 +178,10 @@ cudaError_t launch_givens(int j, int m, double* H, double* cs, double* sn, doubl
 // solve the jend x jend triangle, then x += sum_k y_k Z_k
 cudaError_t launch_update_x(int n, int jend, int m, const double* H, const double* g, double* y, const double* Z,
                             double* x, cudaStream_t s);
+// y = (sum(part_num) / sum(part_den)) s (0 when the denominator sums to 0); both
+// partial arrays written by launch_dot_part over n rows
+cudaError_t launch_mr_step(int n, const double* part_num, const double* part_den, const double* sv, double* y,
+                           cudaStream_t s);
 // *out = sqrt(sum(part_in)) for partials written by a launch over n rows
 cudaError_t launch_norm_final(int n, const double* part_in, double* out, cudaStream_t s);
 

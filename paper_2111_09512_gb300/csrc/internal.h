@@ -142,6 +142,23 @@ struct AmgState {
   int64_t coarse_size = 400;
 };
 
+// The ILUT Schur complement smoother attached to a factor object (Sec. 3.1,
+// Eq. schur): A permuted to [B E; F C] (interior rows first, interface rows
+// last), B factored by ILUT and applied by the sweeps, one GMRES iteration
+// on the interface system.
+struct SchurState {
+  int parts = 0;
+  int64_t nI = 0, nG = 0;
+  std::vector<int32_t> iface;  // 1 = interface row
+  silu_mat Bmat = nullptr;     // B (owned)
+  silu_ilu FB = nullptr;       // ILUT factors of B (owned)
+  DBuf rowsI, rowsG;           // original row of each interior / interface unknown
+  DBuf E_rp, E_ci, E_va, E_t, F_rp, F_ci, F_va, F_t, C_rp, C_ci, C_va, C_t;
+  DevCsr E, F, C;
+  DBuf f, u, t, xi, g, s, w, y, r, part0, part1;
+  ~SchurState();
+};
+
 struct silu_ilu_s {
   silu_ctx ctx = nullptr;
   silu_mat A = nullptr;
@@ -175,6 +192,7 @@ struct silu_ilu_s {
   int autoL = 4, autoU = 4, autoA = 8;
   Workspace ws;
   std::unique_ptr<AmgState> amg;  // silu_amg_setup
+  std::unique_ptr<SchurState> schur;  // silu_schur_setup
 };
 
 // The upper sweep factor is a unit-diagonal scaled copy (F->Us) rather than raw U.
@@ -322,6 +340,9 @@ void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
 // from zero; capturing: a stream capture is recording).  Requires F->amg and
 // F's one-column workspace (and ensure_direct for mL < 0).
 void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_zero, bool capturing);
+// z = M^{-1} r of F's Schur complement smoother (one right-hand side,
+// device vectors of n entries; z is written).  Requires F->schur.
+void schur_apply(silu_ilu F, const double* r, double* z, int mL, int mU);
 // Ruiz equilibration limits for SILU_SCALE_ROWCOL.
 constexpr int kRuizMaxit = 20;
 constexpr double kRuizTol = 1e-2;

@@ -80,6 +80,18 @@ __global__ void __launch_bounds__(KB) k_normalize(int n, const double* __restric
     vout[i] = w[i] / h;
 }
 
+// Minimal-residual step: alpha = sum(part_num) / sum(part_den) (0 when the
+// denominator is 0), y = alpha s.
+__global__ void __launch_bounds__(KB) k_mr_step(int n, const double* __restrict__ part_num,
+                                                const double* __restrict__ part_den, int nparts,
+                                                const double* __restrict__ s, double* __restrict__ y) {
+  const double num = sum_parts(part_num, nparts);
+  const double den = sum_parts(part_den, nparts);
+  const double alpha = den != 0.0 ? num / den : 0.0;
+  for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB)
+    y[i] = alpha * s[i];
+}
+
 __global__ void k_norm_final(const double* __restrict__ part_in, int nparts, double* __restrict__ out) {
   const double h = sqrt(sum_parts(part_in, nparts));
   if (threadIdx.x == 0) *out = h;
@@ -156,6 +168,13 @@ cudaError_t launch_normalize(int n, const double* part_in, double* hout, const d
                              cudaStream_t s) {
   const int np = krylov_parts(n);
   k_normalize<<<np, KB, 0, s>>>(n, part_in, np, hout, w, vout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mr_step(int n, const double* part_num, const double* part_den, const double* sv, double* y,
+                           cudaStream_t s) {
+  const int np = krylov_parts(n);
+  k_mr_step<<<np, KB, 0, s>>>(n, part_num, part_den, np, sv, y);
   return cudaGetLastError();
 }
 

@@ -296,3 +296,18 @@ def test_amg_bad_parameters(ctx):
         assert e.value.status == silu.ERR_INVALID_ARG
     with pytest.raises(silu.SiluError):
         F.amg_stats()
+
+
+@pytest.mark.parametrize("parts", [1, 3, 8])
+def test_schur_interface_matches_oracle(ctx, parts):
+    """Schur complement smoother setup (Sec. 3.1): the interface rows of the
+    contiguous block partition are the oracle's (integer, exact)."""
+    A = synth.cutcell7(9, 8, 7, seed=2)
+    F = silu.ILU(silu.Matrix(ctx, *A), "ilu0")
+    F.schur_setup(parts, 1e-3, 10)
+    st = F.schur_stats()
+    k, marks = oracle.schur_interface(A, parts)
+    assert st["interface"] == k and st["interior"] == len(marks) - k
+    assert np.array_equal(st["marks"], marks)
+    with pytest.raises(silu.SiluError):
+        F.schur_setup(0, 1e-3, 10)
