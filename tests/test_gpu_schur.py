@@ -63,7 +63,12 @@ def test_schur_smoother_matches_oracle(silu, ctx, case):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_fgmres_with_schur_preconditioner(silu, ctx, prec):
-    A = synth.cutcell7(36, 32, 28, seed=5)
+    """FGMRES(30) to 1e-10 preconditioned by one Schur complement smoother
+    application, on the 27-point matrix (the paper applies this smoother to
+    the Nalu-Wind systems the 27-point generator stands in for).  On the
+    cut-cell matrices the single GMRES step on the interface system is too
+    weak and FGMRES stalls, in the oracle as on the device."""
+    A = synth.hex27(28, 26, 24, seed=5)
     n = len(A[0]) - 1
     F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0", prec=silu.FP32 if prec == "fp32" else silu.FP64)
     F.schur_setup(4, 1e-3, 10)
