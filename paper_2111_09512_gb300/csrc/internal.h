@@ -16,6 +16,7 @@
 #include "amg_setup.h"
 #include "device.cuh"
 #include "host_factor.h"
+#include "krylov.cuh"
 #include "silu.h"
 
 namespace silu {

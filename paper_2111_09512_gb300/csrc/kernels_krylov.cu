@@ -8,6 +8,7 @@
 #include <cmath>
 
 #include "device.cuh"
+#include "krylov.cuh"
 
 namespace silu {
 namespace {
