@@ -513,6 +513,21 @@ def batch_workload(silu, ctx, torch, count: int):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     nbytes = apply_bytes(n, nnzA, st["nnz_L"], st["nnz_U"], 1, 4, 3, 3)
+    # per-kernel-class split of the same loop (one event pair per run of sweeps)
+    ctx.profile(True)
+    for _ in range(reps):
+        silu.silu_batch_smooth(B, x, b, 3, 3)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    cls_bytes = {"residual": resid_bytes(n, nnzA, 1), "sweep_L": sweep_bytes(n, st["nnz_L"], 1, 4),
+                 "sweep_U": sweep_bytes(n, st["nnz_U"], 1, 4)}
+    split = {}
+    for k, (cnt, kms) in prof.items():
+        if cnt:
+            split[k] = {"launches": cnt, "ms": round(kms, 4)}
+            if k in cls_bytes and kms > 0:
+                split[k]["gbs"] = round(cnt * cls_bytes[k] / (kms * 1e-3) / 1e9, 1)
     x.zero_()
     silu.silu_batch_fgmres(B, x, b, tol=1e-8, restart=20, maxit=1, sweeps_L=3, sweeps_U=3)
     x.zero_()
@@ -523,7 +538,7 @@ def batch_workload(silu, ctx, torch, count: int):
     solve_s = time.perf_counter() - t0
     out = {"workload": f"{count} cut-cell 7-point systems, edges U[8,64], FP32 ILU(0)", "rows": n,
            "nnz_A": nnzA, "setup_s": round(setup_s, 2), "autotune_choice": choice,
-           "smooth_3_3": {"ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1)},
+           "smooth_3_3": {"ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "kernels": split},
            "fgmres20_1e-8": {"seconds": round(solve_s, 4), "all_converged": stt == silu.OK,
                              "iterations_max": int(np.max(its)), "iterations_mean": round(float(np.mean(its)), 1),
                              "relres_max": float(np.max(rel))}}
