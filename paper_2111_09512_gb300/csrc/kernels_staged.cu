@@ -299,6 +299,70 @@ __device__ __forceinline__ MT row_accumulate(const MT* sv, const int* sc, int le
   return acc;
 }
 
+// One lane per row and RL rows per lane (rows r0 + p * 32 + lane of the
+// tile, p < RL): the short-row case.  Taking the rows one after another costs
+// RL dependent gather rounds per tile; here a round gathers up to CH / RL
+// entries of every row at once (about the registers of CH entries of one row), then
+// runs the FMAs of all RL independent accumulators, then stores the RL
+// results.  Each row still accumulates c - sum t_ij in_j in column order, so
+// results are bitwise those of the one-row-at-a-time loop.  The round count
+// is the warp's longest row over all RL passes (warp-uniform).
+template <class MT, class VI, class VO, int CH, int RL, bool PERM>
+__device__ __forceinline__ void rows_accumulate(const MT* sv, const int* sc, const int* sr, const int* sp, int r0,
+                                                int r1, int q0, int a0, int c0, int p0, int lane,
+                                                const VI* __restrict__ c, const VI* __restrict__ in,
+                                                VO* __restrict__ out, const double* __restrict__ dinv,
+                                                double* __restrict__ x, int epi, uint64_t keep) {
+  // entries of each row per round: CH / RL, at most 3 in FP64 (the 96
+  // registers a thread has here hold 4 x 3 values and gathers without spills)
+  constexpr int KP0 = CH / RL > 0 ? CH / RL : 1;
+  constexpr int KP = (sizeof(MT) == 8 && KP0 > 3) ? 3 : KP0;
+  int b[RL], len[RL], o[RL];
+  MT acc[RL];
+  int wmax = 0;
+#pragma unroll
+  for (int p = 0; p < RL; ++p) {
+    const int r = r0 + p * 32 + lane;
+    const bool act = r < r1;
+    b[p] = act ? sr[r - q0] : p0;
+    len[p] = act ? sr[r + 1 - q0] - b[p] : 0;
+    o[p] = act ? (PERM ? sp[r - q0] : r) : -1;
+    acc[p] = (act && c) ? (MT)ld_keep(c + o[p], keep) : MT(0);
+    wmax = len[p] > wmax ? len[p] : wmax;
+  }
+  wmax = __reduce_max_sync(0xffffffffu, wmax);
+  const bool neg = epi != EPI_SPMV;
+  for (int k0 = 0; k0 < wmax; k0 += KP) {
+    MT v[RL][KP], xv[RL][KP];
+#pragma unroll
+    for (int p = 0; p < RL; ++p)
+#pragma unroll
+      for (int k = 0; k < KP; ++k) {
+        if (k0 + k < len[p]) {
+          v[p][k] = sv[b[p] - a0 + k0 + k];
+          xv[p][k] = (MT)ld_keep(in + sc[b[p] - c0 + k0 + k], keep);
+        } else {
+          v[p][k] = MT(0);
+          xv[p][k] = MT(0);
+        }
+      }
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      if (k0 + k >= wmax) break;  // warp-uniform; padded slots multiply zeros
+#pragma unroll
+      for (int p = 0; p < RL; ++p) acc[p] = fma(neg ? -v[p][k] : v[p][k], xv[p][k], acc[p]);
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < RL; ++p) {
+    if (o[p] < 0) continue;
+    if (epi == EPI_SPMV)
+      st_keep(out + o[p], (VO)acc[p], keep);
+    else
+      epilogue<MT, VI, VO>(epi, o[p], acc[p], in, out, dinv, x, keep);
+  }
+}
+
 template <class MT, class VI, class VO, int G, int CH, int RL, bool PERM>
 __global__ void __launch_bounds__(kStagedThreads, 1)
     k_sweep_staged(int ntiles, const int4* __restrict__ tiles, const int* __restrict__ rp, const int* __restrict__ ci,
@@ -361,6 +425,11 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     const int a0 = p0 & ~(L::kValAlign - 1);
     const int c0 = p0 & ~3;
     const int sub = lane % G;
+    if constexpr (RL > 1 && G == 1) {
+      // several short rows per lane: gather for all of them before any FMA
+      rows_accumulate<MT, VI, VO, CH, RL, PERM>(sv, sc, sr, sp, r0, r1, q0, a0, c0, p0, lane, c, in, out, dinv, x,
+                                                epi, keep);
+    } else {
 #pragma unroll 1
     for (int pass = 0; pass < RL; ++pass) {
       const int r = r0 + pass * (32 / G) + lane / G;  // stored row
@@ -380,6 +449,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
         else
           epilogue<MT, VI, VO>(epi, o, acc, in, out, dinv, x, keep);
       }
+    }
     }
     __syncwarp();
     if (lane == 0 && tn < ntiles)
