@@ -10,7 +10,8 @@
 
 #include <algorithm>
 #include <cmath>
-#include <set>
+#include <memory>
+#include <thread>
 #include <utility>
 
 namespace silu {
@@ -32,9 +33,47 @@ void strength(const Csr& A, double theta, std::vector<char>& s) {
   }
 }
 
-// Ruge-Stueben first pass with an ordered set keyed by (-measure, index):
-// the front is always the undecided point of largest measure, smallest
-// index among equals.
+// A set of indices in [0, n) with the smallest member found in a few word
+// scans: one bit per index, and above it summary levels with one bit per
+// non-zero word of the level below.
+class IndexSet {
+ public:
+  explicit IndexSet(int64_t n) {
+    int64_t len = n;
+    do {
+      len = (len + 63) / 64;
+      lv_.emplace_back((size_t)len, 0ull);
+    } while (len > 1);
+  }
+  void insert(int64_t i) {
+    for (auto& w : lv_) {
+      const bool was = w[(size_t)(i >> 6)] != 0;
+      w[(size_t)(i >> 6)] |= 1ull << (i & 63);
+      if (was) return;
+      i >>= 6;
+    }
+  }
+  void erase(int64_t i) {
+    for (auto& w : lv_) {
+      w[(size_t)(i >> 6)] &= ~(1ull << (i & 63));
+      if (w[(size_t)(i >> 6)] != 0) return;
+      i >>= 6;
+    }
+  }
+  bool empty() const { return lv_.back()[0] == 0; }
+  int64_t first() const {  // smallest member (the set must not be empty)
+    int64_t i = 0;
+    for (size_t l = lv_.size(); l-- > 0;) i = (i << 6) | __builtin_ctzll(lv_[l][(size_t)i]);
+    return i;
+  }
+
+ private:
+  std::vector<std::vector<uint64_t>> lv_;
+};
+
+// Ruge-Stueben first pass.  Undecided points sit in buckets by measure; the
+// pick is the smallest index of the highest non-empty bucket (largest
+// measure, smallest index among equals).  Measures only grow.
 void split(const Csr& A, const std::vector<char>& s, std::vector<int32_t>& cf) {
   const int64_t n = A.n;
   // transpose of the strength graph: for point k, the rows j with k in S_j
@@ -51,30 +90,38 @@ void split(const Csr& A, const std::vector<char>& s, std::vector<int32_t>& cf) {
   }
   std::vector<int64_t> lam(n);
   std::vector<char> und(n, 1);
-  std::set<std::pair<int64_t, int64_t>> order;
+  std::vector<std::unique_ptr<IndexSet>> bucket;
+  auto at = [&](int64_t m) -> IndexSet& {
+    while ((int64_t)bucket.size() <= m) bucket.emplace_back(nullptr);
+    if (!bucket[m]) bucket[m].reset(new IndexSet(n));
+    return *bucket[m];
+  };
+  int64_t top = -1;
   for (int64_t k = 0; k < n; ++k) {
     lam[k] = tp[k + 1] - tp[k];
-    order.insert({-lam[k], k});
+    at(lam[k]).insert(k);
+    top = std::max(top, lam[k]);
   }
   cf.assign(n, 0);
-  while (!order.empty()) {
-    const auto top = *order.begin();
-    const int64_t best = top.second;
-    if (lam[best] == 0) break;  // the remaining undecided points become F
-    order.erase(order.begin());
+  for (;;) {
+    while (top > 0 && (!bucket[top] || bucket[top]->empty())) --top;
+    if (top <= 0) break;  // the remaining undecided points (measure 0) become F
+    const int64_t best = bucket[top]->first();
+    bucket[top]->erase(best);
     und[best] = 0;
     cf[best] = 1;
     for (int64_t t = tp[best]; t < tp[best + 1]; ++t) {
       const int32_t j = tj[t];
       if (!und[j]) continue;
       und[j] = 0;  // F
-      order.erase({-lam[j], j});
+      bucket[lam[j]]->erase(j);
       for (int64_t p = A.rp[j]; p < A.rp[j + 1]; ++p) {
         const int32_t k = A.ci[p];
         if (!s[p] || !und[k]) continue;
-        order.erase({-lam[k], k});
+        bucket[lam[k]]->erase(k);
         lam[k]++;
-        order.insert({-lam[k], k});
+        at(lam[k]).insert(k);
+        top = std::max(top, lam[k]);
       }
     }
   }
@@ -151,42 +198,75 @@ void transpose_p(const Csr& P, int64_t nc, Csr& R) {
 // A_c = R A P, row I accumulated as sum over i in row I of R (ascending),
 // j in row i of A (ascending), J in row j of P of (r_Ii a_ij) p_jJ, in that
 // order, into a dense accumulator with a list of touched columns (sorted
-// before the row is stored).
+// before the row is stored).  Rows are independent: contiguous ranges of
+// them go to host threads, each with its own accumulator, and the ranges
+// are concatenated in order, so the result does not depend on the thread
+// count.
 void galerkin(const Csr& A, const Csr& P, const Csr& R, Csr& Ac) {
   const int64_t nc = R.n;
+  struct Part {
+    std::vector<int64_t> len;
+    std::vector<int32_t> ci;
+    std::vector<double> va;
+  };
+  const int64_t work = R.nnz() + nc;
+  int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+  if (work < (1 << 16)) nt = 1;
+  std::vector<Part> parts(nt);
+  auto run = [&](int t) {
+    const int64_t I0 = nc * t / nt, I1 = nc * (t + 1) / nt;
+    Part& out = parts[t];
+    out.len.assign((size_t)(I1 - I0), 0);
+    std::vector<double> acc((size_t)nc, 0.0);
+    std::vector<char> hit((size_t)nc, 0);
+    std::vector<int32_t> cols;
+    for (int64_t I = I0; I < I1; ++I) {
+      cols.clear();
+      for (int64_t t2 = R.rp[I]; t2 < R.rp[I + 1]; ++t2) {
+        const int64_t i = R.ci[t2];
+        const double rIi = R.va[t2];
+        for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
+          const int64_t j = A.ci[p];
+          const double w = rIi * A.va[p];
+          for (int64_t q = P.rp[j]; q < P.rp[j + 1]; ++q) {
+            const int32_t J = P.ci[q];
+            acc[J] += w * P.va[q];
+            if (!hit[J]) {
+              hit[J] = 1;
+              cols.push_back(J);
+            }
+          }
+        }
+      }
+      std::sort(cols.begin(), cols.end());
+      for (int32_t J : cols) {
+        out.ci.push_back(J);
+        out.va.push_back(acc[J]);
+        acc[J] = 0.0;
+        hit[J] = 0;
+      }
+      out.len[(size_t)(I - I0)] = (int64_t)cols.size();
+    }
+  };
+  if (nt == 1) {
+    run(0);
+  } else {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) pool.emplace_back(run, t);
+    for (std::thread& th : pool) th.join();
+  }
   Ac.n = nc;
   Ac.rp.assign(nc + 1, 0);
   Ac.ci.clear();
   Ac.va.clear();
-  std::vector<double> acc(nc, 0.0);
-  std::vector<char> hit(nc, 0);
-  std::vector<int32_t> cols;
-  for (int64_t I = 0; I < nc; ++I) {
-    cols.clear();
-    for (int64_t t = R.rp[I]; t < R.rp[I + 1]; ++t) {
-      const int64_t i = R.ci[t];
-      const double rIi = R.va[t];
-      for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
-        const int64_t j = A.ci[p];
-        const double w = rIi * A.va[p];
-        for (int64_t q = P.rp[j]; q < P.rp[j + 1]; ++q) {
-          const int32_t J = P.ci[q];
-          acc[J] += w * P.va[q];
-          if (!hit[J]) {
-            hit[J] = 1;
-            cols.push_back(J);
-          }
-        }
-      }
+  int64_t I = 0;
+  for (Part& pt : parts) {
+    for (int64_t l : pt.len) {
+      Ac.rp[I + 1] = Ac.rp[I] + l;
+      ++I;
     }
-    std::sort(cols.begin(), cols.end());
-    for (int32_t J : cols) {
-      Ac.ci.push_back(J);
-      Ac.va.push_back(acc[J]);
-      acc[J] = 0.0;
-      hit[J] = 0;
-    }
-    Ac.rp[I + 1] = (int64_t)Ac.ci.size();
+    Ac.ci.insert(Ac.ci.end(), pt.ci.begin(), pt.ci.end());
+    Ac.va.insert(Ac.va.end(), pt.va.begin(), pt.va.end());
   }
 }
 
