@@ -429,6 +429,26 @@ def run_silu(args):
     return 0
 
 
+def class_split(ctx, torch, fn, reps: int, cls_bytes: dict) -> dict:
+    """Run fn() reps times with the library's event timing on and return, per
+    kernel class, launches, total ms and (for the classes in cls_bytes, bytes
+    per launch) the algorithmic GB/s.  Runs of consecutive sweeps are timed as
+    one record, so gaps inside a run count."""
+    ctx.profile(True)
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    split = {}
+    for k, (cnt, kms) in prof.items():
+        if cnt:
+            split[k] = {"launches": cnt, "ms": round(kms, 4)}
+            if k in cls_bytes and kms > 0:
+                split[k]["gbs"] = round(cnt * cls_bytes[k] / (kms * 1e-3) / 1e9, 1)
+    return split
+
+
 def solve_comparison(silu, ctx, torch, edge: int):
     """The 27-point workload: FGMRES(30) to 1e-10 relative residual with the
     FP32 scaled-ILU(0) Richardson smoother (3+3 FP32 sweeps, FP64 residual and
@@ -449,7 +469,7 @@ def solve_comparison(silu, ctx, torch, edge: int):
            "setup_s": round(setup_s, 2)}
     del A
     b = torch.from_numpy(b_np[:, 0].copy()).cuda()
-    # FP32 smoother application rate (zero initial guess skips the residual)
+    # FP32 smoother application rate (x != 0 after the first application, so the FP64 residual runs)
     x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
     b2 = b.reshape(n, 1)
     for _ in range(3):
@@ -464,7 +484,11 @@ def solve_comparison(silu, ctx, torch, edge: int):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     nbytes = apply_bytes(n, out["nnz_A"], st["nnz_L"], st["nnz_U"], 1, 4, 3, 3)
-    out["fp32_apply"] = {"ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "bytes": nbytes}
+    split = class_split(ctx, torch, lambda: silu.ilu_smooth(F, x, b2, 3, 3), reps,
+                        {"residual": resid_bytes(n, out["nnz_A"], 1), "sweep_L": sweep_bytes(n, st["nnz_L"], 1, 4),
+                         "sweep_U": sweep_bytes(n, st["nnz_U"], 1, 4)})
+    out["fp32_apply"] = {"ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "bytes": nbytes,
+                         "kernels": split}
     for name, pc in (("fp32_sweeps_3_3", silu.PRECOND_SWEEPS), ("fp64_direct", silu.PRECOND_DIRECT)):
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
         silu.fgmres_solve(F, x, b, tol=1e-10, restart=30, maxit=1, sweeps_L=3, sweeps_U=3, precond=pc)
@@ -513,21 +537,10 @@ def batch_workload(silu, ctx, torch, count: int):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     nbytes = apply_bytes(n, nnzA, st["nnz_L"], st["nnz_U"], 1, 4, 3, 3)
-    # per-kernel-class split of the same loop (one event pair per run of sweeps)
-    ctx.profile(True)
-    for _ in range(reps):
-        silu.silu_batch_smooth(B, x, b, 3, 3)
-    torch.cuda.synchronize()
-    prof = ctx.profile_read()
-    ctx.profile(False)
-    cls_bytes = {"residual": resid_bytes(n, nnzA, 1), "sweep_L": sweep_bytes(n, st["nnz_L"], 1, 4),
-                 "sweep_U": sweep_bytes(n, st["nnz_U"], 1, 4)}
-    split = {}
-    for k, (cnt, kms) in prof.items():
-        if cnt:
-            split[k] = {"launches": cnt, "ms": round(kms, 4)}
-            if k in cls_bytes and kms > 0:
-                split[k]["gbs"] = round(cnt * cls_bytes[k] / (kms * 1e-3) / 1e9, 1)
+    # per-kernel-class split of the same loop
+    split = class_split(ctx, torch, lambda: silu.silu_batch_smooth(B, x, b, 3, 3), reps,
+                        {"residual": resid_bytes(n, nnzA, 1), "sweep_L": sweep_bytes(n, st["nnz_L"], 1, 4),
+                         "sweep_U": sweep_bytes(n, st["nnz_U"], 1, 4)})
     x.zero_()
     silu.silu_batch_fgmres(B, x, b, tol=1e-8, restart=20, maxit=1, sweeps_L=3, sweeps_U=3)
     x.zero_()
@@ -550,8 +563,11 @@ def serving(silu, args):
     """Continuous-batching solve server: Poisson arrivals (mean rate
     args.serve_rate per second, seed 4) of cut-cell pressure solves with grid
     edges log-uniform in [16, 192], each FGMRES(30) from zero to 1e-8, under a
-    120 GB HBM budget.  Two paths on the same arrival stream: FP32 scaled-ILU(0)
-    Richardson smoother (3+3 sweeps) and the plain FP64 direct-trisolve path.
+    120 GB HBM budget.  Three paths on the same arrival stream: FP32 scaled-ILU(0)
+    Richardson smoother (3+3 sweeps), the same FP32 smoother (8+8 sweeps) on
+    the finest level of an AMG V-cycle (the paper's GMRES + AMG; the
+    hierarchy is built on the host per request), and the plain FP64
+    direct-trisolve path.
     The client draws every request's edge from the stream but takes its matrix
     from a pool of args.serve_pool distinct systems generated before the clock
     starts (request k uses pool entry k mod pool, whose edge is the pool's own
@@ -575,8 +591,9 @@ def serving(silu, args):
            "rate_per_s": rate, "seconds": dur, "offered": int(len(arrivals)), "pool": P,
            "pool_rows_mean": int(np.mean(edges.astype(np.int64) ** 3)), "hbm_budget_gb": 120,
            "workers": args.serve_workers, "max_queue": args.serve_queue}
-    for name, prec, pc in (("fp32_sweeps_3_3", silu.FP32, silu.PRECOND_SWEEPS),
-                           ("fp64_direct", silu.FP64, silu.PRECOND_DIRECT)):
+    for name, prec, pc, sw in (("fp32_sweeps_3_3", silu.FP32, silu.PRECOND_SWEEPS, 3),
+                               ("fp32_amg_sweeps_8_8", silu.FP32, silu.PRECOND_AMG, 8),
+                               ("fp64_direct", silu.FP64, silu.PRECOND_DIRECT, 3)):
         S = silu.Server(0, 120 << 30, workers=args.serve_workers, max_queue=args.serve_queue)
         tickets, refused = [], 0
         start = time.perf_counter()
@@ -585,19 +602,20 @@ def serving(silu, args):
             if now < t_k:
                 time.sleep(t_k - now)
             A, b = pool[k % P]
-            st, t = S.submit(A, b, prec=prec, tol=1e-8, restart=30, maxit=20000, sweeps_L=3, sweeps_U=3,
+            st, t = S.submit(A, b, prec=prec, tol=1e-8, restart=30, maxit=20000, sweeps_L=sw, sweeps_U=sw,
                              precond=pc)
             if st == silu.OK:
                 tickets.append(t)
             else:
                 refused += 1
-        lat, solved, iters, t_first, t_last = [], 0, [], None, None
+        lat, solved, iters, t_first, t_last, setup = [], 0, [], None, None, []
         for t in tickets:
             _, res, _ = S.poll(t, wait=True, want_x=False)
             if res.status == silu.OK:
                 solved += 1
                 lat.append(res.t_done - res.t_submit)
                 iters.append(res.iterations)
+                setup.append(res.t_setup_done - res.t_admit)
                 t_first = res.t_submit if t_first is None else min(t_first, res.t_submit)
                 t_last = res.t_done if t_last is None else max(t_last, res.t_done)
         S.close()
@@ -606,7 +624,8 @@ def serving(silu, args):
                      "solves_per_s": round(solved / span, 3) if span > 0 else None,
                      "p50_s": round(float(np.percentile(lat, 50)), 4) if lat else None,
                      "p99_s": round(float(np.percentile(lat, 99)), 4) if lat else None,
-                     "iterations_mean": round(float(np.mean(iters)), 1) if iters else None}
+                     "iterations_mean": round(float(np.mean(iters)), 1) if iters else None,
+                     "host_setup_mean_s": round(float(np.mean(setup)), 3) if setup else None}
     return out
 
 

@@ -471,7 +471,9 @@ void silu_batch_destroy(silu_batch B);
  * the whole budget is refused (SILU_ERR_OOM) and so is any request while
  * `max_queue` requests wait (SILU_ERR_BUSY).  Each slot has its own host
  * thread, CUDA stream and context: it factors the system on the host
- * (ilu_setup, row scaling), runs fgmres_solve from x = 0 on its stream and
+ * (ilu_setup, row scaling; with precond SILU_PRECOND_AMG or
+ * SILU_PRECOND_AMG_DIRECT also silu_amg_setup with the default parameters),
+ * runs fgmres_solve from x = 0 on its stream and
  * copies the solution back, so admitted requests overlap on the device and
  * memory is released as each finishes.  Results do not depend on what else
  * runs.  device = -1 makes a host-only server for testing the admission
@@ -485,7 +487,7 @@ typedef struct {
   double tol;           /* relative residual (Eq. relres) */
   int restart, maxit;
   int sweeps_L, sweeps_U;
-  int precond;          /* silu_precond */
+  int precond;          /* silu_precond: SWEEPS, DIRECT, NONE, AMG or AMG_DIRECT */
 } silu_request_params;
 
 typedef struct {

@@ -78,7 +78,10 @@ int64_t estimate_bytes(int64_t n, int64_t nnz, const silu_request_params& p) {
   b += 4 * n * 8;
   b += (int64_t)(2 * p.restart + 2) * n * 8;
   b += 2 * n * 8;
-  if (p.precond == SILU_PRECOND_DIRECT) b += fnnz * 12 + 4 * n;
+  if (p.precond == SILU_PRECOND_DIRECT || p.precond == SILU_PRECOND_AMG_DIRECT) b += fnnz * 12 + 4 * n;
+  // AMG: coarse operators (operator complexity about 2.5 for these matrices),
+  // P and R of every level, four vectors and the l1 diagonal per level
+  if (p.precond == SILU_PRECOND_AMG || p.precond == SILU_PRECOND_AMG_DIRECT) b += nnz * 12 * 8 / 5 + n * 160;
   b += (b / 16) + (1 << 20);  // tiles, padding, small buffers
   return b;
 }
@@ -105,6 +108,10 @@ void solve_one(silu_server S, silu_ctx ctx, const std::shared_ptr<Request>& r) {
     if (status != SILU_OK) break;
     status = ilu_setup(ctx, M, (silu_kind)q.p.kind, q.p.tau, q.p.fill, SILU_SCALE_ROW, (silu_prec)q.p.prec, &F);
     if (status != SILU_OK) break;
+    if (q.p.precond == SILU_PRECOND_AMG || q.p.precond == SILU_PRECOND_AMG_DIRECT) {
+      status = silu_amg_setup(F, nullptr);
+      if (status != SILU_OK) break;
+    }
     q.res.t_setup_done = now_s() - S->t0;
     if (ctx->device < 0) {
       status = SILU_ERR_NO_DEVICE;
@@ -218,7 +225,7 @@ silu_status silu_server_submit(silu_server S, int64_t n, const int64_t* row_ptr,
   if (!S || !params || !ticket || (n > 0 && !b)) return SILU_ERR_INVALID_ARG;
   const silu_request_params& p = *params;
   if (p.kind < SILU_ILU0 || p.kind > SILU_SGS || p.prec < SILU_FP64 || p.prec > SILU_FP32 || p.restart < 1 ||
-      p.maxit < 0 || p.precond < 0 || p.precond > 2 || !(p.tol >= 0.0))
+      p.maxit < 0 || p.precond < 0 || p.precond > SILU_PRECOND_AMG_DIRECT || !(p.tol >= 0.0))
     return SILU_ERR_INVALID_ARG;
   auto r = std::make_shared<Request>();
   std::string msg;

@@ -70,3 +70,33 @@ def test_result_same_alone_and_in_the_mix(silu):
     # admitted requests overlapped on the device
     spans.sort()
     assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
+
+
+def test_served_amg_request_matches_direct_solve(silu):
+    """A request with the AMG V-cycle preconditioner (the paper's GMRES + AMG,
+    FP32 ILU smoothing the finest level) gives the same bits through the
+    server, alone and next to a sweeps-only request, as a direct call."""
+    A = synth.cutcell7(34, 30, 27, seed=51)
+    n = len(A[0]) - 1
+    b = synth.rhs(n, 1, seed=52)[:, 0]
+    S = silu.Server(device=0, hbm_budget=8 << 30, workers=2, max_queue=8)
+    kw = dict(prec=silu.FP32, tol=1e-8, restart=30, maxit=2000, sweeps_L=8, sweeps_U=8, precond=silu.PRECOND_AMG)
+    st, t = S.submit(A, b, **kw)
+    assert st == silu.OK
+    other = synth.cutcell7(40, 40, 40, seed=53)
+    st2, t2 = S.submit(other, synth.rhs(len(other[0]) - 1, 1, seed=54)[:, 0], prec=silu.FP32, tol=1e-8)
+    assert st2 == silu.OK
+    _, res, x = S.poll(t, wait=True)
+    _, res2, _ = S.poll(t2, wait=True, want_x=False)
+    S.close()
+    assert res.status == silu.OK and res.relres <= 1e-8 and res2.status == silu.OK
+    r = oracle.residual(A, x.reshape(n, 1), b.reshape(n, 1))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-8
+    ctx = silu.Context(0, torch.cuda.current_stream())
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0", prec=silu.FP32)
+    F.amg_setup()
+    xd = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st1, its1, _ = silu.fgmres_solve(F, xd, torch.from_numpy(b).cuda(), tol=1e-8, restart=30, maxit=2000,
+                                     sweeps_L=8, sweeps_U=8, precond=silu.PRECOND_AMG)
+    assert st1 == silu.OK and its1 == res.iterations
+    assert np.array_equal(xd.cpu().numpy(), x)
