@@ -354,16 +354,22 @@ silu_status silu_ilu_layout(silu_ilu F, double* pad_natural, double* pad_sorted,
  * A_{l+1} = P^T A_l P.  Coarsening stops at max_levels levels, at
  * coarse_size rows or fewer, or when no further split is possible; the
  * coarsest level (at most 4096 rows, else SILU_ERR_INVALID_ARG) is solved by
- * its dense inverse.  Levels below the finest are smoothed by jacobi_sweeps
- * sweeps of l1-Jacobi, x <- x + D^{-1}(b - A x) with d_i = sum_j |a_ij|, before
- * and after their coarse-grid correction.  params NULL = {0.25, 25, 400, 1}.
- * Blocks.
+ * its dense inverse.  Levels below the finest are smoothed, before and after
+ * their coarse-grid correction, by jacobi_sweeps steps of
+ *   SILU_AMG_L1_JACOBI: x <- x + D^{-1}(b - A x) with d_i = sum_j |a_ij|, or
+ *   SILU_AMG_POLY_GS:   x <- x + sum_{j<gs_terms} (-D^{-1} L)^j D^{-1} (b - A x)
+ *                       (polynomial Gauss-Seidel, Sec. 3.1; the mixed V-cycle
+ *                       of Sec. 6.3), D = diag(A), L its strict lower part.
+ * params NULL = {0.25, 25, 400, 1, SILU_AMG_L1_JACOBI, 2}.  Blocks.
  */
+typedef enum { SILU_AMG_L1_JACOBI = 0, SILU_AMG_POLY_GS = 1 } silu_amg_smoother;
 typedef struct {
-  double theta;       /* strength threshold, 0 < theta <= 1 */
-  int max_levels;     /* >= 1 */
-  int coarse_size;    /* stop coarsening at this many rows or fewer, >= 1 */
-  int jacobi_sweeps;  /* l1-Jacobi sweeps before and after the correction below the finest level */
+  double theta;         /* strength threshold, 0 < theta <= 1 */
+  int max_levels;       /* >= 1 */
+  int coarse_size;      /* stop coarsening at this many rows or fewer, >= 1 */
+  int jacobi_sweeps;    /* smoothing steps before and after the correction below the finest level, >= 0 */
+  int coarse_smoother;  /* silu_amg_smoother */
+  int gs_terms;         /* Neumann terms of each polynomial Gauss-Seidel step, >= 1 */
 } silu_amg_params;
 silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params);
 /*

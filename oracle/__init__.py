@@ -98,7 +98,7 @@ def _load():
         "orc_amg_nlev": (i32, [vp]),
         "orc_amg_level_sizes": (None, [vp, i32] + [ctypes.POINTER(i64)] * 4),
         "orc_amg_level_copy": (None, [vp, i32] + [vp] * 7),
-        "orc_amg_vcycle": (i32, [vp] + [vp] * 7 + [i32, i32, i32, vp, vp]),
+        "orc_amg_vcycle": (i32, [vp] + [vp] * 7 + [i32, i32, i32, i32, i32, vp, vp]),
         "orc_schur_interface": (i64, [i64, vp, vp, i32, vp]),
         "orc_schur_apply": (i32, [i64, vp, vp, vp, i32, dbl, i32, i32, i32, vp, vp]),
     }
@@ -556,16 +556,17 @@ class AMG:
                 P, cf = None, None
             self.levels.append(AMGLevel(m, (lap, lac[:nz.value], lav[:nz.value]), P, cf))
 
-    def vcycle(self, S: Scaled, x, b, mL: int, mU: int, nu: int = 1):
+    def vcycle(self, S: Scaled, x, b, mL: int, mU: int, nu: int = 1, coarse: str = "jacobi", terms: int = 2):
         """One V-cycle (Alg. mgcycle) from x: ILU smoother (m_L + m_U sweeps on S) on the finest
-        level, nu l1-Jacobi sweeps below, direct solve on the coarsest.  Returns a new array."""
+        level, nu steps of l1-Jacobi (coarse="jacobi") or of polynomial Gauss-Seidel with `terms`
+        terms (coarse="gs") below, direct solve on the coarsest.  Returns a new array."""
         n = self.levels[0].n
         x = np.ascontiguousarray(x, np.float64).reshape(n).copy()
         b = np.ascontiguousarray(b, np.float64).reshape(n)
         lp, lc, lv = _csr(S.L)
         sp, sc, sv = _csr(S.Us)
         st = _load().orc_amg_vcycle(self._h, _p(lp), _p(lc), _p(lv), _p(sp), _p(sc), _p(sv), _p(S.dinv), int(mL),
-                                    int(mU), int(nu), _p(x), _p(b))
+                                    int(mU), int(nu), 1 if coarse == "gs" else 0, int(terms), _p(x), _p(b))
         if st:
             raise OracleError(st, "amg_vcycle")
         return x

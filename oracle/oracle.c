@@ -1685,12 +1685,37 @@ static void l1_jacobi(const orc_amg_level* L, const double* b, double* x, int nu
   free(r);
 }
 
+/* nu steps of polynomial Gauss-Seidel on level L (Sec. 3.1):
+ * x <- x + sum_{j<terms} (-D^{-1} L)^j D^{-1} (b - A x). */
+static int poly_gs_steps(const orc_amg_level* L, const double* b, double* x, int nu, int terms) {
+  const int64_t n = L->n;
+  double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* z = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  int st = ORC_OK;
+  for (int k = 0; k < nu && !st; ++k) {
+    orc_residual(n, 1, L->ap, L->ac, L->av, x, b, r);
+    st = orc_poly_gs_lower(n, 1, L->ap, L->ac, L->av, r, terms - 1, z);
+    for (int64_t i = 0; i < n && !st; ++i) x[i] = x[i] + z[i];
+  }
+  free(r);
+  free(z);
+  return st;
+}
+
 typedef struct {
   const int64_t *lp, *sp;
   const int32_t *lc, *sc;
   const double *lv, *sv, *dinv;
   int mL, mU, nu;
+  int coarse; /* 0: l1-Jacobi, 1: polynomial Gauss-Seidel with `terms` terms */
+  int terms;
 } amg_smoother;
+
+static int coarse_smooth(const orc_amg_level* L, const amg_smoother* sm, const double* b, double* x) {
+  if (sm->coarse == 1) return poly_gs_steps(L, b, x, sm->nu, sm->terms);
+  l1_jacobi(L, b, x, sm->nu);
+  return ORC_OK;
+}
 
 /* Alg. mgcycle, Multilevel(A_l, b, x, l) with nu = 1 (V-cycle). */
 static int multilevel(const orc_amg* h, int l, const amg_smoother* sm, const double* b, double* x) {
@@ -1704,7 +1729,7 @@ static int multilevel(const orc_amg* h, int l, const amg_smoother* sm, const dou
                          sm->mL, sm->mU)))
       return st;
   } else {
-    l1_jacobi(L, b, x, sm->nu);
+    if ((st = coarse_smooth(L, sm, b, x))) return st;
   }
   double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   double* bc = (double*)calloc((size_t)(L->nc > 0 ? L->nc : 1), sizeof(double));
@@ -1724,7 +1749,7 @@ static int multilevel(const orc_amg* h, int l, const amg_smoother* sm, const dou
       st = orc_smooth(n, 1, L->ap, L->ac, L->av, sm->lp, sm->lc, sm->lv, sm->sp, sm->sc, sm->sv, sm->dinv, x, b,
                       sm->mL, sm->mU);
     else
-      l1_jacobi(L, b, x, sm->nu);
+      st = coarse_smooth(L, sm, b, x);
   }
   free(r);
   free(bc);
@@ -1736,14 +1761,16 @@ static int multilevel(const orc_amg* h, int l, const amg_smoother* sm, const dou
  * One V-cycle (Alg. mgcycle, nu = 1) on A_0 x = b, updating x in place:
  * the finest level is smoothed before and after the coarse-grid correction
  * by the ILU smoother (m_L + m_U Richardson sweeps on the row-scaled factors
- * L_s, Utilde_s, dinv), every coarser level by nu sweeps of l1-Jacobi, and
- * the coarsest level is solved directly.  A single-level hierarchy is one
+ * L_s, Utilde_s, dinv), every coarser level by nu steps of l1-Jacobi
+ * (coarse = 0) or of polynomial Gauss-Seidel with `terms` Neumann terms
+ * (coarse = 1; Sec. 6.3's mixed V-cycle), and the coarsest level is solved
+ * directly.  A single-level hierarchy is one
  * direct solve.
  */
 int orc_amg_vcycle(const orc_amg* h, const int64_t* lp, const int32_t* lc, const double* lv, const int64_t* sp,
-                   const int32_t* sc, const double* sv, const double* dinv, int mL, int mU, int nu, double* x,
-                   const double* b) {
-  amg_smoother sm = {lp, sp, lc, sc, lv, sv, dinv, mL, mU, nu};
+                   const int32_t* sc, const double* sv, const double* dinv, int mL, int mU, int nu, int coarse,
+                   int terms, double* x, const double* b) {
+  amg_smoother sm = {lp, sp, lc, sc, lv, sv, dinv, mL, mU, nu, coarse, terms};
   return multilevel(h, 0, &sm, b, x);
 }
 

@@ -242,10 +242,13 @@ class Context:
             pass
 
 
+AMG_L1_JACOBI, AMG_POLY_GS = 0, 1
+
+
 class AmgParams(ctypes.Structure):
     """silu_amg_params."""
     _fields_ = [("theta", ctypes.c_double), ("max_levels", ctypes.c_int), ("coarse_size", ctypes.c_int),
-                ("jacobi_sweeps", ctypes.c_int)]
+                ("jacobi_sweeps", ctypes.c_int), ("coarse_smoother", ctypes.c_int), ("gs_terms", ctypes.c_int)]
 
 
 class Matrix:
@@ -356,9 +359,12 @@ class ILU:
         _check(self.ctx.handle, st, "silu_ilu_power_norms")
         return out[:pmax]
 
-    def amg_setup(self, theta: float = 0.25, max_levels: int = 25, coarse_size: int = 400, jacobi_sweeps: int = 1):
-        """Build and attach the AMG hierarchy of A (Sec. 3); this factor object smooths its finest level."""
-        p = AmgParams(float(theta), int(max_levels), int(coarse_size), int(jacobi_sweeps))
+    def amg_setup(self, theta: float = 0.25, max_levels: int = 25, coarse_size: int = 400, jacobi_sweeps: int = 1,
+                  coarse_smoother: int = AMG_L1_JACOBI, gs_terms: int = 2):
+        """Build and attach the AMG hierarchy of A (Sec. 3); this factor object smooths its finest level,
+        l1-Jacobi or polynomial Gauss-Seidel (gs_terms Neumann terms) the coarser ones."""
+        p = AmgParams(float(theta), int(max_levels), int(coarse_size), int(jacobi_sweeps), int(coarse_smoother),
+                      int(gs_terms))
         _check(self.ctx.handle, load().silu_amg_setup(self.handle, ctypes.byref(p)), "silu_amg_setup")
 
     def amg_vcycle(self, x, b, sweeps_L: int, sweeps_U: int):

@@ -69,6 +69,44 @@ double* l1_jacobi(silu_ilu F, AmgDevLevel& L, double* cur, const double* b, int 
   return cur;
 }
 
+// nu steps of polynomial Gauss-Seidel on level l (Sec. 3.1),
+// x <- x + D^{-1} y with y = sum_{j<terms} (-L D^{-1})^j (b - A x), the
+// Neumann series run as Richardson sweeps on L D^{-1} with the last one fused
+// into the update of x (in place: x is not read by that launch).
+double* poly_gs(silu_ilu F, AmgDevLevel& L, double* x, const double* b, int nu, int terms, bool x_zero) {
+  cudaStream_t s = F->ctx->stream;
+  const double* dinv = L.gdinv.as<double>();
+  if (x_zero && nu == 0) CK(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)L.n, s));
+  for (int step = 0; step < nu; ++step) {
+    const bool set = x_zero && step == 0;  // x is still zero: write, do not add
+    const double* r = b;
+    if (!set) {
+      op(F, L.A, SILU_K_RESIDUAL, b, x, L.r.as<double>(), nullptr, nullptr, silu::EPI_STORE);
+      r = L.r.as<double>();
+    }
+    if (terms <= 1) {
+      LAUNCH(F->ctx, SILU_K_ELEMENTWISE, silu::launch_addx((int)L.n, 1, 1, r, false, dinv, x, !set, s));
+      continue;
+    }
+    const double* in = r;
+    double* pp[2] = {L.t.as<double>(), L.y2.as<double>()};
+    for (int k = 2; k <= terms; ++k) {
+      const bool last = k == terms;
+      const int epi = last ? (set ? silu::EPI_SCALE_SETX : silu::EPI_SCALE_ADDX) : silu::EPI_STORE;
+      op(F, L.Lgs, SILU_K_SWEEP_L, r, in, last ? nullptr : pp[k & 1], dinv, x, epi);
+      in = pp[k & 1];
+    }
+  }
+  return x;
+}
+
+// The configured smoother of a level below the finest.
+double* coarse_smooth(silu_ilu F, AmgDevLevel& L, double* x, const double* b, bool x_zero) {
+  const AmgState& G = *F->amg;
+  if (G.coarse_kind == SILU_AMG_POLY_GS) return poly_gs(F, L, x, b, G.nu, G.gs_terms, x_zero);
+  return l1_jacobi(F, L, x, b, G.nu, x_zero);
+}
+
 // Multilevel(A_l, b, x, l) of Alg. mgcycle for l >= 1, from x = 0; returns
 // the buffer that holds x_l.
 double* level_cycle(silu_ilu F, int l) {
@@ -81,16 +119,17 @@ double* level_cycle(silu_ilu F, int l) {
                                                     F->ctx->stream));
     return L.x.as<double>();
   }
-  double* x = l1_jacobi(F, L, L.x.as<double>(), b, G.nu, true);
+  double* x = coarse_smooth(F, L, L.x.as<double>(), b, true);
   AmgDevLevel& C = *G.lev[l + 1];
   op(F, L.A, SILU_K_RESIDUAL, b, x, L.r.as<double>(), nullptr, nullptr, silu::EPI_STORE);       // r = b - A x
   op(F, L.R, SILU_K_RESIDUAL, nullptr, L.r.as<double>(), C.b.as<double>(), nullptr, nullptr, silu::EPI_SPMV);
   const double* v = level_cycle(F, l + 1);
   op(F, L.Pneg, SILU_K_RESIDUAL, nullptr, v, nullptr, nullptr, x, silu::EPI_ADDX);             // x += P v
-  return l1_jacobi(F, L, x, b, G.nu, false);
+  return coarse_smooth(F, L, x, b, false);
 }
 
-cudaError_t upload_level(const silu::AmgLevel& H, AmgDevLevel& D, bool own_a, bool coarsest, cudaStream_t s) {
+cudaError_t upload_level(const silu::AmgLevel& H, AmgDevLevel& D, bool own_a, bool coarsest, bool gs,
+                         cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   D.n = H.A.n;
   if (own_a) e = silu::upload_csr(H.A, false, D.A_rp, D.A_ci, D.A_va, D.A_tiles, D.A, s);
@@ -99,7 +138,12 @@ cudaError_t upload_level(const silu::AmgLevel& H, AmgDevLevel& D, bool own_a, bo
     if (e == cudaSuccess) e = silu::upload_csr(H.R, false, D.R_rp, D.R_ci, D.R_va, D.R_tiles, D.R, s);
   }
   if (e == cudaSuccess) e = silu::upload(D.l1inv, H.l1inv.data(), H.l1inv.size(), s);
+  if (e == cudaSuccess && gs && own_a) {
+    e = silu::upload_csr(H.Lgs, false, D.G_rp, D.G_ci, D.G_va, D.G_tiles, D.Lgs, s);
+    if (e == cudaSuccess) e = silu::upload(D.gdinv, H.dinv.data(), H.dinv.size(), s);
+  }
   const size_t vb = sizeof(double) * (size_t)std::max<int64_t>(D.n, 1);
+  if (e == cudaSuccess) e = D.y2.ensure(vb);
   if (e == cudaSuccess) e = D.x.ensure(vb);
   if (e == cudaSuccess) e = D.t.ensure(vb);
   if (e == cudaSuccess) e = D.b.ensure(vb);
@@ -144,9 +188,11 @@ extern "C" {
 silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params) {
   if (!F) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = F->ctx;
-  silu_amg_params p = {0.25, 25, 400, 1};
+  silu_amg_params p = {0.25, 25, 400, 1, SILU_AMG_L1_JACOBI, 2};
   if (params) p = *params;
   if (p.jacobi_sweeps < 0) return silu::set_err(ctx, SILU_ERR_INVALID_ARG, "jacobi_sweeps must be >= 0");
+  if ((p.coarse_smoother != SILU_AMG_L1_JACOBI && p.coarse_smoother != SILU_AMG_POLY_GS) || p.gs_terms < 1)
+    return silu::set_err(ctx, SILU_ERR_INVALID_ARG, "bad coarse smoother or gs_terms");
   std::unique_ptr<AmgState> G;
   try {
     G.reset(new AmgState);
@@ -154,8 +200,11 @@ silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params) {
     G->max_levels = p.max_levels;
     G->coarse_size = p.coarse_size;
     G->nu = p.jacobi_sweeps;
+    G->coarse_kind = p.coarse_smoother;
+    G->gs_terms = p.gs_terms;
     std::string msg;
-    const int st = silu::amg_build(F->A->A, p.theta, p.max_levels, p.coarse_size, G->host, msg);
+    int st = silu::amg_build(F->A->A, p.theta, p.max_levels, p.coarse_size, G->host, msg);
+    if (st == silu::H_OK && p.coarse_smoother == SILU_AMG_POLY_GS) st = silu::amg_gs_factors(G->host, msg);
     if (st != silu::H_OK) return silu::set_err(ctx, (silu_status)st, msg);
     if (ctx->device >= 0) {
       silu_status ds = silu::device_ok(ctx);
@@ -165,7 +214,7 @@ silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params) {
       cudaError_t e = silu::ensure_vectors(F, 1);
       for (size_t l = 0; e == cudaSuccess && l < nl; ++l) {
         G->lev.emplace_back(new AmgDevLevel);
-        e = upload_level(G->host.lev[l], *G->lev[l], l > 0, l + 1 == nl, s);
+        e = upload_level(G->host.lev[l], *G->lev[l], l > 0, l + 1 == nl, p.coarse_smoother == SILU_AMG_POLY_GS, s);
       }
       if (e == cudaSuccess)
         e = silu::upload(G->cinv, G->host.coarse_inv.data(), G->host.coarse_inv.size(), s);

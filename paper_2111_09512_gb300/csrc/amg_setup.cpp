@@ -359,4 +359,17 @@ int amg_build(const Csr& A, double theta, int max_levels, int64_t coarse_size, A
   return H_OK;
 }
 
+int amg_gs_factors(AmgHost& H, std::string& msg) {
+  for (size_t l = 1; l < H.lev.size(); ++l) {
+    AmgLevel& L = H.lev[l];
+    Factors F;
+    const int st = factor_gs(L.A, false, F, msg);  // L_s = L_A D^{-1}, U = D
+    if (st != H_OK) return st;
+    L.Lgs = std::move(F.L);
+    L.dinv.resize(L.A.n);
+    for (int64_t i = 0; i < L.A.n; ++i) L.dinv[i] = 1.0 / F.U.va[F.U.rp[i]];
+  }
+  return H_OK;
+}
+
 }  // namespace silu

@@ -18,6 +18,8 @@ struct AmgLevel {
   Csr P, R;                   // P_l (n_l x n_{l+1}) and R_l = P_l^T; empty on the coarsest level
   std::vector<int32_t> cf;    // 1 = coarse point (not on the coarsest level)
   std::vector<double> l1inv;  // 1 / sum_j |a_ij| (l1-Jacobi)
+  Csr Lgs;                    // L D^{-1}: strict lower part of A, column j divided by a_jj (polynomial GS)
+  std::vector<double> dinv;   // 1 / a_ii (polynomial GS)
 };
 
 struct AmgHost {
@@ -34,5 +36,8 @@ struct AmgHost {
 // points.  Returns H_OK, H_BADARG (bad parameters, or a coarsest level above
 // kAmgMaxCoarse rows) or H_ZERO_PIVOT (empty row, singular coarsest level).
 int amg_build(const Csr& A, double theta, int max_levels, int64_t coarse_size, AmgHost& H, std::string& msg);
+// Polynomial Gauss-Seidel data of every level below the finest (Lgs, dinv).
+// H_ZERO_PIVOT for a zero or missing diagonal entry.
+int amg_gs_factors(AmgHost& H, std::string& msg);
 
 }  // namespace silu

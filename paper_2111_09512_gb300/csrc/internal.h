@@ -129,6 +129,8 @@ struct AmgDevLevel {
   DBuf A_rp, A_ci, A_va, A_tiles, P_rp, P_ci, P_va, P_tiles, R_rp, R_ci, R_va, R_tiles;
   DevCsr A, Pneg, R;
   DBuf l1inv, x, t, b, r;
+  DBuf G_rp, G_ci, G_va, G_tiles, gdinv, y2;  // polynomial Gauss-Seidel: L D^{-1}, 1 / a_ii, a second sweep buffer
+  DevCsr Lgs;
 };
 
 // An AMG hierarchy attached to a factor object: the factors smooth the
@@ -137,7 +139,9 @@ struct AmgState {
   silu::AmgHost host;
   std::vector<std::unique_ptr<AmgDevLevel>> lev;
   DBuf cinv;  // dense inverse of the coarsest operator
-  int nu = 1;  // l1-Jacobi sweeps before and after the correction on levels >= 1
+  int nu = 1;  // smoothing steps before and after the correction on levels >= 1
+  int coarse_kind = SILU_AMG_L1_JACOBI;
+  int gs_terms = 2;
   double theta = 0.25;
   int max_levels = 25;
   int64_t coarse_size = 400;

@@ -51,13 +51,16 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("coarse", ["jacobi", "gs"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_vcycle_matches_oracle(silu, ctx, case):
+def test_vcycle_matches_oracle(silu, ctx, case, coarse):
     name, gen, kind, tau, fill, theta, cs, nu, (mL, mU), tol = case
     A = gen()
     n = len(A[0]) - 1
     F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), kind, tau, fill)
-    F.amg_setup(theta=theta, max_levels=12, coarse_size=cs, jacobi_sweeps=nu)
+    terms = 3
+    F.amg_setup(theta=theta, max_levels=12, coarse_size=cs, jacobi_sweeps=nu,
+                coarse_smoother=silu.AMG_POLY_GS if coarse == "gs" else silu.AMG_L1_JACOBI, gs_terms=terms)
     H = oracle.AMG(A, theta=theta, max_levels=12, coarse_size=cs)
     assert F.amg_stats()["levels"] == len(H.levels) >= 3
     S = oracle.row_scale(oracle.factor(A, kind, tau, fill))
@@ -66,7 +69,7 @@ def test_vcycle_matches_oracle(silu, ctx, case):
     xd = torch.zeros(n, dtype=torch.float64, device="cuda")
     bd = dev(b)
     for cycle in range(3):  # successive cycles from the previous iterate
-        x = H.vcycle(S, x, b, mL, mU, nu=nu)
+        x = H.vcycle(S, x, b, mL, mU, nu=nu, coarse=coarse, terms=terms)
         F.amg_vcycle(xd, bd, mL, mU)
         ctx.check()
         err = relerr(host(xd), x)
@@ -132,4 +135,21 @@ def test_vcycle_with_exact_triangular_solves(silu, ctx):
                                          precond=silu.PRECOND_AMG_DIRECT)
     assert status == silu.OK and rel <= 1e-10
     r = oracle.residual(A, host(xs).reshape(n, 1), b.reshape(n, 1))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10
+
+
+@pytest.mark.parametrize("terms", [1, 2, 4])
+def test_fgmres_amg_with_polynomial_gs_below(silu, ctx, terms):
+    """The mixed V-cycle of Sec. 6.3 (ILU on the finest level, polynomial
+    Gauss-Seidel below) as the FGMRES preconditioner reaches 1e-10."""
+    A = synth.cutcell7(36, 32, 30, seed=12)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+    F.amg_setup(coarse_size=200, jacobi_sweeps=1, coarse_smoother=silu.AMG_POLY_GS, gs_terms=terms)
+    b = synth.rhs(n, 1, seed=13)[:, 0]
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st, its, rel = silu.fgmres_solve(F, x, dev(b), tol=1e-10, restart=30, maxit=1000, sweeps_L=6, sweeps_U=6,
+                                     precond=silu.PRECOND_AMG)
+    assert st == silu.OK and rel <= 1e-10, (st, its, rel)
+    r = oracle.residual(A, host(x).reshape(n, 1), b.reshape(n, 1))
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10

@@ -311,3 +311,14 @@ def test_schur_interface_matches_oracle(ctx, parts):
     assert np.array_equal(st["marks"], marks)
     with pytest.raises(silu.SiluError):
         F.schur_setup(0, 1e-3, 10)
+
+
+def test_amg_rejects_bad_coarse_smoother(ctx):
+    A = synth.poisson7(6)
+    F = silu.ILU(silu.Matrix(ctx, *A), "ilu0")
+    for kw in ({"coarse_smoother": 7}, {"coarse_smoother": silu.AMG_POLY_GS, "gs_terms": 0}):
+        with pytest.raises(silu.SiluError) as e:
+            F.amg_setup(coarse_size=20, **kw)
+        assert e.value.status == silu.ERR_INVALID_ARG
+    F.amg_setup(coarse_size=20, coarse_smoother=silu.AMG_POLY_GS, gs_terms=3)
+    assert F.amg_stats()["levels"] >= 2

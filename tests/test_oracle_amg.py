@@ -225,3 +225,47 @@ def test_three_level_cycle_with_l1_jacobi_matches_dense_recursion():
     x2 = x1 + P0 @ level1(P0.T @ (b - Ad @ x1))
     x3 = oracle.smooth(A, S, x2, b, 2, 2)[:, 0]
     assert relerr(H.vcycle(S, x0, b, 2, 2, nu=nu), x3) < 1e-12
+
+
+def test_three_level_cycle_with_polynomial_gs_matches_dense_recursion():
+    """The mixed V-cycle of Sec. 6.3: ILU on the finest level, polynomial
+    Gauss-Seidel below, x <- x + sum_{j<terms} (-D^{-1} L)^j D^{-1} (b - A x)
+    with dense matrix powers here."""
+    A = synth.cutcell7(9, 8, 7, seed=9)
+    n = len(A[0]) - 1
+    S = oracle.row_scale(oracle.ilu0(A))
+    H = oracle.AMG(A, theta=0.25, max_levels=3, coarse_size=1)
+    assert len(H.levels) == 3
+
+    def Pmat(L, nc):
+        P = np.zeros((L.n, nc))
+        pp, pc, pv = L.P
+        for i in range(L.n):
+            for q in range(pp[i], pp[i + 1]):
+                P[i, pc[q]] = pv[q]
+        return P
+
+    L0, L1, L2 = H.levels
+    P0, P1 = Pmat(L0, L1.n), Pmat(L1, L2.n)
+    A1, A2 = dense(L1.A, L1.n), dense(L2.A, L2.n)
+    Dinv = np.diag(1.0 / np.diag(A1))
+    G = -Dinv @ np.tril(A1, -1)
+    terms, nu = 3, 2
+    poly = sum(np.linalg.matrix_power(G, j) for j in range(terms)) @ Dinv
+
+    def level1(b1):
+        x = np.zeros(L1.n)
+        for _ in range(nu):
+            x = x + poly @ (b1 - A1 @ x)
+        x = x + P1 @ np.linalg.solve(A2, P1.T @ (b1 - A1 @ x))
+        for _ in range(nu):
+            x = x + poly @ (b1 - A1 @ x)
+        return x
+
+    Ad = dense(A, n)
+    b = synth.rhs(n, 1, seed=6)[:, 0]
+    x1 = oracle.smooth(A, S, np.zeros(n), b, 2, 2)[:, 0]
+    x2 = x1 + P0 @ level1(P0.T @ (b - Ad @ x1))
+    x3 = oracle.smooth(A, S, x2, b, 2, 2)[:, 0]
+    got = H.vcycle(S, np.zeros(n), b, 2, 2, nu=nu, coarse="gs", terms=terms)
+    assert relerr(got, x3) < 1e-12
