@@ -640,8 +640,9 @@ def amg_comparison(silu, ctx, torch, edge: int):
     sweeps (m = 3, 5, 10; the paper reports 20 SpMVs as sufficient at 11M rows
     and fewer as insufficient) against the same cycle smoothed by exact
     level-scheduled triangular solves (the comparison behind the paper's
-    GMRES + AMG gains), and the single-level 3+3-sweep smoother for
-    reference.  Also one V-cycle's time alone."""
+    GMRES + AMG gains), the single-level 3+3-sweep smoother for reference,
+    and the cycle with FP32 factors and sweeps on the finest level.  Also one
+    V-cycle's time alone."""
     import synth
     A = synth.cutcell7(edge, seed=1)
     n = len(A[0]) - 1
@@ -686,8 +687,25 @@ def amg_comparison(silu, ctx, torch, edge: int):
                 break  # a stalled configuration is reported once
         out[label] = {"seconds": round(sec, 4), "iterations": its, "relres": float(f"{rr:.3e}"),
                       "converged": status == silu.OK}
+    # the same cycle with FP32 factors and FP32 sweeps on the finest level (FP64 elsewhere)
+    del F
+    F32 = silu.ilu_setup(ctx, M, "ilu0", prec=silu.FP32)
+    F32.amg_setup(theta=0.25, max_levels=25, coarse_size=400, jacobi_sweeps=1)
+    F32.reserve(1, 30)
+    for m in (5, 10):
+        for rep in range(2):
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            status, its, rr = silu.fgmres_solve(F32, x, b, tol=1e-8, restart=30, maxit=600, sweeps_L=m, sweeps_U=m,
+                                                precond=silu.PRECOND_AMG)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+        out[f"amg_fp32_sweeps_{m}_{m}"] = {"seconds": round(sec, 4), "iterations": its, "relres": float(f"{rr:.3e}"),
+                                           "converged": status == silu.OK}
+    del F32
     best = min((v["seconds"], k) for k, v in out.items()
-               if k.startswith("amg_sweeps") and isinstance(v, dict) and v["converged"])
+               if k.startswith(("amg_sweeps", "amg_fp32")) and isinstance(v, dict) and v["converged"])
     out["fastest_amg_sweeps"] = best[1]
     out["speedup_amg_sweeps_vs_amg_direct"] = round(out["amg_direct"]["seconds"] / best[0], 2)
     return out
