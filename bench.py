@@ -378,6 +378,7 @@ def run_silu(args):
     amg = amg_comparison(silu, ctx, torch, args.amg_edge) if (args.amg_edge > 0 and rank == 0) else None
 
     p32 = poisson32(silu, ctx, torch) if rank == 0 else None
+    f32err = fp32_error(silu, ctx, torch) if rank == 0 else None
     study = sweep_study(silu, ctx, torch) if (args.study and rank == 0) else None
 
     cpu = None
@@ -418,6 +419,8 @@ def run_silu(args):
             line["amg"] = amg
         if p32:
             line["poisson32"] = p32
+        if f32err:
+            line["fp32_error"] = f32err
         if study:
             line["sweep_study"] = study
         if cpu:
@@ -711,6 +714,33 @@ def amg_comparison(silu, ctx, torch, edge: int):
     return out
 
 
+def fp32_error(silu, ctx, torch):
+    """FP32 factors and sweeps against FP64 ones on the 128^3 cut-cell matrix
+    (ILU(0), one right-hand side, seed 1): relative 2-norm difference of one
+    smoother application from zero (3+3 and 10+10 sweeps), and FGMRES(30) to
+    1e-8 with either (iterations, true relative residual)."""
+    import synth
+    A = synth.cutcell7(EDGE, seed=1)
+    n = len(A[0]) - 1
+    M = silu.Matrix(ctx, *A)
+    b = torch.from_numpy(synth.rhs(n, 1, seed=1)).cuda()
+    F64 = silu.ilu_setup(ctx, M, "ilu0", prec=silu.FP64)
+    F32 = silu.ilu_setup(ctx, M, "ilu0", prec=silu.FP32)
+    out = {"workload": "cutcell7-128^3 ILU(0), FP32 vs FP64 factors and sweeps"}
+    for m in (3, 10):
+        x64 = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+        x32 = torch.zeros_like(x64)
+        silu.ilu_smooth(F64, x64, b, m, m)
+        silu.ilu_smooth(F32, x32, b, m, m)
+        out[f"apply_{m}_{m}_relerr"] = float(f"{float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64)):.3e}")
+    for name, F in (("fgmres_fp64", F64), ("fgmres_fp32", F32)):
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st, its, rel = silu.fgmres_solve(F, x, b[:, 0].contiguous(), tol=1e-8, restart=30, maxit=5000,
+                                         sweeps_L=3, sweeps_U=3)
+        out[name] = {"iterations": its, "relres": float(f"{rel:.3e}"), "converged": st == silu.OK}
+    return out
+
+
 def poisson32(silu, ctx, torch):
     """7-point Poisson 32^3 (32,768 rows), ILU(0), 4 interleaved right-hand
     sides U[-1,1] (seed 0): one smoother application (5+5 sweeps) against
@@ -765,7 +795,9 @@ def sweep_study(silu, ctx, torch):
     nilpotence: ||T_s^p||_2 for p = 1..40 (power iteration, 30 steps per p)
     on a 24^3 cut-cell matrix (13,824 rows, the size of the paper's
     14,186-row PeleLM matrix of Fig. Up), upper factor of ILUT(tau, 30) for
-    tau in {1e-2, 1e-3, 1e-4} with row and with row/column scaling, and L_s."""
+    tau in {1e-2, 1e-3, 1e-4} with row and with row/column scaling, and L_s;
+    with the departure from normality (Eq. depB) of L, U and the scaled U
+    (Table dep)."""
     import numpy as np
     import synth
     out = {}
@@ -847,8 +879,10 @@ def sweep_study(silu, ctx, torch):
             F = silu.ilu_setup(ctx, MB, "ilut", tau, 30, scale=sc)
             nu = F.power_norms("U", P, iters, v0)
             below = [p + 1 for p in range(P) if nu[p] < 1.0]
+            dep = F.dep()
             rec = {"norm_Us_p": [float(f"{v:.4e}") for v in nu], "first_p_below_1": below[0] if below else None,
-                   "levels_U": F.stats()["levels_U"]}
+                   "levels_U": F.stats()["levels_U"], "dep_L": float(f"{dep['L']:.4e}"),
+                   "dep_U": float(f"{dep['U']:.4e}"), "dep_scaled_U": float(f"{dep['scaled']:.4e}")}
             if label == "row":
                 nl = F.power_norms("L", P, iters, v0)
                 rec["norm_Ls_p"] = [float(f"{v:.4e}") for v in nl]

@@ -293,6 +293,15 @@ silu_status silu_ilu_export_colscale(silu_ilu F, double* dcol, int32_t* ruiz_ste
  * T and of its transpose for the call; blocks.  Device context only.
  */
 silu_status silu_ilu_power_norms(silu_ilu F, int which, int pmax, int iters, const double* v0, double* out);
+/*
+ * Departure from normality (Eq. depB, Table dep) of the factors, computed on
+ * the host: dep(T) = sqrt(||T||_F^2 - sum |lambda_i|^2), which for a
+ * triangular T is the Frobenius norm of its off-diagonal part.  dep_L: the
+ * unit lower factor L; dep_U: U as factored; dep_scaled: the unit-diagonal
+ * upper factor the sweeps use (D^{-1} U, or D_r U D_c under
+ * SILU_SCALE_ROWCOL).  Any pointer may be NULL; host-only contexts work.
+ */
+silu_status silu_ilu_dep(silu_ilu F, double* dep_L, double* dep_U, double* dep_scaled);
 /* Entry counts of U with diagonal (for export buffer sizing). */
 silu_status silu_ilu_export_sizes(silu_ilu F, int64_t* nnz_L, int64_t* nnz_Ufull, int64_t* nnz_Us);
 

@@ -101,6 +101,7 @@ def load():
         "silu_ilu_export_sizes": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "silu_ilu_export_colscale": (i32, [vp, vp, ctypes.POINTER(ctypes.c_int32)]),
         "silu_ilu_power_norms": (i32, [vp, i32, i32, i32, vp, vp]),
+        "silu_ilu_dep": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "silu_amg_setup": (i32, [vp, vp]),
         "silu_amg_vcycle": (i32, [vp, vp, vp, i32, i32]),
         "silu_amg_stats": (i32, [vp, i32, ctypes.POINTER(i32), vp, vp, vp]),
@@ -147,7 +148,7 @@ def exported_symbols():
     return ["silu_version", "silu_ctx_create", "silu_ctx_destroy", "silu_last_error", "silu_mat_create",
             "silu_mat_destroy", "silu_mat_residual", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
-            "silu_ilu_export_colscale", "silu_ilu_power_norms", "silu_amg_setup", "silu_amg_vcycle",
+            "silu_ilu_export_colscale", "silu_ilu_power_norms", "silu_ilu_dep", "silu_amg_setup", "silu_amg_vcycle",
             "silu_amg_stats", "silu_amg_export_level", "silu_schur_setup", "silu_schur_smooth",
             "silu_schur_stats",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
@@ -349,6 +350,13 @@ class ILU:
         _check(self.ctx.handle, load().silu_ilu_export_colscale(self.handle, _ptr(dc), ctypes.byref(steps)),
                "silu_ilu_export_colscale")
         return dc[:self.n], steps.value
+
+    def dep(self):
+        """Departure from normality (Eq. depB): {"L": dep(L), "U": dep(U), "scaled": dep of the sweep factor}."""
+        a, b_, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(self.ctx.handle, load().silu_ilu_dep(self.handle, ctypes.byref(a), ctypes.byref(b_), ctypes.byref(c)),
+               "silu_ilu_dep")
+        return {"L": a.value, "U": b_.value, "scaled": c.value}
 
     def power_norms(self, which: str, pmax: int, iters: int, v0) -> np.ndarray:
         """Estimates of ||T^p||_2, p = 1..pmax, for T = L_s ("L") or the scaled strict upper factor ("U")."""

@@ -1275,6 +1275,23 @@ silu_status silu_ilu_export_colscale(silu_ilu F, double* dcol, int32_t* ruiz_ste
   return SILU_OK;
 }
 
+silu_status silu_ilu_dep(silu_ilu F, double* dep_L, double* dep_U, double* dep_scaled) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  // dep(T) of a triangular T (Eq. depB): its eigenvalues are its diagonal, so
+  // dep(T)^2 is the sum of the squares of the off-diagonal entries
+  auto offdiag = [](const Csr& T) {
+    double s = 0.0;
+    for (int64_t i = 0; i < T.n; ++i)
+      for (int64_t p = T.rp[i]; p < T.rp[i + 1]; ++p)
+        if (T.ci[p] != i) s += T.va[p] * T.va[p];
+    return std::sqrt(s);
+  };
+  if (dep_L) *dep_L = offdiag(F->F.L);
+  if (dep_U) *dep_U = offdiag(F->F.U);
+  if (dep_scaled) *dep_scaled = offdiag(F->Us);
+  return SILU_OK;
+}
+
 void silu_ilu_destroy(silu_ilu F) { delete F; }
 
 silu_status silu_ilu_set_lanes(silu_ilu F, int lanes_L, int lanes_U, int lanes_A) {

@@ -322,3 +322,22 @@ def test_amg_rejects_bad_coarse_smoother(ctx):
         assert e.value.status == silu.ERR_INVALID_ARG
     F.amg_setup(coarse_size=20, coarse_smoother=silu.AMG_POLY_GS, gs_terms=3)
     assert F.amg_stats()["levels"] >= 2
+
+
+@pytest.mark.parametrize("scale", ["row", "rowcol"])
+def test_dep_matches_oracle(ctx, scale):
+    """Departure from normality (Eq. depB) of L, U and the scaled upper
+    factor against the oracle's; for symmetric A under ILU(0) with row
+    scaling dep(L) = dep(D^{-1} U) (Table dep)."""
+    A = synth.cutcell7(10, 9, 8, seed=3)
+    sc = silu.SCALE_ROWCOL if scale == "rowcol" else silu.SCALE_ROW
+    F = silu.ILU(silu.Matrix(ctx, *A), "ilu0", scale=sc)
+    d = F.dep()
+    OF = oracle.ilu0(A)
+    assert abs(d["L"] - oracle.dep_triangular(OF.L, unit_diag=True)) <= 1e-14 * d["L"]
+    assert abs(d["U"] - oracle.dep_triangular(OF.U)) <= 1e-14 * d["U"]
+    Us = oracle.ruiz_rowcol(OF).Us if scale == "rowcol" else oracle.row_scale(OF).Us
+    assert abs(d["scaled"] - oracle.dep_triangular(Us, unit_diag=True)) <= 1e-14 * d["scaled"]
+    if scale == "row":
+        assert abs(d["L"] - d["scaled"]) <= 1e-13 * d["L"]
+        assert d["U"] > 10 * d["scaled"]
