@@ -153,3 +153,26 @@ def test_fgmres_amg_with_polynomial_gs_below(silu, ctx, terms):
     assert st == silu.OK and rel <= 1e-10, (st, its, rel)
     r = oracle.residual(A, host(x).reshape(n, 1), b.reshape(n, 1))
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10
+
+
+def test_degenerate_systems(silu, ctx):
+    """1 x 1 system: one V-cycle and one Schur smoother step are exact; an
+    empty system is a no-op."""
+    one = (np.array([0, 1], np.int64), np.array([0], np.int32), np.array([4.0]))
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *one), "ilu0")
+    F.amg_setup()
+    F.schur_setup(2, 1e-3, 5)
+    x = torch.zeros(1, dtype=torch.float64, device="cuda")
+    F.amg_vcycle(x, dev(np.array([2.0])), 3, 3)
+    assert host(x)[0] == 0.5
+    x.zero_()
+    F.schur_smooth(x, dev(np.array([2.0])), 3, 3)
+    assert host(x)[0] == 0.5
+    empty = (np.array([0], np.int64), np.zeros(0, np.int32), np.zeros(0))
+    E = silu.ilu_setup(ctx, silu.Matrix(ctx, *empty), "ilu0")
+    E.amg_setup()
+    E.schur_setup(2, 1e-3, 5)
+    z = torch.zeros(1, dtype=torch.float64, device="cuda")
+    E.amg_vcycle(z, z, 1, 1)
+    E.schur_smooth(z, z, 1, 1)
+    ctx.check()

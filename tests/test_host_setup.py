@@ -341,3 +341,18 @@ def test_dep_matches_oracle(ctx, scale):
     if scale == "row":
         assert abs(d["L"] - d["scaled"]) <= 1e-13 * d["L"]
         assert d["U"] > 10 * d["scaled"]
+
+
+def test_amg_and_schur_on_degenerate_systems(ctx):
+    """Empty and 1x1 systems: the AMG hierarchy is a single (directly solved)
+    level, the Schur partition has no interface."""
+    one = (np.array([0, 1], np.int64), np.array([0], np.int32), np.array([4.0]))
+    empty = (np.array([0], np.int64), np.zeros(0, np.int32), np.zeros(0))
+    for A in (one, empty):
+        F = silu.ILU(silu.Matrix(ctx, *A), "ilu0")
+        F.amg_setup()
+        st = F.amg_stats()
+        assert st["levels"] == 1 and st["rows"] == [len(A[0]) - 1]
+        F.schur_setup(4, 1e-3, 5)
+        sst = F.schur_stats()
+        assert sst["interface"] == 0 and sst["interior"] == len(A[0]) - 1
