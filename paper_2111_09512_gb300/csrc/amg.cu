@@ -186,6 +186,7 @@ void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_ze
 extern "C" {
 
 silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params) {
+  NvtxRange nvtx_("silu:silu_amg_setup");
   if (!F) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = F->ctx;
   silu_amg_params p = {0.25, 25, 400, 1, SILU_AMG_L1_JACOBI, 2};
@@ -231,6 +232,7 @@ silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params) {
 }
 
 silu_status silu_amg_vcycle(silu_ilu F, double* x, const double* b, int sweeps_L, int sweeps_U) {
+  NvtxRange nvtx_("silu:silu_amg_vcycle");
   if (!F || !x || !b || (sweeps_L < 0) != (sweeps_U < 0)) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = F->ctx;
   if (!F->amg) return silu::set_err(ctx, SILU_ERR_INVALID_ARG, "no AMG hierarchy (silu_amg_setup)");

@@ -800,6 +800,7 @@ const TuneCandidate kTune[] = {{2, 0, 0, 16}, {2, 0, 0, 8}, {2, 1, 1, 16}, {2, 1
 }  // namespace
 
 silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choice, double* ms_out) {
+  NvtxRange nvtx_("silu:silu_ilu_autotune");
   if (!F || sweeps_L < 0 || sweeps_U < 0) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = F->ctx;
   silu_status ds = device_ok(ctx);
@@ -978,6 +979,7 @@ silu_status silu_mat_create(silu_ctx ctx, int64_t n, int64_t nnz, const int64_t*
 void silu_mat_destroy(silu_mat A) { delete A; }
 
 silu_status silu_mat_residual(silu_mat A, double* r, const double* x, const double* b, int nrhs) {
+  NvtxRange nvtx_("silu:silu_mat_residual");
   if (!A || !r || !x || !b || nrhs < 1) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = A->ctx;
   silu_status ds = device_ok(ctx);
@@ -1005,6 +1007,7 @@ silu_status silu_mat_residual(silu_mat A, double* r, const double* x, const doub
 
 silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int fill, silu_scale scale,
                       silu_prec prec, silu_ilu* out) {
+  NvtxRange nvtx_("silu:ilu_setup");
   if (!ctx || !A || !out || A->ctx != ctx) return set_err(ctx, SILU_ERR_INVALID_ARG, "bad handle");
   *out = nullptr;
   if (kind < SILU_ILU0 || kind > SILU_SGS || scale < SILU_SCALE_NONE || scale > SILU_SCALE_ROWCOL ||
@@ -1040,6 +1043,7 @@ silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int 
 }
 
 silu_status ilu_refactor(silu_ilu F, const double* new_val) {
+  NvtxRange nvtx_("silu:ilu_refactor");
   if (!F || !new_val) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = F->ctx;
   if (F->kind == SILU_ILUT) return set_err(ctx, SILU_ERR_INVALID_ARG, "ILUT has no reusable symbolic phase");
@@ -1083,6 +1087,7 @@ silu_status silu_ilu_reserve(silu_ilu F, int nrhs, int restart) {
 }
 
 silu_status ilu_smooth(silu_ilu F, double* x, const double* b, int nrhs, int sweeps_L, int sweeps_U) {
+  NvtxRange nvtx_("silu:ilu_smooth");
   if (!F) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = F->ctx;
   if (!x || !b || nrhs < 1 || sweeps_L < 0 || sweeps_U < 0)
@@ -1104,6 +1109,7 @@ silu_status ilu_smooth(silu_ilu F, double* x, const double* b, int nrhs, int swe
 }
 
 silu_status direct_trisolve(silu_ilu F, double* x, const double* b, int nrhs) {
+  NvtxRange nvtx_("silu:direct_trisolve");
   if (!F) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = F->ctx;
   if (!x || !b || nrhs < 1) return set_err(ctx, SILU_ERR_INVALID_ARG, "direct_trisolve: bad argument");
@@ -1126,6 +1132,7 @@ silu_status direct_trisolve(silu_ilu F, double* x, const double* b, int nrhs) {
 
 silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int restart, int maxit, int sweeps_L,
                          int sweeps_U, int precond, int* iters_out, double* relres_out) {
+  NvtxRange nvtx_("silu:fgmres_solve");
   if (!F) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = F->ctx;
   if (iters_out) *iters_out = 0;

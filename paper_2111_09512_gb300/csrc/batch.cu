@@ -416,6 +416,7 @@ extern "C" {
 silu_status silu_batch_setup(silu_ctx ctx, int count, const int64_t* n, const int64_t* const* row_ptr,
                              const int32_t* const* col_idx, const double* const* val, silu_kind kind, double tau,
                              int fill, silu_scale scale, silu_prec prec, silu_batch* out) {
+  NvtxRange nvtx_("silu:silu_batch_setup");
   if (!ctx || !out || count < 1 || !n || !row_ptr || !col_idx || !val) return set_err(ctx, SILU_ERR_INVALID_ARG, "bad argument");
   *out = nullptr;
   if (kind < SILU_ILU0 || kind > SILU_SGS || scale < SILU_SCALE_NONE || scale > SILU_SCALE_ROWCOL ||
@@ -551,12 +552,14 @@ silu_status silu_batch_info(silu_batch B, int* count, int64_t* offsets, silu_ilu
 }
 
 silu_status silu_batch_smooth(silu_batch B, double* x, const double* b, int sweeps_L, int sweeps_U) {
+  NvtxRange nvtx_("silu:silu_batch_smooth");
   if (!B) return SILU_ERR_INVALID_ARG;
   return ilu_smooth(B->F, x, b, 1, sweeps_L, sweeps_U);
 }
 
 silu_status silu_batch_fgmres(silu_batch B, double* x, const double* b, double tol, int restart, int maxit,
                               int sweeps_L, int sweeps_U, int precond, int* iters, double* relres) {
+  NvtxRange nvtx_("silu:silu_batch_fgmres");
   if (!B) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = B->ctx;
   if (!x || !b || !(tol >= 0.0) || restart < 1 || maxit < 0 || sweeps_L < 0 || sweeps_U < 0 ||

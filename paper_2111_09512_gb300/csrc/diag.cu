@@ -42,6 +42,7 @@ void transpose(const Csr& T, Csr& Tt) {
 
 extern "C" silu_status silu_ilu_power_norms(silu_ilu F, int which, int pmax, int iters, const double* v0,
                                             double* out) {
+  NvtxRange nvtx_("silu:silu_ilu_power_norms");
   if (!F || !v0 || !out || (which != 0 && which != 1) || pmax < 1 || iters < 1) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = F->ctx;
   silu_status ds = silu::device_ok(ctx);

@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "amg_setup.h"
 #include "device.cuh"
 #include "host_factor.h"
@@ -198,6 +200,15 @@ struct silu_ilu_s {
   Workspace ws;
   std::unique_ptr<AmgState> amg;  // silu_amg_setup
   std::unique_ptr<SchurState> schur;  // silu_schur_setup
+};
+
+// An NVTX range around a public call, so timeline profilers show the library's
+// phases (no effect unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // The upper sweep factor is a unit-diagonal scaled copy (F->Us) rather than raw U.

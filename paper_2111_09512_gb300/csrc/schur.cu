@@ -122,6 +122,7 @@ void schur_apply(silu_ilu F, const double* r, double* z, int mL, int mU) {
 extern "C" {
 
 silu_status silu_schur_setup(silu_ilu F, int parts, double tau, int fill) {
+  NvtxRange nvtx_("silu:silu_schur_setup");
   if (!F || parts < 1 || !(tau >= 0.0) || fill < 0) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = F->ctx;
   const Csr& A = F->A->A;
@@ -193,6 +194,7 @@ silu_status silu_schur_setup(silu_ilu F, int parts, double tau, int fill) {
 }
 
 silu_status silu_schur_smooth(silu_ilu F, double* x, const double* b, int sweeps_L, int sweeps_U) {
+  NvtxRange nvtx_("silu:silu_schur_smooth");
   if (!F || !x || !b || sweeps_L < 0 || sweeps_U < 0) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = F->ctx;
   if (!F->schur) return silu::set_err(ctx, SILU_ERR_INVALID_ARG, "no Schur complement smoother (silu_schur_setup)");
