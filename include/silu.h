@@ -190,6 +190,17 @@ silu_status silu_mat_create(silu_ctx ctx, int64_t n, int64_t nnz, const int64_t*
 void silu_mat_destroy(silu_mat A);
 
 /*
+ * Launch shape of the staged kernel on A (the residual r = b - A x and the
+ * FGMRES products): lanes per row (0 = from the mean row length, else 1, 2
+ * or 4), rows per lane (0 = automatic, else 1, 2 or 4; more than one only
+ * with one lane per row), gather width (8 or 16 entries in flight per lane).
+ * Results change only by summation order across lanes.  Blocks (the new
+ * tiles are uploaded); captured FGMRES iterations of factor objects on A are
+ * rebuilt on their next use.
+ */
+silu_status silu_mat_set_shape(silu_mat A, int lanes, int passes, int chunk);
+
+/*
  * r = b - A x on the device (the residual of Eq. ILUsplit), ordered on A's
  * context stream.  r, x, b: device n x nrhs FP64 (row-major, right-hand sides
  * interleaved); r must not overlap x or b.  Device context only.
@@ -219,6 +230,18 @@ silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int 
  * the values): SILU_ERR_INVALID_ARG otherwise.  Blocks.
  */
 silu_status ilu_refactor(silu_ilu F, const double* new_val);
+
+/*
+ * Save the factors of F (L_s and U as factored, with kind, scaling,
+ * precision, tau and fill) to a binary file, and build a factor object for
+ * the matrix A from such a file without factoring again (checkpoint /
+ * resume of the setup; scaling, level sets and upload are redone).  The file
+ * is host-endian; silu_ilu_load checks its header against A (row count) and
+ * its CSR structure (L strictly lower, U with its diagonal first) and
+ * returns SILU_ERR_INVALID_ARG for a file that does not fit.  Both block.
+ */
+silu_status silu_ilu_save(silu_ilu F, const char* path);
+silu_status silu_ilu_load(silu_ctx ctx, silu_mat A, const char* path, silu_ilu* out);
 
 /*
  * One smoother application (Eq. ILUsplit with M = L D Utilde, Alg. ILUJac):

@@ -88,8 +88,11 @@ def load():
         "silu_mat_create": (i32, [vp, i64, i64, vp, vp, vp, pvp]),
         "silu_mat_destroy": (None, [vp]),
         "silu_mat_residual": (i32, [vp, vp, vp, vp, i32]),
+        "silu_mat_set_shape": (i32, [vp, i32, i32, i32]),
         "ilu_setup": (i32, [vp, vp, i32, dbl, i32, i32, i32, pvp]),
         "ilu_refactor": (i32, [vp, vp]),
+        "silu_ilu_save": (i32, [vp, ctypes.c_char_p]),
+        "silu_ilu_load": (i32, [vp, vp, ctypes.c_char_p, pvp]),
         "ilu_smooth": (i32, [vp, vp, vp, i32, i32, i32]),
         "direct_trisolve": (i32, [vp, vp, vp, i32]),
         "fgmres_solve": (i32, [vp, vp, vp, dbl, i32, i32, i32, i32, i32, ctypes.POINTER(i32),
@@ -146,7 +149,7 @@ def load():
 def exported_symbols():
     """Names the binding declares (all must be exported by libsilu.so)."""
     return ["silu_version", "silu_ctx_create", "silu_ctx_destroy", "silu_last_error", "silu_mat_create",
-            "silu_mat_destroy", "silu_mat_residual", "ilu_setup", "ilu_refactor", "ilu_smooth", "direct_trisolve", "fgmres_solve",
+            "silu_mat_destroy", "silu_mat_residual", "silu_mat_set_shape", "ilu_setup", "ilu_refactor", "silu_ilu_save", "silu_ilu_load", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
             "silu_ilu_export_colscale", "silu_ilu_power_norms", "silu_ilu_dep", "silu_amg_setup", "silu_amg_vcycle",
             "silu_amg_stats", "silu_amg_export_level", "silu_schur_setup", "silu_schur_smooth",
@@ -268,6 +271,11 @@ class Matrix:
         self.n = n
         self.nnz = int(rp[-1])
 
+    def set_shape(self, lanes: int = 0, passes: int = 0, chunk: int = 16):
+        """Launch shape of the staged kernel on this matrix (residual and FGMRES products)."""
+        _check(self.ctx.handle, load().silu_mat_set_shape(self.handle, int(lanes), int(passes), int(chunk)),
+               "silu_mat_set_shape")
+
     def residual(self, r, x, b):
         """r = b - A x on the device (torch tensors n x nrhs or length n, FP64)."""
         nrhs = 1 if b.dim() == 1 else int(b.shape[1])
@@ -302,6 +310,25 @@ class ILU:
         self.n = A.n
         self.prec = prec
         self.scale = scale
+
+    @classmethod
+    def load_file(cls, A: Matrix, path: str) -> "ILU":
+        """Factors of A read from a file written by save() (no factorisation)."""
+        h = ctypes.c_void_p()
+        _check(A.ctx.handle, load().silu_ilu_load(A.ctx.handle, A.handle, os.fsencode(path), ctypes.byref(h)),
+               "silu_ilu_load")
+        F = cls.__new__(cls)
+        F.handle = h.value
+        F.A = A
+        F.ctx = A.ctx
+        F.n = A.n
+        F.prec = None
+        F.scale = None
+        return F
+
+    def save(self, path: str):
+        """Write L_s and U with their kind, scaling and precision to a file."""
+        _check(self.ctx.handle, load().silu_ilu_save(self.handle, os.fsencode(path)), "silu_ilu_save")
 
     def close(self):
         if getattr(self, "handle", None) and not getattr(self, "_borrowed", False):

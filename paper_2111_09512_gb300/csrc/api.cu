@@ -1,5 +1,7 @@
 // C ABI of libsilu (declared in include/silu.h): handles, host setup and
 // the stream-ordered orchestration of the device kernels.
+#include <cstdio>
+
 #include "internal.h"
 
 using namespace silu;
@@ -578,7 +580,8 @@ void fgmres_inner(silu_ilu F, int j, int m, int mL, int mU, int precond, bool ca
 void fgmres_inner_graph(silu_ilu F, int j, int m, int mL, int mU, int precond) {
   silu_ctx ctx = F->ctx;
   for (KrylovGraph& kg : F->ws.kgraphs)
-    if (kg.j == j && kg.m == m && kg.mL == mL && kg.mU == mU && kg.precond == precond && kg.gen == F->config_gen) {
+    if (kg.j == j && kg.m == m && kg.mL == mL && kg.mU == mU && kg.precond == precond && kg.gen == F->config_gen &&
+        kg.agen == F->A->gen) {
       ctx->launches += kg.kernels;
       CK(cudaGraphLaunch(kg.exec, ctx->stream));
       return;
@@ -610,6 +613,7 @@ void fgmres_inner_graph(silu_ilu F, int j, int m, int mL, int mU, int precond) {
   kg.mU = mU;
   kg.precond = precond;
   kg.gen = F->config_gen;
+  kg.agen = F->A->gen;
   kg.kernels = ctx->launches - l0;
   ctx->launches = l0;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&kg.exec, graph, 0);
@@ -978,6 +982,37 @@ silu_status silu_mat_create(silu_ctx ctx, int64_t n, int64_t nnz, const int64_t*
 
 void silu_mat_destroy(silu_mat A) { delete A; }
 
+silu_status silu_mat_set_shape(silu_mat A, int lanes, int passes, int chunk) {
+  if (!A) return SILU_ERR_INVALID_ARG;
+  silu_ctx ctx = A->ctx;
+  if (!(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4) || !(passes == 0 || passes == 1 || passes == 2 ||
+                                                                   passes == 4) ||
+      !(chunk == 8 || chunk == 16) || (lanes != 1 && passes > 1))
+    return set_err(ctx, SILU_ERR_INVALID_ARG, "lanes 0/1/2/4, passes 0/1/2/4 (more than 1 only with one lane), chunk 8/16");
+  if (ctx->device < 0 || A->A.n == 0) return SILU_OK;
+  silu_status ds = device_ok(ctx);
+  if (ds != SILU_OK) return ds;
+  const int g = lanes ? lanes : silu::staged_lanes(A->A.rp.data(), A->A.n);
+  const int rl = g == 1 ? (passes ? passes : silu::staged_passes(A->A.rp.data(), A->A.n, g)) : 1;
+  std::vector<int> tl;
+  if (!silu::make_tiles(A->A.rp.data(), A->A.n, g, rl, tl))
+    return set_err(ctx, SILU_ERR_INVALID_ARG, "a row is too long for the staged kernel");
+  // new tiles in a new buffer (the old one may still be read by queued work)
+  DBuf nt;
+  cudaError_t e = upload(nt, tl.data(), tl.size(), ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_err(ctx, e, "upload of the tiles");
+  std::swap(A->tiles.p, nt.p);
+  std::swap(A->tiles.bytes, nt.bytes);
+  A->d.tiles = A->tiles.as<int4>();
+  A->d.ntiles = (int)(tl.size() / 4);
+  A->d.tile_lanes = g;
+  A->d.tile_passes = rl;
+  A->d.chunk = chunk;
+  A->gen++;
+  return SILU_OK;
+}
+
 silu_status silu_mat_residual(silu_mat A, double* r, const double* x, const double* b, int nrhs) {
   NvtxRange nvtx_("silu:silu_mat_residual");
   if (!A || !r || !x || !b || nrhs < 1) return SILU_ERR_INVALID_ARG;
@@ -1037,6 +1072,109 @@ silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int 
   } catch (const std::bad_alloc&) {
     delete F;
     return set_err(ctx, SILU_ERR_OOM, "out of host memory");
+  }
+  *out = F;
+  return SILU_OK;
+}
+
+namespace {
+
+// Factor file: a fixed header (magic "SILUFAC1", then kind, scale, prec,
+// fill as int32, tau as double, n, nnz(L_s), nnz(U) as int64) followed by
+// L_s and U as CSR (int64 row pointers, int32 columns, double values), all
+// little-endian as the host stores them.
+constexpr char kFacMagic[8] = {'S', 'I', 'L', 'U', 'F', 'A', 'C', '1'};
+
+bool write_csr(FILE* f, const Csr& T) {
+  return fwrite(T.rp.data(), sizeof(int64_t), T.rp.size(), f) == T.rp.size() &&
+         fwrite(T.ci.data(), sizeof(int32_t), T.ci.size(), f) == T.ci.size() &&
+         fwrite(T.va.data(), sizeof(double), T.va.size(), f) == T.va.size();
+}
+
+bool read_csr(FILE* f, int64_t n, int64_t nnz, Csr& T) {
+  T.n = n;
+  T.rp.resize(n + 1);
+  T.ci.resize(nnz);
+  T.va.resize(nnz);
+  if (fread(T.rp.data(), sizeof(int64_t), T.rp.size(), f) != T.rp.size() ||
+      fread(T.ci.data(), sizeof(int32_t), T.ci.size(), f) != T.ci.size() ||
+      fread(T.va.data(), sizeof(double), T.va.size(), f) != T.va.size())
+    return false;
+  if (T.rp[0] != 0 || T.rp[n] != nnz) return false;
+  for (int64_t i = 0; i < n; ++i)
+    if (T.rp[i + 1] < T.rp[i]) return false;
+  for (int32_t c : T.ci)
+    if (c < 0 || c >= n) return false;
+  for (double v : T.va)
+    if (!std::isfinite(v)) return false;
+  return true;
+}
+
+}  // namespace
+
+silu_status silu_ilu_save(silu_ilu F, const char* path) {
+  if (!F || !path) return SILU_ERR_INVALID_ARG;
+  FILE* f = fopen(path, "wb");
+  if (!f) return set_err(F->ctx, SILU_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  const int32_t hdr32[4] = {(int32_t)F->kind, (int32_t)F->scale, (int32_t)F->prec, (int32_t)F->fill};
+  const int64_t hdr64[3] = {F->F.L.n, F->F.L.nnz(), F->F.U.nnz()};
+  bool ok = fwrite(kFacMagic, 1, 8, f) == 8 && fwrite(hdr32, sizeof(int32_t), 4, f) == 4 &&
+            fwrite(&F->tau, sizeof(double), 1, f) == 1 && fwrite(hdr64, sizeof(int64_t), 3, f) == 3 &&
+            write_csr(f, F->F.L) && write_csr(f, F->F.U);
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) return set_err(F->ctx, SILU_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  return SILU_OK;
+}
+
+silu_status silu_ilu_load(silu_ctx ctx, silu_mat A, const char* path, silu_ilu* out) {
+  NvtxRange nvtx_("silu:silu_ilu_load");
+  if (!ctx || !A || !path || !out || A->ctx != ctx) return set_err(ctx, SILU_ERR_INVALID_ARG, "bad handle");
+  *out = nullptr;
+  FILE* f = fopen(path, "rb");
+  if (!f) return set_err(ctx, SILU_ERR_INVALID_ARG, std::string("cannot open ") + path);
+  silu_ilu F = nullptr;
+  silu_status st = SILU_OK;
+  try {
+    char magic[8];
+    int32_t hdr32[4];
+    double tau = 0.0;
+    int64_t hdr64[3];
+    if (fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kFacMagic, 8) != 0 || fread(hdr32, sizeof(int32_t), 4, f) != 4 ||
+        fread(&tau, sizeof(double), 1, f) != 1 || fread(hdr64, sizeof(int64_t), 3, f) != 3) {
+      st = set_err(ctx, SILU_ERR_INVALID_ARG, "not a factor file");
+    } else if (hdr64[0] != A->A.n || hdr64[1] < 0 || hdr64[2] < hdr64[0] || hdr32[0] < SILU_ILU0 ||
+               hdr32[0] > SILU_SGS || hdr32[1] < SILU_SCALE_NONE || hdr32[1] > SILU_SCALE_ROWCOL ||
+               hdr32[2] < SILU_FP64 || hdr32[2] > SILU_FP32) {
+      st = set_err(ctx, SILU_ERR_INVALID_ARG, "factor file does not fit the matrix");
+    } else {
+      F = new silu_ilu_s;
+      F->ctx = ctx;
+      F->A = A;
+      F->kind = (silu_kind)hdr32[0];
+      F->scale = (silu_scale)hdr32[1];
+      F->prec = (silu_prec)hdr32[2];
+      F->fill = hdr32[3];
+      F->tau = tau;
+      if (!read_csr(f, hdr64[0], hdr64[1], F->F.L) || !read_csr(f, hdr64[0], hdr64[2], F->F.U))
+        st = set_err(ctx, SILU_ERR_INVALID_ARG, "corrupt factor file");
+      for (int64_t i = 0; st == SILU_OK && i < F->F.L.n; ++i)  // L strictly lower, U with its diagonal first
+        for (int64_t p = F->F.L.rp[i]; p < F->F.L.rp[i + 1]; ++p)
+          if (F->F.L.ci[p] >= i) st = set_err(ctx, SILU_ERR_INVALID_ARG, "corrupt factor file (L)");
+      for (int64_t i = 0; st == SILU_OK && i < F->F.U.n; ++i) {
+        const int64_t b = F->F.U.rp[i], e = F->F.U.rp[i + 1];
+        if (e <= b || F->F.U.ci[b] != i) st = set_err(ctx, SILU_ERR_INVALID_ARG, "corrupt factor file (U)");
+        for (int64_t p = b + 1; st == SILU_OK && p < e; ++p)
+          if (F->F.U.ci[p] <= i) st = set_err(ctx, SILU_ERR_INVALID_ARG, "corrupt factor file (U)");
+      }
+      if (st == SILU_OK) st = finish_setup(F);
+    }
+  } catch (const std::bad_alloc&) {
+    st = set_err(ctx, SILU_ERR_OOM, "out of host memory");
+  }
+  fclose(f);
+  if (st != SILU_OK) {
+    delete F;
+    return st;
   }
   *out = F;
   return SILU_OK;

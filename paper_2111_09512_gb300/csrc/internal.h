@@ -82,6 +82,7 @@ struct silu_mat_s {
   silu::Csr A;
   DBuf rp, ci, va, tiles;
   DevCsr d;
+  int64_t gen = 0;  // bumped when the launch shape of d changes (captured graphs that use A go stale)
 };
 
 // A captured level-scheduled solve on the workspace vectors of one column block.
@@ -95,7 +96,8 @@ struct LevelGraph {
 // A captured FGMRES inner iteration (Arnoldi index j) on the Krylov workspace.
 struct KrylovGraph {
   int j = -1, m = 0, mL = 0, mU = 0, precond = 0;
-  int64_t gen = -1;  // launch configuration the graph was captured with
+  int64_t gen = -1;   // launch configuration the graph was captured with
+  int64_t agen = -1;  // and the matrix's
   cudaGraphExec_t exec = nullptr;
   int64_t kernels = 0;
 };

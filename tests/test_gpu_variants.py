@@ -218,3 +218,27 @@ def test_mat_residual_matches_oracle(silu, ctx, nrhs):
     r = torch.empty(n, nrhs, dtype=torch.float64, device="cuda")
     M.residual(r, dev(x), dev(b))
     assert percol(host(r), oracle.residual(A, x, b)) < FP64_TOL
+
+
+def test_matrix_launch_shapes(silu, ctx):
+    """silu_mat_set_shape: every launch shape of the staged kernel on A gives
+    the residual to FP64 parity, and captured FGMRES iterations on A are
+    rebuilt after a change (same iteration count, converged)."""
+    A = synth.hex27(19, 17, 15, seed=7)
+    n = len(A[0]) - 1
+    M = silu.Matrix(ctx, *A)
+    F = silu.ilu_setup(ctx, M, "ilu0")
+    x = synth.rhs(n, 1, seed=2)
+    b = synth.rhs(n, 1, seed=3)
+    want = oracle.residual(A, x, b)
+    bd = dev(b[:, 0].copy())
+    xs = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st0, its0, _ = silu.fgmres_solve(F, xs, bd, tol=1e-10, restart=30, maxit=500, sweeps_L=3, sweeps_U=3)
+    for lanes, passes, chunk in [(1, 1, 16), (1, 2, 8), (2, 1, 16), (4, 1, 8), (0, 0, 16)]:
+        M.set_shape(lanes, passes, chunk)
+        r = torch.empty(n, 1, dtype=torch.float64, device="cuda")
+        M.residual(r, dev(x), dev(b))
+        assert percol(host(r), want) < FP64_TOL, (lanes, passes, chunk)
+        xs.zero_()
+        st, its, rel = silu.fgmres_solve(F, xs, bd, tol=1e-10, restart=30, maxit=500, sweeps_L=3, sweeps_U=3)
+        assert st == silu.OK and rel <= 1e-10 and abs(its - its0) <= 1

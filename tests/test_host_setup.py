@@ -356,3 +356,37 @@ def test_amg_and_schur_on_degenerate_systems(ctx):
         F.schur_setup(4, 1e-3, 5)
         sst = F.schur_stats()
         assert sst["interface"] == 0 and sst["interior"] == len(A[0]) - 1
+
+
+@pytest.mark.parametrize("kind,tau,fill,scale", [("ilut", 1e-3, 6, "row"), ("iluk", 0.0, 1, "rowcol"),
+                                                 ("sgs", 0.0, 0, "row")])
+def test_factor_save_and_load(ctx, tmp_path, kind, tau, fill, scale):
+    """silu_ilu_save / silu_ilu_load: the loaded object has the saved factors,
+    scaling and level sets bit for bit, without factoring again; a file that
+    does not fit the matrix, or is corrupt, is refused."""
+    A = synth.cutcell7(9, 8, 7, seed=6)
+    M = silu.Matrix(ctx, *A)
+    sc = silu.SCALE_ROWCOL if scale == "rowcol" else silu.SCALE_ROW
+    F = silu.ILU(M, kind, tau, fill, scale=sc)
+    path = str(tmp_path / "f.silu")
+    F.save(path)
+    G = silu.ILU.load_file(M, path)
+    a, b = F.export(), G.export()
+    for key in a:
+        if isinstance(a[key], tuple):
+            for u, v in zip(a[key], b[key]):
+                assert np.array_equal(u, v), key
+        else:
+            assert np.array_equal(a[key], b[key]), key
+    assert F.stats() == G.stats()
+    other = silu.Matrix(ctx, *synth.cutcell7(5, 5, 5, seed=1))
+    with pytest.raises(silu.SiluError):
+        silu.ILU.load_file(other, path)
+    raw = bytearray(open(path, "rb").read())
+    raw[-200:] = b"\xff" * 200
+    bad = str(tmp_path / "bad.silu")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(silu.SiluError):
+        silu.ILU.load_file(M, bad)
+    with pytest.raises(silu.SiluError):
+        silu.ILU.load_file(M, str(tmp_path / "missing.silu"))
