@@ -242,3 +242,22 @@ def test_matrix_launch_shapes(silu, ctx):
         xs.zero_()
         st, its, rel = silu.fgmres_solve(F, xs, bd, tol=1e-10, restart=30, maxit=500, sweeps_L=3, sweeps_U=3)
         assert st == silu.OK and rel <= 1e-10 and abs(its - its0) <= 1
+
+
+def test_loaded_factors_smooth_like_the_originals(silu, ctx, tmp_path):
+    """Factors written by silu_ilu_save and read back by silu_ilu_load on a
+    device context give the same bits in the smoother and the direct solve."""
+    A = synth.cutcell7(31, 27, 23, seed=9)
+    n = len(A[0]) - 1
+    M = silu.Matrix(ctx, *A)
+    F = silu.ilu_setup(ctx, M, "ilut", 1e-3, 10, prec=silu.FP32)
+    path = str(tmp_path / "f.silu")
+    F.save(path)
+    G = silu.ILU.load_file(M, path)
+    b = dev(synth.rhs(n, 1, seed=4))
+    for fn in (lambda H, x: silu.ilu_smooth(H, x, b, 4, 4), lambda H, x: silu.direct_trisolve(H, x, b)):
+        x1 = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+        x2 = torch.zeros_like(x1)
+        fn(F, x1)
+        fn(G, x2)
+        assert torch.equal(x1, x2)
