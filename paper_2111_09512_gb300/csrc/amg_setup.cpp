@@ -18,19 +18,40 @@ namespace silu {
 
 namespace {
 
+// Host threads for row-parallel setup work (contiguous row ranges; results
+// never depend on the count).
+int setup_threads(int64_t work) {
+  if (work < (1 << 16)) return 1;
+  return (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+}
+
+// fn(r0, r1, t) on nt contiguous ranges of [0, n), in parallel.
+template <class Fn>
+void for_row_ranges(int64_t n, int nt, Fn fn) {
+  if (nt <= 1) {
+    fn(0, n, 0);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t) pool.emplace_back([&, t]() { fn(n * t / nt, n * (t + 1) / nt, t); });
+  for (std::thread& th : pool) th.join();
+}
+
 // s[p] = 1 when entry p of row i (column j != i) is a strong connection:
 // |a_ij| >= theta * max_{k != i} |a_ik| (rows without off-diagonals have none).
 void strength(const Csr& A, double theta, std::vector<char>& s) {
   s.assign(A.ci.size(), 0);
-  for (int64_t i = 0; i < A.n; ++i) {
-    double mx = 0.0;
-    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p)
-      if (A.ci[p] != i) mx = std::max(mx, std::fabs(A.va[p]));
-    if (mx == 0.0) continue;
-    const double cut = theta * mx;
-    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p)
-      if (A.ci[p] != i && std::fabs(A.va[p]) >= cut) s[p] = 1;
-  }
+  for_row_ranges(A.n, setup_threads(A.nnz()), [&](int64_t r0, int64_t r1, int) {
+    for (int64_t i = r0; i < r1; ++i) {
+      double mx = 0.0;
+      for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p)
+        if (A.ci[p] != i) mx = std::max(mx, std::fabs(A.va[p]));
+      if (mx == 0.0) continue;
+      const double cut = theta * mx;
+      for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p)
+        if (A.ci[p] != i && std::fabs(A.va[p]) >= cut) s[p] = 1;
+    }
+  });
 }
 
 // A set of indices in [0, n) with the smallest member found in a few word
@@ -138,43 +159,64 @@ void interpolation(const Csr& A, const std::vector<char>& s, const std::vector<i
   nc = 0;
   for (int64_t i = 0; i < n; ++i)
     if (cf[i]) cidx[i] = nc++;
+  struct Part {
+    std::vector<int64_t> len;
+    std::vector<int32_t> ci;
+    std::vector<double> va;
+  };
+  const int nt = setup_threads(A.nnz());
+  std::vector<Part> parts(nt);
+  for_row_ranges(n, nt, [&](int64_t r0, int64_t r1, int t) {
+    Part& out = parts[t];
+    out.len.assign((size_t)(r1 - r0), 0);
+    for (int64_t i = r0; i < r1; ++i) {
+      const size_t before = out.ci.size();
+      if (cf[i]) {
+        out.ci.push_back((int32_t)cidx[i]);
+        out.va.push_back(1.0);
+      } else {
+        double aii = 0.0, sneg = 0.0, spos = 0.0, cneg = 0.0, cpos = 0.0;
+        for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
+          const double a = A.va[p];
+          if (A.ci[p] == i) {
+            aii += a;
+            continue;
+          }
+          if (a < 0.0) sneg += a;
+          if (a > 0.0) spos += a;
+          if (s[p] && cf[A.ci[p]]) {
+            if (a < 0.0) cneg += a;
+            if (a > 0.0) cpos += a;
+          }
+        }
+        double d = aii;
+        if (cpos == 0.0) d += spos;
+        if (cneg == 0.0) d += sneg;
+        const double fneg = cneg != 0.0 ? sneg / cneg : 0.0;
+        const double fpos = cpos != 0.0 ? spos / cpos : 0.0;
+        for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
+          const int32_t j = A.ci[p];
+          if (j == i || !s[p] || !cf[j]) continue;
+          const double f = A.va[p] < 0.0 ? fneg : fpos;
+          out.ci.push_back((int32_t)cidx[j]);
+          out.va.push_back(-(f * A.va[p]) / d);
+        }
+      }
+      out.len[(size_t)(i - r0)] = (int64_t)(out.ci.size() - before);
+    }
+  });
   P.n = n;
   P.rp.assign(n + 1, 0);
   P.ci.clear();
   P.va.clear();
-  for (int64_t i = 0; i < n; ++i) {
-    if (cf[i]) {
-      P.ci.push_back((int32_t)cidx[i]);
-      P.va.push_back(1.0);
-    } else {
-      double aii = 0.0, sneg = 0.0, spos = 0.0, cneg = 0.0, cpos = 0.0;
-      for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
-        const double a = A.va[p];
-        if (A.ci[p] == i) {
-          aii += a;
-          continue;
-        }
-        if (a < 0.0) sneg += a;
-        if (a > 0.0) spos += a;
-        if (s[p] && cf[A.ci[p]]) {
-          if (a < 0.0) cneg += a;
-          if (a > 0.0) cpos += a;
-        }
-      }
-      double d = aii;
-      if (cpos == 0.0) d += spos;
-      if (cneg == 0.0) d += sneg;
-      const double fneg = cneg != 0.0 ? sneg / cneg : 0.0;
-      const double fpos = cpos != 0.0 ? spos / cpos : 0.0;
-      for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
-        const int32_t j = A.ci[p];
-        if (j == i || !s[p] || !cf[j]) continue;
-        const double f = A.va[p] < 0.0 ? fneg : fpos;
-        P.ci.push_back((int32_t)cidx[j]);
-        P.va.push_back(-(f * A.va[p]) / d);
-      }
+  int64_t i = 0;
+  for (Part& pt : parts) {
+    for (int64_t l : pt.len) {
+      P.rp[i + 1] = P.rp[i] + l;
+      ++i;
     }
-    P.rp[i + 1] = (int64_t)P.ci.size();
+    P.ci.insert(P.ci.end(), pt.ci.begin(), pt.ci.end());
+    P.va.insert(P.va.end(), pt.va.begin(), pt.va.end());
   }
 }
 
@@ -336,15 +378,20 @@ int amg_build(const Csr& A, double theta, int max_levels, int64_t coarse_size, A
   }
   for (AmgLevel& L : H.lev) {  // l1-Jacobi diagonal: 1 / sum_j |a_ij|
     L.l1inv.assign(L.A.n, 0.0);
-    for (int64_t i = 0; i < L.A.n; ++i) {
-      double d = 0.0;
-      for (int64_t p = L.A.rp[i]; p < L.A.rp[i + 1]; ++p) d += std::fabs(L.A.va[p]);
-      if (d == 0.0) {
+    std::vector<char> empty(setup_threads(L.A.nnz()), 0);
+    for_row_ranges(L.A.n, (int)empty.size(), [&](int64_t r0, int64_t r1, int t) {
+      for (int64_t i = r0; i < r1; ++i) {
+        double d = 0.0;
+        for (int64_t p = L.A.rp[i]; p < L.A.rp[i + 1]; ++p) d += std::fabs(L.A.va[p]);
+        if (d == 0.0) empty[t] = 1;
+        L.l1inv[i] = d != 0.0 ? 1.0 / d : 0.0;
+      }
+    });
+    for (char e : empty)
+      if (e) {
         msg = "AMG level with an empty row";
         return H_ZERO_PIVOT;
       }
-      L.l1inv[i] = 1.0 / d;
-    }
   }
   const Csr& Am = H.lev.back().A;
   if (Am.n > kAmgMaxCoarse) {
