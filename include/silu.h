@@ -156,6 +156,21 @@ silu_status silu_ctx_profile_read(silu_ctx ctx, int kclass, int64_t* launches, d
  * launched.
  */
 silu_status silu_ctx_set_overlap(silu_ctx ctx, int enable);
+/*
+ * L2 reuse of staged sweeps (bit flags, default 1; applies to launches and
+ * graph captures made after the call).  Bit 0: consecutive staged launches on the
+ * context alternate their direction (every other launch walks the row tiles
+ * last to first), so a launch starts on the rows the previous one touched
+ * last -- vector entries, and factor tiles when both sweep the same factor --
+ * while they are still in L2.  Bit 1: factor
+ * copies at normal L2 priority (else evict-first).  Bit 2: vector loads and
+ * stores at normal L2 priority (else evict-last).  Every row is still
+ * computed by one lane from the same tile, so results are the same bits for
+ * every setting.  flags outside [0, 7] -> SILU_ERR_INVALID_ARG.  No
+ * counterpart in the paper: it concerns only the order in which a sweep
+ * visits rows.
+ */
+silu_status silu_ctx_set_l2_reuse(silu_ctx ctx, int flags);
 /* Kernels launched on ctx since creation (all classes; always counted). */
 silu_status silu_ctx_launch_count(silu_ctx ctx, int64_t* launches);
 /*

@@ -122,6 +122,7 @@ def load():
         "silu_ilu_set_kernel": (i32, [vp, i32]),
         "silu_ilu_layout": (i32, [vp, vp, vp, vp]),
         "silu_ctx_set_overlap": (i32, [vp, i32]),
+        "silu_ctx_set_l2_reuse": (i32, [vp, i32]),
         "silu_ilu_tune_table": (i32, [vp, i32, vp, vp, vp]),
         "silu_smooth_noalloc": (i32, [i32, vp, i64] + [vp] * 12 + [i32, i32]),
         "silu_batch_setup": (i32, [vp, i32, vp, vp, vp, vp, i32, dbl, i32, i32, i32, pvp]),
@@ -156,6 +157,7 @@ def exported_symbols():
             "silu_schur_stats",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
             "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_layout", "silu_ilu_tune_table", "silu_ctx_set_overlap",
+            "silu_ctx_set_l2_reuse",
             "silu_smooth_noalloc",
             "silu_batch_setup", "silu_batch_info", "silu_batch_smooth", "silu_batch_fgmres", "silu_batch_destroy",
             "silu_ilu_autotune", "silu_server_create", "silu_server_submit", "silu_server_cancel",
@@ -210,6 +212,11 @@ class Context:
     def set_overlap(self, enable: bool):
         """Launch each staged sweep as a programmatic dependent of the kernel before it (default on)."""
         _check(self.handle, load().silu_ctx_set_overlap(self.handle, 1 if enable else 0), "silu_ctx_set_overlap")
+
+    def set_l2_reuse(self, flags: int):
+        """L2 reuse flags of staged sweeps: 1 alternate direction, 2 factor at normal priority, 4 vectors at
+        normal priority (results are the same bits for every setting)."""
+        _check(self.handle, load().silu_ctx_set_l2_reuse(self.handle, int(flags)), "silu_ctx_set_l2_reuse")
 
     def profile(self, enable: bool):
         """Start (clearing earlier records) or stop event timing of the library's launches."""

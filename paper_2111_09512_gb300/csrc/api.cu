@@ -734,6 +734,13 @@ silu_status silu_ctx_set_overlap(silu_ctx ctx, int enable) {
   return SILU_OK;
 }
 
+silu_status silu_ctx_set_l2_reuse(silu_ctx ctx, int flags) {
+  if (!ctx) return SILU_ERR_INVALID_ARG;
+  if (flags < 0 || flags > 7) return set_err(ctx, SILU_ERR_INVALID_ARG, "L2 reuse flags must be in [0, 7]");
+  ctx->env.l2 = flags;
+  return SILU_OK;
+}
+
 silu_status silu_ctx_profile_read(silu_ctx ctx, int kclass, int64_t* launches, double* total_ms) {
   if (!ctx || kclass < 0 || kclass >= SILU_K_NCLASS) return SILU_ERR_INVALID_ARG;
   int64_t cnt = 0;

@@ -108,6 +108,17 @@ bool make_sorted(const int64_t* rp, const int32_t* ci, const double* va, int64_t
 // entries.
 bool make_tiles(const int64_t* rp, int64_t n, int lanes, int passes, std::vector<int>& desc);
 
+// L2 flags of a staged sweep launch.  kFlagReverse: walk the tiles last to
+// first (set on every other staged launch of a context when LaunchEnv::l2
+// has it).
+// kFlagFactorNormal: factor copies at normal L2 priority (else evict-first).
+// kFlagVectorNormal: vector loads and stores at normal priority (else
+// evict-last).  None of them changes a result bit.
+constexpr int kFlagReverse = 1;
+constexpr int kFlagFactorNormal = 2;
+constexpr int kFlagVectorNormal = 4;
+constexpr int kL2Default = kFlagReverse;
+
 // Device-side state shared by launches on one context.
 struct LaunchEnv {
   int sms = 0;          // multiprocessors of the device
@@ -116,6 +127,10 @@ struct LaunchEnv {
                         // that nothing sets (self-test)
   bool overlap = true;  // staged sweeps launched as programmatic dependents of
                         // the kernel before them (prologue overlaps its tail)
+  int l2 = kL2Default;  // L2 reuse flags of staged sweeps (kFlag* above)
+  // staged launches made so far (host side): with alternating directions,
+  // odd launches walk the tiles backwards
+  mutable unsigned flips = 0;
 };
 
 #ifdef __CUDACC__

@@ -167,6 +167,12 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
   return p;
 }
 
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
 __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
@@ -368,7 +374,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     k_sweep_staged(int ntiles, const int4* __restrict__ tiles, const int* __restrict__ rp, const int* __restrict__ ci,
                    const MT* __restrict__ va, const int* __restrict__ perm, const VI* __restrict__ c,
                    const VI* __restrict__ in, VO* __restrict__ out, const double* __restrict__ dinv,
-                   double* __restrict__ x, int epi, int* __restrict__ err) {
+                   double* __restrict__ x, int epi, int flags, int* __restrict__ err) {
   using L = StageLayout<MT, RL, PERM>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kWarps][kWarpStages];
@@ -383,8 +389,13 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
   const int gw = blockIdx.x * kWarps + warp;  // this warp's first tile
   const int nw = gridDim.x * kWarps;          // tile stride
   unsigned char* ring = smem + (size_t)warp * kWarpStages * L::kBytes;
-  const uint64_t stream = policy_evict_first();
-  const uint64_t keep = policy_evict_last();
+  // flags: kFlagReverse walks the tiles last to first (a warp's k-th tile is
+  // ntiles - 1 - (gw + k nw)); kFlagFactorNormal / kFlagVectorNormal give the
+  // factor copies / the vector accesses the normal L2 priority instead of
+  // evict-first / evict-last
+  const bool rev = (flags & kFlagReverse) != 0;
+  const uint64_t stream = (flags & kFlagFactorNormal) ? policy_evict_normal() : policy_evict_first();
+  const uint64_t keep = (flags & kFlagVectorNormal) ? policy_evict_normal() : policy_evict_last();
   grid_launch_dependents();
   // the factor and its tiles are never written by a sweep: the first copies
   // may start before the kernel that produced c and in has finished
@@ -392,7 +403,8 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     for (int s = 0; s < kWarpStages; ++s) {
       const int t = gw + s * nw;
       if (t < ntiles)
-        issue_tile<MT, RL, PERM>(__ldg(tiles + t), ring + s * L::kBytes, &full[warp][s], rp, ci, va, perm, stream);
+        issue_tile<MT, RL, PERM>(__ldg(tiles + (rev ? ntiles - 1 - t : t)), ring + s * L::kBytes, &full[warp][s], rp,
+                                 ci, va, perm, stream);
     }
   grid_wait_prior();  // c, in, out and x below belong to the previous kernel until it completes
   int k = 0;
@@ -400,7 +412,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
     // the issuing lane fetches the descriptor of the tile it will issue next
     const int tn = t + kWarpStages * nw;
     int4 dn = make_int4(0, 0, 0, 0);
-    if (lane == 0 && tn < ntiles) dn = __ldg(tiles + tn);
+    if (lane == 0 && tn < ntiles) dn = __ldg(tiles + (rev ? ntiles - 1 - tn : tn));
     const int s = k % kWarpStages;
     const bool ok = mbar_wait_bounded(&full[warp][s], (uint32_t)(k / kWarpStages) & 1u);
     if (!__all_sync(0xffffffffu, ok)) {
@@ -483,13 +495,18 @@ cudaError_t staged_g(const DevCsr& T, const LaunchEnv& env, const void* c, const
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = env.overlap ? 1 : 0;
+  // consecutive launches alternate their direction, so each starts on the
+  // rows (vector entries, and factor tiles when the matrix is the same) that
+  // the previous one touched last, while they are still in L2
+  int flags = env.l2 & (kFlagFactorNormal | kFlagVectorNormal);
+  if ((env.l2 & kFlagReverse) && (env.flips++ & 1u)) flags |= kFlagReverse;
   if (PERM)
     return cudaLaunchKernelEx(&cfg, k_sweep_staged<MT, VI, VO, G, CH, RL, PERM>, nt, (const int4*)T.stiles,
                               (const int*)T.srp, (const int*)T.sci, (const MT*)T.sva, (const int*)T.perm,
-                              (const VI*)c, (const VI*)in, (VO*)out, dinv, x, epi, env.err);
+                              (const VI*)c, (const VI*)in, (VO*)out, dinv, x, epi, flags, env.err);
   return cudaLaunchKernelEx(&cfg, k_sweep_staged<MT, VI, VO, G, CH, RL, PERM>, nt, (const int4*)T.tiles,
                             (const int*)T.rp, (const int*)T.ci, (const MT*)T.va, (const int*)nullptr, (const VI*)c,
-                            (const VI*)in, (VO*)out, dinv, x, epi, env.err);
+                            (const VI*)in, (VO*)out, dinv, x, epi, flags, env.err);
 }
 
 template <class MT, class VI, class VO, int G, int RL, bool PERM>

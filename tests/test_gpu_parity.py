@@ -409,3 +409,49 @@ def test_profile_records_sweep_runs(silu):
     assert c.launch_count() - l0 == 3 * (1 + 3 + 4)
     assert prof["residual"][0] == 3 and prof["sweep_L"][0] == 9 and prof["sweep_U"][0] == 12
     assert all(prof[k][1] > 0 for k in ("residual", "sweep_L", "sweep_U"))
+
+
+def test_l2_reuse_settings_give_the_same_bits(silu):
+    """Alternating the direction of consecutive sweeps and the L2 priorities
+    of factor and vector accesses changes only which warp takes a row tile and
+    how long lines stay in L2: smoother (FP64 and FP32 factors, natural and
+    length-sorted layouts) and FGMRES results are the same bits for every
+    setting, and the FP64 smoother matches the oracle."""
+    A = synth.cutcell7(44, 40, 36, seed=12)
+    n = len(A[0]) - 1
+    b = synth.rhs(n, 1, seed=13)
+    x0 = synth.rhs(n, 1, seed=14)
+    OF = oracle.ilut(A, 1e-3, 10)
+    want = oracle.smooth(A, oracle.row_scale(OF), x0, b, 7, 6)
+    out = {}
+    for flags in (0, 1, 3, 5, 7):
+        c = silu.Context(0, torch.cuda.current_stream())
+        c.set_l2_reuse(flags)
+        got = []
+        for prec in (silu.FP64, silu.FP32):
+            F = silu.ilu_setup(c, silu.Matrix(c, *A), "ilut", 1e-3, 10, prec=prec)
+            for variant in (2, 3):
+                F.set_kernel(variant)
+                x = dev(x0.copy())
+                silu.ilu_smooth(F, x, dev(b), 7, 6)
+                silu.ilu_smooth(F, x, dev(b), 4, 3)
+                c.check()
+                got.append(host(x))
+            xf = torch.zeros(n, dtype=torch.float64, device="cuda")
+            st, its, _ = silu.fgmres_solve(F, xf, dev(b[:, 0].copy()), tol=1e-9, restart=20, maxit=400,
+                                           sweeps_L=3, sweeps_U=4, precond=silu.PRECOND_SWEEPS)
+            assert st == silu.OK
+            got.append((host(xf), its))
+        out[flags] = got
+        x = dev(x0.copy())
+        F = silu.ilu_setup(c, silu.Matrix(c, *A), "ilut", 1e-3, 10)
+        silu.ilu_smooth(F, x, dev(b), 7, 6)
+        assert relerr(host(x), want) < 1e-12
+    for flags in (1, 3, 5, 7):
+        for a, r in zip(out[flags], out[0]):
+            if isinstance(a, tuple):
+                assert np.array_equal(a[0], r[0]) and a[1] == r[1], flags
+            else:
+                assert np.array_equal(a, r), flags
+    with pytest.raises(silu.SiluError):
+        silu.Context(0, torch.cuda.current_stream()).set_l2_reuse(8)
