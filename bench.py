@@ -433,6 +433,12 @@ def run_silu(args):
                          "achieved": round(achieved, 2) if achieved else None, "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4) if achieved else None, "peak_kind": peak_kind,
                          "traffic": traffic, "launches": nL + nU,
+                         # consecutive sweeps reuse what L2 holds, so DRAM moves less than the algorithmic
+                         # bytes: the DRAM rate is the recorded per-launch traffic over the same mean duration
+                         "dram_achieved": round(traffic / ((msL + msU) * 1e-3 / (nL + nU)) / 1e9, 2)
+                         if (traffic and msL + msU > 0) else None,
+                         "dram_frac": round(traffic / ((msL + msU) * 1e-3 / (nL + nU)) / 1e9 / peak, 4)
+                         if (traffic and msL + msU > 0) else None,
                          "share_of_timed_kernels": round((msL + msU) / total_prof_ms, 4) if total_prof_ms else None},
             "kernel_ms": {k: [v[0], round(v[1], 4)] for k, v in prof.items() if v[0]},
             "e2e": {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": 2 * n * 8,
