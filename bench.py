@@ -503,12 +503,16 @@ def solve_comparison(silu, ctx, torch, edge: int):
     n = len(A[0]) - 1
     b_np = synth.rhs(n, 1, seed=2)
     t0 = time.perf_counter()
-    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0", prec=silu.FP32)
+    M = silu.Matrix(ctx, *A)
+    F = silu.ilu_setup(ctx, M, "ilu0", prec=silu.FP32)
     setup_s = time.perf_counter() - t0
+    # launch shape of the FP64 products with A (residual, FGMRES), timed on A; both paths below use it
+    a_shape, a_ms = M.autotune()
     st = F.stats()
     F.reserve(1, 30)
     out = {"workload": f"hex27-{edge}^3 ILU(0)", "rows": n, "nnz_A": len(A[1]), "tol": 1e-10, "restart": 30,
-           "setup_s": round(setup_s, 2)}
+           "setup_s": round(setup_s, 2), "a_shape": {"lanes": a_shape[0], "rows_per_lane": a_shape[1],
+                                                      "chunk": a_shape[2], "residual_ms": round(a_ms, 4)}}
     del A
     b = torch.from_numpy(b_np[:, 0].copy()).cuda()
     # FP32 smoother application rate (x != 0 after the first application, so the FP64 residual runs)
@@ -689,6 +693,7 @@ def amg_comparison(silu, ctx, torch, edge: int):
     A = synth.cutcell7(edge, seed=1)
     n = len(A[0]) - 1
     M = silu.Matrix(ctx, *A)
+    a_shape, _ = M.autotune()  # launch shape of the products with A, used by every path below
     F = silu.ilu_setup(ctx, M, "ilu0")
     t0 = time.perf_counter()
     F.amg_setup(theta=0.25, max_levels=25, coarse_size=400, jacobi_sweeps=1)
@@ -698,7 +703,8 @@ def amg_comparison(silu, ctx, torch, edge: int):
     out = {"workload": f"cutcell7-{edge}^3 ILU(0) FP64 + AMG", "rows": n, "nnz_A": len(A[1]),
            "amg_setup_s": round(setup_s, 2), "levels": st["levels"], "level_rows": st["rows"],
            "operator_complexity": round(sum(st["nnz_A"]) / st["nnz_A"][0], 3),
-           "ilu_levels": [st_f["levels_L"], st_f["levels_U"]], "tol": 1e-8, "restart": 30, "maxit": 600}
+           "ilu_levels": [st_f["levels_L"], st_f["levels_U"]], "tol": 1e-8, "restart": 30, "maxit": 600,
+           "a_shape": {"lanes": a_shape[0], "rows_per_lane": a_shape[1], "chunk": a_shape[2]}}
     b = torch.from_numpy(synth.rhs(n, 1, seed=1)[:, 0].copy()).cuda()
     F.reserve(1, 30)
     for label, sL, sU in (("vcycle_sweeps_10_10_ms", 10, 10), ("vcycle_direct_ms", -1, -1)):

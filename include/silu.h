@@ -214,6 +214,15 @@ void silu_mat_destroy(silu_mat A);
  * rebuilt on their next use.
  */
 silu_status silu_mat_set_shape(silu_mat A, int lanes, int passes, int chunk);
+/*
+ * Time r = b - A x (one right-hand side) for each launch shape of the staged
+ * kernel (lanes 1/2/4, rows per lane 1/2/4 with one lane, gather width 8/16,
+ * and the automatic choice), keep the fastest (as silu_mat_set_shape), and
+ * return it with its time per product.  Blocks.  Results change only by
+ * summation order across lanes.  Device context only; an empty matrix keeps
+ * the automatic shape and reports 0 ms.  Any output pointer may be NULL.
+ */
+silu_status silu_mat_autotune(silu_mat A, int* lanes, int* passes, int* chunk, double* ms);
 
 /*
  * r = b - A x on the device (the residual of Eq. ILUsplit), ordered on A's

@@ -123,6 +123,7 @@ def load():
         "silu_ilu_layout": (i32, [vp, vp, vp, vp]),
         "silu_ctx_set_overlap": (i32, [vp, i32]),
         "silu_ctx_set_l2_reuse": (i32, [vp, i32]),
+        "silu_mat_autotune": (i32, [vp, vp, vp, vp, vp]),
         "silu_ilu_tune_table": (i32, [vp, i32, vp, vp, vp]),
         "silu_smooth_noalloc": (i32, [i32, vp, i64] + [vp] * 12 + [i32, i32]),
         "silu_batch_setup": (i32, [vp, i32, vp, vp, vp, vp, i32, dbl, i32, i32, i32, pvp]),
@@ -150,7 +151,7 @@ def load():
 def exported_symbols():
     """Names the binding declares (all must be exported by libsilu.so)."""
     return ["silu_version", "silu_ctx_create", "silu_ctx_destroy", "silu_last_error", "silu_mat_create",
-            "silu_mat_destroy", "silu_mat_residual", "silu_mat_set_shape", "ilu_setup", "ilu_refactor", "silu_ilu_save", "silu_ilu_load", "ilu_smooth", "direct_trisolve", "fgmres_solve",
+            "silu_mat_destroy", "silu_mat_residual", "silu_mat_set_shape", "silu_mat_autotune", "ilu_setup", "ilu_refactor", "silu_ilu_save", "silu_ilu_load", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
             "silu_ilu_export_colscale", "silu_ilu_power_norms", "silu_ilu_dep", "silu_amg_setup", "silu_amg_vcycle",
             "silu_amg_stats", "silu_amg_export_level", "silu_schur_setup", "silu_schur_smooth",
@@ -282,6 +283,14 @@ class Matrix:
         """Launch shape of the staged kernel on this matrix (residual and FGMRES products)."""
         _check(self.ctx.handle, load().silu_mat_set_shape(self.handle, int(lanes), int(passes), int(chunk)),
                "silu_mat_set_shape")
+
+    def autotune(self):
+        """Time the launch shapes of the staged kernel on this matrix, keep the fastest;
+        ((lanes, passes, chunk), ms per product)."""
+        g, p, c, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+        _check(self.ctx.handle, load().silu_mat_autotune(self.handle, ctypes.byref(g), ctypes.byref(p),
+                                                         ctypes.byref(c), ctypes.byref(ms)), "silu_mat_autotune")
+        return (g.value, p.value, c.value), ms.value
 
     def residual(self, r, x, b):
         """r = b - A x on the device (torch tensors n x nrhs or length n, FP64)."""

@@ -1020,6 +1020,70 @@ silu_status silu_mat_set_shape(silu_mat A, int lanes, int passes, int chunk) {
   return SILU_OK;
 }
 
+silu_status silu_mat_autotune(silu_mat A, int* lanes, int* passes, int* chunk, double* ms_out) {
+  NvtxRange nvtx_("silu:silu_mat_autotune");
+  if (!A) return SILU_ERR_INVALID_ARG;
+  silu_ctx ctx = A->ctx;
+  silu_status ds = device_ok(ctx);
+  if (ds != SILU_OK) return ds;
+  const size_t n = (size_t)A->A.n;
+  // candidates: {lanes, passes, chunk}, the automatic choice first
+  static const int kShapes[][3] = {{0, 0, 16}, {0, 0, 8}, {1, 1, 16}, {1, 1, 8}, {1, 2, 16}, {1, 2, 8},
+                                   {1, 4, 16}, {1, 4, 8}, {2, 1, 16}, {2, 1, 8}, {4, 1, 16}, {4, 1, 8}};
+  int best = -1;
+  double best_ms = 1e300;
+  if (n > 0) {
+    cudaStream_t s = ctx->stream;
+    DBuf x, b, r;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    try {
+      CK(x.ensure(sizeof(double) * n));
+      CK(b.ensure(sizeof(double) * n));
+      CK(r.ensure(sizeof(double) * n));
+      CK(cudaMemsetAsync(x.p, 0, sizeof(double) * n, s));
+      CK(cudaMemsetAsync(b.p, 0, sizeof(double) * n, s));
+      CK(cudaEventCreate(&e0));
+      CK(cudaEventCreate(&e1));
+      for (int k = 0; k < (int)(sizeof(kShapes) / sizeof(kShapes[0])); ++k) {
+        // shapes a row does not fit are skipped
+        if (silu_mat_set_shape(A, kShapes[k][0], kShapes[k][1], kShapes[k][2]) != SILU_OK) continue;
+        silu_status st = silu_mat_residual(A, r.as<double>(), x.as<double>(), b.as<double>(), 1);
+        CK(cudaEventRecord(e0, s));
+        const int reps = 5;
+        for (int q = 0; q < reps && st == SILU_OK; ++q)
+          st = silu_mat_residual(A, r.as<double>(), x.as<double>(), b.as<double>(), 1);
+        if (st != SILU_OK) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return st;
+        }
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        if ((double)t / reps < best_ms) {
+          best_ms = (double)t / reps;
+          best = k;
+        }
+      }
+    } catch (const CudaFail& f) {
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      return cuda_err(ctx, f.e, f.what);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  if (best < 0) best = 0;
+  silu_status st = silu_mat_set_shape(A, kShapes[best][0], kShapes[best][1], kShapes[best][2]);
+  if (st != SILU_OK) return st;
+  if (lanes) *lanes = A->d.tile_lanes;
+  if (passes) *passes = A->d.tile_passes;
+  if (chunk) *chunk = A->d.chunk;
+  if (ms_out) *ms_out = best < 0 || n == 0 ? 0.0 : best_ms;
+  return silu_ctx_check(ctx);
+}
+
 silu_status silu_mat_residual(silu_mat A, double* r, const double* x, const double* b, int nrhs) {
   NvtxRange nvtx_("silu:silu_mat_residual");
   if (!A || !r || !x || !b || nrhs < 1) return SILU_ERR_INVALID_ARG;

@@ -244,6 +244,30 @@ def test_matrix_launch_shapes(silu, ctx):
         assert st == silu.OK and rel <= 1e-10 and abs(its - its0) <= 1
 
 
+def test_matrix_autotune_keeps_a_valid_fastest_shape(silu, ctx):
+    """silu_mat_autotune: the shape it keeps is one it timed, the residual
+    with it matches the oracle to FP64 parity, FGMRES on A still converges,
+    and an empty matrix keeps the automatic shape."""
+    for A in (synth.hex27(21, 18, 16, seed=8), synth.cutcell7(33, 29, 25, seed=8)):
+        n = len(A[0]) - 1
+        M = silu.Matrix(ctx, *A)
+        F = silu.ilu_setup(ctx, M, "ilu0")
+        (lanes, passes, chunk), ms = M.autotune()
+        assert lanes in (1, 2, 4) and passes in (1, 2, 4) and chunk in (8, 16) and ms > 0
+        assert lanes == 1 or passes == 1
+        x = synth.rhs(n, 1, seed=2)
+        b = synth.rhs(n, 1, seed=3)
+        r = torch.empty(n, 1, dtype=torch.float64, device="cuda")
+        M.residual(r, dev(x), dev(b))
+        assert percol(host(r), oracle.residual(A, x, b)) < FP64_TOL
+        xs = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st, its, rel = silu.fgmres_solve(F, xs, dev(b[:, 0].copy()), tol=1e-10, restart=30, maxit=800,
+                                         sweeps_L=3, sweeps_U=3)
+        assert st == silu.OK and rel <= 1e-10
+    E = silu.Matrix(ctx, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    assert E.autotune()[1] == 0.0
+
+
 def test_loaded_factors_smooth_like_the_originals(silu, ctx, tmp_path):
     """Factors written by silu_ilu_save and read back by silu_ilu_load on a
     device context give the same bits in the smoother and the direct solve."""
