@@ -1358,6 +1358,14 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
   int its = 0;
   double relres = 0.0;
   silu_status result = SILU_OK;
+  struct Events {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~Events() {
+      for (cudaEvent_t v : e)
+        if (v) cudaEventDestroy(v);
+    }
+    cudaEvent_t& operator[](int k) { return e[k]; }
+  } it_done;
   try {
     CK(ensure_vectors(F, 1));
     CK(ensure_krylov(F, m));
@@ -1375,6 +1383,8 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
     double* scal = W.scal.as<double>();
     double* hp = ctx->pinned;
     const int gA = lanes_of(F->lanesA, F->autoA);
+    CK(cudaEventCreateWithFlags(&it_done[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&it_done[1], cudaEventDisableTiming));
     // ||b||
     LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_dot_part(n, b, b, part[0], s));
     LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_norm_final(n, part[0], scal, s));
@@ -1405,17 +1415,29 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
       CK(cudaMemsetAsync(g, 0, sizeof(double) * (size_t)(m + 1), s));
       CK(cudaMemsetAsync(H, 0, sizeof(double) * (size_t)(m + 1) * (size_t)m, s));
       LAUNCH(F->ctx, SILU_K_KRYLOV, silu::launch_normalize(n, part[0], g, V, V, s));
-      int jend = 0;
-      for (int j = 0; j < m; ++j) {
+      // Inner iterations run one ahead of the host: iteration j + 1 is queued
+      // before the host reads |g_{j+1}| and h_{j+1,j} of iteration j (copied
+      // to their own pinned slot), so the device does not wait for the host's
+      // decision.  An iteration queued after the one that ends the cycle only
+      // writes column j + 1 of H, g_{j+1}, g_{j+2}, V_{j+2} and Z_{j+1}, none
+      // of which the update of x with the first j + 1 columns reads, and the
+      // next cycle rewrites them before reading them.
+      auto queue_inner = [&](int j) {
         if (F->ctx->profiling)
           fgmres_inner(F, j, m, sweeps_L, sweeps_U, precond, false);  // per-kernel events need eager launches
         else
           fgmres_inner_graph(F, j, m, sweeps_L, sweeps_U, precond);
-        CK(cudaMemcpyAsync(hp + 1, scal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        CK(cudaMemcpyAsync(hp + 4 + 2 * (j & 1), scal + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(it_done[j & 1], s));
+      };
+      int jend = 0;
+      queue_inner(0);
+      for (int j = 0; j < m; ++j) {
+        if (j + 1 < m && its + 2 <= maxit) queue_inner(j + 1);
+        CK(cudaEventSynchronize(it_done[j & 1]));
         ++its;
         jend = j + 1;
-        const double res = hp[1], hn = hp[2];
+        const double res = hp[4 + 2 * (j & 1)], hn = hp[5 + 2 * (j & 1)];
         if (!std::isfinite(res)) {
           result = SILU_WARN_DIVERGED;
           break;
