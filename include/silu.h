@@ -300,7 +300,11 @@ silu_status direct_trisolve(silu_ilu F, double* x, const double* b, int nrhs);
  * zero guess), SILU_PRECOND_DIRECT, SILU_PRECOND_NONE.  maxit bounds the
  * total inner iterations.  Blocks until done; writes the iteration count and
  * the true relative residual.  SILU_ERR_NOT_CONVERGED when maxit is reached
- * above tol (x holds the last iterate).
+ * above tol (x holds the last iterate).  Each inner iteration runs as a CUDA
+ * graph captured on its first use (per iteration index, restart, sweeps and
+ * preconditioner), and the device runs one inner iteration ahead of the
+ * host's stopping test; the iteration queued past the one that ends a cycle
+ * touches nothing the update of x reads, so results do not depend on it.
  */
 silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int restart, int maxit, int sweeps_L,
                          int sweeps_U, int precond, int* iters_out, double* relres_out);
