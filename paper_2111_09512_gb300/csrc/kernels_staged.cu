@@ -114,8 +114,14 @@ bool make_sorted(const int64_t* rp, const int32_t* ci, const double* va, int64_t
 namespace {
 
 constexpr int kWarpStages = 2;
-constexpr int kWarps = 20;
-constexpr int kStagedThreads = kWarps * 32;
+// Warps per CTA (one CTA per SM; shared memory holds one two-stage ring per
+// warp).  FP32 stages are smaller, so more warps fit beside them.
+constexpr int kWarpsF64 = 20;
+constexpr int kWarpsF32 = 24;
+template <class MT>
+__host__ __device__ constexpr int warps_of() {
+  return sizeof(MT) == 4 ? kWarpsF32 : kWarpsF64;
+}
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -370,12 +376,13 @@ __device__ __forceinline__ void rows_accumulate(const MT* sv, const int* sc, con
 }
 
 template <class MT, class VI, class VO, int G, int CH, int RL, bool PERM>
-__global__ void __launch_bounds__(kStagedThreads, 1)
+__global__ void __launch_bounds__(warps_of<MT>() * 32, 1)
     k_sweep_staged(int ntiles, const int4* __restrict__ tiles, const int* __restrict__ rp, const int* __restrict__ ci,
                    const MT* __restrict__ va, const int* __restrict__ perm, const VI* __restrict__ c,
                    const VI* __restrict__ in, VO* __restrict__ out, const double* __restrict__ dinv,
                    double* __restrict__ x, int epi, int flags, int* __restrict__ err) {
   using L = StageLayout<MT, RL, PERM>;
+  constexpr int kWarps = warps_of<MT>();
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kWarps][kWarpStages];
   const int tid = threadIdx.x;
@@ -472,7 +479,7 @@ __global__ void __launch_bounds__(kStagedThreads, 1)
 template <class MT, class VI, class VO, int G, int CH, int RL, bool PERM>
 cudaError_t staged_attr() {
   using L = StageLayout<MT, RL, PERM>;
-  const size_t smem = (size_t)kWarps * kWarpStages * L::kBytes;
+  const size_t smem = (size_t)warps_of<MT>() * kWarpStages * L::kBytes;
   return cudaFuncSetAttribute(k_sweep_staged<MT, VI, VO, G, CH, RL, PERM>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
@@ -481,13 +488,14 @@ template <class MT, class VI, class VO, int G, int CH, int RL, bool PERM>
 cudaError_t staged_g(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
                      const double* dinv, double* x, int epi, cudaStream_t s) {
   using L = StageLayout<MT, RL, PERM>;
+  constexpr int kWarps = warps_of<MT>();
   const size_t smem = (size_t)kWarps * kWarpStages * L::kBytes;
   const int nt = PERM ? T.nstiles : T.ntiles;
   if (nt == 0) return cudaSuccess;
   const int want = (nt + kWarps - 1) / kWarps;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(want < env.sms ? want : env.sms));
-  cfg.blockDim = dim3(kStagedThreads);
+  cfg.blockDim = dim3(kWarps * 32);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
