@@ -269,6 +269,40 @@ def test_fgmres_matches_oracle(silu, ctx):
         assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10
 
 
+def test_fgmres_stopping_edges(silu, ctx):
+    """The device runs one inner iteration ahead of the host's stopping test:
+    stopping on maxit inside a cycle, on maxit at a restart and on an exact
+    (happy-breakdown) iteration must still return the iterate of exactly the
+    iterations counted -- the oracle's FGMRES after the same number of
+    iterations -- and a queued extra iteration must leave no trace."""
+    A = synth.cutcell7(17, 15, 13, seed=21)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+    _, S = oracle_scaled(A, "ilu0", 0.0, 0)
+    b = synth.rhs(n, 1, seed=22)[:, 0]
+    for maxit in (0, 1, 2, 7, 10, 11):
+        xo, sto, itso, relo = oracle.fgmres(A, S, b, tol=1e-14, restart=10, maxit=maxit, mL=3, mU=3, precond=0)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st, its, rel = silu.fgmres_solve(F, x, dev(b), tol=1e-14, restart=10, maxit=maxit, sweeps_L=3, sweeps_U=3)
+        assert st == silu.ERR_NOT_CONVERGED and sto == oracle.NOT_CONVERGED
+        assert its == itso == maxit
+        if maxit:
+            assert relerr(host(x), xo) < 1e-9, maxit
+            assert abs(rel - relo) <= 1e-9 * relo
+        else:
+            assert not host(x).any()
+    # diagonal system: ILU(0) is exact, the first iteration ends the solve with h_{1,0} = 0
+    d = 1.0 + np.arange(64, dtype=np.float64)
+    D = (np.arange(65, dtype=np.int64), np.arange(64, dtype=np.int32), d)
+    FD = silu.ilu_setup(ctx, silu.Matrix(ctx, *D), "ilu0")
+    bd = synth.rhs(64, 1, seed=23)[:, 0]
+    for _ in range(2):  # the second solve reuses the captured iterations and whatever the first left behind
+        x = torch.zeros(64, dtype=torch.float64, device="cuda")
+        st, its, rel = silu.fgmres_solve(FD, x, dev(bd), tol=1e-12, restart=10, maxit=50, sweeps_L=1, sweeps_U=1)
+        assert st == silu.OK and its == 1 and rel <= 1e-12
+        assert relerr(host(x), bd / d) < 1e-14
+
+
 def test_fgmres_fp32_smoother_reaches_fp64_tolerance(silu, ctx):
     A = synth.hex27(24, 22, 20, seed=12)
     n = len(A[0]) - 1
