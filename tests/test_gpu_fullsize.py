@@ -103,3 +103,37 @@ def test_cutcell224_gmres_amg_full_size():
         assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-8
         its[precond] = k
     assert abs(its[silu.PRECOND_AMG] - its[silu.PRECOND_AMG_DIRECT]) <= 2, its
+
+
+def test_hex27_256_fp32_application_error_vs_fp64_oracle():
+    """The 27-point 256^3 workload at full size: the host ILU(0) patterns
+    equal the oracle's bit for bit, and one FP32 smoother application (3+3
+    FP32 sweeps on FP32 factors, from zero, in the launch shape the benchmark
+    uses) differs from the oracle's all-FP64 application by FP32 rounding
+    only; the relative error is printed and bounded."""
+    import paper_2111_09512_gb300 as silu
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    silu.build()
+    A = synth.hex27(256, seed=2)
+    n = len(A[0]) - 1
+    ctx = silu.Context(0, torch.cuda.current_stream())
+    M = silu.Matrix(ctx, *A)
+    F = silu.ilu_setup(ctx, M, "ilu0", prec=silu.FP32)
+    M.autotune()
+    OF = oracle.ilu0(A)
+    ex = F.export()
+    for part in ("L", "U"):
+        assert np.array_equal(ex[part][0], getattr(OF, part)[0]) and np.array_equal(ex[part][1], getattr(OF, part)[1])
+    del ex
+    S = oracle.row_scale(OF)
+    del OF
+    b = synth.rhs(n, 1, seed=2)
+    want = oracle.smooth(A, S, np.zeros((n, 1)), b, 3, 3)
+    del S
+    x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
+    silu.ilu_smooth(F, x, torch.from_numpy(b).cuda(), 3, 3)
+    torch.cuda.synchronize()
+    err = relerr(x.cpu().numpy(), want)
+    print(f"256^3 27-point FP32 3+3 application, relative 2-norm error vs the FP64 oracle: {err:.3e}")
+    assert err < 1e-5
