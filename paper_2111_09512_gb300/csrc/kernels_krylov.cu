@@ -47,38 +47,87 @@ __device__ double sum_parts(const double* __restrict__ part, int nparts) {
   return block_sum(v);
 }
 
-__global__ void __launch_bounds__(KB) k_dot_part(int n, const double* __restrict__ a, const double* __restrict__ b,
-                                                 double* __restrict__ part) {
+// The streaming loops below visit a thread's elements i0, i0 + S, i0 + 2S, ...
+// (S = the grid's thread count) in that order, as a plain grid-stride loop
+// would, but load two of them before using either: twice the bytes in
+// flight per thread, the same accumulation order, the same bits.  Indices are
+// unsigned 32-bit (n < 2^31, so i + 2S cannot wrap), which keeps each kernel
+// within 32 registers: all 1024 blocks of the largest grid are resident at
+// once (eight per SM) and none waits for a second wave.
+__global__ void __launch_bounds__(KB, 8) k_dot_part(int n, const double* __restrict__ a, const double* __restrict__ b,
+                                                    double* __restrict__ part) {
+  const unsigned N = (unsigned)n, S = gridDim.x * KB;
+  unsigned i = blockIdx.x * KB + threadIdx.x;
   double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB)
-    acc += a[i] * b[i];
+  for (; i + S < N; i += 2 * S) {
+    const double a0 = a[i], a1 = a[i + S];
+    const double b0 = b[i], b1 = b[i + S];
+    acc += a0 * b0;
+    acc += a1 * b1;
+  }
+  for (; i < N; i += S) acc += a[i] * b[i];
   const double s = block_sum(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(KB) k_mgs_step(int n, const double* __restrict__ part_in, int nparts,
-                                                 double* __restrict__ hout, double* __restrict__ w,
-                                                 const double* __restrict__ vi, const double* __restrict__ vnext,
-                                                 double* __restrict__ part_out) {
+__global__ void __launch_bounds__(KB, 8) k_mgs_step(int n, const double* __restrict__ part_in, int nparts,
+                                                    double* __restrict__ hout, double* __restrict__ w,
+                                                    const double* __restrict__ vi, const double* __restrict__ vnext,
+                                                    double* __restrict__ part_out) {
   const double h = sum_parts(part_in, nparts);
   if (blockIdx.x == 0 && threadIdx.x == 0 && hout) *hout = h;
+  const unsigned N = (unsigned)n, S = gridDim.x * KB;
+  unsigned i = blockIdx.x * KB + threadIdx.x;
   double acc = 0.0;
-  for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB) {
-    const double wn = w[i] - h * vi[i];
-    w[i] = wn;
-    acc += wn * (vnext ? vnext[i] : wn);
+  if (vnext) {
+    for (; i + S < N; i += 2 * S) {
+      const double w0 = w[i], w1 = w[i + S];
+      const double v0 = vi[i], v1 = vi[i + S];
+      const double u0 = vnext[i], u1 = vnext[i + S];
+      const double n0 = w0 - h * v0, n1 = w1 - h * v1;
+      w[i] = n0;
+      w[i + S] = n1;
+      acc += n0 * u0;
+      acc += n1 * u1;
+    }
+    for (; i < N; i += S) {
+      const double wn = w[i] - h * vi[i];
+      w[i] = wn;
+      acc += wn * vnext[i];
+    }
+  } else {  // last step: the partial sums of ||w||^2 for the normalisation
+    for (; i + S < N; i += 2 * S) {
+      const double w0 = w[i], w1 = w[i + S];
+      const double v0 = vi[i], v1 = vi[i + S];
+      const double n0 = w0 - h * v0, n1 = w1 - h * v1;
+      w[i] = n0;
+      w[i + S] = n1;
+      acc += n0 * n0;
+      acc += n1 * n1;
+    }
+    for (; i < N; i += S) {
+      const double wn = w[i] - h * vi[i];
+      w[i] = wn;
+      acc += wn * wn;
+    }
   }
   const double s = block_sum(acc);
   if (threadIdx.x == 0) part_out[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(KB) k_normalize(int n, const double* __restrict__ part_in, int nparts,
-                                                  double* __restrict__ hout, const double* w, double* vout) {
+__global__ void __launch_bounds__(KB, 8) k_normalize(int n, const double* __restrict__ part_in, int nparts,
+                                                     double* __restrict__ hout, const double* w, double* vout) {
   const double h = sqrt(sum_parts(part_in, nparts));
   if (blockIdx.x == 0 && threadIdx.x == 0 && hout) *hout = h;
   if (h == 0.0) return;
-  for (long long i = (long long)blockIdx.x * KB + threadIdx.x; i < n; i += (long long)gridDim.x * KB)
-    vout[i] = w[i] / h;
+  const unsigned N = (unsigned)n, S = gridDim.x * KB;
+  unsigned i = blockIdx.x * KB + threadIdx.x;
+  for (; i + S < N; i += 2 * S) {  // w may be vout: each element is read, then written, by one thread
+    const double w0 = w[i], w1 = w[i + S];
+    vout[i] = w0 / h;
+    vout[i + S] = w1 / h;
+  }
+  for (; i < N; i += S) vout[i] = w[i] / h;
 }
 
 // Minimal-residual step: alpha = sum(part_num) / sum(part_den) (0 when the

@@ -207,7 +207,8 @@ __global__ void k_scale(int n, int R, int ldx, const VI* __restrict__ in, const 
                         VO* __restrict__ out) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n * R) return;
-  const int row = (int)(t / R), r = (int)(t % R);
+  // one right-hand side (the common case) needs no 64-bit division
+  const int row = R == 1 ? (int)t : (int)(t / R), r = R == 1 ? 0 : (int)(t % R);
   const size_t o = (size_t)row * (size_t)ldx + r;
   const double v = (double)in[o];
   out[o] = (VO)(dinv ? dinv[row] * v : v);
@@ -218,7 +219,7 @@ __global__ void k_addx(int n, int R, int ldx, const VI* __restrict__ in, const d
                        double* __restrict__ x, int accumulate) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)n * R) return;
-  const int row = (int)(t / R), r = (int)(t % R);
+  const int row = R == 1 ? (int)t : (int)(t / R), r = R == 1 ? 0 : (int)(t % R);
   const size_t o = (size_t)row * (size_t)ldx + r;
   double v = (double)in[o];
   if (dinv) v = dinv[row] * v;
