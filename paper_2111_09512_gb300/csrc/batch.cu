@@ -62,13 +62,23 @@ __device__ double system_sum(const double* __restrict__ part, const int* __restr
   return out;
 }
 
+// The chunk loops below visit a thread's rows d.y + t, d.y + t + KB, ... in
+// that order, two loaded before either is used (the same accumulation order
+// as one at a time, the same bits); eight blocks fit on an SM.
+
 // part[c] = sum over chunk c of a_i * b_i
-__global__ void __launch_bounds__(KB) k_bdot(int nch, const int4* __restrict__ ch, const double* __restrict__ a,
-                                             const double* __restrict__ b, double* __restrict__ part) {
+__global__ void __launch_bounds__(KB, 8) k_bdot(int nch, const int4* __restrict__ ch, const double* __restrict__ a,
+                                                const double* __restrict__ b, double* __restrict__ part) {
   for (int c = blockIdx.x; c < nch; c += gridDim.x) {
     const int4 d = ch[c];
     double acc = 0.0;
-    for (int i = d.y + threadIdx.x; i < d.z; i += KB) acc += a[i] * b[i];
+    int i = d.y + threadIdx.x;
+    for (; i + KB < d.z; i += 2 * KB) {
+      const double a0 = a[i], a1 = a[i + KB], b0 = b[i], b1 = b[i + KB];
+      acc += a0 * b0;
+      acc += a1 * b1;
+    }
+    for (; i < d.z; i += KB) acc += a[i] * b[i];
     const double s = block_sum(acc);
     if (threadIdx.x == 0) part[c] = s;
   }
@@ -77,7 +87,7 @@ __global__ void __launch_bounds__(KB) k_bdot(int nch, const int4* __restrict__ c
 // MGS step i of Arnoldi column j for every active system:
 //   h = <w, v_i>_s (from part_in);  H_s[i][j] = h;  w -= h v_i;
 //   part_out = chunk partials of <w, v_next> (or |w|^2 when v_next is null).
-__global__ void __launch_bounds__(KB) k_bmgs(int nch, const int4* __restrict__ ch, const int* __restrict__ sys_chunk0,
+__global__ void __launch_bounds__(KB, 8) k_bmgs(int nch, const int4* __restrict__ ch, const int* __restrict__ sys_chunk0,
                                              const double* __restrict__ part_in, double* __restrict__ H, int m,
                                              int i, int j, double* __restrict__ w, const double* __restrict__ vi,
                                              const double* __restrict__ vnext, double* __restrict__ part_out,
@@ -92,7 +102,27 @@ __global__ void __launch_bounds__(KB) k_bmgs(int nch, const int4* __restrict__ c
     const double h = system_sum(part_in, sys_chunk0, s);
     if (threadIdx.x == 0 && c == sys_chunk0[s]) H[((size_t)s * (m + 1) + i) * m + j] = h;
     double acc = 0.0;
-    for (int r = d.y + threadIdx.x; r < d.z; r += KB) {
+    int r = d.y + threadIdx.x;
+    if (vnext) {
+      for (; r + KB < d.z; r += 2 * KB) {
+        const double w0 = w[r], w1 = w[r + KB], v0 = vi[r], v1 = vi[r + KB], u0 = vnext[r], u1 = vnext[r + KB];
+        const double n0 = w0 - h * v0, n1 = w1 - h * v1;
+        w[r] = n0;
+        w[r + KB] = n1;
+        acc += n0 * u0;
+        acc += n1 * u1;
+      }
+    } else {
+      for (; r + KB < d.z; r += 2 * KB) {
+        const double w0 = w[r], w1 = w[r + KB], v0 = vi[r], v1 = vi[r + KB];
+        const double n0 = w0 - h * v0, n1 = w1 - h * v1;
+        w[r] = n0;
+        w[r + KB] = n1;
+        acc += n0 * n0;
+        acc += n1 * n1;
+      }
+    }
+    for (; r < d.z; r += KB) {
       const double wn = w[r] - h * vi[r];
       w[r] = wn;
       acc += wn * (vnext ? vnext[r] : wn);
@@ -103,7 +133,7 @@ __global__ void __launch_bounds__(KB) k_bmgs(int nch, const int4* __restrict__ c
 }
 
 // h = sqrt(<w, w>_s); H_s[j+1][j] = h; v_{j+1} = w / h (active systems, h != 0)
-__global__ void __launch_bounds__(KB) k_bnormalize(int nch, const int4* __restrict__ ch,
+__global__ void __launch_bounds__(KB, 8) k_bnormalize(int nch, const int4* __restrict__ ch,
                                                    const int* __restrict__ sys_chunk0,
                                                    const double* __restrict__ part_in, double* __restrict__ H, int m,
                                                    int j, const double* __restrict__ w, double* __restrict__ vout,
@@ -115,7 +145,13 @@ __global__ void __launch_bounds__(KB) k_bnormalize(int nch, const int4* __restri
     const double h = sqrt(system_sum(part_in, sys_chunk0, s));
     if (threadIdx.x == 0 && c == sys_chunk0[s]) H[((size_t)s * (m + 1) + j + 1) * m + j] = h;
     if (h == 0.0) continue;
-    for (int r = d.y + threadIdx.x; r < d.z; r += KB) vout[r] = w[r] / h;
+    int r = d.y + threadIdx.x;
+    for (; r + KB < d.z; r += 2 * KB) {
+      const double w0 = w[r], w1 = w[r + KB];
+      vout[r] = w0 / h;
+      vout[r + KB] = w1 / h;
+    }
+    for (; r < d.z; r += KB) vout[r] = w[r] / h;
   }
 }
 
@@ -284,7 +320,7 @@ namespace {
 
 int grid_for(silu_batch B) {
   const int want = B->nch;
-  const int cap = 4 * (B->ctx->env.sms > 0 ? B->ctx->env.sms : 1);
+  const int cap = 8 * (B->ctx->env.sms > 0 ? B->ctx->env.sms : 1);
   return want < cap ? (want > 0 ? want : 1) : cap;
 }
 
