@@ -10,8 +10,32 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <thread>
 
 namespace silu {
+
+namespace {
+
+// Host threads for row-parallel setup work on `work` stored entries: none
+// below a million (thread start-up would dominate), at most 16.
+int host_threads(int64_t work) {
+  if (work < ((int64_t)1 << 20)) return 1;
+  return (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+}
+
+// fn(r0, r1, t) on nt contiguous ranges of rows [0, n), in parallel.
+template <class Fn>
+void row_ranges(int64_t n, int nt, Fn fn) {
+  if (nt <= 1) {
+    fn((int64_t)0, n, 0);
+    return;
+  }
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t) pool.emplace_back([&, t]() { fn(n * t / nt, n * (t + 1) / nt, t); });
+  for (std::thread& th : pool) th.join();
+}
+
+}  // namespace
 
 int csr_canonical(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* va, Csr& out,
                   std::string& msg) {
@@ -27,47 +51,91 @@ int csr_canonical(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, 
     msg = "row_ptr must start at 0 and end at nnz";
     return H_BADARG;
   }
-  out.n = n;
-  out.rp.assign(n + 1, 0);
-  out.ci.clear();
-  out.va.clear();
-  out.ci.reserve(nnz);
-  out.va.reserve(nnz);
-  std::vector<std::pair<int32_t, double>> row;
-  for (int64_t i = 0; i < n; ++i) {
-    if (rp[i + 1] < rp[i]) {
+  // row pointers first: every row's entries must lie inside [0, nnz) before
+  // any is read
+  for (int64_t i = 0; i < n; ++i)
+    if (rp[i + 1] < rp[i] || rp[i + 1] > nnz) {
       msg = "row_ptr is not monotone at row " + std::to_string(i);
       return H_BADARG;
     }
+  // Rows are checked, sorted (stably) and their duplicates summed
+  // independently, in two passes over contiguous row ranges on host threads:
+  // the first checks and counts each row's distinct columns, the second writes
+  // the rows in place at their final offsets.  The first bad row of the lowest
+  // range that has one is the first bad row of the matrix.
+  const int nt = host_threads(nnz);
+  std::vector<int64_t> bad(nt, -1);
+  std::vector<std::string> why(nt);
+  out.n = n;
+  out.rp.assign(n + 1, 0);
+  auto sorted_row = [&](int64_t i, std::vector<std::pair<int32_t, double>>& row) {
     row.clear();
-    bool sorted = true;
-    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-      if (ci[p] < 0 || ci[p] >= n) {
-        msg = "column index out of range in row " + std::to_string(i);
-        return H_BADARG;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) row.emplace_back(ci[p], va[p]);
+    std::stable_sort(row.begin(), row.end(),
+                     [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+                       return x.first < y.first;
+                     });
+  };
+  row_ranges(n, nt, [&](int64_t r0, int64_t r1, int t) {
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t i = r0; i < r1; ++i) {
+      bool sorted = true;
+      for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        if (ci[p] < 0 || ci[p] >= n) {
+          bad[t] = i;
+          why[t] = "column index out of range in row ";
+          return;
+        }
+        if (!std::isfinite(va[p])) {
+          bad[t] = i;
+          why[t] = "non-finite value in row ";
+          return;
+        }
+        if (p > rp[i] && ci[p] <= ci[p - 1]) sorted = false;
       }
-      if (!std::isfinite(va[p])) {
-        msg = "non-finite value in row " + std::to_string(i);
-        return H_BADARG;
+      int64_t distinct = rp[i + 1] - rp[i];
+      if (!sorted) {
+        sorted_row(i, row);
+        distinct = 0;
+        for (size_t q = 0; q < row.size(); ++q)
+          if (q == 0 || row[q].first != row[q - 1].first) ++distinct;
       }
-      if (!row.empty() && ci[p] <= row.back().first) sorted = false;
-      row.emplace_back(ci[p], va[p]);
+      out.rp[i + 1] = distinct;
     }
-    if (!sorted)
-      std::stable_sort(row.begin(), row.end(),
-                       [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
-                         return a.first < b.first;
-                       });
-    for (size_t t = 0; t < row.size(); ++t) {
-      if (!out.ci.empty() && (int64_t)out.ci.size() > out.rp[i] && out.ci.back() == row[t].first) {
-        out.va.back() += row[t].second;
-      } else {
-        out.ci.push_back(row[t].first);
-        out.va.push_back(row[t].second);
+  });
+  for (int t = 0; t < nt; ++t)
+    if (bad[t] >= 0) {
+      msg = why[t] + std::to_string(bad[t]);
+      return H_BADARG;
+    }
+  for (int64_t i = 0; i < n; ++i) out.rp[i + 1] += out.rp[i];
+  out.ci.resize((size_t)out.rp[n]);
+  out.va.resize((size_t)out.rp[n]);
+  row_ranges(n, nt, [&](int64_t r0, int64_t r1, int) {
+    std::vector<std::pair<int32_t, double>> row;
+    for (int64_t i = r0; i < r1; ++i) {
+      int64_t o = out.rp[i];
+      if (out.rp[i + 1] - o == rp[i + 1] - rp[i]) {  // sorted, no duplicates: copied as is
+        std::copy(ci + rp[i], ci + rp[i + 1], out.ci.begin() + o);
+        std::copy(va + rp[i], va + rp[i + 1], out.va.begin() + o);
+        bool in_order = true;
+        for (int64_t p = rp[i] + 1; p < rp[i + 1]; ++p) in_order = in_order && ci[p] > ci[p - 1];
+        if (in_order) continue;
+      }
+      // duplicates or unsorted: stable sort, then sum equal columns in order
+      sorted_row(i, row);
+      o = out.rp[i] - 1;
+      for (size_t q = 0; q < row.size(); ++q) {
+        if (q > 0 && row[q].first == row[q - 1].first) {
+          out.va[(size_t)o] += row[q].second;
+        } else {
+          ++o;
+          out.ci[(size_t)o] = row[q].first;
+          out.va[(size_t)o] = row[q].second;
+        }
       }
     }
-    out.rp[i + 1] = (int64_t)out.ci.size();
-  }
+  });
   return H_OK;
 }
 
@@ -80,39 +148,102 @@ int64_t find_col(const std::vector<int32_t>& ci, int64_t b, int64_t e, int32_t c
   return it - ci.begin();
 }
 
+// One row of the numeric incomplete LU on pattern P, IKJ order: for each
+// k < i of P(i) in ascending order, l_ik = a_ik / u_kk, then a_ij -= l_ik u_kj
+// for the j > k of row k that are in P(i).  slot[] is -1 everywhere on entry
+// and on return.  Returns H_OK, or H_ZERO_PIVOT for a structurally zero,
+// zero or non-finite pivot.
+int numeric_row(const Csr& A, const std::vector<int64_t>& prp, const std::vector<int32_t>& pci, int64_t i,
+                std::vector<double>& lu, std::vector<int64_t>& dpos, int32_t* slot) {
+  const int64_t b = prp[i], e = prp[i + 1];
+  for (int64_t p = b; p < e; ++p) slot[pci[p]] = (int32_t)p;
+  for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) lu[slot[A.ci[p]]] = A.va[p];
+  const int64_t di = slot[i];
+  if (di < 0) {
+    for (int64_t p = b; p < e; ++p) slot[pci[p]] = -1;
+    return H_ZERO_PIVOT;
+  }
+  dpos[i] = di;
+  for (int64_t p = b; p < di; ++p) {
+    const int32_t k = pci[p];
+    lu[p] = lu[p] / lu[dpos[k]];
+    const double lik = lu[p];
+    for (int64_t q = dpos[k] + 1; q < prp[k + 1]; ++q) {
+      const int64_t t = slot[pci[q]];
+      if (t >= 0) lu[t] = lu[t] - lik * lu[q];
+    }
+  }
+  for (int64_t p = b; p < e; ++p) slot[pci[p]] = -1;
+  const double piv = lu[di];
+  return (piv == 0.0 || !std::isfinite(piv)) ? H_ZERO_PIVOT : H_OK;
+}
+
 // Numeric incomplete LU on a fixed pattern P (which contains the pattern of
-// A), IKJ order: for each row i and each k < i of P(i) in ascending order,
-// l_ik = a_ik / u_kk, then a_ij -= l_ik * u_kj for the j > k of row k that
-// are in P(i).  lu receives the values on P.
+// A), row by row as numeric_row; lu receives the values on P.
+//
+// Row i reads only rows k < i of P(i), so the rows of one level of P's lower
+// part (level(i) = 1 + the largest level of those k) are independent: large
+// systems run level after level, the rows of a large level split over host
+// threads (each with its own slot array).  Every row does the same
+// arithmetic in the same order as in a row-by-row pass, so the factors are
+// the same bits.  A failure reruns the row-by-row pass, which reports the
+// first failing row.
 int numeric_on_pattern(const Csr& A, const std::vector<int64_t>& prp, const std::vector<int32_t>& pci,
                        std::vector<double>& lu, std::vector<int64_t>& dpos, std::string& msg) {
   const int64_t n = A.n;
   lu.assign(pci.size(), 0.0);
   dpos.assign(n, -1);
-  std::vector<int64_t> slot(n, -1);
-  for (int64_t i = 0; i < n; ++i) {
-    const int64_t b = prp[i], e = prp[i + 1];
-    for (int64_t p = b; p < e; ++p) slot[pci[p]] = p;
-    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) lu[slot[A.ci[p]]] = A.va[p];
-    dpos[i] = slot[i];
-    if (dpos[i] < 0) {
-      for (int64_t p = b; p < e; ++p) slot[pci[p]] = -1;
-      msg = "structurally zero pivot in row " + std::to_string(i);
-      return H_ZERO_PIVOT;
+  const int64_t nnz = prp[n];
+  int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+  // per-thread slot arrays of n int32: at most about 1 GB in all
+  nt = (int)std::min<int64_t>(nt, std::max<int64_t>(1, ((int64_t)1 << 30) / (4 * std::max<int64_t>(n, 1))));
+  if (n > 0 && nnz >= ((int64_t)1 << 20) && nt > 1) {
+    std::vector<int32_t> lev(n, 0);
+    int32_t nlev = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      int32_t l = 0;
+      for (int64_t p = prp[i]; p < prp[i + 1] && pci[p] < i; ++p) l = std::max(l, lev[pci[p]] + 1);
+      lev[i] = l;
+      nlev = std::max(nlev, l + 1);
     }
-    for (int64_t p = b; p < dpos[i]; ++p) {
-      const int32_t k = pci[p];
-      lu[p] = lu[p] / lu[dpos[k]];
-      const double lik = lu[p];
-      for (int64_t q = dpos[k] + 1; q < prp[k + 1]; ++q) {
-        const int64_t s = slot[pci[q]];
-        if (s >= 0) lu[s] = lu[s] - lik * lu[q];
+    std::vector<int64_t> lptr(nlev + 1, 0);
+    for (int64_t i = 0; i < n; ++i) lptr[lev[i] + 1]++;
+    for (int32_t l = 0; l < nlev; ++l) lptr[l + 1] += lptr[l];
+    std::vector<int64_t> rows(n), fill(lptr.begin(), lptr.end() - 1);
+    for (int64_t i = 0; i < n; ++i) rows[fill[lev[i]]++] = i;  // ascending within a level
+    std::vector<std::vector<int32_t>> slots(nt, std::vector<int32_t>(n, -1));
+    std::vector<char> bad(nt, 0);
+    bool failed = false;
+    for (int32_t l = 0; l < nlev && !failed; ++l) {
+      const int64_t r0 = lptr[l], r1 = lptr[l + 1];
+      int64_t work = 0;  // entries of the level's rows: a proxy for its updates
+      for (int64_t r = r0; r < r1; ++r) work += prp[rows[r] + 1] - prp[rows[r]];
+      const int use = work >= (1 << 14) ? nt : 1;
+      auto run = [&](int t) {
+        const int64_t q0 = r0 + (r1 - r0) * t / use, q1 = r0 + (r1 - r0) * (t + 1) / use;
+        for (int64_t r = q0; r < q1; ++r)
+          if (numeric_row(A, prp, pci, rows[r], lu, dpos, slots[t].data()) != H_OK) {
+            bad[t] = 1;
+            return;
+          }
+      };
+      if (use == 1) {
+        run(0);
+      } else {
+        std::vector<std::thread> pool;
+        for (int t = 0; t < use; ++t) pool.emplace_back(run, t);
+        for (std::thread& th : pool) th.join();
       }
+      for (char c : bad) failed = failed || c;
     }
-    for (int64_t p = b; p < e; ++p) slot[pci[p]] = -1;
-    const double piv = lu[dpos[i]];
-    if (piv == 0.0 || !std::isfinite(piv)) {
-      msg = "zero or non-finite pivot in row " + std::to_string(i);
+    if (!failed) return H_OK;
+    lu.assign(pci.size(), 0.0);
+    dpos.assign(n, -1);
+  }
+  std::vector<int32_t> slot(n, -1);
+  for (int64_t i = 0; i < n; ++i) {
+    if (numeric_row(A, prp, pci, i, lu, dpos, slot.data()) != H_OK) {
+      msg = (dpos[i] < 0 ? "structurally zero pivot in row " : "zero or non-finite pivot in row ") + std::to_string(i);
       return H_ZERO_PIVOT;
     }
   }
@@ -125,22 +256,22 @@ void split_lu(int64_t n, const std::vector<int64_t>& prp, const std::vector<int3
   F.L.n = F.U.n = n;
   F.L.rp.assign(n + 1, 0);
   F.U.rp.assign(n + 1, 0);
-  F.L.ci.clear();
-  F.L.va.clear();
-  F.U.ci.clear();
-  F.U.va.clear();
   for (int64_t i = 0; i < n; ++i) {
-    for (int64_t p = prp[i]; p < dpos[i]; ++p) {
-      F.L.ci.push_back(pci[p]);
-      F.L.va.push_back(lu[p]);
-    }
-    for (int64_t p = dpos[i]; p < prp[i + 1]; ++p) {
-      F.U.ci.push_back(pci[p]);
-      F.U.va.push_back(lu[p]);
-    }
-    F.L.rp[i + 1] = (int64_t)F.L.ci.size();
-    F.U.rp[i + 1] = (int64_t)F.U.ci.size();
+    F.L.rp[i + 1] = F.L.rp[i] + (dpos[i] - prp[i]);
+    F.U.rp[i + 1] = F.U.rp[i] + (prp[i + 1] - dpos[i]);
   }
+  F.L.ci.resize((size_t)F.L.rp[n]);
+  F.L.va.resize((size_t)F.L.rp[n]);
+  F.U.ci.resize((size_t)F.U.rp[n]);
+  F.U.va.resize((size_t)F.U.rp[n]);
+  row_ranges(n, host_threads(prp[n]), [&](int64_t r0, int64_t r1, int) {
+    for (int64_t i = r0; i < r1; ++i) {
+      std::copy(pci.begin() + prp[i], pci.begin() + dpos[i], F.L.ci.begin() + F.L.rp[i]);
+      std::copy(lu.begin() + prp[i], lu.begin() + dpos[i], F.L.va.begin() + F.L.rp[i]);
+      std::copy(pci.begin() + dpos[i], pci.begin() + prp[i + 1], F.U.ci.begin() + F.U.rp[i]);
+      std::copy(lu.begin() + dpos[i], lu.begin() + prp[i + 1], F.U.va.begin() + F.U.rp[i]);
+    }
+  });
 }
 
 }  // namespace
@@ -413,11 +544,6 @@ int row_scale(const Csr& U, Csr& Us, std::vector<double>& dinv, std::string& msg
   const int64_t n = U.n;
   Us.n = n;
   Us.rp.assign(n + 1, 0);
-  Us.ci.clear();
-  Us.va.clear();
-  Us.ci.reserve(U.ci.size() - std::min<size_t>(U.ci.size(), (size_t)n));
-  Us.va.reserve(U.ci.size() - std::min<size_t>(U.ci.size(), (size_t)n));
-  dinv.assign(n, 0.0);
   for (int64_t i = 0; i < n; ++i) {
     const int64_t b = U.rp[i], e = U.rp[i + 1];
     if (e <= b || U.ci[b] != i) {
@@ -429,13 +555,24 @@ int row_scale(const Csr& U, Csr& Us, std::vector<double>& dinv, std::string& msg
       msg = "zero pivot in row scaling";
       return H_ZERO_PIVOT;
     }
-    dinv[i] = 1.0 / d;
-    for (int64_t p = b + 1; p < e; ++p) {
-      Us.ci.push_back(U.ci[p]);
-      Us.va.push_back(U.va[p] / d);
-    }
-    Us.rp[i + 1] = (int64_t)Us.ci.size();
+    Us.rp[i + 1] = Us.rp[i] + (e - b - 1);
   }
+  Us.ci.resize((size_t)Us.rp[n]);
+  Us.va.resize((size_t)Us.rp[n]);
+  dinv.assign(n, 0.0);
+  // rows are independent: u_ij / u_ii and 1 / u_ii on host threads
+  row_ranges(n, host_threads(U.rp[n]), [&](int64_t r0, int64_t r1, int) {
+    for (int64_t i = r0; i < r1; ++i) {
+      const int64_t b = U.rp[i], e = U.rp[i + 1];
+      const double d = U.va[b];
+      dinv[i] = 1.0 / d;
+      int64_t o = Us.rp[i];
+      for (int64_t p = b + 1; p < e; ++p, ++o) {
+        Us.ci[o] = U.ci[p];
+        Us.va[o] = U.va[p] / d;
+      }
+    }
+  });
   return H_OK;
 }
 

@@ -390,3 +390,36 @@ def test_factor_save_and_load(ctx, tmp_path, kind, tau, fill, scale):
         silu.ILU.load_file(M, bad)
     with pytest.raises(silu.SiluError):
         silu.ILU.load_file(M, str(tmp_path / "missing.silu"))
+
+
+def test_threaded_setup_matches_oracle_bit_for_bit(ctx):
+    """Above a million entries the host setup runs on threads: row ranges for
+    the canonical CSR, the L/U split and the row scaling, level sets of the
+    lower pattern for the numeric ILU(0).  Every row keeps its arithmetic and
+    order, so the factors equal the oracle's bit for bit.  The same matrix
+    given with every row's columns shuffled and every value split into two
+    halves (exact in binary) canonicalises to the same factors."""
+    A = synth.hex27(52, 50, 48, seed=9)
+    assert len(A[1]) > (1 << 20)
+    F = silu.ILU(silu.Matrix(ctx, *A), "ilu0")
+    OF = oracle.ilu0(A)
+    OS = oracle.row_scale(OF)
+    ex = F.export()
+    for mine, theirs in ((ex["L"], OF.L), (ex["U"], OF.U), (ex["Us"], OS.Us)):
+        for k in range(3):
+            assert np.array_equal(mine[k], theirs[k])
+    assert np.array_equal(ex["dinv"], OS.dinv)
+    rp, ci, va = A
+    rng = np.random.default_rng(3)
+    n = len(rp) - 1
+    lens = np.diff(rp)
+    rows = np.repeat(np.arange(n), lens)
+    key = rows * 4.0 + rng.random(len(ci))  # shuffle within each row
+    order = np.argsort(key, kind="stable")
+    ci2 = np.repeat(ci[order], 2)
+    va2 = np.repeat(va[order] * 0.5, 2)
+    rp2 = (2 * rp).astype(np.int64)
+    G = silu.ILU(silu.Matrix(ctx, rp2, ci2.astype(np.int32), va2), "ilu0").export()
+    for part in ("L", "U", "Us"):
+        for k in range(3):
+            assert np.array_equal(G[part][k], ex[part][k])
