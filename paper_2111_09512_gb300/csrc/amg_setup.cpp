@@ -22,7 +22,7 @@ namespace {
 // never depend on the count).
 int setup_threads(int64_t work) {
   if (work < (1 << 16)) return 1;
-  return (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+  return setup_thread_budget();
 }
 
 // fn(r0, r1, t) on nt contiguous ranges of [0, n), in parallel.
@@ -252,8 +252,7 @@ void galerkin(const Csr& A, const Csr& P, const Csr& R, Csr& Ac) {
     std::vector<double> va;
   };
   const int64_t work = R.nnz() + nc;
-  int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
-  if (work < (1 << 16)) nt = 1;
+  const int nt = setup_threads(work);
   std::vector<Part> parts(nt);
   auto run = [&](int t) {
     const int64_t I0 = nc * t / nt, I1 = nc * (t + 1) / nt;

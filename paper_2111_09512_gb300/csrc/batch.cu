@@ -469,6 +469,7 @@ silu_status silu_batch_setup(silu_ctx ctx, int count, const int64_t* n, const in
     std::vector<std::thread> pool;
     for (int t = 0; t < nthreads; ++t)
       pool.emplace_back([&, t]() {
+        set_setup_thread_budget(1);  // the systems are the parallelism here
         for (int k = t; k < count; k += nthreads) {
           const int64_t nk = n[k];
           if (nk < 0 || !row_ptr[k]) {

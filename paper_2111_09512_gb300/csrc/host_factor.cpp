@@ -16,11 +16,14 @@ namespace silu {
 
 namespace {
 
+thread_local int g_thread_budget = 0;
+
 // Host threads for row-parallel setup work on `work` stored entries: none
-// below a million (thread start-up would dominate), at most 16.
+// below a million (thread start-up would dominate), else the calling
+// thread's budget.
 int host_threads(int64_t work) {
   if (work < ((int64_t)1 << 20)) return 1;
-  return (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+  return setup_thread_budget();
 }
 
 // fn(r0, r1, t) on nt contiguous ranges of rows [0, n), in parallel.
@@ -36,6 +39,12 @@ void row_ranges(int64_t n, int nt, Fn fn) {
 }
 
 }  // namespace
+
+void set_setup_thread_budget(int budget) { g_thread_budget = budget < 0 ? 0 : budget; }
+int setup_thread_budget() {
+  const int hw = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+  return g_thread_budget > 0 ? std::min(g_thread_budget, hw) : hw;
+}
 
 int csr_canonical(int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci, const double* va, Csr& out,
                   std::string& msg) {
@@ -194,7 +203,7 @@ int numeric_on_pattern(const Csr& A, const std::vector<int64_t>& prp, const std:
   lu.assign(pci.size(), 0.0);
   dpos.assign(n, -1);
   const int64_t nnz = prp[n];
-  int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+  int nt = host_threads(nnz);
   // per-thread slot arrays of n int32: at most about 1 GB in all
   nt = (int)std::min<int64_t>(nt, std::max<int64_t>(1, ((int64_t)1 << 30) / (4 * std::max<int64_t>(n, 1))));
   if (n > 0 && nnz >= ((int64_t)1 << 20) && nt > 1) {

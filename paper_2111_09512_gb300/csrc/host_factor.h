@@ -18,6 +18,14 @@ struct Csr {
   int64_t nnz() const { return rp.empty() ? 0 : rp.back(); }
 };
 
+// Host setup calls made on the calling thread use up to `budget` host
+// threads for large systems (0: the default, up to 16 and the hardware's
+// count).  Callers that already run several setups side by side (the solve
+// server's workers, a batch's per-system threads) lower it, so that their
+// threads do not multiply.
+void set_setup_thread_budget(int budget);
+int setup_thread_budget();
+
 enum class Kind { ILU0 = 0, ILUK = 1, ILUT = 2, GS = 3, SGS = 4 };
 
 // Result codes mirror silu_status.

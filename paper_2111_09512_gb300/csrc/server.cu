@@ -51,6 +51,7 @@ struct silu_server_s {
   int64_t budget = 0;
   int64_t used = 0;
   int max_queue = 0;
+  int workers_count = 1;  // set before the workers start
   std::vector<std::thread> workers;
   std::mutex mu;
   std::condition_variable cv_work;  // workers wait for admissible work
@@ -146,6 +147,12 @@ void solve_one(silu_server S, silu_ctx ctx, const std::shared_ptr<Request>& r) {
 }
 
 void worker_main(silu_server S, int index) {
+  // requests are the parallelism here: each worker's setups share the host
+  // cores with the other workers'
+  {
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    silu::set_setup_thread_budget(std::max(1, hw / std::max(1, (int)S->workers_count)));
+  }
   silu_ctx ctx = nullptr;
   cudaStream_t stream = nullptr;
   if (S->device >= 0) {
@@ -214,6 +221,7 @@ silu_status silu_server_create(int device, int64_t hbm_budget_bytes, int workers
   S->budget = hbm_budget_bytes;
   S->max_queue = max_queue;
   S->t0 = now_s();
+  S->workers_count = workers;
   for (int w = 0; w < workers; ++w) S->workers.emplace_back(worker_main, S, w);
   *out = S;
   return SILU_OK;
