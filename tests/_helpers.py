@@ -57,3 +57,12 @@ def relerr(a, b):
     b = np.asarray(b, np.float64)
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def maxabs_err(a, b):
+    """max_i |a_i - b_i| / max_i |b_i|: a wrong value in a few rows of a long
+    vector, which the 2-norm ratio can hide, shows here."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    nb = np.max(np.abs(b)) if b.size else 0.0
+    return float(np.max(np.abs(a - b))) / (nb if nb > 0 else 1.0) if b.size else 0.0

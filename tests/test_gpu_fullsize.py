@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from _helpers import relerr
+from _helpers import maxabs_err, relerr
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -35,11 +35,14 @@ def test_cutcell128_ilut_smooth_full_vector():
     torch.cuda.synchronize()
     got = x.cpu().numpy()
     assert relerr(got, want) < 1e-12
+    assert maxabs_err(got, want) < 1e-12
     # a second application from the first iterate (x != 0 exercises the residual)
     want2 = oracle.smooth(A, S, want, b, 10, 10)
     silu.ilu_smooth(F, x, torch.from_numpy(b).cuda(), 10, 10)
     torch.cuda.synchronize()
-    assert relerr(x.cpu().numpy(), want2) < 1e-12
+    got2 = x.cpu().numpy()
+    assert relerr(got2, want2) < 1e-12
+    assert maxabs_err(got2, want2) < 1e-12
 
 
 def test_hex27_256_fp32_smoother_fgmres_full_size():
@@ -134,6 +137,9 @@ def test_hex27_256_fp32_application_error_vs_fp64_oracle():
     x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
     silu.ilu_smooth(F, x, torch.from_numpy(b).cuda(), 3, 3)
     torch.cuda.synchronize()
-    err = relerr(x.cpu().numpy(), want)
-    print(f"256^3 27-point FP32 3+3 application, relative 2-norm error vs the FP64 oracle: {err:.3e}")
-    assert err < 1e-5
+    got = x.cpu().numpy()
+    err = relerr(got, want)
+    emax = maxabs_err(got, want)
+    print(f"256^3 27-point FP32 3+3 application vs the FP64 oracle: relative 2-norm error {err:.3e}, "
+          f"max-abs error / max |ref| {emax:.3e}")
+    assert err < 1e-5 and emax < 1e-5

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import synth
-from _helpers import relerr
+from _helpers import maxabs_err, relerr
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -42,9 +42,11 @@ def host(t):
 
 
 def percol_relerr(got, want):
+    """Per right-hand side, the larger of the relative 2-norm error and the
+    max-abs error over max |ref|; the worst column."""
     got = got.reshape(want.shape[0], -1)
     want = want.reshape(want.shape[0], -1)
-    return max(relerr(got[:, k], want[:, k]) for k in range(want.shape[1]))
+    return max(max(relerr(got[:, k], want[:, k]), maxabs_err(got[:, k], want[:, k])) for k in range(want.shape[1]))
 
 
 def oracle_scaled(A, kind, tau, fill):
@@ -105,18 +107,22 @@ def test_unscaled_variants_match_oracle(silu, ctx, scale):
     F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilut", 1e-3, 10, scale=sc)
     OF, S = oracle_scaled(A, "ilut", 1e-3, 10)
     b = synth.rhs(n, 1, seed=3)
-    for mL, mU in [(3, 1), (3, 2), (2, 5)]:
+    # plain Richardson grows by about 1e3 per sweep here (Sec. 6.1's failure),
+    # so the iterates stay finite through five sweeps, and rounding stays at
+    # the 1e-15 level relative to them: the comparison is unconditional
+    for mL, mU in [(3, 1), (3, 2), (2, 3), (2, 5)]:
         r = oracle.residual(A, np.zeros((n, 1)), b)
         y = oracle.richardson_lower(S.L, r, mL)
         if scale == "none":
             v = oracle.upper_jacobi(OF.U, y, mU)
         else:
             v = oracle.upper_unscaled_richardson(OF.U, y, mU)
+        assert np.all(np.isfinite(v))
         x = torch.zeros(n, 1, dtype=torch.float64, device="cuda")
         silu.ilu_smooth(F, x, dev(b), mL, mU)
         got = host(x)
-        if np.all(np.isfinite(v)) and np.linalg.norm(v) < 1e100:
-            assert relerr(got, v) < FP64_TOL * max(1.0, np.linalg.norm(v) / np.linalg.norm(b)), (mL, mU)
+        assert relerr(got, v) < FP64_TOL, (mL, mU)
+        assert maxabs_err(got, v) < FP64_TOL, (mL, mU)
 
 
 def test_smooth_many_sweeps_equals_direct(silu, ctx):

@@ -124,6 +124,37 @@ def test_unscaled_variants():
     assert grow[2] > 1e3 * grow[0]
 
 
+@pytest.mark.parametrize("gen", ["cutcell_ilu0", "cutcell_ilut", "hex27_ilu0"])
+def test_unscaled_iterations_are_dense_partial_sums(gen):
+    """Plain Richardson on the raw upper factor, v <- y - (U - I) v from
+    v = 0, gives v^m = sum_{j<m} (I - U)^j y; Jacobi on raw U (Eq. LUiterMat,
+    G_U = I - D_U^{-1} U) gives sum_{j<m} G_U^j D_U^{-1} y.  Both by explicit
+    dense matrix powers of U with its true (non-unit) diagonal, so taking
+    y - U v for the Richardson step, or dropping D_U^{-1}, fails here."""
+    if gen == "cutcell_ilu0":
+        A = synth.cutcell7(4, 4, 3, seed=4)
+        F = oracle.factor(A, "ilu0", 0.0, 0)
+    elif gen == "cutcell_ilut":
+        A = synth.cutcell7(4, 3, 3, seed=5)
+        F = oracle.factor(A, "ilut", 1e-3, 5)
+    else:
+        A = synth.hex27(3, 3, 3, seed=6)
+        F = oracle.factor(A, "ilu0", 0.0, 0)
+    n = F.n
+    U = dense(F.U, n)
+    assert np.max(np.abs(np.diag(U) - 1.0)) > 0.5  # a diagonal far from one
+    I = np.eye(n)
+    Dinv = np.diag(1.0 / np.diag(U))
+    y = synth.rhs(n, 2, seed=1)
+    for m in (1, 2, 3, 4, 5):
+        want = sum(np.linalg.matrix_power(I - U, j) @ y for j in range(m))
+        got = oracle.upper_unscaled_richardson(F.U, y, m)
+        assert relerr(got, want) < 1e-13, m
+        want_j = sum(np.linalg.matrix_power(I - Dinv @ U, j) @ (Dinv @ y) for j in range(m))
+        assert relerr(oracle.upper_jacobi(F.U, y, m), want_j) < 1e-13, m
+    assert np.all(oracle.upper_unscaled_richardson(F.U, y, 0) == 0)
+
+
 def test_smooth_composes_the_sweeps():
     """x + M^{-1}(b - A x) (Eq. ILUsplit): residual, m_L lower sweeps, D^{-1},
     m_U upper sweeps, update; with enough sweeps it equals the direct solves,
