@@ -424,7 +424,11 @@ def run_silu(args):
 
     p32 = poisson32(silu, ctx, torch) if rank == 0 else None
     f32err = fp32_error(silu, ctx, torch) if rank == 0 else None
-    study = sweep_study(silu, ctx, torch) if (args.study and rank == 0) else None
+    study = None
+    if rank == 0 and args.study:
+        study = sweep_study(silu, ctx, torch)
+    elif rank == 0 and not args.no_scaling_study:
+        study = {"scaling": scaling_study(silu, ctx, torch)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -640,29 +644,12 @@ def batch_workload(silu, ctx, torch, count: int):
     return out
 
 
-def serving(silu, args):
-    """Continuous-batching solve server: Poisson arrivals (mean rate
-    args.serve_rate per second, seed 4) of cut-cell pressure solves with grid
-    edges log-uniform in [16, 192], each FGMRES(30) from zero to 1e-8, under a
-    120 GB HBM budget.  Four paths on the same arrival stream: FP32 scaled-ILU(0)
-    Richardson smoother with 3+3 sweeps (the default) and with 5+5 sweeps
-    (about the fewest sweeps that bring FGMRES to the iteration count of exact
-    solves on these matrices, and the shortest time to solution), the same
-    FP32 smoother (8+8 sweeps) on the finest level of an AMG V-cycle (the
-    paper's GMRES + AMG; the hierarchy is built on the host per request), and
-    the plain FP64 direct-trisolve path.
-    The client draws every request's edge from the stream but takes its matrix
-    from a pool of args.serve_pool distinct systems generated before the clock
-    starts (request k uses pool entry k mod pool, whose edge is the pool's own
-    log-uniform draw), so submission is never held up by generation.  Latency
-    is completion minus submission on the server's clock."""
+def serve_pool(args):
+    """The pool of distinct systems the serving client draws matrices from
+    (generated before any clock starts): args.serve_pool cut-cell matrices
+    with edges log-uniform in [16, 192] (seed 4), each with its right-hand side."""
     import numpy as np
     import synth
-    rate, dur = args.serve_rate, args.serve_seconds
-    count = int(rate * dur * 1.5) + 16
-    gaps = -np.log1p(-synth.uniform(4, 5, count, 0.0, 1.0)) / rate
-    arrivals = np.cumsum(gaps)
-    arrivals = arrivals[arrivals < dur]
     P = args.serve_pool
     ue = synth.uniform(4, 6, P, 0.0, 1.0)
     edges = np.rint(np.exp(np.log(16.0) + ue * (np.log(192.0) - np.log(16.0)))).astype(int)
@@ -670,46 +657,107 @@ def serving(silu, args):
     for k, e in enumerate(edges):
         A = synth.cutcell7(int(e), seed=40_000 + k)
         pool.append((A, synth.rhs(int(e) ** 3, 1, seed=50_000 + k)[:, 0]))
+    return edges, pool
+
+
+def serve_stream(silu, pool, arrivals, path, workers, max_queue):
+    """Offer the arrival stream to a fresh server on one path; per-request
+    latency is completion minus submission on the server's clock."""
+    import numpy as np
+    prec, pc, sw = path
+    P = len(pool)
+    S = silu.Server(0, 120 << 30, workers=workers, max_queue=max_queue)
+    tickets, refused = [], 0
+    start = time.perf_counter()
+    for k, t_k in enumerate(arrivals):
+        now = time.perf_counter() - start
+        if now < t_k:
+            time.sleep(t_k - now)
+        A, b = pool[k % P]
+        st, t = S.submit(A, b, prec=prec, tol=1e-8, restart=30, maxit=20000, sweeps_L=sw, sweeps_U=sw, precond=pc)
+        if st == silu.OK:
+            tickets.append(t)
+        else:
+            refused += 1
+    lat, solved, iters, t_first, t_last, setup = [], 0, [], None, None, []
+    for t in tickets:
+        _, res, _ = S.poll(t, wait=True, want_x=False)
+        if res.status == silu.OK:
+            solved += 1
+            lat.append(res.t_done - res.t_submit)
+            iters.append(res.iterations)
+            setup.append(res.t_setup_done - res.t_admit)
+            t_first = res.t_submit if t_first is None else min(t_first, res.t_submit)
+            t_last = res.t_done if t_last is None else max(t_last, res.t_done)
+    S.close()
+    span = (t_last - t_first) if solved else 0.0
+    offered = len(arrivals)
+    return {"offered": offered, "admitted": len(tickets), "refused": refused,
+            "refused_fraction": round(refused / offered, 4) if offered else None, "solved": solved,
+            "goodput_solves_per_s": round(solved / span, 3) if span > 0 else None,
+            "p50_s": round(float(np.percentile(lat, 50)), 4) if lat else None,
+            "p99_s": round(float(np.percentile(lat, 99)), 4) if lat else None,
+            "max_s": round(float(np.max(lat)), 4) if lat else None,
+            "iterations_mean": round(float(np.mean(iters)), 1) if iters else None,
+            "host_setup_mean_s": round(float(np.mean(setup)), 3) if setup else None}
+
+
+def poisson_arrivals(rate, count, seed_stream):
+    """count exponential inter-arrival times of mean 1/rate (counter-based
+    uniforms of the given stream), as absolute offsets in seconds."""
+    import numpy as np
+    import synth
+    gaps = -np.log1p(-synth.uniform(4, seed_stream, count, 0.0, 1.0)) / rate
+    return np.cumsum(gaps)
+
+
+def serving(silu, args):
+    """Continuous-batching solve server (cut-cell pressure solves with grid
+    edges log-uniform in [16, 192], each FGMRES(30) from zero to 1e-8, under
+    a 120 GB HBM budget), two runs.
+
+    offered: the stream of the workload's definition, Poisson arrivals at
+    args.serve_rate per second (200; seed 4) until args.serve_requests
+    requests (1000) have been offered, on three paths: the FP32 scaled-ILU(0)
+    Richardson smoother with 3+3 sweeps (the default) and with 5+5 sweeps
+    (about the fewest sweeps that bring FGMRES to the iteration count of exact
+    solves on these matrices), and the plain FP64 direct-trisolve path.  One
+    GPU serves a few solves of ~1M rows per second, so this stream saturates
+    it: the server admits what its slots and queue hold and refuses the rest;
+    the run reports the refused fraction, the goodput and the latency of the
+    admitted requests (queue-bound).
+
+    sustained: Poisson arrivals at args.serve_low_rate per second (below what
+    one GPU serves on either path) for args.serve_low_seconds, FP32 5+5 sweeps
+    against FP64 direct, with a queue long enough that nothing is refused, so
+    p50/p99 are latencies of a server that keeps up.
+
+    The client draws every request's edge from the stream but takes its
+    matrix from a pool of args.serve_pool distinct systems generated before
+    the clock starts (request k uses pool entry k mod pool), so submission is
+    never held up by generation."""
+    import numpy as np
+    edges, pool = serve_pool(args)
     out = {"workload": "cut-cell 7-point solves, edges log-uniform [16,192], FGMRES(30) to 1e-8",
-           "rate_per_s": rate, "seconds": dur, "offered": int(len(arrivals)), "pool": P,
-           "pool_rows_mean": int(np.mean(edges.astype(np.int64) ** 3)), "hbm_budget_gb": 120,
-           "workers": args.serve_workers, "max_queue": args.serve_queue}
-    for name, prec, pc, sw in (("fp32_sweeps_3_3", silu.FP32, silu.PRECOND_SWEEPS, 3),
-                               ("fp32_sweeps_5_5", silu.FP32, silu.PRECOND_SWEEPS, 5),
-                               ("fp32_amg_sweeps_8_8", silu.FP32, silu.PRECOND_AMG, 8),
-                               ("fp64_direct", silu.FP64, silu.PRECOND_DIRECT, 3)):
-        S = silu.Server(0, 120 << 30, workers=args.serve_workers, max_queue=args.serve_queue)
-        tickets, refused = [], 0
-        start = time.perf_counter()
-        for k, t_k in enumerate(arrivals):
-            now = time.perf_counter() - start
-            if now < t_k:
-                time.sleep(t_k - now)
-            A, b = pool[k % P]
-            st, t = S.submit(A, b, prec=prec, tol=1e-8, restart=30, maxit=20000, sweeps_L=sw, sweeps_U=sw,
-                             precond=pc)
-            if st == silu.OK:
-                tickets.append(t)
-            else:
-                refused += 1
-        lat, solved, iters, t_first, t_last, setup = [], 0, [], None, None, []
-        for t in tickets:
-            _, res, _ = S.poll(t, wait=True, want_x=False)
-            if res.status == silu.OK:
-                solved += 1
-                lat.append(res.t_done - res.t_submit)
-                iters.append(res.iterations)
-                setup.append(res.t_setup_done - res.t_admit)
-                t_first = res.t_submit if t_first is None else min(t_first, res.t_submit)
-                t_last = res.t_done if t_last is None else max(t_last, res.t_done)
-        S.close()
-        span = (t_last - t_first) if solved else 0.0
-        out[name] = {"admitted": len(tickets), "refused": refused, "solved": solved,
-                     "solves_per_s": round(solved / span, 3) if span > 0 else None,
-                     "p50_s": round(float(np.percentile(lat, 50)), 4) if lat else None,
-                     "p99_s": round(float(np.percentile(lat, 99)), 4) if lat else None,
-                     "iterations_mean": round(float(np.mean(iters)), 1) if iters else None,
-                     "host_setup_mean_s": round(float(np.mean(setup)), 3) if setup else None}
+           "pool": args.serve_pool, "pool_rows_mean": int(np.mean(edges.astype(np.int64) ** 3)),
+           "hbm_budget_gb": 120, "workers": args.serve_workers}
+    paths = {"fp32_sweeps_3_3": (silu.FP32, silu.PRECOND_SWEEPS, 3),
+             "fp32_sweeps_5_5": (silu.FP32, silu.PRECOND_SWEEPS, 5),
+             "fp64_direct": (silu.FP64, silu.PRECOND_DIRECT, 3)}
+    arr = poisson_arrivals(args.serve_rate, args.serve_requests, 5)
+    off = {"rate_per_s": args.serve_rate, "requests": args.serve_requests,
+           "seconds_of_arrivals": round(float(arr[-1]), 3), "max_queue": args.serve_queue}
+    for name, path in paths.items():
+        off[name] = serve_stream(silu, pool, arr, path, args.serve_workers, args.serve_queue)
+    out["offered"] = off
+    if args.serve_low_seconds > 0:
+        low = poisson_arrivals(args.serve_low_rate, int(args.serve_low_rate * args.serve_low_seconds * 3) + 16, 7)
+        low = low[low < args.serve_low_seconds]
+        sus = {"rate_per_s": args.serve_low_rate, "seconds_of_arrivals": args.serve_low_seconds,
+               "max_queue": len(low)}
+        for name in ("fp32_sweeps_5_5", "fp64_direct"):
+            sus[name] = serve_stream(silu, pool, low, paths[name], args.serve_workers, len(low))
+        out["sustained"] = sus
     return out
 
 
@@ -870,36 +918,16 @@ def poisson32(silu, ctx, torch):
     return out
 
 
-def sweep_study(silu, ctx, torch):
-    """Sweep studies (the paper's Sec. 5.2 and Sec. 6.1 questions on synthetic
-    matrices), all computed by the library on the device.
-
-    scaling: cut-cell 128^3, ILUT(1e-3, 10), FP64, one right-hand side
-    (seed 1): for m = 1..20 sweeps on each factor, one smoother application
-    from zero with the row-scaled factors (the method), row/column (Ruiz)
-    scaled factors, unscaled Jacobi and unscaled plain Richardson; reports
-    ||b - A x_m|| / ||b|| and the distance ||x_m - x*|| / ||x*|| to the exact
-    application x* (direct solves).
-
-    kinds: the same matrix under ILU(0), ILU(1), ILUT(1e-2, 10),
-    ILUT(1e-3, 10), ILUT(1e-4, 20) and the polynomial Gauss-Seidel
-    splittings: relres of one application for m = 1..20, the factor sizes
-    and level counts, and FGMRES(30) to 1e-8 with 3+3 sweeps against the
-    direct solves (iterations, seconds).
-
-    nilpotence: ||T_s^p||_2 for p = 1..40 (power iteration, 30 steps per p)
-    on a 24^3 cut-cell matrix (13,824 rows, the size of the paper's
-    14,186-row PeleLM matrix of Fig. Up), upper factor of ILUT(tau, 30) for
-    tau in {1e-2, 1e-3, 1e-4} with row and with row/column scaling, and L_s;
-    with the departure from normality (Eq. depB) of L, U and the scaled U
-    (Table dep).
-
-    time_to_solution_vs_sweeps: FGMRES(30) to 1e-8 on cut-cell matrices of
-    64^3 to 160^3 rows with FP32 ILU(0) factors and m + m sweeps (m = 2..10)
-    against direct solves of the same factors (iterations, seconds)."""
-    import numpy as np
+def scaling_study(silu, ctx, torch):
+    """Scaled against unscaled factors (the paper's Sec. 6.1, Table NRBE2's
+    question) on the cut-cell 128^3 matrix, ILUT(1e-3, 10), FP64, one
+    right-hand side (seed 1): for m = 1..20 sweeps on each factor, one
+    smoother application from zero with the row-scaled factors (the method),
+    row/column (Ruiz) scaled factors, unscaled Jacobi and unscaled plain
+    Richardson; reports the residual reduction ||b - A x_m|| / ||b|| and the
+    distance ||x_m - x*|| / ||x*|| to the exact application x* (direct
+    solves), all computed by the library on the device."""
     import synth
-    out = {}
 
     def norms_of(M, x, bt):
         r = torch.empty_like(bt)
@@ -933,7 +961,52 @@ def sweep_study(silu, ctx, torch):
         sc_out[name] = {"relres": [None if v is None else float(f"{v:.4e}") for v in rel],
                         "dist_to_exact": [None if v is None else float(f"{v:.4e}") for v in dist]}
         del F
-    out["scaling"] = sc_out
+    return sc_out
+
+
+def sweep_study(silu, ctx, torch):
+    """Sweep studies (the paper's Sec. 5.2 and Sec. 6.1 questions on synthetic
+    matrices), all computed by the library on the device.
+
+    scaling: cut-cell 128^3, ILUT(1e-3, 10), FP64, one right-hand side
+    (seed 1): for m = 1..20 sweeps on each factor, one smoother application
+    from zero with the row-scaled factors (the method), row/column (Ruiz)
+    scaled factors, unscaled Jacobi and unscaled plain Richardson; reports
+    ||b - A x_m|| / ||b|| and the distance ||x_m - x*|| / ||x*|| to the exact
+    application x* (direct solves).
+
+    kinds: the same matrix under ILU(0), ILU(1), ILUT(1e-2, 10),
+    ILUT(1e-3, 10), ILUT(1e-4, 20) and the polynomial Gauss-Seidel
+    splittings: relres of one application for m = 1..20, the factor sizes
+    and level counts, and FGMRES(30) to 1e-8 with 3+3 sweeps against the
+    direct solves (iterations, seconds).
+
+    nilpotence: ||T_s^p||_2 for p = 1..40 (power iteration, 30 steps per p)
+    on a 24^3 cut-cell matrix (13,824 rows, the size of the paper's
+    14,186-row PeleLM matrix of Fig. Up), upper factor of ILUT(tau, 30) for
+    tau in {1e-2, 1e-3, 1e-4} with row and with row/column scaling, and L_s;
+    with the departure from normality (Eq. depB) of L, U and the scaled U
+    (Table dep).
+
+    time_to_solution_vs_sweeps: FGMRES(30) to 1e-8 on cut-cell matrices of
+    64^3 to 160^3 rows with FP32 ILU(0) factors and m + m sweeps (m = 2..10)
+    against direct solves of the same factors (iterations, seconds)."""
+    import numpy as np
+    import synth
+    out = {}
+
+    out["scaling"] = scaling_study(silu, ctx, torch)
+    A = synth.cutcell7(EDGE, seed=1)
+    n = len(A[0]) - 1
+    bh = synth.rhs(n, 1, seed=1)
+    b = torch.from_numpy(bh).cuda()
+    M = silu.Matrix(ctx, *A)
+    sweeps = list(range(1, 21))
+
+    def norms_of(M, x, bt):
+        r = torch.empty_like(bt)
+        M.residual(r, x, bt)
+        return float(torch.linalg.norm(r) / torch.linalg.norm(bt))
 
     kinds = [("ilu0", "ilu0", 0.0, 0), ("iluk1", "iluk", 0.0, 1), ("ilut_1e-2_10", "ilut", 1e-2, 10),
              ("ilut_1e-3_10", "ilut", 1e-3, 10), ("ilut_1e-4_20", "ilut", 1e-4, 20), ("gs", "gs", 0.0, 0),
@@ -1033,9 +1106,16 @@ def main():
     ap.add_argument("--amg-edge", type=int, default=224,
                     help="grid edge of the GMRES+AMG comparison (0 = skip)")
     ap.add_argument("--study", action="store_true",
-                    help="add the sweep studies: scaling variants, factorisation kinds, ||T_s^p||_2")
+                    help="add the sweep studies: factorisation kinds, ||T_s^p||_2, time to solution vs sweeps")
+    ap.add_argument("--no-scaling-study", action="store_true",
+                    help="skip the per-sweep residual reduction of scaled vs unscaled factors (run by default)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-requests", type=int, default=1000,
+                    help="requests offered at --serve-rate per path")
+    ap.add_argument("--serve-low-rate", type=float, default=2.0,
+                    help="arrival rate of the sustained (below-saturation) serving run")
+    ap.add_argument("--serve-low-seconds", type=float, default=30.0,
+                    help="arrival window of the sustained serving run (0 = skip it)")
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-queue", type=int, default=8)
     ap.add_argument("--serve-pool", type=int, default=32)

@@ -280,15 +280,38 @@ silu_status ilu_smooth(silu_ilu F, double* x, const double* b, int nrhs, int swe
 
 /*
  * The comparison path: the same update with exact triangular solves,
- * x <- x + Utilde^{-1} D^{-1} L^{-1} (b - A x), by level-set scheduling
- * (Sec. 4: rows of one level are independent; one device-wide ordering point
- * per level).  Always FP64 arithmetic on the FP64 copy of the factors.
- * The levels run as one captured CUDA graph per column block; the first one
- * built on F is captured twice, with and without each level launched as a
- * programmatic dependent of the previous one (see silu_ctx_set_overlap), and
- * both are timed once; the faster form is kept for F (same bits either way).
+ * x <- x + Utilde^{-1} D^{-1} L^{-1} (b - A x), in the order of the level
+ * sets (Sec. 4: rows of one level are independent; a level needs only rows
+ * of earlier levels).  Always FP64 arithmetic on FP64 copies of the factors.
+ * Two schedules (silu_ilu_set_direct); by default the library times both
+ * once per factor object and column count (on its workspace, when the exact
+ * solves are first set up or first used with that many columns) and keeps
+ * the faster:
+ *   persistent (mode 2): both solves and the update of x in one persistent
+ *     launch after the residual.  Rows are stored in level order and taken
+ *     in items of at most 32 rows of one level, in level order, by whichever
+ *     warp is free; a row waits only for the entries it reads.  Each
+ *     published intermediate entry carries a readiness tag in the lowest bit
+ *     of its FP64 significand (a relative change of at most 2^-52 per entry),
+ *     so one store publishes value and readiness; readers use the entry
+ *     with that bit cleared, so results do not depend on the tag.  An item
+ *     first waits for one row a few levels back, so items far ahead of the
+ *     finished levels do not flood L2 with reads.  Every wait is bounded
+ *     (2 s); one that gives up makes the next silu_ctx_check return
+ *     SILU_ERR_TIMEOUT.  Capturable in CUDA graphs.
+ *   per level (mode 1): one kernel per level, as one captured CUDA graph per column
+ *     block; the first one built on F is captured twice, with and without
+ *     each level launched as a programmatic dependent of the previous one
+ *     (see silu_ctx_set_overlap), and both are timed once; the faster form
+ *     is kept for F (same bits either way).
  */
 silu_status direct_trisolve(silu_ilu F, double* x, const double* b, int nrhs);
+
+/* Schedule of the exact solves (direct_trisolve, SILU_PRECOND_DIRECT and the
+ * AMG cycle with exact solves): 0 automatic (default: the faster of the two,
+ * timed once), 1 one launch per level, 2 one persistent launch.  Other
+ * values -> SILU_ERR_INVALID_ARG. */
+silu_status silu_ilu_set_direct(silu_ilu F, int mode);
 
 /*
  * Right-preconditioned flexible GMRES(restart) on A x = b for one right-hand
@@ -605,12 +628,18 @@ void silu_server_destroy(silu_server S);
  * device that loads the library until the process exits).  n above 524288
  * returns SILU_ERR_TOO_LARGE before any work.  The first call on a device
  * looks up that array's device address (with the device made current, the
- * caller's current device restored afterwards).  All calls share the array
- * and it keeps the last call's contents (every vector is written before it
- * is read); calls whose work overlaps on the GPU race on it.
+ * caller's current device restored afterwards); under CUDA's default lazy
+ * module loading this lookup is what loads the array onto the device, so
+ * the 16 MiB are taken by that first call, which returns SILU_ERR_OOM if
+ * they are not free.  Make the first call before a memory pool claims the
+ * device (and before any stream capture); later calls need no memory.  The
+ * address is kept for the life of the process: calls after cudaDeviceReset
+ * are not supported.  All calls share the array and it keeps the last
+ * call's contents (every vector is written before it is read); calls whose
+ * work overlaps on the GPU race on it.
  * Returns SILU_ERR_INVALID_ARG for null pointers or negative counts,
- * SILU_ERR_NO_DEVICE if the device cannot be selected, SILU_ERR_CUDA if a
- * launch fails.
+ * SILU_ERR_NO_DEVICE if the device cannot be selected, SILU_ERR_OOM as
+ * above, SILU_ERR_CUDA if a launch fails.
  */
 silu_status silu_smooth_noalloc(int device, void* cuda_stream, int64_t n, const int32_t* A_rp, const int32_t* A_ci,
                                 const double* A_val, const int32_t* L_rp, const int32_t* L_ci, const double* L_val,

@@ -120,6 +120,7 @@ def load():
         "silu_ctx_check": (i32, [vp]),
         "silu_ctx_selftest_timeout": (i32, [vp, i32]),
         "silu_ilu_set_kernel": (i32, [vp, i32]),
+        "silu_ilu_set_direct": (i32, [vp, i32]),
         "silu_ilu_layout": (i32, [vp, vp, vp, vp]),
         "silu_ctx_set_overlap": (i32, [vp, i32]),
         "silu_ctx_set_l2_reuse": (i32, [vp, i32]),
@@ -157,7 +158,7 @@ def exported_symbols():
             "silu_amg_stats", "silu_amg_export_level", "silu_schur_setup", "silu_schur_smooth",
             "silu_schur_stats",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
-            "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_layout", "silu_ilu_tune_table", "silu_ctx_set_overlap",
+            "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_set_direct", "silu_ilu_layout", "silu_ilu_tune_table", "silu_ctx_set_overlap",
             "silu_ctx_set_l2_reuse",
             "silu_smooth_noalloc",
             "silu_batch_setup", "silu_batch_info", "silu_batch_smooth", "silu_batch_fgmres", "silu_batch_destroy",
@@ -473,6 +474,11 @@ class ILU:
         """0 automatic, 1 lanes-per-row kernel, 2 staged (bulk-copy) kernel where it applies (natural
         row order), 3 staged kernel on the length-sorted copies where they exist."""
         _check(self.ctx.handle, load().silu_ilu_set_kernel(self.handle, variant), "silu_ilu_set_kernel")
+
+    def set_direct(self, mode: int):
+        """Schedule of the exact triangular solves: 0 automatic (default; the faster of the two, timed
+        once per column count), 1 one launch per level (captured graph), 2 one persistent launch."""
+        _check(self.ctx.handle, load().silu_ilu_set_direct(self.handle, mode), "silu_ilu_set_direct")
 
     def layout(self):
         """FMA slots per entry of one-lane-per-row tiles, natural and length-sorted rows, for

@@ -192,6 +192,173 @@ cudaError_t ensure_krylov(silu_ilu F, int m) {
   return cudaSuccess;
 }
 
+namespace {
+
+// Rows of T (strict triangle, FP64) in the order level_rows lists them: row
+// pointers and columns as int32, values as FP64, each row's entries kept in
+// column order.
+void level_copy(const Csr& T, const std::vector<int32_t>& level_rows, std::vector<int32_t>& rp,
+                std::vector<int32_t>& ci, std::vector<double>& va) {
+  const int64_t n = T.n;
+  rp.assign((size_t)n + 1, 0);
+  for (int64_t k = 0; k < n; ++k) {
+    const int32_t i = level_rows[(size_t)k];
+    rp[(size_t)k + 1] = rp[(size_t)k] + (int32_t)(T.rp[i + 1] - T.rp[i]);
+  }
+  ci.resize((size_t)T.nnz());
+  va.resize((size_t)T.nnz());
+  for (int64_t k = 0; k < n; ++k) {
+    const int32_t i = level_rows[(size_t)k];
+    std::copy(T.ci.begin() + T.rp[i], T.ci.begin() + T.rp[i + 1], ci.begin() + rp[(size_t)k]);
+    std::copy(T.va.begin() + T.rp[i], T.va.begin() + T.rp[i + 1], va.begin() + rp[(size_t)k]);
+  }
+}
+
+// Levels between an item and the row it waits on before reading its entries.
+#ifndef SILU_TRI_GATE_LEVELS
+#define SILU_TRI_GATE_LEVELS 3
+#endif
+constexpr int kTriGateLevels = SILU_TRI_GATE_LEVELS;
+
+// Items of at most 32 consecutive level-ordered rows of one level, four
+// ints each: first and last + 1 level-ordered position, the gate row and
+// whether the gate is a row of the upper solve.  The gate of the item at
+// offset o within level l >= g (g = kTriGateLevels) is the first row of the
+// item at offset min(o, items(l-g) - 1) of level l-g (items of one level
+// spread their gates over that level); levels below g have none (-1).
+void level_items(const std::vector<int32_t>& level_ptr, const std::vector<int32_t>& level_rows, int upper,
+                 std::vector<int32_t>& items) {
+  std::vector<int32_t> lev_first;  // first item (local index) of each level, then the end
+  const size_t base = items.size() / 4;
+  size_t local = 0;
+  for (size_t l = 0; l + 1 < level_ptr.size(); ++l) {
+    lev_first.push_back((int32_t)local);
+    local += (size_t)((level_ptr[l + 1] - level_ptr[l] + 31) / 32);
+  }
+  lev_first.push_back((int32_t)local);
+  for (size_t l = 0; l + 1 < level_ptr.size(); ++l) {
+    int32_t o = 0;
+    for (int32_t b = level_ptr[l]; b < level_ptr[l + 1]; b += 32, ++o) {
+      items.push_back(b);
+      items.push_back(std::min(b + 32, level_ptr[l + 1]));
+      int32_t gate = -1;
+      if (l >= (size_t)kTriGateLevels) {
+        const size_t g = l - (size_t)kTriGateLevels;
+        const int32_t cnt = lev_first[g + 1] - lev_first[g];
+        const int32_t gi = lev_first[g] + std::min(o, cnt - 1);  // local item of level l - kTriGateLevels
+        gate = level_rows[(size_t)items[(base + (size_t)gi) * 4]];
+      }
+      items.push_back(gate);
+      items.push_back(upper);
+    }
+  }
+}
+
+}  // namespace
+
+// Level-ordered copies of L_s and of the scaled strict upper factor, and the
+// item list of the persistent solve (Sec. 4's level sets, one launch).
+cudaError_t build_tri_plan(silu_ilu F) {
+  cudaStream_t s = F->ctx->stream;
+  std::vector<int32_t> rp, ci, items;
+  std::vector<double> va;
+  level_items(F->levLptr, F->levLrows, 0, items);
+  const int nitemsL = (int)(items.size() / 4);
+  level_items(F->levUptr, F->levUrows, 1, items);
+  cudaError_t e = upload(F->tri_items, items.data(), items.size(), s);
+  // uploads are stream-ordered copies from these host vectors: wait before reusing them
+  level_copy(F->F.L, F->levLrows, rp, ci, va);
+  if (e == cudaSuccess) e = upload(F->tri_lrp, rp.data(), rp.size(), s);
+  if (e == cudaSuccess) e = upload(F->tri_lci, ci.data(), ci.size(), s);
+  if (e == cudaSuccess) e = upload(F->tri_lva, va.data(), va.size(), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  level_copy(F->Us, F->levUrows, rp, ci, va);
+  e = upload(F->tri_urp, rp.data(), rp.size(), s);
+  if (e == cudaSuccess) e = upload(F->tri_uci, ci.data(), ci.size(), s);
+  if (e == cudaSuccess) e = upload(F->tri_uva, va.data(), va.size(), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  silu::TriPlan& P = F->tri;
+  P.nitemsL = nitemsL;
+  P.nitems = (int)(items.size() / 4);
+  P.items = F->tri_items.as<int>();
+  P.rowsL = F->levLrows_d.as<int>();
+  P.lrp = F->tri_lrp.as<int>();
+  P.lci = F->tri_lci.as<int>();
+  P.lva = F->tri_lva.as<double>();
+  P.rowsU = F->levUrows_d.as<int>();
+  P.urp = F->tri_urp.as<int>();
+  P.uci = F->tri_uci.as<int>();
+  P.uva = F->tri_uva.as<double>();
+  return cudaSuccess;
+}
+
+int tri_slot(int R) { return R == 1 ? 0 : (R == 2 ? 1 : 2); }
+
+// The tagged vectors and launch state of the persistent solve for R columns
+// (allocated and zeroed once per factor object; never during a capture).
+cudaError_t ensure_tri(silu_ilu F, int R) {
+  const int k = tri_slot(R);
+  if (F->tri_state[k].p) return cudaSuccess;
+  cudaStream_t s = F->ctx->stream;
+  const size_t vb = sizeof(double) * (size_t)std::max<int64_t>(F->F.L.n, 1) * (size_t)R;
+  cudaError_t e = F->tri_y[k].ensure(vb);
+  if (e == cudaSuccess) e = F->tri_v[k].ensure(vb);
+  if (e == cudaSuccess) e = cudaMemsetAsync(F->tri_y[k].p, 0, vb, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(F->tri_v[k].p, 0, vb, s);
+  DBuf st;
+  if (e == cudaSuccess) e = st.ensure(4 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemsetAsync(st.p, 0, 4 * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  std::swap(F->tri_state[k].p, st.p);
+  std::swap(F->tri_state[k].bytes, st.bytes);
+  return cudaSuccess;
+}
+
+// With the automatic schedule, time one direct application of R columns
+// (from zero, on workspace vectors) under each schedule and keep the faster
+// for R (same results either way up to the rounding of the tagged entries).
+cudaError_t decide_direct(silu_ilu F, int R) {
+  const int k = tri_slot(R);
+  if (F->direct_mode != 0 || F->direct_choice[k] != 0) return cudaSuccess;
+  cudaError_t e = ensure_vectors(F, R);
+  if (e != cudaSuccess) return e;
+  cudaStream_t s = F->ctx->stream;
+  const size_t vb = sizeof(double) * (size_t)F->F.L.n * (size_t)R;
+  double* bw = F->ws.p0.as<double>();
+  double* xw = F->ws.p1.as<double>();
+  e = cudaMemsetAsync(bw, 0, vb, s);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  float ms[2] = {0.f, 0.f};
+  const int64_t launches = F->ctx->launches;
+  const bool prof = F->ctx->profiling;
+  F->ctx->profiling = false;
+  try {
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+      F->direct_choice[k] = c == 0 ? 2 : 1;
+      direct_chunk(F, xw, bw, R, R, 0, true);  // warm-up (builds the level graph on first use)
+      CK(cudaEventRecord(ev[0], s));
+      direct_chunk(F, xw, bw, R, R, 0, true);
+      CK(cudaEventRecord(ev[1], s));
+      CK(cudaEventSynchronize(ev[1]));
+      CK(cudaEventElapsedTime(&ms[c], ev[0], ev[1]));
+    }
+  } catch (const CudaFail& f) {
+    e = f.e;
+  }
+  F->ctx->profiling = prof;
+  F->ctx->launches = launches;
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  F->direct_choice[k] = e == cudaSuccess ? (ms[0] <= ms[1] ? 2 : 1) : 0;
+  return e;
+}
+
 cudaError_t ensure_direct(silu_ilu F) {
   if (F->direct_ready) return cudaSuccess;
   F->ws.drop_graphs();  // captured solves refer to the arrays uploaded here
@@ -220,8 +387,12 @@ cudaError_t ensure_direct(silu_ilu F) {
   }
   e = upload(F->levLrows_d, F->levLrows.data(), F->levLrows.size(), s);
   if (e == cudaSuccess) e = upload(F->levUrows_d, F->levUrows.data(), F->levUrows.size(), s);
+  if (e == cudaSuccess) e = build_tri_plan(F);
+  if (e == cudaSuccess) e = ensure_tri(F, 1);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) F->direct_ready = true;
+  for (int& c : F->direct_choice) c = 0;  // the factors changed: decide again
+  if (e == cudaSuccess) e = decide_direct(F, 1);
   return e;
 }
 
@@ -499,6 +670,24 @@ void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
   double* y = F->ws.r.as<double>() + col;
   double* c = F->ws.c.as<double>() + col;
   const int gA = lanes_of(F->lanesA, F->autoA);
+  const int k = tri_slot(R);
+  const int schedule = F->direct_mode != 0 ? F->direct_mode : (F->direct_choice[k] != 0 ? F->direct_choice[k] : 2);
+  if (schedule == 2) {
+    // both solves and the update of x in one persistent launch
+    if (!F->tri_state[k].p) CK(cudaErrorNotReady);  // ensure_tri(F, R) runs before any capture
+    const double* r = b;
+    if (!x_zero) {
+      LAUNCH(F->ctx, SILU_K_RESIDUAL, sweep_launch(F, F->A->d, silu::MODE_D, R, gA, ldx, b, x, y, nullptr, nullptr,
+                                                    silu::EPI_STORE));
+      r = y;
+    }
+    const double* dcol = F->scale == SILU_SCALE_ROWCOL ? F->d_dcol.as<double>() : nullptr;  // x += D_c v
+    LAUNCH(F->ctx, SILU_K_LEVEL, silu::launch_trisolve(F->tri, R, r, ldx, F->d_dinv.as<double>(), dcol,
+                                                       F->tri_y[k].as<double>(), F->tri_v[k].as<double>(),
+                                                       F->tri_state[k].as<unsigned>(), x, ldx, x_zero,
+                                                       F->ctx->env.sms, F->ctx->env.err, s));
+    return;
+  }
   // built before y is written: building may run the graph on the workspace
   cudaGraphExec_t exec = inline_levels ? nullptr : level_graph(F, R, ldx, col);
   const bool overlap = F->ctx->env.overlap && F->level_overlap != 0;
@@ -932,6 +1121,15 @@ silu_status silu_ilu_set_kernel(silu_ilu F, int variant) {
   return SILU_OK;
 }
 
+silu_status silu_ilu_set_direct(silu_ilu F, int mode) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  if (mode < 0 || mode > 2) return set_err(F->ctx, SILU_ERR_INVALID_ARG, "direct mode must be 0, 1 or 2");
+  F->direct_mode = mode;
+  F->ws.drop_graphs();
+  F->config_gen++;
+  return SILU_OK;
+}
+
 silu_status silu_ilu_layout(silu_ilu F, double* pad_natural, double* pad_sorted, int32_t* in_use) {
   if (!F) return SILU_ERR_INVALID_ARG;
   const DevCsr* d[2] = {&F->dL, &F->dU};
@@ -1330,6 +1528,8 @@ silu_status direct_trisolve(silu_ilu F, double* x, const double* b, int nrhs) {
     CK(ensure_direct(F));
     for (int c0 = 0; c0 < nrhs;) {
       const int R = chunk_width(nrhs - c0);
+      CK(ensure_tri(F, R));
+      CK(decide_direct(F, R));
       direct_chunk(F, x + c0, b + c0, R, nrhs, (size_t)c0, false);
       c0 += R;
     }

@@ -123,8 +123,9 @@ constexpr int kL2Default = kFlagReverse;
 struct LaunchEnv {
   int sms = 0;          // multiprocessors of the device
   int* err = nullptr;   // err[0]: device error word (bit 0: a copy wait gave up,
-                        // bit 1: the self-test wait gave up); err[1]: a flag
-                        // that nothing sets (self-test)
+                        // bit 1: the self-test wait gave up, bit 2: a wait of
+                        // the persistent triangular solve gave up); err[1]: a
+                        // flag that nothing sets (self-test)
   bool overlap = true;  // staged sweeps launched as programmatic dependents of
                         // the kernel before them (prologue overlaps its tail)
   int l2 = kL2Default;  // L2 reuse flags of staged sweeps (kFlag* above)
@@ -167,6 +168,33 @@ cudaError_t staged_prepare();
 // overlap: launched as a programmatic dependent of the previous level.
 cudaError_t launch_level(const DevCsr& T, const int* rows, int nrows, int R, int lanes, int ldx, double* y,
                          const double* dinv, double* c_out, double* x, bool overlap, cudaStream_t s);
+
+// Both exact triangular solves of one application in one persistent launch
+// (kernels_trisolve.cu).  Rows of L_s and of the scaled strict upper factor
+// are stored in level order (row numbers in rowsL / rowsU, columns
+// unchanged); items are runs of at most 32 level-ordered rows of one level,
+// {first, last + 1, gate row or -1, gate in the upper solve}, the nitemsL
+// lower items first, then the upper ones.
+struct TriPlan {
+  int nitemsL = 0, nitems = 0;
+  const int* items = nullptr;  // 4 ints per item
+  const int* rowsL = nullptr;
+  const int* lrp = nullptr;
+  const int* lci = nullptr;
+  const double* lva = nullptr;
+  const int* rowsU = nullptr;
+  const int* urp = nullptr;
+  const int* uci = nullptr;
+  const double* uva = nullptr;
+};
+// y = L^{-1} r, c = dinv (.) y, v = Utilde^{-1} c, x (+)= (dcol (.)) v for R
+// right-hand sides (1, 2 or 4; r and x row-major with leading dimensions ldr
+// and ldx).  y, v (n x R doubles) and state (4 unsigned) belong to this R for
+// the factor object: zeroed once when allocated, then only this launch
+// touches them.  A wait that gives up sets bit 2 (value 4) of *err.
+cudaError_t launch_trisolve(const TriPlan& P, int R, const double* r, int ldr, const double* dinv, const double* dcol,
+                            double* y, double* v, unsigned* state, double* x, int ldx, bool x_zero, int sms, int* err,
+                            cudaStream_t s);
 
 // Elementwise helpers over n rows x R columns (leading dimension ldx).
 //  out(float or double) = scale ? dinv_i in : in      (in: double or float)

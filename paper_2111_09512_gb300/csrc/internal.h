@@ -195,6 +195,14 @@ struct silu_ilu_s {
   DevCsr dL64, dS64;
   bool direct_ready = false;
   int level_overlap = -1;  // levels launched as programmatic dependents: -1 undecided, 0 no, 1 yes
+  // persistent exact solves (kernels_trisolve.cu): level-ordered copies of L_s
+  // and the scaled strict upper factor, the item list, and per column count
+  // R = 1, 2, 4 the tagged vectors and the launch state
+  int direct_mode = 0;  // 0 automatic, 1 one launch per level, 2 one persistent launch per application
+  int direct_choice[3] = {0, 0, 0};  // automatic: schedule kept per column count (0 undecided)
+  DBuf tri_items, tri_lrp, tri_lci, tri_lva, tri_urp, tri_uci, tri_uva;
+  DBuf tri_y[3], tri_v[3], tri_state[3];
+  silu::TriPlan tri;
   int lanesL = 0, lanesU = 0, lanesA = 0;
   int64_t config_gen = 0;  // bumped whenever a launch shape changes (captured graphs go stale)
   int variant = 0;  // 0 auto, 1 plain lanes-per-row kernel, 2 staged kernel where possible
@@ -341,6 +349,13 @@ silu_status device_ok(silu_ctx ctx);
 cudaError_t ensure_vectors(silu_ilu F, int nrhs);
 cudaError_t ensure_krylov(silu_ilu F, int m);
 cudaError_t ensure_direct(silu_ilu F);
+// Level-ordered factor copies and items of the persistent exact solves.
+cudaError_t build_tri_plan(silu_ilu F);
+// Tagged vectors and launch state of the persistent solve for R columns.
+cudaError_t ensure_tri(silu_ilu F, int R);
+int tri_slot(int R);
+// Automatic schedule: time both on R columns once and keep the faster.
+cudaError_t decide_direct(silu_ilu F, int R);
 inline int lanes_of(int fixed, int autov) { return fixed > 0 ? fixed : autov; }
 cudaError_t sweep_launch(silu_ilu F, const DevCsr& T, Mode mode, int R, int lanes, int ldx, const void* c,
                          const void* in, void* out, const double* dinv, double* x, int epi);

@@ -11,11 +11,18 @@
 // The scratch array holds four vectors of kNoAllocMaxRows doubles (16 MiB);
 // every device that loads the library keeps it until the process exits.
 // Its device address is looked up once per device, with that device
-// current, on the first call that uses the device.  Every call shares the
-// array and it keeps whatever the previous call left in it; this entry point
-// writes each scratch vector before reading it, so nothing has to start at
-// zero.  Two calls whose work overlaps on the GPU (different streams, or
-// different host threads) race on the array.
+// current, on the first call that uses the device.  With CUDA's lazy module
+// loading (the default), that lookup is also what loads this file's device
+// code on the device and so reserves the 16 MiB: the first call on a device
+// can fail with SILU_ERR_OOM when the caller's pool already holds all device
+// memory, so callers make one call before their pool claims the memory (and
+// before any stream capture); from then on no call needs device memory.  The
+// address is cached for the life of the process, so calls after
+// cudaDeviceReset (or a reset of the primary context) are not supported.
+// Every call shares the array and it keeps whatever the previous call left
+// in it; this entry point writes each scratch vector before reading it, so
+// nothing has to start at zero.  Two calls whose work overlaps on the GPU
+// (different streams, or different host threads) race on the array.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -104,6 +111,11 @@ extern "C" silu_status silu_smooth_noalloc(int device, void* cuda_stream, int64_
   if (prev != device && cudaSetDevice(device) != cudaSuccess) return SILU_ERR_NO_DEVICE;
   double* scratch = nullptr;
   cudaError_t e = scratch_on(device, &scratch);
+  if (e == cudaErrorMemoryAllocation) {
+    // loading the array onto the device needs 16 MiB that are not free
+    if (prev != device) cudaSetDevice(prev);
+    return SILU_ERR_OOM;
+  }
   if (e == cudaSuccess)
     e = run(n, (cudaStream_t)cuda_stream, scratch, csr_view(n, A_rp, A_ci, A_val), csr_view(n, L_rp, L_ci, L_val),
             csr_view(n, U_rp, U_ci, U_val), dinv, x, b, sweeps_L, sweeps_U);

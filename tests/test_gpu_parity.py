@@ -147,19 +147,56 @@ DIRECT_CASES = [
 ]
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["auto", "per_level", "persistent"])
 @pytest.mark.parametrize("case", DIRECT_CASES, ids=[c[0] for c in DIRECT_CASES])
-def test_direct_trisolve_matches_oracle(silu, ctx, case):
+def test_direct_trisolve_matches_oracle(silu, ctx, case, mode):
     name, gen, kind, tau, fill, nrhs = case
     A = gen()
     n = len(A[0]) - 1
     F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), kind, tau, fill)
+    F.set_direct(mode)
     _, S = oracle_scaled(A, kind, tau, fill)
     b = synth.rhs(n, nrhs, seed=21)
     x0 = synth.rhs(n, nrhs, seed=22)
     want = oracle.direct_apply(A, S, x0, b)
     x = dev(x0.copy())
     silu.direct_trisolve(F, x, dev(b))
+    ctx.check()
     assert percol_relerr(host(x), want) < FP64_TOL
+
+
+def test_persistent_direct_over_many_solves(silu, ctx):
+    """The persistent solve alternates its readiness tag from solve to solve
+    and keeps separate tagged vectors per column count: a sequence of solves
+    with 1, 2, 4, 1, 3 (= 2 + 1), 4, 1 columns, from x != 0 and from x = 0
+    inside FGMRES, each equals the oracle; the per-level schedule of the same
+    factors agrees."""
+    A = synth.cutcell7(31, 27, 21, seed=14)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilut", 1e-3, 10)
+    F.set_direct(2)
+    _, S = oracle_scaled(A, "ilut", 1e-3, 10)
+    for k, R in enumerate([1, 2, 4, 1, 3, 4, 1]):
+        b = synth.rhs(n, R, seed=40 + k)
+        x0 = synth.rhs(n, R, seed=60 + k)
+        want = oracle.direct_apply(A, S, x0, b)
+        x = dev(x0.copy())
+        silu.direct_trisolve(F, x, dev(b))
+        ctx.check()
+        assert percol_relerr(host(x), want) < FP64_TOL, (k, R)
+    bv = synth.rhs(n, 1, seed=3)[:, 0]
+    res = {}
+    for mode in (2, 1, 2):
+        F.set_direct(mode)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st, its, rel = silu.fgmres_solve(F, x, dev(bv), tol=1e-10, restart=30, maxit=400, sweeps_L=0, sweeps_U=0,
+                                         precond=silu.PRECOND_DIRECT)
+        ctx.check()
+        assert st == silu.OK and rel <= 1e-10, (mode, st, its, rel)
+        res.setdefault(mode, []).append((its, host(x)))
+    assert abs(res[2][0][0] - res[1][0][0]) <= 1
+    assert relerr(res[2][0][1], res[1][0][1]) < 1e-8
+    assert res[2][0][0] == res[2][1][0] and np.array_equal(res[2][0][1], res[2][1][1])
 
 
 SORTED_CASES = [
