@@ -390,15 +390,19 @@ silu_status silu_ilu_set_lanes(silu_ilu F, int lanes_L, int lanes_U, int lanes_A
 
 /*
  * Sweep kernel variant: 0 = automatic (the staged kernel for one right-hand
- * side, the lanes-per-row kernel otherwise), 1 = always the lanes-per-row
- * kernel, 2 = the staged kernel wherever it applies, 3 = as 2 but on
- * length-sorted copies of the factors (built on first selection, for the
- * factors where silu_ilu_layout shows sorting pays; device memory for one
- * more copy of those factors).  The staged kernel
- * streams nnz-balanced row tiles of the factor into shared memory with bulk
- * asynchronous copies; it needs rows of at most 416 entries.  A sorted copy
- * keeps each row's entries in order, so with one lane per row variants 2 and
- * 3 give the same bits.
+ * side; for 2 or 4 interleaved right-hand sides the staged kernel on
+ * factors tiled one lane per row when the factor has at least 16 tiles per
+ * multiprocessor, the lanes-per-row kernel otherwise), 1 = always the
+ * lanes-per-row kernel, 2 = the staged kernel wherever it applies, 3 = as 2
+ * but on length-sorted copies of the factors for one right-hand side (built
+ * on first selection, for the factors where silu_ilu_layout shows sorting
+ * pays; device memory for one more copy of those factors).  The staged
+ * kernel streams nnz-balanced row tiles of the factor into shared memory
+ * with bulk asynchronous copies; it needs rows of at most 416 entries.  With
+ * R right-hand sides each staged factor entry feeds R FMAs, so the factor is
+ * read once per sweep for all of them.  A sorted copy keeps each row's
+ * entries in order, so with one lane per row variants 2 and 3 give the same
+ * bits.
  */
 silu_status silu_ilu_set_kernel(silu_ilu F, int variant);
 

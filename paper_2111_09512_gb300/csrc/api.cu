@@ -226,8 +226,8 @@ constexpr int kTriGateLevels = SILU_TRI_GATE_LEVELS;
 // offset o within level l >= g (g = kTriGateLevels) is the first row of the
 // item at offset min(o, items(l-g) - 1) of level l-g (items of one level
 // spread their gates over that level); levels below g have none (-1).
-void level_items(const std::vector<int32_t>& level_ptr, const std::vector<int32_t>& level_rows, int upper,
-                 std::vector<int32_t>& items) {
+int level_items(const std::vector<int32_t>& level_ptr, const std::vector<int32_t>& level_rows, int upper,
+                std::vector<int32_t>& items) {
   std::vector<int32_t> lev_first;  // first item (local index) of each level, then the end
   const size_t base = items.size() / 4;
   size_t local = 0;
@@ -252,6 +252,9 @@ void level_items(const std::vector<int32_t>& level_ptr, const std::vector<int32_
       items.push_back(upper);
     }
   }
+  int widest = 0;  // items of the widest level
+  for (size_t l = 0; l + 1 < lev_first.size(); ++l) widest = std::max(widest, lev_first[l + 1] - lev_first[l]);
+  return widest;
 }
 
 }  // namespace
@@ -262,9 +265,9 @@ cudaError_t build_tri_plan(silu_ilu F) {
   cudaStream_t s = F->ctx->stream;
   std::vector<int32_t> rp, ci, items;
   std::vector<double> va;
-  level_items(F->levLptr, F->levLrows, 0, items);
+  const int wideL = level_items(F->levLptr, F->levLrows, 0, items);
   const int nitemsL = (int)(items.size() / 4);
-  level_items(F->levUptr, F->levUrows, 1, items);
+  const int wideU = level_items(F->levUptr, F->levUrows, 1, items);
   cudaError_t e = upload(F->tri_items, items.data(), items.size(), s);
   // uploads are stream-ordered copies from these host vectors: wait before reusing them
   level_copy(F->F.L, F->levLrows, rp, ci, va);
@@ -282,6 +285,8 @@ cudaError_t build_tri_plan(silu_ilu F) {
   silu::TriPlan& P = F->tri;
   P.nitemsL = nitemsL;
   P.nitems = (int)(items.size() / 4);
+  // more warps than the items of a few levels would only wait on their gates
+  P.window = std::max(wideL, wideU) * (kTriGateLevels + 1);
   P.items = F->tri_items.as<int>();
   P.rowsL = F->levLrows_d.as<int>();
   P.lrp = F->tri_lrp.as<int>();
@@ -403,6 +408,13 @@ cudaError_t ensure_direct(silu_ilu F) {
 cudaError_t sweep_launch(silu_ilu F, const DevCsr& T, silu::Mode mode, int R, int lanes, int ldx, const void* c,
                          const void* in, void* out, const double* dinv, double* x, int epi) {
   cudaStream_t s = F->ctx->stream;
+  // several right-hand sides: the staged kernel reads each factor entry once
+  // for all R columns; on small systems (fewer tiles than a grid of warps
+  // has) its pipeline start costs more than it saves, unless a staged
+  // variant was asked for explicitly
+  if (R > 1 && F->variant != 1 && silu::staged_multi_ok(T, R) &&
+      (F->variant >= 2 || T.ntiles >= F->ctx->env.sms * 16))
+    return silu::launch_sweep_staged_multi(T, mode, F->ctx->env, R, ldx, c, in, out, dinv, x, epi, s);
   if (R == 1 && ldx == 1 && T.ntiles > 0 && F->variant != 1) {
     if (F->variant != 3 || T.nstiles == 0) return silu::launch_sweep_staged(T, mode, F->ctx->env, c, in, out, dinv, x, epi, s);
     DevCsr t = T;  // variant 3: the length-sorted copy

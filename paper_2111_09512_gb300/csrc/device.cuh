@@ -158,6 +158,13 @@ cudaError_t launch_sweep(const DevCsr& T, Mode mode, int R, int lanes, int ldx, 
 // row tiles of T into shared memory with bulk asynchronous copies.
 cudaError_t launch_sweep_staged(const DevCsr& T, Mode mode, const LaunchEnv& env, const void* c, const void* in,
                                 void* out, const double* dinv, double* x, int epi, cudaStream_t s);
+// The staged sweep for R = 2 or 4 interleaved right-hand sides (leading
+// dimension ldx >= R): each staged factor entry feeds R FMAs.  Needs a tile
+// partition with one lane per row (staged_multi_ok); natural row order.
+bool staged_multi_ok(const DevCsr& T, int R);
+cudaError_t launch_sweep_staged_multi(const DevCsr& T, Mode mode, const LaunchEnv& env, int R, int ldx, const void* c,
+                                      const void* in, void* out, const double* dinv, double* x, int epi,
+                                      cudaStream_t s);
 // Opt every staged-kernel instantiation into its shared-memory size on the
 // current device (done once per context, before any stream capture).
 cudaError_t staged_prepare();
@@ -177,6 +184,7 @@ cudaError_t launch_level(const DevCsr& T, const int* rows, int nrows, int R, int
 // lower items first, then the upper ones.
 struct TriPlan {
   int nitemsL = 0, nitems = 0;
+  int window = 0;  // items worth keeping in flight: the widest level's items times the gate distance + 1
   const int* items = nullptr;  // 4 ints per item
   const int* rowsL = nullptr;
   const int* lrp = nullptr;

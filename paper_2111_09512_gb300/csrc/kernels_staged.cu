@@ -229,7 +229,7 @@ struct StageLayout {
 // issue its copies into stage buffer `st` (three, or four with the row
 // numbers of a sorted layout).  The header store precedes the arrive on the
 // stage's mbarrier, so waiters see it.
-template <class MT, int RL, bool PERM>
+template <class MT, int RL, bool PERM, bool RP = true>
 __device__ __forceinline__ void issue_tile(int4 d, unsigned char* st, uint64_t* bar, const int* __restrict__ rp,
                                            const int* __restrict__ ci, const MT* __restrict__ va,
                                            const int* __restrict__ perm, uint64_t pol) {
@@ -241,15 +241,45 @@ __device__ __forceinline__ void issue_tile(int4 d, unsigned char* st, uint64_t* 
   const int m1 = (r1 + 3) & ~3;
   const uint32_t bv = (uint32_t)(a1 - a0) * (uint32_t)sizeof(MT);
   const uint32_t bc = (uint32_t)(c1 - c0) * 4u;
-  const uint32_t br = (uint32_t)(q1 - q0) * 4u;
+  const uint32_t br = RP ? (uint32_t)(q1 - q0) * 4u : 0u;
   const uint32_t bp = PERM ? (uint32_t)(m1 - q0) * 4u : 0u;
   *(int4*)st = d;
   fence_proxy_async();
   mbar_expect_tx(bar, bv + bc + br + bp);
   if (bv) bulk_g2s(st + L::kHdr, va + a0, bv, bar, pol);
   if (bc) bulk_g2s(st + L::kHdr + L::kVal, ci + c0, bc, bar, pol);
-  bulk_g2s(st + L::kHdr + L::kVal + L::kCol, rp + q0, br, bar, pol);
+  if (RP) bulk_g2s(st + L::kHdr + L::kVal + L::kCol, rp + q0, br, bar, pol);
   if (PERM && bp) bulk_g2s(st + L::kHdr + L::kVal + L::kCol + L::kRp, perm + q0, bp, bar, pol);
+}
+
+// Epilogue operands (dinv_row, x_row) are read after the accumulation; a
+// prefetch into L1 issued before it takes their memory latency off the end
+// of the tile without holding registers through the gathers.
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+__device__ __forceinline__ void prefetch_epilogue(int epi, int row, const double* dinv, const double* x) {
+  switch (epi) {
+    case EPI_SCALE:
+      prefetch_l1(dinv + row);
+      break;
+    case EPI_SCALE_ADDX:
+    case EPI_JAC_ADDX:
+      prefetch_l1(dinv + row);
+      prefetch_l1(x + row);
+      break;
+    case EPI_SCALE_SETX:
+    case EPI_JAC:
+    case EPI_JAC_SETX:
+      prefetch_l1(dinv + row);
+      break;
+    case EPI_ADDX:
+    case EPI_RICH_ADDX:
+      prefetch_l1(x + row);
+      break;
+    default:
+      break;
+  }
 }
 
 // t = c_row - (T in)_row, already formed by the accumulation
@@ -270,6 +300,62 @@ __device__ __forceinline__ void epilogue(int epi, int row, MT t, const VI* in, V
     case EPI_RICH_ADDX: x[row] += (double)(t + (MT)in[row]); break;
     case EPI_RICH_SETX: x[row] = (double)(t + (MT)in[row]); break;
     default: break;
+  }
+}
+
+// The same epilogues for column k of R interleaved right-hand sides: vector
+// entries at o = row * ldx + k, dinv at row.
+template <class MT, class VI, class VO>
+__device__ __forceinline__ void epilogue_col(int epi, int row, size_t o, MT t, const VI* in, VO* out,
+                                             const double* dinv, double* x, uint64_t keep) {
+  switch (epi) {
+    case EPI_STORE: st_keep(out + o, (VO)t, keep); break;
+    case EPI_SCALE: st_keep(out + o, (VO)(dinv[row] * (double)t), keep); break;
+    case EPI_ADDX: x[o] += (double)t; break;
+    case EPI_SETX: x[o] = (double)t; break;
+    case EPI_SCALE_ADDX: x[o] += dinv[row] * (double)t; break;
+    case EPI_SCALE_SETX: x[o] = dinv[row] * (double)t; break;
+    case EPI_JAC: st_keep(out + o, (VO)((MT)in[o] + (MT)dinv[row] * t), keep); break;
+    case EPI_JAC_ADDX: x[o] += (double)((MT)in[o] + (MT)dinv[row] * t); break;
+    case EPI_JAC_SETX: x[o] = (double)((MT)in[o] + (MT)dinv[row] * t); break;
+    case EPI_RICH: st_keep(out + o, (VO)(t + (MT)in[o]), keep); break;
+    case EPI_RICH_ADDX: x[o] += (double)(t + (MT)in[o]); break;
+    case EPI_RICH_SETX: x[o] = (double)(t + (MT)in[o]); break;
+    case EPI_SPMV: st_keep(out + o, (VO)t, keep); break;
+    default: break;
+  }
+}
+
+// R interleaved right-hand sides, one lane per row: acc[k] -/+= sum v[p]
+// in[col[p] ldx + k] over the row's entries in column order.  All gathers
+// of a chunk of CH entries (R values each, adjacent in memory) are issued
+// before the first FMA; the FMA loop runs to the warp's longest row.  One
+// factor entry read from shared memory feeds R FMAs.
+template <class MT, class VI, bool NEG, int R, int CH>
+__device__ __forceinline__ void row_accumulate_cols(const MT* sv, const int* sc, int len, const VI* __restrict__ in,
+                                                    int ldx, MT (&acc)[R], uint64_t keep) {
+  const int wmax = __reduce_max_sync(0xffffffffu, len);
+  for (int k0 = 0; k0 < wmax; k0 += CH) {
+    MT v[CH], xv[CH][R];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      if (k0 + q < len) {
+        v[q] = sv[k0 + q];
+        const VI* pin = in + (size_t)sc[k0 + q] * (size_t)ldx;
+#pragma unroll
+        for (int k = 0; k < R; ++k) xv[q][k] = (MT)ld_keep(pin + k, keep);
+      } else {
+        v[q] = MT(0);
+#pragma unroll
+        for (int k = 0; k < R; ++k) xv[q][k] = MT(0);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      if (k0 + q >= wmax) break;
+#pragma unroll
+      for (int k = 0; k < R; ++k) acc[k] = fma(NEG ? -v[q] : v[q], xv[q][k], acc[k]);
+    }
   }
 }
 
@@ -476,6 +562,285 @@ __global__ void __launch_bounds__(warps_of<MT>() * 32, 1)
   }
 }
 
+// R = 2 or 4 interleaved right-hand sides (row-major vectors, leading
+// dimension ldx >= R), one lane per row, natural row order, RL rows per
+// lane taken one after another: the factor tile is staged once and each of
+// its entries feeds R FMAs, so the factor is read once for all R columns.
+// The pipeline (per-warp two-stage ring of bulk copies, bounded waits,
+// programmatic launch, alternating direction) is k_sweep_staged's.
+template <class MT, class VI, class VO, int CH, int RL, int R>
+__global__ void __launch_bounds__(warps_of<MT>() * 32, 1)
+    k_sweep_multi(int ntiles, const int4* __restrict__ tiles, const int* __restrict__ rp, const int* __restrict__ ci,
+                  const MT* __restrict__ va, const VI* __restrict__ c, const VI* __restrict__ in, VO* __restrict__ out,
+                  int ldx, const double* __restrict__ dinv, double* __restrict__ x, int epi, int flags,
+                  int* __restrict__ err) {
+  using L = StageLayout<MT, RL, false>;
+  constexpr int kWarps = warps_of<MT>();
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kWarps][kWarpStages];
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int w = 0; w < kWarps; ++w)
+      for (int s = 0; s < kWarpStages; ++s) mbar_init(&full[w][s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int gw = blockIdx.x * kWarps + warp;
+  const int nw = gridDim.x * kWarps;
+  unsigned char* ring = smem + (size_t)warp * kWarpStages * L::kBytes;
+  const bool rev = (flags & kFlagReverse) != 0;
+  const uint64_t stream = (flags & kFlagFactorNormal) ? policy_evict_normal() : policy_evict_first();
+  const uint64_t keep = (flags & kFlagVectorNormal) ? policy_evict_normal() : policy_evict_last();
+  grid_launch_dependents();
+  if (lane == 0)
+    for (int s = 0; s < kWarpStages; ++s) {
+      const int t = gw + s * nw;
+      if (t < ntiles)
+        issue_tile<MT, RL, false>(__ldg(tiles + (rev ? ntiles - 1 - t : t)), ring + s * L::kBytes, &full[warp][s], rp,
+                                  ci, va, nullptr, stream);
+    }
+  grid_wait_prior();
+  int k = 0;
+  for (int t = gw; t < ntiles; t += nw, ++k) {
+    const int tn = t + kWarpStages * nw;
+    int4 dn = make_int4(0, 0, 0, 0);
+    if (lane == 0 && tn < ntiles) dn = __ldg(tiles + (rev ? ntiles - 1 - tn : tn));
+    const int s = k % kWarpStages;
+    const bool ok = mbar_wait_bounded(&full[warp][s], (uint32_t)(k / kWarpStages) & 1u);
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) {
+        atomicOr(err, 1);
+        for (int d = 1; d < kWarpStages; ++d) {
+          const int kd = k + d;
+          if (t + d * nw < ntiles) mbar_wait_bounded(&full[warp][kd % kWarpStages], (uint32_t)(kd / kWarpStages) & 1u);
+        }
+      }
+      return;
+    }
+    const unsigned char* st = ring + s * L::kBytes;
+    const int4 d = *(const int4*)st;
+    const MT* sv = (const MT*)(st + L::kHdr);
+    const int* sc = (const int*)(st + L::kHdr + L::kVal);
+    const int* sr = (const int*)(st + L::kHdr + L::kVal + L::kCol);
+    const int r0 = d.x, r1 = d.y, p0 = d.z;
+    const int q0 = r0 & ~3;
+    const int a0 = p0 & ~(L::kValAlign - 1);
+    const int c0 = p0 & ~3;
+#pragma unroll 1
+    for (int pass = 0; pass < RL; ++pass) {
+      const int r = r0 + pass * 32 + lane;
+      const bool act = r < r1;
+      const int b = act ? sr[r - q0] : p0;
+      const int len = act ? sr[r + 1 - q0] - b : 0;
+      const size_t o = (size_t)r * (size_t)ldx;
+      MT acc[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc[j] = (act && c) ? (MT)ld_keep(c + o + j, keep) : MT(0);
+      if (epi == EPI_SPMV)
+        row_accumulate_cols<MT, VI, false, R, CH>(sv + (b - a0), sc + (b - c0), len, in, ldx, acc, keep);
+      else
+        row_accumulate_cols<MT, VI, true, R, CH>(sv + (b - a0), sc + (b - c0), len, in, ldx, acc, keep);
+      if (act)
+#pragma unroll
+        for (int j = 0; j < R; ++j) epilogue_col<MT, VI, VO>(epi, r, o + j, acc[j], in, out, dinv, x, keep);
+    }
+    __syncwarp();
+    if (lane == 0 && tn < ntiles)
+      issue_tile<MT, RL, false>(dn, ring + s * L::kBytes, &full[warp][s], rp, ci, va, nullptr, stream);
+  }
+}
+
+template <class MT, class VI, class VO, int CH, int RL, int R>
+cudaError_t multi_attr() {
+  using L = StageLayout<MT, RL, false>;
+  const size_t smem = (size_t)warps_of<MT>() * kWarpStages * L::kBytes;
+  return cudaFuncSetAttribute(k_sweep_multi<MT, VI, VO, CH, RL, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+// Entries gathered before the FMAs with R columns (about the registers of
+// sixteen entries of one column).
+template <int R>
+constexpr int multi_chunk() {
+  return R == 2 ? 8 : 4;
+}
+
+template <class MT, class VI, class VO, int RL, int R>
+cudaError_t multi_g(const DevCsr& T, const LaunchEnv& env, int ldx, const void* c, const void* in, void* out,
+                    const double* dinv, double* x, int epi, cudaStream_t s) {
+  using L = StageLayout<MT, RL, false>;
+  constexpr int kWarps = warps_of<MT>();
+  constexpr int CH = multi_chunk<R>();
+  const int nt = T.ntiles;
+  if (nt == 0) return cudaSuccess;
+  const int want = (nt + kWarps - 1) / kWarps;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(want < env.sms ? want : env.sms));
+  cfg.blockDim = dim3(kWarps * 32);
+  cfg.dynamicSmemBytes = (size_t)kWarps * kWarpStages * L::kBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = env.overlap ? 1 : 0;
+  int flags = env.l2 & (kFlagFactorNormal | kFlagVectorNormal);
+  if ((env.l2 & kFlagReverse) && (env.flips++ & 1u)) flags |= kFlagReverse;
+  return cudaLaunchKernelEx(&cfg, k_sweep_multi<MT, VI, VO, CH, RL, R>, nt, (const int4*)T.tiles, (const int*)T.rp,
+                            (const int*)T.ci, (const MT*)T.va, (const VI*)c, (const VI*)in, (VO*)out, ldx, dinv, x,
+                            epi, flags, env.err);
+}
+
+template <class MT, class VI, class VO, int R>
+cudaError_t multi_rl(const DevCsr& T, const LaunchEnv& env, int ldx, const void* c, const void* in, void* out,
+                     const double* dinv, double* x, int epi, cudaStream_t s) {
+  if (T.tile_passes == 4) return multi_g<MT, VI, VO, 4, R>(T, env, ldx, c, in, out, dinv, x, epi, s);
+  if (T.tile_passes == 2) return multi_g<MT, VI, VO, 2, R>(T, env, ldx, c, in, out, dinv, x, epi, s);
+  return multi_g<MT, VI, VO, 1, R>(T, env, ldx, c, in, out, dinv, x, epi, s);
+}
+
+template <class MT, class VI, class VO>
+cudaError_t multi(const DevCsr& T, const LaunchEnv& env, int R, int ldx, const void* c, const void* in, void* out,
+                  const double* dinv, double* x, int epi, cudaStream_t s) {
+  if (R == 2) return multi_rl<MT, VI, VO, 2>(T, env, ldx, c, in, out, dinv, x, epi, s);
+  if (R == 4) return multi_rl<MT, VI, VO, 4>(T, env, ldx, c, in, out, dinv, x, epi, s);
+  return cudaErrorInvalidValue;
+}
+
+template <class MT, class VI, class VO>
+cudaError_t prepare_multi() {
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = multi_attr<MT, VI, VO, multi_chunk<2>(), 1, 2>();
+  if (e == cudaSuccess) e = multi_attr<MT, VI, VO, multi_chunk<2>(), 2, 2>();
+  if (e == cudaSuccess) e = multi_attr<MT, VI, VO, multi_chunk<2>(), 4, 2>();
+  if (e == cudaSuccess) e = multi_attr<MT, VI, VO, multi_chunk<4>(), 1, 4>();
+  if (e == cudaSuccess) e = multi_attr<MT, VI, VO, multi_chunk<4>(), 2, 4>();
+  if (e == cudaSuccess) e = multi_attr<MT, VI, VO, multi_chunk<4>(), 4, 4>();
+  return e;
+}
+
+__device__ __forceinline__ int4 shfl_int4(int4 v, int src) {
+  v.x = __shfl_sync(0xffffffffu, v.x, src);
+  v.y = __shfl_sync(0xffffffffu, v.y, src);
+  v.z = __shfl_sync(0xffffffffu, v.z, src);
+  v.w = __shfl_sync(0xffffffffu, v.w, src);
+  return v;
+}
+
+// The one-row-per-lane shape in natural row order (most factors): the same
+// sweep as k_sweep_staged, with the tile descriptors held by every lane in
+// registers and each lane's row bounds loaded from global memory one tile
+// ahead, so that a tile's critical path is the column-index read from
+// shared memory, the gather and the FMA chain, not a chain of dependent
+// shared-memory reads (descriptor, row pointers, columns).  The stage holds
+// only the values and column indices of the tile.  Each row still
+// accumulates c - sum t_ij in_j in column order, so the results are the
+// bits of k_sweep_staged.
+template <class MT, class VI, class VO, int CH>
+__global__ void __launch_bounds__(warps_of<MT>() * 32, 1)
+    k_sweep_rows(int ntiles, const int4* __restrict__ tiles, const int* __restrict__ rp, const int* __restrict__ ci,
+                 const MT* __restrict__ va, const VI* __restrict__ c, const VI* __restrict__ in, VO* __restrict__ out,
+                 const double* __restrict__ dinv, double* __restrict__ x, int epi, int flags, int* __restrict__ err) {
+  using L = StageLayout<MT, 1, false>;
+  constexpr int kWarps = warps_of<MT>();
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kWarps][kWarpStages];
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int w = 0; w < kWarps; ++w)
+      for (int s = 0; s < kWarpStages; ++s) mbar_init(&full[w][s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int gw = blockIdx.x * kWarps + warp;
+  const int nw = gridDim.x * kWarps;
+  unsigned char* ring = smem + (size_t)warp * kWarpStages * L::kBytes;
+  const bool rev = (flags & kFlagReverse) != 0;
+  const uint64_t stream = (flags & kFlagFactorNormal) ? policy_evict_normal() : policy_evict_first();
+  const uint64_t keep = (flags & kFlagVectorNormal) ? policy_evict_normal() : policy_evict_last();
+  grid_launch_dependents();
+  // descriptors of this warp's first two tiles, in every lane
+  int4 dcur = make_int4(0, 0, 0, 0), dnext = make_int4(0, 0, 0, 0);
+  if (lane == 0) {
+    if (gw < ntiles) dcur = __ldg(tiles + (rev ? ntiles - 1 - gw : gw));
+    if (gw + nw < ntiles) dnext = __ldg(tiles + (rev ? ntiles - 1 - (gw + nw) : gw + nw));
+    // the factor and its tiles are never written by a sweep: the first copies
+    // may start before the kernel that produced c and in has finished
+    if (gw < ntiles) issue_tile<MT, 1, false, false>(dcur, ring, &full[warp][0], rp, ci, va, nullptr, stream);
+    if (gw + nw < ntiles)
+      issue_tile<MT, 1, false, false>(dnext, ring + L::kBytes, &full[warp][1], rp, ci, va, nullptr, stream);
+  }
+  dcur = shfl_int4(dcur, 0);
+  dnext = shfl_int4(dnext, 0);
+  int rb = 0, re = 0;  // bounds of this lane's row of the current tile
+  if (dcur.x + lane < dcur.y) {
+    rb = __ldg(rp + dcur.x + lane);
+    re = __ldg(rp + dcur.x + lane + 1);
+  }
+  grid_wait_prior();  // c, in, out and x below belong to the previous kernel until it completes
+  int k = 0;
+  for (int t = gw; t < ntiles; t += nw, ++k) {
+    const int tn = t + kWarpStages * nw;
+    int4 dn = make_int4(0, 0, 0, 0);
+    if (lane == 0 && tn < ntiles) dn = __ldg(tiles + (rev ? ntiles - 1 - tn : tn));
+    // bounds of this lane's row of the next tile, a whole tile ahead
+    int nb = 0, ne = 0;
+    if (t + nw < ntiles && dnext.x + lane < dnext.y) {
+      nb = __ldg(rp + dnext.x + lane);
+      ne = __ldg(rp + dnext.x + lane + 1);
+    }
+    const int s = k % kWarpStages;
+    const bool ok = mbar_wait_bounded(&full[warp][s], (uint32_t)(k / kWarpStages) & 1u);
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) {
+        atomicOr(err, 1);
+        for (int d = 1; d < kWarpStages; ++d) {
+          const int kd = k + d;
+          if (t + d * nw < ntiles) mbar_wait_bounded(&full[warp][kd % kWarpStages], (uint32_t)(kd / kWarpStages) & 1u);
+        }
+      }
+      return;
+    }
+    const unsigned char* st = ring + s * L::kBytes;
+    const MT* sv = (const MT*)(st + L::kHdr);
+    const int* sc = (const int*)(st + L::kHdr + L::kVal);
+    const int r = dcur.x + lane;
+    const bool act = r < dcur.y;
+    const int a0 = dcur.z & ~(L::kValAlign - 1);
+    const int c0 = dcur.z & ~3;
+    const int len = act ? re - rb : 0;
+    const int off = act ? rb : dcur.z;  // inactive lanes read nothing
+    MT acc = (act && c) ? (MT)ld_keep(c + r, keep) : MT(0);
+    if (act) prefetch_epilogue(epi, r, dinv, x);
+    if (epi == EPI_SPMV)
+      acc = row_accumulate<MT, VI, false, 1, CH>(sv + (off - a0), sc + (off - c0), len, 0, in, acc, keep);
+    else
+      acc = row_accumulate<MT, VI, true, 1, CH>(sv + (off - a0), sc + (off - c0), len, 0, in, acc, keep);
+    if (act) {
+      if (epi == EPI_SPMV)
+        st_keep(out + r, (VO)acc, keep);
+      else
+        epilogue<MT, VI, VO>(epi, r, acc, in, out, dinv, x, keep);
+    }
+    __syncwarp();
+    if (lane == 0 && tn < ntiles)
+      issue_tile<MT, 1, false, false>(dn, ring + s * L::kBytes, &full[warp][s], rp, ci, va, nullptr, stream);
+    dcur = dnext;
+    dnext = shfl_int4(dn, 0);
+    rb = nb;
+    re = ne;
+  }
+}
+
+template <class MT, class VI, class VO, int CH>
+cudaError_t rows_attr() {
+  using L = StageLayout<MT, 1, false>;
+  const size_t smem = (size_t)warps_of<MT>() * kWarpStages * L::kBytes;
+  return cudaFuncSetAttribute(k_sweep_rows<MT, VI, VO, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 template <class MT, class VI, class VO, int G, int CH, int RL, bool PERM>
 cudaError_t staged_attr() {
   using L = StageLayout<MT, RL, PERM>;
@@ -508,6 +873,11 @@ cudaError_t staged_g(const DevCsr& T, const LaunchEnv& env, const void* c, const
   // the previous one touched last, while they are still in L2
   int flags = env.l2 & (kFlagFactorNormal | kFlagVectorNormal);
   if ((env.l2 & kFlagReverse) && (env.flips++ & 1u)) flags |= kFlagReverse;
+  if constexpr (G == 1 && RL == 1 && !PERM) {
+    return cudaLaunchKernelEx(&cfg, k_sweep_rows<MT, VI, VO, CH>, nt, (const int4*)T.tiles, (const int*)T.rp,
+                              (const int*)T.ci, (const MT*)T.va, (const VI*)c, (const VI*)in, (VO*)out, dinv, x, epi,
+                              flags, env.err);
+  }
   if (PERM)
     return cudaLaunchKernelEx(&cfg, k_sweep_staged<MT, VI, VO, G, CH, RL, PERM>, nt, (const int4*)T.stiles,
                               (const int*)T.srp, (const int*)T.sci, (const MT*)T.sva, (const int*)T.perm,
@@ -543,6 +913,10 @@ template <class MT, class VI, class VO, int G, int RL, bool PERM>
 cudaError_t prepare_shape() {
   cudaError_t e = staged_attr<MT, VI, VO, G, 8, RL, PERM>();
   if (e == cudaSuccess) e = staged_attr<MT, VI, VO, G, 16, RL, PERM>();
+  if (G == 1 && RL == 1 && !PERM) {
+    if (e == cudaSuccess) e = rows_attr<MT, VI, VO, 8>();
+    if (e == cudaSuccess) e = rows_attr<MT, VI, VO, 16>();
+  }
   return e;
 }
 
@@ -580,7 +954,26 @@ cudaError_t staged_prepare() {
   cudaError_t e = prepare_mode<double, double, double>();
   if (e == cudaSuccess) e = prepare_mode<float, float, float>();
   if (e == cudaSuccess) e = prepare_mode<double, double, float>();
+  if (e == cudaSuccess) e = prepare_multi<double, double, double>();
+  if (e == cudaSuccess) e = prepare_multi<float, float, float>();
+  if (e == cudaSuccess) e = prepare_multi<double, double, float>();
   return e;
+}
+
+bool staged_multi_ok(const DevCsr& T, int R) {
+  return (R == 2 || R == 4) && T.ntiles > 0 && T.tile_lanes == 1;
+}
+
+cudaError_t launch_sweep_staged_multi(const DevCsr& T, Mode mode, const LaunchEnv& env, int R, int ldx, const void* c,
+                                      const void* in, void* out, const double* dinv, double* x, int epi,
+                                      cudaStream_t s) {
+  if (!staged_multi_ok(T, R) || ldx < R) return cudaErrorInvalidValue;
+  switch (mode) {
+    case MODE_D: return multi<double, double, double>(T, env, R, ldx, c, in, out, dinv, x, epi, s);
+    case MODE_F: return multi<float, float, float>(T, env, R, ldx, c, in, out, dinv, x, epi, s);
+    case MODE_DF: return multi<double, double, float>(T, env, R, ldx, c, in, out, dinv, x, epi, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_sweep_staged(const DevCsr& T, Mode mode, const LaunchEnv& env, const void* c, const void* in,

@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kTriThreads, tri_min_blocks<R>()) k_trisolve(T
 }
 
 template <int R>
-cudaError_t trisolve_r(TriArgs a, int sms, cudaStream_t s) {
+cudaError_t trisolve_r(TriArgs a, int window, int sms, cudaStream_t s) {
   static int occ = 0;  // resident blocks per SM (same on every GB300)
   if (occ == 0) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trisolve<R>, kTriThreads, 0);
@@ -345,7 +345,8 @@ cudaError_t trisolve_r(TriArgs a, int sms, cudaStream_t s) {
     if (occ < 1) occ = 1;
     if (occ > kTriMaxBlocksPerSm) occ = kTriMaxBlocksPerSm;
   }
-  const int want = (a.nitems + kTriThreads / 32 - 1) / (kTriThreads / 32);
+  const int items = window < a.nitems ? window : a.nitems;
+  const int want = (items + kTriThreads / 32 - 1) / (kTriThreads / 32);
   int blocks = sms * occ;
   if (blocks > want) blocks = want;
   if (blocks < 1) return cudaSuccess;
@@ -385,9 +386,9 @@ cudaError_t launch_trisolve(const TriPlan& P, int R, const double* r, int ldr, c
   a.total_warps = 0;
   a.err = err;
   switch (R) {
-    case 1: return trisolve_r<1>(a, sms, s);
-    case 2: return trisolve_r<2>(a, sms, s);
-    case 4: return trisolve_r<4>(a, sms, s);
+    case 1: return trisolve_r<1>(a, P.window > 0 ? P.window : P.nitems, sms, s);
+    case 2: return trisolve_r<2>(a, P.window > 0 ? P.window : P.nitems, sms, s);
+    case 4: return trisolve_r<4>(a, P.window > 0 ? P.window : P.nitems, sms, s);
   }
   return cudaErrorInvalidValue;
 }
