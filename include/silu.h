@@ -130,7 +130,8 @@ typedef enum {
   SILU_K_LEVEL = 3,       /* level-scheduled substitution (direct_trisolve)     */
   SILU_K_KRYLOV = 4,      /* FGMRES dots, Gram-Schmidt, Givens, update          */
   SILU_K_ELEMENTWISE = 5, /* scaling, casts, x updates                          */
-  SILU_K_NCLASS = 6
+  SILU_K_FUSED = 6,       /* a whole smoother application in one launch         */
+  SILU_K_NCLASS = 7
 } silu_kclass;
 
 /*
@@ -312,6 +313,23 @@ silu_status direct_trisolve(silu_ilu F, double* x, const double* b, int nrhs);
  * timed once), 1 one launch per level, 2 one persistent launch.  Other
  * values -> SILU_ERR_INVALID_ARG. */
 silu_status silu_ilu_set_direct(silu_ilu F, int mode);
+
+/*
+ * Fused smoother application (no counterpart in the paper; it concerns only
+ * how the steps of Alg. ILUJac are launched).  With row or row/column
+ * scaling and 1, 2 or 4 right-hand sides per column block, ilu_smooth (and
+ * the smoother inside fgmres_solve) can run the whole application -- the
+ * residual, the sweeps on L_s and on the scaled upper factor and the update
+ * of x -- in one cooperative launch whose steps are separated by grid-wide
+ * barriers, instead of one launch per sweep.  Same step sequence, same
+ * per-row summation order.  mode 0 (default): fused for 2 or 4 columns of
+ * systems of at most 131072 rows, where launches dominate (one column runs
+ * as fast through the staged sweeps, each launched as a programmatic
+ * dependent of the one before); 1 never; 2 always.  Every barrier
+ * wait is bounded (2 s); one that gives up makes the next silu_ctx_check
+ * return SILU_ERR_TIMEOUT.  Other modes -> SILU_ERR_INVALID_ARG.
+ */
+silu_status silu_ilu_set_fused(silu_ilu F, int mode);
 
 /*
  * Right-preconditioned flexible GMRES(restart) on A x = b for one right-hand

@@ -37,7 +37,7 @@ FP64, FP32 = 0, 1
 PRECOND_SWEEPS, PRECOND_DIRECT, PRECOND_NONE, PRECOND_AMG, PRECOND_AMG_DIRECT, PRECOND_SCHUR = 0, 1, 2, 3, 4, 5
 # silu_kclass
 K_RESIDUAL, K_SWEEP_L, K_SWEEP_U, K_LEVEL, K_KRYLOV, K_ELEMENTWISE = range(6)
-K_NAMES = ["residual", "sweep_L", "sweep_U", "level", "krylov", "elementwise"]
+K_NAMES = ["residual", "sweep_L", "sweep_U", "level", "krylov", "elementwise", "fused"]
 
 KINDS = {"ilu0": ILU0, "iluk": ILUK, "ilut": ILUT, "gs": GS, "sgs": SGS}
 
@@ -121,6 +121,7 @@ def load():
         "silu_ctx_selftest_timeout": (i32, [vp, i32]),
         "silu_ilu_set_kernel": (i32, [vp, i32]),
         "silu_ilu_set_direct": (i32, [vp, i32]),
+        "silu_ilu_set_fused": (i32, [vp, i32]),
         "silu_ilu_layout": (i32, [vp, vp, vp, vp]),
         "silu_ctx_set_overlap": (i32, [vp, i32]),
         "silu_ctx_set_l2_reuse": (i32, [vp, i32]),
@@ -158,7 +159,7 @@ def exported_symbols():
             "silu_amg_stats", "silu_amg_export_level", "silu_schur_setup", "silu_schur_smooth",
             "silu_schur_stats",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
-            "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_set_direct", "silu_ilu_layout", "silu_ilu_tune_table", "silu_ctx_set_overlap",
+            "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_set_direct", "silu_ilu_set_fused", "silu_ilu_layout", "silu_ilu_tune_table", "silu_ctx_set_overlap",
             "silu_ctx_set_l2_reuse",
             "silu_smooth_noalloc",
             "silu_batch_setup", "silu_batch_info", "silu_batch_smooth", "silu_batch_fgmres", "silu_batch_destroy",
@@ -479,6 +480,11 @@ class ILU:
         """Schedule of the exact triangular solves: 0 automatic (default; the faster of the two, timed
         once per column count), 1 one launch per level (captured graph), 2 one persistent launch."""
         _check(self.ctx.handle, load().silu_ilu_set_direct(self.handle, mode), "silu_ilu_set_direct")
+
+    def set_fused(self, mode: int):
+        """Whole smoother application in one cooperative launch: 0 for small systems (default), 1 never,
+        2 always."""
+        _check(self.ctx.handle, load().silu_ilu_set_fused(self.handle, mode), "silu_ilu_set_fused")
 
     def layout(self):
         """FMA slots per entry of one-lane-per-row tiles, natural and length-sorted rows, for

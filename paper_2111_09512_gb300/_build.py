@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsilu.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["kernels_sweep.cu", "kernels_staged.cu", "kernels_krylov.cu", "kernels_trisolve.cu", "api.cu", "batch.cu", "server.cu", "noalloc.cu", "diag.cu", "amg.cu", "schur.cu"]
+CU_SOURCES = ["kernels_sweep.cu", "kernels_staged.cu", "kernels_krylov.cu", "kernels_trisolve.cu", "kernels_fused.cu", "api.cu", "batch.cu", "server.cu", "noalloc.cu", "diag.cu", "amg.cu", "schur.cu"]
 CXX_SOURCES = ["host_factor.cpp", "amg_setup.cpp"]
 
 

@@ -429,6 +429,16 @@ cudaError_t sweep_launch(silu_ilu F, const DevCsr& T, silu::Mode mode, int R, in
 // workspace pointers offset by the same column.  x_zero: x is an output only
 // (zero initial guess, so r = b and the result is stored, not added).
 // ---------------------------------------------------------------------------
+// Whether one application of R columns runs as one fused cooperative launch:
+// row-scaled factors (row or row/column scaling), R = 1, 2 or 4, and, in the
+// automatic mode, several columns of a system small enough that launches
+// dominate (with one column the staged sweeps, each launched as a
+// programmatic dependent of the one before, are as fast on small systems).
+bool use_fused(silu_ilu F, int R) {
+  if (F->fused_mode == 1 || !scaled_upper(F) || (R != 1 && R != 2 && R != 4)) return false;
+  return F->fused_mode == 2 || (R > 1 && F->F.L.n <= kFusedMaxRows);
+}
+
 void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, int mL, int mU, bool x_zero) {
   cudaStream_t s = F->ctx->stream;
   const bool f32 = F->prec == SILU_FP32;
@@ -441,6 +451,14 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
   char* bufC = F->ws.c.as<char>() + col * es;
   char* bufP0 = F->ws.p0.as<char>() + col * es;
   char* bufP1 = F->ws.p1.as<char>() + col * es;
+  if (use_fused(F, R)) {
+    const bool rc = F->scale == SILU_SCALE_ROWCOL;
+    LAUNCH(F->ctx, SILU_K_FUSED,
+           silu::launch_smooth_fused(A, F->dL, F->dU, f32, R, ldx, mL, mU, x_zero, rc, dinv,
+                                     rc ? F->d_dcol.as<double>() : nullptr, b, x, bufR, bufC, bufP0, bufP1,
+                                     (unsigned*)(F->ctx->env.err + 2), F->ctx->env.sms, F->ctx->env.err, s));
+    return;
+  }
   const int gL = lanes_of(F->lanesL, F->autoL), gU = lanes_of(F->lanesU, F->autoU), gA = lanes_of(F->lanesA, F->autoA);
   const bool rowscale = scaled_upper(F);
   const bool rowcol = F->scale == SILU_SCALE_ROWCOL;
@@ -897,8 +915,8 @@ silu_status silu_ctx_create(int device, void* cuda_stream, silu_ctx* out) {
     e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->pinned, 64 * sizeof(double));
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->env.sms, cudaDevAttrMultiProcessorCount, device);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->env.err, 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(c->env.err, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->env.err, 4 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->env.err, 0, 4 * sizeof(int));
     if (e == cudaSuccess) e = silu::staged_prepare();
     if (e != cudaSuccess) {
       delete c;
@@ -973,6 +991,9 @@ silu_status silu_ctx_check(silu_ctx ctx) {
   int flag = 0;
   e = cudaMemcpy(&flag, ctx->env.err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess && flag) e = cudaMemset(ctx->env.err, 0, sizeof(int));
+  // a fused application that gave up at a grid barrier may have left the
+  // barrier's arrival count behind: start the next one from a clean state
+  if (e == cudaSuccess && (flag & 8)) e = cudaMemset(ctx->env.err + 2, 0, 2 * sizeof(int));
   if (e != cudaSuccess) return cuda_err(ctx, e, "error word read-back");
   if (flag) return set_err(ctx, SILU_ERR_TIMEOUT, "a bounded device wait gave up; results of the affected calls are invalid");
   return SILU_OK;
@@ -1128,6 +1149,15 @@ silu_status silu_ilu_set_kernel(silu_ilu F, int variant) {
     if (e != cudaSuccess) return cuda_err(F->ctx, e, "upload of the sorted factor copies");
   }
   F->variant = variant;
+  F->ws.drop_graphs();
+  F->config_gen++;
+  return SILU_OK;
+}
+
+silu_status silu_ilu_set_fused(silu_ilu F, int mode) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  if (mode < 0 || mode > 2) return set_err(F->ctx, SILU_ERR_INVALID_ARG, "fused mode must be 0, 1 or 2");
+  F->fused_mode = mode;
   F->ws.drop_graphs();
   F->config_gen++;
   return SILU_OK;

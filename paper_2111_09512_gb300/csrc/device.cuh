@@ -124,8 +124,10 @@ struct LaunchEnv {
   int sms = 0;          // multiprocessors of the device
   int* err = nullptr;   // err[0]: device error word (bit 0: a copy wait gave up,
                         // bit 1: the self-test wait gave up, bit 2: a wait of
-                        // the persistent triangular solve gave up); err[1]: a
-                        // flag that nothing sets (self-test)
+                        // the persistent triangular solve gave up, bit 3: a
+                        // grid barrier of the fused smoother gave up); err[1]:
+                        // a flag that nothing sets (self-test); err[2..3]: the
+                        // fused smoother's grid-barrier words
   bool overlap = true;  // staged sweeps launched as programmatic dependents of
                         // the kernel before them (prologue overlaps its tail)
   int l2 = kL2Default;  // L2 reuse flags of staged sweeps (kFlag* above)
@@ -203,6 +205,18 @@ struct TriPlan {
 cudaError_t launch_trisolve(const TriPlan& P, int R, const double* r, int ldr, const double* dinv, const double* dcol,
                             double* y, double* v, unsigned* state, double* x, int ldx, bool x_zero, int sms, int* err,
                             cudaStream_t s);
+
+// One smoother application with row-scaled (rowcol: row/column scaled)
+// factors in one cooperative launch (kernels_fused.cu): the residual, the
+// sweeps on Ls and Us and the update of x, separated by grid-wide barriers
+// on bar[0..1] (two words zeroed once; each barrier leaves them consistent).
+// Same step sequence and vectors (r, c, p0, p1: the workspace, FP32 when
+// f32) as the launch-per-sweep path.  A barrier wait that gives up sets bit
+// 3 (value 8) of *err.
+cudaError_t launch_smooth_fused(const DevCsr& A, const DevCsr& Ls, const DevCsr& Us, bool f32, int R, int ldx,
+                                int mL, int mU, bool x_zero, bool rowcol, const double* dinv, const double* dcol,
+                                const double* b, double* x, void* r, void* c, void* p0, void* p1, unsigned* bar,
+                                int sms, int* err, cudaStream_t s);
 
 // Elementwise helpers over n rows x R columns (leading dimension ldx).
 //  out(float or double) = scale ? dinv_i in : in      (in: double or float)

@@ -199,6 +199,7 @@ struct silu_ilu_s {
   // and the scaled strict upper factor, the item list, and per column count
   // R = 1, 2, 4 the tagged vectors and the launch state
   int direct_mode = 0;  // 0 automatic, 1 one launch per level, 2 one persistent launch per application
+  int fused_mode = 0;   // smoother in one cooperative launch: 0 for small systems, 1 never, 2 always
   int direct_choice[3] = {0, 0, 0};  // automatic: schedule kept per column count (0 undecided)
   DBuf tri_items, tri_lrp, tri_lci, tri_lva, tri_urp, tri_uci, tri_uva;
   DBuf tri_y[3], tri_v[3], tri_state[3];
@@ -376,6 +377,9 @@ void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_ze
 // z = M^{-1} r of F's Schur complement smoother (one right-hand side,
 // device vectors of n entries; z is written).  Requires F->schur.
 void schur_apply(silu_ilu F, const double* r, double* z, int mL, int mU);
+// Systems of at most this many rows apply the smoother in one fused
+// cooperative launch by default (silu_ilu_set_fused).
+constexpr int64_t kFusedMaxRows = 131072;
 // Ruiz equilibration limits for SILU_SCALE_ROWCOL.
 constexpr int kRuizMaxit = 20;
 constexpr double kRuizTol = 1e-2;
