@@ -1092,6 +1092,64 @@ def sweep_study(silu, ctx, torch):
     return out
 
 
+def run_apply_only(args):
+    """Only smoother applications of one workload, for profiling and quick
+    timing: W untimed and K timed applications from x = 0 on one GPU, one
+    JSON line (time per application, algorithmic GB/s, per-class split).
+      cutcell128: the headline workload (128^3 cut-cell, ILUT(1e-3,10), FP64,
+                  10+10 sweeps, 1 RHS; 19 launches per application)
+      hex27_256:  the 27-point 256^3 perturbed-hex matrix, ILU(0) factors in
+                  FP32, 3+3 FP32 sweeps, FP64 residual (5 launches each)
+      cutcell128_r4: the headline factors with 4 interleaved right-hand sides"""
+    import torch
+    import paper_2111_09512_gb300 as silu
+    import synth
+    silu.build()
+    stream = torch.cuda.current_stream()
+    ctx = silu.Context(0, stream)
+    w = args.apply_only
+    if w in ("cutcell128", "cutcell128_r4"):
+        A = synth.cutcell7(EDGE, seed=1)
+        kind, prec, mL, mU, vb = "ilut", silu.FP64, ML, MU, 8
+        R = 4 if w.endswith("r4") else 1
+    elif w == "hex27_256":
+        A = synth.hex27(256, seed=2)
+        kind, prec, mL, mU, vb, R = "ilu0", silu.FP32, 3, 3, 4, 1
+    else:
+        raise SystemExit(f"unknown workload {w}")
+    n = len(A[0]) - 1
+    nnzA = len(A[1])
+    M = silu.Matrix(ctx, *A)
+    del A
+    F = silu.ilu_setup(ctx, M, kind, TAU, FILL, prec=prec)
+    st = F.stats()
+    b = torch.from_numpy(synth.rhs(n, R, seed=1)).cuda()
+    x = torch.zeros(n, R, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        x.zero_()
+        silu.ilu_smooth(F, x, b, mL, mU)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        silu.ilu_smooth(F, x, b, mL, mU)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    ms = e0.elapsed_time(e1) / args.steps
+    # applications from the second on start from x != 0: residual + (mL-1) + (mU-1) sweeps
+    nbytes = (resid_bytes(n, nnzA, R) + (mL - 1) * sweep_bytes(n, st["nnz_L"], R, vb) + 8 * n
+              + (mU - 1) * sweep_bytes(n, st["nnz_U"], R, vb) + 8 * n * R)
+    line = {"apply_only": w, "rows": n, "rhs": R, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_application": round(ms, 5), "algorithmic_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+            "launches_per_application": {k: v[0] // args.steps for k, v in prof.items() if v[0]},
+            "kernel_ms_per_launch": {k: round(v[1] / v[0], 5) for k, v in prof.items() if v[0]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -1119,6 +1177,8 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-queue", type=int, default=8)
     ap.add_argument("--serve-pool", type=int, default=32)
+    ap.add_argument("--apply-only", choices=["cutcell128", "cutcell128_r4", "hex27_256"], default=None,
+                    help="run only smoother applications of one workload (profiling, quick timing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
@@ -1126,6 +1186,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.apply_only:
+        return run_apply_only(args)
     return run_silu(args)
 
 
