@@ -115,7 +115,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "25"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
             return
@@ -423,6 +423,7 @@ def run_silu(args):
     amg = amg_comparison(silu, ctx, torch, args.amg_edge) if (args.amg_edge > 0 and rank == 0) else None
 
     p32 = poisson32(silu, ctx, torch) if rank == 0 else None
+    mrhs = multi_rhs(silu, ctx, torch, F, n, nnzA, nnzL, nnzU) if rank == 0 else None
     f32err = fp32_error(silu, ctx, torch) if rank == 0 else None
     study = None
     if rank == 0 and args.study:
@@ -479,6 +480,8 @@ def run_silu(args):
             line["amg"] = amg
         if p32:
             line["poisson32"] = p32
+        if mrhs:
+            line["multi_rhs"] = mrhs
         if f32err:
             line["fp32_error"] = f32err
         if study:
@@ -869,6 +872,32 @@ def fp32_error(silu, ctx, torch):
         st, its, rel = silu.fgmres_solve(F, x, b[:, 0].contiguous(), tol=1e-8, restart=30, maxit=5000,
                                          sweeps_L=3, sweeps_U=3)
         out[name] = {"iterations": its, "relres": float(f"{rel:.3e}"), "converged": st == silu.OK}
+    return out
+
+
+def multi_rhs(silu, ctx, torch, F, n, nnzA, nnzL, nnzU):
+    """The headline factors with 4 interleaved right-hand sides (seed 5): one
+    10+10 application reads each factor once per sweep for all four columns
+    (the FP64 pipe bounds it: 4 FMAs per stored entry); time per application
+    and per column against one column."""
+    import synth
+    out = {"workload": WORKLOAD.replace("1 RHS", "4 RHS")}
+    for R in (1, 4):
+        b = torch.from_numpy(synth.rhs(n, R, seed=5)).cuda()
+        x = torch.zeros(n, R, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            silu.ilu_smooth(F, x, b, ML, MU)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            silu.ilu_smooth(F, x, b, ML, MU)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        nbytes = apply_bytes(n, nnzA, nnzL, nnzU, R, 8, ML, MU)
+        out[f"rhs_{R}"] = {"ms": round(ms, 4), "ms_per_column": round(ms / R, 4),
+                           "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1)}
     return out
 
 
