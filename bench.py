@@ -78,10 +78,10 @@ def sweep_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """Per-launch DRAM bytes of the sweep kernel from the committed ncu summary,
-    or None when the kernel source changed since the counters were taken."""
-    p = os.path.join(ROOT, "profiles", "k_sweep_cutcell128_ilut_traffic.txt")
+def recorded_values(name):
+    """key = value lines of a committed ncu traffic summary under profiles/, or
+    None when the kernel source changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     vals = {}
@@ -92,8 +92,14 @@ def recorded_traffic():
                 vals[k.strip()] = v.strip()
     if vals.get("source_hash") != sweep_source_hash():
         return None
+    return vals
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the sweep kernel on the headline workload."""
+    vals = recorded_values("k_sweep_cutcell128_ilut_traffic.txt")
     try:
-        return float(vals["dram_bytes_per_sweep_launch"])
+        return float(vals["dram_bytes_per_sweep_launch"]) if vals else None
     except (KeyError, ValueError):
         return None
 
@@ -518,8 +524,8 @@ def class_split(ctx, torch, fn, reps: int, cls_bytes: dict) -> dict:
 def solve_comparison(silu, ctx, torch, edge: int):
     """The 27-point workload: FGMRES(30) to 1e-10 relative residual with the
     FP32 scaled-ILU(0) Richardson smoother (3+3 FP32 sweeps, FP64 residual and
-    Krylov) against FGMRES(30) with FP64 level-scheduled direct triangular
-    solves of the same factors, on the 27-point perturbed-hex Laplacian
+    Krylov) against FGMRES(30) with FP64 exact triangular solves of the same
+    factors (the faster of the persistent and the per-level schedule), on the 27-point perturbed-hex Laplacian
     (edge^3 rows; 256^3 = 16.8M rows, 449M entries).  Also the FP32 smoother
     application's algorithmic GB/s."""
     import synth
@@ -559,6 +565,20 @@ def solve_comparison(silu, ctx, torch, edge: int):
                          "sweep_U": sweep_bytes(n, st["nnz_U"], 1, 4)})
     out["fp32_apply"] = {"ms": round(ms, 4), "gbs": round(nbytes / (ms * 1e-3) / 1e9, 1), "bytes": nbytes,
                          "kernels": split}
+    # fraction of the measured HBM bandwidth by DRAM bytes: the recorded per-launch traffic of this
+    # workload's sweeps (full size, live L2 state) over this run's mean launch durations
+    rec = recorded_values("k_sweep_hex27_256_fp32_traffic.txt") if edge == 256 else None
+    if rec:
+        peak, kind = load_peaks()
+        dram = {}
+        for cls, key in (("sweep_L", "dram_bytes_per_L_sweep"), ("sweep_U", "dram_bytes_per_U_sweep"),
+                         ("residual", "dram_bytes_per_residual")):
+            if cls in split and key in rec and split[cls]["ms"] > 0:
+                per = split[cls]["ms"] / split[cls]["launches"] * 1e-3
+                gbs = float(rec[key]) / per / 1e9
+                dram[cls] = {"dram_gbs": round(gbs, 1), "dram_frac": round(gbs / peak, 4)}
+        out["fp32_apply"]["dram"] = dram
+        out["fp32_apply"]["dram_peak"] = {"gbs": peak, "kind": kind}
     for name, pc in (("fp32_sweeps_3_3", silu.PRECOND_SWEEPS), ("fp64_direct", silu.PRECOND_DIRECT)):
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
         # one restart cycle first: every inner iteration's graph is captured before the timed solve
