@@ -165,6 +165,32 @@ def test_direct_trisolve_matches_oracle(silu, ctx, case, mode):
     assert percol_relerr(host(x), want) < FP64_TOL
 
 
+@pytest.mark.parametrize("scale,prec", [("rowcol", "fp64"), ("row", "fp32"), ("none", "fp64")])
+def test_persistent_direct_scalings_and_precisions(silu, ctx, scale, prec):
+    """Both exact-solve schedules on row/column-scaled factors, on FP32 sweep
+    factors (the exact solves use FP64 copies) and on unscaled factors: the
+    persistent launch equals the per-level launches to rounding, and, with
+    row scaling, the oracle's exact application."""
+    A = synth.cutcell7(27, 25, 19, seed=15)
+    n = len(A[0]) - 1
+    sc = {"rowcol": silu.SCALE_ROWCOL, "row": silu.SCALE_ROW, "none": silu.SCALE_NONE}[scale]
+    pr = silu.FP32 if prec == "fp32" else silu.FP64
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilut", 1e-3, 10, scale=sc, prec=pr)
+    b = synth.rhs(n, 2, seed=17)
+    x0 = synth.rhs(n, 2, seed=18) * 0.5
+    got = {}
+    for mode in (2, 1):
+        F.set_direct(mode)
+        x = dev(x0.copy())
+        silu.direct_trisolve(F, x, dev(b))
+        ctx.check()
+        got[mode] = host(x)
+    assert percol_relerr(got[2], got[1]) < 1e-13
+    if scale == "row":
+        _, S = oracle_scaled(A, "ilut", 1e-3, 10)
+        assert percol_relerr(got[2], oracle.direct_apply(A, S, x0, b)) < FP64_TOL
+
+
 def test_persistent_direct_over_many_solves(silu, ctx):
     """The persistent solve alternates its readiness tag from solve to solve
     and keeps separate tagged vectors per column count: a sequence of solves
