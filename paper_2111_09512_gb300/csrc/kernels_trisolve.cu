@@ -25,6 +25,10 @@
 // arrays, so at the start of a solve all of them carry the previous tag.
 // The last warp to finish resets the ticket and flips the tag for the next
 // solve, so the launch needs no preparation and can be captured in a graph.
+// With several right-hand sides a lane publishes its row from inside its
+// polling loop, as soon as its own entries are in (with one column that
+// measured slower on short rows, so one column waits, sums and publishes
+// after the loop).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -187,6 +191,87 @@ __host__ __device__ constexpr int tri_chunk() {
   return R == 1 ? 8 : 4;
 }
 
+// The row's entries [p0, p1) read from vec (R columns each), CH at a time:
+// acc[k] -= T_oj vec_jk in column order, waiting for each entry's tag; the
+// FMAs of a run and, after the last run, publish(acc) happen inside the
+// polling loop, so a lane publishes its row as soon as its own entries are
+// in, whatever the other lanes of its warp still wait for.
+template <int R, int CH, class Publish>
+__device__ __forceinline__ void solve_row(const double* vec, const int* __restrict__ ci, const double* __restrict__ va,
+                                          int p0, int p1, long long tag, double (&acc)[R], int* err,
+                                          Publish publish) {
+  if (p0 >= p1) {
+    publish(acc);
+    return;
+  }
+  int p = p0;
+  int cnt = p1 - p < CH ? p1 - p : CH;
+  int j[CH];
+  double w[CH];
+  long long b[CH][R];
+#pragma unroll
+  for (int q = 0; q < CH; ++q)
+    if (q < cnt) {
+      j[q] = __ldg(ci + p + q);
+      w[q] = __ldg(va + p + q);
+    }
+#pragma unroll
+  for (int q = 0; q < CH; ++q)
+    if (q < cnt)
+#pragma unroll
+      for (int k = 0; k < R; ++k) b[q][k] = ld_poll(vec + (size_t)j[q] * R + k);
+  unsigned long long t0 = 0;
+  bool gave_up = false;
+  for (unsigned spins = 0;; ++spins) {
+    bool ready = true;
+#pragma unroll
+    for (int q = 0; q < CH; ++q)
+      if (q < cnt)
+#pragma unroll
+        for (int k = 0; k < R; ++k) ready = ready && ((b[q][k] & 1ll) == tag);
+    if (ready || gave_up) {
+#pragma unroll
+      for (int q = 0; q < CH; ++q)
+        if (q < cnt)
+#pragma unroll
+          for (int k = 0; k < R; ++k) acc[k] = fma(-w[q], untag(b[q][k]), acc[k]);
+      p += CH;
+      if (p >= p1) {
+        publish(acc);
+        return;
+      }
+      cnt = p1 - p < CH ? p1 - p : CH;
+#pragma unroll
+      for (int q = 0; q < CH; ++q)
+        if (q < cnt) {
+          j[q] = __ldg(ci + p + q);
+          w[q] = __ldg(va + p + q);
+        }
+#pragma unroll
+      for (int q = 0; q < CH; ++q)
+        if (q < cnt)
+#pragma unroll
+          for (int k = 0; k < R; ++k) b[q][k] = ld_poll(vec + (size_t)j[q] * R + k);
+      continue;
+    }
+    if (t0 == 0) t0 = tri_ns();
+    __nanosleep(kTriPause);
+#pragma unroll
+    for (int q = 0; q < CH; ++q)
+      if (q < cnt)
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+          if ((b[q][k] & 1ll) != tag) b[q][k] = ld_poll(vec + (size_t)j[q] * R + k);
+    if ((spins & 63u) == 63u) {
+      if (ld_poll_i(err) != 0) gave_up = true;
+      else if (tri_ns() - t0 > kTriWaitNs) {
+        atomicOr(err, 4);
+        gave_up = true;
+      }
+    }
+  }
+}
+
 struct TriArgs {
   int nitemsL, nitems;
   const int4* items;  // {first, last + 1, gate row or -1, gate in v (1) or y (0)}
@@ -221,6 +306,14 @@ __device__ __forceinline__ void lower_row(const TriArgs& a, int idx, long long t
 #pragma unroll
   for (int k = 0; k < R; ++k) acc[k] = a.r[(size_t)o * a.ldr + k];
   const int p0 = __ldg(a.lrp + idx), p1 = __ldg(a.lrp + idx + 1);
+  if constexpr (R > 1) {
+    // several columns: publish from inside the polling loop (see solve_row)
+    solve_row<R, CH>(a.y, a.lci, a.lva, p0, p1, tag, acc, a.err, [&](double (&v)[R]) {
+#pragma unroll
+      for (int k = 0; k < R; ++k) st_publish(a.y + (size_t)o * R + k, tag_of(v[k], tag));
+    });
+    return;
+  }
   for (int p = p0; p < p1; p += CH) {
     const int cnt = p1 - p < CH ? p1 - p : CH;
     int j[CH];
@@ -258,6 +351,22 @@ __device__ __forceinline__ void upper_row(const TriArgs& a, int idx, long long t
     for (int k = 0; k < R; ++k) acc[k] = d * untag(yo[0][k]);
   }
   const int p0 = __ldg(a.urp + idx), p1 = __ldg(a.urp + idx + 1);
+  const double dc = a.dcol ? __ldg(a.dcol + o) : 1.0;
+  auto publish = [&](double (&v)[R]) {
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+      const long long pub = tag_of(v[k], tag);
+      st_publish(a.v + (size_t)o * R + k, pub);
+      const double vo = untag(pub);
+      double* xo = a.x + (size_t)o * a.ldx + k;
+      const double add = a.dcol ? dc * vo : vo;
+      *xo = a.x_zero ? add : *xo + add;
+    }
+  };
+  if constexpr (R > 1) {
+    solve_row<R, CH>(a.v, a.uci, a.uva, p0, p1, tag, acc, a.err, publish);
+    return;
+  }
   for (int p = p0; p < p1; p += CH) {
     const int cnt = p1 - p < CH ? p1 - p : CH;
     int j[CH];
@@ -276,16 +385,7 @@ __device__ __forceinline__ void upper_row(const TriArgs& a, int idx, long long t
 #pragma unroll
         for (int k = 0; k < R; ++k) acc[k] = fma(-w[q], untag(vb[q][k]), acc[k]);
   }
-  const double dc = a.dcol ? __ldg(a.dcol + o) : 1.0;
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    const long long pub = tag_of(acc[k], tag);
-    st_publish(a.v + (size_t)o * R + k, pub);
-    const double vo = untag(pub);
-    double* xo = a.x + (size_t)o * a.ldx + k;
-    const double add = a.dcol ? dc * vo : vo;
-    *xo = a.x_zero ? add : *xo + add;
-  }
+  publish(acc);
 }
 
 // Resident blocks per SM the register budget is set for: many warps keep
