@@ -209,8 +209,13 @@ void silu_mat_destroy(silu_mat A);
  * Launch shape of the staged kernel on A (the residual r = b - A x and the
  * FGMRES products): lanes per row (0 = from the mean row length, else 1, 2
  * or 4), rows per lane (0 = automatic, else 1, 2 or 4; more than one only
- * with one lane per row), gather width (8 or 16 entries in flight per lane).
- * Results change only by summation order across lanes.  Blocks (the new
+ * with one lane per row), gather width (8 or 16 entries in flight per lane;
+ * 10: the narrow configuration -- tiles of at most 352 entries swept by 24
+ * warps per SM with 10 gathers in flight, for one lane and one row per lane
+ * and rows of at most 10 entries, 9 on average, else SILU_ERR_INVALID_ARG;
+ * 0: automatic, the narrow configuration where it fits, else 16).  The
+ * automatic shape (lanes 0, passes 0, chunk 0) is what silu_mat_create
+ * chooses.  Results change only by summation order across lanes.  Blocks (the new
  * tiles are uploaded); captured FGMRES iterations of factor objects on A are
  * rebuilt on their next use.
  */
@@ -218,7 +223,7 @@ silu_status silu_mat_set_shape(silu_mat A, int lanes, int passes, int chunk);
 /*
  * Time r = b - A x (one right-hand side) for each launch shape of the staged
  * kernel (lanes 1/2/4, rows per lane 1/2/4 with one lane, gather width 8/16,
- * and the automatic choice), keep the fastest (as silu_mat_set_shape), and
+ * the narrow configuration, and the automatic choice), keep the fastest (as silu_mat_set_shape), and
  * return it with its time per product.  Blocks.  Results change only by
  * summation order across lanes.  Device context only; an empty matrix keeps
  * the automatic shape and reports 0 ms.  Any output pointer may be NULL.
@@ -556,8 +561,10 @@ silu_status silu_batch_fgmres(silu_batch B, double* x, const double* b, double t
  * rows per warp (staged kernel: 8, 16, 32, 64 or 128 rows per warp tile,
  * i.e. four or two lanes per row, one, or one lane taking two or four rows;
  * or the lanes-per-row kernel with 2, 4 or 8 lanes) and gather width (8 or
- * 16 entries in flight per lane).  Writes the chosen candidate's index and its
- * time per application.  Blocks.
+ * 16 entries in flight per lane; 0 = the automatic configuration: narrow
+ * tiles swept by 24 warps with 10 gathers in flight for FP64 factors whose
+ * rows fit them, see silu_mat_set_shape, else 16).  Writes the chosen
+ * candidate's index and its time per application.  Blocks.
  */
 silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choice, double* ms);
 /*
@@ -566,7 +573,7 @@ silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choic
  * min(cap, *count) candidates, shape[4 k .. 4 k + 3] = {variant (1 lanes-per-
  * row kernel, 2 staged kernel, 3 staged kernel on sorted copies), lanes per
  * row (0 = from the mean row length), rows per lane (0 = automatic), gather
- * width} and ms[k] = time per application (-1 for a candidate not run: a
+ * width (0 = automatic)} and ms[k] = time per application (-1 for a candidate not run: a
  * sorted-copy candidate when no factor has one).  shape and ms may be NULL.
  */
 silu_status silu_ilu_tune_table(silu_ilu F, int cap, int32_t* shape, double* ms, int* count);

@@ -8,7 +8,14 @@ using namespace silu;
 
 namespace silu {
 
-// 16-byte-rounded copies, and the row tiles of the staged kernel are built.
+int auto_tile_nnz(const Csr& T, bool fp32, int lanes, int passes) {
+  return (!fp32 && lanes == 1 && passes == 1 && silu::narrow_fits(T.rp.data(), T.n)) ? silu::kTileNnzNarrow
+                                                                                      : silu::kTileNnz;
+}
+
+// Uploads T (row pointers, columns, values in FP64 or FP32) as
+// 16-byte-rounded copies, and builds the row tiles of the staged kernel in
+// the automatic launch shape.
 cudaError_t upload_csr(const silu::Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& va, DBuf& tiles, DevCsr& d,
                        cudaStream_t s) {
   const size_t n = (size_t)T.n, nnz = (size_t)T.nnz();
@@ -35,7 +42,8 @@ cudaError_t upload_csr(const silu::Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& 
   std::vector<int> tl;
   const int tlanes = silu::staged_lanes(T.rp.data(), T.n);
   const int tpasses = silu::staged_passes(T.rp.data(), T.n, tlanes);
-  const bool tiled = silu::make_tiles(T.rp.data(), T.n, tlanes, tpasses, tl);
+  const int tnnz = auto_tile_nnz(T, fp32, tlanes, tpasses);
+  const bool tiled = silu::make_tiles(T.rp.data(), T.n, tlanes, tpasses, tl, tnnz);
   if (e == cudaSuccess && tiled) e = upload(tiles, tl.data(), tl.size(), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging vectors die at return
   d.n = (int)T.n;
@@ -48,6 +56,7 @@ cudaError_t upload_csr(const silu::Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& 
   d.ntiles = tiled ? (int)(tl.size() / 4) : 0;
   d.tile_lanes = tlanes;
   d.tile_passes = tpasses;
+  d.tile_nnz = tnnz;
   return e;
 }
 
@@ -101,9 +110,13 @@ namespace {
 // row and rl rows per lane, gather width.
 cudaError_t keep_shape(const Csr& h, DBuf& tiles, DevCsr& T, const DevCsr& old, cudaStream_t s) {
   T.chunk = old.chunk;
-  if (old.tile_lanes == T.tile_lanes && old.tile_passes == T.tile_passes) return cudaSuccess;
+  if (old.tile_lanes == T.tile_lanes && old.tile_passes == T.tile_passes && old.tile_nnz == T.tile_nnz)
+    return cudaSuccess;
+  // narrow tiles only where the new values' rows still fit them
+  const int lim = (old.tile_nnz == silu::kTileNnzNarrow && !silu::narrow_fits(h.rp.data(), h.n)) ? silu::kTileNnz
+                                                                                                 : old.tile_nnz;
   std::vector<int> tl;
-  if (!silu::make_tiles(h.rp.data(), h.n, old.tile_lanes, old.tile_passes, tl)) return cudaSuccess;
+  if (!silu::make_tiles(h.rp.data(), h.n, old.tile_lanes, old.tile_passes, tl, lim)) return cudaSuccess;
   cudaError_t e = upload(tiles, tl.data(), tl.size(), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) {
@@ -111,6 +124,7 @@ cudaError_t keep_shape(const Csr& h, DBuf& tiles, DevCsr& T, const DevCsr& old, 
     T.ntiles = (int)(tl.size() / 4);
     T.tile_lanes = old.tile_lanes;
     T.tile_passes = old.tile_passes;
+    T.tile_nnz = lim;
   }
   return e;
 }
@@ -1003,9 +1017,9 @@ namespace {
 
 // Rebuild the staged-kernel tiles of T (host CSR h) for g lanes per row and
 // rl rows per lane.
-cudaError_t retile(const Csr& h, DBuf& tiles, DevCsr& T, int g, int rl, cudaStream_t s) {
+cudaError_t retile(const Csr& h, DBuf& tiles, DevCsr& T, int g, int rl, cudaStream_t s, int max_nnz) {
   std::vector<int> tl;
-  if (!silu::make_tiles(h.rp.data(), h.n, g, rl, tl)) return cudaSuccess;  // keeps the current tiles
+  if (!silu::make_tiles(h.rp.data(), h.n, g, rl, tl, max_nnz)) return cudaSuccess;  // keeps the current tiles
   cudaError_t e = upload(tiles, tl.data(), tl.size(), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) {
@@ -1013,8 +1027,17 @@ cudaError_t retile(const Csr& h, DBuf& tiles, DevCsr& T, int g, int rl, cudaStre
     T.ntiles = (int)(tl.size() / 4);
     T.tile_lanes = g;
     T.tile_passes = rl;
+    T.tile_nnz = max_nnz;
   }
   return e;
+}
+
+// Tile limit of an autotuner candidate's gather width: 0 automatic (narrow
+// tiles where they fit), 10 narrow tiles where they fit, else the default.
+int candidate_tile_nnz(const Csr& h, bool fp32, int g, int rl, int chunk) {
+  if (chunk == 0) return auto_tile_nnz(h, fp32, g, rl);
+  if (chunk == silu::kNarrowChunkRows) return auto_tile_nnz(h, fp32, g, rl);
+  return silu::kTileNnz;
 }
 
 // variant 2: staged kernel with `lanes` lanes per row (0 = from the mean row
@@ -1026,9 +1049,12 @@ struct TuneCandidate {
   int variant, lanes, passes, chunk;
 };
 
-const TuneCandidate kTune[] = {{2, 0, 0, 16}, {2, 0, 0, 8}, {2, 1, 1, 16}, {2, 1, 2, 16}, {2, 1, 4, 16},
-                               {2, 1, 4, 8},  {2, 2, 1, 16}, {2, 4, 1, 16}, {1, 2, 0, 16}, {1, 4, 0, 16},
-                               {1, 8, 0, 16}, {3, 1, 1, 16}, {3, 1, 1, 8}};
+// chunk 0: the automatic configuration (narrow tiles with 10 gathers in
+// flight where the rows fit them, else 16); chunk 10: the narrow
+// configuration where it fits.
+const TuneCandidate kTune[] = {{2, 0, 0, 0},  {2, 0, 0, 16}, {2, 0, 0, 8},  {2, 1, 1, 16}, {2, 1, 2, 16},
+                               {2, 1, 4, 16}, {2, 1, 4, 8},  {2, 2, 1, 16}, {2, 4, 1, 16}, {1, 2, 0, 16},
+                               {1, 4, 0, 16}, {1, 8, 0, 16}, {3, 1, 1, 16}, {3, 1, 1, 8}};
 
 }  // namespace
 
@@ -1069,9 +1095,11 @@ silu_status silu_ilu_autotune(silu_ilu F, int sweeps_L, int sweeps_U, int* choic
         const int gL = c.lanes ? c.lanes : autoL, gU = c.lanes ? c.lanes : autoU;
         const int pL = c.passes ? c.passes : silu::staged_passes(F->F.L.rp.data(), F->F.L.n, gL);
         const int pU = c.passes ? c.passes : silu::staged_passes(Ut.rp.data(), Ut.n, gU);
-        CK(retile(F->F.L, F->L_tiles, F->dL, gL, gL == 1 ? pL : 1, s));
-        CK(retile(Ut, F->U_tiles, F->dU, gU, gU == 1 ? pU : 1, s));
-        F->dL.chunk = F->dU.chunk = c.chunk;
+        const bool f32 = F->prec == SILU_FP32;
+        const int rlL = gL == 1 ? pL : 1, rlU = gU == 1 ? pU : 1;
+        CK(retile(F->F.L, F->L_tiles, F->dL, gL, rlL, s, candidate_tile_nnz(F->F.L, f32, gL, rlL, c.chunk)));
+        CK(retile(Ut, F->U_tiles, F->dU, gU, rlU, s, candidate_tile_nnz(Ut, f32, gU, rlU, c.chunk)));
+        F->dL.chunk = F->dU.chunk = (c.chunk == 8) ? 8 : 16;
       }
     };
     F->tune_ms.assign((size_t)ncand, -1.0);
@@ -1234,15 +1262,19 @@ silu_status silu_mat_set_shape(silu_mat A, int lanes, int passes, int chunk) {
   silu_ctx ctx = A->ctx;
   if (!(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4) || !(passes == 0 || passes == 1 || passes == 2 ||
                                                                    passes == 4) ||
-      !(chunk == 8 || chunk == 16) || (lanes != 1 && passes > 1))
-    return set_err(ctx, SILU_ERR_INVALID_ARG, "lanes 0/1/2/4, passes 0/1/2/4 (more than 1 only with one lane), chunk 8/16");
+      !(chunk == 0 || chunk == 8 || chunk == 10 || chunk == 16) || (lanes != 1 && passes > 1))
+    return set_err(ctx, SILU_ERR_INVALID_ARG,
+                   "lanes 0/1/2/4, passes 0/1/2/4 (more than 1 only with one lane), chunk 0/8/10/16");
   if (ctx->device < 0 || A->A.n == 0) return SILU_OK;
   silu_status ds = device_ok(ctx);
   if (ds != SILU_OK) return ds;
   const int g = lanes ? lanes : silu::staged_lanes(A->A.rp.data(), A->A.n);
   const int rl = g == 1 ? (passes ? passes : silu::staged_passes(A->A.rp.data(), A->A.n, g)) : 1;
+  const int lim = candidate_tile_nnz(A->A, false, g, rl, chunk);
+  if (chunk == silu::kNarrowChunkRows && lim != silu::kTileNnzNarrow)
+    return set_err(ctx, SILU_ERR_INVALID_ARG, "the narrow configuration needs one lane per row and short rows");
   std::vector<int> tl;
-  if (!silu::make_tiles(A->A.rp.data(), A->A.n, g, rl, tl))
+  if (!silu::make_tiles(A->A.rp.data(), A->A.n, g, rl, tl, lim))
     return set_err(ctx, SILU_ERR_INVALID_ARG, "a row is too long for the staged kernel");
   // new tiles in a new buffer (the old one may still be read by queued work)
   DBuf nt;
@@ -1255,7 +1287,8 @@ silu_status silu_mat_set_shape(silu_mat A, int lanes, int passes, int chunk) {
   A->d.ntiles = (int)(tl.size() / 4);
   A->d.tile_lanes = g;
   A->d.tile_passes = rl;
-  A->d.chunk = chunk;
+  A->d.tile_nnz = lim;
+  A->d.chunk = (chunk == 8) ? 8 : 16;
   A->gen++;
   return SILU_OK;
 }
@@ -1268,8 +1301,8 @@ silu_status silu_mat_autotune(silu_mat A, int* lanes, int* passes, int* chunk, d
   if (ds != SILU_OK) return ds;
   const size_t n = (size_t)A->A.n;
   // candidates: {lanes, passes, chunk}, the automatic choice first
-  static const int kShapes[][3] = {{0, 0, 16}, {0, 0, 8}, {1, 1, 16}, {1, 1, 8}, {1, 2, 16}, {1, 2, 8},
-                                   {1, 4, 16}, {1, 4, 8}, {2, 1, 16}, {2, 1, 8}, {4, 1, 16}, {4, 1, 8}};
+  static const int kShapes[][3] = {{0, 0, 0},  {0, 0, 16}, {0, 0, 8}, {1, 1, 10}, {1, 1, 16}, {1, 1, 8}, {1, 2, 16},
+                                   {1, 2, 8},  {1, 4, 16}, {1, 4, 8}, {2, 1, 16}, {2, 1, 8},  {4, 1, 16}, {4, 1, 8}};
   int best = -1;
   double best_ms = 1e300;
   if (n > 0) {
@@ -1319,7 +1352,7 @@ silu_status silu_mat_autotune(silu_mat A, int* lanes, int* passes, int* chunk, d
   if (st != SILU_OK) return st;
   if (lanes) *lanes = A->d.tile_lanes;
   if (passes) *passes = A->d.tile_passes;
-  if (chunk) *chunk = A->d.chunk;
+  if (chunk) *chunk = A->d.tile_nnz == silu::kTileNnzNarrow ? silu::kNarrowChunkRows : A->d.chunk;
   if (ms_out) *ms_out = best < 0 || n == 0 ? 0.0 : best_ms;
   return silu_ctx_check(ctx);
 }

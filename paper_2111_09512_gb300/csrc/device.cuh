@@ -35,6 +35,21 @@ enum Mode : int {
   MODE_DF = 2   // FP64 matrix and input vectors, FP32 output (residual feeding FP32 sweeps)
 };
 
+// Staged-sweep tile limits (entries per warp tile; a tile has
+// 32 * passes / lanes rows).  The CSR arrays of a tiled matrix are allocated with kCsrPad spare
+// elements so that copies rounded out to 16-byte boundaries stay inside the
+// allocation.
+constexpr int kTileNnz = 424;
+constexpr int kTileRows = 32;
+constexpr int kCsrPad = 8;
+// Narrow tiles (FP64 values, one lane per row, rows of at most
+// kNarrowChunkRows entries and kNarrowMeanRow on average): at most
+// kTileNnzNarrow - 8 entries per tile, swept by 24 warps per CTA with
+// kNarrowChunkRows gathers in flight per lane.
+constexpr int kTileNnzNarrow = 360;
+constexpr int kNarrowChunkRows = 10;
+constexpr double kNarrowMeanRow = 9.0;
+
 struct DevCsr {
   int n = 0;
   int64_t nnz = 0;
@@ -63,15 +78,9 @@ struct DevCsr {
   int tile_lanes = 1;  // lanes per row in the staged kernel (1, 2 or 4)
   int tile_passes = 1; // rows per lane in a tile (1, 2 or 4; only with one lane per row)
   int chunk = 16;      // entries gathered per lane before the FMAs (8 or 16)
+  int tile_nnz = kTileNnz;  // the entry limit the tiles were cut with (kTileNnzNarrow: narrow configuration)
 };
 
-// Staged-sweep tile limits (entries per warp tile; a tile has
-// 32 * passes / lanes rows).  The CSR arrays of a tiled matrix are allocated with kCsrPad spare
-// elements so that copies rounded out to 16-byte boundaries stay inside the
-// allocation.
-constexpr int kTileNnz = 424;
-constexpr int kTileRows = 32;
-constexpr int kCsrPad = 8;
 
 // Lanes per row for the staged kernel from the mean row length: one lane per
 // row up to 16 entries, two up to 32, four beyond (each warp-wide FMA then
@@ -106,7 +115,10 @@ bool make_sorted(const int64_t* rp, const int32_t* ci, const double* va, int64_t
 // tile, for `lanes` lanes per row and `passes` rows per lane (32 * passes /
 // lanes rows per tile).  Returns false if a row has more than kTileNnz - 8
 // entries.
-bool make_tiles(const int64_t* rp, int64_t n, int lanes, int passes, std::vector<int>& desc);
+bool make_tiles(const int64_t* rp, int64_t n, int lanes, int passes, std::vector<int>& desc,
+                int max_nnz = kTileNnz);
+// Whether a row pointer suits the narrow configuration (see kTileNnzNarrow).
+bool narrow_fits(const int64_t* rp, int64_t n);
 
 // L2 flags of a staged sweep launch.  kFlagReverse: walk the tiles last to
 // first (set on every other staged launch of a context when LaunchEnv::l2

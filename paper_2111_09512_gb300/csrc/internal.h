@@ -338,6 +338,9 @@ cudaError_t upload(DBuf& b, const T* src, size_t count, cudaStream_t s) {
 
 cudaError_t upload_csr(const Csr& T, bool fp32, DBuf& rp, DBuf& ci, DBuf& va, DBuf& tiles, DevCsr& d,
                        cudaStream_t s);
+// The tile entry limit of the automatic launch shape: narrow tiles for FP64
+// values with one lane per row whose rows fit them (silu::narrow_fits).
+int auto_tile_nnz(const Csr& T, bool fp32, int lanes, int passes);
 // Length-sorted copy of T for the staged kernel (silu::make_sorted); clears
 // the copy in d when it would not pay.
 cudaError_t upload_sorted(const Csr& T, bool fp32, SortedBufs& b, DevCsr& d, cudaStream_t s);

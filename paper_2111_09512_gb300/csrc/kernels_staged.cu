@@ -46,13 +46,13 @@ int staged_passes(const int64_t* rp, int64_t n, int lanes) {
   return avg * 4.0 <= room ? 4 : (avg * 2.0 <= room ? 2 : 1);
 }
 
-bool make_tiles(const int64_t* rp, int64_t n, int lanes, int passes, std::vector<int>& desc) {
+bool make_tiles(const int64_t* rp, int64_t n, int lanes, int passes, std::vector<int>& desc, int max_nnz) {
   desc.clear();
   const int rows = kTileRows * passes / lanes;
   int64_t r0 = 0;
   while (r0 < n) {
     int64_t r1 = r0;
-    while (r1 < n && r1 - r0 < rows && rp[r1 + 1] - rp[r0] <= kTileNnz - 8) ++r1;
+    while (r1 < n && r1 - r0 < rows && rp[r1 + 1] - rp[r0] <= max_nnz - 8) ++r1;
     if (r1 == r0) return false;  // a single row does not fit
     desc.push_back((int)r0);
     desc.push_back((int)r1);
@@ -61,6 +61,14 @@ bool make_tiles(const int64_t* rp, int64_t n, int lanes, int passes, std::vector
     r0 = r1;
   }
   return true;
+}
+
+bool narrow_fits(const int64_t* rp, int64_t n) {
+  if (n <= 0) return false;
+  int64_t longest = 0;
+  for (int64_t r = 0; r < n; ++r) longest = std::max<int64_t>(longest, rp[r + 1] - rp[r]);
+  const double mean = (double)rp[n] / (double)n;
+  return longest <= kNarrowChunkRows && mean <= kNarrowMeanRow;
 }
 
 double tile_pad(const int64_t* rp, int64_t n) {
@@ -214,12 +222,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // One stage: a 16-byte header (the tile descriptor, written by the issuing
 // lane), then values, column indices and row pointers as copied, and, for a
 // length-sorted layout, the tile's row numbers in the vectors.
-template <class MT, int RL, bool PERM>
+template <class MT, int RL, bool PERM, int NNZ = kTileNnz>
 struct StageLayout {
   static constexpr int kValAlign = 16 / (int)sizeof(MT);  // elements per 16 bytes
   static constexpr size_t kHdr = 16;
-  static constexpr size_t kVal = sizeof(MT) * (kTileNnz + 8);
-  static constexpr size_t kCol = sizeof(int) * (kTileNnz + 8);
+  static constexpr size_t kVal = sizeof(MT) * (NNZ + 8);
+  static constexpr size_t kCol = sizeof(int) * (NNZ + 8);
   static constexpr size_t kRp = sizeof(int) * (RL * kTileRows + 8);
   static constexpr size_t kPerm = PERM ? sizeof(int) * (kTileRows + 8) : 0;
   static constexpr size_t kBytes = kHdr + kVal + kCol + kRp + kPerm;  // all multiples of 16
@@ -229,11 +237,11 @@ struct StageLayout {
 // issue its copies into stage buffer `st` (three, or four with the row
 // numbers of a sorted layout).  The header store precedes the arrive on the
 // stage's mbarrier, so waiters see it.
-template <class MT, int RL, bool PERM, bool RP = true>
+template <class MT, int RL, bool PERM, bool RP = true, int NNZ = kTileNnz>
 __device__ __forceinline__ void issue_tile(int4 d, unsigned char* st, uint64_t* bar, const int* __restrict__ rp,
                                            const int* __restrict__ ci, const MT* __restrict__ va,
                                            const int* __restrict__ perm, uint64_t pol) {
-  using L = StageLayout<MT, RL, PERM>;
+  using L = StageLayout<MT, RL, PERM, NNZ>;
   const int r0 = d.x, r1 = d.y, p0 = d.z, p1 = d.w;
   const int a0 = p0 & ~(L::kValAlign - 1), a1 = (p1 + L::kValAlign - 1) & ~(L::kValAlign - 1);
   const int c0 = p0 & ~3, c1 = (p1 + 3) & ~3;
@@ -737,13 +745,13 @@ __device__ __forceinline__ int4 shfl_int4(int4 v, int src) {
 // only the values and column indices of the tile.  Each row still
 // accumulates c - sum t_ij in_j in column order, so the results are the
 // bits of k_sweep_staged.
-template <class MT, class VI, class VO, int CH>
-__global__ void __launch_bounds__(warps_of<MT>() * 32, 1)
+template <class MT, class VI, class VO, int CH, int W = warps_of<MT>(), int NNZ = kTileNnz>
+__global__ void __launch_bounds__(W * 32, 1)
     k_sweep_rows(int ntiles, const int4* __restrict__ tiles, const int* __restrict__ rp, const int* __restrict__ ci,
                  const MT* __restrict__ va, const VI* __restrict__ c, const VI* __restrict__ in, VO* __restrict__ out,
                  const double* __restrict__ dinv, double* __restrict__ x, int epi, int flags, int* __restrict__ err) {
-  using L = StageLayout<MT, 1, false>;
-  constexpr int kWarps = warps_of<MT>();
+  using L = StageLayout<MT, 1, false, NNZ>;
+  constexpr int kWarps = W;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kWarps][kWarpStages];
   const int tid = threadIdx.x;
@@ -768,9 +776,9 @@ __global__ void __launch_bounds__(warps_of<MT>() * 32, 1)
     if (gw + nw < ntiles) dnext = __ldg(tiles + (rev ? ntiles - 1 - (gw + nw) : gw + nw));
     // the factor and its tiles are never written by a sweep: the first copies
     // may start before the kernel that produced c and in has finished
-    if (gw < ntiles) issue_tile<MT, 1, false, false>(dcur, ring, &full[warp][0], rp, ci, va, nullptr, stream);
+    if (gw < ntiles) issue_tile<MT, 1, false, false, NNZ>(dcur, ring, &full[warp][0], rp, ci, va, nullptr, stream);
     if (gw + nw < ntiles)
-      issue_tile<MT, 1, false, false>(dnext, ring + L::kBytes, &full[warp][1], rp, ci, va, nullptr, stream);
+      issue_tile<MT, 1, false, false, NNZ>(dnext, ring + L::kBytes, &full[warp][1], rp, ci, va, nullptr, stream);
   }
   dcur = shfl_int4(dcur, 0);
   dnext = shfl_int4(dnext, 0);
@@ -826,7 +834,7 @@ __global__ void __launch_bounds__(warps_of<MT>() * 32, 1)
     }
     __syncwarp();
     if (lane == 0 && tn < ntiles)
-      issue_tile<MT, 1, false, false>(dn, ring + s * L::kBytes, &full[warp][s], rp, ci, va, nullptr, stream);
+      issue_tile<MT, 1, false, false, NNZ>(dn, ring + s * L::kBytes, &full[warp][s], rp, ci, va, nullptr, stream);
     dcur = dnext;
     dnext = shfl_int4(dn, 0);
     rb = nb;
@@ -834,11 +842,44 @@ __global__ void __launch_bounds__(warps_of<MT>() * 32, 1)
   }
 }
 
-template <class MT, class VI, class VO, int CH>
+template <class MT, class VI, class VO, int CH, int W = warps_of<MT>(), int NNZ = kTileNnz>
 cudaError_t rows_attr() {
-  using L = StageLayout<MT, 1, false>;
-  const size_t smem = (size_t)warps_of<MT>() * kWarpStages * L::kBytes;
-  return cudaFuncSetAttribute(k_sweep_rows<MT, VI, VO, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  using L = StageLayout<MT, 1, false, NNZ>;
+  const size_t smem = (size_t)W * kWarpStages * L::kBytes;
+  return cudaFuncSetAttribute(k_sweep_rows<MT, VI, VO, CH, W, NNZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem);
+}
+
+// The narrow configuration of the one-row-per-lane sweep for FP64 factors
+// whose rows fit one gather round of kNarrowChunk entries: tiles of at most
+// kTileNnzNarrow - 8 entries, so that the stages are smaller and
+// kNarrowWarps warps (more rows in processing per SM) fit beside them, with
+// kNarrowChunk gathers in flight per lane (the registers of 24 warps).
+constexpr int kNarrowWarps = 24;
+constexpr int kNarrowChunk = kNarrowChunkRows;
+
+template <class MT, class VI, class VO>
+cudaError_t narrow_launch(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
+                          const double* dinv, double* x, int epi, cudaStream_t s) {
+  using L = StageLayout<MT, 1, false, kTileNnzNarrow>;
+  const int nt = T.ntiles;
+  if (nt == 0) return cudaSuccess;
+  const int want = (nt + kNarrowWarps - 1) / kNarrowWarps;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(want < env.sms ? want : env.sms));
+  cfg.blockDim = dim3(kNarrowWarps * 32);
+  cfg.dynamicSmemBytes = (size_t)kNarrowWarps * kWarpStages * L::kBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = env.overlap ? 1 : 0;
+  int flags = env.l2 & (kFlagFactorNormal | kFlagVectorNormal);
+  if ((env.l2 & kFlagReverse) && (env.flips++ & 1u)) flags |= kFlagReverse;
+  return cudaLaunchKernelEx(&cfg, k_sweep_rows<MT, VI, VO, kNarrowChunk, kNarrowWarps, kTileNnzNarrow>, nt,
+                            (const int4*)T.tiles, (const int*)T.rp, (const int*)T.ci, (const MT*)T.va, (const VI*)c,
+                            (const VI*)in, (VO*)out, dinv, x, epi, flags, env.err);
 }
 
 template <class MT, class VI, class VO, int G, int CH, int RL, bool PERM>
@@ -898,6 +939,13 @@ template <class MT, class VI, class VO>
 cudaError_t staged(const DevCsr& T, const LaunchEnv& env, const void* c, const void* in, void* out,
                    const double* dinv, double* x, int epi, cudaStream_t s) {
   if (T.use_sorted && T.nstiles > 0) return staged_c<MT, VI, VO, 1, 1, true>(T, env, c, in, out, dinv, x, epi, s);
+  if (T.tile_nnz == kTileNnzNarrow) {
+    // tiles cut for the narrow configuration (one lane per row, FP64 values)
+    if constexpr (sizeof(MT) == 8) {
+      if (T.tile_lanes == 1 && T.tile_passes == 1) return narrow_launch<MT, VI, VO>(T, env, c, in, out, dinv, x, epi, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   switch (T.tile_lanes) {
     case 1:
       if (T.tile_passes == 4) return staged_c<MT, VI, VO, 1, 4, false>(T, env, c, in, out, dinv, x, epi, s);
@@ -928,6 +976,15 @@ cudaError_t prepare_mode() {
   if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 2, 1, false>();
   if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 4, 1, false>();
   if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 1, 1, true>();
+  // The narrow kernel is instantiated here, after k_sweep_staged with the
+  // same gather chunk (prepare_shape above), and must stay after it: nvcc
+  // 13.0 compiles the shared accumulation loop differently for the kernel
+  // instantiated first, and the narrow kernel instantiated first comes out
+  // at 76 registers instead of 80 and about 8% slower (49 instead of 45 us
+  // per lower sweep of the 128^3 cut-cell ILUT factor).
+  if constexpr (sizeof(MT) == 8) {
+    if (e == cudaSuccess) e = rows_attr<MT, VI, VO, kNarrowChunk, kNarrowWarps, kTileNnzNarrow>();
+  }
   return e;
 }
 

@@ -244,6 +244,37 @@ def test_matrix_launch_shapes(silu, ctx):
         assert st == silu.OK and rel <= 1e-10 and abs(its - its0) <= 1
 
 
+def test_matrix_narrow_configuration(silu, ctx):
+    """The narrow configuration (gather width 10: shorter tiles, 24 warps per
+    block) on a 7-point matrix gives the residual of the default one-lane
+    shape bit for bit (each row sums in column order in both), and matches
+    the oracle; a 27-point matrix, whose rows do not fit it, is refused with
+    SILU_ERR_INVALID_ARG and keeps its shape."""
+    A = synth.cutcell7(37, 29, 23, seed=6)
+    n = len(A[0]) - 1
+    M = silu.Matrix(ctx, *A)
+    x = synth.rhs(n, 1, seed=4)
+    b = synth.rhs(n, 1, seed=5)
+    res = {}
+    for chunk in (10, 16, 0):
+        M.set_shape(1, 1, chunk)
+        r = torch.empty(n, 1, dtype=torch.float64, device="cuda")
+        M.residual(r, dev(x), dev(b))
+        res[chunk] = host(r)
+    assert np.array_equal(res[10], res[16]) and np.array_equal(res[0], res[10])
+    assert percol(res[10], oracle.residual(A, x, b)) < FP64_TOL
+    H = synth.hex27(13, 11, 9, seed=6)
+    MH = silu.Matrix(ctx, *H)
+    with pytest.raises(silu.SiluError) as ei:
+        MH.set_shape(1, 1, 10)
+    assert ei.value.status == silu.ERR_INVALID_ARG
+    nh = len(H[0]) - 1
+    xh, bh = synth.rhs(nh, 1, seed=4), synth.rhs(nh, 1, seed=5)
+    r = torch.empty(nh, 1, dtype=torch.float64, device="cuda")
+    MH.residual(r, dev(xh), dev(bh))
+    assert percol(host(r), oracle.residual(H, xh, bh)) < FP64_TOL
+
+
 def test_matrix_autotune_keeps_a_valid_fastest_shape(silu, ctx):
     """silu_mat_autotune: the shape it keeps is one it timed, the residual
     with it matches the oracle to FP64 parity, FGMRES on A still converges,
@@ -253,7 +284,8 @@ def test_matrix_autotune_keeps_a_valid_fastest_shape(silu, ctx):
         M = silu.Matrix(ctx, *A)
         F = silu.ilu_setup(ctx, M, "ilu0")
         (lanes, passes, chunk), ms = M.autotune()
-        assert lanes in (1, 2, 4) and passes in (1, 2, 4) and chunk in (8, 16) and ms > 0
+        assert lanes in (1, 2, 4) and passes in (1, 2, 4) and chunk in (8, 10, 16) and ms > 0
+        assert chunk != 10 or (lanes == 1 and passes == 1)
         assert lanes == 1 or passes == 1
         x = synth.rhs(n, 1, seed=2)
         b = synth.rhs(n, 1, seed=3)
