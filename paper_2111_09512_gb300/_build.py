@@ -7,6 +7,7 @@ only when a source or header is newer than the library.
 from __future__ import annotations
 
 import os
+import re
 import shutil
 import subprocess
 from concurrent.futures import ThreadPoolExecutor
@@ -73,6 +74,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         jobs.append(["g++", *common, "-fPIC", "-ffp-contract=off", "-c", os.path.join(CSRC, src), "-o", obj])
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         logs = list(ex.map(_run, jobs))
+    # ptxas resource reports (registers, spills, shared memory per kernel)
+    for src, log in zip(CU_SOURCES, logs):
+        with open(os.path.join(BUILD, src + ".ptxas.txt"), "w") as fh:
+            fh.write(log)
     if verbose:
         for log in logs:
             print(log)
@@ -80,6 +85,27 @@ def build(force: bool = False, verbose: bool = False) -> str:
     _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
+
+
+def kernel_resources(src: str) -> dict:
+    """{mangled kernel name: (registers, spill store bytes, spill load bytes)} from the
+    ptxas report of CUDA unit `src` written by the last build."""
+    path = os.path.join(BUILD, src + ".ptxas.txt")
+    out, name, spills = {}, None, (0, 0)
+    with open(path) as fh:
+        for line in fh:
+            if "Compiling entry function" in line:
+                name = line.split("'")[1]
+                spills = (0, 0)
+                continue
+            m = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", line)
+            if m and name:
+                spills = (int(m.group(1)), int(m.group(2)))
+            m = re.search(r"Used (\d+) registers", line)
+            if m and name:
+                out[name] = (int(m.group(1)), *spills)
+                name = None
+    return out
 
 
 if __name__ == "__main__":
