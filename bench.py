@@ -1149,7 +1149,12 @@ def run_apply_only(args):
                   10+10 sweeps, 1 RHS; 19 launches per application)
       hex27_256:  the 27-point 256^3 perturbed-hex matrix, ILU(0) factors in
                   FP32, 3+3 FP32 sweeps, FP64 residual (5 launches each)
-      cutcell128_r4: the headline factors with 4 interleaved right-hand sides"""
+      hex27_128:  the same at 128^3
+      hex27_128_direct: 128^3 27-point ILU(0) in FP64, exact triangular solves
+                  (direct_trisolve, the automatic schedule) instead of sweeps
+      cutcell128_r4: the headline factors with 4 interleaved right-hand sides
+      poisson32_r4: 32^3 Poisson ILU(0), 4 interleaved right-hand sides, 5+5
+                  sweeps (a system small enough for the fused application)"""
     import torch
     import paper_2111_09512_gb300 as silu
     import synth
@@ -1157,13 +1162,20 @@ def run_apply_only(args):
     stream = torch.cuda.current_stream()
     ctx = silu.Context(0, stream)
     w = args.apply_only
+    direct = False
     if w in ("cutcell128", "cutcell128_r4"):
         A = synth.cutcell7(EDGE, seed=1)
         kind, prec, mL, mU, vb = "ilut", silu.FP64, ML, MU, 8
         R = 4 if w.endswith("r4") else 1
-    elif w == "hex27_256":
-        A = synth.hex27(256, seed=2)
+    elif w in ("hex27_256", "hex27_128"):
+        A = synth.hex27(256 if w == "hex27_256" else 128, seed=2)
         kind, prec, mL, mU, vb, R = "ilu0", silu.FP32, 3, 3, 4, 1
+    elif w == "hex27_128_direct":
+        A = synth.hex27(128, seed=2)
+        kind, prec, mL, mU, vb, R, direct = "ilu0", silu.FP64, 0, 0, 8, 1, True
+    elif w == "poisson32_r4":
+        A = synth.poisson7(32)
+        kind, prec, mL, mU, vb, R = "ilu0", silu.FP64, 5, 5, 8, 4
     else:
         raise SystemExit(f"unknown workload {w}")
     n = len(A[0]) - 1
@@ -1174,23 +1186,35 @@ def run_apply_only(args):
     st = F.stats()
     b = torch.from_numpy(synth.rhs(n, R, seed=1)).cuda()
     x = torch.zeros(n, R, dtype=torch.float64, device="cuda")
+    def apply():
+        if direct:
+            silu.direct_trisolve(F, x, b)
+        else:
+            silu.ilu_smooth(F, x, b, mL, mU)
+
     for _ in range(args.warmup):
         x.zero_()
-        silu.ilu_smooth(F, x, b, mL, mU)
+        apply()
     torch.cuda.synchronize()
     ctx.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        silu.ilu_smooth(F, x, b, mL, mU)
+        apply()
     e1.record(stream)
     torch.cuda.synchronize()
     ctx.profile(False)
     prof = ctx.profile_read()
     ms = e0.elapsed_time(e1) / args.steps
-    # applications from the second on start from x != 0: residual + (mL-1) + (mU-1) sweeps
-    nbytes = (resid_bytes(n, nnzA, R) + (mL - 1) * sweep_bytes(n, st["nnz_L"], R, vb) + 8 * n
-              + (mU - 1) * sweep_bytes(n, st["nnz_U"], R, vb) + 8 * n * R)
+    if direct:
+        # residual, then each factor read once, with its row pointers; vectors: r and y (L solve),
+        # y, dinv and x read and x written (U solve)
+        nbytes = (resid_bytes(n, nnzA, R) + (st["nnz_L"] + st["nnz_U"]) * (vb + 4) + 8 * (n + 1)
+                  + 6 * n * R * 8)
+    else:
+        # applications from the second on start from x != 0: residual + (mL-1) + (mU-1) sweeps
+        nbytes = (resid_bytes(n, nnzA, R) + (mL - 1) * sweep_bytes(n, st["nnz_L"], R, vb) + 8 * n
+                  + (mU - 1) * sweep_bytes(n, st["nnz_U"], R, vb) + 8 * n * R)
     line = {"apply_only": w, "rows": n, "rhs": R, "steps": args.steps, "warmup": args.warmup,
             "ms_per_application": round(ms, 5), "algorithmic_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
             "launches_per_application": {k: v[0] // args.steps for k, v in prof.items() if v[0]},
@@ -1226,7 +1250,8 @@ def main():
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-queue", type=int, default=8)
     ap.add_argument("--serve-pool", type=int, default=32)
-    ap.add_argument("--apply-only", choices=["cutcell128", "cutcell128_r4", "hex27_256"], default=None,
+    ap.add_argument("--apply-only", choices=["cutcell128", "cutcell128_r4", "hex27_256", "hex27_128",
+                                             "hex27_128_direct", "poisson32_r4"], default=None,
                     help="run only smoother applications of one workload (profiling, quick timing)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)

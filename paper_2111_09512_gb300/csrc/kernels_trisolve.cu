@@ -407,8 +407,9 @@ __global__ void __launch_bounds__(kTriThreads, tri_min_blocks<R>()) k_trisolve(T
     if (t >= a.nitems) break;
     const int4 it = __ldg(a.items + t);
     if (it.z >= 0) {
-      // the gate: a row two levels back whose publication means the rows
-      // this item reads are about to be published; only then do the lanes
+      // the gate: a row a few levels back (the plan's choice; three by
+      // default) whose publication means the rows this item reads are
+      // about to be published; only then do the lanes
       // start reading them, so items far ahead of the finished levels wait
       // on one entry each instead of flooding L2 with reads
       if (lane == 0) wait_gate((it.w ? a.v : a.y) + (size_t)it.z * R, tag, a.err);
