@@ -229,10 +229,7 @@ void level_copy(const Csr& T, const std::vector<int32_t>& level_rows, std::vecto
 }
 
 // Levels between an item and the row it waits on before reading its entries.
-#ifndef SILU_TRI_GATE_LEVELS
-#define SILU_TRI_GATE_LEVELS 3
-#endif
-constexpr int kTriGateLevels = SILU_TRI_GATE_LEVELS;
+constexpr int kTriGateLevels = 3;
 
 // Items of at most 32 consecutive level-ordered rows of one level, four
 // ints each: first and last + 1 level-ordered position, the gate row and

@@ -72,23 +72,12 @@ __device__ __forceinline__ long long tag_of(double v, long long tag) {
 __device__ __forceinline__ double untag(long long b) { return __longlong_as_double(b & ~1ll); }
 
 // Resident blocks per SM at most.
-#ifndef SILU_TRI_MAX_BLOCKS_PER_SM
-#define SILU_TRI_MAX_BLOCKS_PER_SM 8
-#endif
-constexpr int kTriMaxBlocksPerSm = SILU_TRI_MAX_BLOCKS_PER_SM;
-#ifndef SILU_TRI_PIPELINED
-#define SILU_TRI_PIPELINED 0
-#endif
-// Pauses (ns) between reads of entries not yet published: short for the
-// entries a row reads, longer for an item's gate (below).
-#ifndef SILU_TRI_PAUSE
-#define SILU_TRI_PAUSE 0
-#endif
-#ifndef SILU_TRI_GATE_PAUSE
-#define SILU_TRI_GATE_PAUSE 128
-#endif
-constexpr unsigned kTriPause = SILU_TRI_PAUSE;
-constexpr unsigned kTriGatePause = SILU_TRI_GATE_PAUSE;
+constexpr int kTriMaxBlocksPerSm = 8;
+// Pauses (ns) between reads of entries not yet published: none for the
+// entries a row reads (they are re-read at once), longer for an item's gate
+// (below).
+constexpr unsigned kTriPause = 0;
+constexpr unsigned kTriGatePause = 128;
 
 // Wait until *p carries the tag: reads after fixed pauses, bounded by
 // kTriWaitNs, and cut short when another wait has already given up (error
@@ -131,39 +120,9 @@ __device__ __forceinline__ void gather_ready(const double* vec, const int (&j)[C
       for (int k = 0; k < R; ++k) ready = ready && ((b[q][k] & 1ll) == tag);
   if (ready) return;
   const unsigned long long t0 = tri_ns();
-#if SILU_TRI_PIPELINED
-  // two rounds of reads in flight: the next round is issued before the
-  // results of the previous one are looked at
-  long long c[CH][R];
-#pragma unroll
-  for (int q = 0; q < CH; ++q)
-#pragma unroll
-    for (int k = 0; k < R; ++k) c[q][k] = b[q][k];
-#endif
   for (unsigned spins = 1;; ++spins) {
     __nanosleep(kTriPause);
     ready = true;
-#if SILU_TRI_PIPELINED
-#pragma unroll
-    for (int q = 0; q < CH; ++q)
-      if (q < cnt)
-#pragma unroll
-        for (int k = 0; k < R; ++k)
-          if ((b[q][k] & 1ll) != tag) c[q][k] = ld_poll(vec + (size_t)j[q] * R + k);
-    __nanosleep(kTriPause);
-#pragma unroll
-    for (int q = 0; q < CH; ++q)
-      if (q < cnt)
-#pragma unroll
-        for (int k = 0; k < R; ++k)
-          if ((b[q][k] & 1ll) != tag) {
-            if ((c[q][k] & 1ll) == tag)
-              b[q][k] = c[q][k];
-            else
-              b[q][k] = ld_poll(vec + (size_t)j[q] * R + k);
-            ready = ready && ((b[q][k] & 1ll) == tag);
-          }
-#else
 #pragma unroll
     for (int q = 0; q < CH; ++q)
       if (q < cnt)
@@ -173,7 +132,6 @@ __device__ __forceinline__ void gather_ready(const double* vec, const int (&j)[C
             b[q][k] = ld_poll(vec + (size_t)j[q] * R + k);
             ready = ready && ((b[q][k] & 1ll) == tag);
           }
-#endif
     if (ready) return;
     if ((spins & 63u) == 0) {
       if (ld_poll_i(err) != 0) return;
