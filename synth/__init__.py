@@ -165,3 +165,47 @@ def randint(seed: int, stream: int, count: int, lo: int, hi: int) -> np.ndarray:
 def rhs(n: int, nrhs: int, seed: int) -> np.ndarray:
     """Right-hand sides uniform on [-1, 1), shape (n, nrhs), RHS interleaved (row-major)."""
     return uniform(seed, 0, n * nrhs).reshape(n, nrhs)
+
+
+def banded(n: int, max_lower: int, bandwidth: int, seed: int, long_rows: dict | None = None, min_lower: int = 0):
+    """A structurally symmetric, strictly diagonally dominant CSR matrix with
+    uneven rows, for edge cases of the row tiles: row i couples to a seeded
+    random set of c_i earlier rows within `bandwidth` (c_i uniform on
+    [min_lower, max_lower], or long_rows[i] for the rows listed there), and every
+    coupling is mirrored, so the ILU(0) factors have exactly these patterns
+    (a row listed in long_rows may reach back to row 0: long_rows={n-1: n-1}
+    gives a dense last row and column)
+    (L_s row i: c_i entries; some rows end up with a diagonal only).
+    Off-diagonal values are -U(0.1, 1); the diagonal is 1 + the row's
+    absolute off-diagonal sum.  Returns (row_ptr int64, col int32, val)."""
+    long_rows = long_rows or {}
+    counts = randint(seed, 1, n, min_lower, max_lower)
+    lower = []
+    for i in range(n):
+        c = int(long_rows.get(i, counts[i]))
+        width = i if i in long_rows else min(i, bandwidth)
+        c = min(c, width)
+        if c == 0:
+            lower.append(np.zeros(0, dtype=np.int64))
+            continue
+        # c distinct offsets in [1, width], chosen by a seeded partial shuffle
+        keys = uniform(seed, 2 + i, width, 0.0, 1.0)
+        offs = np.argsort(keys, kind="stable")[:c] + 1
+        lower.append(np.sort(i - offs))
+    rows = [[] for _ in range(n)]
+    for i in range(n):
+        for j in lower[i]:
+            rows[i].append(int(j))
+            rows[int(j)].append(i)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    ci_parts, va_parts = [], []
+    for i in range(n):
+        off = np.array(sorted(rows[i]), dtype=np.int64)
+        vals = -uniform(seed, 3_000_000 + i, off.size, 0.1, 1.0)
+        cols = np.concatenate([off[off < i], [i], off[off > i]]).astype(np.int32)
+        d = 1.0 + np.abs(vals).sum()
+        k = int((off < i).sum())
+        ci_parts.append(cols)
+        va_parts.append(np.concatenate([vals[:k], [d], vals[k:]]))
+        rp[i + 1] = rp[i] + cols.size
+    return rp, np.concatenate(ci_parts), np.concatenate(va_parts)
