@@ -799,6 +799,15 @@ __global__ void __launch_bounds__(W * 32, 1)
       nb = __ldg(rp + dnext.x + lane);
       ne = __ldg(rp + dnext.x + lane + 1);
     }
+    // the row's constant term and the epilogue's operands: their addresses
+    // are known before the stage lands, so their loads are issued before the
+    // wait (left to the compiler, where they went depended on unrelated code
+    // in the same file, and the lower sweep of the 128^3 cut-cell ILUT factor
+    // took 45 or 49 us depending on it)
+    const int r = dcur.x + lane;
+    const bool act = r < dcur.y;
+    MT acc = (act && c) ? (MT)ld_keep(c + r, keep) : MT(0);
+    if (act) prefetch_epilogue(epi, r, dinv, x);
     const int s = k % kWarpStages;
     const bool ok = mbar_wait_bounded(&full[warp][s], (uint32_t)(k / kWarpStages) & 1u);
     if (!__all_sync(0xffffffffu, ok)) {
@@ -814,14 +823,10 @@ __global__ void __launch_bounds__(W * 32, 1)
     const unsigned char* st = ring + s * L::kBytes;
     const MT* sv = (const MT*)(st + L::kHdr);
     const int* sc = (const int*)(st + L::kHdr + L::kVal);
-    const int r = dcur.x + lane;
-    const bool act = r < dcur.y;
     const int a0 = dcur.z & ~(L::kValAlign - 1);
     const int c0 = dcur.z & ~3;
     const int len = act ? re - rb : 0;
     const int off = act ? rb : dcur.z;  // inactive lanes read nothing
-    MT acc = (act && c) ? (MT)ld_keep(c + r, keep) : MT(0);
-    if (act) prefetch_epilogue(epi, r, dinv, x);
     if (epi == EPI_SPMV)
       acc = row_accumulate<MT, VI, false, 1, CH>(sv + (off - a0), sc + (off - c0), len, 0, in, acc, keep);
     else
@@ -976,12 +981,6 @@ cudaError_t prepare_mode() {
   if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 2, 1, false>();
   if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 4, 1, false>();
   if (e == cudaSuccess) e = prepare_shape<MT, VI, VO, 1, 1, true>();
-  // The narrow kernel is instantiated here, after k_sweep_staged with the
-  // same gather chunk (prepare_shape above), and must stay after it: nvcc
-  // 13.0 compiles the shared accumulation loop differently for the kernel
-  // instantiated first, and the narrow kernel instantiated first comes out
-  // at 76 registers instead of 80 and about 8% slower (49 instead of 45 us
-  // per lower sweep of the 128^3 cut-cell ILUT factor).
   if constexpr (sizeof(MT) == 8) {
     if (e == cudaSuccess) e = rows_attr<MT, VI, VO, kNarrowChunk, kNarrowWarps, kTileNnzNarrow>();
   }
