@@ -1037,6 +1037,9 @@ def sweep_study(silu, ctx, torch):
     with the departure from normality (Eq. depB) of L, U and the scaled U
     (Table dep).
 
+    schur: the ILUT Schur complement smoother over 8 and 64 row blocks
+    (schur_study).
+
     time_to_solution_vs_sweeps: FGMRES(30) to 1e-8 on cut-cell matrices of
     64^3 to 160^3 rows with FP32 ILU(0) factors and m + m sweeps (m = 2..10)
     against direct solves of the same factors (iterations, seconds)."""
@@ -1138,6 +1141,66 @@ def sweep_study(silu, ctx, torch):
         tts[f"cutcell7_{edge}"] = rec
         del F, M
     out["time_to_solution_vs_sweeps"] = tts
+    out["schur"] = schur_study(silu, ctx, torch)
+    return out
+
+
+def schur_study(silu, ctx, torch, edge=EDGE, parts=(8, 64), kind="cutcell7", sweeps=(3,)):
+    """The ILUT Schur complement smoother (Sec. 3.1, Eq. schur) on the 128^3
+    cut-cell matrix, FP64, the rows split into `parts` contiguous blocks (as
+    ranks would hold them): setup time, interior and interface rows, one
+    smoother application (3+3 sweeps on each block's ILUT(1e-3, 10) factors,
+    no residual of the whole system formed), and FGMRES(30) to 1e-8 from zero
+    preconditioned by it, against the single-level smoother (ILUT(1e-3, 10),
+    3+3 sweeps) and exact solves of the same factors."""
+    import synth
+    A = synth.cutcell7(edge, seed=1) if kind == "cutcell7" else synth.poisson7(edge)
+    n = len(A[0]) - 1
+    M = silu.Matrix(ctx, *A)
+    del A
+    b = torch.from_numpy(synth.rhs(n, 1, seed=1)[:, 0].copy()).cuda()
+    out = {"workload": f"{kind}-{edge}^3 FP64, FGMRES(30) to 1e-8 from x = 0", "rows": n}
+
+    def solve(F, pre, mL, mU):
+        rec = None
+        for _ in range(2):  # the first solve also captures the iteration graphs
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, its, rr = silu.fgmres_solve(F, x, b, tol=1e-8, restart=30, maxit=3000, sweeps_L=mL, sweeps_U=mU,
+                                            precond=pre)
+            torch.cuda.synchronize()
+            rec = {"seconds": round(time.perf_counter() - t0, 4), "iterations": its, "relres": float(f"{rr:.3e}"),
+                   "converged": st == silu.OK}
+        return rec
+
+    for p in parts:
+        F = silu.ilu_setup(ctx, M, "ilu0")
+        t0 = time.perf_counter()
+        F.schur_setup(p, 1e-3, 10)
+        setup_s = time.perf_counter() - t0
+        st = F.schur_stats()
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            F.schur_smooth(x, b, 3, 3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            F.schur_smooth(x, b, 3, 3)
+        e1.record()
+        torch.cuda.synchronize()
+        rec = {"setup_s": round(setup_s, 2), "interior_rows": st["interior"], "interface_rows": st["interface"],
+               "apply_3_3_ms": round(e0.elapsed_time(e1) / 20, 4)}
+        for m in sweeps:
+            rec[f"fgmres_{m}_{m}"] = solve(F, silu.PRECOND_SCHUR, m, m)
+        out[f"parts_{p}"] = rec
+        del F
+    F = silu.ilu_setup(ctx, M, "ilut", 1e-3, 10)
+    for m in sweeps:
+        out[f"single_level_ilut_{m}_{m}"] = solve(F, silu.PRECOND_SWEEPS, m, m)
+    out["single_level_ilut_direct"] = solve(F, silu.PRECOND_DIRECT, 0, 0)
+    del F
     return out
 
 

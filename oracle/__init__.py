@@ -101,6 +101,7 @@ def _load():
         "orc_amg_vcycle": (i32, [vp] + [vp] * 7 + [i32, i32, i32, i32, i32, vp, vp]),
         "orc_schur_interface": (i64, [i64, vp, vp, i32, vp]),
         "orc_schur_apply": (i32, [i64, vp, vp, vp, i32, dbl, i32, i32, i32, vp, vp]),
+        "orc_amg_vcycle_schur": (i32, [vp, i32, dbl, i32, i32, i32, i32, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -569,6 +570,20 @@ class AMG:
                                     int(mU), int(nu), 1 if coarse == "gs" else 0, int(terms), _p(x), _p(b))
         if st:
             raise OracleError(st, "amg_vcycle")
+        return x
+
+    def vcycle_schur(self, x, b, parts: int, tau: float, fill: int, mL: int, mU: int, nu: int = 1,
+                     coarse: str = "jacobi", terms: int = 2):
+        """One V-cycle as vcycle, the finest level smoothed (before and after the coarse-grid
+        correction) by one application of the ILUT Schur complement smoother (schur_apply over
+        `parts` row blocks) instead of the ILU smoother.  Returns a new array."""
+        n = self.levels[0].n
+        x = np.ascontiguousarray(x, np.float64).reshape(n).copy()
+        b = np.ascontiguousarray(b, np.float64).reshape(n)
+        st = _load().orc_amg_vcycle_schur(self._h, int(parts), float(tau), int(fill), int(mL), int(mU), int(nu),
+                                          1 if coarse == "gs" else 0, int(terms), _p(x), _p(b))
+        if st:
+            raise OracleError(st, "amg_vcycle_schur")
         return x
 
     def __del__(self):

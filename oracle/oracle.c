@@ -1709,7 +1709,34 @@ typedef struct {
   int mL, mU, nu;
   int coarse; /* 0: l1-Jacobi, 1: polynomial Gauss-Seidel with `terms` terms */
   int terms;
+  /* the finest level's smoother: the ILU smoother on (lp.., sp.., dinv), or,
+     when schur_parts > 0, the ILUT Schur complement smoother over that many
+     row blocks (ILUT(schur_tau, schur_fill) of each block, m_L + m_U sweeps) */
+  int schur_parts;
+  double schur_tau;
+  int schur_fill;
 } amg_smoother;
+
+int orc_schur_apply(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, int parts, double tau,
+                    int fill, int mL, int mU, const double* r, double* z);
+
+/* x = x + M^{-1} (b - A_0 x) with the finest level's smoother. */
+static int fine_smooth(const orc_amg_level* L, const amg_smoother* sm, const double* b, double* x) {
+  const int64_t n = L->n;
+  if (sm->schur_parts <= 0)
+    return orc_smooth(n, 1, L->ap, L->ac, L->av, sm->lp, sm->lc, sm->lv, sm->sp, sm->sc, sm->sv, sm->dinv, x, b,
+                      sm->mL, sm->mU);
+  double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* z = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  orc_residual(n, 1, L->ap, L->ac, L->av, x, b, r);
+  const int st = orc_schur_apply(n, L->ap, L->ac, L->av, sm->schur_parts, sm->schur_tau, sm->schur_fill, sm->mL,
+                                 sm->mU, r, z);
+  if (!st)
+    for (int64_t i = 0; i < n; ++i) x[i] = x[i] + z[i];
+  free(r);
+  free(z);
+  return st;
+}
 
 static int coarse_smooth(const orc_amg_level* L, const amg_smoother* sm, const double* b, double* x) {
   if (sm->coarse == 1) return poly_gs_steps(L, b, x, sm->nu, sm->terms);
@@ -1724,10 +1751,8 @@ static int multilevel(const orc_amg* h, int l, const amg_smoother* sm, const dou
   if (l == h->nlev - 1) /* coarsest level: direct solve */
     return dense_solve(n, L->ap, L->ac, L->av, b, x);
   int st;
-  if (l == 0) { /* pre-smoothing with the ILU smoother */
-    if ((st = orc_smooth(n, 1, L->ap, L->ac, L->av, sm->lp, sm->lc, sm->lv, sm->sp, sm->sc, sm->sv, sm->dinv, x, b,
-                         sm->mL, sm->mU)))
-      return st;
+  if (l == 0) { /* pre-smoothing with the finest level's smoother */
+    if ((st = fine_smooth(L, sm, b, x))) return st;
   } else {
     if ((st = coarse_smooth(L, sm, b, x))) return st;
   }
@@ -1746,8 +1771,7 @@ static int multilevel(const orc_amg* h, int l, const amg_smoother* sm, const dou
       x[i] = x[i] + s;
     }
     if (l == 0)
-      st = orc_smooth(n, 1, L->ap, L->ac, L->av, sm->lp, sm->lc, sm->lv, sm->sp, sm->sc, sm->sv, sm->dinv, x, b,
-                      sm->mL, sm->mU);
+      st = fine_smooth(L, sm, b, x);
     else
       st = coarse_smooth(L, sm, b, x);
   }
@@ -1770,7 +1794,21 @@ static int multilevel(const orc_amg* h, int l, const amg_smoother* sm, const dou
 int orc_amg_vcycle(const orc_amg* h, const int64_t* lp, const int32_t* lc, const double* lv, const int64_t* sp,
                    const int32_t* sc, const double* sv, const double* dinv, int mL, int mU, int nu, int coarse,
                    int terms, double* x, const double* b) {
-  amg_smoother sm = {lp, sp, lc, sc, lv, sv, dinv, mL, mU, nu, coarse, terms};
+  amg_smoother sm = {lp, sp, lc, sc, lv, sv, dinv, mL, mU, nu, coarse, terms, 0, 0.0, 0};
+  return multilevel(h, 0, &sm, b, x);
+}
+
+/*
+ * The same V-cycle with the finest level smoothed, before and after the
+ * coarse-grid correction, by one application of the ILUT Schur complement
+ * smoother (Sec. 3.1: the smoother of one level of the V-cycle; orc_schur_apply
+ * over `parts` row blocks, ILUT(tau, fill) of each block, m_L + m_U sweeps)
+ * instead of the ILU smoother.
+ */
+int orc_amg_vcycle_schur(const orc_amg* h, int parts, double tau, int fill, int mL, int mU, int nu, int coarse,
+                         int terms, double* x, const double* b) {
+  if (parts <= 0) return ORC_BADARG;
+  amg_smoother sm = {NULL, NULL, NULL, NULL, NULL, NULL, NULL, mL, mU, nu, coarse, terms, parts, tau, fill};
   return multilevel(h, 0, &sm, b, x);
 }
 

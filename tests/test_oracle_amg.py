@@ -155,6 +155,52 @@ def test_two_level_cycle_is_the_two_grid_operator():
     assert relerr(got, x3) < 1e-12
 
 
+def test_two_level_cycle_with_the_schur_smoother_is_the_two_grid_composition():
+    """The V-cycle with the ILUT Schur complement smoother on the finest level
+    (Sec. 3.1: the smoother of one level of the V-cycle) = one application of
+    schur_apply to the residual before and after the exact coarse correction
+    x + P A_c^{-1} P^T (b - A x), composed here from schur_apply and a dense
+    coarse solve (the smoother is not linear in r, so the composition applies
+    it to each residual)."""
+    A = synth.cutcell7(9, 8, 7, seed=6)
+    n = len(A[0]) - 1
+    H = oracle.AMG(A, theta=0.25, max_levels=2, coarse_size=1)
+    assert len(H.levels) == 2
+    L0, C = H.levels
+    P = np.zeros((n, C.n))
+    pp, pc, pv = L0.P
+    for i in range(n):
+        for q in range(pp[i], pp[i + 1]):
+            P[i, pc[q]] = pv[q]
+    Ad = dense(A, n)
+    b = synth.rhs(n, 1, seed=2)[:, 0]
+    x0 = synth.rhs(n, 1, seed=3)[:, 0]
+    parts, tau, fill, mL, mU = 3, 1e-3, 6, 3, 2
+    x1 = x0 + oracle.schur_apply(A, b - Ad @ x0, parts, tau, fill, mL, mU)
+    x2 = x1 + P @ np.linalg.solve(P.T @ Ad @ P, P.T @ (b - Ad @ x1))
+    x3 = x2 + oracle.schur_apply(A, b - Ad @ x2, parts, tau, fill, mL, mU)
+    got = H.vcycle_schur(x0, b, parts, tau, fill, mL, mU)
+    assert relerr(got, x3) < 1e-12
+    assert oracle.schur_interface(A, parts)[0] > 0
+
+
+def test_schur_smoothed_cycle_with_one_part_is_the_ilut_cycle():
+    """One part has no interface rows, and the Schur complement smoother is
+    then the ILUT smoother of the whole matrix: the cycle equals the ILU-smoothed
+    V-cycle with the row-scaled ILUT(tau, fill) factors, on three levels with
+    l1-Jacobi below."""
+    A = synth.cutcell7(10, 9, 8, seed=8)
+    n = len(A[0]) - 1
+    H = oracle.AMG(A, theta=0.25, max_levels=3, coarse_size=1)
+    assert len(H.levels) == 3
+    S = oracle.row_scale(oracle.factor(A, "ilut", 1e-3, 6))
+    b = synth.rhs(n, 1, seed=4)[:, 0]
+    x0 = synth.rhs(n, 1, seed=5)[:, 0]
+    want = H.vcycle(S, x0, b, 4, 3)
+    got = H.vcycle_schur(x0, b, 1, 1e-3, 6, 4, 3)
+    assert relerr(got, want) < 1e-12
+
+
 def test_single_level_is_a_direct_solve():
     A = synth.cutcell7(5, 4, 4, seed=7)
     n = len(A[0]) - 1
