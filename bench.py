@@ -1145,14 +1145,19 @@ def sweep_study(silu, ctx, torch):
     return out
 
 
-def schur_study(silu, ctx, torch, edge=EDGE, parts=(8, 64), kind="cutcell7", sweeps=(3,)):
+def schur_study(silu, ctx, torch, edge=EDGE, parts=(8, 64), kind="cutcell7", sweeps=(3,), maxit=3000):
     """The ILUT Schur complement smoother (Sec. 3.1, Eq. schur) on the 128^3
     cut-cell matrix, FP64, the rows split into `parts` contiguous blocks (as
     ranks would hold them): setup time, interior and interface rows, one
     smoother application (3+3 sweeps on each block's ILUT(1e-3, 10) factors,
     no residual of the whole system formed), and FGMRES(30) to 1e-8 from zero
     preconditioned by it, against the single-level smoother (ILUT(1e-3, 10),
-    3+3 sweeps) and exact solves of the same factors."""
+    3+3 sweeps) and exact solves of the same factors.  Then the smoother where
+    the paper places it: on the finest level of the Ruge-Stueben V-cycle
+    (theta 0.25, coarsest <= 400 rows, l1-Jacobi below), against the same
+    cycle smoothed by ILUT(1e-3, 10) sweeps on the whole finest level.  A
+    configuration that has not converged after `maxit` iterations is reported
+    once (no second, graph-replayed solve)."""
     import synth
     A = synth.cutcell7(edge, seed=1) if kind == "cutcell7" else synth.poisson7(edge)
     n = len(A[0]) - 1
@@ -1167,12 +1172,19 @@ def schur_study(silu, ctx, torch, edge=EDGE, parts=(8, 64), kind="cutcell7", swe
             x = torch.zeros(n, dtype=torch.float64, device="cuda")
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            st, its, rr = silu.fgmres_solve(F, x, b, tol=1e-8, restart=30, maxit=3000, sweeps_L=mL, sweeps_U=mU,
+            st, its, rr = silu.fgmres_solve(F, x, b, tol=1e-8, restart=30, maxit=maxit, sweeps_L=mL, sweeps_U=mU,
                                             precond=pre)
             torch.cuda.synchronize()
             rec = {"seconds": round(time.perf_counter() - t0, 4), "iterations": its, "relres": float(f"{rr:.3e}"),
                    "converged": st == silu.OK}
+            if st != silu.OK:
+                break
         return rec
+
+    def amg(F):
+        t0 = time.perf_counter()
+        F.amg_setup(theta=0.25, max_levels=25, coarse_size=400, jacobi_sweeps=1)
+        return round(time.perf_counter() - t0, 2)
 
     for p in parts:
         F = silu.ilu_setup(ctx, M, "ilu0")
@@ -1194,14 +1206,37 @@ def schur_study(silu, ctx, torch, edge=EDGE, parts=(8, 64), kind="cutcell7", swe
                "apply_3_3_ms": round(e0.elapsed_time(e1) / 20, 4)}
         for m in sweeps:
             rec[f"fgmres_{m}_{m}"] = solve(F, silu.PRECOND_SCHUR, m, m)
+        rec["amg_setup_s"] = amg(F)
+        rec["amg_levels"] = F.amg_stats()["levels"]
+        for m in sweeps:
+            rec[f"amg_schur_fgmres_{m}_{m}"] = solve(F, silu.PRECOND_AMG_SCHUR, m, m)
         out[f"parts_{p}"] = rec
         del F
     F = silu.ilu_setup(ctx, M, "ilut", 1e-3, 10)
     for m in sweeps:
         out[f"single_level_ilut_{m}_{m}"] = solve(F, silu.PRECOND_SWEEPS, m, m)
     out["single_level_ilut_direct"] = solve(F, silu.PRECOND_DIRECT, 0, 0)
+    amg(F)
+    for m in sweeps:
+        out[f"amg_ilut_{m}_{m}"] = solve(F, silu.PRECOND_AMG, m, m)
     del F
     return out
+
+
+def run_schur_study(args):
+    """Only the Schur complement smoother study (schur_study) on one GPU, one
+    JSON line: --schur-study KIND:EDGE (cutcell7 or poisson7)."""
+    import torch
+    import paper_2111_09512_gb300 as silu
+    silu.build()
+    ctx = silu.Context(0, torch.cuda.current_stream())
+    kind, edge = args.schur_study.split(":")
+    if kind not in ("cutcell7", "poisson7"):
+        raise SystemExit(f"unknown matrix kind {kind}")
+    sweeps = tuple(int(m) for m in args.schur_sweeps.split(","))
+    out = schur_study(silu, ctx, torch, edge=int(edge), kind=kind, sweeps=sweeps, maxit=args.schur_maxit)
+    print(json.dumps({"schur_study": out}), flush=True)
+    return 0
 
 
 def run_apply_only(args):
@@ -1316,6 +1351,11 @@ def main():
     ap.add_argument("--apply-only", choices=["cutcell128", "cutcell128_r4", "hex27_256", "hex27_128",
                                              "hex27_128_direct", "poisson32_r4"], default=None,
                     help="run only smoother applications of one workload (profiling, quick timing)")
+    ap.add_argument("--schur-study", default=None, metavar="KIND:EDGE",
+                    help="run only the Schur complement smoother study on cutcell7:EDGE or poisson7:EDGE")
+    ap.add_argument("--schur-maxit", type=int, default=3000)
+    ap.add_argument("--schur-sweeps", default="3", metavar="M[,M...]",
+                    help="m_L = m_U sweep counts of the Schur complement smoother study")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
@@ -1325,6 +1365,8 @@ def main():
         return run_reference(args)
     if args.apply_only:
         return run_apply_only(args)
+    if args.schur_study:
+        return run_schur_study(args)
     return run_silu(args)
 
 

@@ -104,7 +104,9 @@ typedef enum {
   SILU_PRECOND_NONE = 2,
   SILU_PRECOND_AMG = 3,
   SILU_PRECOND_AMG_DIRECT = 4,
-  SILU_PRECOND_SCHUR = 5  /* one application of the Schur complement smoother (silu_schur_setup) */
+  SILU_PRECOND_SCHUR = 5, /* one application of the Schur complement smoother (silu_schur_setup) */
+  SILU_PRECOND_AMG_SCHUR = 6 /* one AMG V-cycle whose finest level is smoothed by the Schur complement
+                                smoother (silu_amg_setup and silu_schur_setup; Sec. 3.1) */
 } silu_precond;
 
 typedef struct silu_ctx_s* silu_ctx;
@@ -491,6 +493,17 @@ silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params);
  * is the direct solve x = A^{-1} b.
  */
 silu_status silu_amg_vcycle(silu_ilu F, double* x, const double* b, int sweeps_L, int sweeps_U);
+/*
+ * The same V-cycle with the finest level smoothed, before and after the
+ * coarse-grid correction, by one application of the ILUT Schur complement
+ * smoother (silu_schur_setup; Sec. 3.1 uses it as the smoother of one level of
+ * the V-cycle), its interior blocks swept sweeps_L + sweeps_U
+ * times; coarser levels as in silu_amg_vcycle.  x (n FP64, device) is updated
+ * in place from its current value; b is read.  Requires silu_amg_setup and
+ * silu_schur_setup on F (else SILU_ERR_INVALID_ARG), negative sweep counts
+ * -> SILU_ERR_INVALID_ARG.  Stream-ordered on F's context.
+ */
+silu_status silu_amg_vcycle_schur(silu_ilu F, double* x, const double* b, int sweeps_L, int sweeps_U);
 /* Levels and, for l < cap, rows, entries of A_l and of P_l (0 on the coarsest level). */
 silu_status silu_amg_stats(silu_ilu F, int cap, int* levels, int64_t* rows, int64_t* nnz_A, int64_t* nnz_P);
 /* Host copies of level l (parity tests): A_l (row pointers n_l + 1), P_l

@@ -35,6 +35,7 @@ SCALE_NONE, SCALE_ROW, SCALE_NONE_RICH, SCALE_ROWCOL = 0, 1, 2, 3
 FP64, FP32 = 0, 1
 # silu_precond
 PRECOND_SWEEPS, PRECOND_DIRECT, PRECOND_NONE, PRECOND_AMG, PRECOND_AMG_DIRECT, PRECOND_SCHUR = 0, 1, 2, 3, 4, 5
+PRECOND_AMG_SCHUR = 6
 # silu_kclass
 K_RESIDUAL, K_SWEEP_L, K_SWEEP_U, K_LEVEL, K_KRYLOV, K_ELEMENTWISE = range(6)
 K_NAMES = ["residual", "sweep_L", "sweep_U", "level", "krylov", "elementwise", "fused"]
@@ -107,6 +108,7 @@ def load():
         "silu_ilu_dep": (i32, [vp, ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]),
         "silu_amg_setup": (i32, [vp, vp]),
         "silu_amg_vcycle": (i32, [vp, vp, vp, i32, i32]),
+        "silu_amg_vcycle_schur": (i32, [vp, vp, vp, i32, i32]),
         "silu_amg_stats": (i32, [vp, i32, ctypes.POINTER(i32), vp, vp, vp]),
         "silu_amg_export_level": (i32, [vp, i32] + [vp] * 7),
         "silu_schur_setup": (i32, [vp, i32, dbl, i32]),
@@ -155,7 +157,7 @@ def exported_symbols():
     return ["silu_version", "silu_ctx_create", "silu_ctx_destroy", "silu_last_error", "silu_mat_create",
             "silu_mat_destroy", "silu_mat_residual", "silu_mat_set_shape", "silu_mat_autotune", "ilu_setup", "ilu_refactor", "silu_ilu_save", "silu_ilu_load", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
-            "silu_ilu_export_colscale", "silu_ilu_power_norms", "silu_ilu_dep", "silu_amg_setup", "silu_amg_vcycle",
+            "silu_ilu_export_colscale", "silu_ilu_power_norms", "silu_ilu_dep", "silu_amg_setup", "silu_amg_vcycle", "silu_amg_vcycle_schur",
             "silu_amg_stats", "silu_amg_export_level", "silu_schur_setup", "silu_schur_smooth",
             "silu_schur_stats",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
@@ -424,6 +426,12 @@ class ILU:
         """One V-cycle on A x = b (device tensors of length n), x in/out."""
         _check(self.ctx.handle, load().silu_amg_vcycle(self.handle, _ptr(x), _ptr(b), int(sweeps_L),
                                                        int(sweeps_U)), "silu_amg_vcycle")
+
+    def amg_vcycle_schur(self, x, b, sweeps_L: int, sweeps_U: int):
+        """One V-cycle whose finest level is smoothed by the Schur complement smoother (schur_setup),
+        x in/out."""
+        _check(self.ctx.handle, load().silu_amg_vcycle_schur(self.handle, _ptr(x), _ptr(b), int(sweeps_L),
+                                                             int(sweeps_U)), "silu_amg_vcycle_schur")
 
     def amg_stats(self):
         """Per level: rows, entries of A_l, entries of P_l."""

@@ -155,7 +155,7 @@ cudaError_t upload_level(const silu::AmgLevel& H, AmgDevLevel& D, bool own_a, bo
 
 namespace silu {
 
-void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_zero, bool capturing) {
+void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_zero, bool capturing, bool schur) {
   AmgState& G = *F->amg;
   AmgDevLevel& L0 = *G.lev[0];
   if (G.lev.size() == 1) {  // a single level: the direct solve
@@ -166,12 +166,25 @@ void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_ze
   }
   const DevCsr& A = F->A->d;
   AmgDevLevel& C = *G.lev[1];
-  // finest-level smoother: Richardson sweeps, or the exact triangular solves when mL < 0
+  // finest-level smoother: Richardson sweeps, the exact triangular solves
+  // when mL < 0, or one application of the ILUT Schur complement smoother
+  // (Sec. 3.1; m_L + m_U sweeps in each block): x (+)= M^{-1} (b - A x)
   auto smooth = [&](bool xz) {
-    if (mL < 0)
+    if (schur) {
+      if (xz) {
+        schur_apply(F, b, x, mL, mU);  // x = M^{-1} b (every row written)
+      } else {
+        double* r = F->schur->r.as<double>();
+        double* z = F->ws.r.as<double>();
+        op(F, A, SILU_K_RESIDUAL, b, x, r, nullptr, nullptr, EPI_STORE);
+        schur_apply(F, r, z, mL, mU);
+        LAUNCH(F->ctx, SILU_K_ELEMENTWISE, launch_addx((int)L0.n, 1, 1, z, false, nullptr, x, true, F->ctx->stream));
+      }
+    } else if (mL < 0) {
       direct_chunk(F, x, b, 1, 1, 0, xz, capturing);
-    else
+    } else {
       smooth_chunk(F, x, b, 1, 1, 0, mL, mU, xz);
+    }
   };
   smooth(x_zero);                                                                   // pre-smoothing
   op(F, A, SILU_K_RESIDUAL, b, x, L0.r.as<double>(), nullptr, nullptr, EPI_STORE);  // r = b - A x
@@ -242,7 +255,25 @@ silu_status silu_amg_vcycle(silu_ilu F, double* x, const double* b, int sweeps_L
   try {
     CK(silu::ensure_vectors(F, 1));
     if (sweeps_L < 0) CK(silu::ensure_direct(F));
-    silu::amg_cycle(F, x, b, sweeps_L, sweeps_U, false, false);
+    silu::amg_cycle(F, x, b, sweeps_L, sweeps_U, false, false, false);
+  } catch (const CudaFail& f) {
+    return silu::cuda_err(ctx, f.e, f.what);
+  }
+  return SILU_OK;
+}
+
+silu_status silu_amg_vcycle_schur(silu_ilu F, double* x, const double* b, int sweeps_L, int sweeps_U) {
+  NvtxRange nvtx_("silu:silu_amg_vcycle_schur");
+  if (!F || !x || !b || sweeps_L < 0 || sweeps_U < 0) return SILU_ERR_INVALID_ARG;
+  silu_ctx ctx = F->ctx;
+  if (!F->amg) return silu::set_err(ctx, SILU_ERR_INVALID_ARG, "no AMG hierarchy (silu_amg_setup)");
+  if (!F->schur) return silu::set_err(ctx, SILU_ERR_INVALID_ARG, "no Schur complement smoother (silu_schur_setup)");
+  silu_status ds = silu::device_ok(ctx);
+  if (ds != SILU_OK) return ds;
+  if (F->F.L.n == 0) return SILU_OK;
+  try {
+    CK(silu::ensure_vectors(F, 1));
+    silu::amg_cycle(F, x, b, sweeps_L, sweeps_U, false, false, true);
   } catch (const CudaFail& f) {
     return silu::cuda_err(ctx, f.e, f.what);
   }

@@ -787,9 +787,11 @@ void fgmres_inner(silu_ilu F, int j, int m, int mL, int mU, int precond, bool ca
   else if (precond == SILU_PRECOND_DIRECT)
     direct_chunk(F, zj, vj, 1, 1, 0, true, capturing);
   else if (precond == SILU_PRECOND_AMG)
-    amg_cycle(F, zj, vj, mL, mU, true, capturing);
+    amg_cycle(F, zj, vj, mL, mU, true, capturing, false);
   else if (precond == SILU_PRECOND_AMG_DIRECT)
-    amg_cycle(F, zj, vj, -1, -1, true, capturing);
+    amg_cycle(F, zj, vj, -1, -1, true, capturing, false);
+  else if (precond == SILU_PRECOND_AMG_SCHUR)
+    amg_cycle(F, zj, vj, mL, mU, true, capturing, true);
   else if (precond == SILU_PRECOND_SCHUR)
     schur_apply(F, vj, zj, mL, mU);
   else
@@ -1619,8 +1621,10 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
   if (iters_out) *iters_out = 0;
   if (relres_out) *relres_out = 0.0;
   if (!x || !b || !(tol >= 0.0) || restart < 1 || maxit < 0 || sweeps_L < 0 || sweeps_U < 0 || precond < 0 ||
-      precond > 5 || ((precond == SILU_PRECOND_AMG || precond == SILU_PRECOND_AMG_DIRECT) && !F->amg) ||
-      (precond == SILU_PRECOND_SCHUR && !F->schur))
+      precond > 6 ||
+      ((precond == SILU_PRECOND_AMG || precond == SILU_PRECOND_AMG_DIRECT || precond == SILU_PRECOND_AMG_SCHUR) &&
+       !F->amg) ||
+      ((precond == SILU_PRECOND_SCHUR || precond == SILU_PRECOND_AMG_SCHUR) && !F->schur))
     return set_err(ctx, SILU_ERR_INVALID_ARG, "fgmres_solve: bad argument");
   silu_status ds = device_ok(ctx);
   if (ds != SILU_OK) return ds;

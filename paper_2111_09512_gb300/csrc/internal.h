@@ -372,11 +372,15 @@ void smooth_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
 void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t col, bool x_zero,
                   bool inline_levels = false);
 // One AMG V-cycle (Alg. mgcycle) on A x = b for one right-hand side, the
-// finest level smoothed by m_L + m_U sweeps of F's smoother, or by its exact
-// triangular solves when mL < 0 (x_zero: x is an output, the cycle starts
-// from zero; capturing: a stream capture is recording).  Requires F->amg and
-// F's one-column workspace (and ensure_direct for mL < 0).
-void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_zero, bool capturing);
+// finest level smoothed by m_L + m_U sweeps of F's smoother, by its exact
+// triangular solves when mL < 0, or, with schur, by one application of F's
+// Schur complement smoother (m_L + m_U sweeps in its blocks) before and after
+// the coarse-grid correction (x_zero: x is an output, the cycle starts from
+// zero; capturing: a stream capture is recording).  Requires F->amg (and
+// F->schur with schur) and F's one-column workspace (and ensure_direct for
+// mL < 0).
+void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_zero, bool capturing,
+               bool schur = false);
 // z = M^{-1} r of F's Schur complement smoother (one right-hand side,
 // device vectors of n entries; z is written).  Requires F->schur.
 void schur_apply(silu_ilu F, const double* r, double* z, int mL, int mU);
