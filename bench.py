@@ -1145,26 +1145,31 @@ def sweep_study(silu, ctx, torch):
     return out
 
 
-def schur_study(silu, ctx, torch, edge=EDGE, parts=(8, 64), kind="cutcell7", sweeps=(3,), maxit=3000):
-    """The ILUT Schur complement smoother (Sec. 3.1, Eq. schur) on the 128^3
-    cut-cell matrix, FP64, the rows split into `parts` contiguous blocks (as
-    ranks would hold them): setup time, interior and interface rows, one
-    smoother application (3+3 sweeps on each block's ILUT(1e-3, 10) factors,
-    no residual of the whole system formed), and FGMRES(30) to 1e-8 from zero
-    preconditioned by it, against the single-level smoother (ILUT(1e-3, 10),
-    3+3 sweeps) and exact solves of the same factors.  Then the smoother where
-    the paper places it: on the finest level of the Ruge-Stueben V-cycle
-    (theta 0.25, coarsest <= 400 rows, l1-Jacobi below), against the same
-    cycle smoothed by ILUT(1e-3, 10) sweeps on the whole finest level.  A
+def schur_study(silu, ctx, torch, edge=EDGE, parts=(8, 64), kind="cutcell7", sweeps=(3,), maxit=3000, tau=1e-3,
+                fill=10, theta=0.25):
+    """The ILUT Schur complement smoother (Sec. 3.1, Eq. schur) on an edge^3
+    matrix (cut-cell 7-point by default; Poisson or the 27-point perturbed
+    hex), FP64, the rows split into `parts` contiguous blocks (as ranks would
+    hold them): setup time, interior and interface rows, one smoother
+    application (3+3 sweeps on each block's ILUT(tau, fill) factors, no
+    residual of the whole system formed), and FGMRES(30) to 1e-8 from zero
+    preconditioned by it (m+m sweeps for each m in `sweeps`), against the
+    single-level smoother (ILUT(tau, fill), m+m sweeps) and exact solves of
+    the same factors.  Then the smoother where the paper places it: on the
+    finest level of the Ruge-Stueben V-cycle (strength theta, coarsest <= 400
+    rows, l1-Jacobi below), against the same cycle smoothed by ILUT(tau, fill)
+    sweeps on the whole finest level.  A
     configuration that has not converged after `maxit` iterations is reported
     once (no second, graph-replayed solve)."""
     import synth
-    A = synth.cutcell7(edge, seed=1) if kind == "cutcell7" else synth.poisson7(edge)
+    A = {"cutcell7": lambda: synth.cutcell7(edge, seed=1), "poisson7": lambda: synth.poisson7(edge),
+         "hex27": lambda: synth.hex27(edge, seed=2)}[kind]()
     n = len(A[0]) - 1
     M = silu.Matrix(ctx, *A)
     del A
     b = torch.from_numpy(synth.rhs(n, 1, seed=1)[:, 0].copy()).cuda()
-    out = {"workload": f"{kind}-{edge}^3 FP64, FGMRES(30) to 1e-8 from x = 0", "rows": n}
+    out = {"workload": f"{kind}-{edge}^3 FP64, FGMRES(30) to 1e-8 from x = 0", "rows": n,
+           "ilut": {"tau": tau, "fill": fill}, "theta": theta}
 
     def solve(F, pre, mL, mU):
         rec = None
@@ -1183,13 +1188,13 @@ def schur_study(silu, ctx, torch, edge=EDGE, parts=(8, 64), kind="cutcell7", swe
 
     def amg(F):
         t0 = time.perf_counter()
-        F.amg_setup(theta=0.25, max_levels=25, coarse_size=400, jacobi_sweeps=1)
+        F.amg_setup(theta=theta, max_levels=25, coarse_size=400, jacobi_sweeps=1)
         return round(time.perf_counter() - t0, 2)
 
     for p in parts:
         F = silu.ilu_setup(ctx, M, "ilu0")
         t0 = time.perf_counter()
-        F.schur_setup(p, 1e-3, 10)
+        F.schur_setup(p, tau, fill)
         setup_s = time.perf_counter() - t0
         st = F.schur_stats()
         x = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -1212,7 +1217,7 @@ def schur_study(silu, ctx, torch, edge=EDGE, parts=(8, 64), kind="cutcell7", swe
             rec[f"amg_schur_fgmres_{m}_{m}"] = solve(F, silu.PRECOND_AMG_SCHUR, m, m)
         out[f"parts_{p}"] = rec
         del F
-    F = silu.ilu_setup(ctx, M, "ilut", 1e-3, 10)
+    F = silu.ilu_setup(ctx, M, "ilut", tau, fill)
     for m in sweeps:
         out[f"single_level_ilut_{m}_{m}"] = solve(F, silu.PRECOND_SWEEPS, m, m)
     out["single_level_ilut_direct"] = solve(F, silu.PRECOND_DIRECT, 0, 0)
@@ -1231,10 +1236,12 @@ def run_schur_study(args):
     silu.build()
     ctx = silu.Context(0, torch.cuda.current_stream())
     kind, edge = args.schur_study.split(":")
-    if kind not in ("cutcell7", "poisson7"):
+    if kind not in ("cutcell7", "poisson7", "hex27"):
         raise SystemExit(f"unknown matrix kind {kind}")
     sweeps = tuple(int(m) for m in args.schur_sweeps.split(","))
-    out = schur_study(silu, ctx, torch, edge=int(edge), kind=kind, sweeps=sweeps, maxit=args.schur_maxit)
+    parts = tuple(int(p) for p in args.schur_parts.split(","))
+    out = schur_study(silu, ctx, torch, edge=int(edge), parts=parts, kind=kind, sweeps=sweeps, maxit=args.schur_maxit,
+                      tau=args.schur_tau, fill=args.schur_fill, theta=args.schur_theta)
     print(json.dumps({"schur_study": out}), flush=True)
     return 0
 
@@ -1352,7 +1359,11 @@ def main():
                                              "hex27_128_direct", "poisson32_r4"], default=None,
                     help="run only smoother applications of one workload (profiling, quick timing)")
     ap.add_argument("--schur-study", default=None, metavar="KIND:EDGE",
-                    help="run only the Schur complement smoother study on cutcell7:EDGE or poisson7:EDGE")
+                    help="run only the Schur complement smoother study on cutcell7:EDGE, poisson7:EDGE or hex27:EDGE")
+    ap.add_argument("--schur-parts", default="8,64", metavar="P[,P...]")
+    ap.add_argument("--schur-tau", type=float, default=1e-3)
+    ap.add_argument("--schur-fill", type=int, default=10)
+    ap.add_argument("--schur-theta", type=float, default=0.25)
     ap.add_argument("--schur-maxit", type=int, default=3000)
     ap.add_argument("--schur-sweeps", default="3", metavar="M[,M...]",
                     help="m_L = m_U sweep counts of the Schur complement smoother study")
