@@ -102,6 +102,7 @@ def _load():
         "orc_schur_interface": (i64, [i64, vp, vp, i32, vp]),
         "orc_schur_apply": (i32, [i64, vp, vp, vp, i32, dbl, i32, i32, i32, vp, vp]),
         "orc_amg_vcycle_schur": (i32, [vp, i32, dbl, i32, i32, i32, i32, i32, i32, vp, vp]),
+        "orc_amg_vcycle_ilu": (i32, [vp, i32] + [vp] * 9 + [i32, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -570,6 +571,41 @@ class AMG:
                                     int(mU), int(nu), 1 if coarse == "gs" else 0, int(terms), _p(x), _p(b))
         if st:
             raise OracleError(st, "amg_vcycle")
+        return x
+
+    def level_factors(self, kind: str = "ilu0", tau: float = 0.0, fill: int = 0, count: int | None = None):
+        """Row-scaled incomplete factors of A_l for the first `count` levels (default: every level
+        above the coarsest), for vcycle_ilu."""
+        top = max(len(self.levels) - 1, 1)
+        k = top if count is None else max(1, min(int(count), top))
+        return [row_scale(factor(self.levels[l].A, kind, tau, fill)) for l in range(k)]
+
+    def vcycle_ilu(self, factors, x, b, mL, mU, nu: int = 1, coarse: str = "jacobi", terms: int = 2):
+        """One V-cycle as vcycle with the ILU smoother on the first len(factors) levels: level l
+        is smoothed by m_L + m_U sweeps on factors[l] (the row-scaled factors of A_l; mL, mU an
+        int or one count per level), the levels below by the coarse smoother.  Returns a new
+        array."""
+        k = len(factors)
+        n = self.levels[0].n
+        x = np.ascontiguousarray(x, np.float64).reshape(n).copy()
+        b = np.ascontiguousarray(b, np.float64).reshape(n)
+        mLs = np.ascontiguousarray(np.broadcast_to(np.asarray(mL, np.int32), (k,)), np.int32)
+        mUs = np.ascontiguousarray(np.broadcast_to(np.asarray(mU, np.int32), (k,)), np.int32)
+        keep = []
+
+        def ptrs(arrays):
+            arrs = [np.ascontiguousarray(a) for a in arrays]
+            keep.extend(arrs)
+            return (ctypes.c_void_p * k)(*[a.ctypes.data for a in arrs])
+
+        Ls = [_csr(S.L) for S in factors]
+        Us = [_csr(S.Us) for S in factors]
+        st = _load().orc_amg_vcycle_ilu(self._h, k, ptrs([t[0] for t in Ls]), ptrs([t[1] for t in Ls]),
+                                        ptrs([t[2] for t in Ls]), ptrs([t[0] for t in Us]), ptrs([t[1] for t in Us]),
+                                        ptrs([t[2] for t in Us]), ptrs([S.dinv for S in factors]), _p(mLs), _p(mUs),
+                                        int(nu), 1 if coarse == "gs" else 0, int(terms), _p(x), _p(b))
+        if st:
+            raise OracleError(st, "amg_vcycle_ilu")
         return x
 
     def vcycle_schur(self, x, b, parts: int, tau: float, fill: int, mL: int, mU: int, nu: int = 1,

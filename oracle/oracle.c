@@ -1702,6 +1702,15 @@ static int poly_gs_steps(const orc_amg_level* L, const double* b, double* x, int
   return st;
 }
 
+/* the ILU smoother of one level below the finest: row-scaled factors of A_l
+   and its sweep counts */
+typedef struct {
+  const int64_t *lp, *sp;
+  const int32_t *lc, *sc;
+  const double *lv, *sv, *dinv;
+  int mL, mU;
+} level_ilu;
+
 typedef struct {
   const int64_t *lp, *sp;
   const int32_t *lc, *sc;
@@ -1715,6 +1724,10 @@ typedef struct {
   int schur_parts;
   double schur_tau;
   int schur_fill;
+  /* levels 1 .. ilu_levels - 1 (above the coarsest) are smoothed by the ILU
+     smoother on ilu[l] instead of the coarse smoother */
+  int ilu_levels;
+  const level_ilu* ilu;
 } amg_smoother;
 
 int orc_schur_apply(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, int parts, double tau,
@@ -1744,6 +1757,19 @@ static int coarse_smooth(const orc_amg_level* L, const amg_smoother* sm, const d
   return ORC_OK;
 }
 
+/* The smoother of level l >= 0 (not the coarsest): the finest level's, the
+   ILU smoother x = x + M_l^{-1} (b - A_l x) on level l's own factors where
+   the cycle asks for ILU on that level, else the coarse smoother. */
+static int level_smooth(int l, const orc_amg_level* L, const amg_smoother* sm, const double* b, double* x) {
+  if (l == 0) return fine_smooth(L, sm, b, x);
+  if (l < sm->ilu_levels) {
+    const level_ilu* f = &sm->ilu[l];
+    return orc_smooth(L->n, 1, L->ap, L->ac, L->av, f->lp, f->lc, f->lv, f->sp, f->sc, f->sv, f->dinv, x, b, f->mL,
+                      f->mU);
+  }
+  return coarse_smooth(L, sm, b, x);
+}
+
 /* Alg. mgcycle, Multilevel(A_l, b, x, l) with nu = 1 (V-cycle). */
 static int multilevel(const orc_amg* h, int l, const amg_smoother* sm, const double* b, double* x) {
   const orc_amg_level* L = &h->lev[l];
@@ -1751,11 +1777,7 @@ static int multilevel(const orc_amg* h, int l, const amg_smoother* sm, const dou
   if (l == h->nlev - 1) /* coarsest level: direct solve */
     return dense_solve(n, L->ap, L->ac, L->av, b, x);
   int st;
-  if (l == 0) { /* pre-smoothing with the finest level's smoother */
-    if ((st = fine_smooth(L, sm, b, x))) return st;
-  } else {
-    if ((st = coarse_smooth(L, sm, b, x))) return st;
-  }
+  if ((st = level_smooth(l, L, sm, b, x))) return st; /* pre-smoothing */
   double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   double* bc = (double*)calloc((size_t)(L->nc > 0 ? L->nc : 1), sizeof(double));
   double* v = (double*)calloc((size_t)(L->nc > 0 ? L->nc : 1), sizeof(double));
@@ -1770,10 +1792,7 @@ static int multilevel(const orc_amg* h, int l, const amg_smoother* sm, const dou
       for (int64_t q = L->pp[i]; q < L->pp[i + 1]; ++q) s = s + L->pv[q] * v[L->pc[q]];
       x[i] = x[i] + s;
     }
-    if (l == 0)
-      st = fine_smooth(L, sm, b, x);
-    else
-      st = coarse_smooth(L, sm, b, x);
+    st = level_smooth(l, L, sm, b, x); /* post-smoothing */
   }
   free(r);
   free(bc);
@@ -1794,8 +1813,36 @@ static int multilevel(const orc_amg* h, int l, const amg_smoother* sm, const dou
 int orc_amg_vcycle(const orc_amg* h, const int64_t* lp, const int32_t* lc, const double* lv, const int64_t* sp,
                    const int32_t* sc, const double* sv, const double* dinv, int mL, int mU, int nu, int coarse,
                    int terms, double* x, const double* b) {
-  amg_smoother sm = {lp, sp, lc, sc, lv, sv, dinv, mL, mU, nu, coarse, terms, 0, 0.0, 0};
+  amg_smoother sm = {lp, sp, lc, sc, lv, sv, dinv, mL, mU, nu, coarse, terms, 0, 0.0, 0, 1, NULL};
   return multilevel(h, 0, &sm, b, x);
+}
+
+/*
+ * The V-cycle with the ILU smoother on the first `nilu` levels (Sec. 6: the
+ * ILU smoother applied on any number of levels from the finest down, up to
+ * all levels above the coarsest direct solve): level l < nilu is smoothed
+ * before and after its coarse-grid correction by m_L[l] + m_U[l] Richardson
+ * sweeps on its own row-scaled factors (lp[l] .. dinv[l]: L_s, Utilde_s and
+ * D^{-1} of an incomplete factorisation of A_l); the levels below by the
+ * coarse smoother as in orc_amg_vcycle.  Entries at l >= nlev - 1 are not
+ * used.  nilu >= 1 (level 0's factors are entry 0).
+ */
+int orc_amg_vcycle_ilu(const orc_amg* h, int nilu, const int64_t* const* lp, const int32_t* const* lc,
+                       const double* const* lv, const int64_t* const* sp, const int32_t* const* sc,
+                       const double* const* sv, const double* const* dinv, const int* mL, const int* mU, int nu,
+                       int coarse, int terms, double* x, const double* b) {
+  if (nilu < 1) return ORC_BADARG;
+  level_ilu* f = (level_ilu*)malloc(sizeof(level_ilu) * (size_t)nilu);
+  if (!f) return ORC_NOMEM;
+  for (int l = 0; l < nilu; ++l) {
+    level_ilu e = {lp[l], sp[l], lc[l], sc[l], lv[l], sv[l], dinv[l], mL[l], mU[l]};
+    f[l] = e;
+  }
+  amg_smoother sm = {lp[0], sp[0], lc[0], sc[0], lv[0], sv[0], dinv[0], mL[0], mU[0], nu, coarse, terms,
+                     0, 0.0, 0, nilu, f};
+  const int st = multilevel(h, 0, &sm, b, x);
+  free(f);
+  return st;
 }
 
 /*
@@ -1808,7 +1855,7 @@ int orc_amg_vcycle(const orc_amg* h, const int64_t* lp, const int32_t* lc, const
 int orc_amg_vcycle_schur(const orc_amg* h, int parts, double tau, int fill, int mL, int mU, int nu, int coarse,
                          int terms, double* x, const double* b) {
   if (parts <= 0) return ORC_BADARG;
-  amg_smoother sm = {NULL, NULL, NULL, NULL, NULL, NULL, NULL, mL, mU, nu, coarse, terms, parts, tau, fill};
+  amg_smoother sm = {NULL, NULL, NULL, NULL, NULL, NULL, NULL, mL, mU, nu, coarse, terms, parts, tau, fill, 1, NULL};
   return multilevel(h, 0, &sm, b, x);
 }
 

@@ -1,6 +1,7 @@
 """Pins of the oracle's algebraic multigrid (Sec. 3: strength threshold,
 Ruge-Stueben coarsening, Galerkin coarse operators A_{l+1} = P^T A_l P, and
-the V-cycle of Alg. mgcycle with the ILU smoother on the finest level).
+the V-cycle of Alg. mgcycle with the ILU smoother on the finest level, or on
+the first few levels).
 CPU only."""
 import numpy as np
 import pytest
@@ -315,3 +316,105 @@ def test_three_level_cycle_with_polynomial_gs_matches_dense_recursion():
     x3 = oracle.smooth(A, S, x2, b, 2, 2)[:, 0]
     got = H.vcycle(S, np.zeros(n), b, 2, 2, nu=nu, coarse="gs", terms=terms)
     assert relerr(got, x3) < 1e-12
+
+
+def dense_smoother(S, n, mL, mU):
+    """M^{-1} of the row-scaled ILU smoother with m_L + m_U sweeps (Eq. LUiterMat),
+    written as the dense truncated Neumann series (sum_{j<m_U} (-Utilde_s)^j)
+    D^{-1} (sum_{j<m_L} (-L_s)^j)."""
+    Ls, Us = dense(S.L, n), dense(S.Us, n)
+    left = sum(np.linalg.matrix_power(-Us, j) for j in range(mU))
+    right = sum(np.linalg.matrix_power(-Ls, j) for j in range(mL))
+    return left @ np.diag(S.dinv) @ right
+
+
+def test_ilu_on_the_finest_level_only_is_the_mixed_cycle():
+    """vcycle_ilu with one level of factors is vcycle, bit for bit."""
+    A = synth.cutcell7(9, 8, 7, seed=8)
+    n = len(A[0]) - 1
+    H = oracle.AMG(A, theta=0.25, max_levels=4, coarse_size=1)
+    fac = H.level_factors("ilu0")
+    assert len(fac) == len(H.levels) - 1 == 3
+    b = synth.rhs(n, 1, seed=5)[:, 0]
+    x0 = synth.rhs(n, 1, seed=6)[:, 0]
+    for coarse in ("jacobi", "gs"):
+        want = H.vcycle(fac[0], x0, b, 3, 2, nu=2, coarse=coarse, terms=3)
+        assert np.array_equal(H.vcycle_ilu(fac[:1], x0, b, 3, 2, nu=2, coarse=coarse, terms=3), want)
+
+
+def test_three_level_cycle_with_ilu_on_two_levels_matches_dense_recursion():
+    """Alg. mgcycle on three levels with the ILU smoother on levels 0 and 1
+    (Sec. 6: ILU smoothing from the finest level down), each level with its
+    own sweep counts, written densely: x <- x + M_l^{-1} (b - A_l x) with M_l^{-1}
+    the dense Neumann series of level l's row-scaled ILU(0) factors, before
+    and after the correction, direct solve on level 2."""
+    A = synth.cutcell7(9, 8, 7, seed=8)
+    n = len(A[0]) - 1
+    H = oracle.AMG(A, theta=0.25, max_levels=3, coarse_size=1)
+    assert len(H.levels) == 3
+    L0, L1, L2 = H.levels
+
+    def Pmat(L, nc):
+        P = np.zeros((L.n, nc))
+        pp, pc, pv = L.P
+        for i in range(L.n):
+            for q in range(pp[i], pp[i + 1]):
+                P[i, pc[q]] = pv[q]
+        return P
+
+    P0, P1 = Pmat(L0, L1.n), Pmat(L1, L2.n)
+    A0, A1, A2 = dense(A, n), dense(L1.A, L1.n), dense(L2.A, L2.n)
+    S0 = oracle.row_scale(oracle.ilu0(A))
+    S1 = oracle.row_scale(oracle.ilu0(L1.A))
+    mL, mU = (3, 2), (2, 4)
+    M0 = dense_smoother(S0, n, mL[0], mU[0])
+    M1 = dense_smoother(S1, L1.n, mL[1], mU[1])
+
+    def level1(b1):
+        x = M1 @ b1
+        x = x + P1 @ np.linalg.solve(A2, P1.T @ (b1 - A1 @ x))
+        return x + M1 @ (b1 - A1 @ x)
+
+    b = synth.rhs(n, 1, seed=5)[:, 0]
+    x0 = synth.rhs(n, 1, seed=7)[:, 0]
+    x1 = x0 + M0 @ (b - A0 @ x0)
+    x2 = x1 + P0 @ level1(P0.T @ (b - A0 @ x1))
+    x3 = x2 + M0 @ (b - A0 @ x2)
+    got = H.vcycle_ilu([S0, S1], x0, b, list(mL), list(mU), nu=3, coarse="gs", terms=2)
+    assert relerr(got, x3) < 1e-12
+    # the coarse smoother's settings no longer reach level 1
+    assert np.array_equal(got, H.vcycle_ilu([S0, S1], x0, b, list(mL), list(mU), nu=1, coarse="jacobi"))
+    # and level 1 is not smoothed by it: l1-Jacobi there gives another iterate (far outside the
+    # 1e-12 agreement above; the coarse correction is a small part of this iterate)
+    assert relerr(H.vcycle(S0, x0, b, mL[0], mU[0], nu=1), x3) > 1e-9
+
+
+def test_exact_ilu_on_level_one_gives_the_two_grid_cycle():
+    """On the 1-D Laplacian every level is tridiagonal, ILU(0) is its exact LU
+    and n_l + n_l sweeps reach the exact solve (nilpotence): with that
+    smoother on level 1 the coarse-grid correction is exact, so the cycle is
+    the two-grid cycle x + P A_1^{-1} P^T (b - A x) between two finest-level
+    smoothings, whatever the levels below do."""
+    n = 63
+    A = laplace1d(n)
+    H = oracle.AMG(A, theta=0.25, max_levels=6, coarse_size=2)
+    assert len(H.levels) >= 4
+    fac = H.level_factors("ilu0", count=2)
+    n1 = H.levels[1].n
+    L0 = H.levels[0]
+    P = np.zeros((n, n1))
+    pp, pc, pv = L0.P
+    for i in range(n):
+        for q in range(pp[i], pp[i + 1]):
+            P[i, pc[q]] = pv[q]
+    A0 = dense(A, n)
+    M0 = dense_smoother(fac[0], n, 1, 1)  # one sweep each: D^{-1}, a weak smoother
+    b = synth.rhs(n, 1, seed=3)[:, 0]
+    x0 = np.zeros(n)
+    x1 = x0 + M0 @ (b - A0 @ x0)
+    x2 = x1 + P @ np.linalg.solve(P.T @ A0 @ P, P.T @ (b - A0 @ x1))
+    x3 = x2 + M0 @ (b - A0 @ x2)
+    got = H.vcycle_ilu(fac, x0, b, [1, n1], [1, n1], nu=1)
+    assert relerr(got, x3) < 1e-13
+    # with too few sweeps on level 1 the correction is no longer exact
+    assert relerr(H.vcycle_ilu(fac, x0, b, [1, 2], [1, 2], nu=1), x3) > 1e-6
