@@ -472,7 +472,15 @@ silu_status silu_ilu_layout(silu_ilu F, double* pad_natural, double* pad_sorted,
  *   SILU_AMG_POLY_GS:   x <- x + sum_{j<gs_terms} (-D^{-1} L)^j D^{-1} (b - A x)
  *                       (polynomial Gauss-Seidel, Sec. 3.1; the mixed V-cycle
  *                       of Sec. 6.3), D = diag(A), L its strict lower part.
- * params NULL = {0.25, 25, 400, 1, SILU_AMG_L1_JACOBI, 2}.  Blocks.
+ * ilu_levels > 1 smooths levels 1 .. ilu_levels - 1 (those above the
+ * coarsest) with the ILU smoother instead (Sec. 6: ILU smoothing from the
+ * finest level down, up to all levels): each gets its own incomplete
+ * factorisation of A_l of F's kind, drop tolerance and fill (ILU(0), ILU(k)
+ * or ILUT; a Gauss-Seidel kind -> SILU_ERR_INVALID_ARG), row-scaled, in F's
+ * precision, and is smoothed once before and once after its correction with
+ * the cycle's sweep counts (or its exact triangular solves when the cycle
+ * uses them on the finest level).  0 or 1: the finest level only.
+ * params NULL = {0.25, 25, 400, 1, SILU_AMG_L1_JACOBI, 2, 1}.  Blocks.
  */
 typedef enum { SILU_AMG_L1_JACOBI = 0, SILU_AMG_POLY_GS = 1 } silu_amg_smoother;
 typedef struct {
@@ -482,6 +490,7 @@ typedef struct {
   int jacobi_sweeps;    /* smoothing steps before and after the correction below the finest level, >= 0 */
   int coarse_smoother;  /* silu_amg_smoother */
   int gs_terms;         /* Neumann terms of each polynomial Gauss-Seidel step, >= 1 */
+  int ilu_levels;       /* levels from the finest smoothed by the ILU smoother, >= 0 (0 and 1: the finest only) */
 } silu_amg_params;
 silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params);
 /*
@@ -489,8 +498,9 @@ silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params);
  * ordered): the finest level is smoothed before and after the coarse-grid
  * correction by ilu_smooth's update with sweeps_L / sweeps_U sweeps of F's
  * smoother, or, with sweeps_L and sweeps_U both negative, by
- * direct_trisolve's update (exact triangular solves).  A one-level hierarchy
- * is the direct solve x = A^{-1} b.
+ * direct_trisolve's update (exact triangular solves); the levels that
+ * silu_amg_params.ilu_levels gives the ILU smoother the same way on their own
+ * factors.  A one-level hierarchy is the direct solve x = A^{-1} b.
  */
 silu_status silu_amg_vcycle(silu_ilu F, double* x, const double* b, int sweeps_L, int sweeps_U);
 /*
@@ -498,7 +508,7 @@ silu_status silu_amg_vcycle(silu_ilu F, double* x, const double* b, int sweeps_L
  * coarse-grid correction, by one application of the ILUT Schur complement
  * smoother (silu_schur_setup; Sec. 3.1 uses it as the smoother of one level of
  * the V-cycle), its interior blocks swept sweeps_L + sweeps_U
- * times; coarser levels as in silu_amg_vcycle.  x (n FP64, device) is updated
+ * times; coarser levels as in silu_amg_vcycle (ILU levels with sweeps).  x (n FP64, device) is updated
  * in place from its current value; b is read.  Requires silu_amg_setup and
  * silu_schur_setup on F (else SILU_ERR_INVALID_ARG), negative sweep counts
  * -> SILU_ERR_INVALID_ARG.  Stream-ordered on F's context.

@@ -264,7 +264,8 @@ AMG_L1_JACOBI, AMG_POLY_GS = 0, 1
 class AmgParams(ctypes.Structure):
     """silu_amg_params."""
     _fields_ = [("theta", ctypes.c_double), ("max_levels", ctypes.c_int), ("coarse_size", ctypes.c_int),
-                ("jacobi_sweeps", ctypes.c_int), ("coarse_smoother", ctypes.c_int), ("gs_terms", ctypes.c_int)]
+                ("jacobi_sweeps", ctypes.c_int), ("coarse_smoother", ctypes.c_int), ("gs_terms", ctypes.c_int),
+                ("ilu_levels", ctypes.c_int)]
 
 
 class Matrix:
@@ -415,11 +416,12 @@ class ILU:
         return out[:pmax]
 
     def amg_setup(self, theta: float = 0.25, max_levels: int = 25, coarse_size: int = 400, jacobi_sweeps: int = 1,
-                  coarse_smoother: int = AMG_L1_JACOBI, gs_terms: int = 2):
+                  coarse_smoother: int = AMG_L1_JACOBI, gs_terms: int = 2, ilu_levels: int = 1):
         """Build and attach the AMG hierarchy of A (Sec. 3); this factor object smooths its finest level,
-        l1-Jacobi or polynomial Gauss-Seidel (gs_terms Neumann terms) the coarser ones."""
+        l1-Jacobi or polynomial Gauss-Seidel (gs_terms Neumann terms) the coarser ones; with ilu_levels > 1
+        the next ilu_levels - 1 levels get ILU smoothers of their own (same kind, tau and fill)."""
         p = AmgParams(float(theta), int(max_levels), int(coarse_size), int(jacobi_sweeps), int(coarse_smoother),
-                      int(gs_terms))
+                      int(gs_terms), int(ilu_levels))
         _check(self.ctx.handle, load().silu_amg_setup(self.handle, ctypes.byref(p)), "silu_amg_setup")
 
     def amg_vcycle(self, x, b, sweeps_L: int, sweeps_U: int):

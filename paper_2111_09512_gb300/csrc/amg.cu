@@ -3,8 +3,9 @@
 // hierarchy is built on the host (amg_setup.cpp); every level's operator,
 // restriction R = P^T and (negated) prolongation P are swept by the same
 // sweep kernels as the smoother, the finest level is smoothed by the
-// factor object's ILU smoother, coarser levels by l1-Jacobi, and the
-// coarsest level is solved by a dense inverse.
+// factor object's ILU smoother (optionally the next levels by ILU smoothers
+// of their own, Sec. 6), coarser levels by l1-Jacobi or polynomial
+// Gauss-Seidel, and the coarsest level is solved by a dense inverse.
 #include <cstring>
 
 #include "internal.h"
@@ -100,16 +101,26 @@ double* poly_gs(silu_ilu F, AmgDevLevel& L, double* x, const double* b, int nu, 
   return x;
 }
 
-// The configured smoother of a level below the finest.
-double* coarse_smooth(silu_ilu F, AmgDevLevel& L, double* x, const double* b, bool x_zero) {
+// The configured smoother of a level below the finest: the level's own ILU
+// smoother where it has one (m_L + m_U sweeps, or its exact triangular
+// solves when mL < 0; x is updated in place), else the coarse smoother.
+double* coarse_smooth(silu_ilu F, AmgDevLevel& L, double* x, const double* b, bool x_zero, int mL, int mU,
+                      bool capturing) {
   const AmgState& G = *F->amg;
+  if (L.FL) {
+    if (mL < 0)
+      silu::direct_chunk(L.FL, x, b, 1, 1, 0, x_zero, capturing);
+    else
+      silu::smooth_chunk(L.FL, x, b, 1, 1, 0, mL, mU, x_zero);
+    return x;
+  }
   if (G.coarse_kind == SILU_AMG_POLY_GS) return poly_gs(F, L, x, b, G.nu, G.gs_terms, x_zero);
   return l1_jacobi(F, L, x, b, G.nu, x_zero);
 }
 
 // Multilevel(A_l, b, x, l) of Alg. mgcycle for l >= 1, from x = 0; returns
 // the buffer that holds x_l.
-double* level_cycle(silu_ilu F, int l) {
+double* level_cycle(silu_ilu F, int l, int mL, int mU, bool capturing) {
   AmgState& G = *F->amg;
   AmgDevLevel& L = *G.lev[l];
   const int last = (int)G.lev.size() - 1;
@@ -119,13 +130,13 @@ double* level_cycle(silu_ilu F, int l) {
                                                     F->ctx->stream));
     return L.x.as<double>();
   }
-  double* x = coarse_smooth(F, L, L.x.as<double>(), b, true);
+  double* x = coarse_smooth(F, L, L.x.as<double>(), b, true, mL, mU, capturing);
   AmgDevLevel& C = *G.lev[l + 1];
   op(F, L.A, SILU_K_RESIDUAL, b, x, L.r.as<double>(), nullptr, nullptr, silu::EPI_STORE);       // r = b - A x
   op(F, L.R, SILU_K_RESIDUAL, nullptr, L.r.as<double>(), C.b.as<double>(), nullptr, nullptr, silu::EPI_SPMV);
-  const double* v = level_cycle(F, l + 1);
+  const double* v = level_cycle(F, l + 1, mL, mU, capturing);
   op(F, L.Pneg, SILU_K_RESIDUAL, nullptr, v, nullptr, nullptr, x, silu::EPI_ADDX);             // x += P v
-  return coarse_smooth(F, L, x, b, false);
+  return coarse_smooth(F, L, x, b, false, mL, mU, capturing);
 }
 
 cudaError_t upload_level(const silu::AmgLevel& H, AmgDevLevel& D, bool own_a, bool coarsest, bool gs,
@@ -153,7 +164,28 @@ cudaError_t upload_level(const silu::AmgLevel& H, AmgDevLevel& D, bool own_a, bo
 
 }  // namespace
 
+AmgDevLevel::~AmgDevLevel() {
+  if (FL) silu_ilu_destroy(FL);
+  if (Amat) silu_mat_destroy(Amat);
+}
+
 namespace silu {
+
+cudaError_t amg_prepare_direct(silu_ilu F) {
+  cudaError_t e = ensure_direct(F);
+  if (e != cudaSuccess || !F->amg) return e;
+  for (auto& L : F->amg->lev) {
+    if (!L->FL) continue;
+    e = ensure_direct(L->FL);
+    if (e != cudaSuccess) return e;
+    try {
+      level_graph(L->FL, 1, 1, 0);  // settles the level launch form before a capture records the cycle
+    } catch (const CudaFail& f) {
+      return f.e;
+    }
+  }
+  return cudaSuccess;
+}
 
 void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_zero, bool capturing, bool schur) {
   AmgState& G = *F->amg;
@@ -189,7 +221,7 @@ void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_ze
   smooth(x_zero);                                                                   // pre-smoothing
   op(F, A, SILU_K_RESIDUAL, b, x, L0.r.as<double>(), nullptr, nullptr, EPI_STORE);  // r = b - A x
   op(F, L0.R, SILU_K_RESIDUAL, nullptr, L0.r.as<double>(), C.b.as<double>(), nullptr, nullptr, EPI_SPMV);
-  const double* v = level_cycle(F, 1);
+  const double* v = level_cycle(F, 1, mL, mU, capturing);
   op(F, L0.Pneg, SILU_K_RESIDUAL, nullptr, v, nullptr, nullptr, x, EPI_ADDX);        // x += P v
   smooth(false);                                                                    // post-smoothing
 }
@@ -202,11 +234,14 @@ silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params) {
   NvtxRange nvtx_("silu:silu_amg_setup");
   if (!F) return SILU_ERR_INVALID_ARG;
   silu_ctx ctx = F->ctx;
-  silu_amg_params p = {0.25, 25, 400, 1, SILU_AMG_L1_JACOBI, 2};
+  silu_amg_params p = {0.25, 25, 400, 1, SILU_AMG_L1_JACOBI, 2, 1};
   if (params) p = *params;
   if (p.jacobi_sweeps < 0) return silu::set_err(ctx, SILU_ERR_INVALID_ARG, "jacobi_sweeps must be >= 0");
   if ((p.coarse_smoother != SILU_AMG_L1_JACOBI && p.coarse_smoother != SILU_AMG_POLY_GS) || p.gs_terms < 1)
     return silu::set_err(ctx, SILU_ERR_INVALID_ARG, "bad coarse smoother or gs_terms");
+  if (p.ilu_levels < 0) return silu::set_err(ctx, SILU_ERR_INVALID_ARG, "ilu_levels must be >= 0");
+  if (p.ilu_levels > 1 && F->kind != SILU_ILU0 && F->kind != SILU_ILUK && F->kind != SILU_ILUT)
+    return silu::set_err(ctx, SILU_ERR_INVALID_ARG, "ILU smoothing below the finest level needs an ILU kind");
   std::unique_ptr<AmgState> G;
   try {
     G.reset(new AmgState);
@@ -234,6 +269,18 @@ silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params) {
         e = silu::upload(G->cinv, G->host.coarse_inv.data(), G->host.coarse_inv.size(), s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return silu::cuda_err(ctx, e, "upload of the AMG hierarchy");
+      // levels 1 .. ilu_levels - 1 above the coarsest: an incomplete
+      // factorisation of A_l of F's kind, row-scaled, as a factor object
+      G->ilu_levels = std::max(1, std::min(p.ilu_levels, (int)nl - 1));
+      for (int l = 1; l < G->ilu_levels; ++l) {
+        const silu::Csr& Al = G->host.lev[l].A;
+        AmgDevLevel& D = *G->lev[l];
+        silu_status sl = silu_mat_create(ctx, Al.n, Al.nnz(), Al.rp.data(), Al.ci.data(), Al.va.data(), &D.Amat);
+        if (sl == SILU_OK) sl = ilu_setup(ctx, D.Amat, F->kind, F->tau, F->fill, SILU_SCALE_ROW, F->prec, &D.FL);
+        if (sl != SILU_OK) return sl;  // the context's message names the failure
+        e = silu::ensure_vectors(D.FL, 1);
+        if (e != cudaSuccess) return silu::cuda_err(ctx, e, "workspace of an AMG level's ILU smoother");
+      }
     }
   } catch (const std::bad_alloc&) {
     return silu::set_err(ctx, SILU_ERR_OOM, "out of host memory");
@@ -254,7 +301,7 @@ silu_status silu_amg_vcycle(silu_ilu F, double* x, const double* b, int sweeps_L
   if (F->F.L.n == 0) return SILU_OK;
   try {
     CK(silu::ensure_vectors(F, 1));
-    if (sweeps_L < 0) CK(silu::ensure_direct(F));
+    if (sweeps_L < 0) CK(silu::amg_prepare_direct(F));
     silu::amg_cycle(F, x, b, sweeps_L, sweeps_U, false, false, false);
   } catch (const CudaFail& f) {
     return silu::cuda_err(ctx, f.e, f.what);

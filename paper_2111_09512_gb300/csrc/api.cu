@@ -1648,6 +1648,7 @@ silu_status fgmres_solve(silu_ilu F, double* x, const double* b, double tol, int
     if (precond == SILU_PRECOND_DIRECT || precond == SILU_PRECOND_AMG_DIRECT) {
       CK(ensure_direct(F));
       level_graph(F, 1, 1, 0);  // settles the level launch form before iterations are captured
+      if (precond == SILU_PRECOND_AMG_DIRECT) CK(amg_prepare_direct(F));  // and the ILU levels'
     }
     Workspace& W = F->ws;
     double* V = W.V.as<double>();

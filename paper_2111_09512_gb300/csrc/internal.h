@@ -135,10 +135,20 @@ struct AmgDevLevel {
   DBuf l1inv, x, t, b, r;
   DBuf G_rp, G_ci, G_va, G_tiles, gdinv, y2;  // polynomial Gauss-Seidel: L D^{-1}, 1 / a_ii, a second sweep buffer
   DevCsr Lgs;
+  // the ILU smoother of this level (silu_amg_params.ilu_levels): A_l and its
+  // row-scaled factors as a factor object of their own (owned; null elsewhere)
+  silu_mat Amat = nullptr;
+  silu_ilu FL = nullptr;
+  AmgDevLevel() = default;
+  AmgDevLevel(const AmgDevLevel&) = delete;
+  AmgDevLevel& operator=(const AmgDevLevel&) = delete;
+  ~AmgDevLevel();
 };
 
 // An AMG hierarchy attached to a factor object: the factors smooth the
-// finest level, l1-Jacobi the coarser ones, the coarsest is solved directly.
+// finest level (and, with ilu_levels > 1, factors of their own the next
+// levels), l1-Jacobi or polynomial Gauss-Seidel the coarser ones, the
+// coarsest is solved directly.
 struct AmgState {
   silu::AmgHost host;
   std::vector<std::unique_ptr<AmgDevLevel>> lev;
@@ -146,6 +156,7 @@ struct AmgState {
   int nu = 1;  // smoothing steps before and after the correction on levels >= 1
   int coarse_kind = SILU_AMG_L1_JACOBI;
   int gs_terms = 2;
+  int ilu_levels = 1;
   double theta = 0.25;
   int max_levels = 25;
   int64_t coarse_size = 400;
@@ -353,6 +364,9 @@ silu_status device_ok(silu_ctx ctx);
 cudaError_t ensure_vectors(silu_ilu F, int nrhs);
 cudaError_t ensure_krylov(silu_ilu F, int m);
 cudaError_t ensure_direct(silu_ilu F);
+// The captured level-by-level exact solve of one column block (built and
+// cached on first use; settles whether levels overlap).
+cudaGraphExec_t level_graph(silu_ilu F, int R, int ldx, size_t col);
 // Level-ordered factor copies and items of the persistent exact solves.
 cudaError_t build_tri_plan(silu_ilu F);
 // Tagged vectors and launch state of the persistent solve for R columns.
@@ -377,10 +391,15 @@ void direct_chunk(silu_ilu F, double* x, const double* b, int R, int ldx, size_t
 // Schur complement smoother (m_L + m_U sweeps in its blocks) before and after
 // the coarse-grid correction (x_zero: x is an output, the cycle starts from
 // zero; capturing: a stream capture is recording).  Requires F->amg (and
-// F->schur with schur) and F's one-column workspace (and ensure_direct for
-// mL < 0).
+// F->schur with schur) and F's one-column workspace (and amg_prepare_direct
+// for mL < 0).  Levels with an ILU smoother of their own are smoothed the way
+// the finest level is (sweeps, or exact solves when mL < 0; sweeps under
+// schur).
 void amg_cycle(silu_ilu F, double* x, const double* b, int mL, int mU, bool x_zero, bool capturing,
                bool schur = false);
+// Before a cycle with exact triangular solves (mL < 0) runs or is captured:
+// F's and every ILU level's direct-solve data and launch form (ensure_direct).
+cudaError_t amg_prepare_direct(silu_ilu F);
 // z = M^{-1} r of F's Schur complement smoother (one right-hand side,
 // device vectors of n entries; z is written).  Requires F->schur.
 void schur_apply(silu_ilu F, const double* r, double* z, int mL, int mU);

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 import synth
-from _helpers import relerr
+from _helpers import maxabs_err, relerr
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -234,3 +234,87 @@ def test_schur_cycle_refused_without_setup(silu, ctx):
         F.amg_vcycle_schur(x, b, 2, 2)  # no Schur complement smoother
     with pytest.raises(silu.SiluError):
         silu.fgmres_solve(F, x, b, tol=1e-8, precond=silu.PRECOND_AMG_SCHUR)
+
+
+ILU_LEVEL_CASES = [
+    # name, generator, kind, tau, fill, ilu_levels, coarse smoother, (mL, mU)
+    ("cutcell 23x21x19 ilu0 two levels", lambda: synth.cutcell7(23, 21, 19, seed=3), "ilu0", 0.0, 0, 2, "jacobi",
+     (3, 2)),
+    ("cutcell 23x21x19 ilu0 all levels", lambda: synth.cutcell7(23, 21, 19, seed=3), "ilu0", 0.0, 0, 25, "gs",
+     (2, 3)),
+    ("hex27 13x12x11 ilut all levels", lambda: synth.hex27(13, 12, 11, seed=4), "ilut", 1e-3, 10, 3, "jacobi",
+     (2, 2)),
+    ("poisson 16^3 iluk1 all levels", lambda: synth.poisson7(16), "iluk", 0.0, 1, 25, "jacobi", (1, 1)),
+]
+
+
+@pytest.mark.parametrize("case", ILU_LEVEL_CASES, ids=[c[0] for c in ILU_LEVEL_CASES])
+def test_vcycle_with_ilu_on_several_levels_matches_oracle(silu, ctx, case):
+    """ILU smoothing from the finest level down (Sec. 6): levels below the
+    finest get incomplete factorisations of A_l of their own (the same kind,
+    tau and fill; bit-identical host factors on both sides) and are swept
+    like the finest; three successive cycles against the oracle's
+    vcycle_ilu at 1e-12, then FGMRES(30) preconditioned by the cycle."""
+    name, gen, kind, tau, fill, nilu, coarse, (mL, mU) = case
+    A = gen()
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), kind, tau, fill)
+    F.amg_setup(theta=0.25, max_levels=12, coarse_size=40, jacobi_sweeps=1,
+                coarse_smoother=silu.AMG_POLY_GS if coarse == "gs" else silu.AMG_L1_JACOBI, gs_terms=2,
+                ilu_levels=nilu)
+    H = oracle.AMG(A, theta=0.25, max_levels=12, coarse_size=40)
+    assert F.amg_stats()["levels"] == len(H.levels) >= 3
+    fac = H.level_factors(kind, tau, fill, count=nilu)
+    assert len(fac) == min(nilu, len(H.levels) - 1) >= 2
+    b = synth.rhs(n, 1, seed=11)[:, 0]
+    x = synth.rhs(n, 1, seed=12)[:, 0]
+    xd, bd = dev(x.copy()), dev(b)
+    for cycle in range(3):
+        x = H.vcycle_ilu(fac, x, b, mL, mU, nu=1, coarse=coarse, terms=2)
+        F.amg_vcycle(xd, bd, mL, mU)
+        ctx.check()
+        got = host(xd)
+        assert relerr(got, x) < 1e-12, (cycle, relerr(got, x))
+        assert maxabs_err(got, x) < 1e-12, cycle
+    xs = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st, its, rel = silu.fgmres_solve(F, xs, bd, tol=1e-10, restart=30, maxit=500, sweeps_L=max(mL, 2),
+                                     sweeps_U=max(mU, 2), precond=silu.PRECOND_AMG)
+    assert st == silu.OK and rel <= 1e-10, (st, its, rel)
+    r = oracle.residual(A, host(xs).reshape(n, 1), b.reshape(n, 1))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10
+
+
+def test_vcycle_with_exact_solves_on_several_levels(silu, ctx):
+    """With negative sweep counts every ILU level is smoothed by its exact
+    triangular solves; the oracle reaches the same operator with as many
+    sweeps as each factor has levels (nilpotence, Sec. 5.2), per level."""
+    A = synth.cutcell7(17, 15, 13, seed=6)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+    F.amg_setup(theta=0.25, coarse_size=40, jacobi_sweeps=1, ilu_levels=3)
+    H = oracle.AMG(A, theta=0.25, coarse_size=40)
+    fac = H.level_factors("ilu0", count=3)
+    assert len(fac) == 3
+    mL = [oracle.levels_lower(S.L)[0] for S in fac]
+    mU = [oracle.levels_upper(S.Us)[0] for S in fac]
+    b = synth.rhs(n, 1, seed=8)[:, 0]
+    want = H.vcycle_ilu(fac, np.zeros(n), b, mL, mU)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    F.amg_vcycle(x, dev(b), -1, -1)
+    assert relerr(host(x), want) < 1e-12
+    xs = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st, its, rel = silu.fgmres_solve(F, xs, dev(b), tol=1e-10, restart=30, maxit=500, sweeps_L=0, sweeps_U=0,
+                                     precond=silu.PRECOND_AMG_DIRECT)
+    assert st == silu.OK and rel <= 1e-10, (st, its, rel)
+    r = oracle.residual(A, host(xs).reshape(n, 1), b.reshape(n, 1))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10
+
+
+def test_ilu_levels_refused_for_gauss_seidel_factors(silu, ctx):
+    A = synth.poisson7(10)
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "gs")
+    with pytest.raises(silu.SiluError):
+        F.amg_setup(coarse_size=40, ilu_levels=2)
+    with pytest.raises(silu.SiluError):
+        F.amg_setup(coarse_size=40, ilu_levels=-1)
+    F.amg_setup(coarse_size=40, ilu_levels=1)  # the finest level alone takes any kind
