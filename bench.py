@@ -427,6 +427,8 @@ def run_silu(args):
         serve = serving(silu, args)
 
     amg = amg_comparison(silu, ctx, torch, args.amg_edge) if (args.amg_edge > 0 and rank == 0) else None
+    place = (smoother_placement(silu, ctx, torch, args.placement_edge)
+             if (args.placement_edge > 0 and rank == 0) else None)
 
     p32 = poisson32(silu, ctx, torch) if rank == 0 else None
     mrhs = multi_rhs(silu, ctx, torch, F, n, nnzA, nnzL, nnzU) if rank == 0 else None
@@ -484,6 +486,8 @@ def run_silu(args):
             line["serving"] = serve
         if amg:
             line["amg"] = amg
+        if place:
+            line["smoother_placement"] = place
         if p32:
             line["poisson32"] = p32
         if mrhs:
@@ -865,6 +869,77 @@ def amg_comparison(silu, ctx, torch, edge: int):
                if k.startswith(("amg_sweeps", "amg_fp32")) and isinstance(v, dict) and v["converged"])
     out["fastest_amg_sweeps"] = best[1]
     out["speedup_amg_sweeps_vs_amg_direct"] = round(out["amg_direct"]["seconds"] / best[0], 2)
+    return out
+
+
+def smoother_placement(silu, ctx, torch, edge: int, sweeps=(5, 10)):
+    """Where the ILU smoother sits in the V-cycle (Sec. 6, Fig. multi-level-ilu:
+    ILU on the finest level only, ILU on all levels, polynomial Gauss-Seidel):
+    the cut-cell 7-point matrix on edge^3 (seed 1), FP64, one right-hand side
+    (seed 1), Ruge-Stueben hierarchy (theta 0.25, coarsest <= 400 rows),
+    FGMRES(30) to 1e-8 from zero with one V-cycle as the preconditioner.
+      ilu_finest_jacobi_m: ILU(0) on the finest level (m + m sweeps), one
+                           l1-Jacobi step before and after below;
+      ilu_finest_gs_m:     the same with one polynomial Gauss-Seidel step (two
+                           terms) below (the paper's mixed V-cycle);
+      ilu_all_levels_m:    ILU(0) factors of every A_l above the coarsest,
+                           each swept m + m times;
+      gs_all_levels:       polynomial Gauss-Seidel (two terms) on every level,
+                           the finest one included.
+    Each with its V-cycle's time (CUDA events over 10 cycles) and the host
+    setup of the hierarchy (and of the coarse factors)."""
+    import synth
+    A = synth.cutcell7(edge, seed=1)
+    n = len(A[0]) - 1
+    M = silu.Matrix(ctx, *A)
+    del A
+    b = torch.from_numpy(synth.rhs(n, 1, seed=1)[:, 0].copy()).cuda()
+    out = {"workload": f"cutcell7-{edge}^3 FP64, FGMRES(30) to 1e-8 from x = 0, one V-cycle per iteration",
+           "rows": n}
+
+    def run(F, mL, mU):
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            F.amg_vcycle(x, b, mL, mU)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            F.amg_vcycle(x, b, mL, mU)
+        e1.record()
+        torch.cuda.synchronize()
+        rec = {"vcycle_ms": round(e0.elapsed_time(e1) / 10, 3)}
+        for rep in range(2):  # the first solve also captures the iteration graphs
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, its, rr = silu.fgmres_solve(F, x, b, tol=1e-8, restart=30, maxit=600, sweeps_L=mL, sweeps_U=mU,
+                                            precond=silu.PRECOND_AMG)
+            torch.cuda.synchronize()
+            rec.update({"seconds": round(time.perf_counter() - t0, 4), "iterations": its,
+                        "relres": float(f"{rr:.3e}"), "converged": st == silu.OK})
+            if st != silu.OK:
+                break
+        return rec
+
+    F = silu.ilu_setup(ctx, M, "ilu0")
+    for label, coarse, nilu in (("ilu_finest_jacobi", silu.AMG_L1_JACOBI, 1), ("ilu_finest_gs", silu.AMG_POLY_GS, 1),
+                                ("ilu_all_levels", silu.AMG_L1_JACOBI, 25)):
+        t0 = time.perf_counter()
+        F.amg_setup(theta=0.25, max_levels=25, coarse_size=400, jacobi_sweeps=1, coarse_smoother=coarse, gs_terms=2,
+                    ilu_levels=nilu)
+        setup_s = round(time.perf_counter() - t0, 2)
+        out.setdefault("levels", F.amg_stats()["levels"])
+        for m in sweeps:
+            out[f"{label}_{m}"] = dict(run(F, m, m), amg_setup_s=setup_s)
+    del F
+    G = silu.ilu_setup(ctx, M, "gs")
+    t0 = time.perf_counter()
+    G.amg_setup(theta=0.25, max_levels=25, coarse_size=400, jacobi_sweeps=1, coarse_smoother=silu.AMG_POLY_GS,
+                gs_terms=2)
+    setup_s = round(time.perf_counter() - t0, 2)
+    out["gs_all_levels"] = dict(run(G, 2, 1), amg_setup_s=setup_s)  # L_s = L D^{-1}: two terms, U = D
+    del G
     return out
 
 
@@ -1341,6 +1416,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--amg-edge", type=int, default=224,
                     help="grid edge of the GMRES+AMG comparison (0 = skip)")
+    ap.add_argument("--placement-edge", type=int, default=128,
+                    help="grid edge of the V-cycle smoother placement study (0 = skip)")
     ap.add_argument("--study", action="store_true",
                     help="add the sweep studies: factorisation kinds, ||T_s^p||_2, time to solution vs sweeps")
     ap.add_argument("--no-scaling-study", action="store_true",
