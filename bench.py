@@ -437,7 +437,7 @@ def run_silu(args):
     if rank == 0 and args.study:
         study = sweep_study(silu, ctx, torch)
     elif rank == 0 and not args.no_scaling_study:
-        study = {"scaling": scaling_study(silu, ctx, torch)}
+        study = {"scaling": scaling_study(silu, ctx, torch), "nrbe_amg": nrbe_amg_study(silu, ctx, torch)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1042,6 +1042,55 @@ def poisson32(silu, ctx, torch):
     return out
 
 
+def nrbe_amg_study(silu, ctx, torch, edge: int = 24):
+    """Table NRBE2 in kind (Sec. 6.1): GMRES+AMG with the ILUT(1e-3, 5)
+    smoother on the finest level and m + m Richardson sweeps (m = 1..5), the
+    upper factor row-scaled or row/column (Ruiz) scaled, on the cut-cell
+    7-point matrix of edge^3 rows (24^3 = 13,824, the size of the paper's
+    smallest PeleLM system), theta 0.25, one l1-Jacobi step below, FGMRES(30)
+    to 1e-9 from zero (at most 300 iterations), right-hand side U[-1,1)
+    (seed 1).  Reports the iterations and the norm-wise relative backward
+    error ||b - A x|| / (||b|| + ||A||_2 ||x||) (Eq. nbre) and the true relative
+    residual of the result (iterations null: not converged), the
+    residual and ||A||_2 computed by the library on the device (A is
+    symmetric positive definite, so ||A||_2 is its largest eigenvalue: 200
+    power-iteration steps)."""
+    import synth
+    A = synth.cutcell7(edge, seed=1)
+    n = len(A[0]) - 1
+    M = silu.Matrix(ctx, *A)
+    b = torch.from_numpy(synth.rhs(n, 1, seed=1)[:, 0].copy()).cuda()
+    zero = torch.zeros(n, dtype=torch.float64, device="cuda")
+    v = torch.from_numpy(synth.rhs(n, 1, seed=2)[:, 0].copy()).cuda()
+    w = torch.empty_like(v)
+    lam = 0.0
+    for _ in range(200):  # w = -A v
+        M.residual(w, v / torch.linalg.norm(v), zero)
+        lam = float(torch.linalg.norm(w))
+        v = w.clone()
+    normA = lam
+    nb = float(torch.linalg.norm(b))
+    sweeps = [1, 2, 3, 4, 5]
+    out = {"workload": f"cutcell7-{edge}^3 ({n} rows), ILUT(1e-3, 5) + AMG, FGMRES(30) to 1e-9",
+           "norm2_A": float(f"{normA:.6e}"), "sweeps": sweeps}
+    for label, sc in (("row", silu.SCALE_ROW), ("rowcol", silu.SCALE_ROWCOL)):
+        F = silu.ilu_setup(ctx, M, "ilut", 1e-3, 5, scale=sc)
+        F.amg_setup(theta=0.25, max_levels=25, coarse_size=400, jacobi_sweeps=1)
+        its_l, nrbe_l, rel_l = [], [], []
+        for m in sweeps:
+            x = torch.zeros(n, dtype=torch.float64, device="cuda")
+            st, its, rr = silu.fgmres_solve(F, x, b, tol=1e-9, restart=30, maxit=300, sweeps_L=m, sweeps_U=m,
+                                            precond=silu.PRECOND_AMG)
+            r = torch.empty_like(b)
+            M.residual(r, x, b)
+            its_l.append(its if st == silu.OK else None)
+            rel_l.append(float(f"{float(torch.linalg.norm(r)) / nb:.3e}"))
+            nrbe_l.append(float(f"{float(torch.linalg.norm(r)) / (nb + normA * float(torch.linalg.norm(x))):.3e}"))
+        out[label] = {"iterations": its_l, "relres": rel_l, "nrbe": nrbe_l}
+        del F
+    return out
+
+
 def scaling_study(silu, ctx, torch):
     """Scaled against unscaled factors (the paper's Sec. 6.1, Table NRBE2's
     question) on the cut-cell 128^3 matrix, ILUT(1e-3, 10), FP64, one
@@ -1123,6 +1172,7 @@ def sweep_study(silu, ctx, torch):
     out = {}
 
     out["scaling"] = scaling_study(silu, ctx, torch)
+    out["nrbe_amg"] = nrbe_amg_study(silu, ctx, torch)
     A = synth.cutcell7(EDGE, seed=1)
     n = len(A[0]) - 1
     bh = synth.rhs(n, 1, seed=1)
