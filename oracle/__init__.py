@@ -102,7 +102,7 @@ def _load():
         "orc_schur_interface": (i64, [i64, vp, vp, i32, vp]),
         "orc_schur_apply": (i32, [i64, vp, vp, vp, i32, dbl, i32, i32, i32, vp, vp]),
         "orc_amg_vcycle_schur": (i32, [vp, i32, dbl, i32, i32, i32, i32, i32, i32, vp, vp]),
-        "orc_amg_vcycle_ilu": (i32, [vp, i32] + [vp] * 9 + [i32, i32, i32, vp, vp]),
+        "orc_amg_vcycle_ilu": (i32, [vp, i32] + [vp] * 9 + [i32, i32, i32, i32, dbl, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -580,11 +580,13 @@ class AMG:
         k = top if count is None else max(1, min(int(count), top))
         return [row_scale(factor(self.levels[l].A, kind, tau, fill)) for l in range(k)]
 
-    def vcycle_ilu(self, factors, x, b, mL, mU, nu: int = 1, coarse: str = "jacobi", terms: int = 2):
+    def vcycle_ilu(self, factors, x, b, mL, mU, nu: int = 1, coarse: str = "jacobi", terms: int = 2,
+                   schur=None):
         """One V-cycle as vcycle with the ILU smoother on the first len(factors) levels: level l
         is smoothed by m_L + m_U sweeps on factors[l] (the row-scaled factors of A_l; mL, mU an
-        int or one count per level), the levels below by the coarse smoother.  Returns a new
-        array."""
+        int or one count per level), the levels below by the coarse smoother.  schur = (parts,
+        tau, fill) smooths the finest level by the ILUT Schur complement smoother instead
+        (factors[0] is then not read).  Returns a new array."""
         k = len(factors)
         n = self.levels[0].n
         x = np.ascontiguousarray(x, np.float64).reshape(n).copy()
@@ -603,7 +605,9 @@ class AMG:
         st = _load().orc_amg_vcycle_ilu(self._h, k, ptrs([t[0] for t in Ls]), ptrs([t[1] for t in Ls]),
                                         ptrs([t[2] for t in Ls]), ptrs([t[0] for t in Us]), ptrs([t[1] for t in Us]),
                                         ptrs([t[2] for t in Us]), ptrs([S.dinv for S in factors]), _p(mLs), _p(mUs),
-                                        int(nu), 1 if coarse == "gs" else 0, int(terms), _p(x), _p(b))
+                                        int(nu), 1 if coarse == "gs" else 0, int(terms),
+                                        int(schur[0]) if schur else 0, float(schur[1]) if schur else 0.0,
+                                        int(schur[2]) if schur else 0, _p(x), _p(b))
         if st:
             raise OracleError(st, "amg_vcycle_ilu")
         return x

@@ -1825,13 +1825,17 @@ int orc_amg_vcycle(const orc_amg* h, const int64_t* lp, const int32_t* lc, const
  * sweeps on its own row-scaled factors (lp[l] .. dinv[l]: L_s, Utilde_s and
  * D^{-1} of an incomplete factorisation of A_l); the levels below by the
  * coarse smoother as in orc_amg_vcycle.  Entries at l >= nlev - 1 are not
- * used.  nilu >= 1 (level 0's factors are entry 0).
+ * used.  nilu >= 1 (level 0's factors are entry 0).  With schur_parts > 0
+ * the finest level is smoothed by the ILUT Schur complement smoother instead
+ * (as in orc_amg_vcycle_schur, with m_L[0] + m_U[0] sweeps in its blocks;
+ * entry 0's factors are then not read).
  */
 int orc_amg_vcycle_ilu(const orc_amg* h, int nilu, const int64_t* const* lp, const int32_t* const* lc,
                        const double* const* lv, const int64_t* const* sp, const int32_t* const* sc,
                        const double* const* sv, const double* const* dinv, const int* mL, const int* mU, int nu,
-                       int coarse, int terms, double* x, const double* b) {
-  if (nilu < 1) return ORC_BADARG;
+                       int coarse, int terms, int schur_parts, double schur_tau, int schur_fill, double* x,
+                       const double* b) {
+  if (nilu < 1 || schur_parts < 0) return ORC_BADARG;
   level_ilu* f = (level_ilu*)malloc(sizeof(level_ilu) * (size_t)nilu);
   if (!f) return ORC_NOMEM;
   for (int l = 0; l < nilu; ++l) {
@@ -1839,7 +1843,7 @@ int orc_amg_vcycle_ilu(const orc_amg* h, int nilu, const int64_t* const* lp, con
     f[l] = e;
   }
   amg_smoother sm = {lp[0], sp[0], lc[0], sc[0], lv[0], sv[0], dinv[0], mL[0], mU[0], nu, coarse, terms,
-                     0, 0.0, 0, nilu, f};
+                     schur_parts, schur_tau, schur_fill, nilu, f};
   const int st = multilevel(h, 0, &sm, b, x);
   free(f);
   return st;

@@ -418,3 +418,45 @@ def test_exact_ilu_on_level_one_gives_the_two_grid_cycle():
     assert relerr(got, x3) < 1e-13
     # with too few sweeps on level 1 the correction is no longer exact
     assert relerr(H.vcycle_ilu(fac, x0, b, [1, 2], [1, 2], nu=1), x3) > 1e-6
+
+
+def test_schur_on_the_finest_level_with_ilu_below_matches_dense_recursion():
+    """The Schur-smoothed cycle with the ILU smoother on level 1 as well:
+    schur_apply to the residual on level 0 (before and after), the dense
+    Neumann series of level 1's row-scaled ILU(0) factors there, direct solve
+    on level 2; and with one level of factors it is vcycle_schur bit for bit."""
+    A = synth.cutcell7(10, 9, 8, seed=8)
+    n = len(A[0]) - 1
+    H = oracle.AMG(A, theta=0.25, max_levels=3, coarse_size=1)
+    assert len(H.levels) == 3
+    L0, L1, L2 = H.levels
+
+    def Pmat(L, nc):
+        P = np.zeros((L.n, nc))
+        pp, pc, pv = L.P
+        for i in range(L.n):
+            for q in range(pp[i], pp[i + 1]):
+                P[i, pc[q]] = pv[q]
+        return P
+
+    P0, P1 = Pmat(L0, L1.n), Pmat(L1, L2.n)
+    A0, A1, A2 = dense(A, n), dense(L1.A, L1.n), dense(L2.A, L2.n)
+    fac = H.level_factors("ilu0", count=2)
+    parts, tau, fill = 3, 1e-3, 6
+    mL, mU = [3, 2], [2, 3]
+    M1 = dense_smoother(fac[1], L1.n, mL[1], mU[1])
+
+    def level1(b1):
+        x = M1 @ b1
+        x = x + P1 @ np.linalg.solve(A2, P1.T @ (b1 - A1 @ x))
+        return x + M1 @ (b1 - A1 @ x)
+
+    b = synth.rhs(n, 1, seed=4)[:, 0]
+    x0 = synth.rhs(n, 1, seed=5)[:, 0]
+    x1 = x0 + oracle.schur_apply(A, b - A0 @ x0, parts, tau, fill, mL[0], mU[0])
+    x2 = x1 + P0 @ level1(P0.T @ (b - A0 @ x1))
+    x3 = x2 + oracle.schur_apply(A, b - A0 @ x2, parts, tau, fill, mL[0], mU[0])
+    got = H.vcycle_ilu(fac, x0, b, mL, mU, schur=(parts, tau, fill))
+    assert relerr(got, x3) < 1e-12
+    one = H.vcycle_ilu(fac[:1], x0, b, mL[0], mU[0], nu=2, schur=(parts, tau, fill))
+    assert np.array_equal(one, H.vcycle_schur(x0, b, parts, tau, fill, mL[0], mU[0], nu=2))
