@@ -318,3 +318,52 @@ def test_ilu_levels_refused_for_gauss_seidel_factors(silu, ctx):
     with pytest.raises(silu.SiluError):
         F.amg_setup(coarse_size=40, ilu_levels=-1)
     F.amg_setup(coarse_size=40, ilu_levels=1)  # the finest level alone takes any kind
+
+
+def test_schur_smoothed_cycle_with_ilu_below_matches_oracle(silu, ctx):
+    """The Schur complement smoother on the finest level and ILU smoothers of
+    their own on the next two levels, three successive cycles against the
+    oracle at 1e-12, and FGMRES(30) preconditioned by it."""
+    A = synth.poisson7(21, 19, 17)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+    F.amg_setup(theta=0.25, max_levels=12, coarse_size=40, jacobi_sweeps=1, ilu_levels=3)
+    F.schur_setup(4, 1e-3, 10)
+    H = oracle.AMG(A, theta=0.25, max_levels=12, coarse_size=40)
+    assert len(H.levels) >= 4
+    fac = H.level_factors("ilu0", count=3)
+    b = synth.rhs(n, 1, seed=8)[:, 0]
+    x = synth.rhs(n, 1, seed=9)[:, 0]
+    xd, bd = dev(x.copy()), dev(b)
+    for cycle in range(3):
+        x = H.vcycle_ilu(fac, x, b, 3, 2, schur=(4, 1e-3, 10))
+        F.amg_vcycle_schur(xd, bd, 3, 2)
+        ctx.check()
+        assert relerr(host(xd), x) < 1e-12, cycle
+    xs = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st, its, rel = silu.fgmres_solve(F, xs, bd, tol=1e-10, restart=30, maxit=500, sweeps_L=3, sweeps_U=2,
+                                     precond=silu.PRECOND_AMG_SCHUR)
+    assert st == silu.OK and rel <= 1e-10, (st, its, rel)
+
+
+def test_fp32_factors_on_every_ilu_level(silu, ctx):
+    """FP32 factors and sweeps on the finest and every coarser ILU level (the
+    rest of the cycle and FGMRES in FP64): one cycle within FP32 rounding of
+    the oracle's FP64 cycle, and FGMRES(30) still reaches 1e-10."""
+    A = synth.cutcell7(40, 36, 30, seed=10)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0", prec=silu.FP32)
+    F.amg_setup(theta=0.25, coarse_size=200, jacobi_sweeps=1, ilu_levels=25)
+    H = oracle.AMG(A, theta=0.25, coarse_size=200)
+    fac = H.level_factors("ilu0")
+    b = synth.rhs(n, 1, seed=1)[:, 0]
+    want = H.vcycle_ilu(fac, np.zeros(n), b, 3, 3)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    F.amg_vcycle(x, dev(b), 3, 3)
+    assert relerr(host(x), want) < 1e-5
+    xs = torch.zeros(n, dtype=torch.float64, device="cuda")
+    st, its, rel = silu.fgmres_solve(F, xs, dev(b), tol=1e-10, restart=30, maxit=2000, sweeps_L=3, sweeps_U=3,
+                                     precond=silu.PRECOND_AMG)
+    assert st == silu.OK and rel <= 1e-10, (st, its, rel)
+    r = oracle.residual(A, host(xs).reshape(n, 1), b.reshape(n, 1))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10
