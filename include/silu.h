@@ -514,6 +514,15 @@ silu_status silu_amg_vcycle(silu_ilu F, double* x, const double* b, int sweeps_L
  * -> SILU_ERR_INVALID_ARG.  Stream-ordered on F's context.
  */
 silu_status silu_amg_vcycle_schur(silu_ilu F, double* x, const double* b, int sweeps_L, int sweeps_U);
+/*
+ * The factor object that smooths AMG level `level` with the ILU smoother:
+ * F itself for level 0, the row-scaled factorisation of A_l for levels
+ * 1 .. ilu_levels - 1 (silu_amg_params).  *out is borrowed: valid until the
+ * next silu_amg_setup on F or F's destruction, never passed to
+ * silu_ilu_destroy.  Queries (silu_ilu_stats, silu_ilu_export) work on it.
+ * A level without one, or no hierarchy -> SILU_ERR_INVALID_ARG.
+ */
+silu_status silu_amg_level_ilu(silu_ilu F, int level, silu_ilu* out);
 /* Levels and, for l < cap, rows, entries of A_l and of P_l (0 on the coarsest level). */
 silu_status silu_amg_stats(silu_ilu F, int cap, int* levels, int64_t* rows, int64_t* nnz_A, int64_t* nnz_P);
 /* Host copies of level l (parity tests): A_l (row pointers n_l + 1), P_l

@@ -109,6 +109,7 @@ def load():
         "silu_amg_setup": (i32, [vp, vp]),
         "silu_amg_vcycle": (i32, [vp, vp, vp, i32, i32]),
         "silu_amg_vcycle_schur": (i32, [vp, vp, vp, i32, i32]),
+        "silu_amg_level_ilu": (i32, [vp, i32, vp]),
         "silu_amg_stats": (i32, [vp, i32, ctypes.POINTER(i32), vp, vp, vp]),
         "silu_amg_export_level": (i32, [vp, i32] + [vp] * 7),
         "silu_schur_setup": (i32, [vp, i32, dbl, i32]),
@@ -158,7 +159,7 @@ def exported_symbols():
             "silu_mat_destroy", "silu_mat_residual", "silu_mat_set_shape", "silu_mat_autotune", "ilu_setup", "ilu_refactor", "silu_ilu_save", "silu_ilu_load", "ilu_smooth", "direct_trisolve", "fgmres_solve",
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
             "silu_ilu_export_colscale", "silu_ilu_power_norms", "silu_ilu_dep", "silu_amg_setup", "silu_amg_vcycle", "silu_amg_vcycle_schur",
-            "silu_amg_stats", "silu_amg_export_level", "silu_schur_setup", "silu_schur_smooth",
+            "silu_amg_level_ilu", "silu_amg_stats", "silu_amg_export_level", "silu_schur_setup", "silu_schur_smooth",
             "silu_schur_stats",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
             "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_set_direct", "silu_ilu_set_fused", "silu_ilu_layout", "silu_ilu_tune_table", "silu_ctx_set_overlap",
@@ -443,6 +444,26 @@ class ILU:
                                                       _ptr(nzp)), "silu_amg_stats")
         k = lev.value
         return {"levels": k, "rows": rows[:k].tolist(), "nnz_A": nza[:k].tolist(), "nnz_P": nzp[:k].tolist()}
+
+    def amg_level_ilu(self, level: int) -> "ILU":
+        """The (borrowed) factor object that smooths AMG level `level` with the ILU smoother: self for
+        level 0, the row-scaled factors of A_l for levels below it that amg_setup(ilu_levels=...)
+        gave one; valid while this hierarchy lives."""
+        h = ctypes.c_void_p()
+        _check(self.ctx.handle, load().silu_amg_level_ilu(self.handle, int(level), ctypes.byref(h)),
+               "silu_amg_level_ilu")
+        if level == 0:
+            return self
+        G = ILU.__new__(ILU)
+        G.handle = h.value
+        G._borrowed = True
+        G._owner = self
+        G.A = None
+        G.ctx = self.ctx
+        G.n = int(self.amg_stats()["rows"][level])
+        G.prec = self.prec
+        G.scale = SCALE_ROW
+        return G
 
     def amg_level(self, level: int):
         """Host copies of level `level`: A_l, P_l (None on the coarsest level), coarse-point marks."""

@@ -104,14 +104,14 @@ double* poly_gs(silu_ilu F, AmgDevLevel& L, double* x, const double* b, int nu, 
 // The configured smoother of a level below the finest: the level's own ILU
 // smoother where it has one (m_L + m_U sweeps, or its exact triangular
 // solves when mL < 0; x is updated in place), else the coarse smoother.
-double* coarse_smooth(silu_ilu F, AmgDevLevel& L, double* x, const double* b, bool x_zero, int mL, int mU,
-                      bool capturing) {
+double* coarse_smooth(silu_ilu F, int l, double* x, const double* b, bool x_zero, int mL, int mU, bool capturing) {
   const AmgState& G = *F->amg;
-  if (L.FL) {
+  AmgDevLevel& L = *G.lev[l];
+  if (silu_ilu FL = G.ilu_fac[l]) {
     if (mL < 0)
-      silu::direct_chunk(L.FL, x, b, 1, 1, 0, x_zero, capturing);
+      silu::direct_chunk(FL, x, b, 1, 1, 0, x_zero, capturing);
     else
-      silu::smooth_chunk(L.FL, x, b, 1, 1, 0, mL, mU, x_zero);
+      silu::smooth_chunk(FL, x, b, 1, 1, 0, mL, mU, x_zero);
     return x;
   }
   if (G.coarse_kind == SILU_AMG_POLY_GS) return poly_gs(F, L, x, b, G.nu, G.gs_terms, x_zero);
@@ -130,13 +130,13 @@ double* level_cycle(silu_ilu F, int l, int mL, int mU, bool capturing) {
                                                     F->ctx->stream));
     return L.x.as<double>();
   }
-  double* x = coarse_smooth(F, L, L.x.as<double>(), b, true, mL, mU, capturing);
+  double* x = coarse_smooth(F, l, L.x.as<double>(), b, true, mL, mU, capturing);
   AmgDevLevel& C = *G.lev[l + 1];
   op(F, L.A, SILU_K_RESIDUAL, b, x, L.r.as<double>(), nullptr, nullptr, silu::EPI_STORE);       // r = b - A x
   op(F, L.R, SILU_K_RESIDUAL, nullptr, L.r.as<double>(), C.b.as<double>(), nullptr, nullptr, silu::EPI_SPMV);
   const double* v = level_cycle(F, l + 1, mL, mU, capturing);
   op(F, L.Pneg, SILU_K_RESIDUAL, nullptr, v, nullptr, nullptr, x, silu::EPI_ADDX);             // x += P v
-  return coarse_smooth(F, L, x, b, false, mL, mU, capturing);
+  return coarse_smooth(F, l, x, b, false, mL, mU, capturing);
 }
 
 cudaError_t upload_level(const silu::AmgLevel& H, AmgDevLevel& D, bool own_a, bool coarsest, bool gs,
@@ -164,9 +164,11 @@ cudaError_t upload_level(const silu::AmgLevel& H, AmgDevLevel& D, bool own_a, bo
 
 }  // namespace
 
-AmgDevLevel::~AmgDevLevel() {
-  if (FL) silu_ilu_destroy(FL);
-  if (Amat) silu_mat_destroy(Amat);
+AmgState::~AmgState() {
+  for (silu_ilu f : ilu_fac)
+    if (f) silu_ilu_destroy(f);
+  for (silu_mat m : ilu_mat)
+    if (m) silu_mat_destroy(m);
 }
 
 namespace silu {
@@ -174,12 +176,12 @@ namespace silu {
 cudaError_t amg_prepare_direct(silu_ilu F) {
   cudaError_t e = ensure_direct(F);
   if (e != cudaSuccess || !F->amg) return e;
-  for (auto& L : F->amg->lev) {
-    if (!L->FL) continue;
-    e = ensure_direct(L->FL);
+  for (silu_ilu FL : F->amg->ilu_fac) {
+    if (!FL) continue;
+    e = ensure_direct(FL);
     if (e != cudaSuccess) return e;
     try {
-      level_graph(L->FL, 1, 1, 0);  // settles the level launch form before a capture records the cycle
+      level_graph(FL, 1, 1, 0);  // settles the level launch form before a capture records the cycle
     } catch (const CudaFail& f) {
       return f.e;
     }
@@ -255,6 +257,19 @@ silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params) {
     int st = silu::amg_build(F->A->A, p.theta, p.max_levels, p.coarse_size, G->host, msg);
     if (st == silu::H_OK && p.coarse_smoother == SILU_AMG_POLY_GS) st = silu::amg_gs_factors(G->host, msg);
     if (st != silu::H_OK) return silu::set_err(ctx, (silu_status)st, msg);
+    // levels 1 .. ilu_levels - 1 above the coarsest: an incomplete
+    // factorisation of A_l of F's kind, row-scaled, as a factor object
+    const int nlev = (int)G->host.lev.size();
+    G->ilu_levels = std::max(1, std::min(p.ilu_levels, nlev - 1));
+    G->ilu_mat.assign(nlev, nullptr);
+    G->ilu_fac.assign(nlev, nullptr);
+    for (int l = 1; l < G->ilu_levels; ++l) {
+      const silu::Csr& Al = G->host.lev[l].A;
+      silu_status sl = silu_mat_create(ctx, Al.n, Al.nnz(), Al.rp.data(), Al.ci.data(), Al.va.data(), &G->ilu_mat[l]);
+      if (sl == SILU_OK)
+        sl = ilu_setup(ctx, G->ilu_mat[l], F->kind, F->tau, F->fill, SILU_SCALE_ROW, F->prec, &G->ilu_fac[l]);
+      if (sl != SILU_OK) return sl;  // the context's message names the failure
+    }
     if (ctx->device >= 0) {
       silu_status ds = silu::device_ok(ctx);
       if (ds != SILU_OK) return ds;
@@ -269,16 +284,9 @@ silu_status silu_amg_setup(silu_ilu F, const silu_amg_params* params) {
         e = silu::upload(G->cinv, G->host.coarse_inv.data(), G->host.coarse_inv.size(), s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return silu::cuda_err(ctx, e, "upload of the AMG hierarchy");
-      // levels 1 .. ilu_levels - 1 above the coarsest: an incomplete
-      // factorisation of A_l of F's kind, row-scaled, as a factor object
-      G->ilu_levels = std::max(1, std::min(p.ilu_levels, (int)nl - 1));
-      for (int l = 1; l < G->ilu_levels; ++l) {
-        const silu::Csr& Al = G->host.lev[l].A;
-        AmgDevLevel& D = *G->lev[l];
-        silu_status sl = silu_mat_create(ctx, Al.n, Al.nnz(), Al.rp.data(), Al.ci.data(), Al.va.data(), &D.Amat);
-        if (sl == SILU_OK) sl = ilu_setup(ctx, D.Amat, F->kind, F->tau, F->fill, SILU_SCALE_ROW, F->prec, &D.FL);
-        if (sl != SILU_OK) return sl;  // the context's message names the failure
-        e = silu::ensure_vectors(D.FL, 1);
+      for (silu_ilu FL : G->ilu_fac) {
+        if (!FL) continue;
+        e = silu::ensure_vectors(FL, 1);
         if (e != cudaSuccess) return silu::cuda_err(ctx, e, "workspace of an AMG level's ILU smoother");
       }
     }
@@ -324,6 +332,22 @@ silu_status silu_amg_vcycle_schur(silu_ilu F, double* x, const double* b, int sw
   } catch (const CudaFail& f) {
     return silu::cuda_err(ctx, f.e, f.what);
   }
+  return SILU_OK;
+}
+
+silu_status silu_amg_level_ilu(silu_ilu F, int level, silu_ilu* out) {
+  if (!F || !out) return SILU_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!F->amg) return silu::set_err(F->ctx, SILU_ERR_INVALID_ARG, "no AMG hierarchy (silu_amg_setup)");
+  const int nlev = (int)F->amg->host.lev.size();
+  if (level < 0 || level >= nlev) return silu::set_err(F->ctx, SILU_ERR_INVALID_ARG, "no such level");
+  if (level == 0) {
+    *out = F;
+    return SILU_OK;
+  }
+  if (!F->amg->ilu_fac[level])
+    return silu::set_err(F->ctx, SILU_ERR_INVALID_ARG, "this level has no ILU smoother (silu_amg_params.ilu_levels)");
+  *out = F->amg->ilu_fac[level];
   return SILU_OK;
 }
 

@@ -135,14 +135,6 @@ struct AmgDevLevel {
   DBuf l1inv, x, t, b, r;
   DBuf G_rp, G_ci, G_va, G_tiles, gdinv, y2;  // polynomial Gauss-Seidel: L D^{-1}, 1 / a_ii, a second sweep buffer
   DevCsr Lgs;
-  // the ILU smoother of this level (silu_amg_params.ilu_levels): A_l and its
-  // row-scaled factors as a factor object of their own (owned; null elsewhere)
-  silu_mat Amat = nullptr;
-  silu_ilu FL = nullptr;
-  AmgDevLevel() = default;
-  AmgDevLevel(const AmgDevLevel&) = delete;
-  AmgDevLevel& operator=(const AmgDevLevel&) = delete;
-  ~AmgDevLevel();
 };
 
 // An AMG hierarchy attached to a factor object: the factors smooth the
@@ -160,6 +152,15 @@ struct AmgState {
   double theta = 0.25;
   int max_levels = 25;
   int64_t coarse_size = 400;
+  // the ILU smoothers of levels 1 .. ilu_levels - 1 (silu_amg_params.ilu_levels):
+  // A_l and its row-scaled factors as objects of their own, indexed by level
+  // (owned; null at level 0, which F smooths, and below)
+  std::vector<silu_mat> ilu_mat;
+  std::vector<silu_ilu> ilu_fac;
+  AmgState() = default;
+  AmgState(const AmgState&) = delete;
+  AmgState& operator=(const AmgState&) = delete;
+  ~AmgState();
 };
 
 // The ILUT Schur complement smoother attached to a factor object (Sec. 3.1,

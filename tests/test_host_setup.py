@@ -423,3 +423,37 @@ def test_threaded_setup_matches_oracle_bit_for_bit(ctx):
     for part in ("L", "U", "Us"):
         for k in range(3):
             assert np.array_equal(G[part][k], ex[part][k])
+
+
+@pytest.mark.parametrize("gen,kind,tau,fill", [("cutcell", "ilu0", 0.0, 0), ("hex27", "ilut", 1e-3, 8),
+                                               ("cutcell", "iluk", 0.0, 1), ("poisson", "ilut", 1e-2, 3)])
+def test_amg_ilu_levels_factors_match_oracle(ctx, gen, kind, tau, fill):
+    """ILU smoothing below the finest level (Sec. 6): the factor object of
+    every ILU level holds the row-scaled factorisation of that level's A_l of
+    the finest level's kind: the oracle's patterns exactly and its values to
+    1e-14 (the hierarchy is bit for bit the oracle's), with the oracle's level
+    counts; a level without one is refused."""
+    A = {"cutcell": lambda: synth.cutcell7(11, 10, 9, seed=4), "hex27": lambda: synth.hex27(9, 8, 8, seed=5),
+         "poisson": lambda: synth.poisson7(12, 11, 10)}[gen]()
+    F = silu.ILU(silu.Matrix(ctx, *A), kind, tau=tau, fill=fill)
+    F.amg_setup(theta=0.25, max_levels=10, coarse_size=30, jacobi_sweeps=1, ilu_levels=25)
+    H = oracle.AMG(A, theta=0.25, max_levels=10, coarse_size=30)
+    nlev = F.amg_stats()["levels"]
+    assert nlev == len(H.levels) >= 3
+    fac = H.level_factors(kind, tau, fill)
+    assert len(fac) == nlev - 1
+    assert F.amg_level_ilu(0) is F
+    for l in range(1, nlev - 1):
+        G = F.amg_level_ilu(l)
+        OF = oracle.factor(H.levels[l].A, kind, tau, fill)
+        ex = compare_with_oracle(G, OF, fac[l])
+        st = G.stats()
+        assert st["levels_L"] == oracle.levels_lower(fac[l].L)[0], l
+        assert st["levels_U"] == oracle.levels_upper(fac[l].Us)[0], l
+        assert len(ex["dinv"]) == H.levels[l].n
+    with pytest.raises(silu.SiluError):
+        F.amg_level_ilu(nlev - 1)  # the coarsest level is solved directly
+    F.amg_setup(theta=0.25, max_levels=10, coarse_size=30, ilu_levels=2)
+    F.amg_level_ilu(1)
+    with pytest.raises(silu.SiluError):
+        F.amg_level_ilu(2)
