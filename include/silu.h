@@ -259,7 +259,11 @@ silu_status ilu_setup(silu_ctx ctx, silu_mat A, silu_kind kind, double tau, int 
  * values in the sorted, duplicate-free order of the silu_mat), reusing the
  * symbolic phase (Sec. 3.1: the pattern of the pressure matrix does not change
  * during a fluid step).  ILU0, ILUK, GS and SGS (ILUT's pattern depends on
- * the values): SILU_ERR_INVALID_ARG otherwise.  Blocks.
+ * the values): SILU_ERR_INVALID_ARG otherwise.  Blocks.  An AMG hierarchy or
+ * a Schur complement smoother already attached to F keeps the operators it
+ * was built from (the finest level's residual uses the new values): reusing
+ * it is a valid, possibly weaker, preconditioner; silu_amg_setup /
+ * silu_schur_setup again rebuild it from the new values.
  */
 silu_status ilu_refactor(silu_ilu F, const double* new_val);
 
