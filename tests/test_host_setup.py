@@ -353,6 +353,8 @@ def test_amg_and_schur_on_degenerate_systems(ctx):
         F.amg_setup()
         st = F.amg_stats()
         assert st["levels"] == 1 and st["rows"] == [len(A[0]) - 1]
+        F.amg_setup(ilu_levels=5)  # no level below the finest to give an ILU smoother
+        assert F.amg_stats()["levels"] == 1 and F.amg_level_ilu(0) is F
         F.schur_setup(4, 1e-3, 5)
         sst = F.schur_stats()
         assert sst["interface"] == 0 and sst["interior"] == len(A[0]) - 1
