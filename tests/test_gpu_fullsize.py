@@ -117,7 +117,8 @@ def test_cutcell224_gmres_amg_full_size():
     """GMRES + AMG at the size of the paper's 11M-row PeleLM system (224^3 cut-cell, 11,239,424 rows):
     FP32 ILU(0) factors smoothing the finest level with 5+5 Richardson sweeps reach 1e-8 in the same
     number of FGMRES iterations as the cycle with exact triangular solves; the true relative residual
-    of the returned iterate is recomputed by the oracle over the whole system."""
+    of the returned iterate is recomputed by the oracle over the whole system; then the cycle with ILU
+    smoothers on every level above the coarsest."""
     import paper_2111_09512_gb300 as silu
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -142,6 +143,17 @@ def test_cutcell224_gmres_amg_full_size():
         assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-8
         its[precond] = k
     assert abs(its[silu.PRECOND_AMG] - its[silu.PRECOND_AMG_DIRECT]) <= 2, its
+    # ILU smoothing on every level above the coarsest (Sec. 6): FP32 factors of each A_l, the same 5+5
+    # sweeps; a stronger cycle, so no more iterations than with ILU on the finest level alone
+    F.amg_setup(theta=0.25, coarse_size=400, jacobi_sweeps=1, ilu_levels=25)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    status, k, rel = silu.fgmres_solve(F, x, bd, tol=1e-8, restart=30, maxit=600, sweeps_L=5, sweeps_U=5,
+                                       precond=silu.PRECOND_AMG)
+    assert status == silu.OK and rel <= 1e-8, (status, k, rel)
+    torch.cuda.synchronize()
+    r = oracle.residual(A, x.cpu().numpy().reshape(n, 1), b.reshape(n, 1))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-8
+    assert k <= its[silu.PRECOND_AMG], (k, its)
 
 
 def test_hex27_256_fp32_application_error_vs_fp64_oracle():
