@@ -40,6 +40,9 @@ CASES = [
     ("hex27 17x15x14 p3", lambda: synth.hex27(17, 15, 14, seed=2), 3, 1e-3, 12, (2, 2)),
     ("poisson 24^3 p8", lambda: synth.poisson7(24), 8, 1e-2, 6, (4, 1)),
     ("poisson 12^3 p1", lambda: synth.poisson7(12), 1, 1e-3, 10, (3, 3)),
+    # no interior rows: every row its own part, and more parts than rows (B is empty, S = A)
+    ("poisson 6^3 every row a part", lambda: synth.poisson7(6), 216, 1e-3, 10, (3, 3)),
+    ("poisson 6^3 more parts than rows", lambda: synth.poisson7(6), 300, 1e-3, 10, (2, 1)),
 ]
 
 
