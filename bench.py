@@ -1411,6 +1411,52 @@ def run_schur_study(args):
     return 0
 
 
+def run_vcycle_only(args):
+    """Only V-cycles of the GMRES+AMG workload, for profiling and quick timing:
+    the 224^3 cut-cell matrix (seed 1), FP64 ILU(0) factors with 10+10 sweeps
+    on the finest level, Ruge-Stueben hierarchy (theta 0.25, coarsest <= 400
+    rows), one l1-Jacobi step below; W untimed and K timed cycles, one JSON
+    line (time per cycle, the cycle's algorithmic bytes and their fraction of
+    the measured HBM bandwidth, per-class kernel split)."""
+    import torch
+    import paper_2111_09512_gb300 as silu
+    import synth
+    silu.build()
+    stream = torch.cuda.current_stream()
+    ctx = silu.Context(0, stream)
+    A = synth.cutcell7(224, seed=1)
+    n = len(A[0]) - 1
+    M = silu.Matrix(ctx, *A)
+    del A
+    F = silu.ilu_setup(ctx, M, "ilu0")
+    F.amg_setup(theta=0.25, max_levels=25, coarse_size=400, jacobi_sweeps=1)
+    st, sf = F.amg_stats(), F.stats()
+    b = torch.from_numpy(synth.rhs(n, 1, seed=1)[:, 0].copy()).cuda()
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        F.amg_vcycle(x, b, 10, 10)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        F.amg_vcycle(x, b, 10, 10)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    ms = e0.elapsed_time(e1) / args.steps
+    peak, _ = load_peaks()
+    nbytes = vcycle_bytes(st, sf["nnz_L"], sf["nnz_U"], 10, 10, 1)
+    line = {"vcycle_only": "cutcell7-224^3 ILU(0) FP64 + AMG, 10+10 sweeps on the finest level", "rows": n,
+            "levels": st["levels"], "steps": args.steps, "warmup": args.warmup, "ms_per_cycle": round(ms, 4),
+            "algorithmic_bytes": int(nbytes), "fraction_of_measured_hbm": round(nbytes / (ms * 1e-3) / 1e9 / peak, 3),
+            "launches_per_cycle": {k: v[0] // args.steps for k, v in prof.items() if v[0]},
+            "kernel_ms_per_cycle": {k: round(v[1] / args.steps, 4) for k, v in prof.items() if v[0]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_apply_only(args):
     """Only smoother applications of one workload, for profiling and quick
     timing: W untimed and K timed applications from x = 0 on one GPU, one
@@ -1525,6 +1571,8 @@ def main():
     ap.add_argument("--apply-only", choices=["cutcell128", "cutcell128_r4", "hex27_256", "hex27_128",
                                              "hex27_128_direct", "poisson32_r4"], default=None,
                     help="run only smoother applications of one workload (profiling, quick timing)")
+    ap.add_argument("--vcycle-only", action="store_true",
+                    help="run only V-cycles of the 224^3 GMRES+AMG workload (profiling, quick timing)")
     ap.add_argument("--schur-study", default=None, metavar="KIND:EDGE",
                     help="run only the Schur complement smoother study on cutcell7:EDGE, poisson7:EDGE or hex27:EDGE")
     ap.add_argument("--schur-parts", default="8,64", metavar="P[,P...]")
@@ -1545,6 +1593,8 @@ def main():
         return run_apply_only(args)
     if args.schur_study:
         return run_schur_study(args)
+    if args.vcycle_only:
+        return run_vcycle_only(args)
     return run_silu(args)
 
 
