@@ -391,6 +391,14 @@ def run_silu(args):
     peak, peak_kind = load_peaks()
     traffic = recorded_traffic()
     total_prof_ms = sum(v[1] for v in prof.values())
+    # the FP64 pipe, the sweeps' other bound: with one lane per row a tile costs as many warp-wide FMAs as
+    # its longest row has entries (silu_ilu_layout's slots per entry); GB300 retires 2 FP64 lanes per clock
+    # per SM
+    padL, padU = (float(v) for v in F.layout()["pad_natural"])
+    slots = nL * nnzL * padL + nU * nnzU * padU
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    fp64_peak = sms * 2 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6
+    fp64_rate = slots / ((msL + msU) * 1e-3) if msL + msU > 0 else None
 
     # end to end through the public API with host buffers, copies inside the region: every step uploads
     # its x and b from pinned host memory, applies the smoother and reads x back.  Steps are independent
@@ -500,7 +508,12 @@ def run_silu(args):
                          if (traffic and msL + msU > 0) else None,
                          "dram_frac": round(traffic / ((msL + msU) * 1e-3 / (nL + nU)) / 1e9 / peak, 4)
                          if (traffic and msL + msU > 0) else None,
-                         "share_of_timed_kernels": round((msL + msU) / total_prof_ms, 4) if total_prof_ms else None},
+                         "share_of_timed_kernels": round((msL + msU) / total_prof_ms, 4) if total_prof_ms else None,
+                         "fp64": {"fma_slots_per_entry": [round(padL, 4), round(padU, 4)],
+                                  "achieved_gfma_s": round(fp64_rate / 1e9, 1) if fp64_rate else None,
+                                  "peak_gfma_s": round(fp64_peak / 1e9, 1),
+                                  "frac": round(fp64_rate / fp64_peak, 4) if fp64_rate else None,
+                                  "peak_basis": f"2 FP64 lanes per clock per SM x {sms} SMs x max SM clock"}},
             "kernel_ms": {k: [v[0], round(v[1], 4)] for k, v in prof.items() if v[0]},
             "e2e": {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": 2 * n * 8,
                     "d2h_bytes_per_step": n * 8, "ms_per_step": round(ms_e2e / args.steps, 5),
