@@ -38,3 +38,26 @@ def test_headline_workload_bytes():
     assert bench.apply_bytes(n, nnzA, nnzL, nnzU, 1, 8, 10, 10) == 5286503540
     assert round(bench.sweep_bytes(n, nnzL, 1, 8) / 1e6, 1) == 256.3
     assert round(bench.sweep_bytes(n, nnzU, 1, 8) / 1e6, 1) == 301.4
+
+
+def test_vcycle_bytes_by_hand():
+    """The V-cycle model (Sec. 6.3 in kind) on a three-level hierarchy with
+    hand-picked sizes: finest level 10 rows (A 28 entries, P 12), level 1 4
+    rows (A 10, P 5), coarsest 2 rows; L_s / Utilde_s 9 entries each, 2 + 2
+    sweeps, one l1-Jacobi step."""
+    st = {"levels": 3, "rows": [10, 4, 2], "nnz_A": [28, 10, 3], "nnz_P": [12, 5, 0]}
+    n0, n1, n2 = 10, 4, 2
+    post = bench.apply_bytes(n0, 28, 9, 9, 1, 8, 2, 2)
+    pre = post - bench.resid_bytes(n0, 28, 1) - 8 * n0      # from x = 0: no residual, no read of x
+    lev0 = (bench.resid_bytes(n0, 28, 1)                     # r = b - A x
+            + (12 * 12 + 4 * (n1 + 1) + 8 * n0 + 8 * n1)     # R r: P's entries, n1 rows, reads r, writes b_1
+            + (12 * 12 + 4 * (n0 + 1) + 8 * n1 + 8 * n0) + 8 * n0)  # x += P v (x read and written)
+    jac1 = 3 * 8 * n1 + (10 * 12 + 4 * (n1 + 1) + 8 * n1 + 8 * n1 + 3 * 8 * n1)  # x = D^-1 b, then one sweep
+    lev1 = (jac1 + bench.resid_bytes(n1, 10, 1)
+            + (5 * 12 + 4 * (n2 + 1) + 8 * n1 + 8 * n2)
+            + (5 * 12 + 4 * (n1 + 1) + 8 * n2 + 8 * n1) + 8 * n1)
+    coarsest = 8 * n2 * n2 + 16 * n2
+    assert bench.vcycle_bytes(st, 9, 9, 2, 2, 1) == pre + post + lev0 + lev1 + coarsest
+    # no smoothing steps below the finest level: the level's x is only cleared (one write)
+    assert (bench.vcycle_bytes(st, 9, 9, 2, 2, 1) - bench.vcycle_bytes(st, 9, 9, 2, 2, 0)
+            == jac1 - 8 * n1)
