@@ -101,8 +101,9 @@ def _load():
         "orc_amg_vcycle": (i32, [vp] + [vp] * 7 + [i32, i32, i32, i32, i32, vp, vp]),
         "orc_schur_interface": (i64, [i64, vp, vp, i32, vp]),
         "orc_schur_apply": (i32, [i64, vp, vp, vp, i32, dbl, i32, i32, i32, vp, vp]),
-        "orc_amg_vcycle_schur": (i32, [vp, i32, dbl, i32, i32, i32, i32, i32, i32, vp, vp]),
-        "orc_amg_vcycle_ilu": (i32, [vp, i32] + [vp] * 9 + [i32, i32, i32, i32, dbl, i32, vp, vp]),
+        "orc_schur_apply_prec": (i32, [i64, vp, vp, vp, i32, dbl, i32, i32, i32, i32, vp, vp]),
+        "orc_amg_vcycle_schur": (i32, [vp, i32, dbl, i32, i32, i32, i32, i32, i32, i32, vp, vp]),
+        "orc_amg_vcycle_ilu": (i32, [vp, i32] + [vp] * 9 + [i32, i32, i32, i32, dbl, i32, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -585,8 +586,8 @@ class AMG:
         """One V-cycle as vcycle with the ILU smoother on the first len(factors) levels: level l
         is smoothed by m_L + m_U sweeps on factors[l] (the row-scaled factors of A_l; mL, mU an
         int or one count per level), the levels below by the coarse smoother.  schur = (parts,
-        tau, fill) smooths the finest level by the ILUT Schur complement smoother instead
-        (factors[0] is then not read).  Returns a new array."""
+        tau, fill[, iface_prec]) smooths the finest level by the ILUT Schur complement smoother
+        instead (factors[0] is then not read).  Returns a new array."""
         k = len(factors)
         n = self.levels[0].n
         x = np.ascontiguousarray(x, np.float64).reshape(n).copy()
@@ -607,21 +608,22 @@ class AMG:
                                         ptrs([t[2] for t in Us]), ptrs([S.dinv for S in factors]), _p(mLs), _p(mUs),
                                         int(nu), 1 if coarse == "gs" else 0, int(terms),
                                         int(schur[0]) if schur else 0, float(schur[1]) if schur else 0.0,
-                                        int(schur[2]) if schur else 0, _p(x), _p(b))
+                                        int(schur[2]) if schur else 0,
+                                        int(schur[3]) if schur and len(schur) > 3 else 0, _p(x), _p(b))
         if st:
             raise OracleError(st, "amg_vcycle_ilu")
         return x
 
     def vcycle_schur(self, x, b, parts: int, tau: float, fill: int, mL: int, mU: int, nu: int = 1,
-                     coarse: str = "jacobi", terms: int = 2):
+                     coarse: str = "jacobi", terms: int = 2, iface_prec: int = 0):
         """One V-cycle as vcycle, the finest level smoothed (before and after the coarse-grid
         correction) by one application of the ILUT Schur complement smoother (schur_apply over
-        `parts` row blocks) instead of the ILU smoother.  Returns a new array."""
+        `parts` row blocks, iface_prec as there) instead of the ILU smoother.  Returns a new array."""
         n = self.levels[0].n
         x = np.ascontiguousarray(x, np.float64).reshape(n).copy()
         b = np.ascontiguousarray(b, np.float64).reshape(n)
-        st = _load().orc_amg_vcycle_schur(self._h, int(parts), float(tau), int(fill), int(mL), int(mU), int(nu),
-                                          1 if coarse == "gs" else 0, int(terms), _p(x), _p(b))
+        st = _load().orc_amg_vcycle_schur(self._h, int(parts), float(tau), int(fill), int(iface_prec), int(mL),
+                                          int(mU), int(nu), 1 if coarse == "gs" else 0, int(terms), _p(x), _p(b))
         if st:
             raise OracleError(st, "amg_vcycle_schur")
         return x
@@ -644,14 +646,15 @@ def schur_interface(A, parts: int):
     return int(k), marks[:n]
 
 
-def schur_apply(A, r, parts: int, tau: float, fill: int, mL: int, mU: int):
-    """z = M^{-1} r of the ILUT Schur complement smoother (Sec. 3.1, Eq. schur), one right-hand side."""
+def schur_apply(A, r, parts: int, tau: float, fill: int, mL: int, mU: int, iface_prec: int = 0):
+    """z = M^{-1} r of the ILUT Schur complement smoother (Sec. 3.1, Eq. schur), one right-hand side;
+    iface_prec = 1 right-preconditions the interface GMRES iteration by diag(C) (not in the paper)."""
     ap, ac, av = _csr(A)
     n = len(ap) - 1
     r = np.ascontiguousarray(r, np.float64).reshape(n)
     z = np.empty(max(n, 1), np.float64)
-    st = _load().orc_schur_apply(n, _p(ap), _p(ac), _p(av), int(parts), float(tau), int(fill), int(mL), int(mU),
-                                 _p(r), _p(z))
+    st = _load().orc_schur_apply_prec(n, _p(ap), _p(ac), _p(av), int(parts), float(tau), int(fill), int(mL),
+                                      int(mU), int(iface_prec), _p(r), _p(z))
     if st:
         raise OracleError(st, "schur_apply")
     return z[:n]

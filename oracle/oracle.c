@@ -1724,14 +1724,15 @@ typedef struct {
   int schur_parts;
   double schur_tau;
   int schur_fill;
+  int schur_prec; /* interface iteration preconditioned by diag(C) (orc_schur_apply_prec) */
   /* levels 1 .. ilu_levels - 1 (above the coarsest) are smoothed by the ILU
      smoother on ilu[l] instead of the coarse smoother */
   int ilu_levels;
   const level_ilu* ilu;
 } amg_smoother;
 
-int orc_schur_apply(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, int parts, double tau,
-                    int fill, int mL, int mU, const double* r, double* z);
+int orc_schur_apply_prec(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, int parts, double tau,
+                         int fill, int mL, int mU, int iface_prec, const double* r, double* z);
 
 /* x = x + M^{-1} (b - A_0 x) with the finest level's smoother. */
 static int fine_smooth(const orc_amg_level* L, const amg_smoother* sm, const double* b, double* x) {
@@ -1742,8 +1743,8 @@ static int fine_smooth(const orc_amg_level* L, const amg_smoother* sm, const dou
   double* r = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   double* z = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   orc_residual(n, 1, L->ap, L->ac, L->av, x, b, r);
-  const int st = orc_schur_apply(n, L->ap, L->ac, L->av, sm->schur_parts, sm->schur_tau, sm->schur_fill, sm->mL,
-                                 sm->mU, r, z);
+  const int st = orc_schur_apply_prec(n, L->ap, L->ac, L->av, sm->schur_parts, sm->schur_tau, sm->schur_fill,
+                                      sm->mL, sm->mU, sm->schur_prec, r, z);
   if (!st)
     for (int64_t i = 0; i < n; ++i) x[i] = x[i] + z[i];
   free(r);
@@ -1813,7 +1814,7 @@ static int multilevel(const orc_amg* h, int l, const amg_smoother* sm, const dou
 int orc_amg_vcycle(const orc_amg* h, const int64_t* lp, const int32_t* lc, const double* lv, const int64_t* sp,
                    const int32_t* sc, const double* sv, const double* dinv, int mL, int mU, int nu, int coarse,
                    int terms, double* x, const double* b) {
-  amg_smoother sm = {lp, sp, lc, sc, lv, sv, dinv, mL, mU, nu, coarse, terms, 0, 0.0, 0, 1, NULL};
+  amg_smoother sm = {lp, sp, lc, sc, lv, sv, dinv, mL, mU, nu, coarse, terms, 0, 0.0, 0, 0, 1, NULL};
   return multilevel(h, 0, &sm, b, x);
 }
 
@@ -1827,14 +1828,15 @@ int orc_amg_vcycle(const orc_amg* h, const int64_t* lp, const int32_t* lc, const
  * coarse smoother as in orc_amg_vcycle.  Entries at l >= nlev - 1 are not
  * used.  nilu >= 1 (level 0's factors are entry 0).  With schur_parts > 0
  * the finest level is smoothed by the ILUT Schur complement smoother instead
- * (as in orc_amg_vcycle_schur, with m_L[0] + m_U[0] sweeps in its blocks;
+ * (as in orc_amg_vcycle_schur, with m_L[0] + m_U[0] sweeps in its blocks and
+ * its interface iteration preconditioned by diag(C) when schur_prec = 1;
  * entry 0's factors are then not read).
  */
 int orc_amg_vcycle_ilu(const orc_amg* h, int nilu, const int64_t* const* lp, const int32_t* const* lc,
                        const double* const* lv, const int64_t* const* sp, const int32_t* const* sc,
                        const double* const* sv, const double* const* dinv, const int* mL, const int* mU, int nu,
-                       int coarse, int terms, int schur_parts, double schur_tau, int schur_fill, double* x,
-                       const double* b) {
+                       int coarse, int terms, int schur_parts, double schur_tau, int schur_fill, int schur_prec,
+                       double* x, const double* b) {
   if (nilu < 1 || schur_parts < 0) return ORC_BADARG;
   level_ilu* f = (level_ilu*)malloc(sizeof(level_ilu) * (size_t)nilu);
   if (!f) return ORC_NOMEM;
@@ -1843,7 +1845,7 @@ int orc_amg_vcycle_ilu(const orc_amg* h, int nilu, const int64_t* const* lp, con
     f[l] = e;
   }
   amg_smoother sm = {lp[0], sp[0], lc[0], sc[0], lv[0], sv[0], dinv[0], mL[0], mU[0], nu, coarse, terms,
-                     schur_parts, schur_tau, schur_fill, nilu, f};
+                     schur_parts, schur_tau, schur_fill, schur_prec, nilu, f};
   const int st = multilevel(h, 0, &sm, b, x);
   free(f);
   return st;
@@ -1853,13 +1855,14 @@ int orc_amg_vcycle_ilu(const orc_amg* h, int nilu, const int64_t* const* lp, con
  * The same V-cycle with the finest level smoothed, before and after the
  * coarse-grid correction, by one application of the ILUT Schur complement
  * smoother (Sec. 3.1: the smoother of one level of the V-cycle; orc_schur_apply
- * over `parts` row blocks, ILUT(tau, fill) of each block, m_L + m_U sweeps)
- * instead of the ILU smoother.
+ * over `parts` row blocks, ILUT(tau, fill) of each block, m_L + m_U sweeps;
+ * iface_prec as in orc_schur_apply_prec) instead of the ILU smoother.
  */
-int orc_amg_vcycle_schur(const orc_amg* h, int parts, double tau, int fill, int mL, int mU, int nu, int coarse,
-                         int terms, double* x, const double* b) {
+int orc_amg_vcycle_schur(const orc_amg* h, int parts, double tau, int fill, int iface_prec, int mL, int mU, int nu,
+                         int coarse, int terms, double* x, const double* b) {
   if (parts <= 0) return ORC_BADARG;
-  amg_smoother sm = {NULL, NULL, NULL, NULL, NULL, NULL, NULL, mL, mU, nu, coarse, terms, parts, tau, fill, 1, NULL};
+  amg_smoother sm = {NULL, NULL, NULL, NULL, NULL, NULL, NULL, mL, mU, nu, coarse, terms, parts, tau, fill,
+                     iface_prec, 1, NULL};
   return multilevel(h, 0, &sm, b, x);
 }
 
@@ -2002,11 +2005,15 @@ static int schur_binv(const schur_parts* S, const double* f, int mL, int mU, dou
  *   one GMRES iteration on S y = s, S = C - F B^{-1} E, from y = 0:
  *     beta = ||s||, v = s / beta, w = S v, h11 = v.w, h21 = ||w - h11 v||,
  *     Givens rho = hypot(h11, h21), y = (beta h11 / rho^2) v
- *   (no residual of the full system is formed);
+ *   (no residual of the full system is formed); with iface_prec = 1 the
+ *   iteration is right-preconditioned by M = diag(C) (not in the paper, which
+ *   leaves the interface iteration unpreconditioned): w = S M^{-1} v and
+ *   y = (beta h11 / rho^2) M^{-1} v; a zero c_kk gives ORC_ZERO_PIVOT;
  *   x_I = B^{-1} (f - E y);  z = [x_I; y] in the original order.
  */
-int orc_schur_apply(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, int parts, double tau,
-                    int fill, int mL, int mU, const double* r, double* z) {
+int orc_schur_apply_prec(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, int parts, double tau,
+                         int fill, int mL, int mU, int iface_prec, const double* r, double* z) {
+  if (iface_prec != 0 && iface_prec != 1) return ORC_BADARG;
   schur_parts S;
   int st = schur_build(n, ap, ac, av, parts, tau, fill, &S);
   const int64_t nI = S.nI, nG = S.nG;
@@ -2018,30 +2025,44 @@ int orc_schur_apply(int64_t n, const int64_t* ap, const int32_t* ac, const doubl
   double* v = (double*)malloc(sizeof(double) * mg);
   double* w = (double*)malloc(sizeof(double) * mg);
   double* y = (double*)calloc(mg, sizeof(double));
+  double* q = (double*)malloc(sizeof(double) * mg);
   if (st) goto done;
   for (int64_t k = 0; k < nI; ++k) f[k] = r[S.rowsI[k]];
   /* s = g - F B^{-1} f */
   if ((st = schur_binv(&S, f, mL, mU, u))) goto done;
   orc_spmv(nG, 1, S.fp, S.fc, S.fv, u, w);
   for (int64_t k = 0; k < nG; ++k) s[k] = r[S.rowsG[k]] - w[k];
-  /* one GMRES iteration on S y = s */
+  /* one GMRES iteration on S y = s, right-preconditioned by M = diag(C) when
+     iface_prec = 1 (M = I otherwise): Arnoldi on S M^{-1}, y = M^{-1} (coef v) */
   {
     const double beta = sqrt(dot(nG, s, s));
     if (beta > 0.0) {
       for (int64_t k = 0; k < nG; ++k) v[k] = s[k] / beta;
-      orc_spmv(nI, 1, S.ep, S.ec, S.ev, v, t);                 /* E v */
-      if ((st = schur_binv(&S, t, mL, mU, u))) goto done;      /* B^{-1} E v */
-      orc_spmv(nG, 1, S.fp, S.fc, S.fv, u, w);                 /* F B^{-1} E v */
+      for (int64_t k = 0; k < nG; ++k) q[k] = v[k];
+      if (iface_prec == 1)
+        for (int64_t k = 0; k < nG; ++k) {
+          double d = 0.0; /* c_kk */
+          for (int64_t p = S.cp[k]; p < S.cp[k + 1]; ++p)
+            if (S.cc[p] == k) d = S.cv[p];
+          if (d == 0.0) {
+            st = ORC_ZERO_PIVOT;
+            goto done;
+          }
+          q[k] = v[k] / d;                                     /* q = M^{-1} v */
+        }
+      orc_spmv(nI, 1, S.ep, S.ec, S.ev, q, t);                 /* E q */
+      if ((st = schur_binv(&S, t, mL, mU, u))) goto done;      /* B^{-1} E q */
+      orc_spmv(nG, 1, S.fp, S.fc, S.fv, u, w);                 /* F B^{-1} E q */
       double* cvv = (double*)malloc(sizeof(double) * mg);
-      orc_spmv(nG, 1, S.cp, S.cc, S.cv, v, cvv);               /* C v */
-      for (int64_t k = 0; k < nG; ++k) w[k] = cvv[k] - w[k];   /* w = S v */
+      orc_spmv(nG, 1, S.cp, S.cc, S.cv, q, cvv);               /* C q */
+      for (int64_t k = 0; k < nG; ++k) w[k] = cvv[k] - w[k];   /* w = S M^{-1} v */
       free(cvv);
       const double h11 = dot(nG, v, w);
       for (int64_t k = 0; k < nG; ++k) w[k] = w[k] - h11 * v[k];
       const double h21 = sqrt(dot(nG, w, w));
       const double rho = hypot(h11, h21);
       const double coef = rho > 0.0 ? (beta * h11) / (rho * rho) : 0.0;
-      for (int64_t k = 0; k < nG; ++k) y[k] = coef * v[k];
+      for (int64_t k = 0; k < nG; ++k) y[k] = coef * q[k];
     }
   }
   /* x_I = B^{-1} (f - E y) */
@@ -2059,5 +2080,11 @@ done:
   free(v);
   free(w);
   free(y);
+  free(q);
   return st;
+}
+
+int orc_schur_apply(int64_t n, const int64_t* ap, const int32_t* ac, const double* av, int parts, double tau,
+                    int fill, int mL, int mU, const double* r, double* z) {
+  return orc_schur_apply_prec(n, ap, ac, av, parts, tau, fill, mL, mU, 0, r, z);
 }

@@ -156,7 +156,8 @@ def test_two_level_cycle_is_the_two_grid_operator():
     assert relerr(got, x3) < 1e-12
 
 
-def test_two_level_cycle_with_the_schur_smoother_is_the_two_grid_composition():
+@pytest.mark.parametrize("iface_prec", [0, 1])
+def test_two_level_cycle_with_the_schur_smoother_is_the_two_grid_composition(iface_prec):
     """The V-cycle with the ILUT Schur complement smoother on the finest level
     (Sec. 3.1: the smoother of one level of the V-cycle) = one application of
     schur_apply to the residual before and after the exact coarse correction
@@ -177,10 +178,10 @@ def test_two_level_cycle_with_the_schur_smoother_is_the_two_grid_composition():
     b = synth.rhs(n, 1, seed=2)[:, 0]
     x0 = synth.rhs(n, 1, seed=3)[:, 0]
     parts, tau, fill, mL, mU = 3, 1e-3, 6, 3, 2
-    x1 = x0 + oracle.schur_apply(A, b - Ad @ x0, parts, tau, fill, mL, mU)
+    x1 = x0 + oracle.schur_apply(A, b - Ad @ x0, parts, tau, fill, mL, mU, iface_prec)
     x2 = x1 + P @ np.linalg.solve(P.T @ Ad @ P, P.T @ (b - Ad @ x1))
-    x3 = x2 + oracle.schur_apply(A, b - Ad @ x2, parts, tau, fill, mL, mU)
-    got = H.vcycle_schur(x0, b, parts, tau, fill, mL, mU)
+    x3 = x2 + oracle.schur_apply(A, b - Ad @ x2, parts, tau, fill, mL, mU, iface_prec)
+    got = H.vcycle_schur(x0, b, parts, tau, fill, mL, mU, iface_prec=iface_prec)
     assert relerr(got, x3) < 1e-12
     assert oracle.schur_interface(A, parts)[0] > 0
 
