@@ -1336,9 +1336,10 @@ def schur_study(silu, ctx, torch, edge=EDGE, parts=(8, 64), kind="cutcell7", swe
     the same factors.  Then the smoother where the paper places it: on the
     finest level of the Ruge-Stueben V-cycle (strength theta, coarsest <= 400
     rows, l1-Jacobi below), against the same cycle smoothed by ILUT(tau, fill)
-    sweeps on the whole finest level.  A
-    configuration that has not converged after `maxit` iterations is reported
-    once (no second, graph-replayed solve)."""
+    sweeps on the whole finest level.  Both placements again with the
+    smoother's interface iteration right-preconditioned by diag(C) (`diag_*`,
+    not in the paper).  A configuration that has not converged after `maxit`
+    iterations is reported once (no second, graph-replayed solve)."""
     import synth
     A = {"cutcell7": lambda: synth.cutcell7(edge, seed=1), "poisson7": lambda: synth.poisson7(edge),
          "hex27": lambda: synth.hex27(edge, seed=2)}[kind]()
@@ -1393,6 +1394,11 @@ def schur_study(silu, ctx, torch, edge=EDGE, parts=(8, 64), kind="cutcell7", swe
         rec["amg_levels"] = F.amg_stats()["levels"]
         for m in sweeps:
             rec[f"amg_schur_fgmres_{m}_{m}"] = solve(F, silu.PRECOND_AMG_SCHUR, m, m)
+        # the interface iteration right-preconditioned by diag(C) (not in the paper)
+        F.schur_set_interface_prec(silu.SCHUR_IFACE_DIAG)
+        for m in sweeps:
+            rec[f"diag_fgmres_{m}_{m}"] = solve(F, silu.PRECOND_SCHUR, m, m)
+            rec[f"diag_amg_schur_fgmres_{m}_{m}"] = solve(F, silu.PRECOND_AMG_SCHUR, m, m)
         out[f"parts_{p}"] = rec
         del F
     F = silu.ilu_setup(ctx, M, "ilut", tau, fill)

@@ -553,6 +553,20 @@ silu_status silu_schur_setup(silu_ilu F, int parts, double tau, int fill);
 /* x <- x + M^{-1} (b - A x) with the Schur complement smoother (device, one
  * right-hand side, stream-ordered). */
 silu_status silu_schur_smooth(silu_ilu F, double* x, const double* b, int sweeps_L, int sweeps_U);
+/*
+ * The right preconditioner of the smoother's single interface GMRES
+ * iteration: SILU_SCHUR_IFACE_NONE (the default, the paper's unpreconditioned
+ * iteration) or SILU_SCHUR_IFACE_DIAG, M = diag(C): the step becomes
+ * y = ((S q).s / (S q).(S q)) q with q = M^{-1} s, which takes the scale of
+ * each interface row into account (not in the paper; it makes the smoother
+ * converge where the interface rows' scales vary over orders of magnitude).
+ * Requires silu_schur_setup (else SILU_ERR_INVALID_ARG); a zero c_kk ->
+ * SILU_ERR_ZERO_PIVOT for SILU_SCHUR_IFACE_DIAG; other modes ->
+ * SILU_ERR_INVALID_ARG.  Applies to every later application on F (the
+ * stand-alone smoother, SILU_PRECOND_SCHUR and SILU_PRECOND_AMG_SCHUR).
+ */
+typedef enum { SILU_SCHUR_IFACE_NONE = 0, SILU_SCHUR_IFACE_DIAG = 1 } silu_schur_iface;
+silu_status silu_schur_set_interface_prec(silu_ilu F, int mode);
 /* Interior and interface counts, and the interface mark of every row (n
  * int32, may be NULL). */
 silu_status silu_schur_stats(silu_ilu F, int64_t* n_interior, int64_t* n_interface, int32_t* iface);

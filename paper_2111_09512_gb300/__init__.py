@@ -36,6 +36,8 @@ FP64, FP32 = 0, 1
 # silu_precond
 PRECOND_SWEEPS, PRECOND_DIRECT, PRECOND_NONE, PRECOND_AMG, PRECOND_AMG_DIRECT, PRECOND_SCHUR = 0, 1, 2, 3, 4, 5
 PRECOND_AMG_SCHUR = 6
+# silu_schur_iface
+SCHUR_IFACE_NONE, SCHUR_IFACE_DIAG = 0, 1
 # silu_kclass
 K_RESIDUAL, K_SWEEP_L, K_SWEEP_U, K_LEVEL, K_KRYLOV, K_ELEMENTWISE = range(6)
 K_NAMES = ["residual", "sweep_L", "sweep_U", "level", "krylov", "elementwise", "fused"]
@@ -115,6 +117,7 @@ def load():
         "silu_schur_setup": (i32, [vp, i32, dbl, i32]),
         "silu_schur_smooth": (i32, [vp, vp, vp, i32, i32]),
         "silu_schur_stats": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), vp]),
+        "silu_schur_set_interface_prec": (i32, [vp, i32]),
         "silu_ilu_destroy": (None, [vp]),
         "silu_ilu_set_lanes": (i32, [vp, i32, i32, i32]),
         "silu_ctx_profile": (i32, [vp, i32]),
@@ -160,7 +163,7 @@ def exported_symbols():
             "silu_ilu_reserve", "silu_ilu_stats", "silu_ilu_export", "silu_ilu_export_sizes",
             "silu_ilu_export_colscale", "silu_ilu_power_norms", "silu_ilu_dep", "silu_amg_setup", "silu_amg_vcycle", "silu_amg_vcycle_schur",
             "silu_amg_level_ilu", "silu_amg_stats", "silu_amg_export_level", "silu_schur_setup", "silu_schur_smooth",
-            "silu_schur_stats",
+            "silu_schur_stats", "silu_schur_set_interface_prec",
             "silu_ilu_destroy", "silu_ilu_set_lanes", "silu_ctx_profile", "silu_ctx_profile_read",
             "silu_ctx_launch_count", "silu_ctx_check", "silu_ctx_selftest_timeout", "silu_ilu_set_kernel", "silu_ilu_set_direct", "silu_ilu_set_fused", "silu_ilu_layout", "silu_ilu_tune_table", "silu_ctx_set_overlap",
             "silu_ctx_set_l2_reuse",
@@ -491,6 +494,12 @@ class ILU:
         """x <- x + M^{-1}(b - A x) with the Schur complement smoother (device tensors of length n)."""
         _check(self.ctx.handle, load().silu_schur_smooth(self.handle, _ptr(x), _ptr(b), int(sweeps_L),
                                                          int(sweeps_U)), "silu_schur_smooth")
+
+    def schur_set_interface_prec(self, mode: int):
+        """Right preconditioner of the Schur complement smoother's interface GMRES iteration:
+        SCHUR_IFACE_NONE (the paper's) or SCHUR_IFACE_DIAG (diag(C))."""
+        _check(self.ctx.handle, load().silu_schur_set_interface_prec(self.handle, int(mode)),
+               "silu_schur_set_interface_prec")
 
     def schur_stats(self):
         ni, ng = ctypes.c_int64(), ctypes.c_int64()

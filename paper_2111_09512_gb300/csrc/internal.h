@@ -177,6 +177,11 @@ struct SchurState {
   DBuf E_rp, E_ci, E_va, E_t, F_rp, F_ci, F_va, F_t, C_rp, C_ci, C_va, C_t;
   DevCsr E, F, C;
   DBuf f, u, t, xi, g, s, w, y, r, part0, part1;
+  // the interface GMRES iteration's right preconditioner (silu_schur_set_interface_prec):
+  // 0 none (the paper's iteration), 1 diag(C); 1 / c_kk and its scratch vector
+  int iface_prec = 0;
+  bool cdiag_ok = false;
+  DBuf cdinv, q;
   ~SchurState();
 };
 

@@ -8,7 +8,9 @@
 //   f = r_I, g = r_G;  s = g - F B^{-1} f;
 //   one GMRES iteration on S y = s (S = C - F B^{-1} E) from y = 0, which is
 //   the minimal-residual step y = ((S s).s / (S s).(S s)) s, so no residual
-//   of the full system is formed (the saving the paper points out);
+//   of the full system is formed (the saving the paper points out); with the
+//   optional right preconditioner M = diag(C) (not in the paper) the step is
+//   y = ((S q).s / (S q).(S q)) q with q = M^{-1} s;
 //   x_I = B^{-1} (f - E y);  z = [x_I; y] in the original order.
 // Every B^{-1} is the row-scaled ILUT smoother of B from zero: m_L + m_U
 // Richardson sweeps on the sweep kernels.
@@ -94,17 +96,23 @@ void schur_apply(silu_ilu F, const double* r, double* z, int mL, int mU) {
     } else {
       CK(cudaMemcpyAsync(s, g, sizeof(double) * (size_t)nG, cudaMemcpyDeviceToDevice, st));
     }
-    // w = S s = C s - F B^{-1} E s
-    op(F, S.C, nullptr, s, w, EPI_SPMV);
+    // the direction q: s, or M^{-1} s with M = diag(C)
+    double* q = s;
+    if (S.iface_prec == 1) {
+      q = S.q.as<double>();
+      LAUNCH(F->ctx, SILU_K_ELEMENTWISE, launch_scale(nG, 1, 1, s, false, S.cdinv.as<double>(), q, false, st));
+    }
+    // w = S q = C q - F B^{-1} E q
+    op(F, S.C, nullptr, q, w, EPI_SPMV);
     if (nI > 0) {
-      op(F, S.E, nullptr, s, t, EPI_SPMV);
+      op(F, S.E, nullptr, q, t, EPI_SPMV);
       smooth_chunk(FB, u, t, 1, 1, 0, mL, mU, true);
-      op(F, S.F, w, u, g, EPI_STORE);  // g is free now: g = C s - F u
+      op(F, S.F, w, u, g, EPI_STORE);  // g is free now: g = C q - F u
       std::swap(g, w);
     }
     LAUNCH(F->ctx, SILU_K_KRYLOV, launch_dot_part(nG, w, s, S.part0.as<double>(), st));
     LAUNCH(F->ctx, SILU_K_KRYLOV, launch_dot_part(nG, w, w, S.part1.as<double>(), st));
-    LAUNCH(F->ctx, SILU_K_KRYLOV, launch_mr_step(nG, S.part0.as<double>(), S.part1.as<double>(), s, y, st));
+    LAUNCH(F->ctx, SILU_K_KRYLOV, launch_mr_step(nG, S.part0.as<double>(), S.part1.as<double>(), q, y, st));
   }
   if (nI > 0) {
     if (nG > 0)
@@ -159,6 +167,16 @@ silu_status silu_schur_setup(silu_ilu F, int parts, double tau, int fill) {
     submatrix(A, rowsI, mapG, E);
     submatrix(A, rowsG, mapI, Fm);
     submatrix(A, rowsG, mapG, C);
+    // 1 / c_kk for the optional diag(C) preconditioner of the interface iteration
+    std::vector<double> cdinv((size_t)S->nG, 0.0);
+    S->cdiag_ok = true;
+    for (int64_t k = 0; k < S->nG; ++k) {
+      double d = 0.0;
+      for (int64_t p = C.rp[k]; p < C.rp[k + 1]; ++p)
+        if (C.ci[p] == k) d = C.va[p];
+      if (d == 0.0) S->cdiag_ok = false;
+      cdinv[(size_t)k] = d != 0.0 ? 1.0 / d : 0.0;
+    }
     silu_status st = silu_mat_create(ctx, B.n, B.nnz(), B.rp.data(), B.ci.data(), B.va.data(), &S->Bmat);
     if (st == SILU_OK) st = ilu_setup(ctx, S->Bmat, SILU_ILUT, tau, fill, SILU_SCALE_ROW, F->prec, &S->FB);
     if (st != SILU_OK) return st;
@@ -176,8 +194,9 @@ silu_status silu_schur_setup(silu_ilu F, int parts, double tau, int fill) {
       const size_t bg = sizeof(double) * (size_t)std::max<int64_t>(S->nG, 1);
       for (DBuf* d : {&S->f, &S->u, &S->t, &S->xi})
         if (e == cudaSuccess) e = d->ensure(bi);
-      for (DBuf* d : {&S->g, &S->s, &S->w, &S->y})
+      for (DBuf* d : {&S->g, &S->s, &S->w, &S->y, &S->q})
         if (e == cudaSuccess) e = d->ensure(bg);
+      if (e == cudaSuccess && S->nG > 0) e = silu::upload(S->cdinv, cdinv.data(), cdinv.size(), s);
       if (e == cudaSuccess) e = S->r.ensure(sizeof(double) * (size_t)std::max<int64_t>(n, 1));
       if (e == cudaSuccess) e = S->part0.ensure(sizeof(double) * 1024);
       if (e == cudaSuccess) e = S->part1.ensure(sizeof(double) * 1024);
@@ -214,6 +233,21 @@ silu_status silu_schur_smooth(silu_ilu F, double* x, const double* b, int sweeps
     LAUNCH(ctx, SILU_K_ELEMENTWISE, silu::launch_addx(n, 1, 1, z, false, nullptr, x, true, s));
   } catch (const CudaFail& f) {
     return silu::cuda_err(ctx, f.e, f.what);
+  }
+  return SILU_OK;
+}
+
+silu_status silu_schur_set_interface_prec(silu_ilu F, int mode) {
+  if (!F) return SILU_ERR_INVALID_ARG;
+  silu_ctx ctx = F->ctx;
+  if (!F->schur) return silu::set_err(ctx, SILU_ERR_INVALID_ARG, "no Schur complement smoother (silu_schur_setup)");
+  if (mode != 0 && mode != 1) return silu::set_err(ctx, SILU_ERR_INVALID_ARG, "mode must be 0 or 1");
+  if (mode == 1 && !F->schur->cdiag_ok)
+    return silu::set_err(ctx, SILU_ERR_ZERO_PIVOT, "an interface row has a zero diagonal entry");
+  if (F->schur->iface_prec != mode) {
+    F->schur->iface_prec = mode;
+    F->ws.drop_graphs();  // captured FGMRES iterations hold the other form
+    F->config_gen++;
   }
   return SILU_OK;
 }

@@ -367,3 +367,24 @@ def test_fp32_factors_on_every_ilu_level(silu, ctx):
     assert st == silu.OK and rel <= 1e-10, (st, its, rel)
     r = oracle.residual(A, host(xs).reshape(n, 1), b.reshape(n, 1))
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10
+
+
+def test_schur_smoothed_cycle_with_the_preconditioned_interface_step(silu, ctx):
+    """The V-cycle whose finest level is smoothed by the Schur complement
+    smoother with the diag(C)-preconditioned interface iteration, against the
+    oracle's, three successive cycles at 1e-12 on a cut-cell matrix."""
+    A = synth.cutcell7(23, 21, 19, seed=3)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+    F.amg_setup(theta=0.25, max_levels=12, coarse_size=60, jacobi_sweeps=1)
+    F.schur_setup(3, 1e-3, 8)
+    F.schur_set_interface_prec(silu.SCHUR_IFACE_DIAG)
+    H = oracle.AMG(A, theta=0.25, max_levels=12, coarse_size=60)
+    b = synth.rhs(n, 1, seed=8)[:, 0]
+    x = synth.rhs(n, 1, seed=9)[:, 0] * 0.5
+    xd, bd = dev(x.copy()), dev(b)
+    for cycle in range(3):
+        x = H.vcycle_schur(x, b, 3, 1e-3, 8, 2, 4, iface_prec=1)
+        F.amg_vcycle_schur(xd, bd, 2, 4)
+        ctx.check()
+        assert relerr(host(xd), x) < 1e-12, cycle

@@ -46,18 +46,23 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("iface_prec", [0, 1])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_schur_smoother_matches_oracle(silu, ctx, case):
+def test_schur_smoother_matches_oracle(silu, ctx, case, iface_prec):
+    """The smoother with the paper's unpreconditioned interface iteration and
+    with the diag(C) right preconditioner, against the oracle's, from zero and
+    from a nonzero iterate."""
     name, gen, parts, tau, fill, (mL, mU) = case
     A = gen()
     n = len(A[0]) - 1
     F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
     F.schur_setup(parts, tau, fill)
+    F.schur_set_interface_prec(iface_prec)
     b = synth.rhs(n, 1, seed=3)[:, 0]
     x0 = synth.rhs(n, 1, seed=4)[:, 0] * 0.5
     for start in (np.zeros(n), x0):
         r = oracle.residual(A, start.reshape(n, 1), b.reshape(n, 1))[:, 0]
-        want = start + oracle.schur_apply(A, r, parts, tau, fill, mL, mU)
+        want = start + oracle.schur_apply(A, r, parts, tau, fill, mL, mU, iface_prec)
         x = dev(start.copy())
         F.schur_smooth(x, dev(b), mL, mU)
         ctx.check()
@@ -88,3 +93,29 @@ def test_fgmres_with_schur_preconditioner(silu, ctx, prec):
     assert st == silu.OK and rel <= 1e-10, (st, its, rel)
     r = oracle.residual(A, host(x).reshape(n, 1), b.reshape(n, 1))
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10
+
+
+def test_fgmres_on_cut_cell_with_the_preconditioned_interface_step(silu, ctx):
+    """With the interface iteration right-preconditioned by diag(C) the
+    smoother makes FGMRES converge on a cut-cell matrix, where the paper's
+    unpreconditioned iteration stalls (checked here over the same number of
+    iterations)."""
+    A = synth.cutcell7(31, 27, 23, seed=1)
+    n = len(A[0]) - 1
+    F = silu.ilu_setup(ctx, silu.Matrix(ctx, *A), "ilu0")
+    F.schur_setup(4, 1e-3, 10)
+    b = synth.rhs(n, 1, seed=6)[:, 0]
+    its, xs = {}, {}
+    for mode in (silu.SCHUR_IFACE_DIAG, silu.SCHUR_IFACE_NONE):
+        F.schur_set_interface_prec(mode)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        st, k, rel = silu.fgmres_solve(F, x, dev(b), tol=1e-10, restart=30, maxit=1500, sweeps_L=3, sweeps_U=3,
+                                       precond=silu.PRECOND_SCHUR)
+        its[mode], xs[mode] = (st, k, rel), host(x)
+    st, k, rel = its[silu.SCHUR_IFACE_DIAG]
+    assert st == silu.OK and rel <= 1e-10, its
+    r = oracle.residual(A, xs[silu.SCHUR_IFACE_DIAG].reshape(n, 1), b.reshape(n, 1))
+    assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.5e-10
+    assert its[silu.SCHUR_IFACE_NONE][0] != silu.OK or its[silu.SCHUR_IFACE_NONE][1] > k, its
+    with pytest.raises(silu.SiluError):
+        F.schur_set_interface_prec(2)

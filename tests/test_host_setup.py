@@ -11,6 +11,7 @@ import pytest
 import oracle
 import paper_2111_09512_gb300 as silu
 import synth
+from _helpers import csr_from_dense
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -459,3 +460,26 @@ def test_amg_ilu_levels_factors_match_oracle(ctx, gen, kind, tau, fill):
     F.amg_level_ilu(1)
     with pytest.raises(silu.SiluError):
         F.amg_level_ilu(2)
+
+
+def test_schur_interface_prec_modes(ctx):
+    """silu_schur_set_interface_prec: refused before silu_schur_setup and for
+    an unknown mode; the diag(C) mode is refused when an interface row has no
+    diagonal entry (its c_kk is zero), the plain mode is always accepted."""
+    A = synth.cutcell7(8, 7, 6, seed=2)
+    F = silu.ILU(silu.Matrix(ctx, *A), "ilu0")
+    with pytest.raises(silu.SiluError):
+        F.schur_set_interface_prec(silu.SCHUR_IFACE_DIAG)
+    F.schur_setup(3, 1e-3, 8)
+    F.schur_set_interface_prec(silu.SCHUR_IFACE_DIAG)
+    F.schur_set_interface_prec(silu.SCHUR_IFACE_NONE)
+    with pytest.raises(silu.SiluError) as e:
+        F.schur_set_interface_prec(3)
+    assert e.value.status == silu.ERR_INVALID_ARG
+    M = np.array([[2.0, 1.0], [1.0, 0.0]])  # two parts: both rows interface, C = M, c_11 = 0
+    G = silu.ILU(silu.Matrix(ctx, *csr_from_dense(M)), "ilu0")
+    G.schur_setup(2, 0.0, 2)
+    with pytest.raises(silu.SiluError) as e:
+        G.schur_set_interface_prec(silu.SCHUR_IFACE_DIAG)
+    assert e.value.status == silu.ERR_ZERO_PIVOT
+    G.schur_set_interface_prec(silu.SCHUR_IFACE_NONE)
