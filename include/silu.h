@@ -519,9 +519,10 @@ silu_status silu_amg_vcycle(silu_ilu F, double* x, const double* b, int sweeps_L
  */
 silu_status silu_amg_vcycle_schur(silu_ilu F, double* x, const double* b, int sweeps_L, int sweeps_U);
 /*
- * The factor object that smooths AMG level `level` with the ILU smoother:
- * F itself for level 0, the row-scaled factorisation of A_l for levels
- * 1 .. ilu_levels - 1 (silu_amg_params).  *out is borrowed: valid until the
+ * The factor object that smooths AMG level `level` with the ILU smoother
+ * (Sec. 6: ILU smoothing from the finest level down): F itself for level 0,
+ * the row-scaled factorisation of A_l for levels 1 .. ilu_levels - 1
+ * (silu_amg_params).  *out is borrowed: valid until the
  * next silu_amg_setup on F or F's destruction, never passed to
  * silu_ilu_destroy.  Queries (silu_ilu_stats, silu_ilu_export) work on it.
  * A level without one, or no hierarchy -> SILU_ERR_INVALID_ARG.
