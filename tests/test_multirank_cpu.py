@@ -52,3 +52,24 @@ def test_reference_arm_nonzero_rank_exits_without_work():
                         "--warmup", "3"], env=env, capture_output=True, text=True, timeout=120)
     assert p.returncode == 0
     assert p.stdout.strip() == ""
+
+
+def test_reference_arm_rank0_json_line():
+    """Rank 0 of the reference arm times the oracle on a bounded slab of the
+    headline workload and prints one JSON line with the main arm's metric,
+    unit and direction, a cpu_baseline describing the run and an e2e block
+    that moves no bytes."""
+    import json
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], env=env, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "Richardson ILU-apply GB/s" and d["unit"] == "GB/s"
+    assert d["higher_is_better"] is True and d["value"] > 0 and d["dtype"] == "f64" and d["n_gpus"] == 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("cutcell7-128^3 ILUT(1e-3,10) FP64")
